@@ -1,0 +1,148 @@
+"""The oracle's pins are not vacuous: each plausible mistake planted here in the
+oracle (on the CPU, by monkeypatching) makes at least one pin fail."""
+import numpy as np
+import pytest
+
+from oracle import quadrature, sdc, sht, swe
+
+import test_oracle_quadrature as T_q
+import test_oracle_sdc as T_sdc
+import test_oracle_sht as T_sht
+import test_oracle_swe as T_swe
+
+
+def _fails(fn, *args):
+    with pytest.raises(AssertionError):
+        fn(*args)
+
+
+def _vector_analysis_factory(sign_div_h=-1.0, sign_curl_h=1.0):
+    def vector_analysis(self, X, Y, a):
+        wt = self.w / (1.0 - self.mu ** 2)
+        Xm, Ym = self.fourier_analysis(X), self.fourier_analysis(Y)
+        im = 1j * self.m
+        div = (im * self.legendre_analysis(Xm, self.P, wt) + sign_div_h * self.legendre_analysis(Ym, self.H, wt)) / a
+        curl = (im * self.legendre_analysis(Ym, self.P, wt) + sign_curl_h * self.legendre_analysis(Xm, self.H, wt)) / a
+        return sht.zero_m0_imag(self, div), sht.zero_m0_imag(self, curl)
+    return vector_analysis
+
+
+def test_curl_sign_mistake_is_caught(monkeypatch):
+    monkeypatch.setattr(sht.Grid, "vector_analysis", _vector_analysis_factory(sign_curl_h=-1.0))
+    _fails(T_sht.test_solid_body_rotation_vorticity)
+    _fails(T_swe.test_steady_zonal_flow_is_exact_equilibrium)
+
+
+def test_div_sign_mistake_is_caught(monkeypatch):
+    monkeypatch.setattr(sht.Grid, "vector_analysis", _vector_analysis_factory(sign_div_h=1.0))
+    _fails(T_sht.test_laplacian_eigenfunction_through_gradient, 10, 32, 16)
+    _fails(T_swe.test_tilted_rigid_rotation_preserves_degree_and_is_skew)
+
+
+def test_missing_im_in_vector_synthesis_is_caught(monkeypatch):
+    def vector_synthesis(self, psi, chi, a):
+        U_m = (self.legendre_synthesis(chi, self.P) - self.legendre_synthesis(psi, self.H)) / a
+        V_m = (self.legendre_synthesis(psi, self.P) + self.legendre_synthesis(chi, self.H)) / a
+        return self.fourier_synthesis(U_m), self.fourier_synthesis(V_m)
+    monkeypatch.setattr(sht.Grid, "vector_synthesis", vector_synthesis)
+    _fails(T_sht.test_laplacian_eigenfunction_through_gradient, 10, 32, 16)
+
+
+def test_kinetic_energy_factor_mistake_is_caught(monkeypatch):
+    orig = swe.SWE.explicit_rhs
+
+    def rhs(self, x):
+        out = orig(self, x)
+        g = self.grid
+        psi, chi = self.inverse_laplacian(x[1]), self.inverse_laplacian(x[2])
+        U, V = g.vector_synthesis(psi, chi, self.p.a)
+        E = (U * U + V * V) / (2.0 * (1.0 - g.mu[:, None] ** 2))
+        out[2] = out[2] - self.L * g.analysis(E)      # doubles the V.V/2 term
+        return out
+    monkeypatch.setattr(swe.SWE, "explicit_rhs", rhs)
+    _fails(T_swe.test_steady_zonal_flow_is_exact_equilibrium)
+
+
+def test_coriolis_factor_mistake_is_caught(monkeypatch):
+    monkeypatch.setattr(swe, "Params", swe.Params)
+    orig = swe.SWE.explicit_rhs
+
+    def rhs(self, x):
+        p = self.p
+        self.p = swe.Params(p.a, p.omega / 2, p.g, p.phibar, p.nu)   # f = Omega mu
+        try:
+            return orig(self, x)
+        finally:
+            self.p = p
+    monkeypatch.setattr(swe.SWE, "explicit_rhs", rhs)
+    _fails(T_swe.test_coriolis_is_linear_part_closed_form, 10, 32, 16)
+    _fails(T_swe.test_steady_zonal_flow_is_exact_equilibrium)
+
+
+def test_implicit_solve_sign_mistake_is_caught(monkeypatch):
+    def solve(self, b, alpha):
+        p, L = self.p, self.L
+        c = 1.0 - alpha * p.nu * L
+        zeta = b[1] / c
+        phi = (c * b[0] + alpha * p.phibar * b[2]) / (c * c - alpha * alpha * p.phibar * L)
+        delta = (b[2] - alpha * L * phi) / c
+        return np.stack([phi, zeta, delta])
+    monkeypatch.setattr(swe.SWE, "implicit_solve", solve)
+    _fails(T_swe.test_implicit_solve_matches_dense_solve)
+
+
+def test_transposed_lu_factor_is_caught(monkeypatch):
+    orig = quadrature.lu_implicit_matrix
+
+    def upper(Q):
+        QI = orig(Q)
+        QI[1:, 1:] = QI[1:, 1:].T
+        return QI
+    monkeypatch.setattr(quadrature, "lu_implicit_matrix", upper)
+    _fails(T_q.test_lu_trick_three_nodes_by_hand)
+    _fails(T_q.test_lu_trick_nilpotent, 5)
+
+
+def test_wrong_fas_sign_is_caught(monkeypatch):
+    orig = sdc.collocation_operator
+
+    def bad(lev, dt, Theta, FI, FE):
+        n = lev.M + 1
+        return [Theta[m] + dt * sum(lev.Q[m, j] * (FI[j] + FE[j]) for j in range(n)) for m in range(n)]
+    monkeypatch.setattr(sdc, "collocation_operator", bad)
+    _fails(T_sdc.test_mlsdc_fixed_point_is_not_moved)
+
+
+def test_dropped_interpolation_of_F_is_caught(monkeypatch):
+    """Step D without the F corrections: the fine F values go stale, so MLSDC
+    with an identical coarse level no longer equals SDC."""
+    src_interp = sdc.mlsdc_step
+
+    def no_f_interp(fine, coarse, u0, dt, n_iter, n_coarse_sweeps=1, return_nodes=False):
+        pf, pc = fine.prob, coarse.prob
+        Pi_cf = quadrature.lagrange_matrix(fine.t, coarse.t)
+        Pi_fc = quadrature.lagrange_matrix(coarse.t, fine.t)
+        Mf, Mc = fine.M, coarse.M
+        rn = lambda v, i: pf.restrict(sum(Pi_cf[i, j] * v[j] for j in range(Mf + 1)), pc)
+        ip = lambda d, m: pf.interpolate(sum(Pi_fc[m, i] * d[i] for i in range(Mc + 1)), pc)
+        Th_f, FI_f, FE_f = sdc.spread(fine, u0)
+        u0c = rn(Th_f, 0)
+        Th_c, FI_c, FE_c = [u0c] * (Mc + 1), [pc.implicit_rhs(u0c)] * (Mc + 1), [pc.explicit_rhs(u0c)] * (Mc + 1)
+        for _ in range(n_iter):
+            Th_f, FI_f, FE_f = sdc.sweep(fine, dt, Th_f, FI_f, FE_f)
+            Th_c, FI_c, FE_c = list(Th_c), list(FI_c), list(FE_c)
+            for m in range(1, Mc + 1):
+                Th_c[m] = rn(Th_f, m)
+                FI_c[m], FE_c[m] = pc.implicit_rhs(Th_c[m]), pc.explicit_rhs(Th_c[m])
+            Th_s = list(Th_c)
+            A_c = sdc.collocation_operator(coarse, dt, Th_c, FI_c, FE_c)
+            A_f = sdc.collocation_operator(fine, dt, Th_f, FI_f, FE_f)
+            tau = [A_c[i] - rn(A_f, i) for i in range(Mc + 1)]
+            for _s in range(n_coarse_sweeps):
+                Th_c, FI_c, FE_c = sdc.sweep(coarse, dt, Th_c, FI_c, FE_c, tau)
+            dT = [Th_c[i] - Th_s[i] for i in range(Mc + 1)]
+            Th_f = [Th_f[0]] + [Th_f[m] + ip(dT, m) for m in range(1, Mf + 1)]
+        return (Th_f, FI_f, FE_f) if return_nodes else Th_f[-1]
+    monkeypatch.setattr(sdc, "mlsdc_step", no_f_interp)
+    _fails(T_sdc.test_mlsdc_with_identical_levels_is_sdc)
+    assert src_interp is not sdc.mlsdc_step
