@@ -1,0 +1,375 @@
+#!/usr/bin/env python
+"""Benchmark: MLSDC-SH time steps per second at T170/T85 on one GB300.
+
+Workload (one "step" = one MLSDC time step, the whole hot path): two-level
+MLSDC, fine T170 on a 512 x 256 Gaussian grid with 5 Gauss-Lobatto nodes,
+coarse T85 on 256 x 128 with 3 nodes, 4 iterations of 1 fine + 2 coarse
+sweeps, dt = 150 s, seeded n^-3/2 synthetic state (the paper's test cases are
+not used).  Each step is one CUDA-graph replay of the library's kernels.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision P] [--impl ours|reference]
+
+Timing: W untimed warm-up steps; then K steps, each bracketed by CUDA events
+on the launching stream, with a 256 MB buffer write between steps (L2 is
+129 MB, so every step starts from a cold L2); value = K / sum(step times).
+Under torchrun every rank runs its own independent member (replicas; no
+collective on the data path); value = total steps / max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(Rf=170, If=512, Jf=256, Rc=85, Ic=256, Jc=128, nf=5, nc=3, n_iter=4, n_coarse=2, dt=150.0,
+                total_steps=400)
+WORKLOAD_NAME = ("MLSDC(5,3,4,1/2) fine T170 512x256 / coarse T85 256x128, 1 fine + 2 coarse sweeps per "
+                 "iteration, dt 150 s, seeded n^-3/2 spectra")
+METRIC = "MLSDC-SH steps/s at T170 vs plain FP64 GPU path at <=1e-6 rel error; SH TFLOP/s"
+
+
+def sh_flops_per_eval(R, I, J):
+    """Algorithmic SH FLOPs of one F_E evaluation: Legendre = N_c * J * 26
+    (12 synthesis + 14 analysis real columns, 2 flops per multiply-add over
+    J/2 hemispheric pairs), FFT = 9 real FFTs per latitude x 2.5 I log2 I."""
+    nc = (R + 1) * (R + 2) // 2
+    return nc * J * 26 + 9 * J * 2.5 * I * math.log2(I)
+
+
+def legendre_stage_flops(R, J, stage):
+    nc = (R + 1) * (R + 2) // 2
+    return nc * (J // 2) * 2 * (12 if stage == 0 else 14)
+
+
+def grid_stage_flops(R, I, J):
+    return 9 * J * 2.5 * I * math.log2(I)
+
+
+def evals_per_step(w):
+    f = 1 + w["n_iter"] * (w["nf"] - 1)
+    c = 1 + w["n_iter"] * ((w["nc"] - 1) + w["n_coarse"] * (w["nc"] - 1))
+    return f, c
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.idx = gpu_index
+        self.out = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            txt, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            txt, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in txt.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if os.environ.get("MLSDC_BENCH_GLOO") is None else "gloo")
+    return ws, rank, local
+
+
+def barrier_max(value: float, ws: int, device):
+    if ws == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.barrier()
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def measured_fp64_tflops(torch, device) -> float:
+    """cuBLAS DGEMM throughput (the FP64 denominator; no FP64 peak is recorded
+    in the measured-peaks file)."""
+    n = 4096
+    a = torch.randn(n, n, dtype=torch.float64, device=device)
+    b = torch.randn(n, n, dtype=torch.float64, device=device)
+    for _ in range(2):
+        torch.matmul(a, b)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    best = 1e30
+    for _ in range(3):
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        e1.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    return 2 * n ** 3 / (best * 1e-3) / 1e12
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def traffic_for(kernel: str):
+    """DRAM bytes per launch from a committed ncu capture, if the kernel's
+    sources have not changed since (profiles/traffic.json)."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            d = json.load(f)
+    except OSError:
+        return None
+    ent = d.get(kernel)
+    if not ent:
+        return None
+    if ent.get("src_sha") != sources_sha():
+        return None
+    return ent.get("bytes_per_launch")
+
+
+def sources_sha() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1805_07923_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".h", ".cuh")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def cpu_baseline(steps_cap_s: float = 25.0):
+    """The float64 oracle as it stands, timed on this host for a bounded sample."""
+    from oracle import sdc as osdc
+    from oracle.swe import SWE, Params
+    from paper_1805_07923_gb300 import inputs
+    w = WORKLOAD
+    t0 = time.perf_counter()
+    fine = osdc.Level(SWE(w["Rf"], w["If"], w["Jf"], Params()), w["nf"])
+    coarse = osdc.Level(SWE(w["Rc"], w["Ic"], w["Jc"], Params()), w["nc"])
+    setup = time.perf_counter() - t0
+    u = inputs.initial_state(w["Rf"])
+    n, t = 0, 0.0
+    while n == 0 or (t < steps_cap_s and n < 8):
+        t1 = time.perf_counter()
+        u = osdc.mlsdc_step(fine, coarse, u, w["dt"], w["n_iter"], w["n_coarse"])
+        t += time.perf_counter() - t1
+        n += 1
+    return {"value": n / t, "unit": "steps/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{n} MLSDC steps of the same workload (float64 numpy oracle, setup {setup:.1f} s untimed)"}
+
+
+def run_reference(args):
+    ws, rank, local = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0
+    if rank != 0:
+        return
+    from oracle import sdc as osdc
+    from oracle.swe import SWE, Params
+    from paper_1805_07923_gb300 import inputs
+    w = WORKLOAD
+    fine = osdc.Level(SWE(w["Rf"], w["If"], w["Jf"], Params()), w["nf"])
+    coarse = osdc.Level(SWE(w["Rc"], w["Ic"], w["Jc"], Params()), w["nc"])
+    u = inputs.initial_state(w["Rf"])
+    # bounded sample: each timed "step" is one full oracle MLSDC step; the
+    # number of steps is capped so the run ends within a few minutes
+    t = time.perf_counter()
+    u = osdc.mlsdc_step(fine, coarse, u, w["dt"], w["n_iter"], w["n_coarse"])
+    first = time.perf_counter() - t
+    k = max(1, min(args.steps, int(90.0 / max(first, 1e-3))))
+    t = time.perf_counter()
+    for _ in range(k):
+        u = osdc.mlsdc_step(fine, coarse, u, w["dt"], w["n_iter"], w["n_coarse"])
+    el = time.perf_counter() - t
+    v = k / el
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "steps/s", "n_gpus": args.gpus,
+            "steps": k, "warmup": 1, "ms_per_step": 1e3 * el / k, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD_NAME, "sample": f"{k} of {args.steps} requested steps"},
+            "cpu_baseline": {"value": v, "unit": "steps/s", "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": f"{k} oracle MLSDC steps after 1 warm-up step"},
+            "e2e": {"value": v, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "tf32", "bf16x3", "fp32"])
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    args.warmup = max(3, args.warmup)
+
+    import numpy as np
+    import torch
+
+    from paper_1805_07923_gb300 import inputs
+    from paper_1805_07923_gb300 import mlsdc as M
+
+    ws, rank, local = dist_init()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = WORKLOAD
+    prec = args.precision
+    pf = M.Plan(w["Rf"], w["If"], w["Jf"], prec)
+    pc = M.Plan(w["Rc"], w["Ic"], w["Jc"], prec)
+    lf, lc = M.Level(pf, w["nf"]), M.Level(pc, w["nc"])
+    ml = M.MLSDC(lf, lc)
+    u0 = inputs.initial_state(w["Rf"], seed=1805 + rank)
+    state = torch.from_numpy(u0).to(dev)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    for _ in range(args.warmup):
+        M.mlsdc_step(ml, state, w["dt"], w["n_iter"], w["n_coarse"], use_graph=True)
+    torch.cuda.synchronize()
+    launches_per_step = ml.launch_count()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    K = args.steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    for k in range(K):
+        flush.zero_()
+        ev[k][0].record(stream)
+        M.mlsdc_step(ml, state, w["dt"], w["n_iter"], w["n_coarse"], use_graph=True)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = barrier_max(sum(step_ms), ws, dev)
+    value = ws * K / (total_ms * 1e-3)
+
+    # end to end through the public API with host buffers: H2D of the state from
+    # pinned memory, the step, D2H of the result, every step
+    host_in = torch.from_numpy(u0).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    Ke = min(K, 100)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(Ke):
+        state.copy_(host_in, non_blocking=True)
+        M.mlsdc_step(ml, state, w["dt"], w["n_iter"], w["n_coarse"], use_graph=True)
+        host_out.copy_(state, non_blocking=True)
+    e1.record(stream)
+    e1.synchronize()
+    e2e_ms = barrier_max(e0.elapsed_time(e1), ws, dev)
+    clk = clocks.stop()
+    nbytes = host_in.numel() * host_in.element_size()
+
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return
+
+    # roofline of the dominant kernel (stage timing with CUDA events on this stream)
+    FE = torch.empty_like(state)
+    x0 = torch.from_numpy(u0).to(dev)
+    fine_ms = M.mlsdc_profile_rhs(pf, lf.prm, x0, FE, reps=50)
+    coarse_ms = M.mlsdc_profile_rhs(pc, lc.prm, torch.from_numpy(np.ascontiguousarray(inputs.truncate(u0, w["Rf"], w["Rc"]))).to(dev),
+                                    torch.empty((3, pc.nc), dtype=torch.complex128, device=dev), reps=50)
+    nfe, nce = evals_per_step(w)
+    names = ["legendre_synthesis", "grid_fft_products", "legendre_analysis"]
+    shares = []
+    for lvl, ms, (R, I, J), cnt in (("T170", fine_ms, (w["Rf"], w["If"], w["Jf"]), nfe),
+                                    ("T85", coarse_ms, (w["Rc"], w["Ic"], w["Jc"]), nce)):
+        for s in range(3):
+            flops = legendre_stage_flops(R, J, s) if s != 1 else grid_stage_flops(R, I, J)
+            shares.append((ms[s] * cnt, lvl, names[s], ms[s], flops))
+    shares.sort(reverse=True)
+    step_ms_mean = total_ms / K
+    top = shares[0]
+    peaks = load_peaks()
+    kern_names = {"legendre_synthesis": "k_synth_rhs_f64", "grid_fft_products": "k_grid_rhs_f64",
+                  "legendre_analysis": "k_anal_rhs_f64"}
+    if prec == "fp64":
+        peak = measured_fp64_tflops(torch, dev)
+        roof = {"bound": "alu", "achieved": top[4] / (top[3] * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+                "peak_source": "measured cuBLAS DGEMM on this GPU (float64 FMA pipe)"}
+    else:
+        peak = peaks.get("bf16_tflops", 1925.0)
+        roof = {"bound": "tensor", "achieved": top[4] / (top[3] * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+                "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst)"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = traffic_for(f"{top[1]}:{kern_names[top[2]]}")
+    roof["kernel"] = f"{top[2]} ({kern_names[top[2]]}) at {top[1]}"
+    roof["kernel_ms"] = top[3]
+    roof["share_of_step"] = top[0] / step_ms_mean
+
+    sh_flops = nfe * sh_flops_per_eval(w["Rf"], w["If"], w["Jf"]) + nce * sh_flops_per_eval(w["Rc"], w["Ic"], w["Jc"])
+    line = {
+        "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": ws, "steps": K, "warmup": args.warmup,
+        "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if prec == "fp64" else f"f64+{prec}", "data": "synthetic",
+        "config": {"workload": WORKLOAD_NAME, "precision": prec, "steps_of_run": w["total_steps"],
+                   "l2": "flushed between timed steps (256 MB write)", "graph": "one CUDA graph per step"},
+        "sh_tflops": sh_flops * value / ws / 1e12,
+        "gpu_launches": launches_per_step * K,
+        "e2e": {"value": ws * Ke / (e2e_ms * 1e-3), "unit": "steps/s", "h2d_bytes_per_step": nbytes,
+                "d2h_bytes_per_step": nbytes},
+        "roofline": roof,
+        "stage_ms": {"T170": dict(zip(names, fine_ms)), "T85": dict(zip(names, coarse_ms))},
+        "clocks": clk,
+    }
+    if ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,204 @@
+/*
+ * mlsdc_sh.h -- C ABI of the GB300 (sm_103a) MLSDC-SH library.
+ *
+ * The library integrates the rotating shallow-water equations in
+ * vorticity-divergence-geopotential form (Hamon, Schreiber, Minion, Sec. 2,
+ * Eqs. geopotential_equation, vorticity_equation, divergence_equation) with
+ * a global spherical-harmonic (SH) discretisation (Sec. 3) and IMEX
+ * spectral deferred corrections, single-level (Sec. 4.2) or two-level MLSDC
+ * (Sec. 4.3, Algorithm 1).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Spectral field at triangular truncation R (Sec. 3, Eq. spectral_space with
+ * r = m the zonal wavenumber and s = n the total degree, m >= 0 only):
+ *   N_c = (R+1)(R+2)/2 complex coefficients xi^m_n, 0 <= m <= n <= R, stored
+ *   m-major (for m = 0..R: n = m..R, index m(R+1) - m(m-1)/2 + (n-m)), each
+ *   complex as two consecutive doubles (re, im).  Im xi^0_n is zero.
+ *   Legendre functions are orthonormal on [-1, 1] without Condon-Shortley
+ *   phase, so a field is f = sum_n xi^0_n P^0_n + 2 Re sum_{m>=1} xi^m_n P^m_n e^{i m lambda}.
+ * State: [3][N_c] complex in the order (Phi', zeta, delta), Phi' = Phi - Phibar.
+ * Grid field: [J][I] doubles, latitude-major from north (mu_0 > 0) to south,
+ *   longitude lambda_i = 2 pi i / I contiguous.
+ * Node arrays ("space-time vectors", Sec. 4.2): [M+1][3][N_c] complex.
+ *
+ * Memory: every data pointer is a DEVICE pointer owned by the caller, 16-byte
+ * aligned, contiguous.  Plans, levels and MLSDC objects own their tables and
+ * scratch (allocated at creation, freed at destroy).  Calls are asynchronous
+ * on the given CUDA stream (NULL = legacy default stream); calls that share a
+ * plan, level or MLSDC object must be ordered on one stream, since they share
+ * that object's scratch.  No exception crosses the ABI; each call returns a
+ * status.  Argument errors are detected before any launch; a CUDA error is
+ * reported as MLSDC_ERR_CUDA with its text in mlsdc_last_error().
+ */
+#ifndef MLSDC_SH_H
+#define MLSDC_SH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int mlsdc_status;
+#define MLSDC_OK 0
+#define MLSDC_ERR_INVALID (-1)     /* bad size, null pointer, unsupported configuration */
+#define MLSDC_ERR_CUDA (-2)        /* a CUDA runtime call or launch failed */
+#define MLSDC_ERR_NONFINITE (-3)   /* a state check found NaN or Inf */
+#define MLSDC_ERR_TIMEOUT (-4)     /* a bounded device-side wait gave up */
+#define MLSDC_ERR_ALLOC (-5)       /* device memory allocation failed */
+
+/* Arithmetic of the Legendre stage (Sec. 3, Eq. legendre_transform and its
+ * inverse).  MLSDC_FP64: everything in float64.  MLSDC_TF32 / MLSDC_BF16X3:
+ * the Legendre contractions run on tcgen05 tensor cores (TF32 operands, or
+ * bf16 hi+lo splits with the three products hi*hi + hi*lo + lo*hi), with
+ * float32 accumulation; the longitude FFTs and grid products run in float32;
+ * the Legendre recurrence, quadrature, SDC matrices, implicit solve and all
+ * state accumulation stay float64.  MLSDC_FP32: as the tensor-core modes but
+ * with float32 FMA contractions on the CUDA cores. */
+typedef enum {
+    MLSDC_FP64 = 0,
+    MLSDC_TF32 = 1,
+    MLSDC_BF16X3 = 2,
+    MLSDC_FP32 = 3
+} mlsdc_precision;
+
+/* Physical constants in SI units (Sec. 2): Earth radius a, rotation rate
+ * Omega (f = 2 Omega mu), gravity g, mean geopotential Phibar, diffusion nu. */
+typedef struct {
+    double a, omega, g, phibar, nu;
+} swe_params;
+
+typedef struct sh_plan_s* sh_plan_t;
+typedef struct sdc_level_s* sdc_level_t;
+typedef struct mlsdc_s* mlsdc_t;
+
+/* Text of a status code, and the last CUDA error message seen by this thread. */
+const char* mlsdc_status_string(mlsdc_status s);
+const char* mlsdc_last_error(void);
+
+/* ---------------------------------------------------------------------------
+ * sh_plan: Gaussian grid and Legendre tables of one truncation (Sec. 3:
+ * Eq. legendre_transform's Gaussian latitudes and weights; the normalised
+ * associated Legendre functions of Eq. spectral_to_physical_space and
+ * H = (1 - mu^2) dP/dmu for the velocity and divergence/curl transforms).
+ * R >= 1; nlon a power of two in [16, 1024] with nlon >= 3R+1 (alias-free
+ * quadratic products); nlat even with nlat >= (3R+1)/2 and nlat/2 <= 1024.
+ * Tables are computed on the host in float64 and copied to the device of the
+ * current CUDA context.  Returns MLSDC_ERR_INVALID for other sizes.
+ */
+mlsdc_status sh_plan(int R, int nlon, int nlat, int precision, sh_plan_t* out);
+mlsdc_status sh_plan_destroy(sh_plan_t plan);
+/* Copies of the host-side grid: mu[nlat], w[nlat] (north to south). */
+mlsdc_status sh_plan_grid(sh_plan_t plan, double* mu_host, double* w_host);
+/* Bytes of device memory the plan holds (tables plus scratch). */
+mlsdc_status sh_plan_device_bytes(sh_plan_t plan, int64_t* bytes);
+
+/* sh_inverse: spectral -> grid for nf independent scalar fields,
+ * Eq. spectral_to_physical_space (Legendre sum per m, then the inverse
+ * longitude DFT).  spec: [nf][N_c] complex; grid: [nf][J][I]; 1 <= nf <= 16. */
+mlsdc_status sh_inverse(sh_plan_t plan, const double* spec, double* grid, int nf, void* stream);
+
+/* sh_forward: grid -> spectral, Eq. fourier_transform (with its 1/I) then
+ * Eq. legendre_transform (Gaussian weights); Im of m = 0 set to zero.
+ * grid: [nf][J][I]; spec: [nf][N_c] complex; 1 <= nf <= 16. */
+mlsdc_status sh_forward(sh_plan_t plan, const double* grid, double* spec, int nf, void* stream);
+
+/* swe_explicit_rhs: F_E = L_F + N (Sec. 4.1, Eq. system_of_odes_explicit_part)
+ * of a state, by the transform method:
+ *   F_E = [ -div(Phi' V), -div((zeta+f) V), curl((zeta+f) V) - lap(V.V/2) ].
+ * state, FE: [3][N_c] complex (must not alias).  Uses the plan's precision. */
+mlsdc_status swe_explicit_rhs(sh_plan_t plan, const swe_params* prm, const double* state,
+                              double* FE, void* stream);
+
+/* swe_implicit_rhs: F_I = L_G (Sec. 2, Eq.
+ * linear_wave_motion_induced_by_gravitational_forces; Sec. 4.1):
+ *   F_I = [ -Phibar delta + nu lap Phi', nu lap zeta, -lap Phi' + nu lap delta ].
+ * Always float64.  state, FI: [3][N_c]; FI may alias state. */
+mlsdc_status swe_implicit_rhs(sh_plan_t plan, const swe_params* prm, const double* state,
+                              double* FI, void* stream);
+
+/* swe_implicit_solve: x - alpha F_I(x) = b (Sec. 4.4, Eq. implicit_systems),
+ * diagonal per coefficient: zeta = b_zeta / c, then the 2x2 (Phi', delta)
+ * elimination, c = 1 + alpha nu n(n+1)/a^2.  alpha = dt * q~I_{m+1,m+1} >= 0.
+ * b, x: [3][N_c]; x may alias b.  Always float64. */
+mlsdc_status swe_implicit_solve(sh_plan_t plan, const swe_params* prm, double alpha,
+                                const double* b, double* x, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * sdc_level: one space-time level: a plan, the physics, and n_nodes
+ * Gauss-Lobatto nodes on [0, 1] with the collocation matrix Q (Sec. 4.2,
+ * Eq. weights), the forward-Euler weights q~E and the LU-trick weights q~I
+ * (q~I[1:,1:] = U^T where Q[1:,1:]^T = L U, Doolittle).  2 <= n_nodes <= 9.
+ * The level keeps a pointer to the plan, which must outlive it.
+ */
+mlsdc_status sdc_level_create(sh_plan_t plan, const swe_params* prm, int n_nodes, sdc_level_t* out);
+mlsdc_status sdc_level_destroy(sdc_level_t lev);
+/* Host copies of the node times t[n_nodes] and row-major Q, QE, QI [n_nodes^2]
+ * (any pointer may be NULL). */
+mlsdc_status sdc_level_matrices(sdc_level_t lev, double* t, double* Q, double* QE, double* QI);
+
+/* sdc_sweep: one IMEX SDC sweep (Sec. 4.2, Eq.
+ * update_equation_sdcq_discrete_form; with tau != NULL the coarse-level form
+ * Eq. modified_update_equation_sdcq_discrete_form).  For m = 0..M-1 in order:
+ * b = Theta[0] + dt sum_{j<=m} q~E_{m+1,j}(FE_new[j] - FE_old[j])
+ *   + dt sum_{j<=m} q~I_{m+1,j}(FI_new[j] - FI_old[j]) - dt q~I_{m+1,m+1} FI_old[m+1]
+ *   + dt sum_j q_{m+1,j}(FI_old[j] + FE_old[j]) + tau[m+1];
+ * Theta[m+1] = implicit solve of b with alpha = dt q~I_{m+1,m+1};
+ * FI_new[m+1] = F_I(Theta[m+1]); FE_new[m+1] = F_E(Theta[m+1]).
+ * Theta: [M+1][3][N_c] in/out (node 0 is read only); FI_old, FE_old: inputs;
+ * FI_new, FE_new: outputs (node 0 copied from the old arrays); tau:
+ * [M+1][3][N_c] or NULL.  The old and new F arrays must not alias. */
+mlsdc_status sdc_sweep(sdc_level_t lev, double dt, double* Theta, const double* FI_old,
+                       const double* FE_old, double* FI_new, double* FE_new, const double* tau,
+                       void* stream);
+
+/* sdc_step: one step of single-level SDC(M+1, n_sweeps): Theta^n copied to
+ * every node and F evaluated once (Sec. 4.3.2 initialisation), n_sweeps
+ * sweeps, result = last node.  state: [3][N_c] in/out. */
+mlsdc_status sdc_step(sdc_level_t lev, double* state, double dt, int n_sweeps, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * mlsdc: two space-time levels (Sec. 4.3).  The coarse level must have
+ * R_c <= R_f and nodes whose Lagrange transfer matrices Pi^c_f, Pi^f_c
+ * (Sec. 4.3.3) are computed from the two node sets.  Both levels must
+ * outlive the object.
+ */
+mlsdc_status mlsdc_create(sdc_level_t fine, sdc_level_t coarse, mlsdc_t* out);
+mlsdc_status mlsdc_destroy(mlsdc_t ml);
+
+/* mlsdc_step: one time step of two-level MLSDC: initialisation, then n_iter
+ * iterations of Algorithm 1 -- A) fine sweep; B) restriction (time
+ * interpolation Pi^c_f, then spectral truncation, Eqs. two_step_restriction,
+ * time_restriction, space_restriction) and coarse F evaluation, saved;
+ * C) FAS correction tau_c = A_c(R Theta_f) - R A_f(Theta_f) (Eq.
+ * tau_term_level_l+1) and n_coarse_sweeps coarse sweeps; D) zero-pad and
+ * Pi^f_c interpolation of the coarse corrections of Theta, F_I and F_E added
+ * to fine nodes 1..M_f.  Result: the last fine node.
+ * state: [3][N_c,fine] in/out.  With use_graph != 0 the launch sequence is
+ * captured once into a CUDA graph per (state, dt, n_iter, n_coarse_sweeps)
+ * and replayed on `stream` afterwards. */
+mlsdc_status mlsdc_step(mlsdc_t ml, double* state, double dt, int n_iter, int n_coarse_sweeps,
+                        int use_graph, void* stream);
+
+/* Kernel launches issued by the last mlsdc_step / sdc_step call made without
+ * a graph replay (a count of this library's kernels, for reporting). */
+mlsdc_status mlsdc_launch_count(mlsdc_t ml, int64_t* launches);
+
+/* Stage timing of swe_explicit_rhs for roofline reporting: launches each of
+ * the plan's F_E stage kernels `reps` times back to back on `stream`, timed
+ * with CUDA events on that stream, and writes the mean milliseconds per
+ * launch of [0] the Legendre synthesis, [1] the longitude FFT / grid-product
+ * kernel, [2] the Legendre analysis to ms_host[3] (synchronises the stream).
+ * Not a paper operation: a measurement utility over the same kernels. */
+mlsdc_status mlsdc_profile_rhs(sh_plan_t plan, const swe_params* prm, const double* state, double* FE,
+                               int reps, float* ms_host, void* stream);
+
+/* Device check that a state (n doubles) is finite: writes 1 to *ok_host if
+ * every value is finite, else 0 (synchronises the stream). */
+mlsdc_status mlsdc_check_finite(const double* state, int64_t n, int* ok_host, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MLSDC_SH_H */

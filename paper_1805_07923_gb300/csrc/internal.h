@@ -1,0 +1,97 @@
+// Internal declarations of the MLSDC-SH library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "mlsdc_sh.h"
+
+namespace mlsdc {
+
+// thread-local text of the last CUDA error
+void set_error(const char* where, cudaError_t e);
+void set_error_text(const std::string& s);
+
+#define MLSDC_CUDA(call)                                  \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) {                          \
+            ::mlsdc::set_error(#call, e_);                \
+            return MLSDC_ERR_CUDA;                        \
+        }                                                 \
+    } while (0)
+
+#define MLSDC_LAUNCHED(name)                              \
+    do {                                                  \
+        cudaError_t e_ = cudaGetLastError();              \
+        if (e_ != cudaSuccess) {                          \
+            ::mlsdc::set_error(name, e_);                 \
+            return MLSDC_ERR_CUDA;                        \
+        }                                                 \
+    } while (0)
+
+inline int nc_of(int R) { return (R + 1) * (R + 2) / 2; }
+inline int moff(int R, int m) { return m * (R + 1) - m * (m - 1) / 2; }
+
+// Work item of a Legendre kernel: zonal wavenumber m and the first
+// latitude (synthesis) or the first degree offset n - m (analysis).
+struct Chunk {
+    int m;
+    int start;
+};
+
+// Mixed-precision tables and scratch of a plan (float32 path).
+struct MPTables {
+    float* P32 = nullptr;   // [nc][J2] float32 copy of P
+    float* H32 = nullptr;   // [nc][J2]
+    float2* four_in = nullptr;   // [16][J][R+1]
+    float2* four_out = nullptr;  // [16][J][R+1]
+    // tensor-core operand tables (bf16 hi/lo or tf32), laid out per m-tile
+    void* tc_synth = nullptr;
+    void* tc_anal = nullptr;
+    int64_t tc_bytes = 0;
+};
+
+}  // namespace mlsdc
+
+struct sh_plan_s {
+    int R, I, J, J2, nc, logI, precision;
+    std::vector<double> mu, w;        // host copies, north to south, length J
+    double* d_mu = nullptr;           // [J]
+    double* d_w = nullptr;            // [J]
+    double* d_P = nullptr;            // [nc][J2], northern latitudes
+    double* d_H = nullptr;            // [nc][J2]
+    double2* d_tw = nullptr;          // [I/2] exp(-2 pi i k / I)
+    int* d_ndeg = nullptr;            // [nc] total degree n of each coefficient
+    mlsdc::Chunk* d_synth = nullptr;  // synthesis work items, largest first
+    mlsdc::Chunk* d_anal = nullptr;   // analysis work items, largest first
+    int n_synth = 0, n_anal = 0;
+    double2* d_four_in = nullptr;     // [16][J][R+1] Fourier coefficients (synthesis out)
+    double2* d_four_out = nullptr;    // [16][J][R+1] Fourier coefficients (analysis in)
+    mlsdc::MPTables mp;
+    int64_t bytes = 0;
+};
+
+namespace mlsdc {
+// chunk sizes of the float64 Legendre kernels
+constexpr int kSynthLat = 32;   // latitudes per synthesis work item (one warp)
+constexpr int kAnalRows = 32;   // degrees per analysis work item (one warp)
+constexpr int kMaxFields = 16;
+
+// float64 kernels (transform_f64.cu)
+// stage < 0: the whole F_E evaluation; 0, 1, 2: only that stage's kernel
+mlsdc_status rhs_explicit_f64(sh_plan_t p, const swe_params* prm, const double* state, double* FE,
+                              cudaStream_t st, int64_t* launches, int stage = -1);
+mlsdc_status f64_prepare(sh_plan_t p);
+// float32 / tensor-core path (transform_mp.cu)
+mlsdc_status mp_init(sh_plan_t p);
+void mp_free(sh_plan_t p);
+mlsdc_status rhs_explicit_mp(sh_plan_t p, const swe_params* prm, const double* state, double* FE,
+                             cudaStream_t st, int64_t* launches, int stage = -1);
+// pointwise float64 kernels (sdc.cu)
+mlsdc_status implicit_rhs_launch(sh_plan_t p, const swe_params* prm, const double* state, double* FI,
+                                 cudaStream_t st);
+}  // namespace mlsdc

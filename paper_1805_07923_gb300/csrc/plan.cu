@@ -1,0 +1,248 @@
+// sh_plan: Gaussian grid, normalised associated Legendre tables and FFT
+// twiddles of one truncation (Sec. 3), computed on the host in float64.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+
+#include "internal.h"
+
+namespace mlsdc {
+
+static thread_local std::string g_last_error;
+
+void set_error(const char* where, cudaError_t e) {
+    g_last_error = std::string(where) + ": " + cudaGetErrorString(e);
+}
+void set_error_text(const std::string& s) { g_last_error = s; }
+
+// Gaussian latitudes: roots of the degree-J Legendre polynomial by Newton's
+// method, ordered north to south, with weights w = 2 / ((1 - mu^2) P_J'(mu)^2).
+static void gaussian_latitudes(int J, std::vector<double>& mu, std::vector<double>& w) {
+    mu.assign(J, 0.0);
+    w.assign(J, 0.0);
+    const double pi = 3.14159265358979323846;
+    for (int j = 0; j < (J + 1) / 2; ++j) {
+        double x = std::cos(pi * (j + 0.75) / (J + 0.5));
+        double dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = x;
+            for (int k = 2; k <= J; ++k) {
+                double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = J * (x * p1 - p0) / (x * x - 1.0);
+            double dx = p1 / dp;
+            x -= dx;
+            if (std::fabs(dx) < 1e-16) break;
+        }
+        {
+            double p0 = 1.0, p1 = x;
+            for (int k = 2; k <= J; ++k) {
+                double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = J * (x * p1 - p0) / (x * x - 1.0);
+        }
+        double wj = 2.0 / ((1.0 - x * x) * dp * dp);
+        mu[j] = x;
+        mu[J - 1 - j] = -x;
+        w[j] = wj;
+        w[J - 1 - j] = wj;
+    }
+    if (J % 2 == 1) mu[J / 2] = 0.0;
+}
+
+static inline double eps_mn(int m, int n) {
+    if (n <= m) return 0.0;
+    return std::sqrt((double(n) * n - double(m) * m) / (4.0 * double(n) * n - 1.0));
+}
+
+// P^m_n(mu_j) and H^m_n = (1 - mu^2) dP^m_n/dmu for the northern latitudes,
+// orthonormal on [-1, 1], no Condon-Shortley phase; |values| < 1e-300 -> 0.
+static void legendre_tables(int R, int J2, const std::vector<double>& mu, std::vector<double>& P,
+                            std::vector<double>& H) {
+    const int nc = nc_of(R);
+    P.assign((size_t)nc * J2, 0.0);
+    H.assign((size_t)nc * J2, 0.0);
+    std::vector<double> col(R + 3);
+    for (int j = 0; j < J2; ++j) {
+        const double x = mu[j];
+        const double s = std::sqrt(1.0 - x * x);
+        double pmm = std::sqrt(0.5);
+        for (int m = 0; m <= R; ++m) {
+            if (m > 0) pmm *= std::sqrt((2.0 * m + 1.0) / (2.0 * m)) * s;
+            if (std::fabs(pmm) < 1e-300) pmm = 0.0;
+            // col[k] = P^m_{m+k}, k = 0 .. R+1-m
+            col[0] = pmm;
+            double pm1 = 0.0, pn = pmm;
+            for (int n = m; n <= R; ++n) {
+                double pn1 = (x * pn - eps_mn(m, n) * pm1) / eps_mn(m, n + 1);
+                if (std::fabs(pn1) < 1e-300) pn1 = 0.0;
+                col[n + 1 - m] = pn1;
+                pm1 = pn;
+                pn = pn1;
+            }
+            const int off = moff(R, m);
+            for (int n = m; n <= R; ++n) {
+                const int k = n - m;
+                double pnm1 = (k >= 1) ? col[k - 1] : 0.0;
+                double h = -n * eps_mn(m, n + 1) * col[k + 1] + (n + 1.0) * eps_mn(m, n) * pnm1;
+                P[(size_t)(off + k) * J2 + j] = col[k];
+                H[(size_t)(off + k) * J2 + j] = h;
+            }
+        }
+    }
+}
+
+template <class T>
+static mlsdc_status dev_alloc(T** ptr, size_t count, int64_t* bytes) {
+    cudaError_t e = cudaMalloc((void**)ptr, count * sizeof(T));
+    if (e != cudaSuccess) {
+        set_error("cudaMalloc", e);
+        *ptr = nullptr;
+        return MLSDC_ERR_ALLOC;
+    }
+    *bytes += (int64_t)(count * sizeof(T));
+    return MLSDC_OK;
+}
+
+static void free_plan(sh_plan_t p) {
+    if (!p) return;
+    mp_free(p);
+    cudaFree(p->d_mu);
+    cudaFree(p->d_w);
+    cudaFree(p->d_P);
+    cudaFree(p->d_H);
+    cudaFree(p->d_tw);
+    cudaFree(p->d_ndeg);
+    cudaFree(p->d_synth);
+    cudaFree(p->d_anal);
+    cudaFree(p->d_four_in);
+    cudaFree(p->d_four_out);
+    delete p;
+}
+
+}  // namespace mlsdc
+
+using namespace mlsdc;
+
+extern "C" const char* mlsdc_status_string(mlsdc_status s) {
+    switch (s) {
+        case MLSDC_OK: return "ok";
+        case MLSDC_ERR_INVALID: return "invalid argument";
+        case MLSDC_ERR_CUDA: return "CUDA error";
+        case MLSDC_ERR_NONFINITE: return "non-finite state";
+        case MLSDC_ERR_TIMEOUT: return "device wait timed out";
+        case MLSDC_ERR_ALLOC: return "device allocation failed";
+        default: return "unknown status";
+    }
+}
+
+extern "C" const char* mlsdc_last_error(void) { return g_last_error.c_str(); }
+
+#define TRY(x)                      \
+    do {                            \
+        mlsdc_status s_ = (x);      \
+        if (s_ != MLSDC_OK) {       \
+            free_plan(p);           \
+            return s_;              \
+        }                           \
+    } while (0)
+
+extern "C" mlsdc_status sh_plan(int R, int nlon, int nlat, int precision, sh_plan_t* out) {
+    if (!out) return MLSDC_ERR_INVALID;
+    *out = nullptr;
+    if (R < 1 || nlon < 16 || nlon > 1024 || (nlon & (nlon - 1)) != 0 || nlon < 3 * R + 1)
+        return MLSDC_ERR_INVALID;
+    if (nlat < 2 || nlat % 2 != 0 || 2 * nlat < 3 * R + 1 || nlat / 2 > 1024) return MLSDC_ERR_INVALID;
+    if (precision < MLSDC_FP64 || precision > MLSDC_FP32) return MLSDC_ERR_INVALID;
+
+    sh_plan_t p = new sh_plan_s();
+    p->R = R;
+    p->I = nlon;
+    p->J = nlat;
+    p->J2 = nlat / 2;
+    p->nc = nc_of(R);
+    p->precision = precision;
+    p->logI = 0;
+    while ((1 << p->logI) < nlon) ++p->logI;
+
+    gaussian_latitudes(nlat, p->mu, p->w);
+    std::vector<double> P, H;
+    legendre_tables(R, p->J2, p->mu, P, H);
+
+    std::vector<double2> tw(nlon / 2);
+    const double pi = 3.14159265358979323846;
+    for (int k = 0; k < nlon / 2; ++k) {
+        double ang = 2.0 * pi * k / nlon;
+        tw[k] = make_double2(std::cos(ang), -std::sin(ang));
+    }
+    std::vector<int> ndeg(p->nc);
+    for (int m = 0; m <= R; ++m)
+        for (int n = m; n <= R; ++n) ndeg[moff(R, m) + n - m] = n;
+
+    // Legendre work items, largest first so the block scheduler balances them.
+    std::vector<Chunk> cs, ca;
+    for (int m = 0; m <= R; ++m)
+        for (int j0 = 0; j0 < p->J2; j0 += kSynthLat) cs.push_back({m, j0});
+    std::stable_sort(cs.begin(), cs.end(), [](const Chunk& a, const Chunk& b) { return a.m < b.m; });
+    for (int m = 0; m <= R; ++m)
+        for (int k0 = 0; k0 < R + 1 - m; k0 += kAnalRows) ca.push_back({m, k0});
+    std::stable_sort(ca.begin(), ca.end(), [R](const Chunk& a, const Chunk& b) {
+        int ra = std::min(kAnalRows, R + 1 - a.m - a.start), rb = std::min(kAnalRows, R + 1 - b.m - b.start);
+        return ra > rb;
+    });
+    p->n_synth = (int)cs.size();
+    p->n_anal = (int)ca.size();
+
+    const size_t nfour = (size_t)kMaxFields * nlat * (R + 1);
+    TRY(dev_alloc(&p->d_mu, nlat, &p->bytes));
+    TRY(dev_alloc(&p->d_w, nlat, &p->bytes));
+    TRY(dev_alloc(&p->d_P, P.size(), &p->bytes));
+    TRY(dev_alloc(&p->d_H, H.size(), &p->bytes));
+    TRY(dev_alloc(&p->d_tw, tw.size(), &p->bytes));
+    TRY(dev_alloc(&p->d_ndeg, ndeg.size(), &p->bytes));
+    TRY(dev_alloc(&p->d_synth, cs.size(), &p->bytes));
+    TRY(dev_alloc(&p->d_anal, ca.size(), &p->bytes));
+    TRY(dev_alloc(&p->d_four_in, nfour, &p->bytes));
+    TRY(dev_alloc(&p->d_four_out, nfour, &p->bytes));
+
+#define H2D(dst, src, n) \
+    if (cudaMemcpy(dst, src, (n) * sizeof(*(src)), cudaMemcpyHostToDevice) != cudaSuccess) { \
+        set_error("cudaMemcpy", cudaGetLastError()); free_plan(p); return MLSDC_ERR_CUDA; }
+    H2D(p->d_mu, p->mu.data(), nlat);
+    H2D(p->d_w, p->w.data(), nlat);
+    H2D(p->d_P, P.data(), P.size());
+    H2D(p->d_H, H.data(), H.size());
+    H2D(p->d_tw, tw.data(), tw.size());
+    H2D(p->d_ndeg, ndeg.data(), ndeg.size());
+    H2D(p->d_synth, cs.data(), cs.size());
+    H2D(p->d_anal, ca.data(), ca.size());
+#undef H2D
+    TRY(f64_prepare(p));
+    if (precision != MLSDC_FP64) TRY(mp_init(p));
+    *out = p;
+    return MLSDC_OK;
+}
+
+extern "C" mlsdc_status sh_plan_destroy(sh_plan_t plan) {
+    if (!plan) return MLSDC_ERR_INVALID;
+    free_plan(plan);
+    return MLSDC_OK;
+}
+
+extern "C" mlsdc_status sh_plan_grid(sh_plan_t p, double* mu_host, double* w_host) {
+    if (!p) return MLSDC_ERR_INVALID;
+    if (mu_host) std::memcpy(mu_host, p->mu.data(), sizeof(double) * p->J);
+    if (w_host) std::memcpy(w_host, p->w.data(), sizeof(double) * p->J);
+    return MLSDC_OK;
+}
+
+extern "C" mlsdc_status sh_plan_device_bytes(sh_plan_t p, int64_t* bytes) {
+    if (!p || !bytes) return MLSDC_ERR_INVALID;
+    *bytes = p->bytes + p->mp.tc_bytes;
+    return MLSDC_OK;
+}

@@ -1,0 +1,728 @@
+// IMEX SDC sweeps and two-level MLSDC on the device (Sec. 4.2, Sec. 4.3,
+// Algorithm 1), the implicit right-hand side and the per-coefficient implicit
+// solve (Sec. 4.4).  All arithmetic here is float64.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <tuple>
+
+#include "internal.h"
+
+namespace mlsdc {
+
+constexpr int kMaxNodes = 9;
+
+struct Phys {
+    double inv_a2, phibar, nu;
+};
+
+// Row m+1 of the SDC matrices for one node update.
+struct NodeRow {
+    double qe[kMaxNodes], qi[kMaxNodes], q[kMaxNodes];
+    double qimm;
+    int m;    // updating node m+1
+    int M;    // nodes 0..M
+};
+
+__device__ __forceinline__ double2 cax(double2 acc, double s, double2 x) {
+    return make_double2(fma(s, x.x, acc.x), fma(s, x.y, acc.y));
+}
+
+// F_I = [ -Phibar delta + nu L Phi', nu L zeta, -L Phi' + nu L delta ], L = -n(n+1)/a^2
+__device__ __forceinline__ void implicit_rhs_coef(double L, const Phys& ph, double2 p, double2 z, double2 d,
+                                                  double2& fp, double2& fz, double2& fd) {
+    const double nl = ph.nu * L;
+    fp = make_double2(-ph.phibar * d.x + nl * p.x, -ph.phibar * d.y + nl * p.y);
+    fz = make_double2(nl * z.x, nl * z.y);
+    fd = make_double2(-L * p.x + nl * d.x, -L * p.y + nl * d.y);
+}
+
+// x - alpha F_I(x) = b, diagonal per coefficient (Sec. 4.4).
+__device__ __forceinline__ void implicit_solve_coef(double L, double alpha, const Phys& ph, double2 bp,
+                                                    double2 bz, double2 bd, double2& p, double2& z,
+                                                    double2& d) {
+    const double c = 1.0 - alpha * ph.nu * L;
+    const double ic = 1.0 / c;
+    const double den = 1.0 / (c * c - alpha * alpha * ph.phibar * L);
+    z = make_double2(bz.x * ic, bz.y * ic);
+    p = make_double2((c * bp.x - alpha * ph.phibar * bd.x) * den, (c * bp.y - alpha * ph.phibar * bd.y) * den);
+    d = make_double2((bd.x - alpha * L * p.x) * ic, (bd.y - alpha * L * p.y) * ic);
+}
+
+__global__ void k_implicit_rhs(const double2* __restrict__ x, double2* __restrict__ F,
+                               const int* __restrict__ ndeg, int nc, Phys ph) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) {
+        const double n = ndeg[c];
+        const double L = -n * (n + 1.0) * ph.inv_a2;
+        double2 fp, fz, fd;
+        implicit_rhs_coef(L, ph, x[c], x[nc + c], x[2 * nc + c], fp, fz, fd);
+        F[c] = fp;
+        F[nc + c] = fz;
+        F[2 * nc + c] = fd;
+    }
+}
+
+__global__ void k_implicit_solve(const double2* __restrict__ b, double2* __restrict__ x,
+                                 const int* __restrict__ ndeg, int nc, double alpha, Phys ph) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) {
+        const double n = ndeg[c];
+        const double L = -n * (n + 1.0) * ph.inv_a2;
+        double2 p, z, d;
+        implicit_solve_coef(L, alpha, ph, b[c], b[nc + c], b[2 * nc + c], p, z, d);
+        x[c] = p;
+        x[nc + c] = z;
+        x[2 * nc + c] = d;
+    }
+}
+
+// One SDC node update (Eq. update_equation_sdcq_discrete_form, plus tau on a
+// coarse level), the implicit solve, and F_I at the new node.  Node arrays
+// are [M+1][3][nc] complex; `node` = 3 nc complex values.  The m = 0 launch
+// also copies node 0 of the old F arrays into the new ones.
+__global__ void k_sweep_node(double2* Th, const double2* __restrict__ FIo, const double2* __restrict__ FEo,
+                             double2* FIn, const double2* FEn, const double2* __restrict__ tau,
+                             const int* __restrict__ ndeg, int nc, double dt, NodeRow row, Phys ph,
+                             double2* FEn_w) {
+    const size_t node = (size_t)3 * nc;
+    const int m = row.m;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) {
+        double2 b[3];
+        for (int f = 0; f < 3; ++f) {
+            const size_t o = (size_t)f * nc + c;
+            double2 acc = Th[o];  // Theta^n (node 0)
+            for (int j = 1; j <= m; ++j) {
+                const size_t oj = j * node + o;
+                const double2 de = make_double2(FEn[oj].x - FEo[oj].x, FEn[oj].y - FEo[oj].y);
+                const double2 di = make_double2(FIn[oj].x - FIo[oj].x, FIn[oj].y - FIo[oj].y);
+                acc = cax(acc, dt * row.qe[j], de);
+                acc = cax(acc, dt * row.qi[j], di);
+            }
+            acc = cax(acc, -dt * row.qimm, FIo[(m + 1) * node + o]);
+            for (int j = 0; j <= row.M; ++j) {
+                const size_t oj = j * node + o;
+                const double2 s = make_double2(FIo[oj].x + FEo[oj].x, FIo[oj].y + FEo[oj].y);
+                acc = cax(acc, dt * row.q[j], s);
+            }
+            if (tau) {
+                const double2 t = tau[(m + 1) * node + o];
+                acc = make_double2(acc.x + t.x, acc.y + t.y);
+            }
+            b[f] = acc;
+        }
+        const double n = ndeg[c];
+        const double L = -n * (n + 1.0) * ph.inv_a2;
+        double2 p, z, d;
+        implicit_solve_coef(L, dt * row.qimm, ph, b[0], b[1], b[2], p, z, d);
+        const size_t om = (m + 1) * node + c;
+        Th[om] = p;
+        Th[om + nc] = z;
+        Th[om + 2 * nc] = d;
+        double2 fp, fz, fd;
+        implicit_rhs_coef(L, ph, p, z, d, fp, fz, fd);
+        FIn[om] = fp;
+        FIn[om + nc] = fz;
+        FIn[om + 2 * nc] = fd;
+        if (m == 0) {
+            for (int f = 0; f < 3; ++f) {
+                FIn[(size_t)f * nc + c] = FIo[(size_t)f * nc + c];
+                FEn_w[(size_t)f * nc + c] = FEo[(size_t)f * nc + c];
+            }
+        }
+    }
+}
+
+// dst[k] = src for k = 0..count-1 (node broadcast), src and dst [3 nc] complex.
+__global__ void k_broadcast(const double2* __restrict__ src, double2* __restrict__ dst, int n3, int count) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n3; c += gridDim.x * blockDim.x) {
+        const double2 v = src[c];
+        for (int k = 0; k < count; ++k) dst[(size_t)k * n3 + c] = v;
+    }
+}
+
+// Restriction (Eqs. two_step_restriction, time_restriction, space_restriction):
+// Theta_c[i] = D( sum_j Pi^c_f[i][j] Theta_f[j] ) for i in [i0, i1).
+struct TransferMat {
+    double a[kMaxNodes * kMaxNodes];
+};
+
+__global__ void k_restrict(const double2* __restrict__ Tf, double2* __restrict__ Tc, const int* __restrict__ c2f,
+                           int ncf, int ncc, int nf_nodes, int i0, int i1, TransferMat Pcf) {
+    const int total = 3 * ncc;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+        const int f = t / ncc, k = t - f * ncc;
+        const size_t of = (size_t)f * ncf + c2f[k];
+        for (int i = i0; i < i1; ++i) {
+            double2 acc{0.0, 0.0};
+            for (int j = 0; j < nf_nodes; ++j) acc = cax(acc, Pcf.a[i * nf_nodes + j], Tf[(size_t)j * 3 * ncf + of]);
+            Tc[(size_t)i * 3 * ncc + t] = acc;
+        }
+    }
+}
+
+struct FasArgs {
+    double Qf[kMaxNodes * kMaxNodes];
+    double Qc[kMaxNodes * kMaxNodes];
+    double Pcf[kMaxNodes * kMaxNodes];
+    int nfn, ncn;
+};
+
+// tau_c = A_c(R Theta_f) - R A_f(Theta_f), A(Theta) = Theta - dt (Q x I) F
+// (Eq. tau_term_level_l+1 with tau_f = 0; Eq. collocation_problem).
+__global__ void k_fas_tau(const double2* __restrict__ Tf, const double2* __restrict__ FIf,
+                          const double2* __restrict__ FEf, const double2* __restrict__ Tc,
+                          const double2* __restrict__ FIc, const double2* __restrict__ FEc,
+                          double2* __restrict__ tau, const int* __restrict__ c2f, int ncf, int ncc,
+                          double dt, FasArgs A) {
+    const int total = 3 * ncc;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+        const int f = t / ncc, k = t - f * ncc;
+        const size_t of = (size_t)f * ncf + c2f[k];
+        const size_t nf3 = (size_t)3 * ncf, nc3 = (size_t)3 * ncc;
+        double2 Af[kMaxNodes];
+        for (int j = 0; j < A.nfn; ++j) {
+            double2 acc = Tf[j * nf3 + of];
+            for (int l = 0; l < A.nfn; ++l) {
+                const double2 s = make_double2(FIf[l * nf3 + of].x + FEf[l * nf3 + of].x,
+                                               FIf[l * nf3 + of].y + FEf[l * nf3 + of].y);
+                acc = cax(acc, -dt * A.Qf[j * A.nfn + l], s);
+            }
+            Af[j] = acc;
+        }
+        for (int i = 0; i < A.ncn; ++i) {
+            double2 acc = Tc[i * nc3 + t];
+            for (int l = 0; l < A.ncn; ++l) {
+                const double2 s = make_double2(FIc[l * nc3 + t].x + FEc[l * nc3 + t].x,
+                                               FIc[l * nc3 + t].y + FEc[l * nc3 + t].y);
+                acc = cax(acc, -dt * A.Qc[i * A.ncn + l], s);
+            }
+            for (int j = 0; j < A.nfn; ++j) acc = cax(acc, -A.Pcf[i * A.nfn + j], Af[j]);
+            tau[i * nc3 + t] = acc;
+        }
+    }
+}
+
+// Step D: X_f[m] += P( sum_i Pi^f_c[m][i] (X_c[i] - X_s[i]) ), m = 1..M_f,
+// for X = Theta, F_I, F_E (zero-padding leaves the fine-only modes unchanged).
+__global__ void k_interp(double2* __restrict__ Tf, double2* __restrict__ FIf, double2* __restrict__ FEf,
+                         const double2* __restrict__ Tc, const double2* __restrict__ FIc,
+                         const double2* __restrict__ FEc, const double2* __restrict__ Ts,
+                         const double2* __restrict__ FIs, const double2* __restrict__ FEs,
+                         const int* __restrict__ c2f, int ncf, int ncc, int nfn, int ncn, TransferMat Pfc) {
+    const int total = 3 * ncc;
+    const size_t nf3 = (size_t)3 * ncf, nc3 = (size_t)3 * ncc;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+        const int f = t / ncc, k = t - f * ncc;
+        const size_t of = (size_t)f * ncf + c2f[k];
+        double2 dT[kMaxNodes], dI[kMaxNodes], dE[kMaxNodes];
+        for (int i = 0; i < ncn; ++i) {
+            const size_t oc = i * nc3 + t;
+            dT[i] = make_double2(Tc[oc].x - Ts[oc].x, Tc[oc].y - Ts[oc].y);
+            dI[i] = make_double2(FIc[oc].x - FIs[oc].x, FIc[oc].y - FIs[oc].y);
+            dE[i] = make_double2(FEc[oc].x - FEs[oc].x, FEc[oc].y - FEs[oc].y);
+        }
+        for (int m = 1; m < nfn; ++m) {
+            double2 aT{0, 0}, aI{0, 0}, aE{0, 0};
+            for (int i = 0; i < ncn; ++i) {
+                const double w = Pfc.a[m * ncn + i];
+                aT = cax(aT, w, dT[i]);
+                aI = cax(aI, w, dI[i]);
+                aE = cax(aE, w, dE[i]);
+            }
+            const size_t o = m * nf3 + of;
+            Tf[o] = make_double2(Tf[o].x + aT.x, Tf[o].y + aT.y);
+            FIf[o] = make_double2(FIf[o].x + aI.x, FIf[o].y + aI.y);
+            FEf[o] = make_double2(FEf[o].x + aE.x, FEf[o].y + aE.y);
+        }
+    }
+}
+
+__global__ void k_finite(const double* __restrict__ x, int64_t n, int* __restrict__ bad) {
+    int local = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        local |= !isfinite(x[i]);
+    local = __any_sync(0xffffffffu, local);
+    if (local && (threadIdx.x & 31) == 0) atomicOr(bad, 1);
+}
+
+// ---------------------------------------------------------------------------
+// Host-side SDC matrices (Sec. 4.2, Sec. 4.3.3)
+
+static void gauss_nodes(int n, std::vector<double>& x, std::vector<double>& w) {
+    x.assign(n, 0.0);
+    w.assign(n, 0.0);
+    const double pi = 3.14159265358979323846;
+    for (int i = 0; i < n; ++i) {
+        double z = std::cos(pi * (i + 0.75) / (n + 0.5));
+        double dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= n; ++k) {
+                double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = n * (z * p1 - p0) / (z * z - 1.0);
+            double dz = p1 / dp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-16) break;
+        }
+        double p0 = 1.0, p1 = z;
+        for (int k = 2; k <= n; ++k) {
+            double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+            p0 = p1;
+            p1 = p2;
+        }
+        dp = n * (z * p1 - p0) / (z * z - 1.0);
+        x[i] = z;
+        w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+// n Gauss-Lobatto nodes on [0, 1]: end points and the roots of P'_{n-1}
+// (Newton on P'_N with P'' from the Legendre equation), symmetrised.
+static std::vector<double> lobatto(int n) {
+    const int N = n - 1;
+    std::vector<double> x(n);
+    x[0] = -1.0;
+    x[N] = 1.0;
+    const double pi = 3.14159265358979323846;
+    for (int i = 1; i < N; ++i) {
+        double z = -std::cos(pi * i / N);
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= N; ++k) {
+                double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            const double dP = N * (z * p1 - p0) / (z * z - 1.0);
+            const double d2P = (2.0 * z * dP - N * (N + 1.0) * p1) / (1.0 - z * z);
+            const double dz = dP / d2P;
+            z -= dz;
+            if (std::fabs(dz) < 1e-16) break;
+        }
+        x[i] = z;
+    }
+    for (int i = 0; i < n / 2; ++i) {
+        const double s = 0.5 * (x[n - 1 - i] - x[i]);
+        x[i] = -s;
+        x[n - 1 - i] = s;
+    }
+    if (n % 2 == 1) x[n / 2] = 0.0;
+    std::vector<double> t(n);
+    for (int i = 0; i < n; ++i) t[i] = 0.5 * (x[i] + 1.0);
+    return t;
+}
+
+static double lagrange(const std::vector<double>& t, int j, double s) {
+    double v = 1.0;
+    for (int k = 0; k < (int)t.size(); ++k)
+        if (k != j) v *= (s - t[k]) / (t[j] - t[k]);
+    return v;
+}
+
+}  // namespace mlsdc
+
+using namespace mlsdc;
+
+struct sdc_level_s {
+    sh_plan_t plan;
+    swe_params prm;
+    int n;  // nodes
+    std::vector<double> t, Q, QE, QI;
+    double2* Th = nullptr;     // [n][3][nc]
+    double2* FI[2] = {nullptr, nullptr};
+    double2* FE[2] = {nullptr, nullptr};
+    int cur = 0;
+    int64_t launches = 0;
+};
+
+namespace mlsdc {
+
+static Phys phys_of(const swe_params& p) { return Phys{1.0 / (p.a * p.a), p.phibar, p.nu}; }
+
+static int grid_for(int n) {
+    int b = (n + 255) / 256;
+    return std::max(1, std::min(b, 152 * 8));
+}
+
+static mlsdc_status eval_FE(sdc_level_t L, const double2* x, double2* FE, cudaStream_t st) {
+    if (L->plan->precision == MLSDC_FP64)
+        return rhs_explicit_f64(L->plan, &L->prm, (const double*)x, (double*)FE, st, &L->launches);
+    return rhs_explicit_mp(L->plan, &L->prm, (const double*)x, (double*)FE, st, &L->launches);
+}
+
+static mlsdc_status eval_FI(sdc_level_t L, const double2* x, double2* FI, cudaStream_t st) {
+    const int nc = L->plan->nc;
+    k_implicit_rhs<<<grid_for(nc), 256, 0, st>>>(x, FI, L->plan->d_ndeg, nc, phys_of(L->prm));
+    MLSDC_LAUNCHED("k_implicit_rhs");
+    L->launches++;
+    return MLSDC_OK;
+}
+
+// One sweep on explicit buffers.
+static mlsdc_status sweep(sdc_level_t L, double dt, double2* Th, const double2* FIo, const double2* FEo,
+                          double2* FIn, double2* FEn, const double2* tau, cudaStream_t st) {
+    const int nc = L->plan->nc;
+    const int n = L->n;
+    const size_t node = (size_t)3 * nc;
+    Phys ph = phys_of(L->prm);
+    for (int m = 0; m < n - 1; ++m) {
+        NodeRow row;
+        std::memset(&row, 0, sizeof(row));
+        row.m = m;
+        row.M = n - 1;
+        for (int j = 0; j < n; ++j) {
+            row.qe[j] = L->QE[(m + 1) * n + j];
+            row.qi[j] = L->QI[(m + 1) * n + j];
+            row.q[j] = L->Q[(m + 1) * n + j];
+        }
+        row.qimm = L->QI[(m + 1) * n + m + 1];
+        k_sweep_node<<<grid_for(nc), 256, 0, st>>>(Th, FIo, FEo, FIn, FEn, tau, L->plan->d_ndeg, nc, dt, row, ph,
+                                                 FEn);
+        MLSDC_LAUNCHED("k_sweep_node");
+        L->launches++;
+        mlsdc_status s = eval_FE(L, Th + (m + 1) * node, FEn + (m + 1) * node, st);
+        if (s != MLSDC_OK) return s;
+    }
+    return MLSDC_OK;
+}
+
+// Initialisation: Theta^n at every node, F_I and F_E evaluated once and spread.
+static mlsdc_status spread(sdc_level_t L, const double2* state, cudaStream_t st) {
+    const int nc = L->plan->nc;
+    const int n3 = 3 * nc;
+    k_broadcast<<<grid_for(n3), 256, 0, st>>>(state, L->Th, n3, L->n);
+    MLSDC_LAUNCHED("k_broadcast");
+    L->launches++;
+    mlsdc_status s;
+    if ((s = eval_FI(L, L->Th, L->FI[L->cur], st)) != MLSDC_OK) return s;
+    if ((s = eval_FE(L, L->Th, L->FE[L->cur], st)) != MLSDC_OK) return s;
+    k_broadcast<<<grid_for(n3), 256, 0, st>>>(L->FI[L->cur], L->FI[L->cur] + n3, n3, L->n - 1);
+    MLSDC_LAUNCHED("k_broadcast");
+    k_broadcast<<<grid_for(n3), 256, 0, st>>>(L->FE[L->cur], L->FE[L->cur] + n3, n3, L->n - 1);
+    MLSDC_LAUNCHED("k_broadcast");
+    L->launches += 2;
+    return MLSDC_OK;
+}
+
+mlsdc_status implicit_rhs_launch(sh_plan_t p, const swe_params* prm, const double* state, double* FI,
+                                 cudaStream_t st) {
+    k_implicit_rhs<<<grid_for(p->nc), 256, 0, st>>>((const double2*)state, (double2*)FI, p->d_ndeg, p->nc,
+                                                   phys_of(*prm));
+    MLSDC_LAUNCHED("k_implicit_rhs");
+    return MLSDC_OK;
+}
+
+}  // namespace mlsdc
+
+struct mlsdc_s {
+    sdc_level_t f, c;
+    TransferMat Pcf, Pfc;
+    int* d_c2f = nullptr;
+    double2 *Ts = nullptr, *FIs = nullptr, *FEs = nullptr, *tau = nullptr;
+    cudaStream_t cap = nullptr;
+    std::map<std::tuple<double*, double, int, int>, cudaGraphExec_t> graphs;
+    int64_t launches = 0;
+};
+
+extern "C" mlsdc_status swe_implicit_rhs(sh_plan_t p, const swe_params* prm, const double* state, double* FI,
+                                         void* stream) {
+    if (!p || !prm || !state || !FI) return MLSDC_ERR_INVALID;
+    return implicit_rhs_launch(p, prm, state, FI, (cudaStream_t)stream);
+}
+
+extern "C" mlsdc_status swe_implicit_solve(sh_plan_t p, const swe_params* prm, double alpha, const double* b,
+                                           double* x, void* stream) {
+    if (!p || !prm || !b || !x || !(alpha >= 0.0)) return MLSDC_ERR_INVALID;
+    k_implicit_solve<<<grid_for(p->nc), 256, 0, (cudaStream_t)stream>>>((const double2*)b, (double2*)x, p->d_ndeg,
+                                                                       p->nc, alpha, phys_of(*prm));
+    MLSDC_LAUNCHED("k_implicit_solve");
+    return MLSDC_OK;
+}
+
+extern "C" mlsdc_status mlsdc_check_finite(const double* state, int64_t n, int* ok_host, void* stream) {
+    if (!state || n < 0 || !ok_host) return MLSDC_ERR_INVALID;
+    cudaStream_t st = (cudaStream_t)stream;
+    int* d_bad = nullptr;
+    MLSDC_CUDA(cudaMallocAsync((void**)&d_bad, sizeof(int), st));
+    MLSDC_CUDA(cudaMemsetAsync(d_bad, 0, sizeof(int), st));
+    k_finite<<<grid_for((int)std::min<int64_t>(n, 1 << 30)), 256, 0, st>>>(state, n, d_bad);
+    MLSDC_LAUNCHED("k_finite");
+    int bad = 0;
+    MLSDC_CUDA(cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+    MLSDC_CUDA(cudaFreeAsync(d_bad, st));
+    MLSDC_CUDA(cudaStreamSynchronize(st));
+    *ok_host = bad ? 0 : 1;
+    return MLSDC_OK;
+}
+
+extern "C" mlsdc_status sdc_level_create(sh_plan_t plan, const swe_params* prm, int n_nodes, sdc_level_t* out) {
+    if (!plan || !prm || !out || n_nodes < 2 || n_nodes > kMaxNodes) return MLSDC_ERR_INVALID;
+    sdc_level_t L = new sdc_level_s();
+    L->plan = plan;
+    L->prm = *prm;
+    L->n = n_nodes;
+    const int n = n_nodes;
+    L->t = lobatto(n);
+    L->Q.assign(n * n, 0.0);
+    L->QE.assign(n * n, 0.0);
+    L->QI.assign(n * n, 0.0);
+    std::vector<double> gx, gw;
+    gauss_nodes(n, gx, gw);
+    for (int m = 0; m < n; ++m)
+        for (int j = 0; j < n; ++j) {
+            double s = 0.0;
+            for (int q = 0; q < n; ++q) s += gw[q] * lagrange(L->t, j, L->t[m] * (gx[q] + 1.0) / 2.0);
+            L->Q[m * n + j] = L->t[m] / 2.0 * s;
+        }
+    for (int m = 0; m + 1 < n; ++m)
+        for (int j = 0; j <= m; ++j) L->QE[(m + 1) * n + j] = L->t[j + 1] - L->t[j];
+    // LU trick: (Q[1:,1:])^T = L U (Doolittle), q~I[1:,1:] = U^T
+    const int k = n - 1;
+    std::vector<double> A(k * k), Lm(k * k, 0.0), U(k * k, 0.0);
+    for (int r = 0; r < k; ++r)
+        for (int c = 0; c < k; ++c) A[r * k + c] = L->Q[(c + 1) * n + (r + 1)];
+    for (int i = 0; i < k; ++i) {
+        Lm[i * k + i] = 1.0;
+        for (int c = i; c < k; ++c) {
+            double s = A[i * k + c];
+            for (int q = 0; q < i; ++q) s -= Lm[i * k + q] * U[q * k + c];
+            U[i * k + c] = s;
+        }
+        for (int r = i + 1; r < k; ++r) {
+            double s = A[r * k + i];
+            for (int q = 0; q < i; ++q) s -= Lm[r * k + q] * U[q * k + i];
+            Lm[r * k + i] = s / U[i * k + i];
+        }
+    }
+    for (int r = 0; r < k; ++r)
+        for (int c = 0; c < k; ++c) L->QI[(r + 1) * n + (c + 1)] = U[c * k + r];
+
+    const size_t cnt = (size_t)n * 3 * plan->nc;
+    bool ok = cudaMalloc((void**)&L->Th, cnt * sizeof(double2)) == cudaSuccess;
+    for (int b = 0; b < 2 && ok; ++b) {
+        ok = ok && cudaMalloc((void**)&L->FI[b], cnt * sizeof(double2)) == cudaSuccess;
+        ok = ok && cudaMalloc((void**)&L->FE[b], cnt * sizeof(double2)) == cudaSuccess;
+    }
+    if (!ok) {
+        set_error("cudaMalloc", cudaGetLastError());
+        sdc_level_destroy(L);
+        return MLSDC_ERR_ALLOC;
+    }
+    *out = L;
+    return MLSDC_OK;
+}
+
+extern "C" mlsdc_status sdc_level_destroy(sdc_level_t L) {
+    if (!L) return MLSDC_ERR_INVALID;
+    cudaFree(L->Th);
+    for (int b = 0; b < 2; ++b) {
+        cudaFree(L->FI[b]);
+        cudaFree(L->FE[b]);
+    }
+    delete L;
+    return MLSDC_OK;
+}
+
+extern "C" mlsdc_status sdc_level_matrices(sdc_level_t L, double* t, double* Q, double* QE, double* QI) {
+    if (!L) return MLSDC_ERR_INVALID;
+    const size_t nn = (size_t)L->n * L->n;
+    if (t) std::memcpy(t, L->t.data(), sizeof(double) * L->n);
+    if (Q) std::memcpy(Q, L->Q.data(), sizeof(double) * nn);
+    if (QE) std::memcpy(QE, L->QE.data(), sizeof(double) * nn);
+    if (QI) std::memcpy(QI, L->QI.data(), sizeof(double) * nn);
+    return MLSDC_OK;
+}
+
+extern "C" mlsdc_status sdc_sweep(sdc_level_t L, double dt, double* Theta, const double* FI_old,
+                                  const double* FE_old, double* FI_new, double* FE_new, const double* tau,
+                                  void* stream) {
+    if (!L || !Theta || !FI_old || !FE_old || !FI_new || !FE_new) return MLSDC_ERR_INVALID;
+    if (FI_old == FI_new || FE_old == FE_new) return MLSDC_ERR_INVALID;
+    return sweep(L, dt, (double2*)Theta, (const double2*)FI_old, (const double2*)FE_old, (double2*)FI_new,
+                 (double2*)FE_new, (const double2*)tau, (cudaStream_t)stream);
+}
+
+extern "C" mlsdc_status sdc_step(sdc_level_t L, double* state, double dt, int n_sweeps, void* stream) {
+    if (!L || !state || n_sweeps < 0) return MLSDC_ERR_INVALID;
+    cudaStream_t st = (cudaStream_t)stream;
+    L->launches = 0;
+    mlsdc_status s;
+    if ((s = spread(L, (const double2*)state, st)) != MLSDC_OK) return s;
+    const size_t node = (size_t)3 * L->plan->nc;
+    for (int k = 0; k < n_sweeps; ++k) {
+        const int c = L->cur;
+        if ((s = sweep(L, dt, L->Th, L->FI[c], L->FE[c], L->FI[1 - c], L->FE[1 - c], nullptr, st)) != MLSDC_OK)
+            return s;
+        L->cur = 1 - c;
+    }
+    MLSDC_CUDA(cudaMemcpyAsync(state, L->Th + (L->n - 1) * node, node * sizeof(double2), cudaMemcpyDeviceToDevice,
+                               st));
+    return MLSDC_OK;
+}
+
+extern "C" mlsdc_status mlsdc_create(sdc_level_t fine, sdc_level_t coarse, mlsdc_t* out) {
+    if (!fine || !coarse || !out) return MLSDC_ERR_INVALID;
+    if (coarse->plan->R > fine->plan->R) return MLSDC_ERR_INVALID;
+    mlsdc_t ml = new mlsdc_s();
+    ml->f = fine;
+    ml->c = coarse;
+    const int nf = fine->n, ncn = coarse->n;
+    std::memset(&ml->Pcf, 0, sizeof(TransferMat));
+    std::memset(&ml->Pfc, 0, sizeof(TransferMat));
+    for (int i = 0; i < ncn; ++i)
+        for (int j = 0; j < nf; ++j) ml->Pcf.a[i * nf + j] = lagrange(fine->t, j, coarse->t[i]);
+    for (int m = 0; m < nf; ++m)
+        for (int i = 0; i < ncn; ++i) ml->Pfc.a[m * ncn + i] = lagrange(coarse->t, i, fine->t[m]);
+    const int Rf = fine->plan->R, Rc = coarse->plan->R;
+    std::vector<int> c2f(coarse->plan->nc);
+    for (int m = 0; m <= Rc; ++m)
+        for (int n = m; n <= Rc; ++n) c2f[moff(Rc, m) + n - m] = moff(Rf, m) + n - m;
+    const size_t cnt = (size_t)ncn * 3 * coarse->plan->nc;
+    bool ok = cudaMalloc((void**)&ml->d_c2f, c2f.size() * sizeof(int)) == cudaSuccess;
+    ok = ok && cudaMalloc((void**)&ml->Ts, cnt * sizeof(double2)) == cudaSuccess;
+    ok = ok && cudaMalloc((void**)&ml->FIs, cnt * sizeof(double2)) == cudaSuccess;
+    ok = ok && cudaMalloc((void**)&ml->FEs, cnt * sizeof(double2)) == cudaSuccess;
+    ok = ok && cudaMalloc((void**)&ml->tau, cnt * sizeof(double2)) == cudaSuccess;
+    ok = ok && cudaStreamCreateWithFlags(&ml->cap, cudaStreamNonBlocking) == cudaSuccess;
+    ok = ok && cudaMemcpy(ml->d_c2f, c2f.data(), c2f.size() * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess;
+    if (!ok) {
+        set_error("mlsdc_create", cudaGetLastError());
+        mlsdc_destroy(ml);
+        return MLSDC_ERR_ALLOC;
+    }
+    *out = ml;
+    return MLSDC_OK;
+}
+
+extern "C" mlsdc_status mlsdc_destroy(mlsdc_t ml) {
+    if (!ml) return MLSDC_ERR_INVALID;
+    for (auto& kv : ml->graphs) cudaGraphExecDestroy(kv.second);
+    cudaFree(ml->d_c2f);
+    cudaFree(ml->Ts);
+    cudaFree(ml->FIs);
+    cudaFree(ml->FEs);
+    cudaFree(ml->tau);
+    if (ml->cap) cudaStreamDestroy(ml->cap);
+    delete ml;
+    return MLSDC_OK;
+}
+
+namespace mlsdc {
+
+static mlsdc_status mlsdc_enqueue(mlsdc_t ml, double* state, double dt, int n_iter, int n_c, cudaStream_t st) {
+    sdc_level_t F = ml->f, C = ml->c;
+    const int ncf = F->plan->nc, ncc = C->plan->nc;
+    const size_t nodef = (size_t)3 * ncf, nodec = (size_t)3 * ncc;
+    const int nfn = F->n, ncn = C->n;
+    F->launches = C->launches = 0;
+    int64_t own = 0;
+    mlsdc_status s;
+    // initialisation: fine spread; coarse node 0 = restriction of Theta^n, evaluated once
+    if ((s = spread(F, (const double2*)state, st)) != MLSDC_OK) return s;
+    k_restrict<<<grid_for(3 * ncc), 256, 0, st>>>(F->Th, C->Th, ml->d_c2f, ncf, ncc, nfn, 0, 1, ml->Pcf);
+    MLSDC_LAUNCHED("k_restrict");
+    own++;
+    if ((s = eval_FI(C, C->Th, C->FI[C->cur], st)) != MLSDC_OK) return s;
+    if ((s = eval_FE(C, C->Th, C->FE[C->cur], st)) != MLSDC_OK) return s;
+    FasArgs fa;
+    std::memset(&fa, 0, sizeof(fa));
+    fa.nfn = nfn;
+    fa.ncn = ncn;
+    for (int i = 0; i < nfn * nfn; ++i) fa.Qf[i] = F->Q[i];
+    for (int i = 0; i < ncn * ncn; ++i) fa.Qc[i] = C->Q[i];
+    for (int i = 0; i < ncn * nfn; ++i) fa.Pcf[i] = ml->Pcf.a[i];
+    for (int it = 0; it < n_iter; ++it) {
+        // A) fine sweep
+        int cf = F->cur;
+        if ((s = sweep(F, dt, F->Th, F->FI[cf], F->FE[cf], F->FI[1 - cf], F->FE[1 - cf], nullptr, st)) != MLSDC_OK)
+            return s;
+        F->cur = cf = 1 - cf;
+        // B) restrict nodes 1..Mc, evaluate, save
+        k_restrict<<<grid_for(3 * ncc), 256, 0, st>>>(F->Th, C->Th, ml->d_c2f, ncf, ncc, nfn, 1, ncn, ml->Pcf);
+        MLSDC_LAUNCHED("k_restrict");
+        own++;
+        int cc = C->cur;
+        for (int i = 1; i < ncn; ++i) {
+            if ((s = eval_FI(C, C->Th + i * nodec, C->FI[cc] + i * nodec, st)) != MLSDC_OK) return s;
+            if ((s = eval_FE(C, C->Th + i * nodec, C->FE[cc] + i * nodec, st)) != MLSDC_OK) return s;
+        }
+        const size_t bytes = (size_t)ncn * nodec * sizeof(double2);
+        MLSDC_CUDA(cudaMemcpyAsync(ml->Ts, C->Th, bytes, cudaMemcpyDeviceToDevice, st));
+        MLSDC_CUDA(cudaMemcpyAsync(ml->FIs, C->FI[cc], bytes, cudaMemcpyDeviceToDevice, st));
+        MLSDC_CUDA(cudaMemcpyAsync(ml->FEs, C->FE[cc], bytes, cudaMemcpyDeviceToDevice, st));
+        // C) FAS correction, coarse sweeps
+        k_fas_tau<<<grid_for(3 * ncc), 256, 0, st>>>(F->Th, F->FI[cf], F->FE[cf], C->Th, C->FI[cc], C->FE[cc],
+                                                     ml->tau, ml->d_c2f, ncf, ncc, dt, fa);
+        MLSDC_LAUNCHED("k_fas_tau");
+        own++;
+        for (int k = 0; k < n_c; ++k) {
+            cc = C->cur;
+            if ((s = sweep(C, dt, C->Th, C->FI[cc], C->FE[cc], C->FI[1 - cc], C->FE[1 - cc], ml->tau, st)) !=
+                MLSDC_OK)
+                return s;
+            C->cur = 1 - cc;
+        }
+        cc = C->cur;
+        // D) interpolate the coarse corrections to fine nodes 1..Mf
+        k_interp<<<grid_for(3 * ncc), 256, 0, st>>>(F->Th, F->FI[cf], F->FE[cf], C->Th, C->FI[cc], C->FE[cc],
+                                                    ml->Ts, ml->FIs, ml->FEs, ml->d_c2f, ncf, ncc, nfn, ncn,
+                                                    ml->Pfc);
+        MLSDC_LAUNCHED("k_interp");
+        own++;
+    }
+    MLSDC_CUDA(cudaMemcpyAsync(state, F->Th + (nfn - 1) * nodef, nodef * sizeof(double2), cudaMemcpyDeviceToDevice,
+                               st));
+    ml->launches = own + F->launches + C->launches;
+    return MLSDC_OK;
+}
+
+}  // namespace mlsdc
+
+extern "C" mlsdc_status mlsdc_step(mlsdc_t ml, double* state, double dt, int n_iter, int n_coarse_sweeps,
+                                   int use_graph, void* stream) {
+    if (!ml || !state || n_iter < 0 || n_coarse_sweeps < 0) return MLSDC_ERR_INVALID;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!use_graph) return mlsdc_enqueue(ml, state, dt, n_iter, n_coarse_sweeps, st);
+    auto key = std::make_tuple(state, dt, n_iter, n_coarse_sweeps);
+    auto it = ml->graphs.find(key);
+    if (it == ml->graphs.end()) {
+        // The F ping-pong parity must be the same at every replay: it is,
+        // because each step flips each level's buffer a fixed number of times;
+        // reset both to 0 so capture and replays agree.
+        ml->f->cur = 0;
+        ml->c->cur = 0;
+        MLSDC_CUDA(cudaStreamBeginCapture(ml->cap, cudaStreamCaptureModeThreadLocal));
+        mlsdc_status s = mlsdc_enqueue(ml, state, dt, n_iter, n_coarse_sweeps, ml->cap);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(ml->cap, &g);
+        if (s != MLSDC_OK) {
+            if (g) cudaGraphDestroy(g);
+            return s;
+        }
+        if (e != cudaSuccess) {
+            set_error("cudaStreamEndCapture", e);
+            return MLSDC_ERR_CUDA;
+        }
+        cudaGraphExec_t ex = nullptr;
+        e = cudaGraphInstantiate(&ex, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            set_error("cudaGraphInstantiate", e);
+            return MLSDC_ERR_CUDA;
+        }
+        it = ml->graphs.emplace(key, ex).first;
+        ml->f->cur = 0;
+        ml->c->cur = 0;
+    }
+    MLSDC_CUDA(cudaGraphLaunch(it->second, st));
+    return MLSDC_OK;
+}
+
+extern "C" mlsdc_status mlsdc_launch_count(mlsdc_t ml, int64_t* launches) {
+    if (!ml || !launches) return MLSDC_ERR_INVALID;
+    *launches = ml->launches;
+    return MLSDC_OK;
+}

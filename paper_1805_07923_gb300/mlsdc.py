@@ -1,0 +1,269 @@
+"""Thin ctypes binding of the C-ABI library libmlsdc_sh.so (include/mlsdc_sh.h).
+
+Functions keep the C names; arguments are torch CUDA tensors (float64,
+contiguous; complex values as interleaved (re, im) pairs, i.e. a
+complex128 tensor or a float64 tensor of twice the length).  The binding only
+marshals pointers and sizes: every step of the computation runs in the
+library's CUDA kernels.  There is no CPU fallback: if the library is missing
+or no GPU is present, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmlsdc_sh.so")
+
+MLSDC_FP64, MLSDC_TF32, MLSDC_BF16X3, MLSDC_FP32 = 0, 1, 2, 3
+PRECISIONS = {"fp64": MLSDC_FP64, "tf32": MLSDC_TF32, "bf16x3": MLSDC_BF16X3, "fp32": MLSDC_FP32}
+
+_lib = None
+
+
+class SweParams(ctypes.Structure):
+    _fields_ = [("a", ctypes.c_double), ("omega", ctypes.c_double), ("g", ctypes.c_double),
+                ("phibar", ctypes.c_double), ("nu", ctypes.c_double)]
+
+
+DEFAULT_PARAMS = dict(a=6.37122e6, omega=7.292e-5, g=9.80616, phibar=9.80616e4, nu=1.0e5)
+
+_VP, _DP, _I, _D, _I64 = ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int64
+
+_SIGS = {
+    "mlsdc_status_string": ([_I], ctypes.c_char_p),
+    "mlsdc_last_error": ([], ctypes.c_char_p),
+    "sh_plan": ([_I, _I, _I, _I, ctypes.POINTER(_VP)], _I),
+    "sh_plan_destroy": ([_VP], _I),
+    "sh_plan_grid": ([_VP, _DP, _DP], _I),
+    "sh_plan_device_bytes": ([_VP, ctypes.POINTER(_I64)], _I),
+    "sh_inverse": ([_VP, _DP, _DP, _I, _VP], _I),
+    "sh_forward": ([_VP, _DP, _DP, _I, _VP], _I),
+    "swe_explicit_rhs": ([_VP, ctypes.POINTER(SweParams), _DP, _DP, _VP], _I),
+    "swe_implicit_rhs": ([_VP, ctypes.POINTER(SweParams), _DP, _DP, _VP], _I),
+    "swe_implicit_solve": ([_VP, ctypes.POINTER(SweParams), _D, _DP, _DP, _VP], _I),
+    "sdc_level_create": ([_VP, ctypes.POINTER(SweParams), _I, ctypes.POINTER(_VP)], _I),
+    "sdc_level_destroy": ([_VP], _I),
+    "sdc_level_matrices": ([_VP, _DP, _DP, _DP, _DP], _I),
+    "sdc_sweep": ([_VP, _D, _DP, _DP, _DP, _DP, _DP, _DP, _VP], _I),
+    "sdc_step": ([_VP, _DP, _D, _I, _VP], _I),
+    "mlsdc_create": ([_VP, _VP, ctypes.POINTER(_VP)], _I),
+    "mlsdc_destroy": ([_VP], _I),
+    "mlsdc_step": ([_VP, _DP, _D, _I, _I, _I, _VP], _I),
+    "mlsdc_launch_count": ([_VP, ctypes.POINTER(_I64)], _I),
+    "mlsdc_check_finite": ([_DP, _I64, ctypes.POINTER(_I), _VP], _I),
+    "mlsdc_profile_rhs": ([_VP, ctypes.POINTER(SweParams), _DP, _DP, _I, ctypes.POINTER(ctypes.c_float), _VP], _I),
+}
+
+
+def lib():
+    """Load the library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: run __graft_entry__.build() first "
+                               "(there is no CPU fallback)")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (args, res) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+    return _lib
+
+
+def exported_symbols() -> list[str]:
+    return list(_SIGS)
+
+
+class MlsdcError(RuntimeError):
+    pass
+
+
+def _check(status: int, what: str):
+    if status != 0:
+        L = lib()
+        raise MlsdcError(f"{what}: {L.mlsdc_status_string(status).decode()} "
+                         f"({L.mlsdc_last_error().decode()})")
+
+
+def _ptr(t: torch.Tensor | None, numel_f64: int | None = None):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise MlsdcError("tensor must live on a CUDA device")
+    if t.dtype not in (torch.float64, torch.complex128):
+        raise MlsdcError(f"tensor must be float64 or complex128, got {t.dtype}")
+    if not t.is_contiguous():
+        raise MlsdcError("tensor must be contiguous")
+    if numel_f64 is not None:
+        n = t.numel() * (2 if t.dtype == torch.complex128 else 1)
+        if n < numel_f64:
+            raise MlsdcError(f"tensor holds {n} doubles, {numel_f64} needed")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def swe_params(**kw) -> SweParams:
+    d = dict(DEFAULT_PARAMS)
+    d.update(kw)
+    return SweParams(**d)
+
+
+def n_coeffs(R: int) -> int:
+    return (R + 1) * (R + 2) // 2
+
+
+class Plan:
+    """sh_plan: Gaussian grid and Legendre tables of one truncation."""
+
+    def __init__(self, R: int, nlon: int, nlat: int, precision="fp64"):
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        h = ctypes.c_void_p()
+        _check(lib().sh_plan(R, nlon, nlat, prec, ctypes.byref(h)), "sh_plan")
+        self.h, self.R, self.I, self.J, self.precision = h, R, nlon, nlat, prec
+        self.nc = n_coeffs(R)
+
+    def close(self):
+        if self.h:
+            lib().sh_plan_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def grid(self):
+        import numpy as np
+        mu = np.zeros(self.J)
+        w = np.zeros(self.J)
+        _check(lib().sh_plan_grid(self.h, mu.ctypes.data_as(ctypes.c_void_p), w.ctypes.data_as(ctypes.c_void_p)),
+               "sh_plan_grid")
+        return mu, w
+
+    def device_bytes(self) -> int:
+        b = ctypes.c_int64()
+        _check(lib().sh_plan_device_bytes(self.h, ctypes.byref(b)), "sh_plan_device_bytes")
+        return b.value
+
+
+def sh_inverse(plan: Plan, spec: torch.Tensor, grid: torch.Tensor, nf: int, stream=None):
+    _check(lib().sh_inverse(plan.h, _ptr(spec, 2 * nf * plan.nc), _ptr(grid, nf * plan.I * plan.J), nf,
+                            _stream(stream)), "sh_inverse")
+
+
+def sh_forward(plan: Plan, grid: torch.Tensor, spec: torch.Tensor, nf: int, stream=None):
+    _check(lib().sh_forward(plan.h, _ptr(grid, nf * plan.I * plan.J), _ptr(spec, 2 * nf * plan.nc), nf,
+                            _stream(stream)), "sh_forward")
+
+
+def swe_explicit_rhs(plan: Plan, prm: SweParams, state: torch.Tensor, FE: torch.Tensor, stream=None):
+    _check(lib().swe_explicit_rhs(plan.h, ctypes.byref(prm), _ptr(state, 6 * plan.nc), _ptr(FE, 6 * plan.nc),
+                                  _stream(stream)), "swe_explicit_rhs")
+
+
+def swe_implicit_rhs(plan: Plan, prm: SweParams, state: torch.Tensor, FI: torch.Tensor, stream=None):
+    _check(lib().swe_implicit_rhs(plan.h, ctypes.byref(prm), _ptr(state, 6 * plan.nc), _ptr(FI, 6 * plan.nc),
+                                  _stream(stream)), "swe_implicit_rhs")
+
+
+def swe_implicit_solve(plan: Plan, prm: SweParams, alpha: float, b: torch.Tensor, x: torch.Tensor, stream=None):
+    _check(lib().swe_implicit_solve(plan.h, ctypes.byref(prm), float(alpha), _ptr(b, 6 * plan.nc),
+                                    _ptr(x, 6 * plan.nc), _stream(stream)), "swe_implicit_solve")
+
+
+class Level:
+    """sdc_level: a plan, the physics and n Gauss-Lobatto nodes."""
+
+    def __init__(self, plan: Plan, n_nodes: int, prm: SweParams | None = None):
+        self.plan = plan
+        self.prm = prm if prm is not None else swe_params()
+        h = ctypes.c_void_p()
+        _check(lib().sdc_level_create(plan.h, ctypes.byref(self.prm), n_nodes, ctypes.byref(h)), "sdc_level_create")
+        self.h, self.n = h, n_nodes
+
+    def close(self):
+        if self.h:
+            lib().sdc_level_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def matrices(self):
+        import numpy as np
+        n = self.n
+        t, Q, QE, QI = np.zeros(n), np.zeros(n * n), np.zeros(n * n), np.zeros(n * n)
+        args = [a.ctypes.data_as(ctypes.c_void_p) for a in (t, Q, QE, QI)]
+        _check(lib().sdc_level_matrices(self.h, *args), "sdc_level_matrices")
+        return t, Q.reshape(n, n), QE.reshape(n, n), QI.reshape(n, n)
+
+
+def sdc_sweep(level: Level, dt: float, Theta, FI_old, FE_old, FI_new, FE_new, tau=None, stream=None):
+    n = 6 * level.n * level.plan.nc
+    _check(lib().sdc_sweep(level.h, float(dt), _ptr(Theta, n), _ptr(FI_old, n), _ptr(FE_old, n), _ptr(FI_new, n),
+                           _ptr(FE_new, n), _ptr(tau, n), _stream(stream)), "sdc_sweep")
+
+
+def sdc_step(level: Level, state: torch.Tensor, dt: float, n_sweeps: int, stream=None):
+    _check(lib().sdc_step(level.h, _ptr(state, 6 * level.plan.nc), float(dt), int(n_sweeps), _stream(stream)),
+           "sdc_step")
+
+
+class MLSDC:
+    """Two-level MLSDC object (fine and coarse levels must outlive it)."""
+
+    def __init__(self, fine: Level, coarse: Level):
+        self.fine, self.coarse = fine, coarse
+        h = ctypes.c_void_p()
+        _check(lib().mlsdc_create(fine.h, coarse.h, ctypes.byref(h)), "mlsdc_create")
+        self.h = h
+
+    def close(self):
+        if self.h:
+            lib().mlsdc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def launch_count(self) -> int:
+        v = ctypes.c_int64()
+        _check(lib().mlsdc_launch_count(self.h, ctypes.byref(v)), "mlsdc_launch_count")
+        return v.value
+
+
+def mlsdc_step(ml: MLSDC, state: torch.Tensor, dt: float, n_iter: int, n_coarse_sweeps: int, use_graph: bool = False,
+               stream=None):
+    _check(lib().mlsdc_step(ml.h, _ptr(state, 6 * ml.fine.plan.nc), float(dt), int(n_iter), int(n_coarse_sweeps),
+                            1 if use_graph else 0, _stream(stream)), "mlsdc_step")
+
+
+def mlsdc_check_finite(x: torch.Tensor, stream=None) -> bool:
+    ok = ctypes.c_int()
+    n = x.numel() * (2 if x.dtype == torch.complex128 else 1)
+    _check(lib().mlsdc_check_finite(_ptr(x), n, ctypes.byref(ok), _stream(stream)), "mlsdc_check_finite")
+    return bool(ok.value)
+
+
+def mlsdc_profile_rhs(plan: Plan, prm: SweParams, state: torch.Tensor, FE: torch.Tensor, reps: int = 50,
+                      stream=None) -> list[float]:
+    """Mean ms per launch of the three F_E stage kernels (synthesis, grid, analysis)."""
+    out = (ctypes.c_float * 3)()
+    _check(lib().mlsdc_profile_rhs(plan.h, ctypes.byref(prm), _ptr(state, 6 * plan.nc), _ptr(FE, 6 * plan.nc),
+                                   int(reps), out, _stream(stream)), "mlsdc_profile_rhs")
+    return [float(v) for v in out]
