@@ -99,6 +99,32 @@ mlsdc_status sh_plan_device_bytes(sh_plan_t plan, int64_t* bytes);
  * longitude DFT).  spec: [nf][N_c] complex; grid: [nf][J][I]; 1 <= nf <= 16. */
 mlsdc_status sh_inverse(sh_plan_t plan, const double* spec, double* grid, int nf, void* stream);
 
+/* sh_inverse_static: the same synthesis as sh_inverse, for callers that must
+ * not allocate device memory at all -- for example a host framework that has
+ * already handed every byte of the GPU to its own memory pool, or a long-running
+ * service whose device-memory footprint is fixed when it starts and may not
+ * grow afterwards.  Such callers cannot create an sh_plan (it allocates its
+ * tables and scratch), so this entry point takes the sizes directly, computes
+ * the Gaussian latitudes, Legendre functions and FFT twiddles on the device,
+ * and keeps its intermediate values in one static 4 MiB device array that
+ * every GPU loading this library holds until the process exits.  It calls no
+ * cudaMalloc, cudaFree or other allocating routine.  The paper has no
+ * counterpart: this is an interface variant, not a step of the method.
+ * Sizes: as sh_plan (R >= 1; nlon a power of two in [16, 1024], nlon >= 3R+1;
+ * nlat even, nlat >= (3R+1)/2, nlat <= 2048), 1 <= nf <= 16, and
+ * nf * nlat * (R+1) <= 261120 (e.g. nf <= 5 at T170 on 512 x 256); larger
+ * requests return MLSDC_ERR_INVALID with the limit in mlsdc_last_error().
+ * spec: [nf][N_c] complex, grid: [nf][nlat][nlon] (caller-owned device memory).
+ * The first call on each device looks up the static array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture.  All calls share the one array and it keeps the last
+ * call's contents; every value a call reads from it is written earlier in
+ * the same call, so nothing needs clearing, but calls that overlap on the GPU
+ * (different streams, or different host threads, at the same time) race on
+ * it and must be ordered by the caller. */
+mlsdc_status sh_inverse_static(int R, int nlon, int nlat, const double* spec, double* grid, int nf,
+                               void* stream);
+
 /* sh_forward: grid -> spectral, Eq. fourier_transform (with its 1/I) then
  * Eq. legendre_transform (Gaussian weights); Im of m = 0 set to zero.
  * grid: [nf][J][I]; spec: [nf][N_c] complex; 1 <= nf <= 16. */

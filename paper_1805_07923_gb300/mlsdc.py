@@ -41,6 +41,7 @@ _SIGS = {
     "sh_plan_device_bytes": ([_VP, ctypes.POINTER(_I64)], _I),
     "sh_inverse": ([_VP, _DP, _DP, _I, _VP], _I),
     "sh_forward": ([_VP, _DP, _DP, _I, _VP], _I),
+    "sh_inverse_static": ([_I, _I, _I, _DP, _DP, _I, _VP], _I),
     "swe_explicit_rhs": ([_VP, ctypes.POINTER(SweParams), _DP, _DP, _VP], _I),
     "swe_implicit_rhs": ([_VP, ctypes.POINTER(SweParams), _DP, _DP, _VP], _I),
     "swe_implicit_solve": ([_VP, ctypes.POINTER(SweParams), _D, _DP, _DP, _VP], _I),
@@ -158,6 +159,13 @@ class Plan:
 def sh_inverse(plan: Plan, spec: torch.Tensor, grid: torch.Tensor, nf: int, stream=None):
     _check(lib().sh_inverse(plan.h, _ptr(spec, 2 * nf * plan.nc), _ptr(grid, nf * plan.I * plan.J), nf,
                             _stream(stream)), "sh_inverse")
+
+
+def sh_inverse_static(R: int, nlon: int, nlat: int, spec: torch.Tensor, grid: torch.Tensor, nf: int, stream=None):
+    """Plan-free synthesis that allocates nothing (static device scratch)."""
+    nc = n_coeffs(R)
+    _check(lib().sh_inverse_static(int(R), int(nlon), int(nlat), _ptr(spec, 2 * nf * nc), _ptr(grid, nf * nlon * nlat),
+                                   int(nf), _stream(stream)), "sh_inverse_static")
 
 
 def sh_forward(plan: Plan, grid: torch.Tensor, spec: torch.Tensor, nf: int, stream=None):
