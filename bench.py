@@ -333,16 +333,27 @@ def main():
     step_ms_mean = total_ms / K
     top = shares[0]
     peaks = load_peaks()
-    kern_names = {"legendre_synthesis": "k_synth_rhs_f64", "grid_fft_products": "k_grid_rhs_f64",
-                  "legendre_analysis": "k_anal_rhs_f64"}
-    if prec == "fp64":
-        peak = measured_fp64_tflops(torch, dev)
-        roof = {"bound": "alu", "achieved": top[4] / (top[3] * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
-                "peak_source": "measured cuBLAS DGEMM on this GPU (float64 FMA pipe)"}
+    tname = {"fp64": "double", "fp32": "float", "tf32": "float", "bf16x3": "float"}[prec]
+    kern_names = {"legendre_synthesis": f"k_synth_rhs<{tname}>", "grid_fft_products": f"k_grid_rhs<{tname}>",
+                  "legendre_analysis": f"k_anal_rhs<{tname}>"}
+    if prec in ("tf32", "bf16x3"):
+        kern_names.update({"legendre_synthesis": f"k_tc_synth<{prec}>", "legendre_analysis": f"k_tc_anal<{prec}>"})
+    achieved = top[4] / (top[3] * 1e-3) / 1e12
+    sm_max = (clk.get("sm_max_mhz") or 2070.0) * 1e6
+    if top[2] == "grid_fft_products" or prec in ("fp64", "fp32"):
+        if prec == "fp64":
+            peak, src = measured_fp64_tflops(torch, dev), "measured cuBLAS DGEMM on this GPU (float64 pipe)"
+        else:
+            peak = 152 * 128 * 2 * sm_max / 1e12
+            src = "float32 CUDA-core FMA: 152 SMs x 128 lanes x 2 flops x max SM clock"
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "peak_source": src}
     else:
-        peak = peaks.get("bf16_tflops", 1925.0)
-        roof = {"bound": "tensor", "achieved": top[4] / (top[3] * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
-                "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst)"}
+        bf16 = peaks.get("bf16_tflops", 1900.0)
+        if prec == "tf32":
+            peak, src = bf16 * 1.1 / 2.25, "measured bf16 burst peak x nominal tf32/bf16 ratio (1.1/2.25)"
+        else:
+            peak, src = bf16, "measured bf16 burst peak (bf16 hi/lo operands; 3 tensor products per algorithmic one)"
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "peak_source": src}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["traffic"] = traffic_for(f"{top[1]}:{kern_names[top[2]]}")
     roof["kernel"] = f"{top[2]} ({kern_names[top[2]]}) at {top[1]}"

@@ -93,6 +93,12 @@ mlsdc_status sh_plan_destroy(sh_plan_t plan);
 mlsdc_status sh_plan_grid(sh_plan_t plan, double* mu_host, double* w_host);
 /* Bytes of device memory the plan holds (tables plus scratch). */
 mlsdc_status sh_plan_device_bytes(sh_plan_t plan, int64_t* bytes);
+/* Device-side error code recorded by the plan's tensor-core kernels (0 = none;
+ * 1 = a TMA wait gave up, 2 = an MMA completion wait gave up).  Every such
+ * wait is bounded: on timeout the kernel records the code, releases its
+ * tensor memory and returns without writing results.  Synchronises the
+ * device.  Always 0 for MLSDC_FP64 / MLSDC_FP32 plans. */
+mlsdc_status sh_plan_device_error(sh_plan_t plan, int* code);
 
 /* sh_inverse: spectral -> grid for nf independent scalar fields,
  * Eq. spectral_to_physical_space (Legendre sum per m, then the inverse

@@ -34,6 +34,11 @@ void set_error_text(const std::string& s);
     } while (0)
 
 inline int nc_of(int R) { return (R + 1) * (R + 2) / 2; }
+
+// Raise (never lower) a kernel's dynamic shared-memory limit.  The attribute
+// belongs to the kernel, not to a plan, so a plan needing less must not undo
+// the setting another live plan relies on.
+mlsdc_status raise_smem_limit(const void* fn, size_t bytes);
 inline int moff(int R, int m) { return m * (R + 1) - m * (m - 1) / 2; }
 
 // Work item of a Legendre kernel: zonal wavenumber m and the first
@@ -45,13 +50,13 @@ struct Chunk {
 
 // Mixed-precision tables and scratch of a plan (float32 path).
 struct MPTables {
-    float* P32 = nullptr;   // [nc][J2] float32 copy of P
-    float* H32 = nullptr;   // [nc][J2]
-    float2* four_in = nullptr;   // [16][J][R+1]
-    float2* four_out = nullptr;  // [16][J][R+1]
-    // tensor-core operand tables (bf16 hi/lo or tf32), laid out per m-tile
-    void* tc_synth = nullptr;
-    void* tc_anal = nullptr;
+    float* P32 = nullptr;        // [nc][J2] float32 copy of P
+    float* H32 = nullptr;        // [nc][J2]
+    float2* tw32 = nullptr;      // [I/2] float32 twiddles
+    float2* four_in = nullptr;   // [4][J][R+1]
+    float2* four_out = nullptr;  // [5][J][R+1]
+    // tensor-core state (legendre_tc.cu): operand tables, tensor maps, error flag
+    void* tc = nullptr;
     int64_t tc_bytes = 0;
 };
 

@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 
 #include "internal.h"
 
@@ -15,6 +16,21 @@ void set_error(const char* where, cudaError_t e) {
     g_last_error = std::string(where) + ": " + cudaGetErrorString(e);
 }
 void set_error_text(const std::string& s) { g_last_error = s; }
+
+mlsdc_status raise_smem_limit(const void* fn, size_t bytes) {
+    static std::mutex mu;
+    if (bytes <= 48 * 1024) return MLSDC_OK;
+    std::lock_guard<std::mutex> lock(mu);
+    cudaFuncAttributes at;
+    if (cudaFuncGetAttributes(&at, fn) == cudaSuccess && (size_t)at.maxDynamicSharedSizeBytes >= bytes)
+        return MLSDC_OK;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) {
+        set_error("cudaFuncSetAttribute", e);
+        return MLSDC_ERR_CUDA;
+    }
+    return MLSDC_OK;
+}
 
 // Gaussian latitudes: roots of the degree-J Legendre polynomial by Newton's
 // method, ordered north to south, with weights w = 2 / ((1 - mu^2) P_J'(mu)^2).
@@ -245,4 +261,16 @@ extern "C" mlsdc_status sh_plan_device_bytes(sh_plan_t p, int64_t* bytes) {
     if (!p || !bytes) return MLSDC_ERR_INVALID;
     *bytes = p->bytes + p->mp.tc_bytes;
     return MLSDC_OK;
+}
+
+namespace mlsdc {
+mlsdc_status tc_error(sh_plan_t p, int* code);
+}
+
+extern "C" mlsdc_status sh_plan_device_error(sh_plan_t p, int* code) {
+    if (!p || !code) return MLSDC_ERR_INVALID;
+    *code = 0;
+    if (p->precision != MLSDC_TF32 && p->precision != MLSDC_BF16X3) return MLSDC_OK;
+    MLSDC_CUDA(cudaDeviceSynchronize());
+    return mlsdc::tc_error(p, code);
 }

@@ -1,0 +1,262 @@
+// The three stage kernels of one explicit right-hand-side evaluation F_E
+// (Sec. 2, Sec. 3, Sec. 4.1), templated on the arithmetic type T of the
+// Legendre sums and FFTs: T = double (float64 path) or float (mixed
+// precision).  The state is always float64 on input and F_E float64 on
+// output.
+//
+//   k_synth_rhs<T>  per (m, 32 northern latitudes), 4 warps splitting the
+//                   degrees n: Legendre sums split in even/odd n - m so one
+//                   pass serves a latitude and its southern mirror
+//                   (P^m_n(-mu) = (-1)^(n-m) P^m_n(mu), H^m_n(-mu) =
+//                   -(-1)^(n-m) H^m_n(mu)); writes the Fourier coefficients
+//                   of zeta, Phi', U, V                  -> four_in[4][J][R+1]
+//   k_grid_rhs<T>   per latitude: real inverse FFTs, the grid products
+//                   A = (zeta+f)U, B = (zeta+f)V, C = Phi'U, D = Phi'V,
+//                   E = (U^2+V^2)/(2(1-mu^2)), real forward FFTs, weights
+//                   w/(1-mu^2)/I (A..D) or w/I (E)        -> four_out[5][J][R+1]
+//   k_anal_rhs<T>   per (m, 32 degrees), latitude tiles split over warps:
+//                   Gaussian sums with even/odd combinations, then in float64
+//                   F_E = [-div(C,D), -div(A,B), curl(A,B) + n(n+1)/a^2 E].
+#pragma once
+
+#include "complex.cuh"
+#include "internal.h"
+
+namespace mlsdc {
+
+constexpr int kSynthWarps = 4;
+constexpr int kAnalWarpsMax = 4;
+
+// U^m = (1/a) sum_n [ i m chi P - psi H ],  V^m = (1/a) sum_n [ i m psi P + chi H ]
+// with psi, chi = -a^2/(n(n+1)) (zeta, delta) (Helmholtz, Sec. 2).
+template <class T>
+__global__ void __launch_bounds__(32 * kSynthWarps) k_synth_rhs(const double2* __restrict__ state,
+                                                                const T* __restrict__ P, const T* __restrict__ H,
+                                                                const Chunk* __restrict__ chunks, int R, int J2,
+                                                                int nc, double a, C_t<T>* __restrict__ four) {
+    using C = C_t<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* sc = reinterpret_cast<C*>(smem_raw);  // [nm][4]: zeta, Phi', chi, psi; reused for the reduction
+    const Chunk ch = chunks[blockIdx.x];
+    const int m = ch.m;
+    const int nm = R + 1 - m;
+    const int off = m * (R + 1) - m * (m - 1) / 2;
+    for (int k = threadIdx.x; k < nm; k += blockDim.x) {
+        const int n = m + k;
+        const double s = n > 0 ? -a * a / (n * (n + 1.0)) : 0.0;
+        const double2 ph = state[off + k];
+        const double2 ze = state[nc + off + k];
+        const double2 de = state[2 * nc + off + k];
+        sc[4 * k + 0] = mkc(T(ze.x), T(ze.y));
+        sc[4 * k + 1] = mkc(T(ph.x), T(ph.y));
+        sc[4 * k + 2] = mkc(T(de.x * s), T(de.y * s));
+        sc[4 * k + 3] = mkc(T(ze.x * s), T(ze.y * s));
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int wid = threadIdx.x >> 5;
+    const int j = ch.start + lane;
+    const bool live = j < J2;
+    const C zero = mkc(T(0), T(0));
+    // this warp sums k = wid, wid + 4, ...: one parity (wid & 1) only
+    C az = zero, ap = zero, axP = zero, asP = zero, asH = zero, axH = zero;
+    if (live) {
+        const T* Pm = P + (size_t)off * J2 + j;
+        const T* Hm = H + (size_t)off * J2 + j;
+#pragma unroll 8
+        for (int k = wid; k < nm; k += kSynthWarps) {
+            const T p = Pm[(size_t)k * J2], h = Hm[(size_t)k * J2];
+            const C z = sc[4 * k], f = sc[4 * k + 1], x = sc[4 * k + 2], s = sc[4 * k + 3];
+            cfma(az, p, z);
+            cfma(ap, p, f);
+            cfma(axP, p, x);
+            cfma(asP, p, s);
+            cfma(asH, h, s);
+            cfma(axH, h, x);
+        }
+    }
+    __syncthreads();  // coefficient table no longer needed: reuse it for the partial sums
+    C* red = sc;      // [kSynthWarps][6][32]
+    red[(wid * 6 + 0) * 32 + lane] = az;
+    red[(wid * 6 + 1) * 32 + lane] = ap;
+    red[(wid * 6 + 2) * 32 + lane] = axP;
+    red[(wid * 6 + 3) * 32 + lane] = asP;
+    red[(wid * 6 + 4) * 32 + lane] = asH;
+    red[(wid * 6 + 5) * 32 + lane] = axH;
+    __syncthreads();
+    if (wid != 0 || !live) return;
+    C e[6], o[6];
+    for (int q = 0; q < 6; ++q) {
+        e[q] = cadd(red[(0 * 6 + q) * 32 + lane], red[(2 * 6 + q) * 32 + lane]);
+        o[q] = cadd(red[(1 * 6 + q) * 32 + lane], red[(3 * 6 + q) * 32 + lane]);
+    }
+    const T ia = T(1.0 / a);
+    const T dm = T(m);
+    const int J = 2 * J2;
+    const int jS = J - 1 - j;
+    const size_t fs = (size_t)J * (R + 1);
+    // north: P-sums e + o, H-sums e + o; south: P-sums e - o, H-sums o - e
+    const C zN = cadd(e[0], o[0]), zS = csub(e[0], o[0]);
+    const C pN = cadd(e[1], o[1]), pS = csub(e[1], o[1]);
+    const C xPN = cadd(e[2], o[2]), xPS = csub(e[2], o[2]);
+    const C sPN = cadd(e[3], o[3]), sPS = csub(e[3], o[3]);
+    const C sHN = cadd(e[4], o[4]), sHS = csub(o[4], e[4]);
+    const C xHN = cadd(e[5], o[5]), xHS = csub(o[5], e[5]);
+    four[0 * fs + (size_t)j * (R + 1) + m] = zN;
+    four[0 * fs + (size_t)jS * (R + 1) + m] = zS;
+    four[1 * fs + (size_t)j * (R + 1) + m] = pN;
+    four[1 * fs + (size_t)jS * (R + 1) + m] = pS;
+    four[2 * fs + (size_t)j * (R + 1) + m] = cscale(csub(cim(dm, xPN), sHN), ia);
+    four[2 * fs + (size_t)jS * (R + 1) + m] = cscale(csub(cim(dm, xPS), sHS), ia);
+    four[3 * fs + (size_t)j * (R + 1) + m] = cscale(cadd(cim(dm, sPN), xHN), ia);
+    four[3 * fs + (size_t)jS * (R + 1) + m] = cscale(cadd(cim(dm, sPS), xHS), ia);
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_grid_rhs(const C_t<T>* __restrict__ four_in, C_t<T>* __restrict__ four_out,
+                                                  const double* __restrict__ mu, const double* __restrict__ w,
+                                                  const C_t<T>* __restrict__ tw, int R, int I, int logI, int J,
+                                                  double two_omega) {
+    using C = C_t<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* sx = reinterpret_cast<C*>(smem_raw);  // [9][I/2]: zeta, Phi', U, V packed rows, then A..E
+    const int j = blockIdx.x;
+    const int Hn = I >> 1, logH = logI - 1;
+    const size_t fs = (size_t)J * (R + 1);
+    for (int t = threadIdx.x; t < 4 * Hn; t += blockDim.x) {
+        const int f = t >> logH, k = t & (Hn - 1);
+        sx[f * Hn + bitrev(k, logH)] = irfft_pack(four_in + f * fs + (size_t)j * (R + 1), k, R, Hn, tw);
+    }
+    __syncthreads();
+    fft_dit(sx, 4, Hn, logH, tw, true);
+    const double muj = mu[j];
+    const T f = T(two_omega * muj);
+    const T rc = T(1.0 / (1.0 - muj * muj));
+    C* y = sx + 4 * Hn;
+    for (int k = threadIdx.x; k < Hn; k += blockDim.x) {
+        // .x holds longitude 2k, .y longitude 2k+1
+        const C z = sx[k], p = sx[Hn + k], u = sx[2 * Hn + k], v = sx[3 * Hn + k];
+        const T zf0 = z.x + f, zf1 = z.y + f;
+        const int r = bitrev(k, logH);
+        y[r] = mkc(zf0 * u.x, zf1 * u.y);                                        // A
+        y[Hn + r] = mkc(zf0 * v.x, zf1 * v.y);                                   // B
+        y[2 * Hn + r] = mkc(p.x * u.x, p.y * u.y);                               // C
+        y[3 * Hn + r] = mkc(p.x * v.x, p.y * v.y);                               // D
+        y[4 * Hn + r] = mkc(T(0.5) * (u.x * u.x + v.x * v.x) * rc,               // E
+                            T(0.5) * (u.y * u.y + v.y * v.y) * rc);
+    }
+    __syncthreads();
+    fft_dit(y, 5, Hn, logH, tw, false);
+    const T sAD = T(w[j] / (1.0 - muj * muj) / I);
+    const T sE = T(w[j] / I);
+    for (int t = threadIdx.x; t < 5 * (R + 1); t += blockDim.x) {
+        const int fld = t / (R + 1);
+        const int m = t - fld * (R + 1);
+        const C X = rfft_unpack(y + fld * Hn, m, Hn, tw);
+        four_out[(size_t)fld * fs + (size_t)j * (R + 1) + m] = cscale(X, fld < 4 ? sAD : sE);
+    }
+}
+
+// div(X,Y)^m_n = (1/a) sum_j [ i m X' P - Y' H ], curl(X,Y)^m_n = (1/a) sum_j [ i m Y' P + X' H ]
+// with X', Y' the weighted Fourier coefficients (integration by parts of the
+// mu-derivatives); E^m_n = sum_j E' P.
+template <class T>
+__global__ void __launch_bounds__(32 * kAnalWarpsMax) k_anal_rhs(const C_t<T>* __restrict__ four_out,
+                                                                 const T* __restrict__ P, const T* __restrict__ H,
+                                                                 const Chunk* __restrict__ chunks, int R, int J2,
+                                                                 int nc, double a, double2* __restrict__ FE) {
+    using C = C_t<T>;
+    constexpr int TW = 32;                    // latitudes per tile
+    __shared__ C sG[kAnalWarpsMax][TW][5][2];  // per warp: [lat][field A..E][even, odd]
+    __shared__ C red[kAnalWarpsMax - 1][7][32];
+    const Chunk ch = chunks[blockIdx.x];
+    const int m = ch.m;
+    const int nm = R + 1 - m;
+    const int off = m * (R + 1) - m * (m - 1) / 2;
+    const int k0 = ch.start;
+    const int lane = threadIdx.x & 31;
+    const int wid = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
+    const int k = k0 + lane;
+    const int par = k & 1;
+    const int J = 2 * J2;
+    const size_t fs = (size_t)J * (R + 1);
+    const bool live = lane < nm - k0;
+    const C zero = mkc(T(0), T(0));
+    C aC = zero, aA = zero, aB = zero, aE = zero, hD = zero, hB = zero, hA = zero;
+    const T* Prow = P + (size_t)(off + (live ? k : k0)) * J2;
+    const T* Hrow = H + (size_t)(off + (live ? k : k0)) * J2;
+    for (int jt = wid * TW; jt < J2; jt += nw * TW) {
+        const int nl = min(TW, J2 - jt);
+        for (int t = lane; t < nl * 5; t += 32) {
+            const int jj = t / 5, f = t - jj * 5;
+            const int jn = jt + jj, js = J - 1 - jn;
+            const C gN = four_out[(size_t)f * fs + (size_t)jn * (R + 1) + m];
+            const C gS = four_out[(size_t)f * fs + (size_t)js * (R + 1) + m];
+            sG[wid][jj][f][0] = cadd(gN, gS);
+            sG[wid][jj][f][1] = csub(gN, gS);
+        }
+        __syncwarp();
+        if (live) {
+#pragma unroll 8
+            for (int jj = 0; jj < nl; ++jj) {
+                const T p = Prow[jt + jj], h = Hrow[jt + jj];
+                cfma(aC, p, sG[wid][jj][2][par]);
+                cfma(aA, p, sG[wid][jj][0][par]);
+                cfma(aB, p, sG[wid][jj][1][par]);
+                cfma(aE, p, sG[wid][jj][4][par]);
+                cfma(hD, h, sG[wid][jj][3][par ^ 1]);
+                cfma(hB, h, sG[wid][jj][1][par ^ 1]);
+                cfma(hA, h, sG[wid][jj][0][par ^ 1]);
+            }
+        }
+        __syncwarp();
+    }
+    if (wid > 0) {
+        red[wid - 1][0][lane] = aC;
+        red[wid - 1][1][lane] = aA;
+        red[wid - 1][2][lane] = aB;
+        red[wid - 1][3][lane] = aE;
+        red[wid - 1][4][lane] = hD;
+        red[wid - 1][5][lane] = hB;
+        red[wid - 1][6][lane] = hA;
+    }
+    __syncthreads();
+    if (wid != 0 || !live) return;
+    double2 s[7] = {{(double)aC.x, (double)aC.y}, {(double)aA.x, (double)aA.y}, {(double)aB.x, (double)aB.y},
+                    {(double)aE.x, (double)aE.y}, {(double)hD.x, (double)hD.y}, {(double)hB.x, (double)hB.y},
+                    {(double)hA.x, (double)hA.y}};
+    for (int w2 = 1; w2 < nw; ++w2)
+        for (int q = 0; q < 7; ++q) {
+            s[q].x += (double)red[w2 - 1][q][lane].x;
+            s[q].y += (double)red[w2 - 1][q][lane].y;
+        }
+    const int n = m + k;
+    const double ia = 1.0 / a;
+    const double dm = (double)m;
+    const double2 divCD = cscale(csub(cim(dm, s[0]), s[4]), ia);
+    const double2 divAB = cscale(csub(cim(dm, s[1]), s[5]), ia);
+    const double2 curlAB = cscale(cadd(cim(dm, s[2]), s[6]), ia);
+    const double lap = n * (n + 1.0) * ia * ia;
+    double2 f0 = make_double2(-divCD.x, -divCD.y);
+    double2 f1 = make_double2(-divAB.x, -divAB.y);
+    double2 f2 = make_double2(curlAB.x + lap * s[3].x, curlAB.y + lap * s[3].y);
+    if (m == 0) f0.y = f1.y = f2.y = 0.0;
+    FE[off + k] = f0;
+    FE[nc + off + k] = f1;
+    FE[2 * nc + off + k] = f2;
+}
+
+// Launch helpers shared by both precisions.
+template <class T>
+inline size_t synth_smem(int R) {
+    const size_t coef = sizeof(C_t<T>) * 4 * (R + 1);
+    const size_t red = sizeof(C_t<T>) * kSynthWarps * 6 * 32;
+    return coef > red ? coef : red;
+}
+inline int anal_warps(int J2) {
+    const int tiles = (J2 + 31) / 32;
+    return tiles < kAnalWarpsMax ? tiles : kAnalWarpsMax;
+}
+
+}  // namespace mlsdc

@@ -1,10 +1,102 @@
-// Mixed-precision transforms (placeholder until the float32 path lands).
+// Mixed-precision explicit right-hand side.  The Legendre sums and the
+// longitude FFTs run in float32 (float32 FMAs on the CUDA cores for
+// MLSDC_FP32; tcgen05 tensor cores for MLSDC_TF32 / MLSDC_BF16X3, see
+// legendre_tc.cu); the state arrives in float64 and F_E leaves in float64,
+// with the final combination (div, curl, n(n+1)/a^2 E) done in float64.
+// The float32 tables are rounded on the device from the float64 master tables
+// that sh_plan computes on the host.
+#include "complex.cuh"
 #include "internal.h"
+#include "rhs_kernels.cuh"
 
 namespace mlsdc {
-mlsdc_status mp_init(sh_plan_t) { return MLSDC_ERR_INVALID; }
-void mp_free(sh_plan_t) {}
-mlsdc_status rhs_explicit_mp(sh_plan_t, const swe_params*, const double*, double*, cudaStream_t, int64_t*, int) {
-    return MLSDC_ERR_INVALID;
+
+__global__ void k_round_f32(const double* __restrict__ x, float* __restrict__ y, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        y[i] = (float)x[i];
 }
+
+__global__ void k_round_c32(const double2* __restrict__ x, float2* __restrict__ y, int n) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        y[i] = make_float2((float)x[i].x, (float)x[i].y);
+}
+
+mlsdc_status tc_init(sh_plan_t p);   // legendre_tc.cu
+void tc_free(sh_plan_t p);
+mlsdc_status tc_synth(sh_plan_t p, const double* state, double a, cudaStream_t st);
+mlsdc_status tc_anal(sh_plan_t p, double a, double* FE, cudaStream_t st);
+
+mlsdc_status mp_init(sh_plan_t p) {
+    MPTables& t = p->mp;
+    const size_t ntab = (size_t)p->nc * p->J2;
+    const size_t nfour = (size_t)p->J * (p->R + 1);
+    auto alloc = [&](void** ptr, size_t bytes) -> bool {
+        if (cudaMalloc(ptr, bytes) != cudaSuccess) return false;
+        p->bytes += (int64_t)bytes;
+        return true;
+    };
+    bool ok = alloc((void**)&t.P32, ntab * sizeof(float)) && alloc((void**)&t.H32, ntab * sizeof(float)) &&
+              alloc((void**)&t.tw32, (p->I / 2) * sizeof(float2)) &&
+              alloc((void**)&t.four_in, 4 * nfour * sizeof(float2)) &&
+              alloc((void**)&t.four_out, 5 * nfour * sizeof(float2));
+    if (!ok) {
+        set_error("cudaMalloc (mixed-precision tables)", cudaGetLastError());
+        return MLSDC_ERR_ALLOC;
+    }
+    k_round_f32<<<1024, 256>>>(p->d_P, t.P32, ntab);
+    k_round_f32<<<1024, 256>>>(p->d_H, t.H32, ntab);
+    k_round_c32<<<8, 256>>>(p->d_tw, t.tw32, p->I / 2);
+    MLSDC_LAUNCHED("k_round_f32");
+    MLSDC_CUDA(cudaDeviceSynchronize());
+    const size_t grid_smem = sizeof(float2) * 9 * (p->I / 2);
+    mlsdc_status rs = raise_smem_limit((const void*)k_grid_rhs<float>, grid_smem);
+    if (rs != MLSDC_OK) return rs;
+    if (p->precision == MLSDC_TF32 || p->precision == MLSDC_BF16X3) return tc_init(p);
+    return MLSDC_OK;
+}
+
+void mp_free(sh_plan_t p) {
+    MPTables& t = p->mp;
+    tc_free(p);
+    cudaFree(t.P32);
+    cudaFree(t.H32);
+    cudaFree(t.tw32);
+    cudaFree(t.four_in);
+    cudaFree(t.four_out);
+    t = MPTables();
+}
+
+mlsdc_status rhs_explicit_mp(sh_plan_t p, const swe_params* prm, const double* state, double* FE, cudaStream_t st,
+                             int64_t* launches, int stage) {
+    const int R = p->R;
+    MPTables& t = p->mp;
+    const bool tc = p->precision == MLSDC_TF32 || p->precision == MLSDC_BF16X3;
+    mlsdc_status s;
+    if (stage == 0 || stage < 0) {
+        if (tc) {
+            if ((s = tc_synth(p, state, prm->a, st)) != MLSDC_OK) return s;
+        } else {
+            k_synth_rhs<float><<<p->n_synth, 32 * kSynthWarps, synth_smem<float>(R), st>>>(
+                (const double2*)state, t.P32, t.H32, p->d_synth, R, p->J2, p->nc, prm->a, t.four_in);
+            MLSDC_LAUNCHED("k_synth_rhs<float>");
+        }
+    }
+    if (stage == 1 || stage < 0) {
+        k_grid_rhs<float><<<p->J, 256, sizeof(float2) * 9 * (p->I / 2), st>>>(
+            t.four_in, t.four_out, p->d_mu, p->d_w, t.tw32, R, p->I, p->logI, p->J, 2.0 * prm->omega);
+        MLSDC_LAUNCHED("k_grid_rhs<float>");
+    }
+    if (stage == 2 || stage < 0) {
+        if (tc) {
+            if ((s = tc_anal(p, prm->a, FE, st)) != MLSDC_OK) return s;
+        } else {
+            k_anal_rhs<float><<<p->n_anal, 32 * anal_warps(p->J2), 0, st>>>(
+                t.four_out, t.P32, t.H32, p->d_anal, R, p->J2, p->nc, prm->a, (double2*)FE);
+            MLSDC_LAUNCHED("k_anal_rhs<float>");
+        }
+    }
+    if (launches) *launches += stage < 0 ? 3 : 1;
+    return MLSDC_OK;
+}
+
 }  // namespace mlsdc

@@ -39,6 +39,7 @@ _SIGS = {
     "sh_plan_destroy": ([_VP], _I),
     "sh_plan_grid": ([_VP, _DP, _DP], _I),
     "sh_plan_device_bytes": ([_VP, ctypes.POINTER(_I64)], _I),
+    "sh_plan_device_error": ([_VP, ctypes.POINTER(_I)], _I),
     "sh_inverse": ([_VP, _DP, _DP, _I, _VP], _I),
     "sh_forward": ([_VP, _DP, _DP, _I, _VP], _I),
     "sh_inverse_static": ([_I, _I, _I, _DP, _DP, _I, _VP], _I),
@@ -149,6 +150,12 @@ class Plan:
         _check(lib().sh_plan_grid(self.h, mu.ctypes.data_as(ctypes.c_void_p), w.ctypes.data_as(ctypes.c_void_p)),
                "sh_plan_grid")
         return mu, w
+
+    def device_error(self) -> int:
+        """Error code recorded by the plan's tensor-core kernels (0 = none)."""
+        c = ctypes.c_int()
+        _check(lib().sh_plan_device_error(self.h, ctypes.byref(c)), "sh_plan_device_error")
+        return c.value
 
     def device_bytes(self) -> int:
         b = ctypes.c_int64()
