@@ -60,6 +60,33 @@ __device__ void fft_dit(C* x, int narr, int Hn, int logH, const C* __restrict__ 
     }
 }
 
+// In-place radix-2 decimation-in-frequency FFT, same conventions as fft_dit
+// but natural-order input and bit-reversed output.  Pairing it with fft_dit
+// (bit-reversed input) lets a pointwise stage run between the two transforms
+// in the permuted order, so no permutation is ever written out.
+template <class C>
+__device__ void fft_dif(C* x, int narr, int Hn, int logH, const C* __restrict__ tw, bool inverse) {
+    const int half = Hn >> 1;
+    for (int s = logH - 1; s >= 0; --s) {
+        const int h = 1 << s;
+        const int tstride = (half >> s) * 2;
+        for (int t = threadIdx.x; t < narr * half; t += blockDim.x) {
+            const int a = t >> (logH - 1);
+            const int b = t & (half - 1);
+            const int pos = b & (h - 1);
+            const int i0 = ((b >> s) << (s + 1)) + pos;
+            C w = __ldg(&tw[pos * tstride]);
+            if (inverse) w.y = -w.y;
+            C* xa = x + a * Hn;
+            const C u = xa[i0];
+            const C v = xa[i0 + h];
+            xa[i0] = cadd(u, v);
+            xa[i0 + h] = cmul(csub(u, v), w);
+        }
+        __syncthreads();
+    }
+}
+
 // Real DFTs of length I through complex DFTs of length I/2 over the packed
 // samples z_k = x_{2k} + i x_{2k+1} of ONE real row (packing two different
 // fields would tie the smaller field's rounding error to the larger one).

@@ -71,6 +71,7 @@ struct sh_plan_s {
     double* d_H = nullptr;            // [nc][J2]
     double2* d_tw = nullptr;          // [I/2] exp(-2 pi i k / I)
     int* d_ndeg = nullptr;            // [nc] total degree n of each coefficient
+    double* d_cor = nullptr;          // [nc][5] Coriolis recurrence factors (coriolis_linear)
     mlsdc::Chunk* d_synth = nullptr;  // synthesis work items, largest first
     mlsdc::Chunk* d_anal = nullptr;   // analysis work items, largest first
     int n_synth = 0, n_anal = 0;

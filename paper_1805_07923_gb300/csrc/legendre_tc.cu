@@ -30,6 +30,7 @@
 
 #include "complex.cuh"
 #include "internal.h"
+#include "rhs_kernels.cuh"  // coriolis_linear
 
 namespace mlsdc {
 namespace {
@@ -341,6 +342,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_anal(const float2* __restr
                                                            const __grid_constant__ Maps maps,
                                                            const int2* __restrict__ tiles, int R, int J2, int nc,
                                                            int J2p, double a, double2* __restrict__ FE,
+                                                           const double2* __restrict__ state, double two_omega,
+                                                           const double* __restrict__ cor,
                                                            int* __restrict__ err) {
     using S = Shape<MODE>;
     extern __shared__ unsigned char smem_raw[];
@@ -471,6 +474,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_anal(const float2* __restr
         double2 f0 = make_double2(-divCD.x, -divCD.y);
         double2 f1 = make_double2(-divAB.x, -divAB.y);
         double2 f2 = make_double2(curlAB.x + lap * sE.x, curlAB.y + lap * sE.y);
+        double2 dz, dd;  // the Coriolis part, exactly in float64 (grid products carry no f)
+        coriolis_linear(state, cor, nc, R, m, n, off, a, two_omega, dz, dd);
+        f1 = cadd(f1, dz);
+        f2 = cadd(f2, dd);
         if (m == 0) f0.y = f1.y = f2.y = 0.0;
         FE[off + k] = f0;
         FE[nc + off + k] = f1;
@@ -638,14 +645,16 @@ mlsdc_status tc_synth(sh_plan_t p, const double* state, double a, cudaStream_t s
     return MLSDC_OK;
 }
 
-mlsdc_status tc_anal(sh_plan_t p, double a, double* FE, cudaStream_t st) {
+mlsdc_status tc_anal(sh_plan_t p, double a, double* FE, const double* state, double two_omega, cudaStream_t st) {
     TcState* s = st_of(p);
     if (s->mode == MODE_TF32)
         k_tc_anal<MODE_TF32><<<s->n_tiles, kTcThreads, s->smem_ana, st>>>(
-            p->mp.four_out, s->map_ana, s->d_tiles, p->R, p->J2, p->nc, s->J2p, a, (double2*)FE, s->d_err);
+            p->mp.four_out, s->map_ana, s->d_tiles, p->R, p->J2, p->nc, s->J2p, a, (double2*)FE,
+            (const double2*)state, two_omega, p->d_cor, s->d_err);
     else
         k_tc_anal<MODE_BF16X3><<<s->n_tiles, kTcThreads, s->smem_ana, st>>>(
-            p->mp.four_out, s->map_ana, s->d_tiles, p->R, p->J2, p->nc, s->J2p, a, (double2*)FE, s->d_err);
+            p->mp.four_out, s->map_ana, s->d_tiles, p->R, p->J2, p->nc, s->J2p, a, (double2*)FE,
+            (const double2*)state, two_omega, p->d_cor, s->d_err);
     MLSDC_LAUNCHED("k_tc_anal");
     return MLSDC_OK;
 }

@@ -134,6 +134,7 @@ static void free_plan(sh_plan_t p) {
     cudaFree(p->d_H);
     cudaFree(p->d_tw);
     cudaFree(p->d_ndeg);
+    cudaFree(p->d_cor);
     cudaFree(p->d_synth);
     cudaFree(p->d_anal);
     cudaFree(p->d_four_in);
@@ -199,6 +200,22 @@ extern "C" mlsdc_status sh_plan(int R, int nlon, int nlat, int precision, sh_pla
     std::vector<int> ndeg(p->nc);
     for (int m = 0; m <= R; ++m)
         for (int n = m; n <= R; ++n) ndeg[moff(R, m) + n - m] = n;
+    // Coriolis recurrence factors per coefficient (see coriolis_linear):
+    // eps_n, eps_{n+1}, -(n-1) eps_n inv_{n-1}, (n+2) eps_{n+1} inv_{n+1}, inv_n
+    // with inv_n = -1/(n(n+1)); the radius is a call parameter, so the last
+    // three are stored for a = 1 and multiplied by a^2 on the device.
+    std::vector<double> cor((size_t)5 * p->nc);
+    for (int m = 0; m <= R; ++m)
+        for (int n = m; n <= R; ++n) {
+            auto inv = [](int nn) { return nn > 0 ? -1.0 / (nn * (nn + 1.0)) : 0.0; };
+            const double en = eps_mn(m, n), en1 = (n + 1 <= R) ? eps_mn(m, n + 1) : 0.0;
+            double* c = &cor[(size_t)5 * (moff(R, m) + n - m)];
+            c[0] = en;
+            c[1] = en1;
+            c[2] = -(n - 1.0) * en * inv(n - 1);
+            c[3] = (n + 2.0) * en1 * inv(n + 1);
+            c[4] = inv(n);
+        }
 
     // Legendre work items, largest first so the block scheduler balances them.
     std::vector<Chunk> cs, ca;
@@ -221,6 +238,7 @@ extern "C" mlsdc_status sh_plan(int R, int nlon, int nlat, int precision, sh_pla
     TRY(dev_alloc(&p->d_H, H.size(), &p->bytes));
     TRY(dev_alloc(&p->d_tw, tw.size(), &p->bytes));
     TRY(dev_alloc(&p->d_ndeg, ndeg.size(), &p->bytes));
+    TRY(dev_alloc(&p->d_cor, cor.size(), &p->bytes));
     TRY(dev_alloc(&p->d_synth, cs.size(), &p->bytes));
     TRY(dev_alloc(&p->d_anal, ca.size(), &p->bytes));
     TRY(dev_alloc(&p->d_four_in, nfour, &p->bytes));
@@ -235,6 +253,7 @@ extern "C" mlsdc_status sh_plan(int R, int nlon, int nlat, int precision, sh_pla
     H2D(p->d_H, H.data(), H.size());
     H2D(p->d_tw, tw.data(), tw.size());
     H2D(p->d_ndeg, ndeg.data(), ndeg.size());
+    H2D(p->d_cor, cor.data(), cor.size());
     H2D(p->d_synth, cs.data(), cs.size());
     H2D(p->d_anal, ca.data(), ca.size());
 #undef H2D

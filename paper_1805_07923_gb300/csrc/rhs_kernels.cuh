@@ -125,27 +125,29 @@ __global__ void __launch_bounds__(256) k_grid_rhs(const C_t<T>* __restrict__ fou
     const size_t fs = (size_t)J * (R + 1);
     for (int t = threadIdx.x; t < 4 * Hn; t += blockDim.x) {
         const int f = t >> logH, k = t & (Hn - 1);
-        sx[f * Hn + bitrev(k, logH)] = irfft_pack(four_in + f * fs + (size_t)j * (R + 1), k, R, Hn, tw);
+        sx[f * Hn + k] = irfft_pack(four_in + f * fs + (size_t)j * (R + 1), k, R, Hn, tw);
     }
     __syncthreads();
-    fft_dit(sx, 4, Hn, logH, tw, true);
+    // inverse by decimation in frequency: slot q now holds the longitude pair bitrev(q)
+    fft_dif(sx, 4, Hn, logH, tw, true);
     const double muj = mu[j];
     const T f = T(two_omega * muj);
     const T rc = T(1.0 / (1.0 - muj * muj));
     C* y = sx + 4 * Hn;
-    for (int k = threadIdx.x; k < Hn; k += blockDim.x) {
-        // .x holds longitude 2k, .y longitude 2k+1
-        const C z = sx[k], p = sx[Hn + k], u = sx[2 * Hn + k], v = sx[3 * Hn + k];
+    for (int q = threadIdx.x; q < Hn; q += blockDim.x) {
+        // .x and .y hold the two longitudes of one packed pair; products are
+        // pointwise, so they stay in the same (bit-reversed) slot
+        const C z = sx[q], p = sx[Hn + q], u = sx[2 * Hn + q], v = sx[3 * Hn + q];
         const T zf0 = z.x + f, zf1 = z.y + f;
-        const int r = bitrev(k, logH);
-        y[r] = mkc(zf0 * u.x, zf1 * u.y);                                        // A
-        y[Hn + r] = mkc(zf0 * v.x, zf1 * v.y);                                   // B
-        y[2 * Hn + r] = mkc(p.x * u.x, p.y * u.y);                               // C
-        y[3 * Hn + r] = mkc(p.x * v.x, p.y * v.y);                               // D
-        y[4 * Hn + r] = mkc(T(0.5) * (u.x * u.x + v.x * v.x) * rc,               // E
+        y[q] = mkc(zf0 * u.x, zf1 * u.y);                                        // A
+        y[Hn + q] = mkc(zf0 * v.x, zf1 * v.y);                                   // B
+        y[2 * Hn + q] = mkc(p.x * u.x, p.y * u.y);                               // C
+        y[3 * Hn + q] = mkc(p.x * v.x, p.y * v.y);                               // D
+        y[4 * Hn + q] = mkc(T(0.5) * (u.x * u.x + v.x * v.x) * rc,               // E
                             T(0.5) * (u.y * u.y + v.y * v.y) * rc);
     }
     __syncthreads();
+    // forward by decimation in time from the bit-reversed slots: natural order out
     fft_dit(y, 5, Hn, logH, tw, false);
     const T sAD = T(w[j] / (1.0 - muj * muj) / I);
     const T sE = T(w[j] / I);
@@ -157,14 +159,55 @@ __global__ void __launch_bounds__(256) k_grid_rhs(const C_t<T>* __restrict__ fou
     }
 }
 
+// The Coriolis (linear) part of F_E at coefficient (m, n), exactly, in
+// float64 spectral arithmetic.  With f = 2 Omega mu, -div(f V) and curl(f V)
+// are tridiagonal in n for each m:
+//   dzeta  = -2 Omega (mu delta)_n - (2 Omega / a^2) [ i m psi_n + (H chi)_n ]
+//   ddelta =  2 Omega (mu zeta)_n  - (2 Omega / a^2) [ i m chi_n - (H psi)_n ]
+//   (mu x)_n = eps_n x_{n-1} + eps_{n+1} x_{n+1},
+//   (H x)_n  = -(n-1) eps_n x_{n-1} + (n+2) eps_{n+1} x_{n+1},
+// from mu P_n = eps_{n+1} P_{n+1} + eps_n P_{n-1} and H_n = (1 - mu^2) dP_n/dmu,
+// projected on n <= R; psi, chi = -a^2/(n(n+1)) (zeta, delta).  The
+// mixed-precision paths add this term in float64 and send only the nonlinear
+// part of the products through the reduced-precision transforms.
+// cor[5 * idx .. +4] = (eps_n, eps_{n+1}, -(n-1) eps_n inv_{n-1}, (n+2) eps_{n+1} inv_{n+1}, inv_n)
+// with inv_n = -1/(n(n+1)) (0 for n = 0; times a^2 here) and eps zero outside
+// m <= n <= R (precomputed per plan: float64 square roots and divisions are
+// slow on this GPU).
+__device__ inline void coriolis_linear(const double2* __restrict__ state, const double* __restrict__ cor, int nc,
+                                       int R, int m, int n, int off, double a, double two_omega, double2& dz,
+                                       double2& dd) {
+    const int k = n - m;
+    const double2* z = state + nc + off;
+    const double2* d = state + 2 * nc + off;
+    double2 zl{0, 0}, zu{0, 0}, dl{0, 0}, du{0, 0};
+    if (n - 1 >= m) { zl = z[k - 1]; dl = d[k - 1]; }
+    if (n + 1 <= R) { zu = z[k + 1]; du = d[k + 1]; }
+    const double* c5 = cor + 5 * (size_t)(off + k);
+    const double a2 = a * a;
+    const double en = c5[0], en1 = c5[1], cl = c5[2] * a2, cu = c5[3] * a2, in = c5[4] * a2;
+    const double2 muD = make_double2(en * dl.x + en1 * du.x, en * dl.y + en1 * du.y);
+    const double2 muZ = make_double2(en * zl.x + en1 * zu.x, en * zl.y + en1 * zu.y);
+    const double2 Hchi = make_double2(cl * dl.x + cu * du.x, cl * dl.y + cu * du.y);
+    const double2 Hpsi = make_double2(cl * zl.x + cu * zu.x, cl * zl.y + cu * zu.y);
+    const double2 psi = make_double2(in * z[k].x, in * z[k].y);
+    const double2 chi = make_double2(in * d[k].x, in * d[k].y);
+    const double c = two_omega / (a * a), dm = (double)m;
+    dz = make_double2(-two_omega * muD.x - c * (-dm * psi.y + Hchi.x), -two_omega * muD.y - c * (dm * psi.x + Hchi.y));
+    dd = make_double2(two_omega * muZ.x - c * (-dm * chi.y - Hpsi.x), two_omega * muZ.y - c * (dm * chi.x - Hpsi.y));
+}
+
 // div(X,Y)^m_n = (1/a) sum_j [ i m X' P - Y' H ], curl(X,Y)^m_n = (1/a) sum_j [ i m Y' P + X' H ]
 // with X', Y' the weighted Fourier coefficients (integration by parts of the
-// mu-derivatives); E^m_n = sum_j E' P.
+// mu-derivatives); E^m_n = sum_j E' P.  With two_omega_lin != 0 the grid
+// products were formed without f and the Coriolis part is added here exactly.
 template <class T>
 __global__ void __launch_bounds__(32 * kAnalWarpsMax) k_anal_rhs(const C_t<T>* __restrict__ four_out,
                                                                  const T* __restrict__ P, const T* __restrict__ H,
                                                                  const Chunk* __restrict__ chunks, int R, int J2,
-                                                                 int nc, double a, double2* __restrict__ FE) {
+                                                                 int nc, double a, double2* __restrict__ FE,
+                                                                 const double2* __restrict__ state,
+                                                                 double two_omega_lin, const double* __restrict__ cor) {
     using C = C_t<T>;
     constexpr int TW = 32;                    // latitudes per tile
     __shared__ C sG[kAnalWarpsMax][TW][5][2];  // per warp: [lat][field A..E][even, odd]
@@ -241,6 +284,12 @@ __global__ void __launch_bounds__(32 * kAnalWarpsMax) k_anal_rhs(const C_t<T>* _
     double2 f0 = make_double2(-divCD.x, -divCD.y);
     double2 f1 = make_double2(-divAB.x, -divAB.y);
     double2 f2 = make_double2(curlAB.x + lap * s[3].x, curlAB.y + lap * s[3].y);
+    if (two_omega_lin != 0.0) {
+        double2 dz, dd;
+        coriolis_linear(state, cor, nc, R, m, n, off, a, two_omega_lin, dz, dd);
+        f1 = cadd(f1, dz);
+        f2 = cadd(f2, dd);
+    }
     if (m == 0) f0.y = f1.y = f2.y = 0.0;
     FE[off + k] = f0;
     FE[nc + off + k] = f1;

@@ -134,7 +134,8 @@ mlsdc_status rhs_explicit_f64(sh_plan_t p, const swe_params* prm, const double* 
     }
     if (stage == 2 || stage < 0) {
         k_anal_rhs<double><<<p->n_anal, 32 * anal_warps(p->J2), 0, st>>>(
-            p->d_four_out, p->d_P, p->d_H, p->d_anal, R, p->J2, p->nc, prm->a, (double2*)FE);
+            p->d_four_out, p->d_P, p->d_H, p->d_anal, R, p->J2, p->nc, prm->a, (double2*)FE,
+            (const double2*)state, 0.0, p->d_cor);
         MLSDC_LAUNCHED("k_anal_rhs<double>");
     }
     if (launches) *launches += stage < 0 ? 3 : 1;

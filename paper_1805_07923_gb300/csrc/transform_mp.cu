@@ -3,6 +3,10 @@
 // MLSDC_FP32; tcgen05 tensor cores for MLSDC_TF32 / MLSDC_BF16X3, see
 // legendre_tc.cu); the state arrives in float64 and F_E leaves in float64,
 // with the final combination (div, curl, n(n+1)/a^2 E) done in float64.
+// F_E = L_F + N is evaluated as the exact float64 spectral Coriolis part
+// (coriolis_linear) plus the nonlinear products through the transforms, so
+// the reduced-precision error scales with the nonlinear terms (f is about ten
+// times the vorticity) instead of the full (zeta + f) V flux.
 // The float32 tables are rounded on the device from the float64 master tables
 // that sh_plan computes on the host.
 #include "complex.cuh"
@@ -24,7 +28,7 @@ __global__ void k_round_c32(const double2* __restrict__ x, float2* __restrict__ 
 mlsdc_status tc_init(sh_plan_t p);   // legendre_tc.cu
 void tc_free(sh_plan_t p);
 mlsdc_status tc_synth(sh_plan_t p, const double* state, double a, cudaStream_t st);
-mlsdc_status tc_anal(sh_plan_t p, double a, double* FE, cudaStream_t st);
+mlsdc_status tc_anal(sh_plan_t p, double a, double* FE, const double* state, double two_omega, cudaStream_t st);
 
 mlsdc_status mp_init(sh_plan_t p) {
     MPTables& t = p->mp;
@@ -83,15 +87,16 @@ mlsdc_status rhs_explicit_mp(sh_plan_t p, const swe_params* prm, const double* s
     }
     if (stage == 1 || stage < 0) {
         k_grid_rhs<float><<<p->J, 256, sizeof(float2) * 9 * (p->I / 2), st>>>(
-            t.four_in, t.four_out, p->d_mu, p->d_w, t.tw32, R, p->I, p->logI, p->J, 2.0 * prm->omega);
+            t.four_in, t.four_out, p->d_mu, p->d_w, t.tw32, R, p->I, p->logI, p->J, 0.0);
         MLSDC_LAUNCHED("k_grid_rhs<float>");
     }
     if (stage == 2 || stage < 0) {
         if (tc) {
-            if ((s = tc_anal(p, prm->a, FE, st)) != MLSDC_OK) return s;
+            if ((s = tc_anal(p, prm->a, FE, state, 2.0 * prm->omega, st)) != MLSDC_OK) return s;
         } else {
             k_anal_rhs<float><<<p->n_anal, 32 * anal_warps(p->J2), 0, st>>>(
-                t.four_out, t.P32, t.H32, p->d_anal, R, p->J2, p->nc, prm->a, (double2*)FE);
+                t.four_out, t.P32, t.H32, p->d_anal, R, p->J2, p->nc, prm->a, (double2*)FE, (const double2*)state,
+                2.0 * prm->omega, p->d_cor);
             MLSDC_LAUNCHED("k_anal_rhs<float>");
         }
     }
