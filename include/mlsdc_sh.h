@@ -72,6 +72,7 @@ typedef struct {
 typedef struct sh_plan_s* sh_plan_t;
 typedef struct sdc_level_s* sdc_level_t;
 typedef struct mlsdc_s* mlsdc_t;
+typedef struct mlsdc_ensemble_s* mlsdc_ensemble_t;
 
 /* Text of a status code, and the last CUDA error message seen by this thread. */
 const char* mlsdc_status_string(mlsdc_status s);
@@ -88,6 +89,11 @@ const char* mlsdc_last_error(void);
  * current CUDA context.  Returns MLSDC_ERR_INVALID for other sizes.
  */
 mlsdc_status sh_plan(int R, int nlon, int nlat, int precision, sh_plan_t* out);
+/* sh_plan_batched: the same plan with scratch for up to max_members
+ * ensemble members per F_E launch (1 <= max_members <= 4096).  For the
+ * tensor-core precisions the number of members per CTA (1, 2, 4, 8 or 16)
+ * is chosen at creation by timing each feasible choice on a full batch. */
+mlsdc_status sh_plan_batched(int R, int nlon, int nlat, int precision, int max_members, sh_plan_t* out);
 mlsdc_status sh_plan_destroy(sh_plan_t plan);
 /* Copies of the host-side grid: mu[nlat], w[nlat] (north to south). */
 mlsdc_status sh_plan_grid(sh_plan_t plan, double* mu_host, double* w_host);
@@ -140,6 +146,11 @@ mlsdc_status sh_forward(sh_plan_t plan, const double* grid, double* spec, int nf
  * of a state, by the transform method:
  *   F_E = [ -div(Phi' V), -div((zeta+f) V), curl((zeta+f) V) - lap(V.V/2) ].
  * state, FE: [3][N_c] complex (must not alias).  Uses the plan's precision. */
+/* swe_explicit_rhs_batched: F_E of `members` states in one launch per stage
+ * (states: [members][3][N_c], FE: the same layout; members <= the plan's
+ * max_members).  Each member's result equals swe_explicit_rhs on it. */
+mlsdc_status swe_explicit_rhs_batched(sh_plan_t plan, const swe_params* prm, const double* states, double* FE,
+                                      int members, void* stream);
 mlsdc_status swe_explicit_rhs(sh_plan_t plan, const swe_params* prm, const double* state,
                               double* FE, void* stream);
 
@@ -165,6 +176,12 @@ mlsdc_status swe_implicit_solve(sh_plan_t plan, const swe_params* prm, double al
  * The level keeps a pointer to the plan, which must outlive it.
  */
 mlsdc_status sdc_level_create(sh_plan_t plan, const swe_params* prm, int n_nodes, sdc_level_t* out);
+/* sdc_level_create_batched: a level advancing `members` ensemble members in
+ * lockstep (members <= the plan's max_members).  Every state argument of
+ * sdc_step / mlsdc_step on such a level is [members][3][N_c], and the node
+ * arrays of sdc_sweep are [members][M+1][3][N_c]. */
+mlsdc_status sdc_level_create_batched(sh_plan_t plan, const swe_params* prm, int n_nodes, int members,
+                                      sdc_level_t* out);
 mlsdc_status sdc_level_destroy(sdc_level_t lev);
 /* Host copies of the node times t[n_nodes] and row-major Q, QE, QI [n_nodes^2]
  * (any pointer may be NULL). */
@@ -216,6 +233,21 @@ mlsdc_status mlsdc_step(mlsdc_t ml, double* state, double dt, int n_iter, int n_
 /* Kernel launches issued by the last mlsdc_step / sdc_step call made without
  * a graph replay (a count of this library's kernels, for reporting). */
 mlsdc_status mlsdc_launch_count(mlsdc_t ml, int64_t* launches);
+
+/* ---------------------------------------------------------------------------
+ * Ensembles of uneven truncation: one MLSDC object per truncation group
+ * (each built on batched levels holding that group's members), stepped
+ * together.  The groups' steps run on separate streams forked from `stream`
+ * and joined back; with use_graph != 0 the whole fork/join is captured once
+ * per (states, dt, n_iter, n_coarse_sweeps) into one CUDA graph with one
+ * branch per group and replayed with a single graph launch.  The groups
+ * must outlive the ensemble.  states: host array of ngroups device pointers,
+ * group g's [members_g][3][N_c,g]. */
+mlsdc_status mlsdc_ensemble_create(const mlsdc_t* groups, int ngroups, mlsdc_ensemble_t* out);
+mlsdc_status mlsdc_ensemble_destroy(mlsdc_ensemble_t ens);
+mlsdc_status mlsdc_ensemble_step(mlsdc_ensemble_t ens, double* const* states, double dt, int n_iter,
+                                 int n_coarse_sweeps, int use_graph, void* stream);
+mlsdc_status mlsdc_ensemble_launch_count(mlsdc_ensemble_t ens, int64_t* launches);
 
 /* Stage timing of swe_explicit_rhs for roofline reporting: launches each of
  * the plan's F_E stage kernels `reps` times back to back on `stream`, timed

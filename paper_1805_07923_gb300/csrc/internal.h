@@ -64,6 +64,8 @@ struct MPTables {
 
 struct sh_plan_s {
     int R, I, J, J2, nc, logI, precision;
+    int max_members = 1;              // ensemble members one F_E launch may carry
+    int tc_chunk = 1;                 // members per tensor-core CTA (autotuned)
     std::vector<double> mu, w;        // host copies, north to south, length J
     double* d_mu = nullptr;           // [J]
     double* d_w = nullptr;            // [J]
@@ -75,8 +77,8 @@ struct sh_plan_s {
     mlsdc::Chunk* d_synth = nullptr;  // synthesis work items, largest first
     mlsdc::Chunk* d_anal = nullptr;   // analysis work items, largest first
     int n_synth = 0, n_anal = 0;
-    double2* d_four_in = nullptr;     // [16][J][R+1] Fourier coefficients (synthesis out)
-    double2* d_four_out = nullptr;    // [16][J][R+1] Fourier coefficients (analysis in)
+    double2* d_four_in = nullptr;     // [max(16, 4 members)][J][R+1] Fourier coefficients (synthesis out)
+    double2* d_four_out = nullptr;    // [max(16, 5 members)][J][R+1] Fourier coefficients (analysis in)
     mlsdc::MPTables mp;
     int64_t bytes = 0;
 };
@@ -87,16 +89,24 @@ constexpr int kSynthLat = 32;   // latitudes per synthesis work item (one warp)
 constexpr int kAnalRows = 32;   // degrees per analysis work item (one warp)
 constexpr int kMaxFields = 16;
 
+// Members of one F_E launch: `members` states `state_ms` complex values
+// apart, results `fe_ms` apart.
+struct RhsBatch {
+    int members = 1;
+    size_t state_ms = 0, fe_ms = 0;
+};
+
 // float64 kernels (transform_f64.cu)
 // stage < 0: the whole F_E evaluation; 0, 1, 2: only that stage's kernel
 mlsdc_status rhs_explicit_f64(sh_plan_t p, const swe_params* prm, const double* state, double* FE,
-                              cudaStream_t st, int64_t* launches, int stage = -1);
+                              cudaStream_t st, int64_t* launches, int stage = -1, RhsBatch b = RhsBatch());
 mlsdc_status f64_prepare(sh_plan_t p);
 // float32 / tensor-core path (transform_mp.cu)
 mlsdc_status mp_init(sh_plan_t p);
 void mp_free(sh_plan_t p);
 mlsdc_status rhs_explicit_mp(sh_plan_t p, const swe_params* prm, const double* state, double* FE,
-                             cudaStream_t st, int64_t* launches, int stage = -1);
+                             cudaStream_t st, int64_t* launches, int stage = -1, RhsBatch b = RhsBatch());
+mlsdc_status create_plan(int R, int nlon, int nlat, int precision, int max_members, sh_plan_t* out);
 // pointwise float64 kernels (sdc.cu)
 mlsdc_status implicit_rhs_launch(sh_plan_t p, const swe_params* prm, const double* state, double* FI,
                                  cudaStream_t st);

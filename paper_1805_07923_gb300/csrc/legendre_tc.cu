@@ -1,22 +1,27 @@
 // Tensor-core Legendre contractions for MLSDC_TF32 and MLSDC_BF16X3 on
-// sm_103a: tcgen05.mma with accumulators in tensor memory, operands staged in
-// shared memory by TMA (cp.async.bulk.tensor, 128-byte swizzle).
+// sm_103a: tcgen05.mma with accumulators in tensor memory, the Legendre
+// table tiles brought into shared memory by TMA (cp.async.bulk.tensor,
+// 128-byte swizzle), a two-stage pipeline over K, and ensemble members
+// batched along N.
 //
 // Synthesis (Eq. spectral_to_physical_space, the Legendre sum per m), one CTA
-// per zonal wavenumber m:
-//   D[lat, c] = sum_k A[lat, k] B[c, k],  A = P^m_{m+k}(mu_lat) or H^m_{m+k},
-//   M = 128 northern latitudes (zero padded), K = degrees n - m (padded),
-//   N = 16 columns: the real and imaginary parts of the coefficients
-//   (zeta, Phi', chi, psi for P; psi, chi for H) in two column groups, one
-//   holding the even-(n-m) coefficients and one the odd ones, so that
-//   north = even + odd and south = even - odd (H: odd - even).
-// Analysis (Eq. legendre_transform), one CTA per (m, 128 degrees):
-//   D[k, c] = sum_lat A[k, lat] B[c, lat],  A = P or H rows, K = latitudes,
-//   B = the weighted Fourier coefficients of A..E combined north + south
-//   (even) and north - south (odd); each row picks its parity's columns.
+// per (zonal wavenumber m, chunk of members):
+//   D[lat, 16 b + c] = sum_k A[lat, k] B[16 b + c, k],  A = P^m_{m+k}(mu_lat) or H^m_{m+k},
+//   M = 128 northern latitudes (zero padded), K = degrees n - m in blocks of
+//   128 bytes, and per member b 16 columns: the real and imaginary parts of
+//   the coefficients (zeta, Phi', chi, psi for P; psi, chi for H) in two
+//   column groups, one holding the even-(n-m) coefficients and one the odd
+//   ones, so that north = even + odd and south = even - odd (H: odd - even).
+// Analysis (Eq. legendre_transform), one CTA per (m, 128 degrees, member chunk):
+//   D[k, 16 b + c] = sum_lat A[k, lat] B[16 b + c, lat],  A = P or H rows,
+//   K = latitudes, B = each member's weighted Fourier coefficients of A..E
+//   combined north + south (even) and north - south (odd); each row picks
+//   its parity's columns.  The Coriolis part is added exactly in float64.
 // TF32: operands rounded to tf32 (round to nearest); BF16X3: x = hi + lo in
 // bf16 and D += A_hi B_hi + A_hi B_lo + A_lo B_hi.  Accumulation is float32
-// in tensor memory; the final combination of F_E is float64.
+// in tensor memory; the final combination of F_E is float64.  With N = 16 x
+// members per CTA (up to 256) a batch of members turns the skinny per-member
+// contraction into a dense one.
 //
 // Every wait is bounded; on timeout the kernel records an error code in
 // device memory (read by sh_plan_device_error), releases its tensor memory and
@@ -37,8 +42,6 @@ namespace {
 
 constexpr int kTcThreads = 128;
 constexpr int kTileRows = 128;   // MMA M
-constexpr int kTcN = 16;         // MMA N per column group
-constexpr uint32_t kTmemCols = 32;
 constexpr int kMaxKS = 192;      // synthesis K limit (R + 1 <= 192)
 constexpr int kTileBytes = 16384;  // 128 rows x 128 B
 constexpr uint32_t kSpinLimit = 1u << 24;
@@ -60,7 +63,7 @@ struct TcState {
     int* d_err = nullptr;
     int2* d_tiles = nullptr;
     int n_tiles = 0;
-    size_t smem_syn = 0, smem_ana = 0;
+    int chunk = 1;  // members per CTA (autotuned)
 };
 
 // ---------------------------------------------------------------- PTX helpers
@@ -99,15 +102,6 @@ __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.a
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-__device__ __forceinline__ void tmem_alloc(uint32_t dst_smem) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem), "r"(kTmemCols)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(kTmemCols) : "memory");
-}
-
 // K-major operand tile written by TMA with the 128-byte swizzle: rows of
 // 128 B, 8-row groups 1024 B apart.
 __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
@@ -121,26 +115,21 @@ __device__ __forceinline__ uint64_t desc_plain(uint32_t saddr, uint32_t lbo, uin
            ((uint64_t)1 << 46);
 }
 
-// Instruction descriptors: D float32, A and B of one type (tf32, or bf16),
-// both K-major, N = 16, M = 128.
-constexpr uint32_t kIdescTf32 = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kTcN >> 3) << 17) |
-                                ((uint32_t)(kTileRows >> 4) << 24);
-constexpr uint32_t kIdescBf16 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTcN >> 3) << 17) |
-                                ((uint32_t)(kTileRows >> 4) << 24);
-
+// tcgen05.mma of one K step; the instruction descriptor carries D float32,
+// A and B of one type (tf32, or bf16), both K-major, N and M = 128.
 template <int MODE>
-__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
+__device__ __forceinline__ void mma_n(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
     if (MODE == MODE_TF32) {
         asm volatile(
             "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
             "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
-            "l"(a), "l"(b), "r"(kIdescTf32), "r"(acc)
+            "l"(a), "l"(b), "r"(idesc), "r"(acc)
             : "memory");
     } else {
         asm volatile(
             "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
             "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
-            "l"(a), "l"(b), "r"(kIdescBf16), "r"(acc)
+            "l"(a), "l"(b), "r"(idesc), "r"(acc)
             : "memory");
     }
 }
@@ -168,15 +157,17 @@ __device__ __forceinline__ uint32_t to_tf32(float x) {
     return r;
 }
 
-// Store one B-operand value (row c of N = 16, column k) in the plain K-major
-// layout: byte offset (k / kc) * 256 + (c / 8) * 128 + (c % 8) * 16 + (k % kc) * esz.
+
+// Store one B-operand value (row r of N rows, column k of one K block) in the
+// plain K-major layout: byte offset (k / kc) * lbo + (r / 8) * 128 + (r % 8) * 16
+// + (k % kc) * esz, kc = 16 / esz elements per core-matrix row, lbo = 16 N.
 template <int MODE>
-__device__ __forceinline__ void put_b(unsigned char* hi, unsigned char* lo, int c, int k, float v) {
+__device__ __forceinline__ void put_b(unsigned char* hi, unsigned char* lo, int r, int k, float v, uint32_t lbo) {
     if (MODE == MODE_TF32) {
-        const int off = (k >> 2) * 256 + (c >> 3) * 128 + (c & 7) * 16 + (k & 3) * 4;
+        const uint32_t off = (uint32_t)(k >> 2) * lbo + (r >> 3) * 128 + (r & 7) * 16 + (k & 3) * 4;
         *reinterpret_cast<uint32_t*>(hi + off) = to_tf32(v);
     } else {
-        const int off = (k >> 3) * 256 + (c >> 3) * 128 + (c & 7) * 16 + (k & 7) * 2;
+        const uint32_t off = (uint32_t)(k >> 3) * lbo + (r >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2;
         const __nv_bfloat16 h = __float2bfloat16_rn(v);
         const __nv_bfloat16 l = __float2bfloat16_rn(v - __bfloat162float(h));
         *reinterpret_cast<__nv_bfloat16*>(hi + off) = h;
@@ -189,133 +180,245 @@ template <int MODE>
 struct Shape {
     static constexpr int KB = MODE == MODE_TF32 ? 32 : 64;     // elements per 128-B K block
     static constexpr int KSTEP = MODE == MODE_TF32 ? 8 : 16;   // K per MMA
-    static constexpr int ESZ = MODE == MODE_TF32 ? 4 : 2;
     static constexpr int NT = MODE == MODE_TF32 ? 2 : 4;       // A tables (P, H) or (P hi, P lo, H hi, H lo)
     static constexpr int NPART = MODE == MODE_TF32 ? 1 : 2;    // B parts (hi, lo)
-    // bytes of one B operand (16 rows) for K elements
-    static constexpr int b_bytes(int K) { return K * kTcN * ESZ; }
 };
 
-template <int MODE>
-__host__ __device__ inline size_t tc_smem_bytes(int nkb_max) {
-    using S = Shape<MODE>;
-    return 1024 + (size_t)S::NT * nkb_max * kTileBytes + (size_t)2 * S::NPART * S::b_bytes(nkb_max * S::KB) + 64;
+// One pipeline stage: the A tiles of one K block, then the B tiles of the
+// two column groups (P, H) for `chunk` members (16 rows each) and each part.
+__host__ __device__ inline size_t stage_bytes(int mode, int chunk) {
+    const int nt = mode == MODE_TF32 ? 2 : 4, npart = mode == MODE_TF32 ? 1 : 2;
+    return (size_t)nt * kTileBytes + (size_t)2 * npart * (16 * chunk) * 128;
+}
+__host__ __device__ inline size_t cta_smem_bytes(int mode, int chunk, int stages) {
+    return 1024 + (size_t)stages * stage_bytes(mode, chunk) + 128;
+}
+__host__ __device__ inline uint32_t tmem_cols_for(int ncols) {
+    uint32_t c = 32;
+    while (c < (uint32_t)ncols) c <<= 1;
+    return c;
 }
 
-// ---------------------------------------------------------------- synthesis
-template <int MODE>
-__global__ void __launch_bounds__(kTcThreads, 1) k_tc_synth(const double2* __restrict__ state,
-                                                            const __grid_constant__ Maps maps, int R, int J2, int nc,
-                                                            double a, float2* __restrict__ four, int* __restrict__ err) {
-    using S = Shape<MODE>;
-    extern __shared__ unsigned char smem_raw[];
-    unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    const int m = blockIdx.x;
-    const int nm = R + 1 - m;
-    const int off = m * (R + 1) - m * (m - 1) / 2;
-    const int nkb = (nm + S::KB - 1) / S::KB;
-    const int Kp = nkb * S::KB;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    unsigned char* A = smem;                                   // [NT][nkb][16 KB]
-    unsigned char* B = A + (size_t)S::NT * nkb * kTileBytes;  // [group][part][b_bytes(Kp)]
-    const int bsz = S::b_bytes(Kp);
-    uint64_t* bars = reinterpret_cast<uint64_t*>(B + 2 * S::NPART * bsz);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 2);
-    volatile int* issued = reinterpret_cast<volatile int*>(tslot + 1);
-    const uint32_t bar_tma = sa(&bars[0]), bar_mma = sa(&bars[1]);
+struct TcArgs {
+    int R, J2, nc, J2p, members, chunk, stages;
+    double a, two_omega;
+    const double2* state;
+    size_t state_ms;      // member stride of the state (complex values)
+    float2* four_in;      // synthesis output, member stride 4 J (R+1)
+    const float2* four_out;  // analysis input, member stride 5 J (R+1)
+    double2* FE;
+    size_t fe_ms;
+    const double* cor;
+    const int2* tiles;
+    int* err;
+};
 
-    if (tid == 0) {
-        mbar_init(bar_tma, 1);
-        mbar_init(bar_mma, 1);
+// Stage buffers, barriers and tensor memory of one CTA.
+struct Cta {
+    unsigned char* smem;
+    size_t stage_sz;
+    uint64_t* bars;  // [0, kMaxStages): TMA full; [kMaxStages, 2 kMaxStages): MMA done
+    uint32_t* tslot;
+    volatile int* abort;
+};
+constexpr int kMaxStages = 2;
+
+template <int MODE>
+__device__ inline Cta cta_setup(unsigned char* smem_raw, int chunk, int stages, uint32_t ncols) {
+    Cta c;
+    c.smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    c.stage_sz = stage_bytes(MODE, chunk);
+    c.bars = reinterpret_cast<uint64_t*>(c.smem + stages * c.stage_sz);
+    c.tslot = reinterpret_cast<uint32_t*>(c.bars + 2 * kMaxStages);
+    c.abort = reinterpret_cast<volatile int*>(c.tslot + 1);
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < 2 * kMaxStages; ++s) mbar_init(sa(&c.bars[s]), 1);
+        *c.abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 0) tmem_alloc(sa(tslot));
-    __syncthreads();
-    if (tid == 0) {
-        mbar_expect_tx(bar_tma, (uint32_t)(S::NT * nkb * kTileBytes));
-        for (int t = 0; t < S::NT; ++t)
-            for (int kb = 0; kb < nkb; ++kb)
-                tma_load_2d(sa(A + ((size_t)t * nkb + kb) * kTileBytes), &maps.m[t], kb * S::KB, m * kTileRows,
-                            bar_tma);
+    if ((threadIdx.x >> 5) == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sa(c.tslot)),
+                     "r"(ncols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    // B operands: P group columns (zeta, Phi', chi, psi) x (re, im) + 8 x parity,
-    //             H group columns (psi, chi) x (re, im) + 8 x parity (4..7, 12..15 zero)
-    unsigned char* BP = B;
-    unsigned char* BH = B + S::NPART * bsz;
-    const double sa2 = -a * a;
-    for (int k = tid; k < Kp; k += kTcThreads) {
-        float pv[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        const int par = k & 1;
-        if (k < nm) {
-            const int n = m + k;
-            const double s = n > 0 ? sa2 / (n * (n + 1.0)) : 0.0;
-            const double2 ph = state[off + k], ze = state[nc + off + k], de = state[2 * nc + off + k];
-            pv[0] = (float)ze.x; pv[1] = (float)ze.y;
-            pv[2] = (float)ph.x; pv[3] = (float)ph.y;
-            pv[4] = (float)(de.x * s); pv[5] = (float)(de.y * s);
-            pv[6] = (float)(ze.x * s); pv[7] = (float)(ze.y * s);
-        }
-        for (int c = 0; c < 16; ++c) {
-            const int comp = c & 7, cpar = c >> 3;
-            const float vP = cpar == par ? pv[comp] : 0.f;
-            const float vH = (cpar == par && comp < 4) ? pv[comp < 2 ? comp + 6 : comp + 2] : 0.f;
-            put_b<MODE>(BP, BP + bsz, c, k, vP);
-            put_b<MODE>(BH, BH + bsz, c, k, vH);
-        }
-    }
-    fence_async_smem();
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    const uint32_t tmem = *tslot;
-    if (tid == 0) {
-        *issued = 0;
-        if (!mbar_wait(bar_tma, 0)) {
-            atomicExch(err, kErrTmaTimeout);
-        } else {
-            *issued = 1;
-            tc_fence_after();
-            const int nsteps = Kp / S::KSTEP;
-            for (int s = 0; s < nsteps; ++s) {
-                const int kb = (s * S::KSTEP) / S::KB;
-                const uint32_t ain = (uint32_t)((s * S::KSTEP) % S::KB) * S::ESZ;
-                const uint32_t boff = (uint32_t)s * 512;
-                for (int g = 0; g < 2; ++g) {
-                    const uint32_t d = tmem + (uint32_t)(g * kTcN);
-                    unsigned char* Bg = g == 0 ? BP : BH;
-                    if (MODE == MODE_TF32) {
-                        const uint64_t ad = desc_sw128(sa(A + ((size_t)g * nkb + kb) * kTileBytes) + ain);
-                        const uint64_t bd = desc_plain(sa(Bg) + boff, 256, 128);
-                        mma<MODE>(d, ad, bd, s > 0);
-                    } else {
-                        const uint64_t ah = desc_sw128(sa(A + ((size_t)(2 * g) * nkb + kb) * kTileBytes) + ain);
-                        const uint64_t al = desc_sw128(sa(A + ((size_t)(2 * g + 1) * nkb + kb) * kTileBytes) + ain);
-                        const uint64_t bh = desc_plain(sa(Bg) + boff, 256, 128);
-                        const uint64_t bl = desc_plain(sa(Bg + bsz) + boff, 256, 128);
-                        mma<MODE>(d, ah, bh, s > 0);
-                        mma<MODE>(d, ah, bl, 1);
-                        mma<MODE>(d, al, bh, 1);
-                    }
-                }
+    return c;
+}
+
+template <int MODE>
+__device__ __forceinline__ unsigned char* a_tile(const Cta& c, int st, int t) {
+    return c.smem + st * c.stage_sz + (size_t)t * kTileBytes;
+}
+template <int MODE>
+__device__ __forceinline__ unsigned char* b_tile(const Cta& c, int st, int grp, int part, int chunk) {
+    using S = Shape<MODE>;
+    return c.smem + st * c.stage_sz + (size_t)S::NT * kTileBytes + (size_t)(grp * S::NPART + part) * (16 * chunk) * 128;
+}
+
+// Issue the four MMA steps of one K block for both column groups.
+template <int MODE>
+__device__ __forceinline__ void mma_block(const Cta& c, int st, int chunk, uint32_t tmem, int N, uint32_t idesc,
+                                          bool first) {
+    using S = Shape<MODE>;
+    const uint32_t lbo = 16u * N;
+    for (int s = 0; s < S::KB / S::KSTEP; ++s) {
+        const uint32_t acc = (!first || s > 0) ? 1u : 0u;
+        for (int grp = 0; grp < 2; ++grp) {
+            const uint32_t d = tmem + (uint32_t)(grp * N);
+            const uint32_t bofs = (uint32_t)s * 2 * lbo;
+            if (MODE == MODE_TF32) {
+                const uint64_t ad = desc_sw128(sa(a_tile<MODE>(c, st, grp)) + s * 32);
+                const uint64_t bd = desc_plain(sa(b_tile<MODE>(c, st, grp, 0, chunk)) + bofs, lbo, 128);
+                mma_n<MODE>(d, ad, bd, idesc, acc);
+            } else {
+                const uint64_t ah = desc_sw128(sa(a_tile<MODE>(c, st, 2 * grp)) + s * 32);
+                const uint64_t al = desc_sw128(sa(a_tile<MODE>(c, st, 2 * grp + 1)) + s * 32);
+                const uint64_t bh = desc_plain(sa(b_tile<MODE>(c, st, grp, 0, chunk)) + bofs, lbo, 128);
+                const uint64_t bl = desc_plain(sa(b_tile<MODE>(c, st, grp, 1, chunk)) + bofs, lbo, 128);
+                mma_n<MODE>(d, ah, bh, idesc, acc);
+                mma_n<MODE>(d, ah, bl, idesc, 1u);
+                mma_n<MODE>(d, al, bh, idesc, 1u);
             }
-            mma_commit(bar_mma);
         }
     }
-    __syncthreads();
-    const bool ok = *issued && mbar_wait(bar_mma, 0);
-    if (*issued && !ok && lane == 0) atomicExch(err, kErrMmaTimeout);
+}
+
+// The K loop shared by synthesis and analysis.  Stage st holds K block kb
+// (st = kb % stages).  Before the threads overwrite a stage's B tiles and
+// thread 0 reloads its A tiles, the MMAs that read it (K block kb - stages)
+// must have completed; thread 0 issues the MMAs of a block once its TMA
+// bytes have landed and the B tiles are written, then commits to the stage's
+// MMA barrier.  build_b(st, kb) writes the B tiles of block kb; load_a(st,
+// kb) issues its TMA loads.  Returns false if a wait gave up.
+template <int MODE, class BuildB, class LoadA>
+__device__ inline bool k_loop(const Cta& c, int nkb, int stages, int chunk, uint32_t tmem, int N, uint32_t idesc,
+                              int* err, BuildB build_b, LoadA load_a) {
+    if (threadIdx.x == 0)
+        for (int kb = 0; kb < nkb && kb < stages; ++kb) load_a(kb % stages, kb);
+    for (int kb = 0; kb < nkb; ++kb) {
+        const int st = kb % stages;
+        const uint32_t use = (uint32_t)(kb / stages);
+        if (kb >= stages) {
+            if (!mbar_wait(sa(&c.bars[kMaxStages + st]), (use - 1) & 1)) {
+                if ((threadIdx.x & 31) == 0) atomicExch(err, kErrMmaTimeout);
+                *c.abort = 1;
+            }
+            if (threadIdx.x == 0 && !*c.abort) load_a(st, kb);
+        }
+        build_b(st, kb);
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        if (*c.abort) return false;
+        if (threadIdx.x == 0) {
+            if (!mbar_wait(sa(&c.bars[st]), use & 1)) {
+                atomicExch(err, kErrTmaTimeout);
+                *c.abort = 1;
+            } else {
+                tc_fence_after();
+                mma_block<MODE>(c, st, chunk, tmem, N, idesc, kb == 0);
+                mma_commit(sa(&c.bars[kMaxStages + st]));
+            }
+        }
+        __syncthreads();
+        if (*c.abort) return false;
+    }
+    const int last = nkb - 1;
+    if (!mbar_wait(sa(&c.bars[kMaxStages + last % stages]), (uint32_t)(last / stages) & 1)) {
+        if ((threadIdx.x & 31) == 0) atomicExch(err, kErrMmaTimeout);
+        return false;
+    }
     tc_fence_after();
-    float vP[16], vH[16];
+    return true;
+}
+
+template <int MODE>
+__device__ __forceinline__ uint32_t idesc_for(int N) {
+    const uint32_t base = MODE == MODE_TF32 ? ((1u << 4) | (2u << 7) | (2u << 10)) : ((1u << 4) | (1u << 7) | (1u << 10));
+    return base | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(kTileRows >> 4) << 24);
+}
+
+__device__ __forceinline__ void cta_release(const Cta& c, uint32_t tmem, uint32_t ncols) {
+    tc_fence_before();
+    __syncthreads();
+    if ((threadIdx.x >> 5) == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+}
+
+// ---------------------------------------------------------------- synthesis
+// grid (R + 1, member chunks): one zonal wavenumber m and up to `chunk`
+// members per CTA; D[lat, 16 b + c] accumulates over the degrees of m.
+template <int MODE>
+__global__ void __launch_bounds__(kTcThreads, 1) k_tc_synth(const __grid_constant__ Maps maps, const TcArgs g) {
+    using S = Shape<MODE>;
+    extern __shared__ unsigned char smem_raw[];
+    const int m = blockIdx.x;
+    const int b0 = blockIdx.y * g.chunk;
+    const int bc = min(g.chunk, g.members - b0);
+    const int N = 16 * bc;
+    const int R = g.R, nm = R + 1 - m;
+    const int off = m * (R + 1) - m * (m - 1) / 2;
+    const int nkb = (nm + S::KB - 1) / S::KB;
+    const uint32_t ncols = tmem_cols_for(2 * N);
+    const Cta c = cta_setup<MODE>(smem_raw, g.chunk, g.stages, ncols);
+    const uint32_t tmem = *c.tslot;
+    const uint32_t lbo = 16u * N;
+    const double sa2 = -g.a * g.a;
+    auto load_a = [&](int st, int kb) {
+        mbar_expect_tx(sa(&c.bars[st]), (uint32_t)(S::NT * kTileBytes));
+        for (int t = 0; t < S::NT; ++t)
+            tma_load_2d(sa(a_tile<MODE>(c, st, t)), &maps.m[t], kb * S::KB, m * kTileRows, sa(&c.bars[st]));
+    };
+    // B columns per member b: P group (zeta, Phi', chi, psi) x (re, im) + 8 x parity,
+    // H group (psi, chi) x (re, im) + 8 x parity (4..7 and 12..15 zero).
+    auto build_b = [&](int st, int kb) {
+        unsigned char* P0 = b_tile<MODE>(c, st, 0, 0, g.chunk);
+        unsigned char* P1 = b_tile<MODE>(c, st, 0, S::NPART - 1, g.chunk);
+        unsigned char* H0 = b_tile<MODE>(c, st, 1, 0, g.chunk);
+        unsigned char* H1 = b_tile<MODE>(c, st, 1, S::NPART - 1, g.chunk);
+        for (int it = threadIdx.x; it < bc * S::KB; it += kTcThreads) {
+            const int b = it / S::KB, k = it - b * S::KB;
+            const int kk = kb * S::KB + k;
+            float pv[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            if (kk < nm) {
+                const int n = m + kk;
+                const double s = n > 0 ? sa2 / (n * (n + 1.0)) : 0.0;
+                const double2* x = g.state + (size_t)(b0 + b) * g.state_ms + off + kk;
+                const double2 ph = x[0], ze = x[g.nc], de = x[2 * g.nc];
+                pv[0] = (float)ze.x; pv[1] = (float)ze.y;
+                pv[2] = (float)ph.x; pv[3] = (float)ph.y;
+                pv[4] = (float)(de.x * s); pv[5] = (float)(de.y * s);
+                pv[6] = (float)(ze.x * s); pv[7] = (float)(ze.y * s);
+            }
+            const int par = kk & 1;
+            for (int col = 0; col < 16; ++col) {
+                const int comp = col & 7, cpar = col >> 3;
+                const float vP = cpar == par ? pv[comp] : 0.f;
+                const float vH = (cpar == par && comp < 4) ? pv[comp < 2 ? comp + 6 : comp + 2] : 0.f;
+                put_b<MODE>(P0, P1, 16 * b + col, k, vP, lbo);
+                put_b<MODE>(H0, H1, 16 * b + col, k, vH, lbo);
+            }
+        }
+    };
+    const bool ok = k_loop<MODE>(c, nkb, g.stages, g.chunk, tmem, N, idesc_for<MODE>(N), g.err, build_b, load_a);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t lane_base = tmem + ((uint32_t)(32 * warp) << 16);
-    tmem_ld16(lane_base, vP);
-    tmem_ld16(lane_base + kTcN, vH);
     const int j = 32 * warp + lane;
-    if (ok && j < J2) {
-        const float ia = (float)(1.0 / a), dm = (float)m;
-        const int J = 2 * J2, jS = J - 1 - j;
-        const size_t fs = (size_t)J * (R + 1);
-        auto cx = [&](const float* v, int c) { return make_float2(v[c], v[c + 1]); };
-        // even parts at columns c, odd parts at c + 8
+    const int J = 2 * g.J2, jS = J - 1 - j;
+    const size_t fs = (size_t)J * (R + 1);
+    for (int b = 0; b < bc; ++b) {
+        float vP[16], vH[16];
+        tmem_ld16(lane_base + 16 * b, vP);
+        tmem_ld16(lane_base + N + 16 * b, vH);
+        if (!ok || j >= g.J2) continue;
+        float2* four = g.four_in + (size_t)(b0 + b) * 4 * fs;
+        const float ia = (float)(1.0 / g.a), dm = (float)m;
+        auto cx = [&](const float* v, int q) { return make_float2(v[q], v[q + 1]); };
+        // even parts at columns q, odd parts at q + 8
         const float2 zN = cadd(cx(vP, 0), cx(vP, 8)), zS = csub(cx(vP, 0), cx(vP, 8));
         const float2 pN = cadd(cx(vP, 2), cx(vP, 10)), pS = csub(cx(vP, 2), cx(vP, 10));
         const float2 xPN = cadd(cx(vP, 4), cx(vP, 12)), xPS = csub(cx(vP, 4), cx(vP, 12));
@@ -331,142 +434,91 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_synth(const double2* __res
         four[3 * fs + (size_t)j * (R + 1) + m] = cscale(cadd(cim(dm, sPN), xHN), ia);
         four[3 * fs + (size_t)jS * (R + 1) + m] = cscale(cadd(cim(dm, sPS), xHS), ia);
     }
-    tc_fence_before();
-    __syncthreads();
-    if (warp == 0) tmem_dealloc(tmem);
+    cta_release(c, tmem, ncols);
 }
 
 // ----------------------------------------------------------------- analysis
+// grid (tiles, member chunks): one (m, 128 degrees) tile and up to `chunk`
+// members per CTA; D[k, 16 b + c] accumulates over the latitudes.
 template <int MODE>
-__global__ void __launch_bounds__(kTcThreads, 1) k_tc_anal(const float2* __restrict__ four_out,
-                                                           const __grid_constant__ Maps maps,
-                                                           const int2* __restrict__ tiles, int R, int J2, int nc,
-                                                           int J2p, double a, double2* __restrict__ FE,
-                                                           const double2* __restrict__ state, double two_omega,
-                                                           const double* __restrict__ cor,
-                                                           int* __restrict__ err) {
+__global__ void __launch_bounds__(kTcThreads, 1) k_tc_anal(const __grid_constant__ Maps maps, const TcArgs g) {
     using S = Shape<MODE>;
     extern __shared__ unsigned char smem_raw[];
-    unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    const int2 tl = tiles[blockIdx.x];
+    const int2 tl = g.tiles[blockIdx.x];
     const int m = tl.x, t = tl.y;
-    const int nm = R + 1 - m;
+    const int b0 = blockIdx.y * g.chunk;
+    const int bc = min(g.chunk, g.members - b0);
+    const int N = 16 * bc;
+    const int R = g.R, nm = R + 1 - m;
     const int off = m * (R + 1) - m * (m - 1) / 2;
-    const int nkb = (J2p + S::KB - 1) / S::KB;
-    const int Kp = nkb * S::KB;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    unsigned char* A = smem;
-    unsigned char* B = A + (size_t)S::NT * nkb * kTileBytes;
-    const int bsz = S::b_bytes(Kp);
-    uint64_t* bars = reinterpret_cast<uint64_t*>(B + 2 * S::NPART * bsz);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 2);
-    volatile int* issued = reinterpret_cast<volatile int*>(tslot + 1);
-    const uint32_t bar_tma = sa(&bars[0]), bar_mma = sa(&bars[1]);
-
-    if (tid == 0) {
-        mbar_init(bar_tma, 1);
-        mbar_init(bar_mma, 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    if (warp == 0) tmem_alloc(sa(tslot));
-    __syncthreads();
-    if (tid == 0) {
-        mbar_expect_tx(bar_tma, (uint32_t)(S::NT * nkb * kTileBytes));
-        for (int q = 0; q < S::NT; ++q)
-            for (int kb = 0; kb < nkb; ++kb)
-                tma_load_2d(sa(A + ((size_t)q * nkb + kb) * kTileBytes), &maps.m[q], kb * S::KB,
-                            off + t * kTileRows, bar_tma);
-    }
-    // B operands over latitudes: P group (C, A, B, E) x (re, im) + 8 x parity;
-    // H group (D, B, A) x (re, im) + 8 x parity (columns 6, 7, 14, 15 zero).
-    // even = north + south, odd = north - south.
-    unsigned char* BP = B;
-    unsigned char* BH = B + S::NPART * bsz;
-    const int J = 2 * J2;
+    const int nkb = (g.J2p + S::KB - 1) / S::KB;
+    const uint32_t ncols = tmem_cols_for(2 * N);
+    const Cta c = cta_setup<MODE>(smem_raw, g.chunk, g.stages, ncols);
+    const uint32_t tmem = *c.tslot;
+    const uint32_t lbo = 16u * N;
+    const int J = 2 * g.J2;
     const size_t fs = (size_t)J * (R + 1);
-    for (int j = tid; j < Kp; j += kTcThreads) {
-        float2 e[5], o[5];
-        for (int f = 0; f < 5; ++f) {
-            if (j < J2) {
-                const float2 gN = four_out[(size_t)f * fs + (size_t)j * (R + 1) + m];
-                const float2 gS = four_out[(size_t)f * fs + (size_t)(J - 1 - j) * (R + 1) + m];
-                e[f] = cadd(gN, gS);
-                o[f] = csub(gN, gS);
-            } else {
-                e[f] = o[f] = make_float2(0.f, 0.f);
-            }
-        }
-        // field order in four_out: A, B, C, D, E
-        const int pf[4] = {2, 0, 1, 4};   // C, A, B, E
-        const int hf[3] = {3, 1, 0};      // D, B, A
-        for (int c = 0; c < 16; ++c) {
-            const int comp = c & 7, cpar = c >> 3;
-            const float2* src = cpar ? o : e;
-            const float2 zp = src[pf[comp >> 1]];
-            const float vP = (comp & 1) ? zp.y : zp.x;
-            float vH = 0.f;
-            if (comp < 6) {
-                const float2 zh = src[hf[comp >> 1]];
-                vH = (comp & 1) ? zh.y : zh.x;
-            }
-            put_b<MODE>(BP, BP + bsz, c, j, vP);
-            put_b<MODE>(BH, BH + bsz, c, j, vH);
-        }
-    }
-    fence_async_smem();
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tmem = *tslot;
-    if (tid == 0) {
-        *issued = 0;
-        if (!mbar_wait(bar_tma, 0)) {
-            atomicExch(err, kErrTmaTimeout);
-        } else {
-            *issued = 1;
-            tc_fence_after();
-            const int nsteps = Kp / S::KSTEP;
-            for (int s = 0; s < nsteps; ++s) {
-                const int kb = (s * S::KSTEP) / S::KB;
-                const uint32_t ain = (uint32_t)((s * S::KSTEP) % S::KB) * S::ESZ;
-                const uint32_t boff = (uint32_t)s * 512;
-                for (int g = 0; g < 2; ++g) {
-                    const uint32_t d = tmem + (uint32_t)(g * kTcN);
-                    unsigned char* Bg = g == 0 ? BP : BH;
-                    if (MODE == MODE_TF32) {
-                        const uint64_t ad = desc_sw128(sa(A + ((size_t)g * nkb + kb) * kTileBytes) + ain);
-                        mma<MODE>(d, ad, desc_plain(sa(Bg) + boff, 256, 128), s > 0);
-                    } else {
-                        const uint64_t ah = desc_sw128(sa(A + ((size_t)(2 * g) * nkb + kb) * kTileBytes) + ain);
-                        const uint64_t al = desc_sw128(sa(A + ((size_t)(2 * g + 1) * nkb + kb) * kTileBytes) + ain);
-                        const uint64_t bh = desc_plain(sa(Bg) + boff, 256, 128);
-                        const uint64_t bl = desc_plain(sa(Bg + bsz) + boff, 256, 128);
-                        mma<MODE>(d, ah, bh, s > 0);
-                        mma<MODE>(d, ah, bl, 1);
-                        mma<MODE>(d, al, bh, 1);
-                    }
+    auto load_a = [&](int st, int kb) {
+        mbar_expect_tx(sa(&c.bars[st]), (uint32_t)(S::NT * kTileBytes));
+        for (int q = 0; q < S::NT; ++q)
+            tma_load_2d(sa(a_tile<MODE>(c, st, q)), &maps.m[q], kb * S::KB, off + t * kTileRows, sa(&c.bars[st]));
+    };
+    // B columns per member over latitudes: P group (C, A, B, E) x (re, im) + 8 x parity,
+    // H group (D, B, A) x (re, im) + 8 x parity (6, 7, 14, 15 zero);
+    // even = north + south, odd = north - south.
+    auto build_b = [&](int st, int kb) {
+        unsigned char* P0 = b_tile<MODE>(c, st, 0, 0, g.chunk);
+        unsigned char* P1 = b_tile<MODE>(c, st, 0, S::NPART - 1, g.chunk);
+        unsigned char* H0 = b_tile<MODE>(c, st, 1, 0, g.chunk);
+        unsigned char* H1 = b_tile<MODE>(c, st, 1, S::NPART - 1, g.chunk);
+        for (int it = threadIdx.x; it < bc * S::KB; it += kTcThreads) {
+            const int b = it / S::KB, k = it - b * S::KB;
+            const int j = kb * S::KB + k;
+            float2 e[5], o[5];
+            const float2* F = g.four_out + (size_t)(b0 + b) * 5 * fs;
+            for (int f = 0; f < 5; ++f) {
+                if (j < g.J2) {
+                    const float2 gN = F[(size_t)f * fs + (size_t)j * (R + 1) + m];
+                    const float2 gS = F[(size_t)f * fs + (size_t)(J - 1 - j) * (R + 1) + m];
+                    e[f] = cadd(gN, gS);
+                    o[f] = csub(gN, gS);
+                } else {
+                    e[f] = o[f] = make_float2(0.f, 0.f);
                 }
             }
-            mma_commit(bar_mma);
+            const int pf[4] = {2, 0, 1, 4};  // C, A, B, E in four_out order A, B, C, D, E
+            const int hf[3] = {3, 1, 0};     // D, B, A
+            for (int col = 0; col < 16; ++col) {
+                const int comp = col & 7, cpar = col >> 3;
+                const float2* src = cpar ? o : e;
+                const float2 zp = src[pf[comp >> 1]];
+                const float vP = (comp & 1) ? zp.y : zp.x;
+                float vH = 0.f;
+                if (comp < 6) {
+                    const float2 zh = src[hf[comp >> 1]];
+                    vH = (comp & 1) ? zh.y : zh.x;
+                }
+                put_b<MODE>(P0, P1, 16 * b + col, k, vP, lbo);
+                put_b<MODE>(H0, H1, 16 * b + col, k, vH, lbo);
+            }
         }
-    }
-    __syncthreads();
-    const bool ok = *issued && mbar_wait(bar_mma, 0);
-    if (*issued && !ok && lane == 0) atomicExch(err, kErrMmaTimeout);
-    tc_fence_after();
-    float vP[16], vH[16];
+    };
+    const bool ok = k_loop<MODE>(c, nkb, g.stages, g.chunk, tmem, N, idesc_for<MODE>(N), g.err, build_b, load_a);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t lane_base = tmem + ((uint32_t)(32 * warp) << 16);
-    tmem_ld16(lane_base, vP);
-    tmem_ld16(lane_base + kTcN, vH);
     const int k = t * kTileRows + 32 * warp + lane;
-    if (ok && k < nm) {
+    for (int b = 0; b < bc; ++b) {
+        float vP[16], vH[16];
+        tmem_ld16(lane_base + 16 * b, vP);
+        tmem_ld16(lane_base + N + 16 * b, vH);
+        if (!ok || k >= nm) continue;
         const int par = k & 1;
         const float* P8 = vP + 8 * par;        // C, A, B, E at this row's parity
         const float* H8 = vH + 8 * (par ^ 1);  // D, B, A at the opposite parity
         const double2 sC{P8[0], P8[1]}, sA{P8[2], P8[3]}, sB{P8[4], P8[5]}, sE{P8[6], P8[7]};
         const double2 hD{H8[0], H8[1]}, hB{H8[2], H8[3]}, hA{H8[4], H8[5]};
         const int n = m + k;
-        const double ia = 1.0 / a, dm = (double)m;
+        const double ia = 1.0 / g.a, dm = (double)m;
         const double2 divCD = cscale(csub(cim(dm, sC), hD), ia);
         const double2 divAB = cscale(csub(cim(dm, sA), hB), ia);
         const double2 curlAB = cscale(cadd(cim(dm, sB), hA), ia);
@@ -475,17 +527,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_anal(const float2* __restr
         double2 f1 = make_double2(-divAB.x, -divAB.y);
         double2 f2 = make_double2(curlAB.x + lap * sE.x, curlAB.y + lap * sE.y);
         double2 dz, dd;  // the Coriolis part, exactly in float64 (grid products carry no f)
-        coriolis_linear(state, cor, nc, R, m, n, off, a, two_omega, dz, dd);
+        coriolis_linear(g.state + (size_t)(b0 + b) * g.state_ms, g.cor, g.nc, R, m, n, off, g.a, g.two_omega, dz, dd);
         f1 = cadd(f1, dz);
         f2 = cadd(f2, dd);
         if (m == 0) f0.y = f1.y = f2.y = 0.0;
+        double2* FE = g.FE + (size_t)(b0 + b) * g.fe_ms;
         FE[off + k] = f0;
-        FE[nc + off + k] = f1;
-        FE[2 * nc + off + k] = f2;
+        FE[g.nc + off + k] = f1;
+        FE[2 * g.nc + off + k] = f2;
     }
-    tc_fence_before();
-    __syncthreads();
-    if (warp == 0) tmem_dealloc(tmem);
+    cta_release(c, tmem, ncols);
 }
 
 // ---------------------------------------------------------- table builders
@@ -557,6 +608,15 @@ bool make_map(CUtensorMap* map, void* base, int mode, uint64_t cols, uint64_t ro
 
 TcState* st_of(sh_plan_t p) { return reinterpret_cast<TcState*>(p->mp.tc); }
 
+constexpr size_t kSmemBudget = 227 * 1024;
+
+// Pipeline depth for a member chunk: two stages when they fit, else one.
+int stages_for(int mode, int chunk) {
+    if (cta_smem_bytes(mode, chunk, 2) <= kSmemBudget) return 2;
+    if (cta_smem_bytes(mode, chunk, 1) <= kSmemBudget) return 1;
+    return 0;
+}
+
 template <int MODE>
 mlsdc_status build_tables(sh_plan_t p, TcState* s) {
     const int esz = MODE == MODE_TF32 ? 4 : 2;
@@ -587,14 +647,98 @@ mlsdc_status build_tables(sh_plan_t p, TcState* s) {
             return MLSDC_ERR_CUDA;
         }
     }
-    const int nkb_syn = s->KS / Shape<MODE>::KB;
-    const int nkb_ana = s->J2p / Shape<MODE>::KB;
-    s->smem_syn = tc_smem_bytes<MODE>(nkb_syn);
-    s->smem_ana = tc_smem_bytes<MODE>(nkb_ana);
-    mlsdc_status rs = raise_smem_limit((const void*)k_tc_synth<MODE>, s->smem_syn);
-    if (rs == MLSDC_OK) rs = raise_smem_limit((const void*)k_tc_anal<MODE>, s->smem_ana);
-    if (rs != MLSDC_OK) return rs;
     return MLSDC_OK;
+}
+
+template <int MODE>
+mlsdc_status launch_synth(sh_plan_t p, TcState* s, const TcArgs& g, cudaStream_t st) {
+    const int nchunks = (g.members + g.chunk - 1) / g.chunk;
+    const size_t smem = cta_smem_bytes(MODE, g.chunk, g.stages);
+    mlsdc_status rs = raise_smem_limit((const void*)k_tc_synth<MODE>, smem);
+    if (rs != MLSDC_OK) return rs;
+    k_tc_synth<MODE><<<dim3(p->R + 1, nchunks), kTcThreads, smem, st>>>(s->map_syn, g);
+    MLSDC_LAUNCHED("k_tc_synth");
+    return MLSDC_OK;
+}
+
+template <int MODE>
+mlsdc_status launch_anal(sh_plan_t p, TcState* s, const TcArgs& g, cudaStream_t st) {
+    const int nchunks = (g.members + g.chunk - 1) / g.chunk;
+    const size_t smem = cta_smem_bytes(MODE, g.chunk, g.stages);
+    mlsdc_status rs = raise_smem_limit((const void*)k_tc_anal<MODE>, smem);
+    if (rs != MLSDC_OK) return rs;
+    k_tc_anal<MODE><<<dim3(s->n_tiles, nchunks), kTcThreads, smem, st>>>(s->map_ana, g);
+    MLSDC_LAUNCHED("k_tc_anal");
+    return MLSDC_OK;
+}
+
+TcArgs base_args(sh_plan_t p, TcState* s, double a, int members) {
+    TcArgs g{};
+    g.R = p->R;
+    g.J2 = p->J2;
+    g.nc = p->nc;
+    g.J2p = s->J2p;
+    g.members = members;
+    g.chunk = std::min(s->chunk, members);
+    g.stages = stages_for(s->mode, g.chunk);
+    g.a = a;
+    g.four_in = p->mp.four_in;
+    g.four_out = p->mp.four_out;
+    g.cor = p->d_cor;
+    g.tiles = s->d_tiles;
+    g.err = s->d_err;
+    return g;
+}
+
+// Autotuner: time the synthesis and analysis for a full batch of members
+// with each feasible member chunk (1, 2, 4, 8, 16 members per CTA) and keep
+// the fastest.  Runs once per plan, on zero inputs, at plan creation.
+template <int MODE>
+mlsdc_status autotune(sh_plan_t p, TcState* s) {
+    const int B = p->max_members;
+    if (B == 1) {
+        s->chunk = 1;
+        return MLSDC_OK;
+    }
+    const size_t n = (size_t)B * 3 * p->nc;
+    double2 *x = nullptr, *fe = nullptr;
+    MLSDC_CUDA(cudaMalloc((void**)&x, n * sizeof(double2)));
+    MLSDC_CUDA(cudaMalloc((void**)&fe, n * sizeof(double2)));
+    MLSDC_CUDA(cudaMemset(x, 0, n * sizeof(double2)));
+    cudaEvent_t e0, e1;
+    MLSDC_CUDA(cudaEventCreate(&e0));
+    MLSDC_CUDA(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int best_chunk = 1;
+    mlsdc_status rs = MLSDC_OK;
+    for (int chunk = 1; chunk <= 16 && chunk <= B && rs == MLSDC_OK; chunk *= 2) {
+        if (stages_for(MODE, chunk) == 0) continue;
+        s->chunk = chunk;
+        TcArgs g = base_args(p, s, 6.37122e6, B);
+        g.state = x;
+        g.state_ms = (size_t)3 * p->nc;
+        g.FE = fe;
+        g.fe_ms = (size_t)3 * p->nc;
+        for (int rep = 0; rep < 4 && rs == MLSDC_OK; ++rep) {
+            if (rep == 1) cudaEventRecord(e0);
+            rs = launch_synth<MODE>(p, s, g, 0);
+            if (rs == MLSDC_OK) rs = launch_anal<MODE>(p, s, g, 0);
+        }
+        cudaEventRecord(e1);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rs == MLSDC_OK && ms < best) {
+            best = ms;
+            best_chunk = chunk;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(x);
+    cudaFree(fe);
+    s->chunk = best_chunk;
+    return rs;
 }
 
 }  // namespace
@@ -617,7 +761,13 @@ mlsdc_status tc_init(sh_plan_t p) {
     s->n_tiles = (int)tiles.size();
     MLSDC_CUDA(cudaMalloc((void**)&s->d_tiles, tiles.size() * sizeof(int2)));
     MLSDC_CUDA(cudaMemcpy(s->d_tiles, tiles.data(), tiles.size() * sizeof(int2), cudaMemcpyHostToDevice));
-    return s->mode == MODE_TF32 ? build_tables<MODE_TF32>(p, s) : build_tables<MODE_BF16X3>(p, s);
+    mlsdc_status rs = s->mode == MODE_TF32 ? build_tables<MODE_TF32>(p, s) : build_tables<MODE_BF16X3>(p, s);
+    if (rs != MLSDC_OK) return rs;
+    rs = s->mode == MODE_TF32 ? autotune<MODE_TF32>(p, s) : autotune<MODE_BF16X3>(p, s);
+    if (rs != MLSDC_OK) return rs;
+    p->tc_chunk = s->chunk;
+    MLSDC_CUDA(cudaMemset(s->d_err, 0, sizeof(int)));
+    return MLSDC_OK;
 }
 
 void tc_free(sh_plan_t p) {
@@ -633,30 +783,24 @@ void tc_free(sh_plan_t p) {
     p->mp.tc = nullptr;
 }
 
-mlsdc_status tc_synth(sh_plan_t p, const double* state, double a, cudaStream_t st) {
+mlsdc_status tc_synth(sh_plan_t p, const double* state, double a, RhsBatch b, cudaStream_t st) {
     TcState* s = st_of(p);
-    if (s->mode == MODE_TF32)
-        k_tc_synth<MODE_TF32><<<p->R + 1, kTcThreads, s->smem_syn, st>>>(
-            (const double2*)state, s->map_syn, p->R, p->J2, p->nc, a, p->mp.four_in, s->d_err);
-    else
-        k_tc_synth<MODE_BF16X3><<<p->R + 1, kTcThreads, s->smem_syn, st>>>(
-            (const double2*)state, s->map_syn, p->R, p->J2, p->nc, a, p->mp.four_in, s->d_err);
-    MLSDC_LAUNCHED("k_tc_synth");
-    return MLSDC_OK;
+    TcArgs g = base_args(p, s, a, b.members);
+    g.state = (const double2*)state;
+    g.state_ms = b.state_ms;
+    return s->mode == MODE_TF32 ? launch_synth<MODE_TF32>(p, s, g, st) : launch_synth<MODE_BF16X3>(p, s, g, st);
 }
 
-mlsdc_status tc_anal(sh_plan_t p, double a, double* FE, const double* state, double two_omega, cudaStream_t st) {
+mlsdc_status tc_anal(sh_plan_t p, double a, double* FE, const double* state, double two_omega, RhsBatch b,
+                     cudaStream_t st) {
     TcState* s = st_of(p);
-    if (s->mode == MODE_TF32)
-        k_tc_anal<MODE_TF32><<<s->n_tiles, kTcThreads, s->smem_ana, st>>>(
-            p->mp.four_out, s->map_ana, s->d_tiles, p->R, p->J2, p->nc, s->J2p, a, (double2*)FE,
-            (const double2*)state, two_omega, p->d_cor, s->d_err);
-    else
-        k_tc_anal<MODE_BF16X3><<<s->n_tiles, kTcThreads, s->smem_ana, st>>>(
-            p->mp.four_out, s->map_ana, s->d_tiles, p->R, p->J2, p->nc, s->J2p, a, (double2*)FE,
-            (const double2*)state, two_omega, p->d_cor, s->d_err);
-    MLSDC_LAUNCHED("k_tc_anal");
-    return MLSDC_OK;
+    TcArgs g = base_args(p, s, a, b.members);
+    g.state = (const double2*)state;
+    g.state_ms = b.state_ms;
+    g.two_omega = two_omega;
+    g.FE = (double2*)FE;
+    g.fe_ms = b.fe_ms;
+    return s->mode == MODE_TF32 ? launch_anal<MODE_TF32>(p, s, g, st) : launch_anal<MODE_BF16X3>(p, s, g, st);
 }
 
 mlsdc_status tc_error(sh_plan_t p, int* code) {

@@ -170,14 +170,25 @@ extern "C" const char* mlsdc_last_error(void) { return g_last_error.c_str(); }
     } while (0)
 
 extern "C" mlsdc_status sh_plan(int R, int nlon, int nlat, int precision, sh_plan_t* out) {
+    return create_plan(R, nlon, nlat, precision, 1, out);
+}
+
+extern "C" mlsdc_status sh_plan_batched(int R, int nlon, int nlat, int precision, int max_members,
+                                        sh_plan_t* out) {
+    return create_plan(R, nlon, nlat, precision, max_members, out);
+}
+
+mlsdc_status mlsdc::create_plan(int R, int nlon, int nlat, int precision, int max_members, sh_plan_t* out) {
     if (!out) return MLSDC_ERR_INVALID;
     *out = nullptr;
     if (R < 1 || nlon < 16 || nlon > 1024 || (nlon & (nlon - 1)) != 0 || nlon < 3 * R + 1)
         return MLSDC_ERR_INVALID;
     if (nlat < 2 || nlat % 2 != 0 || 2 * nlat < 3 * R + 1 || nlat / 2 > 1024) return MLSDC_ERR_INVALID;
     if (precision < MLSDC_FP64 || precision > MLSDC_FP32) return MLSDC_ERR_INVALID;
+    if (max_members < 1 || max_members > 4096) return MLSDC_ERR_INVALID;
 
     sh_plan_t p = new sh_plan_s();
+    p->max_members = max_members;
     p->R = R;
     p->I = nlon;
     p->J = nlat;
@@ -231,7 +242,7 @@ extern "C" mlsdc_status sh_plan(int R, int nlon, int nlat, int precision, sh_pla
     p->n_synth = (int)cs.size();
     p->n_anal = (int)ca.size();
 
-    const size_t nfour = (size_t)kMaxFields * nlat * (R + 1);
+    const size_t nfour = (size_t)std::max(kMaxFields, 5 * max_members) * nlat * (R + 1);
     TRY(dev_alloc(&p->d_mu, nlat, &p->bytes));
     TRY(dev_alloc(&p->d_w, nlat, &p->bytes));
     TRY(dev_alloc(&p->d_P, P.size(), &p->bytes));

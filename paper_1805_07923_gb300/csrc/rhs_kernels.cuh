@@ -27,16 +27,25 @@ namespace mlsdc {
 constexpr int kSynthWarps = 4;
 constexpr int kAnalWarpsMax = 4;
 
+// Ensemble batching: blockIdx.y selects the member, and each array advances
+// by its member stride (in complex elements).  One member: all strides unused.
+struct MemberStrides {
+    size_t state, four_in, four_out, fe;
+};
+
 // U^m = (1/a) sum_n [ i m chi P - psi H ],  V^m = (1/a) sum_n [ i m psi P + chi H ]
 // with psi, chi = -a^2/(n(n+1)) (zeta, delta) (Helmholtz, Sec. 2).
 template <class T>
 __global__ void __launch_bounds__(32 * kSynthWarps) k_synth_rhs(const double2* __restrict__ state,
                                                                 const T* __restrict__ P, const T* __restrict__ H,
                                                                 const Chunk* __restrict__ chunks, int R, int J2,
-                                                                int nc, double a, C_t<T>* __restrict__ four) {
+                                                                int nc, double a, C_t<T>* __restrict__ four,
+                                                                MemberStrides ms) {
     using C = C_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* sc = reinterpret_cast<C*>(smem_raw);  // [nm][4]: zeta, Phi', chi, psi; reused for the reduction
+    state += blockIdx.y * ms.state;
+    four += blockIdx.y * ms.four_in;
     const Chunk ch = chunks[blockIdx.x];
     const int m = ch.m;
     const int nm = R + 1 - m;
@@ -116,10 +125,12 @@ template <class T>
 __global__ void __launch_bounds__(256) k_grid_rhs(const C_t<T>* __restrict__ four_in, C_t<T>* __restrict__ four_out,
                                                   const double* __restrict__ mu, const double* __restrict__ w,
                                                   const C_t<T>* __restrict__ tw, int R, int I, int logI, int J,
-                                                  double two_omega) {
+                                                  double two_omega, MemberStrides ms) {
     using C = C_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* sx = reinterpret_cast<C*>(smem_raw);  // [9][I/2]: zeta, Phi', U, V packed rows, then A..E
+    four_in += blockIdx.y * ms.four_in;
+    four_out += blockIdx.y * ms.four_out;
     const int j = blockIdx.x;
     const int Hn = I >> 1, logH = logI - 1;
     const size_t fs = (size_t)J * (R + 1);
@@ -207,9 +218,13 @@ __global__ void __launch_bounds__(32 * kAnalWarpsMax) k_anal_rhs(const C_t<T>* _
                                                                  const Chunk* __restrict__ chunks, int R, int J2,
                                                                  int nc, double a, double2* __restrict__ FE,
                                                                  const double2* __restrict__ state,
-                                                                 double two_omega_lin, const double* __restrict__ cor) {
+                                                                 double two_omega_lin, const double* __restrict__ cor,
+                                                                 MemberStrides ms) {
     using C = C_t<T>;
     constexpr int TW = 32;                    // latitudes per tile
+    four_out += blockIdx.y * ms.four_out;
+    FE += blockIdx.y * ms.fe;
+    state += blockIdx.y * ms.state;
     __shared__ C sG[kAnalWarpsMax][TW][5][2];  // per warp: [lat][field A..E][even, odd]
     __shared__ C red[kAnalWarpsMax - 1][7][32];
     const Chunk ch = chunks[blockIdx.x];

@@ -1,11 +1,17 @@
 // IMEX SDC sweeps and two-level MLSDC on the device (Sec. 4.2, Sec. 4.3,
 // Algorithm 1), the implicit right-hand side and the per-coefficient implicit
-// solve (Sec. 4.4).  All arithmetic here is float64.
+// solve (Sec. 4.4), for one member or a batch of ensemble members advanced in
+// lockstep.  All arithmetic here is float64.
+//
+// Layout: a level with B members holds node arrays [B][M+1][3][nc] (member
+// major, so each member's slice is the single-member layout); member b of a
+// batched kernel is blockIdx.y and every array advances by its member stride.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <map>
 #include <tuple>
+#include <vector>
 
 #include "internal.h"
 
@@ -51,7 +57,9 @@ __device__ __forceinline__ void implicit_solve_coef(double L, double alpha, cons
 }
 
 __global__ void k_implicit_rhs(const double2* __restrict__ x, double2* __restrict__ F,
-                               const int* __restrict__ ndeg, int nc, Phys ph) {
+                               const int* __restrict__ ndeg, int nc, Phys ph, size_t ms_x, size_t ms_f) {
+    x += blockIdx.y * ms_x;
+    F += blockIdx.y * ms_f;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) {
         const double n = ndeg[c];
         const double L = -n * (n + 1.0) * ph.inv_a2;
@@ -78,12 +86,19 @@ __global__ void k_implicit_solve(const double2* __restrict__ b, double2* __restr
 
 // One SDC node update (Eq. update_equation_sdcq_discrete_form, plus tau on a
 // coarse level), the implicit solve, and F_I at the new node.  Node arrays
-// are [M+1][3][nc] complex; `node` = 3 nc complex values.  The m = 0 launch
-// also copies node 0 of the old F arrays into the new ones.
+// are [M+1][3][nc] complex per member (member stride ms); `node` = 3 nc
+// complex values.  The m = 0 launch also copies node 0 of the old F arrays
+// into the new ones.
 __global__ void k_sweep_node(double2* Th, const double2* __restrict__ FIo, const double2* __restrict__ FEo,
-                             double2* FIn, const double2* FEn, const double2* __restrict__ tau,
-                             const int* __restrict__ ndeg, int nc, double dt, NodeRow row, Phys ph,
-                             double2* FEn_w) {
+                             double2* FIn, double2* FEn, const double2* __restrict__ tau,
+                             const int* __restrict__ ndeg, int nc, double dt, NodeRow row, Phys ph, size_t ms) {
+    const size_t mo = blockIdx.y * ms;
+    Th += mo;
+    FIo += mo;
+    FEo += mo;
+    FIn += mo;
+    FEn += mo;
+    if (tau) tau += mo;
     const size_t node = (size_t)3 * nc;
     const int m = row.m;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) {
@@ -126,14 +141,18 @@ __global__ void k_sweep_node(double2* Th, const double2* __restrict__ FIo, const
         if (m == 0) {
             for (int f = 0; f < 3; ++f) {
                 FIn[(size_t)f * nc + c] = FIo[(size_t)f * nc + c];
-                FEn_w[(size_t)f * nc + c] = FEo[(size_t)f * nc + c];
+                FEn[(size_t)f * nc + c] = FEo[(size_t)f * nc + c];
             }
         }
     }
 }
 
-// dst[k] = src for k = 0..count-1 (node broadcast), src and dst [3 nc] complex.
-__global__ void k_broadcast(const double2* __restrict__ src, double2* __restrict__ dst, int n3, int count) {
+// dst[k] = src for k = 0..count-1 (node broadcast), src and dst [3 nc] complex
+// per member.
+__global__ void k_broadcast(const double2* __restrict__ src, double2* __restrict__ dst, int n3, int count,
+                            size_t ms_src, size_t ms_dst) {
+    src += blockIdx.y * ms_src;
+    dst += blockIdx.y * ms_dst;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n3; c += gridDim.x * blockDim.x) {
         const double2 v = src[c];
         for (int k = 0; k < count; ++k) dst[(size_t)k * n3 + c] = v;
@@ -147,7 +166,9 @@ struct TransferMat {
 };
 
 __global__ void k_restrict(const double2* __restrict__ Tf, double2* __restrict__ Tc, const int* __restrict__ c2f,
-                           int ncf, int ncc, int nf_nodes, int i0, int i1, TransferMat Pcf) {
+                           int ncf, int ncc, int nf_nodes, int i0, int i1, TransferMat Pcf, size_t msf, size_t msc) {
+    Tf += blockIdx.y * msf;
+    Tc += blockIdx.y * msc;
     const int total = 3 * ncc;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
         const int f = t / ncc, k = t - f * ncc;
@@ -173,7 +194,15 @@ __global__ void k_fas_tau(const double2* __restrict__ Tf, const double2* __restr
                           const double2* __restrict__ FEf, const double2* __restrict__ Tc,
                           const double2* __restrict__ FIc, const double2* __restrict__ FEc,
                           double2* __restrict__ tau, const int* __restrict__ c2f, int ncf, int ncc,
-                          double dt, FasArgs A) {
+                          double dt, FasArgs A, size_t msf, size_t msc) {
+    const size_t of_m = blockIdx.y * msf, oc_m = blockIdx.y * msc;
+    Tf += of_m;
+    FIf += of_m;
+    FEf += of_m;
+    Tc += oc_m;
+    FIc += oc_m;
+    FEc += oc_m;
+    tau += oc_m;
     const int total = 3 * ncc;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
         const int f = t / ncc, k = t - f * ncc;
@@ -208,7 +237,18 @@ __global__ void k_interp(double2* __restrict__ Tf, double2* __restrict__ FIf, do
                          const double2* __restrict__ Tc, const double2* __restrict__ FIc,
                          const double2* __restrict__ FEc, const double2* __restrict__ Ts,
                          const double2* __restrict__ FIs, const double2* __restrict__ FEs,
-                         const int* __restrict__ c2f, int ncf, int ncc, int nfn, int ncn, TransferMat Pfc) {
+                         const int* __restrict__ c2f, int ncf, int ncc, int nfn, int ncn, TransferMat Pfc,
+                         size_t msf, size_t msc) {
+    const size_t of_m = blockIdx.y * msf, oc_m = blockIdx.y * msc;
+    Tf += of_m;
+    FIf += of_m;
+    FEf += of_m;
+    Tc += oc_m;
+    FIc += oc_m;
+    FEc += oc_m;
+    Ts += oc_m;
+    FIs += oc_m;
+    FEs += oc_m;
     const int total = 3 * ncc;
     const size_t nf3 = (size_t)3 * ncf, nc3 = (size_t)3 * ncc;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
@@ -329,13 +369,16 @@ using namespace mlsdc;
 struct sdc_level_s {
     sh_plan_t plan;
     swe_params prm;
-    int n;  // nodes
+    int n;        // nodes
+    int members;  // ensemble members advanced together
     std::vector<double> t, Q, QE, QI;
-    double2* Th = nullptr;     // [n][3][nc]
+    double2* Th = nullptr;  // [members][n][3][nc]
     double2* FI[2] = {nullptr, nullptr};
     double2* FE[2] = {nullptr, nullptr};
     int cur = 0;
     int64_t launches = 0;
+    size_t node() const { return (size_t)3 * plan->nc; }
+    size_t ms() const { return (size_t)n * node(); }  // member stride of node arrays
 };
 
 namespace mlsdc {
@@ -347,26 +390,31 @@ static int grid_for(int n) {
     return std::max(1, std::min(b, 152 * 8));
 }
 
+// F_E at one node of every member: x and FE point at that node of member 0.
 static mlsdc_status eval_FE(sdc_level_t L, const double2* x, double2* FE, cudaStream_t st) {
+    RhsBatch b;
+    b.members = L->members;
+    b.state_ms = b.fe_ms = L->ms();
     if (L->plan->precision == MLSDC_FP64)
-        return rhs_explicit_f64(L->plan, &L->prm, (const double*)x, (double*)FE, st, &L->launches);
-    return rhs_explicit_mp(L->plan, &L->prm, (const double*)x, (double*)FE, st, &L->launches);
+        return rhs_explicit_f64(L->plan, &L->prm, (const double*)x, (double*)FE, st, &L->launches, -1, b);
+    return rhs_explicit_mp(L->plan, &L->prm, (const double*)x, (double*)FE, st, &L->launches, -1, b);
 }
 
 static mlsdc_status eval_FI(sdc_level_t L, const double2* x, double2* FI, cudaStream_t st) {
     const int nc = L->plan->nc;
-    k_implicit_rhs<<<grid_for(nc), 256, 0, st>>>(x, FI, L->plan->d_ndeg, nc, phys_of(L->prm));
+    k_implicit_rhs<<<dim3(grid_for(nc), L->members), 256, 0, st>>>(x, FI, L->plan->d_ndeg, nc, phys_of(L->prm),
+                                                                   L->ms(), L->ms());
     MLSDC_LAUNCHED("k_implicit_rhs");
     L->launches++;
     return MLSDC_OK;
 }
 
-// One sweep on explicit buffers.
+// One sweep on explicit buffers ([members][n][3][nc] each).
 static mlsdc_status sweep(sdc_level_t L, double dt, double2* Th, const double2* FIo, const double2* FEo,
                           double2* FIn, double2* FEn, const double2* tau, cudaStream_t st) {
     const int nc = L->plan->nc;
     const int n = L->n;
-    const size_t node = (size_t)3 * nc;
+    const size_t node = L->node();
     Phys ph = phys_of(L->prm);
     for (int m = 0; m < n - 1; ++m) {
         NodeRow row;
@@ -379,8 +427,8 @@ static mlsdc_status sweep(sdc_level_t L, double dt, double2* Th, const double2* 
             row.q[j] = L->Q[(m + 1) * n + j];
         }
         row.qimm = L->QI[(m + 1) * n + m + 1];
-        k_sweep_node<<<grid_for(nc), 256, 0, st>>>(Th, FIo, FEo, FIn, FEn, tau, L->plan->d_ndeg, nc, dt, row, ph,
-                                                 FEn);
+        k_sweep_node<<<dim3(grid_for(nc), L->members), 256, 0, st>>>(Th, FIo, FEo, FIn, FEn, tau, L->plan->d_ndeg, nc,
+                                                                     dt, row, ph, L->ms());
         MLSDC_LAUNCHED("k_sweep_node");
         L->launches++;
         mlsdc_status s = eval_FE(L, Th + (m + 1) * node, FEn + (m + 1) * node, st);
@@ -389,28 +437,37 @@ static mlsdc_status sweep(sdc_level_t L, double dt, double2* Th, const double2* 
     return MLSDC_OK;
 }
 
-// Initialisation: Theta^n at every node, F_I and F_E evaluated once and spread.
+// Initialisation: Theta^n ([members][3][nc]) at every node, F_I and F_E
+// evaluated once and spread.
 static mlsdc_status spread(sdc_level_t L, const double2* state, cudaStream_t st) {
-    const int nc = L->plan->nc;
-    const int n3 = 3 * nc;
-    k_broadcast<<<grid_for(n3), 256, 0, st>>>(state, L->Th, n3, L->n);
+    const int n3 = (int)L->node();
+    const dim3 g(grid_for(n3), L->members);
+    k_broadcast<<<g, 256, 0, st>>>(state, L->Th, n3, L->n, (size_t)n3, L->ms());
     MLSDC_LAUNCHED("k_broadcast");
     L->launches++;
     mlsdc_status s;
     if ((s = eval_FI(L, L->Th, L->FI[L->cur], st)) != MLSDC_OK) return s;
     if ((s = eval_FE(L, L->Th, L->FE[L->cur], st)) != MLSDC_OK) return s;
-    k_broadcast<<<grid_for(n3), 256, 0, st>>>(L->FI[L->cur], L->FI[L->cur] + n3, n3, L->n - 1);
+    k_broadcast<<<g, 256, 0, st>>>(L->FI[L->cur], L->FI[L->cur] + n3, n3, L->n - 1, L->ms(), L->ms());
     MLSDC_LAUNCHED("k_broadcast");
-    k_broadcast<<<grid_for(n3), 256, 0, st>>>(L->FE[L->cur], L->FE[L->cur] + n3, n3, L->n - 1);
+    k_broadcast<<<g, 256, 0, st>>>(L->FE[L->cur], L->FE[L->cur] + n3, n3, L->n - 1, L->ms(), L->ms());
     MLSDC_LAUNCHED("k_broadcast");
     L->launches += 2;
+    return MLSDC_OK;
+}
+
+// The last node of every member into state [members][3][nc].
+static mlsdc_status copy_last_node(sdc_level_t L, double* state, cudaStream_t st) {
+    const size_t w = L->node() * sizeof(double2);
+    MLSDC_CUDA(cudaMemcpy2DAsync(state, w, L->Th + (L->n - 1) * L->node(), L->ms() * sizeof(double2), w,
+                                 (size_t)L->members, cudaMemcpyDeviceToDevice, st));
     return MLSDC_OK;
 }
 
 mlsdc_status implicit_rhs_launch(sh_plan_t p, const swe_params* prm, const double* state, double* FI,
                                  cudaStream_t st) {
     k_implicit_rhs<<<grid_for(p->nc), 256, 0, st>>>((const double2*)state, (double2*)FI, p->d_ndeg, p->nc,
-                                                   phys_of(*prm));
+                                                   phys_of(*prm), 0, 0);
     MLSDC_LAUNCHED("k_implicit_rhs");
     return MLSDC_OK;
 }
@@ -424,6 +481,16 @@ struct mlsdc_s {
     double2 *Ts = nullptr, *FIs = nullptr, *FEs = nullptr, *tau = nullptr;
     cudaStream_t cap = nullptr;
     std::map<std::tuple<double*, double, int, int>, cudaGraphExec_t> graphs;
+    int64_t launches = 0;
+};
+
+struct mlsdc_ensemble_s {
+    std::vector<mlsdc_t> groups;
+    std::vector<cudaStream_t> streams;  // one per group (fork-join branches)
+    std::vector<cudaEvent_t> done;      // one per group
+    cudaEvent_t fork = nullptr;
+    cudaStream_t cap = nullptr;
+    std::map<std::tuple<std::vector<double*>, double, int, int>, cudaGraphExec_t> graphs;
     int64_t launches = 0;
 };
 
@@ -458,12 +525,15 @@ extern "C" mlsdc_status mlsdc_check_finite(const double* state, int64_t n, int* 
     return MLSDC_OK;
 }
 
-extern "C" mlsdc_status sdc_level_create(sh_plan_t plan, const swe_params* prm, int n_nodes, sdc_level_t* out) {
+extern "C" mlsdc_status sdc_level_create_batched(sh_plan_t plan, const swe_params* prm, int n_nodes, int members,
+                                                 sdc_level_t* out) {
     if (!plan || !prm || !out || n_nodes < 2 || n_nodes > kMaxNodes) return MLSDC_ERR_INVALID;
+    if (members < 1 || members > plan->max_members) return MLSDC_ERR_INVALID;
     sdc_level_t L = new sdc_level_s();
     L->plan = plan;
     L->prm = *prm;
     L->n = n_nodes;
+    L->members = members;
     const int n = n_nodes;
     L->t = lobatto(n);
     L->Q.assign(n * n, 0.0);
@@ -500,7 +570,7 @@ extern "C" mlsdc_status sdc_level_create(sh_plan_t plan, const swe_params* prm, 
     for (int r = 0; r < k; ++r)
         for (int c = 0; c < k; ++c) L->QI[(r + 1) * n + (c + 1)] = U[c * k + r];
 
-    const size_t cnt = (size_t)n * 3 * plan->nc;
+    const size_t cnt = (size_t)members * L->ms();
     bool ok = cudaMalloc((void**)&L->Th, cnt * sizeof(double2)) == cudaSuccess;
     for (int b = 0; b < 2 && ok; ++b) {
         ok = ok && cudaMalloc((void**)&L->FI[b], cnt * sizeof(double2)) == cudaSuccess;
@@ -513,6 +583,10 @@ extern "C" mlsdc_status sdc_level_create(sh_plan_t plan, const swe_params* prm, 
     }
     *out = L;
     return MLSDC_OK;
+}
+
+extern "C" mlsdc_status sdc_level_create(sh_plan_t plan, const swe_params* prm, int n_nodes, sdc_level_t* out) {
+    return sdc_level_create_batched(plan, prm, n_nodes, 1, out);
 }
 
 extern "C" mlsdc_status sdc_level_destroy(sdc_level_t L) {
@@ -551,21 +625,18 @@ extern "C" mlsdc_status sdc_step(sdc_level_t L, double* state, double dt, int n_
     L->launches = 0;
     mlsdc_status s;
     if ((s = spread(L, (const double2*)state, st)) != MLSDC_OK) return s;
-    const size_t node = (size_t)3 * L->plan->nc;
     for (int k = 0; k < n_sweeps; ++k) {
         const int c = L->cur;
         if ((s = sweep(L, dt, L->Th, L->FI[c], L->FE[c], L->FI[1 - c], L->FE[1 - c], nullptr, st)) != MLSDC_OK)
             return s;
         L->cur = 1 - c;
     }
-    MLSDC_CUDA(cudaMemcpyAsync(state, L->Th + (L->n - 1) * node, node * sizeof(double2), cudaMemcpyDeviceToDevice,
-                               st));
-    return MLSDC_OK;
+    return copy_last_node(L, state, st);
 }
 
 extern "C" mlsdc_status mlsdc_create(sdc_level_t fine, sdc_level_t coarse, mlsdc_t* out) {
     if (!fine || !coarse || !out) return MLSDC_ERR_INVALID;
-    if (coarse->plan->R > fine->plan->R) return MLSDC_ERR_INVALID;
+    if (coarse->plan->R > fine->plan->R || coarse->members != fine->members) return MLSDC_ERR_INVALID;
     mlsdc_t ml = new mlsdc_s();
     ml->f = fine;
     ml->c = coarse;
@@ -580,7 +651,7 @@ extern "C" mlsdc_status mlsdc_create(sdc_level_t fine, sdc_level_t coarse, mlsdc
     std::vector<int> c2f(coarse->plan->nc);
     for (int m = 0; m <= Rc; ++m)
         for (int n = m; n <= Rc; ++n) c2f[moff(Rc, m) + n - m] = moff(Rf, m) + n - m;
-    const size_t cnt = (size_t)ncn * 3 * coarse->plan->nc;
+    const size_t cnt = (size_t)coarse->members * coarse->ms();
     bool ok = cudaMalloc((void**)&ml->d_c2f, c2f.size() * sizeof(int)) == cudaSuccess;
     ok = ok && cudaMalloc((void**)&ml->Ts, cnt * sizeof(double2)) == cudaSuccess;
     ok = ok && cudaMalloc((void**)&ml->FIs, cnt * sizeof(double2)) == cudaSuccess;
@@ -615,14 +686,17 @@ namespace mlsdc {
 static mlsdc_status mlsdc_enqueue(mlsdc_t ml, double* state, double dt, int n_iter, int n_c, cudaStream_t st) {
     sdc_level_t F = ml->f, C = ml->c;
     const int ncf = F->plan->nc, ncc = C->plan->nc;
-    const size_t nodef = (size_t)3 * ncf, nodec = (size_t)3 * ncc;
+    const size_t nodec = C->node();
     const int nfn = F->n, ncn = C->n;
+    const int B = F->members;
+    const size_t msf = F->ms(), msc = C->ms();
+    const dim3 gt(grid_for(3 * ncc), B);
     F->launches = C->launches = 0;
     int64_t own = 0;
     mlsdc_status s;
     // initialisation: fine spread; coarse node 0 = restriction of Theta^n, evaluated once
     if ((s = spread(F, (const double2*)state, st)) != MLSDC_OK) return s;
-    k_restrict<<<grid_for(3 * ncc), 256, 0, st>>>(F->Th, C->Th, ml->d_c2f, ncf, ncc, nfn, 0, 1, ml->Pcf);
+    k_restrict<<<gt, 256, 0, st>>>(F->Th, C->Th, ml->d_c2f, ncf, ncc, nfn, 0, 1, ml->Pcf, msf, msc);
     MLSDC_LAUNCHED("k_restrict");
     own++;
     if ((s = eval_FI(C, C->Th, C->FI[C->cur], st)) != MLSDC_OK) return s;
@@ -641,7 +715,7 @@ static mlsdc_status mlsdc_enqueue(mlsdc_t ml, double* state, double dt, int n_it
             return s;
         F->cur = cf = 1 - cf;
         // B) restrict nodes 1..Mc, evaluate, save
-        k_restrict<<<grid_for(3 * ncc), 256, 0, st>>>(F->Th, C->Th, ml->d_c2f, ncf, ncc, nfn, 1, ncn, ml->Pcf);
+        k_restrict<<<gt, 256, 0, st>>>(F->Th, C->Th, ml->d_c2f, ncf, ncc, nfn, 1, ncn, ml->Pcf, msf, msc);
         MLSDC_LAUNCHED("k_restrict");
         own++;
         int cc = C->cur;
@@ -649,13 +723,13 @@ static mlsdc_status mlsdc_enqueue(mlsdc_t ml, double* state, double dt, int n_it
             if ((s = eval_FI(C, C->Th + i * nodec, C->FI[cc] + i * nodec, st)) != MLSDC_OK) return s;
             if ((s = eval_FE(C, C->Th + i * nodec, C->FE[cc] + i * nodec, st)) != MLSDC_OK) return s;
         }
-        const size_t bytes = (size_t)ncn * nodec * sizeof(double2);
+        const size_t bytes = (size_t)B * msc * sizeof(double2);
         MLSDC_CUDA(cudaMemcpyAsync(ml->Ts, C->Th, bytes, cudaMemcpyDeviceToDevice, st));
         MLSDC_CUDA(cudaMemcpyAsync(ml->FIs, C->FI[cc], bytes, cudaMemcpyDeviceToDevice, st));
         MLSDC_CUDA(cudaMemcpyAsync(ml->FEs, C->FE[cc], bytes, cudaMemcpyDeviceToDevice, st));
         // C) FAS correction, coarse sweeps
-        k_fas_tau<<<grid_for(3 * ncc), 256, 0, st>>>(F->Th, F->FI[cf], F->FE[cf], C->Th, C->FI[cc], C->FE[cc],
-                                                     ml->tau, ml->d_c2f, ncf, ncc, dt, fa);
+        k_fas_tau<<<gt, 256, 0, st>>>(F->Th, F->FI[cf], F->FE[cf], C->Th, C->FI[cc], C->FE[cc], ml->tau, ml->d_c2f,
+                                      ncf, ncc, dt, fa, msf, msc);
         MLSDC_LAUNCHED("k_fas_tau");
         own++;
         for (int k = 0; k < n_c; ++k) {
@@ -667,15 +741,37 @@ static mlsdc_status mlsdc_enqueue(mlsdc_t ml, double* state, double dt, int n_it
         }
         cc = C->cur;
         // D) interpolate the coarse corrections to fine nodes 1..Mf
-        k_interp<<<grid_for(3 * ncc), 256, 0, st>>>(F->Th, F->FI[cf], F->FE[cf], C->Th, C->FI[cc], C->FE[cc],
-                                                    ml->Ts, ml->FIs, ml->FEs, ml->d_c2f, ncf, ncc, nfn, ncn,
-                                                    ml->Pfc);
+        k_interp<<<gt, 256, 0, st>>>(F->Th, F->FI[cf], F->FE[cf], C->Th, C->FI[cc], C->FE[cc], ml->Ts, ml->FIs,
+                                     ml->FEs, ml->d_c2f, ncf, ncc, nfn, ncn, ml->Pfc, msf, msc);
         MLSDC_LAUNCHED("k_interp");
         own++;
     }
-    MLSDC_CUDA(cudaMemcpyAsync(state, F->Th + (nfn - 1) * nodef, nodef * sizeof(double2), cudaMemcpyDeviceToDevice,
-                               st));
+    if ((s = copy_last_node(F, state, st)) != MLSDC_OK) return s;
     ml->launches = own + F->launches + C->launches;
+    return MLSDC_OK;
+}
+
+// Capture `enqueue(stream)` once into an executable graph.
+template <class Enqueue>
+static mlsdc_status capture(cudaStream_t cap, cudaGraphExec_t* out, Enqueue enqueue) {
+    MLSDC_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+    mlsdc_status s = enqueue(cap);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(cap, &g);
+    if (s != MLSDC_OK) {
+        if (g) cudaGraphDestroy(g);
+        return s;
+    }
+    if (e != cudaSuccess) {
+        set_error("cudaStreamEndCapture", e);
+        return MLSDC_ERR_CUDA;
+    }
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        set_error("cudaGraphInstantiate", e);
+        return MLSDC_ERR_CUDA;
+    }
     return MLSDC_OK;
 }
 
@@ -694,25 +790,11 @@ extern "C" mlsdc_status mlsdc_step(mlsdc_t ml, double* state, double dt, int n_i
         // reset both to 0 so capture and replays agree.
         ml->f->cur = 0;
         ml->c->cur = 0;
-        MLSDC_CUDA(cudaStreamBeginCapture(ml->cap, cudaStreamCaptureModeThreadLocal));
-        mlsdc_status s = mlsdc_enqueue(ml, state, dt, n_iter, n_coarse_sweeps, ml->cap);
-        cudaGraph_t g = nullptr;
-        cudaError_t e = cudaStreamEndCapture(ml->cap, &g);
-        if (s != MLSDC_OK) {
-            if (g) cudaGraphDestroy(g);
-            return s;
-        }
-        if (e != cudaSuccess) {
-            set_error("cudaStreamEndCapture", e);
-            return MLSDC_ERR_CUDA;
-        }
         cudaGraphExec_t ex = nullptr;
-        e = cudaGraphInstantiate(&ex, g, 0);
-        cudaGraphDestroy(g);
-        if (e != cudaSuccess) {
-            set_error("cudaGraphInstantiate", e);
-            return MLSDC_ERR_CUDA;
-        }
+        mlsdc_status s = capture(ml->cap, &ex, [&](cudaStream_t cs) {
+            return mlsdc_enqueue(ml, state, dt, n_iter, n_coarse_sweeps, cs);
+        });
+        if (s != MLSDC_OK) return s;
         it = ml->graphs.emplace(key, ex).first;
         ml->f->cur = 0;
         ml->c->cur = 0;
@@ -724,5 +806,96 @@ extern "C" mlsdc_status mlsdc_step(mlsdc_t ml, double* state, double dt, int n_i
 extern "C" mlsdc_status mlsdc_launch_count(mlsdc_t ml, int64_t* launches) {
     if (!ml || !launches) return MLSDC_ERR_INVALID;
     *launches = ml->launches;
+    return MLSDC_OK;
+}
+
+// ------------------------------------------------------------------ ensemble
+extern "C" mlsdc_status mlsdc_ensemble_create(const mlsdc_t* groups, int ngroups, mlsdc_ensemble_t* out) {
+    if (!groups || ngroups < 1 || ngroups > 64 || !out) return MLSDC_ERR_INVALID;
+    for (int g = 0; g < ngroups; ++g)
+        if (!groups[g]) return MLSDC_ERR_INVALID;
+    mlsdc_ensemble_t e = new mlsdc_ensemble_s();
+    e->groups.assign(groups, groups + ngroups);
+    bool ok = cudaStreamCreateWithFlags(&e->cap, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&e->fork, cudaEventDisableTiming) == cudaSuccess;
+    for (int g = 0; g < ngroups && ok; ++g) {
+        cudaStream_t s;
+        cudaEvent_t ev;
+        ok = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess;
+        if (ok) {
+            e->streams.push_back(s);
+            e->done.push_back(ev);
+        }
+    }
+    if (!ok) {
+        set_error("mlsdc_ensemble_create", cudaGetLastError());
+        mlsdc_ensemble_destroy(e);
+        return MLSDC_ERR_CUDA;
+    }
+    *out = e;
+    return MLSDC_OK;
+}
+
+extern "C" mlsdc_status mlsdc_ensemble_destroy(mlsdc_ensemble_t e) {
+    if (!e) return MLSDC_ERR_INVALID;
+    for (auto& kv : e->graphs) cudaGraphExecDestroy(kv.second);
+    for (auto s : e->streams) cudaStreamDestroy(s);
+    for (auto ev : e->done) cudaEventDestroy(ev);
+    if (e->fork) cudaEventDestroy(e->fork);
+    if (e->cap) cudaStreamDestroy(e->cap);
+    delete e;
+    return MLSDC_OK;
+}
+
+namespace mlsdc {
+
+// Fork: every group's step runs on its own stream after `st`; join: `st`
+// waits for all of them.  Inside a capture this becomes one graph with one
+// branch per group.
+static mlsdc_status ensemble_enqueue(mlsdc_ensemble_t e, const std::vector<double*>& states, double dt, int n_iter,
+                                     int n_c, cudaStream_t st) {
+    MLSDC_CUDA(cudaEventRecord(e->fork, st));
+    e->launches = 0;
+    for (size_t g = 0; g < e->groups.size(); ++g) {
+        MLSDC_CUDA(cudaStreamWaitEvent(e->streams[g], e->fork, 0));
+        mlsdc_status s = mlsdc_enqueue(e->groups[g], states[g], dt, n_iter, n_c, e->streams[g]);
+        if (s != MLSDC_OK) return s;
+        e->launches += e->groups[g]->launches;
+        MLSDC_CUDA(cudaEventRecord(e->done[g], e->streams[g]));
+        MLSDC_CUDA(cudaStreamWaitEvent(st, e->done[g], 0));
+    }
+    return MLSDC_OK;
+}
+
+}  // namespace mlsdc
+
+extern "C" mlsdc_status mlsdc_ensemble_step(mlsdc_ensemble_t e, double* const* states, double dt, int n_iter,
+                                            int n_coarse_sweeps, int use_graph, void* stream) {
+    if (!e || !states || n_iter < 0 || n_coarse_sweeps < 0) return MLSDC_ERR_INVALID;
+    std::vector<double*> sv(states, states + e->groups.size());
+    for (double* p : sv)
+        if (!p) return MLSDC_ERR_INVALID;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!use_graph) return ensemble_enqueue(e, sv, dt, n_iter, n_coarse_sweeps, st);
+    auto key = std::make_tuple(sv, dt, n_iter, n_coarse_sweeps);
+    auto it = e->graphs.find(key);
+    if (it == e->graphs.end()) {
+        for (mlsdc_t ml : e->groups) ml->f->cur = ml->c->cur = 0;
+        cudaGraphExec_t ex = nullptr;
+        mlsdc_status s = capture(e->cap, &ex, [&](cudaStream_t cs) {
+            return ensemble_enqueue(e, sv, dt, n_iter, n_coarse_sweeps, cs);
+        });
+        if (s != MLSDC_OK) return s;
+        it = e->graphs.emplace(key, ex).first;
+        for (mlsdc_t ml : e->groups) ml->f->cur = ml->c->cur = 0;
+    }
+    MLSDC_CUDA(cudaGraphLaunch(it->second, st));
+    return MLSDC_OK;
+}
+
+extern "C" mlsdc_status mlsdc_ensemble_launch_count(mlsdc_ensemble_t e, int64_t* launches) {
+    if (!e || !launches) return MLSDC_ERR_INVALID;
+    *launches = e->launches;
     return MLSDC_OK;
 }

@@ -120,22 +120,25 @@ mlsdc_status f64_prepare(sh_plan_t p) {
 }
 
 mlsdc_status rhs_explicit_f64(sh_plan_t p, const swe_params* prm, const double* state, double* FE,
-                              cudaStream_t st, int64_t* launches, int stage) {
+                              cudaStream_t st, int64_t* launches, int stage, RhsBatch b) {
     const int R = p->R;
+    if (b.members < 1 || b.members > p->max_members) return MLSDC_ERR_INVALID;
+    const size_t fs = (size_t)p->J * (R + 1);
+    const MemberStrides ms{b.state_ms, 4 * fs, 5 * fs, b.fe_ms};
     if (stage == 0 || stage < 0) {
-        k_synth_rhs<double><<<p->n_synth, 32 * kSynthWarps, synth_smem<double>(R), st>>>(
-            (const double2*)state, p->d_P, p->d_H, p->d_synth, R, p->J2, p->nc, prm->a, p->d_four_in);
+        k_synth_rhs<double><<<dim3(p->n_synth, b.members), 32 * kSynthWarps, synth_smem<double>(R), st>>>(
+            (const double2*)state, p->d_P, p->d_H, p->d_synth, R, p->J2, p->nc, prm->a, p->d_four_in, ms);
         MLSDC_LAUNCHED("k_synth_rhs<double>");
     }
     if (stage == 1 || stage < 0) {
-        k_grid_rhs<double><<<p->J, 256, sizeof(double2) * 9 * (p->I / 2), st>>>(
-            p->d_four_in, p->d_four_out, p->d_mu, p->d_w, p->d_tw, R, p->I, p->logI, p->J, 2.0 * prm->omega);
+        k_grid_rhs<double><<<dim3(p->J, b.members), 256, sizeof(double2) * 9 * (p->I / 2), st>>>(
+            p->d_four_in, p->d_four_out, p->d_mu, p->d_w, p->d_tw, R, p->I, p->logI, p->J, 2.0 * prm->omega, ms);
         MLSDC_LAUNCHED("k_grid_rhs<double>");
     }
     if (stage == 2 || stage < 0) {
-        k_anal_rhs<double><<<p->n_anal, 32 * anal_warps(p->J2), 0, st>>>(
+        k_anal_rhs<double><<<dim3(p->n_anal, b.members), 32 * anal_warps(p->J2), 0, st>>>(
             p->d_four_out, p->d_P, p->d_H, p->d_anal, R, p->J2, p->nc, prm->a, (double2*)FE,
-            (const double2*)state, 0.0, p->d_cor);
+            (const double2*)state, 0.0, p->d_cor, ms);
         MLSDC_LAUNCHED("k_anal_rhs<double>");
     }
     if (launches) *launches += stage < 0 ? 3 : 1;
@@ -181,6 +184,18 @@ extern "C" mlsdc_status swe_explicit_rhs(sh_plan_t p, const swe_params* prm, con
     cudaStream_t st = (cudaStream_t)stream;
     if (p->precision == MLSDC_FP64) return rhs_explicit_f64(p, prm, state, FE, st, nullptr, -1);
     return rhs_explicit_mp(p, prm, state, FE, st, nullptr, -1);
+}
+
+extern "C" mlsdc_status swe_explicit_rhs_batched(sh_plan_t p, const swe_params* prm, const double* states, double* FE,
+                                                 int members, void* stream) {
+    if (!p || !prm || !states || !FE || states == FE || members < 1 || members > p->max_members)
+        return MLSDC_ERR_INVALID;
+    RhsBatch b;
+    b.members = members;
+    b.state_ms = b.fe_ms = (size_t)3 * p->nc;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (p->precision == MLSDC_FP64) return rhs_explicit_f64(p, prm, states, FE, st, nullptr, -1, b);
+    return rhs_explicit_mp(p, prm, states, FE, st, nullptr, -1, b);
 }
 
 extern "C" mlsdc_status mlsdc_profile_rhs(sh_plan_t p, const swe_params* prm, const double* state, double* FE,

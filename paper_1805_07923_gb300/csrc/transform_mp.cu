@@ -27,8 +27,9 @@ __global__ void k_round_c32(const double2* __restrict__ x, float2* __restrict__ 
 
 mlsdc_status tc_init(sh_plan_t p);   // legendre_tc.cu
 void tc_free(sh_plan_t p);
-mlsdc_status tc_synth(sh_plan_t p, const double* state, double a, cudaStream_t st);
-mlsdc_status tc_anal(sh_plan_t p, double a, double* FE, const double* state, double two_omega, cudaStream_t st);
+mlsdc_status tc_synth(sh_plan_t p, const double* state, double a, RhsBatch b, cudaStream_t st);
+mlsdc_status tc_anal(sh_plan_t p, double a, double* FE, const double* state, double two_omega, RhsBatch b,
+                     cudaStream_t st);
 
 mlsdc_status mp_init(sh_plan_t p) {
     MPTables& t = p->mp;
@@ -41,8 +42,8 @@ mlsdc_status mp_init(sh_plan_t p) {
     };
     bool ok = alloc((void**)&t.P32, ntab * sizeof(float)) && alloc((void**)&t.H32, ntab * sizeof(float)) &&
               alloc((void**)&t.tw32, (p->I / 2) * sizeof(float2)) &&
-              alloc((void**)&t.four_in, 4 * nfour * sizeof(float2)) &&
-              alloc((void**)&t.four_out, 5 * nfour * sizeof(float2));
+              alloc((void**)&t.four_in, 4 * nfour * p->max_members * sizeof(float2)) &&
+              alloc((void**)&t.four_out, 5 * nfour * p->max_members * sizeof(float2));
     if (!ok) {
         set_error("cudaMalloc (mixed-precision tables)", cudaGetLastError());
         return MLSDC_ERR_ALLOC;
@@ -71,32 +72,35 @@ void mp_free(sh_plan_t p) {
 }
 
 mlsdc_status rhs_explicit_mp(sh_plan_t p, const swe_params* prm, const double* state, double* FE, cudaStream_t st,
-                             int64_t* launches, int stage) {
+                             int64_t* launches, int stage, RhsBatch b) {
     const int R = p->R;
     MPTables& t = p->mp;
+    if (b.members < 1 || b.members > p->max_members) return MLSDC_ERR_INVALID;
     const bool tc = p->precision == MLSDC_TF32 || p->precision == MLSDC_BF16X3;
+    const size_t fs = (size_t)p->J * (R + 1);
+    const MemberStrides ms{b.state_ms, 4 * fs, 5 * fs, b.fe_ms};
     mlsdc_status s;
     if (stage == 0 || stage < 0) {
         if (tc) {
-            if ((s = tc_synth(p, state, prm->a, st)) != MLSDC_OK) return s;
+            if ((s = tc_synth(p, state, prm->a, b, st)) != MLSDC_OK) return s;
         } else {
-            k_synth_rhs<float><<<p->n_synth, 32 * kSynthWarps, synth_smem<float>(R), st>>>(
-                (const double2*)state, t.P32, t.H32, p->d_synth, R, p->J2, p->nc, prm->a, t.four_in);
+            k_synth_rhs<float><<<dim3(p->n_synth, b.members), 32 * kSynthWarps, synth_smem<float>(R), st>>>(
+                (const double2*)state, t.P32, t.H32, p->d_synth, R, p->J2, p->nc, prm->a, t.four_in, ms);
             MLSDC_LAUNCHED("k_synth_rhs<float>");
         }
     }
     if (stage == 1 || stage < 0) {
-        k_grid_rhs<float><<<p->J, 256, sizeof(float2) * 9 * (p->I / 2), st>>>(
-            t.four_in, t.four_out, p->d_mu, p->d_w, t.tw32, R, p->I, p->logI, p->J, 0.0);
+        k_grid_rhs<float><<<dim3(p->J, b.members), 256, sizeof(float2) * 9 * (p->I / 2), st>>>(
+            t.four_in, t.four_out, p->d_mu, p->d_w, t.tw32, R, p->I, p->logI, p->J, 0.0, ms);
         MLSDC_LAUNCHED("k_grid_rhs<float>");
     }
     if (stage == 2 || stage < 0) {
         if (tc) {
-            if ((s = tc_anal(p, prm->a, FE, state, 2.0 * prm->omega, st)) != MLSDC_OK) return s;
+            if ((s = tc_anal(p, prm->a, FE, state, 2.0 * prm->omega, b, st)) != MLSDC_OK) return s;
         } else {
-            k_anal_rhs<float><<<p->n_anal, 32 * anal_warps(p->J2), 0, st>>>(
+            k_anal_rhs<float><<<dim3(p->n_anal, b.members), 32 * anal_warps(p->J2), 0, st>>>(
                 t.four_out, t.P32, t.H32, p->d_anal, R, p->J2, p->nc, prm->a, (double2*)FE, (const double2*)state,
-                2.0 * prm->omega, p->d_cor);
+                2.0 * prm->omega, p->d_cor, ms);
             MLSDC_LAUNCHED("k_anal_rhs<float>");
         }
     }

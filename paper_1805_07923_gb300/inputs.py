@@ -87,7 +87,7 @@ def truncate(x: np.ndarray, R_from: int, R_to: int) -> np.ndarray:
     """Keep the coefficients with n <= R_to of an m-major field (last axis)."""
     m, n = sh_mn(R_from)
     keep = n <= R_to
-    return x[..., keep]
+    return np.ascontiguousarray(x[..., keep])
 
 
 def perturbed_member(base: np.ndarray, R_base: int, R: int, k: int, rel: float = 0.01) -> np.ndarray:
@@ -99,7 +99,7 @@ def perturbed_member(base: np.ndarray, R_base: int, R: int, k: int, rel: float =
         weight = np.where(sh_mn(R)[0] == 0, 1.0, 2.0)
         rms = np.sqrt(np.sum(weight * np.abs(xb[f]) ** 2) / 2.0)
         out[f] = xb[f] + spectrum(R, 3000 + k, f, rel * rms)
-    return out
+    return np.ascontiguousarray(out)
 
 
 def to_real(x: np.ndarray) -> np.ndarray:

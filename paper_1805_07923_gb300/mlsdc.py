@@ -36,6 +36,13 @@ _SIGS = {
     "mlsdc_status_string": ([_I], ctypes.c_char_p),
     "mlsdc_last_error": ([], ctypes.c_char_p),
     "sh_plan": ([_I, _I, _I, _I, ctypes.POINTER(_VP)], _I),
+    "sh_plan_batched": ([_I, _I, _I, _I, _I, ctypes.POINTER(_VP)], _I),
+    "swe_explicit_rhs_batched": ([_VP, ctypes.POINTER(SweParams), _DP, _DP, _I, _VP], _I),
+    "sdc_level_create_batched": ([_VP, ctypes.POINTER(SweParams), _I, _I, ctypes.POINTER(_VP)], _I),
+    "mlsdc_ensemble_create": ([ctypes.POINTER(_VP), _I, ctypes.POINTER(_VP)], _I),
+    "mlsdc_ensemble_destroy": ([_VP], _I),
+    "mlsdc_ensemble_step": ([_VP, ctypes.POINTER(_VP), _D, _I, _I, _I, _VP], _I),
+    "mlsdc_ensemble_launch_count": ([_VP, ctypes.POINTER(_I64)], _I),
     "sh_plan_destroy": ([_VP], _I),
     "sh_plan_grid": ([_VP, _DP, _DP], _I),
     "sh_plan_device_bytes": ([_VP, ctypes.POINTER(_I64)], _I),
@@ -125,11 +132,15 @@ def n_coeffs(R: int) -> int:
 class Plan:
     """sh_plan: Gaussian grid and Legendre tables of one truncation."""
 
-    def __init__(self, R: int, nlon: int, nlat: int, precision="fp64"):
+    def __init__(self, R: int, nlon: int, nlat: int, precision="fp64", max_members: int = 1):
         prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         h = ctypes.c_void_p()
-        _check(lib().sh_plan(R, nlon, nlat, prec, ctypes.byref(h)), "sh_plan")
+        if max_members == 1:
+            _check(lib().sh_plan(R, nlon, nlat, prec, ctypes.byref(h)), "sh_plan")
+        else:
+            _check(lib().sh_plan_batched(R, nlon, nlat, prec, int(max_members), ctypes.byref(h)), "sh_plan_batched")
         self.h, self.R, self.I, self.J, self.precision = h, R, nlon, nlat, prec
+        self.max_members = max_members
         self.nc = n_coeffs(R)
 
     def close(self):
@@ -185,6 +196,13 @@ def swe_explicit_rhs(plan: Plan, prm: SweParams, state: torch.Tensor, FE: torch.
                                   _stream(stream)), "swe_explicit_rhs")
 
 
+def swe_explicit_rhs_batched(plan: Plan, prm: SweParams, states: torch.Tensor, FE: torch.Tensor, members: int,
+                             stream=None):
+    n = 6 * plan.nc * members
+    _check(lib().swe_explicit_rhs_batched(plan.h, ctypes.byref(prm), _ptr(states, n), _ptr(FE, n), int(members),
+                                          _stream(stream)), "swe_explicit_rhs_batched")
+
+
 def swe_implicit_rhs(plan: Plan, prm: SweParams, state: torch.Tensor, FI: torch.Tensor, stream=None):
     _check(lib().swe_implicit_rhs(plan.h, ctypes.byref(prm), _ptr(state, 6 * plan.nc), _ptr(FI, 6 * plan.nc),
                                   _stream(stream)), "swe_implicit_rhs")
@@ -198,12 +216,13 @@ def swe_implicit_solve(plan: Plan, prm: SweParams, alpha: float, b: torch.Tensor
 class Level:
     """sdc_level: a plan, the physics and n Gauss-Lobatto nodes."""
 
-    def __init__(self, plan: Plan, n_nodes: int, prm: SweParams | None = None):
+    def __init__(self, plan: Plan, n_nodes: int, prm: SweParams | None = None, members: int = 1):
         self.plan = plan
         self.prm = prm if prm is not None else swe_params()
         h = ctypes.c_void_p()
-        _check(lib().sdc_level_create(plan.h, ctypes.byref(self.prm), n_nodes, ctypes.byref(h)), "sdc_level_create")
-        self.h, self.n = h, n_nodes
+        _check(lib().sdc_level_create_batched(plan.h, ctypes.byref(self.prm), n_nodes, int(members), ctypes.byref(h)),
+               "sdc_level_create_batched")
+        self.h, self.n, self.members = h, n_nodes, members
 
     def close(self):
         if self.h:
@@ -226,13 +245,13 @@ class Level:
 
 
 def sdc_sweep(level: Level, dt: float, Theta, FI_old, FE_old, FI_new, FE_new, tau=None, stream=None):
-    n = 6 * level.n * level.plan.nc
+    n = 6 * level.n * level.plan.nc * level.members
     _check(lib().sdc_sweep(level.h, float(dt), _ptr(Theta, n), _ptr(FI_old, n), _ptr(FE_old, n), _ptr(FI_new, n),
                            _ptr(FE_new, n), _ptr(tau, n), _stream(stream)), "sdc_sweep")
 
 
 def sdc_step(level: Level, state: torch.Tensor, dt: float, n_sweeps: int, stream=None):
-    _check(lib().sdc_step(level.h, _ptr(state, 6 * level.plan.nc), float(dt), int(n_sweeps), _stream(stream)),
+    _check(lib().sdc_step(level.h, _ptr(state, 6 * level.plan.nc * level.members), float(dt), int(n_sweeps), _stream(stream)),
            "sdc_step")
 
 
@@ -264,7 +283,7 @@ class MLSDC:
 
 def mlsdc_step(ml: MLSDC, state: torch.Tensor, dt: float, n_iter: int, n_coarse_sweeps: int, use_graph: bool = False,
                stream=None):
-    _check(lib().mlsdc_step(ml.h, _ptr(state, 6 * ml.fine.plan.nc), float(dt), int(n_iter), int(n_coarse_sweeps),
+    _check(lib().mlsdc_step(ml.h, _ptr(state, 6 * ml.fine.plan.nc * ml.fine.members), float(dt), int(n_iter), int(n_coarse_sweeps),
                             1 if use_graph else 0, _stream(stream)), "mlsdc_step")
 
 
@@ -282,3 +301,40 @@ def mlsdc_profile_rhs(plan: Plan, prm: SweParams, state: torch.Tensor, FE: torch
     _check(lib().mlsdc_profile_rhs(plan.h, ctypes.byref(prm), _ptr(state, 6 * plan.nc), _ptr(FE, 6 * plan.nc),
                                    int(reps), out, _stream(stream)), "mlsdc_profile_rhs")
     return [float(v) for v in out]
+
+
+class Ensemble:
+    """MLSDC groups of uneven truncation stepped together (one graph per step)."""
+
+    def __init__(self, groups: list[MLSDC]):
+        self.groups = list(groups)
+        arr = (ctypes.c_void_p * len(groups))(*[g.h for g in groups])
+        h = ctypes.c_void_p()
+        _check(lib().mlsdc_ensemble_create(arr, len(groups), ctypes.byref(h)), "mlsdc_ensemble_create")
+        self.h = h
+
+    def close(self):
+        if self.h:
+            lib().mlsdc_ensemble_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def launch_count(self) -> int:
+        v = ctypes.c_int64()
+        _check(lib().mlsdc_ensemble_launch_count(self.h, ctypes.byref(v)), "mlsdc_ensemble_launch_count")
+        return v.value
+
+
+def mlsdc_ensemble_step(ens: Ensemble, states: list[torch.Tensor], dt: float, n_iter: int, n_coarse_sweeps: int,
+                        use_graph: bool = True, stream=None):
+    if len(states) != len(ens.groups):
+        raise MlsdcError("one state tensor per group")
+    ptrs = [_ptr(s, 6 * g.fine.plan.nc * g.fine.members) for s, g in zip(states, ens.groups)]
+    arr = (ctypes.c_void_p * len(ptrs))(*[p.value for p in ptrs])
+    _check(lib().mlsdc_ensemble_step(ens.h, arr, float(dt), int(n_iter), int(n_coarse_sweeps), 1 if use_graph else 0,
+                                     _stream(stream)), "mlsdc_ensemble_step")
