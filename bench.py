@@ -217,6 +217,114 @@ def total_phi_rel_l2(a, b, phibar=9.80616e4):
     return float(np.sqrt(np.sum(wt * np.abs(a[0] - b[0]) ** 2) / np.sum(wt * np.abs(tot) ** 2)))
 
 
+ENSEMBLE = [  # (Rf, If, Jf, Rc, Ic, Jc, members)
+    (42, 128, 64, 21, 64, 32, 32),
+    (85, 256, 128, 42, 128, 64, 48),
+    (170, 512, 256, 85, 256, 128, 16),
+]
+ENSEMBLE_NAME = ("96-member ensemble of uneven truncation: 32 x T42/T21, 48 x T85/T42, 16 x T170/T85 "
+                 "(2-level MLSDC 5/3 nodes, 4 iterations, 1 fine + 2 coarse sweeps, dt 150 s), members = 1% "
+                 "seeded perturbations of one T170 base state; one CUDA graph launch per ensemble step")
+
+
+def build_ensemble(M, torch, dev, prec):
+    from paper_1805_07923_gb300 import inputs
+    base = inputs.initial_state(170)
+    groups, keep, states = [], [], []
+    k0 = 0
+    for (Rf, If, Jf, Rc, Ic, Jc, B) in ENSEMBLE:
+        pf, pc = M.Plan(Rf, If, Jf, prec, B), M.Plan(Rc, Ic, Jc, prec, B)
+        lf, lc = M.Level(pf, 5, members=B), M.Level(pc, 3, members=B)
+        groups.append(M.MLSDC(lf, lc))
+        keep.append((pf, pc, lf, lc))
+        import numpy as np
+        x = np.stack([inputs.perturbed_member(base, 170, Rf, k0 + j) for j in range(B)])
+        k0 += B
+        states.append(torch.from_numpy(x).to(dev))
+    return M.Ensemble(groups), groups, keep, states
+
+
+def run_ensemble(args):
+    import torch
+
+    from paper_1805_07923_gb300 import mlsdc as M
+    dev = torch.device("cuda", 0)
+    w = WORKLOAD
+    prec = args.precision
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def timed(prec_, K):
+        ens, groups, keep, states = build_ensemble(M, torch, dev, prec_)
+        for _ in range(3):
+            M.mlsdc_ensemble_step(ens, states, w["dt"], w["n_iter"], w["n_coarse"], use_graph=True)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        for k in range(K):
+            flush.zero_()
+            ev[k][0].record(stream)
+            M.mlsdc_ensemble_step(ens, states, w["dt"], w["n_iter"], w["n_coarse"], use_graph=True)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in ev), ens, groups, keep, states
+
+    K = args.steps
+    clocks = ClockSampler(0)
+    clocks.start()
+    time.sleep(0.3)
+    total_ms, ens, groups, keep, states = timed(prec, K)
+    clk = clocks.stop()
+    members = sum(g[-1] for g in ENSEMBLE)
+    value = members * K / (total_ms * 1e-3)
+    nfe, nce = evals_per_step(w)
+    flops = sum(B * (nfe * sh_flops_per_eval(Rf, If, Jf) + nce * sh_flops_per_eval(Rc, Ic, Jc))
+                for (Rf, If, Jf, Rc, Ic, Jc, B) in ENSEMBLE)
+    # batched stage timing of every level's F_E kernels (CUDA events, this stream)
+    names = ["legendre_synthesis", "grid_fft_products", "legendre_analysis"]
+    stages, shares = {}, []
+    for (Rf, If, Jf, Rc, Ic, Jc, B), (pf, pc, lf, lc), x in zip(ENSEMBLE, keep, states):
+        for lvl, plan, (R, I, J), cnt in ((f"T{Rf}", pf, (Rf, If, Jf), nfe), (f"T{Rc}", pc, (Rc, Ic, Jc), nce)):
+            xs = x if plan is pf else torch.zeros((B, 3, plan.nc), dtype=torch.complex128, device=dev)
+            fe = torch.empty_like(xs)
+            ms = M.mlsdc_profile_rhs(plan, lf.prm, xs, fe, reps=20, members=B)
+            stages[f"{lvl}x{B}"] = dict(zip(names, ms))
+            for s in range(3):
+                fl = (legendre_stage_flops(R, J, s) if s != 1 else grid_stage_flops(R, I, J)) * B
+                shares.append((ms[s] * cnt, f"{lvl}x{B}", names[s], ms[s], fl))
+    shares.sort(reverse=True)
+    top = shares[0]
+    peaks = load_peaks()
+    bf16 = peaks.get("bf16_tflops", 1900.0)
+    achieved = top[4] / (top[3] * 1e-3) / 1e12
+    roof = {"bound": "tensor" if top[2] != "grid_fft_products" and prec in ("tf32", "bf16x3") else "alu",
+            "achieved": achieved, "unit": "TFLOP/s", "kernel": f"{top[2]} at {top[1]}", "kernel_ms": top[3]}
+    if roof["bound"] == "tensor":
+        roof["peak"] = bf16 if prec == "bf16x3" else bf16 * 1.1 / 2.25
+        roof["peak_source"] = "measured bf16 burst peak" + (" x 1.1/2.25 (tf32)" if prec == "tf32" else "")
+        if prec == "bf16x3":
+            roof["tensor_products_per_flop"] = 3
+    else:
+        roof["peak"] = measured_fp64_tflops(torch, dev) if prec == "fp64" else 152 * 128 * 2 * 2.07e9 / 1e12
+        roof["peak_source"] = "measured DGEMM" if prec == "fp64" else "float32 CUDA-core FMA rate"
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
+    line = {"metric": "ensemble member-steps/s (MLSDC-SH); SH TFLOP/s", "value": value, "unit": "member-steps/s",
+            "n_gpus": 1, "steps": K, "warmup": 3, "ms_per_step": total_ms / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": f"f64+{prec}" if prec != "fp64" else "f64",
+            "data": "synthetic", "config": {"workload": ENSEMBLE_NAME, "precision": prec, "members": members,
+                                            "l2": "flushed between timed steps (256 MB write)"},
+            "sh_tflops": flops * K / (total_ms * 1e-3) / 1e12, "gpu_launches": ens.launch_count() * K,
+            "roofline": roof, "stage_ms": stages, "clocks": clk,
+            }
+    if prec != "fp64":
+        del ens, groups, keep, states
+        K64 = max(3, min(K, 10))
+        ms64, *_ = timed("fp64", K64)
+        line["vs_fp64_ensemble"] = {"fp64_member_steps_per_s": members * K64 / (ms64 * 1e-3),
+                                    "speedup": value / (members * K64 / (ms64 * 1e-3))}
+    print(json.dumps(line), flush=True)
+
+
 def cpu_baseline(steps_cap_s: float = 25.0):
     """The float64 oracle as it stands, timed on this host for a bounded sample."""
     from oracle import sdc as osdc
@@ -279,9 +387,13 @@ def main():
                     help="Legendre/FFT arithmetic; bf16x3 (the fastest variant within 1e-6) by default")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="headline", choices=["headline", "ensemble"],
+                    help="headline: one T170/T85 member; ensemble: the 96-member uneven-truncation ensemble")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "ensemble":
+        return run_ensemble(args)
     args.warmup = max(3, args.warmup)
 
     import numpy as np

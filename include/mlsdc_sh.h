@@ -257,6 +257,9 @@ mlsdc_status mlsdc_ensemble_launch_count(mlsdc_ensemble_t ens, int64_t* launches
  * Not a paper operation: a measurement utility over the same kernels. */
 mlsdc_status mlsdc_profile_rhs(sh_plan_t plan, const swe_params* prm, const double* state, double* FE,
                                int reps, float* ms_host, void* stream);
+/* The same for a batch of `members` states ([members][3][N_c]) per launch. */
+mlsdc_status mlsdc_profile_rhs_batched(sh_plan_t plan, const swe_params* prm, const double* states, double* FE,
+                                       int members, int reps, float* ms_host, void* stream);
 
 /* Device check that a state (n doubles) is finite: writes 1 to *ok_host if
  * every value is finite, else 0 (synchronises the stream). */

@@ -200,11 +200,20 @@ extern "C" mlsdc_status swe_explicit_rhs_batched(sh_plan_t p, const swe_params* 
 
 extern "C" mlsdc_status mlsdc_profile_rhs(sh_plan_t p, const swe_params* prm, const double* state, double* FE,
                                           int reps, float* ms_host, void* stream) {
+    return mlsdc_profile_rhs_batched(p, prm, state, FE, 1, reps, ms_host, stream);
+}
+
+extern "C" mlsdc_status mlsdc_profile_rhs_batched(sh_plan_t p, const swe_params* prm, const double* state, double* FE,
+                                                  int members, int reps, float* ms_host, void* stream) {
     if (!p || !prm || !state || !FE || state == FE || reps < 1 || !ms_host) return MLSDC_ERR_INVALID;
+    if (members < 1 || members > p->max_members) return MLSDC_ERR_INVALID;
     cudaStream_t st = (cudaStream_t)stream;
+    RhsBatch b;
+    b.members = members;
+    b.state_ms = b.fe_ms = (size_t)3 * p->nc;
     auto run = [&](int stage) {
-        return p->precision == MLSDC_FP64 ? rhs_explicit_f64(p, prm, state, FE, st, nullptr, stage)
-                                          : rhs_explicit_mp(p, prm, state, FE, st, nullptr, stage);
+        return p->precision == MLSDC_FP64 ? rhs_explicit_f64(p, prm, state, FE, st, nullptr, stage, b)
+                                          : rhs_explicit_mp(p, prm, state, FE, st, nullptr, stage, b);
     };
     // one full evaluation first so every stage reads valid inputs
     mlsdc_status s = run(-1);

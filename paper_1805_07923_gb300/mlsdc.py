@@ -64,6 +64,8 @@ _SIGS = {
     "mlsdc_launch_count": ([_VP, ctypes.POINTER(_I64)], _I),
     "mlsdc_check_finite": ([_DP, _I64, ctypes.POINTER(_I), _VP], _I),
     "mlsdc_profile_rhs": ([_VP, ctypes.POINTER(SweParams), _DP, _DP, _I, ctypes.POINTER(ctypes.c_float), _VP], _I),
+    "mlsdc_profile_rhs_batched": ([_VP, ctypes.POINTER(SweParams), _DP, _DP, _I, _I, ctypes.POINTER(ctypes.c_float),
+                                   _VP], _I),
 }
 
 
@@ -295,11 +297,12 @@ def mlsdc_check_finite(x: torch.Tensor, stream=None) -> bool:
 
 
 def mlsdc_profile_rhs(plan: Plan, prm: SweParams, state: torch.Tensor, FE: torch.Tensor, reps: int = 50,
-                      stream=None) -> list[float]:
+                      stream=None, members: int = 1) -> list[float]:
     """Mean ms per launch of the three F_E stage kernels (synthesis, grid, analysis)."""
     out = (ctypes.c_float * 3)()
-    _check(lib().mlsdc_profile_rhs(plan.h, ctypes.byref(prm), _ptr(state, 6 * plan.nc), _ptr(FE, 6 * plan.nc),
-                                   int(reps), out, _stream(stream)), "mlsdc_profile_rhs")
+    n = 6 * plan.nc * members
+    _check(lib().mlsdc_profile_rhs_batched(plan.h, ctypes.byref(prm), _ptr(state, n), _ptr(FE, n), int(members),
+                                           int(reps), out, _stream(stream)), "mlsdc_profile_rhs_batched")
     return [float(v) for v in out]
 
 

@@ -1,0 +1,66 @@
+"""The whole headline run on the GPU against the float64 oracle's end state.
+
+tests/golden/headline_T170_T85_400.npy is written by
+tests/golden/make_headline_reference.py, which calls only the oracle:
+two-level MLSDC, T170 on 512 x 256 (5 Lobatto nodes) and T85 on 256 x 128
+(3 nodes), 4 iterations of 1 fine + 2 coarse sweeps, dt 150 s, 400 steps from
+the seeded state (seed 1805).
+
+Bars: the float64 path matches per step to 1e-12 (test_gpu_parity); over 400
+steps rounding differences grow, and the end state must agree to 1e-9 per
+field.  The mixed-precision variants that carry the headline must meet the
+1e-6 relative L2 bound on the total geopotential against the oracle."""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import sht as osht
+from paper_1805_07923_gb300 import inputs
+from paper_1805_07923_gb300 import mlsdc as M
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "headline_T170_T85_400.npy")
+
+
+def _run(prec, steps=400):
+    pf, pc = M.Plan(170, 512, 256, prec), M.Plan(85, 256, 128, prec)
+    ml = M.MLSDC(M.Level(pf, 5), M.Level(pc, 3))
+    x = torch.from_numpy(inputs.initial_state(170)).cuda()
+    for _ in range(steps):
+        M.mlsdc_step(ml, x, 150.0, 4, 2, use_graph=True)
+    torch.cuda.synchronize()
+    return x.cpu().numpy()
+
+
+def _rel(got, ref):
+    return float(np.sqrt(osht.norm2(170, got - ref) / osht.norm2(170, ref)))
+
+
+def _total_phi(got, ref, phibar=9.80616e4):
+    tot = ref[0].copy()
+    tot[0] += np.sqrt(2.0) * phibar
+    return float(np.sqrt(osht.norm2(170, got[0] - ref[0]) / osht.norm2(170, tot)))
+
+
+@pytest.fixture(scope="module")
+def oracle_end():
+    return np.load(GOLDEN)
+
+
+def test_fp64_run_matches_oracle_end_state(oracle_end):
+    got = _run("fp64")
+    errs = [_rel(got[k], oracle_end[k]) for k in range(3)]
+    print(f"fp64 400-step end state vs oracle: {errs}")
+    assert max(errs) <= 1e-9
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "fp32"])
+def test_mixed_run_meets_total_geopotential_bar_vs_oracle(prec, oracle_end):
+    got = _run(prec)
+    err = _total_phi(got, oracle_end)
+    print(f"{prec} 400-step total-Phi rel L2 vs oracle: {err:.3e}; fields "
+          f"{[round(_rel(got[k], oracle_end[k]), 10) for k in range(3)]}")
+    assert err <= 1e-6
