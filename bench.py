@@ -117,6 +117,8 @@ def dist_init():
 
 
 def barrier_max(value: float, ws: int, device):
+    """Max of a per-rank time over all ranks (the job's time); the ranks'
+    data never meet: replicas run independent members."""
     if ws == 1:
         return value
     import torch
@@ -125,6 +127,16 @@ def barrier_max(value: float, ws: int, device):
     dist.barrier()
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def replica_seed(rank: int) -> int:
+    """Seed of the member replica `rank` runs (rank 0 runs the headline state)."""
+    return 1805 + rank
+
+
+def job_value(ws: int, units_per_rank: int, max_ms: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return ws * units_per_rank / (max_ms * 1e-3)
 
 
 def measured_fp64_tflops(torch, device) -> float:
@@ -408,7 +420,7 @@ def main():
     w = WORKLOAD
     prec = args.precision
     ml, (pf, pc, lf, lc) = build_mlsdc(M, prec)
-    u0 = inputs.initial_state(w["Rf"], seed=1805 + rank)
+    u0 = inputs.initial_state(w["Rf"], seed=replica_seed(rank))
     state = torch.from_numpy(u0).to(dev)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -425,7 +437,7 @@ def main():
     if ws > 1:
         torch.distributed.barrier()
     total_ms = barrier_max(timed_steps(torch, M, ml, state, K, flush, stream), ws, dev)
-    value = ws * K / (total_ms * 1e-3)
+    value = job_value(ws, K, total_ms)
 
     # end to end through the public API with host buffers: H2D of the state from
     # pinned memory, the step, D2H of the result, every step
@@ -528,7 +540,7 @@ def main():
                    "l2": "flushed between timed steps (256 MB write)", "graph": "one CUDA graph per step"},
         "sh_tflops": sh_flops * value / ws / 1e12,
         "gpu_launches": launches_per_step * K,
-        "e2e": {"value": ws * Ke / (e2e_ms * 1e-3), "unit": "steps/s", "h2d_bytes_per_step": nbytes,
+        "e2e": {"value": job_value(ws, Ke, e2e_ms), "unit": "steps/s", "h2d_bytes_per_step": nbytes,
                 "d2h_bytes_per_step": nbytes},
         "roofline": roof,
         "stage_ms": {"T170": dict(zip(names, fine_ms)), "T85": dict(zip(names, coarse_ms))},
