@@ -77,11 +77,17 @@ def spread(lev: Level, u0):
     return [u0.copy() for _ in range(n)], [fi] * n, [fe] * n
 
 
-def sdc_step(lev: Level, u0, dt: float, n_sweeps: int):
-    """SDC(M+1, N_S): spread then N_S sweeps; returns the last node."""
+def sdc_step(lev: Level, u0, dt: float, n_sweeps: int, tape=None):
+    """SDC(M+1, N_S): spread then N_S sweeps; returns the last node.
+    With a `tape` dict, the node values of every sweep are recorded (the
+    points where F_E was evaluated, for the adjoint)."""
     Theta, FI, FE = spread(lev, u0)
+    if tape is not None:
+        tape["sweeps"] = []
     for _ in range(n_sweeps):
         Theta, FI, FE = sweep(lev, dt, Theta, FI, FE)
+        if tape is not None:
+            tape["sweeps"].append(Theta)
     return Theta[-1]
 
 
@@ -92,8 +98,10 @@ def collocation_operator(lev: Level, dt: float, Theta, FI, FE):
 
 
 def mlsdc_step(fine: Level, coarse: Level, u0, dt: float, n_iter: int, n_coarse_sweeps: int = 1,
-               return_nodes: bool = False):
-    """One time step of two-level MLSDC (Algorithm 1, repeated n_iter times)."""
+               return_nodes: bool = False, tape=None):
+    """One time step of two-level MLSDC (Algorithm 1, repeated n_iter times).
+    With a `tape` dict, the node values at which F_E was evaluated are
+    recorded per iteration (fine sweep, restriction, coarse sweeps)."""
     pf, pc = fine.prob, coarse.prob
     Pi_cf = quadrature.lagrange_matrix(fine.t, coarse.t)   # fine -> coarse (time)
     Pi_fc = quadrature.lagrange_matrix(coarse.t, fine.t)   # coarse -> fine (time)
@@ -110,6 +118,8 @@ def mlsdc_step(fine: Level, coarse: Level, u0, dt: float, n_iter: int, n_coarse_
     Th_c = [u0c] * (Mc + 1)
     FI_c = [pc.implicit_rhs(u0c)] * (Mc + 1)
     FE_c = [pc.explicit_rhs(u0c)] * (Mc + 1)
+    if tape is not None:
+        tape.update(u0c=u0c, iters=[])
     for _ in range(n_iter):
         # A) fine sweep
         Th_f, FI_f, FE_f = sweep(fine, dt, Th_f, FI_f, FE_f)
@@ -124,8 +134,12 @@ def mlsdc_step(fine: Level, coarse: Level, u0, dt: float, n_iter: int, n_coarse_
         A_c = collocation_operator(coarse, dt, Th_c, FI_c, FE_c)
         A_f = collocation_operator(fine, dt, Th_f, FI_f, FE_f)
         tau = [A_c[i] - restrict_node(A_f, i) for i in range(Mc + 1)]
+        coarse_nodes = []
         for _s in range(n_coarse_sweeps):
             Th_c, FI_c, FE_c = sweep(coarse, dt, Th_c, FI_c, FE_c, tau)
+            coarse_nodes.append(Th_c)
+        if tape is not None:
+            tape["iters"].append({"fine": Th_f, "restricted": Th_s, "coarse": coarse_nodes})
         # D) return to the fine level (no function evaluations)
         dT = [Th_c[i] - Th_s[i] for i in range(Mc + 1)]
         dI = [FI_c[i] - FI_s[i] for i in range(Mc + 1)]

@@ -146,3 +146,45 @@ def test_dropped_interpolation_of_F_is_caught(monkeypatch):
     monkeypatch.setattr(sdc, "mlsdc_step", no_f_interp)
     _fails(T_sdc.test_mlsdc_with_identical_levels_is_sdc)
     assert src_interp is not sdc.mlsdc_step
+
+
+# ---- the adjoint's pins (tests/test_oracle_adjoint.py) -----------------------
+import test_oracle_adjoint as T_ad  # noqa: E402
+from oracle import adjoint as oad  # noqa: E402
+
+
+def test_adjoint_sign_of_im_m_mistake_is_caught(monkeypatch):
+    monkeypatch.setattr(oad, "times_im_t", lambda g, x: 1j * g.m * x)
+    _fails(T_ad.test_scalar_and_vector_transform_transposes)
+    _fails(T_ad.test_explicit_rhs_adjoint_dot_product)
+
+
+def test_adjoint_untransposed_implicit_solve_is_caught(monkeypatch):
+    monkeypatch.setattr(oad, "implicit_solve_t", lambda swe_, lam, alpha: swe_.implicit_solve(lam, alpha))
+    _fails(T_ad.test_implicit_transposes)
+    _fails(T_ad.test_sdc_step_adjoint_dot_product)
+
+
+def test_adjoint_dropped_F_I_term_in_sweep_is_caught(monkeypatch):
+    monkeypatch.setattr(oad, "implicit_rhs_t", lambda swe_, lam: 0.0 * lam)
+    _fails(T_ad.test_sdc_step_adjoint_dot_product)
+
+
+def test_adjoint_dropped_tau_is_caught(monkeypatch):
+    orig = oad.sweep_ad
+
+    def no_tau(lev, dt, Tn, Tb, FIb, FEb, with_tau):
+        Thb, FIob, FEob, taub = orig(lev, dt, Tn, Tb, FIb, FEb, with_tau)
+        return Thb, FIob, FEob, ([0.0 * t for t in taub] if with_tau else None)
+    monkeypatch.setattr(oad, "sweep_ad", no_tau)
+    _fails(T_ad.test_mlsdc_step_adjoint_dot_product)
+
+
+def test_adjoint_missing_kinetic_energy_weight_is_caught(monkeypatch):
+    """The E-term adjoint without its 1/(1 - mu^2) factor."""
+    orig_t = oad.analysis_t
+
+    def bad(g, s):
+        return orig_t(g, s) * (1.0 - g.mu[:, None] ** 2)
+    monkeypatch.setattr(oad, "analysis_t", bad)
+    _fails(T_ad.test_explicit_rhs_adjoint_dot_product)
