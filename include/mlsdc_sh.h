@@ -73,6 +73,7 @@ typedef struct sh_plan_s* sh_plan_t;
 typedef struct sdc_level_s* sdc_level_t;
 typedef struct mlsdc_s* mlsdc_t;
 typedef struct mlsdc_ensemble_s* mlsdc_ensemble_t;
+typedef struct mlsdc_adjoint_s* mlsdc_adjoint_t;
 
 /* Text of a status code, and the last CUDA error message seen by this thread. */
 const char* mlsdc_status_string(mlsdc_status s);
@@ -260,6 +261,65 @@ mlsdc_status mlsdc_profile_rhs(sh_plan_t plan, const swe_params* prm, const doub
 /* The same for a batch of `members` states ([members][3][N_c]) per launch. */
 mlsdc_status mlsdc_profile_rhs_batched(sh_plan_t plan, const swe_params* prm, const double* states, double* FE,
                                        int members, int reps, float* ms_host, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Adjoint (reverse mode) of the MLSDC time step with respect to its initial
+ * state, float64, single member.  Inner product: a state is the real vector
+ * of the (Re, Im) parts of its stored coefficients, <x, y> = sum Re(conj(x) y);
+ * Im of m = 0 is not a degree of freedom (the fields are real, Sec. 3), so
+ * every adjoint returned has it zero and every adjoint passed in is
+ * projected (that part dropped).  This is the convention of PyTorch's
+ * complex gradients (dL/dRe + i dL/dIm for a real L).
+ *
+ * Only F_E is nonlinear; every other operation of a step (Sec. 4.2 node
+ * update, Sec. 4.4 implicit solve and F_I, Sec. 4.3.3 transfers, the FAS
+ * correction of Algorithm 1 step C) is linear with constant coefficients.
+ * The step is a fixed list of operations; its adjoint applies their
+ * transposes in reverse order, with F_E replaced by the transpose of its
+ * Jacobian at the input the forward step recorded.
+ *
+ * swe_explicit_rhs_adjoint: state_bar += F_E'(state)^t lambda, and lambda
+ * is set to zero (its value consumed).  state, lambda, state_bar: [3][N_c],
+ * pairwise distinct.  Needs an MLSDC_FP64 plan (one member).
+ */
+mlsdc_status swe_explicit_rhs_adjoint(sh_plan_t plan, const swe_params* prm, const double* state,
+                                      double* lambda, double* state_bar, void* stream);
+
+/* mlsdc_phi_misfit: J = 1/2 ||Phi'(state) - phi_target||^2 in the Parseval
+ * norm of Sec. 3 (sum |.|^2 over m = 0 plus twice over m >= 1, which equals
+ * 1/2 (1/I) sum_{i,j} w_j (Phi - Phi_t)^2 on the grid), written to the
+ * device double *J, and its gradient lambda = dJ/dstate ([3][N_c]: the
+ * weighted residual in the Phi' field, zeta and delta zero).  phi_target:
+ * [N_c] complex. */
+mlsdc_status mlsdc_phi_misfit(sh_plan_t plan, const double* state, const double* phi_target, double* J,
+                              double* lambda, void* stream);
+
+/* mlsdc_adjoint_create: a reverse-mode driver for n_steps steps of
+ * mlsdc_step(ml, ., dt, n_iter, n_coarse_sweeps) that stores the state every
+ * checkpoint_every steps (>= 1; n_steps/checkpoint_every states) and, during
+ * the backward pass, recomputes one segment of checkpoint_every steps at a
+ * time, recording that segment's F_E inputs, then walks it backwards.  Device
+ * memory: the checkpoints, checkpoint_every steps of F_E inputs, and one
+ * adjoint copy of every buffer a step uses.  The MLSDC object (float64 plans,
+ * one member) must outlive the driver and shares its buffers: order calls
+ * on one stream. */
+mlsdc_status mlsdc_adjoint_create(mlsdc_t ml, int n_steps, int checkpoint_every, double dt, int n_iter,
+                                  int n_coarse_sweeps, mlsdc_adjoint_t* out);
+mlsdc_status mlsdc_adjoint_destroy(mlsdc_adjoint_t adj);
+/* mlsdc_adjoint_forward: state_T = n_steps MLSDC steps from state0 ([3][N_c]
+ * each; may alias), storing the checkpoints.  The same arithmetic as
+ * mlsdc_step. */
+mlsdc_status mlsdc_adjoint_forward(mlsdc_adjoint_t adj, const double* state0, double* state_T, int use_graph,
+                                   void* stream);
+/* mlsdc_adjoint_backward: lambda_0 = (d state_T / d state0)^t lambda_T for
+ * the trajectory of the last mlsdc_adjoint_forward call (MLSDC_ERR_INVALID
+ * if there was none).  lambda_T, lambda_0: [3][N_c] (may alias).  With
+ * use_graph != 0 each recomputed step and each reverse step is one CUDA graph
+ * launch (captured on first use). */
+mlsdc_status mlsdc_adjoint_backward(mlsdc_adjoint_t adj, const double* lambda_T, double* lambda_0, int use_graph,
+                                    void* stream);
+/* Kernel launches of one forward step and of one reverse step (reporting). */
+mlsdc_status mlsdc_adjoint_launch_count(mlsdc_adjoint_t adj, int64_t* forward_step, int64_t* reverse_step);
 
 /* Device check that a state (n doubles) is finite: writes 1 to *ok_host if
  * every value is finite, else 0 (synchronises the stream). */

@@ -14,22 +14,10 @@
 #include <vector>
 
 #include "internal.h"
+#include "sdc_internal.h"
 
 namespace mlsdc {
 
-constexpr int kMaxNodes = 9;
-
-struct Phys {
-    double inv_a2, phibar, nu;
-};
-
-// Row m+1 of the SDC matrices for one node update.
-struct NodeRow {
-    double qe[kMaxNodes], qi[kMaxNodes], q[kMaxNodes];
-    double qimm;
-    int m;    // updating node m+1
-    int M;    // nodes 0..M
-};
 
 __device__ __forceinline__ double2 cax(double2 acc, double s, double2 x) {
     return make_double2(fma(s, x.x, acc.x), fma(s, x.y, acc.y));
@@ -159,12 +147,9 @@ __global__ void k_broadcast(const double2* __restrict__ src, double2* __restrict
     }
 }
 
+
 // Restriction (Eqs. two_step_restriction, time_restriction, space_restriction):
 // Theta_c[i] = D( sum_j Pi^c_f[i][j] Theta_f[j] ) for i in [i0, i1).
-struct TransferMat {
-    double a[kMaxNodes * kMaxNodes];
-};
-
 __global__ void k_restrict(const double2* __restrict__ Tf, double2* __restrict__ Tc, const int* __restrict__ c2f,
                            int ncf, int ncc, int nf_nodes, int i0, int i1, TransferMat Pcf, size_t msf, size_t msc) {
     Tf += blockIdx.y * msf;
@@ -181,12 +166,6 @@ __global__ void k_restrict(const double2* __restrict__ Tf, double2* __restrict__
     }
 }
 
-struct FasArgs {
-    double Qf[kMaxNodes * kMaxNodes];
-    double Qc[kMaxNodes * kMaxNodes];
-    double Pcf[kMaxNodes * kMaxNodes];
-    int nfn, ncn;
-};
 
 // tau_c = A_c(R Theta_f) - R A_f(Theta_f), A(Theta) = Theta - dt (Q x I) F
 // (Eq. tau_term_level_l+1 with tau_f = 0; Eq. collocation_problem).
@@ -366,29 +345,8 @@ static double lagrange(const std::vector<double>& t, int j, double s) {
 
 using namespace mlsdc;
 
-struct sdc_level_s {
-    sh_plan_t plan;
-    swe_params prm;
-    int n;        // nodes
-    int members;  // ensemble members advanced together
-    std::vector<double> t, Q, QE, QI;
-    double2* Th = nullptr;  // [members][n][3][nc]
-    double2* FI[2] = {nullptr, nullptr};
-    double2* FE[2] = {nullptr, nullptr};
-    int cur = 0;
-    int64_t launches = 0;
-    size_t node() const { return (size_t)3 * plan->nc; }
-    size_t ms() const { return (size_t)n * node(); }  // member stride of node arrays
-};
 
 namespace mlsdc {
-
-static Phys phys_of(const swe_params& p) { return Phys{1.0 / (p.a * p.a), p.phibar, p.nu}; }
-
-static int grid_for(int n) {
-    int b = (n + 255) / 256;
-    return std::max(1, std::min(b, 152 * 8));
-}
 
 // F_E at one node of every member: x and FE point at that node of member 0.
 static mlsdc_status eval_FE(sdc_level_t L, const double2* x, double2* FE, cudaStream_t st) {
@@ -409,29 +367,48 @@ static mlsdc_status eval_FI(sdc_level_t L, const double2* x, double2* FI, cudaSt
     return MLSDC_OK;
 }
 
+static NodeRow node_row(sdc_level_t L, int m) {
+    const int n = L->n;
+    NodeRow row;
+    std::memset(&row, 0, sizeof(row));
+    row.m = m;
+    row.M = n - 1;
+    for (int j = 0; j < n; ++j) {
+        row.qe[j] = L->QE[(m + 1) * n + j];
+        row.qi[j] = L->QI[(m + 1) * n + j];
+        row.q[j] = L->Q[(m + 1) * n + j];
+    }
+    row.qimm = L->QI[(m + 1) * n + m + 1];
+    return row;
+}
+
+static mlsdc_status launch_node(sdc_level_t L, double dt, const NodeRow& row, double2* Th, const double2* FIo,
+                                const double2* FEo, double2* FIn, double2* FEn, const double2* tau,
+                                cudaStream_t st) {
+    const int nc = L->plan->nc;
+    k_sweep_node<<<dim3(grid_for(nc), L->members), 256, 0, st>>>(Th, FIo, FEo, FIn, FEn, tau, L->plan->d_ndeg, nc,
+                                                                 dt, row, phys_of(L->prm), L->ms());
+    MLSDC_LAUNCHED("k_sweep_node");
+    L->launches++;
+    return MLSDC_OK;
+}
+
+static mlsdc_status launch_bcast(sdc_level_t L, const double2* src, double2* dst, int n3, int count, size_t ms_src,
+                                 size_t ms_dst, cudaStream_t st) {
+    k_broadcast<<<dim3(grid_for(n3), L->members), 256, 0, st>>>(src, dst, n3, count, ms_src, ms_dst);
+    MLSDC_LAUNCHED("k_broadcast");
+    L->launches++;
+    return MLSDC_OK;
+}
+
 // One sweep on explicit buffers ([members][n][3][nc] each).
 static mlsdc_status sweep(sdc_level_t L, double dt, double2* Th, const double2* FIo, const double2* FEo,
                           double2* FIn, double2* FEn, const double2* tau, cudaStream_t st) {
-    const int nc = L->plan->nc;
-    const int n = L->n;
     const size_t node = L->node();
-    Phys ph = phys_of(L->prm);
-    for (int m = 0; m < n - 1; ++m) {
-        NodeRow row;
-        std::memset(&row, 0, sizeof(row));
-        row.m = m;
-        row.M = n - 1;
-        for (int j = 0; j < n; ++j) {
-            row.qe[j] = L->QE[(m + 1) * n + j];
-            row.qi[j] = L->QI[(m + 1) * n + j];
-            row.q[j] = L->Q[(m + 1) * n + j];
-        }
-        row.qimm = L->QI[(m + 1) * n + m + 1];
-        k_sweep_node<<<dim3(grid_for(nc), L->members), 256, 0, st>>>(Th, FIo, FEo, FIn, FEn, tau, L->plan->d_ndeg, nc,
-                                                                     dt, row, ph, L->ms());
-        MLSDC_LAUNCHED("k_sweep_node");
-        L->launches++;
-        mlsdc_status s = eval_FE(L, Th + (m + 1) * node, FEn + (m + 1) * node, st);
+    for (int m = 0; m < L->n - 1; ++m) {
+        mlsdc_status s = launch_node(L, dt, node_row(L, m), Th, FIo, FEo, FIn, FEn, tau, st);
+        if (s != MLSDC_OK) return s;
+        s = eval_FE(L, Th + (m + 1) * node, FEn + (m + 1) * node, st);
         if (s != MLSDC_OK) return s;
     }
     return MLSDC_OK;
@@ -441,19 +418,13 @@ static mlsdc_status sweep(sdc_level_t L, double dt, double2* Th, const double2* 
 // evaluated once and spread.
 static mlsdc_status spread(sdc_level_t L, const double2* state, cudaStream_t st) {
     const int n3 = (int)L->node();
-    const dim3 g(grid_for(n3), L->members);
-    k_broadcast<<<g, 256, 0, st>>>(state, L->Th, n3, L->n, (size_t)n3, L->ms());
-    MLSDC_LAUNCHED("k_broadcast");
-    L->launches++;
     mlsdc_status s;
+    if ((s = launch_bcast(L, state, L->Th, n3, L->n, (size_t)n3, L->ms(), st)) != MLSDC_OK) return s;
     if ((s = eval_FI(L, L->Th, L->FI[L->cur], st)) != MLSDC_OK) return s;
     if ((s = eval_FE(L, L->Th, L->FE[L->cur], st)) != MLSDC_OK) return s;
-    k_broadcast<<<g, 256, 0, st>>>(L->FI[L->cur], L->FI[L->cur] + n3, n3, L->n - 1, L->ms(), L->ms());
-    MLSDC_LAUNCHED("k_broadcast");
-    k_broadcast<<<g, 256, 0, st>>>(L->FE[L->cur], L->FE[L->cur] + n3, n3, L->n - 1, L->ms(), L->ms());
-    MLSDC_LAUNCHED("k_broadcast");
-    L->launches += 2;
-    return MLSDC_OK;
+    if ((s = launch_bcast(L, L->FI[L->cur], L->FI[L->cur] + n3, n3, L->n - 1, L->ms(), L->ms(), st)) != MLSDC_OK)
+        return s;
+    return launch_bcast(L, L->FE[L->cur], L->FE[L->cur] + n3, n3, L->n - 1, L->ms(), L->ms(), st);
 }
 
 // The last node of every member into state [members][3][nc].
@@ -474,15 +445,6 @@ mlsdc_status implicit_rhs_launch(sh_plan_t p, const swe_params* prm, const doubl
 
 }  // namespace mlsdc
 
-struct mlsdc_s {
-    sdc_level_t f, c;
-    TransferMat Pcf, Pfc;
-    int* d_c2f = nullptr;
-    double2 *Ts = nullptr, *FIs = nullptr, *FEs = nullptr, *tau = nullptr;
-    cudaStream_t cap = nullptr;
-    std::map<std::tuple<double*, double, int, int>, cudaGraphExec_t> graphs;
-    int64_t launches = 0;
-};
 
 struct mlsdc_ensemble_s {
     std::vector<mlsdc_t> groups;
@@ -683,24 +645,135 @@ extern "C" mlsdc_status mlsdc_destroy(mlsdc_t ml) {
 
 namespace mlsdc {
 
-static mlsdc_status mlsdc_enqueue(mlsdc_t ml, double* state, double dt, int n_iter, int n_c, cudaStream_t st) {
+// The schedule of one MLSDC step (Sec. 4.3.2 initialisation, then Algorithm 1
+// steps A-D per iteration) as a list of operations.
+size_t build_mlsdc_ops(mlsdc_t ml, double2* state, double dt, int n_iter, int n_c, std::vector<Op>& ops) {
     sdc_level_t F = ml->f, C = ml->c;
-    const int ncf = F->plan->nc, ncc = C->plan->nc;
-    const size_t nodec = C->node();
+    const size_t nodef = F->node(), nodec = C->node();
     const int nfn = F->n, ncn = C->n;
     const int B = F->members;
+    size_t tape = 0;
+    ops.clear();
+    auto bcast = [&](sdc_level_t L, const double2* src, double2* dst, int count, size_t ms_src) {
+        Op o{OpK::Bcast};
+        o.L = L;
+        o.p[0] = const_cast<double2*>(src);
+        o.p[1] = dst;
+        o.n3 = (int)L->node();
+        o.count = count;
+        o.ms_src = ms_src;
+        o.ms_dst = L->ms();
+        ops.push_back(o);
+    };
+    auto fi = [&](sdc_level_t L, double2* x, double2* f) {
+        Op o{OpK::FI};
+        o.L = L;
+        o.p[0] = x;
+        o.p[1] = f;
+        ops.push_back(o);
+    };
+    auto fe = [&](sdc_level_t L, double2* x, double2* f) {
+        Op o{OpK::FE};
+        o.L = L;
+        o.p[0] = x;
+        o.p[1] = f;
+        o.tape_off = tape;
+        tape += (size_t)L->members * L->node();
+        ops.push_back(o);
+    };
+    auto sweep_ops = [&](sdc_level_t L, double2* FIo, double2* FEo, double2* FIn, double2* FEn, double2* tau) {
+        for (int m = 0; m < L->n - 1; ++m) {
+            Op o{OpK::Node};
+            o.L = L;
+            o.p[0] = L->Th;
+            o.p[1] = FIo;
+            o.p[2] = FEo;
+            o.p[3] = FIn;
+            o.p[4] = FEn;
+            o.p[5] = tau;
+            o.dt = dt;
+            o.row = node_row(L, m);
+            ops.push_back(o);
+            fe(L, L->Th + (m + 1) * L->node(), FEn + (m + 1) * L->node());
+        }
+    };
+    auto restrict_ops = [&](int i0, int i1) {
+        Op o{OpK::Restrict};
+        o.L = C;
+        o.p[0] = F->Th;
+        o.p[1] = C->Th;
+        o.i0 = i0;
+        o.i1 = i1;
+        ops.push_back(o);
+    };
+    auto copy = [&](double2* dst, const double2* src, size_t bytes) {
+        Op o{OpK::Copy};
+        o.L = C;
+        o.p[0] = const_cast<double2*>(src);
+        o.p[1] = dst;
+        o.bytes = bytes;
+        ops.push_back(o);
+    };
+    int cf = F->cur, cc = C->cur;
+    // initialisation: fine spread; coarse node 0 = restriction of Theta^n, evaluated once
+    bcast(F, state, F->Th, nfn, nodef);
+    fi(F, F->Th, F->FI[cf]);
+    fe(F, F->Th, F->FE[cf]);
+    bcast(F, F->FI[cf], F->FI[cf] + nodef, nfn - 1, F->ms());
+    bcast(F, F->FE[cf], F->FE[cf] + nodef, nfn - 1, F->ms());
+    restrict_ops(0, 1);
+    fi(C, C->Th, C->FI[cc]);
+    fe(C, C->Th, C->FE[cc]);
+    for (int it = 0; it < n_iter; ++it) {
+        // A) fine sweep
+        sweep_ops(F, F->FI[cf], F->FE[cf], F->FI[1 - cf], F->FE[1 - cf], nullptr);
+        cf = 1 - cf;
+        // B) restrict nodes 1..Mc, evaluate, save
+        restrict_ops(1, ncn);
+        for (int i = 1; i < ncn; ++i) {
+            fi(C, C->Th + i * nodec, C->FI[cc] + i * nodec);
+            fe(C, C->Th + i * nodec, C->FE[cc] + i * nodec);
+        }
+        const size_t bytes = (size_t)B * C->ms() * sizeof(double2);
+        copy(ml->Ts, C->Th, bytes);
+        copy(ml->FIs, C->FI[cc], bytes);
+        copy(ml->FEs, C->FE[cc], bytes);
+        // C) FAS correction, coarse sweeps
+        Op fa{OpK::Fas};
+        fa.L = C;
+        double2* fas[7] = {F->Th, F->FI[cf], F->FE[cf], C->Th, C->FI[cc], C->FE[cc], ml->tau};
+        std::copy(fas, fas + 7, fa.p);
+        fa.dt = dt;
+        ops.push_back(fa);
+        for (int k = 0; k < n_c; ++k) {
+            sweep_ops(C, C->FI[cc], C->FE[cc], C->FI[1 - cc], C->FE[1 - cc], ml->tau);
+            cc = 1 - cc;
+        }
+        // D) interpolate the coarse corrections to fine nodes 1..Mf
+        Op ip{OpK::Interp};
+        ip.L = C;
+        double2* ipp[9] = {F->Th, F->FI[cf], F->FE[cf], C->Th, C->FI[cc], C->FE[cc], ml->Ts, ml->FIs, ml->FEs};
+        std::copy(ipp, ipp + 9, ip.p);
+        ops.push_back(ip);
+    }
+    Op last{OpK::CopyLast};
+    last.L = F;
+    last.p[0] = F->Th + (nfn - 1) * nodef;
+    last.p[1] = state;
+    ops.push_back(last);
+    F->cur = cf;
+    C->cur = cc;
+    return tape;
+}
+
+mlsdc_status run_ops(mlsdc_t ml, const std::vector<Op>& ops, cudaStream_t st, int64_t* launches, double2* tape) {
+    sdc_level_t F = ml->f, C = ml->c;
+    const int ncf = F->plan->nc, ncc = C->plan->nc;
+    const int nfn = F->n, ncn = C->n;
     const size_t msf = F->ms(), msc = C->ms();
-    const dim3 gt(grid_for(3 * ncc), B);
+    const dim3 gt(grid_for(3 * ncc), F->members);
     F->launches = C->launches = 0;
     int64_t own = 0;
-    mlsdc_status s;
-    // initialisation: fine spread; coarse node 0 = restriction of Theta^n, evaluated once
-    if ((s = spread(F, (const double2*)state, st)) != MLSDC_OK) return s;
-    k_restrict<<<gt, 256, 0, st>>>(F->Th, C->Th, ml->d_c2f, ncf, ncc, nfn, 0, 1, ml->Pcf, msf, msc);
-    MLSDC_LAUNCHED("k_restrict");
-    own++;
-    if ((s = eval_FI(C, C->Th, C->FI[C->cur], st)) != MLSDC_OK) return s;
-    if ((s = eval_FE(C, C->Th, C->FE[C->cur], st)) != MLSDC_OK) return s;
     FasArgs fa;
     std::memset(&fa, 0, sizeof(fa));
     fa.nfn = nfn;
@@ -708,47 +781,64 @@ static mlsdc_status mlsdc_enqueue(mlsdc_t ml, double* state, double dt, int n_it
     for (int i = 0; i < nfn * nfn; ++i) fa.Qf[i] = F->Q[i];
     for (int i = 0; i < ncn * ncn; ++i) fa.Qc[i] = C->Q[i];
     for (int i = 0; i < ncn * nfn; ++i) fa.Pcf[i] = ml->Pcf.a[i];
-    for (int it = 0; it < n_iter; ++it) {
-        // A) fine sweep
-        int cf = F->cur;
-        if ((s = sweep(F, dt, F->Th, F->FI[cf], F->FE[cf], F->FI[1 - cf], F->FE[1 - cf], nullptr, st)) != MLSDC_OK)
-            return s;
-        F->cur = cf = 1 - cf;
-        // B) restrict nodes 1..Mc, evaluate, save
-        k_restrict<<<gt, 256, 0, st>>>(F->Th, C->Th, ml->d_c2f, ncf, ncc, nfn, 1, ncn, ml->Pcf, msf, msc);
-        MLSDC_LAUNCHED("k_restrict");
-        own++;
-        int cc = C->cur;
-        for (int i = 1; i < ncn; ++i) {
-            if ((s = eval_FI(C, C->Th + i * nodec, C->FI[cc] + i * nodec, st)) != MLSDC_OK) return s;
-            if ((s = eval_FE(C, C->Th + i * nodec, C->FE[cc] + i * nodec, st)) != MLSDC_OK) return s;
+    mlsdc_status s = MLSDC_OK;
+    for (const Op& o : ops) {
+        switch (o.k) {
+            case OpK::Bcast:
+                s = launch_bcast(o.L, o.p[0], o.p[1], o.n3, o.count, o.ms_src, o.ms_dst, st);
+                break;
+            case OpK::FI:
+                s = eval_FI(o.L, o.p[0], o.p[1], st);
+                break;
+            case OpK::FE:
+                if (tape) {
+                    const size_t w = o.L->node() * sizeof(double2);
+                    MLSDC_CUDA(cudaMemcpy2DAsync(tape + o.tape_off, w, o.p[0], o.L->ms() * sizeof(double2), w,
+                                                 (size_t)o.L->members, cudaMemcpyDeviceToDevice, st));
+                }
+                s = eval_FE(o.L, o.p[0], o.p[1], st);
+                break;
+            case OpK::Node:
+                s = launch_node(o.L, o.dt, o.row, o.p[0], o.p[1], o.p[2], o.p[3], o.p[4], o.p[5], st);
+                break;
+            case OpK::Restrict:
+                k_restrict<<<gt, 256, 0, st>>>(o.p[0], o.p[1], ml->d_c2f, ncf, ncc, nfn, o.i0, o.i1, ml->Pcf, msf,
+                                               msc);
+                MLSDC_LAUNCHED("k_restrict");
+                own++;
+                break;
+            case OpK::Copy:
+                MLSDC_CUDA(cudaMemcpyAsync(o.p[1], o.p[0], o.bytes, cudaMemcpyDeviceToDevice, st));
+                break;
+            case OpK::Fas:
+                k_fas_tau<<<gt, 256, 0, st>>>(o.p[0], o.p[1], o.p[2], o.p[3], o.p[4], o.p[5], o.p[6], ml->d_c2f,
+                                              ncf, ncc, o.dt, fa, msf, msc);
+                MLSDC_LAUNCHED("k_fas_tau");
+                own++;
+                break;
+            case OpK::Interp:
+                k_interp<<<gt, 256, 0, st>>>(o.p[0], o.p[1], o.p[2], o.p[3], o.p[4], o.p[5], o.p[6], o.p[7], o.p[8],
+                                             ml->d_c2f, ncf, ncc, nfn, ncn, ml->Pfc, msf, msc);
+                MLSDC_LAUNCHED("k_interp");
+                own++;
+                break;
+            case OpK::CopyLast: {
+                const size_t w = o.L->node() * sizeof(double2);
+                MLSDC_CUDA(cudaMemcpy2DAsync(o.p[1], w, o.p[0], o.L->ms() * sizeof(double2), w,
+                                             (size_t)o.L->members, cudaMemcpyDeviceToDevice, st));
+                break;
+            }
         }
-        const size_t bytes = (size_t)B * msc * sizeof(double2);
-        MLSDC_CUDA(cudaMemcpyAsync(ml->Ts, C->Th, bytes, cudaMemcpyDeviceToDevice, st));
-        MLSDC_CUDA(cudaMemcpyAsync(ml->FIs, C->FI[cc], bytes, cudaMemcpyDeviceToDevice, st));
-        MLSDC_CUDA(cudaMemcpyAsync(ml->FEs, C->FE[cc], bytes, cudaMemcpyDeviceToDevice, st));
-        // C) FAS correction, coarse sweeps
-        k_fas_tau<<<gt, 256, 0, st>>>(F->Th, F->FI[cf], F->FE[cf], C->Th, C->FI[cc], C->FE[cc], ml->tau, ml->d_c2f,
-                                      ncf, ncc, dt, fa, msf, msc);
-        MLSDC_LAUNCHED("k_fas_tau");
-        own++;
-        for (int k = 0; k < n_c; ++k) {
-            cc = C->cur;
-            if ((s = sweep(C, dt, C->Th, C->FI[cc], C->FE[cc], C->FI[1 - cc], C->FE[1 - cc], ml->tau, st)) !=
-                MLSDC_OK)
-                return s;
-            C->cur = 1 - cc;
-        }
-        cc = C->cur;
-        // D) interpolate the coarse corrections to fine nodes 1..Mf
-        k_interp<<<gt, 256, 0, st>>>(F->Th, F->FI[cf], F->FE[cf], C->Th, C->FI[cc], C->FE[cc], ml->Ts, ml->FIs,
-                                     ml->FEs, ml->d_c2f, ncf, ncc, nfn, ncn, ml->Pfc, msf, msc);
-        MLSDC_LAUNCHED("k_interp");
-        own++;
+        if (s != MLSDC_OK) return s;
     }
-    if ((s = copy_last_node(F, state, st)) != MLSDC_OK) return s;
-    ml->launches = own + F->launches + C->launches;
+    if (launches) *launches = own + F->launches + C->launches;
     return MLSDC_OK;
+}
+
+static mlsdc_status mlsdc_enqueue(mlsdc_t ml, double* state, double dt, int n_iter, int n_c, cudaStream_t st) {
+    std::vector<Op> ops;
+    build_mlsdc_ops(ml, (double2*)state, dt, n_iter, n_c, ops);
+    return run_ops(ml, ops, st, &ml->launches, nullptr);
 }
 
 // Capture `enqueue(stream)` once into an executable graph.

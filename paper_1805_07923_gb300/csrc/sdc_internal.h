@@ -1,0 +1,117 @@
+// Internal declarations of the time-stepping part of the library (SDC levels,
+// two-level MLSDC, the step's operation list), shared by the forward step
+// (sdc.cu) and its adjoint (adjoint.cu).  Not part of the ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <map>
+#include <tuple>
+#include <vector>
+
+#include "internal.h"
+
+namespace mlsdc {
+
+constexpr int kMaxNodes = 9;
+
+struct Phys {
+    double inv_a2, phibar, nu;
+};
+
+// Row m+1 of the SDC matrices for one node update.
+struct NodeRow {
+    double qe[kMaxNodes], qi[kMaxNodes], q[kMaxNodes];
+    double qimm;
+    int m;    // updating node m+1
+    int M;    // nodes 0..M
+};
+
+// Time interpolation matrix between two node sets (Sec. 4.3.3).
+struct TransferMat {
+    double a[kMaxNodes * kMaxNodes];
+};
+
+struct FasArgs {
+    double Qf[kMaxNodes * kMaxNodes];
+    double Qc[kMaxNodes * kMaxNodes];
+    double Pcf[kMaxNodes * kMaxNodes];
+    int nfn, ncn;
+};
+
+// One operation of an MLSDC step.  A step is a fixed, straight-line list of
+// these (built on the host from the schedule of Algorithm 1), run in order
+// by the forward step and walked backwards by the adjoint.  Every operation
+// except FE is linear in its operands with constant coefficients.
+enum class OpK : int {
+    Bcast,     // p[1][k] = p[0] for k < count                (node broadcast, spread)
+    FI,        // p[1] = F_I(p[0])                              (one node, every member)
+    FE,        // p[1] = F_E(p[0])
+    Node,      // k_sweep_node: node m+1 update, solve, F_I     (p: Th FIo FEo FIn FEn tau)
+    Restrict,  // coarse p[1][i] = D(sum_j Pcf[i][j] p[0][j]), i in [i0, i1)
+    Copy,      // p[1] = p[0], `bytes` bytes
+    Fas,       // tau (p[6]) from fine (p[0..2]) and coarse (p[3..5]) nodes
+    Interp,    // fine p[0..2] += P(Pfc (coarse p[3..5] - saved p[6..8]))
+    CopyLast,  // p[1] (the state) = last fine node p[0], every member
+};
+
+struct Op {
+    OpK k;
+    sdc_level_t L = nullptr;         // the level the operation runs on
+    double2* p[9] = {};              // operands, by kind (above)
+    int n3 = 0, count = 0;           // Bcast
+    size_t ms_src = 0, ms_dst = 0;   // Bcast member strides
+    int i0 = 0, i1 = 0;              // Restrict
+    size_t bytes = 0;                // Copy
+    double dt = 0.0;                 // Node, Fas
+    NodeRow row{};                   // Node
+    size_t tape_off = 0;             // FE: offset of its linearisation point in a step's tape (complex)
+};
+
+inline Phys phys_of(const swe_params& p) { return Phys{1.0 / (p.a * p.a), p.phibar, p.nu}; }
+
+inline int grid_for(int n) {
+    int b = (n + 255) / 256;
+    return b < 1 ? 1 : (b > 152 * 8 ? 152 * 8 : b);
+}
+
+}  // namespace mlsdc
+
+struct sdc_level_s {
+    sh_plan_t plan;
+    swe_params prm;
+    int n;        // nodes
+    int members;  // ensemble members advanced together
+    std::vector<double> t, Q, QE, QI;
+    double2* Th = nullptr;  // [members][n][3][nc]
+    double2* FI[2] = {nullptr, nullptr};
+    double2* FE[2] = {nullptr, nullptr};
+    int cur = 0;
+    int64_t launches = 0;
+    size_t node() const { return (size_t)3 * plan->nc; }
+    size_t ms() const { return (size_t)n * node(); }  // member stride of node arrays
+};
+
+struct mlsdc_s {
+    sdc_level_t f, c;
+    mlsdc::TransferMat Pcf, Pfc;
+    int* d_c2f = nullptr;
+    double2 *Ts = nullptr, *FIs = nullptr, *FEs = nullptr, *tau = nullptr;
+    cudaStream_t cap = nullptr;
+    std::map<std::tuple<double*, double, int, int>, cudaGraphExec_t> graphs;
+    int64_t launches = 0;
+};
+
+namespace mlsdc {
+
+// The operations of one MLSDC step on `state` (Algorithm 1, n_iter
+// iterations of one fine and n_c coarse sweeps), starting from the levels'
+// current buffer parities, which it advances as the step will.  Returns the
+// number of complex values one step's F_E linearisation points take.
+size_t build_mlsdc_ops(mlsdc_t ml, double2* state, double dt, int n_iter, int n_c, std::vector<Op>& ops);
+
+// Launch the operations in order on `st`.  With `tape`, each FE operation
+// first copies its input to tape + tape_off.
+mlsdc_status run_ops(mlsdc_t ml, const std::vector<Op>& ops, cudaStream_t st, int64_t* launches, double2* tape);
+
+}  // namespace mlsdc

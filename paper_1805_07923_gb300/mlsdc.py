@@ -66,6 +66,13 @@ _SIGS = {
     "mlsdc_profile_rhs": ([_VP, ctypes.POINTER(SweParams), _DP, _DP, _I, ctypes.POINTER(ctypes.c_float), _VP], _I),
     "mlsdc_profile_rhs_batched": ([_VP, ctypes.POINTER(SweParams), _DP, _DP, _I, _I, ctypes.POINTER(ctypes.c_float),
                                    _VP], _I),
+    "swe_explicit_rhs_adjoint": ([_VP, ctypes.POINTER(SweParams), _DP, _DP, _DP, _VP], _I),
+    "mlsdc_phi_misfit": ([_VP, _DP, _DP, _DP, _DP, _VP], _I),
+    "mlsdc_adjoint_create": ([_VP, _I, _I, _D, _I, _I, ctypes.POINTER(_VP)], _I),
+    "mlsdc_adjoint_destroy": ([_VP], _I),
+    "mlsdc_adjoint_forward": ([_VP, _DP, _DP, _I, _VP], _I),
+    "mlsdc_adjoint_backward": ([_VP, _DP, _DP, _I, _VP], _I),
+    "mlsdc_adjoint_launch_count": ([_VP, ctypes.POINTER(_I64), ctypes.POINTER(_I64)], _I),
 }
 
 
@@ -341,3 +348,85 @@ def mlsdc_ensemble_step(ens: Ensemble, states: list[torch.Tensor], dt: float, n_
     arr = (ctypes.c_void_p * len(ptrs))(*[p.value for p in ptrs])
     _check(lib().mlsdc_ensemble_step(ens.h, arr, float(dt), int(n_iter), int(n_coarse_sweeps), 1 if use_graph else 0,
                                      _stream(stream)), "mlsdc_ensemble_step")
+
+
+# ---------------------------------------------------------------------------
+# adjoint (reverse mode with respect to the initial state)
+
+
+def swe_explicit_rhs_adjoint(plan: Plan, prm: SweParams, state: torch.Tensor, lam: torch.Tensor,
+                             state_bar: torch.Tensor, stream=None):
+    """state_bar += F_E'(state)^t lam; lam is zeroed (consumed)."""
+    n = 6 * plan.nc
+    _check(lib().swe_explicit_rhs_adjoint(plan.h, ctypes.byref(prm), _ptr(state, n), _ptr(lam, n), _ptr(state_bar, n),
+                                          _stream(stream)), "swe_explicit_rhs_adjoint")
+
+
+def mlsdc_phi_misfit(plan: Plan, state: torch.Tensor, phi_target: torch.Tensor, J: torch.Tensor, lam: torch.Tensor,
+                     stream=None):
+    """J[0] = 1/2 ||Phi'(state) - phi_target||^2 (Parseval) and lam = dJ/dstate, on the device."""
+    _check(lib().mlsdc_phi_misfit(plan.h, _ptr(state, 6 * plan.nc), _ptr(phi_target, 2 * plan.nc), _ptr(J, 1),
+                                  _ptr(lam, 6 * plan.nc), _stream(stream)), "mlsdc_phi_misfit")
+
+
+class Adjoint:
+    """mlsdc_adjoint: n_steps MLSDC steps and their reverse mode, with a
+    checkpoint every `checkpoint_every` steps."""
+
+    def __init__(self, ml: MLSDC, n_steps: int, checkpoint_every: int, dt: float, n_iter: int, n_coarse_sweeps: int,
+                 use_graph: bool = True):
+        self.ml = ml
+        self.nc = ml.fine.plan.nc
+        self.use_graph = 1 if use_graph else 0
+        h = ctypes.c_void_p()
+        _check(lib().mlsdc_adjoint_create(ml.h, int(n_steps), int(checkpoint_every), float(dt), int(n_iter),
+                                          int(n_coarse_sweeps), ctypes.byref(h)), "mlsdc_adjoint_create")
+        self.h = h
+
+    def close(self):
+        if self.h:
+            lib().mlsdc_adjoint_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def forward(self, state0: torch.Tensor, state_T: torch.Tensor, stream=None):
+        n = 6 * self.nc
+        _check(lib().mlsdc_adjoint_forward(self.h, _ptr(state0, n), _ptr(state_T, n), self.use_graph,
+                                           _stream(stream)), "mlsdc_adjoint_forward")
+
+    def backward(self, lam_T: torch.Tensor, lam_0: torch.Tensor, stream=None):
+        n = 6 * self.nc
+        _check(lib().mlsdc_adjoint_backward(self.h, _ptr(lam_T, n), _ptr(lam_0, n), self.use_graph,
+                                            _stream(stream)), "mlsdc_adjoint_backward")
+
+    def launch_counts(self) -> tuple[int, int]:
+        a, b = ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().mlsdc_adjoint_launch_count(self.h, ctypes.byref(a), ctypes.byref(b)), "mlsdc_adjoint_launch_count")
+        return a.value, b.value
+
+
+class MLSDCFunction(torch.autograd.Function):
+    """state_T = (n_steps MLSDC steps)(state0) with the library's hand-written
+    adjoint as its backward: MLSDCFunction.apply(state0, adjoint) for a
+    complex128 [3][N_c] CUDA tensor; gradients follow PyTorch's complex
+    convention (dL/dRe + i dL/dIm), Im of m = 0 excluded."""
+
+    @staticmethod
+    def forward(ctx, state0: torch.Tensor, adj: Adjoint):
+        x0 = state0.detach().contiguous()
+        out = torch.empty_like(x0)
+        adj.forward(x0, out)
+        ctx.adj = adj
+        return out
+
+    @staticmethod
+    def backward(ctx, grad_out: torch.Tensor):
+        g = grad_out.detach().contiguous().clone()
+        out = torch.empty_like(g)
+        ctx.adj.backward(g, out)
+        return out, None
