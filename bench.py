@@ -337,6 +337,169 @@ def run_ensemble(args):
     print(json.dumps(line), flush=True)
 
 
+ADJOINT = dict(Rf=85, If=256, Jf=128, Rc=42, Ic=128, Jc=64, nf=5, nc=3, n_iter=4, n_coarse=2, dt=300.0,
+               n_steps=48, every=8)
+ADJOINT_NAME = ("gradient of J = 1/2 ||Phi'(T) - Phi_t||^2 w.r.t. the initial state: 48 steps of MLSDC(5,3) "
+                "T85 256x128 / T42 128x64, 4 iterations 1 fine + 2 coarse sweeps, dt 300 s, checkpoint every 8 "
+                "steps; forward, checkpointed recompute and reverse sweep, float64")
+
+
+def run_adjoint(args):
+    """One gradient evaluation per timed iteration: forward with checkpoints,
+    misfit and its seed, then the checkpointed reverse pass."""
+    import numpy as np
+    import torch
+
+    from paper_1805_07923_gb300 import inputs
+    from paper_1805_07923_gb300 import mlsdc as M
+    dev = torch.device("cuda", 0)
+    a = ADJOINT
+    stream = torch.cuda.current_stream()
+    pf, pc = M.Plan(a["Rf"], a["If"], a["Jf"]), M.Plan(a["Rc"], a["Ic"], a["Jc"])
+    lf, lc = M.Level(pf, a["nf"]), M.Level(pc, a["nc"])
+    ml = M.MLSDC(lf, lc)
+    adj = M.Adjoint(ml, a["n_steps"], a["every"], a["dt"], a["n_iter"], a["n_coarse"])
+    x0_h = inputs.initial_state(a["Rf"], seed=1805)
+    tgt_h = inputs.initial_state(a["Rf"], seed=1806)[0]
+    x0, tgt = torch.from_numpy(x0_h).to(dev), torch.from_numpy(np.ascontiguousarray(tgt_h)).to(dev)
+    xT, lam, g = torch.empty_like(x0), torch.empty_like(x0), torch.empty_like(x0)
+    J = torch.zeros(1, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def gradient():
+        adj.forward(x0, xT)
+        M.mlsdc_phi_misfit(pf, xT, tgt, J, lam)
+        adj.backward(lam, g)
+
+    def forward_only():
+        adj.forward(x0, xT)
+        M.mlsdc_phi_misfit(pf, xT, tgt, J, lam)
+
+    for _ in range(max(3, args.warmup)):
+        gradient()
+    torch.cuda.synchronize()
+    K = min(args.steps, 20)  # one gradient is ~3 x 48 MLSDC steps
+
+    def timed(fn, n):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+        torch.cuda.synchronize()
+        for k in range(n):
+            flush.zero_()
+            ev[k][0].record(stream)
+            fn()
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        return sum(x.elapsed_time(y) for x, y in ev) / n
+
+    clocks = ClockSampler(0)
+    clocks.start()
+    time.sleep(0.3)
+    grad_ms = timed(gradient, K)
+    fwd_ms = timed(forward_only, K)
+    clk = clocks.stop()
+    g_h = g.cpu().numpy()
+    J_h = float(J.cpu()[0])
+
+    # end to end through the public API with host buffers: initial state and
+    # target from pinned memory, gradient and J back, every iteration
+    hx, ht = torch.from_numpy(x0_h).pin_memory(), torch.from_numpy(np.ascontiguousarray(tgt_h)).pin_memory()
+    hg, hJ = torch.empty_like(hx).pin_memory(), torch.empty(1, dtype=torch.float64).pin_memory()
+    Ke = min(K, 20)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(Ke):
+        x0.copy_(hx, non_blocking=True)
+        tgt.copy_(ht, non_blocking=True)
+        gradient()
+        hg.copy_(g, non_blocking=True)
+        hJ.copy_(J, non_blocking=True)
+    e1.record(stream)
+    e1.synchronize()
+    e2e_s = e0.elapsed_time(e1) * 1e-3 / Ke
+
+    # finite differences of the GPU objective along 4 of the 16 seeded directions
+    def objective(x):
+        adj.forward(x, xT)
+        M.mlsdc_phi_misfit(pf, xT, tgt, J, lam)
+        return float(J.cpu()[0])
+
+    x0.copy_(torch.from_numpy(x0_h))
+    nx = float(np.sqrt(np.sum(np.abs(x0_h) ** 2)))
+    fd_err = 0.0
+    for i in range(4):
+        d = inputs.initial_state(a["Rf"], seed=2000 + i)
+        eps = 1e-6 * nx / float(np.sqrt(np.sum(np.abs(d) ** 2)))
+        Jp = objective(torch.from_numpy(x0_h + eps * d).to(dev))
+        Jm = objective(torch.from_numpy(x0_h - eps * d).to(dev))
+        gd = float(np.sum(np.real(np.conj(g_h) * d)))
+        fd_err = max(fd_err, abs((Jp - Jm) / (2 * eps) - gd) / abs(gd))
+    oracle_err = None
+    golden = os.path.join(ROOT, "tests", "golden", "adjoint_T85_T42_48.npz")
+    if os.path.exists(golden):
+        ref = np.load(golden)
+        oracle_err = float(np.sqrt(np.sum(np.abs(g_h - ref["grad"]) ** 2) / np.sum(np.abs(ref["grad"]) ** 2)))
+
+    # roofline of the dominant adjoint stage kernel (CUDA events on this stream)
+    fwd_stage = M.mlsdc_profile_rhs(pf, lf.prm, x0, torch.empty_like(x0), reps=50)
+    lam_r = torch.from_numpy(inputs.initial_state(a["Rf"], seed=7)).to(dev)
+    adj_stage = M.mlsdc_profile_rhs_adjoint(pf, lf.prm, x0, lam_r, torch.zeros_like(x0), reps=50)
+    R, I, Jl = a["Rf"], a["If"], a["Jf"]
+    nc_ = (R + 1) * (R + 2) // 2
+    flops = [26.0 * nc_ * Jl, 13 * Jl * 2.5 * I * math.log2(I), 12.0 * nc_ * Jl]
+    names = ["adjoint_legendre_sums (k_synth_ad)", "adjoint_fft_grid (k_grid_ad)", "adjoint_gaussian_sums (k_anal_ad)"]
+    top = max(range(3), key=lambda s: adj_stage[s])
+    achieved = flops[top] / (adj_stage[top] * 1e-3) / 1e12
+    peak = measured_fp64_tflops(torch, dev)
+    nfe, nce = evals_per_step(dict(nf=a["nf"], nc=a["nc"], n_iter=a["n_iter"], n_coarse=a["n_coarse"]))
+    line = {"metric": "adjoint gradient time (48-step MLSDC T85/T42, checkpoint every 8)", "value": grad_ms * 1e-3,
+            "unit": "s/gradient", "n_gpus": 1, "steps": K, "warmup": max(3, args.warmup), "ms_per_step": grad_ms,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": ADJOINT_NAME, "l2": "flushed between timed gradients (256 MB write)",
+                       "graph": "one CUDA graph per forward step and per reverse step"},
+            "forward_s": fwd_ms * 1e-3, "gradient_over_forward": grad_ms / fwd_ms,
+            "J": J_h, "fd_max_rel_err_4_dirs": fd_err, "bar_fd": 1e-5,
+            "oracle_grad_rel_l2": oracle_err, "bar_oracle": 1e-10,
+            "gpu_launches": None,
+            "e2e": {"value": e2e_s, "unit": "s/gradient", "h2d_bytes_per_step": int(hx.numel() * 16 + ht.numel() * 16),
+                    "d2h_bytes_per_step": int(hg.numel() * 16 + 8)},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None, "kernel": f"{names[top]} at T{R}",
+                         "kernel_ms": adj_stage[top], "peak_source": "measured cuBLAS DGEMM on this GPU (float64 pipe)"},
+            "stage_ms": {"forward": dict(zip(["legendre_synthesis", "grid_fft_products", "legendre_analysis"],
+                                             fwd_stage)), "adjoint": dict(zip(names, adj_stage))},
+            "clocks": clk}
+    fl, rl = adj.launch_counts()
+    n_ck = (a["n_steps"] + a["every"] - 1) // a["every"]
+    # forward: n_steps steps; backward: n_steps recomputed + n_steps reversed, plus misfit and projections
+    line["gpu_launches"] = (2 * a["n_steps"]) * fl + a["n_steps"] * rl + 3
+    line["config"]["evals_per_step"] = {"fine": nfe, "coarse": nce}
+    line["config"]["checkpoints"] = n_ck
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_adjoint()
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline_adjoint(n_sample: int = 2):
+    """The oracle's gradient over a bounded sample of the same workload (2 of
+    the 48 steps), scaled to the 48-step gradient."""
+    from oracle import adjoint as oad
+    from oracle import sdc as osdc
+    from oracle.swe import SWE, Params
+    from paper_1805_07923_gb300 import inputs
+    a = ADJOINT
+    fine = osdc.Level(SWE(a["Rf"], a["If"], a["Jf"], Params()), a["nf"])
+    coarse = osdc.Level(SWE(a["Rc"], a["Ic"], a["Jc"], Params()), a["nc"])
+    x0 = inputs.initial_state(a["Rf"], seed=1805)
+    tgt = inputs.initial_state(a["Rf"], seed=1806)[0]
+    t = time.perf_counter()
+    oad.gradient(fine, coarse, x0, tgt, a["dt"], n_sample, a["n_iter"], a["n_coarse"])
+    el = time.perf_counter() - t
+    return {"value": el * a["n_steps"] / n_sample, "unit": "s/gradient", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"oracle gradient over {n_sample} of the {a['n_steps']} steps ({el:.1f} s), scaled by "
+                      f"{a['n_steps'] // n_sample}"}
+
+
 def cpu_baseline(steps_cap_s: float = 25.0):
     """The float64 oracle as it stands, timed on this host for a bounded sample."""
     from oracle import sdc as osdc
@@ -399,13 +562,16 @@ def main():
                     help="Legendre/FFT arithmetic; bf16x3 (the fastest variant within 1e-6) by default")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="headline", choices=["headline", "ensemble"],
-                    help="headline: one T170/T85 member; ensemble: the 96-member uneven-truncation ensemble")
+    ap.add_argument("--workload", default="headline", choices=["headline", "ensemble", "adjoint"],
+                    help="headline: one T170/T85 member; ensemble: the 96-member uneven-truncation ensemble; "
+                         "adjoint: the 48-step T85/T42 gradient")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "ensemble":
         return run_ensemble(args)
+    if args.workload == "adjoint":
+        return run_adjoint(args)
     args.warmup = max(3, args.warmup)
 
     import numpy as np

@@ -318,6 +318,12 @@ mlsdc_status mlsdc_adjoint_forward(mlsdc_adjoint_t adj, const double* state0, do
  * launch (captured on first use). */
 mlsdc_status mlsdc_adjoint_backward(mlsdc_adjoint_t adj, const double* lambda_T, double* lambda_0, int use_graph,
                                     void* stream);
+/* Stage timing of swe_explicit_rhs_adjoint (as mlsdc_profile_rhs): mean ms
+ * per launch of [0] the Legendre sums of state and adjoint, [1] the FFT /
+ * grid-point transpose kernel, [2] the unweighted Gaussian sums.  lambda is
+ * consumed (zeroed) by the first evaluation; a measurement utility. */
+mlsdc_status mlsdc_profile_rhs_adjoint(sh_plan_t plan, const swe_params* prm, const double* state, double* lambda,
+                                       double* state_bar, int reps, float* ms_host, void* stream);
 /* Kernel launches of one forward step and of one reverse step (reporting). */
 mlsdc_status mlsdc_adjoint_launch_count(mlsdc_adjoint_t adj, int64_t* forward_step, int64_t* reverse_step);
 

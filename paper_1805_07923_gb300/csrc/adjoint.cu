@@ -886,6 +886,52 @@ extern "C" mlsdc_status swe_explicit_rhs_adjoint(sh_plan_t p, const swe_params* 
                       nullptr);
 }
 
+extern "C" mlsdc_status mlsdc_profile_rhs_adjoint(sh_plan_t p, const swe_params* prm, const double* state,
+                                                  double* lambda, double* state_bar, int reps, float* ms_host,
+                                                  void* stream) {
+    if (!p || !prm || !state || !lambda || !state_bar || reps < 1 || !ms_host) return MLSDC_ERR_INVALID;
+    if (p->precision != MLSDC_FP64 || state_bar == lambda || state_bar == state || lambda == state)
+        return MLSDC_ERR_INVALID;
+    cudaStream_t st = (cudaStream_t)stream;
+    mlsdc_status s = fe_adjoint_prepare(p);
+    if (s != MLSDC_OK) return s;
+    const int R = p->R;
+    const size_t ss = synth_ad_smem(R), gs = grid_ad_smem(p->I);
+    const double2* x = (const double2*)state;
+    double2* lam = (double2*)lambda;
+    double2* xb = (double2*)state_bar;
+    auto stage = [&](int k) -> mlsdc_status {
+        if (k == 0)
+            k_synth_ad<<<p->n_synth, 32 * kAdSynthWarps, ss, st>>>(x, lam, p->d_P, p->d_H, p->d_synth, R, p->J2,
+                                                                  p->nc, prm->a, p->d_four_in);
+        else if (k == 1)
+            k_grid_ad<<<p->J, 256, gs, st>>>(p->d_four_in, p->d_four_out, p->d_mu, p->d_w, p->d_tw, R, p->I,
+                                             p->logI, p->J, 2.0 * prm->omega);
+        else
+            k_anal_ad<<<p->n_anal, 32 * anal_warps(p->J2), 0, st>>>(p->d_four_out, p->d_P, p->d_H, p->d_anal, R,
+                                                                   p->J2, p->nc, prm->a, xb, lam);
+        MLSDC_LAUNCHED("profile_rhs_adjoint");
+        return MLSDC_OK;
+    };
+    // one full evaluation first so every stage reads valid inputs
+    if ((s = fe_adjoint(p, prm, x, lam, xb, st, nullptr)) != MLSDC_OK) return s;
+    cudaEvent_t e0, e1;
+    MLSDC_CUDA(cudaEventCreate(&e0));
+    MLSDC_CUDA(cudaEventCreate(&e1));
+    for (int k = 0; k < 3 && s == MLSDC_OK; ++k) {
+        MLSDC_CUDA(cudaEventRecord(e0, st));
+        for (int r = 0; r < reps && s == MLSDC_OK; ++r) s = stage(k);
+        MLSDC_CUDA(cudaEventRecord(e1, st));
+        MLSDC_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        MLSDC_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        ms_host[k] = ms / reps;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return s;
+}
+
 extern "C" mlsdc_status mlsdc_phi_misfit(sh_plan_t p, const double* state, const double* phi_target, double* J,
                                          double* lambda, void* stream) {
     if (!p || !state || !phi_target || !J || !lambda) return MLSDC_ERR_INVALID;

@@ -73,6 +73,8 @@ _SIGS = {
     "mlsdc_adjoint_forward": ([_VP, _DP, _DP, _I, _VP], _I),
     "mlsdc_adjoint_backward": ([_VP, _DP, _DP, _I, _VP], _I),
     "mlsdc_adjoint_launch_count": ([_VP, ctypes.POINTER(_I64), ctypes.POINTER(_I64)], _I),
+    "mlsdc_profile_rhs_adjoint": ([_VP, ctypes.POINTER(SweParams), _DP, _DP, _DP, _I, ctypes.POINTER(ctypes.c_float),
+                                   _VP], _I),
 }
 
 
@@ -367,6 +369,17 @@ def mlsdc_phi_misfit(plan: Plan, state: torch.Tensor, phi_target: torch.Tensor, 
     """J[0] = 1/2 ||Phi'(state) - phi_target||^2 (Parseval) and lam = dJ/dstate, on the device."""
     _check(lib().mlsdc_phi_misfit(plan.h, _ptr(state, 6 * plan.nc), _ptr(phi_target, 2 * plan.nc), _ptr(J, 1),
                                   _ptr(lam, 6 * plan.nc), _stream(stream)), "mlsdc_phi_misfit")
+
+
+def mlsdc_profile_rhs_adjoint(plan: Plan, prm: SweParams, state: torch.Tensor, lam: torch.Tensor,
+                              state_bar: torch.Tensor, reps: int = 50, stream=None) -> list[float]:
+    """Mean ms per launch of the three F_E-adjoint stage kernels."""
+    out = (ctypes.c_float * 3)()
+    n = 6 * plan.nc
+    _check(lib().mlsdc_profile_rhs_adjoint(plan.h, ctypes.byref(prm), _ptr(state, n), _ptr(lam, n),
+                                           _ptr(state_bar, n), int(reps), out, _stream(stream)),
+           "mlsdc_profile_rhs_adjoint")
+    return [float(v) for v in out]
 
 
 class Adjoint:
