@@ -212,7 +212,9 @@ def timed_steps(torch, M, ml, state, K, flush, stream) -> float:
 def build_mlsdc(M, prec):
     w = WORKLOAD
     pf = M.Plan(w["Rf"], w["If"], w["Jf"], prec)
-    pc = M.Plan(w["Rc"], w["Ic"], w["Jc"], prec)
+    # the coarse plan holds scratch for M_c states: step B's coarse evaluations
+    # run as one batched launch per stage
+    pc = M.Plan(w["Rc"], w["Ic"], w["Jc"], prec, w["nc"] - 1)
     lf, lc = M.Level(pf, w["nf"]), M.Level(pc, w["nc"])
     return M.MLSDC(lf, lc), (pf, pc, lf, lc)
 
@@ -355,7 +357,7 @@ def run_adjoint(args):
     dev = torch.device("cuda", 0)
     a = ADJOINT
     stream = torch.cuda.current_stream()
-    pf, pc = M.Plan(a["Rf"], a["If"], a["Jf"]), M.Plan(a["Rc"], a["Ic"], a["Jc"])
+    pf, pc = M.Plan(a["Rf"], a["If"], a["Jf"]), M.Plan(a["Rc"], a["Ic"], a["Jc"], "fp64", a["nc"] - 1)
     lf, lc = M.Level(pf, a["nf"]), M.Level(pc, a["nc"])
     ml = M.MLSDC(lf, lc)
     adj = M.Adjoint(ml, a["n_steps"], a["every"], a["dt"], a["n_iter"], a["n_coarse"])

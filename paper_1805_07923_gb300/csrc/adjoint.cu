@@ -631,17 +631,25 @@ mlsdc_status reverse_step(mlsdc_adjoint_t A, const double2* tape, cudaStream_t s
                 MLSDC_LAUNCHED("k_bcast_ad");
                 break;
             case OpK::FI:
-                k_fi_ad<<<grid_for(L->plan->nc), 256, 0, st>>>(adj_of(A, o.p[0]), adj_of(A, o.p[1]), L->plan->d_ndeg,
-                                                              L->plan->nc, phys_of(L->prm));
-                MLSDC_LAUNCHED("k_fi_ad");
-                break;
-            case OpK::FE: {
-                mlsdc_status s = fe_adjoint(L->plan, &L->prm, tape + o.tape_off, adj_of(A, o.p[1]),
-                                            adj_of(A, o.p[0]), st, &n);
-                if (s != MLSDC_OK) return s;
+                for (int k = 0; k < std::max(1, o.nodes); ++k) {
+                    const size_t sh = (size_t)k * L->node();
+                    k_fi_ad<<<grid_for(L->plan->nc), 256, 0, st>>>(adj_of(A, o.p[0]) + sh, adj_of(A, o.p[1]) + sh,
+                                                                  L->plan->d_ndeg, L->plan->nc, phys_of(L->prm));
+                    MLSDC_LAUNCHED("k_fi_ad");
+                    n++;
+                }
                 n--;  // counted below with the others
                 break;
-            }
+            case OpK::FE:
+                // one transpose per node of a node-batched evaluation
+                for (int k = 0; k < std::max(1, o.nodes); ++k) {
+                    const size_t sh = (size_t)k * L->node();
+                    mlsdc_status s = fe_adjoint(L->plan, &L->prm, tape + o.tape_off + sh, adj_of(A, o.p[1]) + sh,
+                                                adj_of(A, o.p[0]) + sh, st, &n);
+                    if (s != MLSDC_OK) return s;
+                }
+                n--;  // counted below with the others
+                break;
             case OpK::Node:
                 k_node_ad<<<grid_for(L->plan->nc), 256, 0, st>>>(adj_of(A, o.p[0]), adj_of(A, o.p[1]),
                                                                 adj_of(A, o.p[2]), adj_of(A, o.p[3]),

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "mlsdc_sh.h"
@@ -34,6 +35,47 @@ void set_error_text(const std::string& s);
     } while (0)
 
 inline int nc_of(int R) { return (R + 1) * (R + 2) / 2; }
+
+// Programmatic dependent launch.  The step's kernels are launched with
+// programmatic stream serialisation, so a kernel's CTAs may start while its
+// predecessor in the stream is still running; every kernel therefore calls
+// pdl_wait() before its first global access that depends on, or could race
+// with, an earlier kernel (reads of its inputs, any write), and only
+// constant tables are touched before it.  pdl_wait() returns at once for a
+// kernel launched without the attribute.  pdl_launch() lets the successor
+// start its own prologue; it carries no memory guarantee (the successor's
+// pdl_wait() waits for this grid to complete and its writes to be visible).
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// Whether launches use programmatic stream serialisation (on unless the
+// environment sets MLSDC_PDL=0, e.g. to time the difference).
+bool pdl_enabled();
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                            Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = pdl_enabled() ? 1 : 0;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
+#define MLSDC_LAUNCH(name, call)                          \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) {                          \
+            ::mlsdc::set_error(name, e_);                 \
+            return MLSDC_ERR_CUDA;                        \
+        }                                                 \
+    } while (0)
 
 // Raise (never lower) a kernel's dynamic shared-memory limit.  The attribute
 // belongs to the kernel, not to a plan, so a plan needing less must not undo

@@ -298,6 +298,10 @@ __device__ inline bool k_loop(const Cta& c, int nkb, int stages, int chunk, uint
                               int* err, BuildB build_b, LoadA load_a) {
     if (threadIdx.x == 0)
         for (int kb = 0; kb < nkb && kb < stages; ++kb) load_a(kb % stages, kb);
+    // the table tiles are constant: their loads overlap the previous kernel;
+    // the B operand depends on it
+    pdl_wait();
+    pdl_launch();
     for (int kb = 0; kb < nkb; ++kb) {
         const int st = kb % stages;
         const uint32_t use = (uint32_t)(kb / stages);
@@ -656,8 +660,8 @@ mlsdc_status launch_synth(sh_plan_t p, TcState* s, const TcArgs& g, cudaStream_t
     const size_t smem = cta_smem_bytes(MODE, g.chunk, g.stages);
     mlsdc_status rs = raise_smem_limit((const void*)k_tc_synth<MODE>, smem);
     if (rs != MLSDC_OK) return rs;
-    k_tc_synth<MODE><<<dim3(p->R + 1, nchunks), kTcThreads, smem, st>>>(s->map_syn, g);
-    MLSDC_LAUNCHED("k_tc_synth");
+    MLSDC_LAUNCH("k_tc_synth", launch_k(k_tc_synth<MODE>, dim3(p->R + 1, nchunks), dim3(kTcThreads), smem, st,
+                                        s->map_syn, g));
     return MLSDC_OK;
 }
 
@@ -667,8 +671,8 @@ mlsdc_status launch_anal(sh_plan_t p, TcState* s, const TcArgs& g, cudaStream_t 
     const size_t smem = cta_smem_bytes(MODE, g.chunk, g.stages);
     mlsdc_status rs = raise_smem_limit((const void*)k_tc_anal<MODE>, smem);
     if (rs != MLSDC_OK) return rs;
-    k_tc_anal<MODE><<<dim3(s->n_tiles, nchunks), kTcThreads, smem, st>>>(s->map_ana, g);
-    MLSDC_LAUNCHED("k_tc_anal");
+    MLSDC_LAUNCH("k_tc_anal", launch_k(k_tc_anal<MODE>, dim3(s->n_tiles, nchunks), dim3(kTcThreads), smem, st,
+                                       s->map_ana, g));
     return MLSDC_OK;
 }
 

@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 
@@ -16,6 +17,14 @@ void set_error(const char* where, cudaError_t e) {
     g_last_error = std::string(where) + ": " + cudaGetErrorString(e);
 }
 void set_error_text(const std::string& s) { g_last_error = s; }
+
+bool pdl_enabled() {
+    static const bool on = [] {
+        const char* v = std::getenv("MLSDC_PDL");
+        return !(v && v[0] == '0');
+    }();
+    return on;
+}
 
 mlsdc_status raise_smem_limit(const void* fn, size_t bytes) {
     static std::mutex mu;

@@ -44,6 +44,8 @@ __global__ void __launch_bounds__(32 * kSynthWarps) k_synth_rhs(const double2* _
     using C = C_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* sc = reinterpret_cast<C*>(smem_raw);  // [nm][4]: zeta, Phi', chi, psi; reused for the reduction
+    pdl_wait();
+    pdl_launch();
     state += blockIdx.y * ms.state;
     four += blockIdx.y * ms.four_in;
     const Chunk ch = chunks[blockIdx.x];
@@ -129,6 +131,8 @@ __global__ void __launch_bounds__(256) k_grid_rhs(const C_t<T>* __restrict__ fou
     using C = C_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* sx = reinterpret_cast<C*>(smem_raw);  // [9][I/2]: zeta, Phi', U, V packed rows, then A..E
+    pdl_wait();
+    pdl_launch();
     four_in += blockIdx.y * ms.four_in;
     four_out += blockIdx.y * ms.four_out;
     const int j = blockIdx.x;
@@ -222,6 +226,8 @@ __global__ void __launch_bounds__(32 * kAnalWarpsMax) k_anal_rhs(const C_t<T>* _
                                                                  MemberStrides ms) {
     using C = C_t<T>;
     constexpr int TW = 32;                    // latitudes per tile
+    pdl_wait();
+    pdl_launch();
     four_out += blockIdx.y * ms.four_out;
     FE += blockIdx.y * ms.fe;
     state += blockIdx.y * ms.state;

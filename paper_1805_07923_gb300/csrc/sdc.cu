@@ -46,6 +46,8 @@ __device__ __forceinline__ void implicit_solve_coef(double L, double alpha, cons
 
 __global__ void k_implicit_rhs(const double2* __restrict__ x, double2* __restrict__ F,
                                const int* __restrict__ ndeg, int nc, Phys ph, size_t ms_x, size_t ms_f) {
+    pdl_wait();
+    pdl_launch();
     x += blockIdx.y * ms_x;
     F += blockIdx.y * ms_f;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) {
@@ -76,10 +78,17 @@ __global__ void k_implicit_solve(const double2* __restrict__ b, double2* __restr
 // coarse level), the implicit solve, and F_I at the new node.  Node arrays
 // are [M+1][3][nc] complex per member (member stride ms); `node` = 3 nc
 // complex values.  The m = 0 launch also copies node 0 of the old F arrays
-// into the new ones.
-__global__ void k_sweep_node(double2* Th, const double2* __restrict__ FIo, const double2* __restrict__ FEo,
-                             double2* FIn, double2* FEn, const double2* __restrict__ tau,
-                             const int* __restrict__ ndeg, int nc, double dt, NodeRow row, Phys ph, size_t ms) {
+// into the new ones.  Each CTA takes kNodeCoefs coefficients with one thread
+// per (field, coefficient) for the weighted sums; the three fields of a
+// coefficient meet in shared memory for the coupled solve.
+__global__ void __launch_bounds__(3 * kNodeCoefs) k_sweep_node(double2* Th, const double2* __restrict__ FIo,
+                                                             const double2* __restrict__ FEo, double2* FIn,
+                                                             double2* FEn, const double2* __restrict__ tau,
+                                                             const int* __restrict__ ndeg, int nc, double dt,
+                                                             NodeRow row, Phys ph, size_t ms) {
+    __shared__ double2 sb[3][kNodeCoefs];
+    pdl_wait();
+    pdl_launch();
     const size_t mo = blockIdx.y * ms;
     Th += mo;
     FIo += mo;
@@ -89,49 +98,45 @@ __global__ void k_sweep_node(double2* Th, const double2* __restrict__ FIo, const
     if (tau) tau += mo;
     const size_t node = (size_t)3 * nc;
     const int m = row.m;
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) {
-        double2 b[3];
-        for (int f = 0; f < 3; ++f) {
-            const size_t o = (size_t)f * nc + c;
-            double2 acc = Th[o];  // Theta^n (node 0)
-            for (int j = 1; j <= m; ++j) {
-                const size_t oj = j * node + o;
-                const double2 de = make_double2(FEn[oj].x - FEo[oj].x, FEn[oj].y - FEo[oj].y);
-                const double2 di = make_double2(FIn[oj].x - FIo[oj].x, FIn[oj].y - FIo[oj].y);
-                acc = cax(acc, dt * row.qe[j], de);
-                acc = cax(acc, dt * row.qi[j], di);
-            }
-            acc = cax(acc, -dt * row.qimm, FIo[(m + 1) * node + o]);
-            for (int j = 0; j <= row.M; ++j) {
-                const size_t oj = j * node + o;
-                const double2 s = make_double2(FIo[oj].x + FEo[oj].x, FIo[oj].y + FEo[oj].y);
-                acc = cax(acc, dt * row.q[j], s);
-            }
-            if (tau) {
-                const double2 t = tau[(m + 1) * node + o];
-                acc = make_double2(acc.x + t.x, acc.y + t.y);
-            }
-            b[f] = acc;
+    const int f = threadIdx.x / kNodeCoefs, cl = threadIdx.x - f * kNodeCoefs;
+    const int c = blockIdx.x * kNodeCoefs + cl;
+    const bool live = c < nc;
+    const size_t o = (size_t)f * nc + c;
+    if (live) {
+        double2 acc = Th[o];  // Theta^n (node 0)
+        for (int j = 1; j <= m; ++j) {
+            const size_t oj = j * node + o;
+            const double2 de = make_double2(FEn[oj].x - FEo[oj].x, FEn[oj].y - FEo[oj].y);
+            const double2 di = make_double2(FIn[oj].x - FIo[oj].x, FIn[oj].y - FIo[oj].y);
+            acc = cax(acc, dt * row.qe[j], de);
+            acc = cax(acc, dt * row.qi[j], di);
         }
-        const double n = ndeg[c];
-        const double L = -n * (n + 1.0) * ph.inv_a2;
-        double2 p, z, d;
-        implicit_solve_coef(L, dt * row.qimm, ph, b[0], b[1], b[2], p, z, d);
-        const size_t om = (m + 1) * node + c;
-        Th[om] = p;
-        Th[om + nc] = z;
-        Th[om + 2 * nc] = d;
-        double2 fp, fz, fd;
-        implicit_rhs_coef(L, ph, p, z, d, fp, fz, fd);
-        FIn[om] = fp;
-        FIn[om + nc] = fz;
-        FIn[om + 2 * nc] = fd;
-        if (m == 0) {
-            for (int f = 0; f < 3; ++f) {
-                FIn[(size_t)f * nc + c] = FIo[(size_t)f * nc + c];
-                FEn[(size_t)f * nc + c] = FEo[(size_t)f * nc + c];
-            }
+        acc = cax(acc, -dt * row.qimm, FIo[(m + 1) * node + o]);
+        for (int j = 0; j <= row.M; ++j) {
+            const size_t oj = j * node + o;
+            const double2 s = make_double2(FIo[oj].x + FEo[oj].x, FIo[oj].y + FEo[oj].y);
+            acc = cax(acc, dt * row.q[j], s);
         }
+        if (tau) {
+            const double2 t = tau[(m + 1) * node + o];
+            acc = make_double2(acc.x + t.x, acc.y + t.y);
+        }
+        sb[f][cl] = acc;
+    }
+    __syncthreads();
+    if (!live) return;
+    const double n = ndeg[c];
+    const double L = -n * (n + 1.0) * ph.inv_a2;
+    double2 p, z, d;
+    implicit_solve_coef(L, dt * row.qimm, ph, sb[0][cl], sb[1][cl], sb[2][cl], p, z, d);
+    double2 fp, fz, fd;
+    implicit_rhs_coef(L, ph, p, z, d, fp, fz, fd);
+    const size_t om = (m + 1) * node + o;
+    Th[om] = f == 0 ? p : (f == 1 ? z : d);
+    FIn[om] = f == 0 ? fp : (f == 1 ? fz : fd);
+    if (m == 0) {
+        FIn[o] = FIo[o];
+        FEn[o] = FEo[o];
     }
 }
 
@@ -139,6 +144,8 @@ __global__ void k_sweep_node(double2* Th, const double2* __restrict__ FIo, const
 // per member.
 __global__ void k_broadcast(const double2* __restrict__ src, double2* __restrict__ dst, int n3, int count,
                             size_t ms_src, size_t ms_dst) {
+    pdl_wait();
+    pdl_launch();
     src += blockIdx.y * ms_src;
     dst += blockIdx.y * ms_dst;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n3; c += gridDim.x * blockDim.x) {
@@ -152,6 +159,8 @@ __global__ void k_broadcast(const double2* __restrict__ src, double2* __restrict
 // Theta_c[i] = D( sum_j Pi^c_f[i][j] Theta_f[j] ) for i in [i0, i1).
 __global__ void k_restrict(const double2* __restrict__ Tf, double2* __restrict__ Tc, const int* __restrict__ c2f,
                            int ncf, int ncc, int nf_nodes, int i0, int i1, TransferMat Pcf, size_t msf, size_t msc) {
+    pdl_wait();
+    pdl_launch();
     Tf += blockIdx.y * msf;
     Tc += blockIdx.y * msc;
     const int total = 3 * ncc;
@@ -174,6 +183,8 @@ __global__ void k_fas_tau(const double2* __restrict__ Tf, const double2* __restr
                           const double2* __restrict__ FIc, const double2* __restrict__ FEc,
                           double2* __restrict__ tau, const int* __restrict__ c2f, int ncf, int ncc,
                           double dt, FasArgs A, size_t msf, size_t msc) {
+    pdl_wait();
+    pdl_launch();
     const size_t of_m = blockIdx.y * msf, oc_m = blockIdx.y * msc;
     Tf += of_m;
     FIf += of_m;
@@ -218,6 +229,8 @@ __global__ void k_interp(double2* __restrict__ Tf, double2* __restrict__ FIf, do
                          const double2* __restrict__ FIs, const double2* __restrict__ FEs,
                          const int* __restrict__ c2f, int ncf, int ncc, int nfn, int ncn, TransferMat Pfc,
                          size_t msf, size_t msc) {
+    pdl_wait();
+    pdl_launch();
     const size_t of_m = blockIdx.y * msf, oc_m = blockIdx.y * msc;
     Tf += of_m;
     FIf += of_m;
@@ -348,21 +361,24 @@ using namespace mlsdc;
 
 namespace mlsdc {
 
-// F_E at one node of every member: x and FE point at that node of member 0.
-static mlsdc_status eval_FE(sdc_level_t L, const double2* x, double2* FE, cudaStream_t st) {
+// F_E at one node of every member (x and FE point at that node of member 0),
+// or, with nodes > 0 on a one-member level, at `nodes` consecutive nodes in
+// one launch per stage (the nodes are the batch).
+static mlsdc_status eval_FE(sdc_level_t L, const double2* x, double2* FE, cudaStream_t st, int nodes = 0) {
     RhsBatch b;
-    b.members = L->members;
-    b.state_ms = b.fe_ms = L->ms();
+    b.members = nodes > 0 ? nodes : L->members;
+    b.state_ms = b.fe_ms = nodes > 0 ? L->node() : L->ms();
     if (L->plan->precision == MLSDC_FP64)
         return rhs_explicit_f64(L->plan, &L->prm, (const double*)x, (double*)FE, st, &L->launches, -1, b);
     return rhs_explicit_mp(L->plan, &L->prm, (const double*)x, (double*)FE, st, &L->launches, -1, b);
 }
 
-static mlsdc_status eval_FI(sdc_level_t L, const double2* x, double2* FI, cudaStream_t st) {
+static mlsdc_status eval_FI(sdc_level_t L, const double2* x, double2* FI, cudaStream_t st, int nodes = 0) {
     const int nc = L->plan->nc;
-    k_implicit_rhs<<<dim3(grid_for(nc), L->members), 256, 0, st>>>(x, FI, L->plan->d_ndeg, nc, phys_of(L->prm),
-                                                                   L->ms(), L->ms());
-    MLSDC_LAUNCHED("k_implicit_rhs");
+    const size_t ms = nodes > 0 ? L->node() : L->ms();
+    MLSDC_LAUNCH("k_implicit_rhs", launch_k(k_implicit_rhs, dim3(grid_for(nc), nodes > 0 ? nodes : L->members),
+                                            dim3(256), 0, st, x, FI, (const int*)L->plan->d_ndeg, nc,
+                                            phys_of(L->prm), ms, ms));
     L->launches++;
     return MLSDC_OK;
 }
@@ -386,17 +402,18 @@ static mlsdc_status launch_node(sdc_level_t L, double dt, const NodeRow& row, do
                                 const double2* FEo, double2* FIn, double2* FEn, const double2* tau,
                                 cudaStream_t st) {
     const int nc = L->plan->nc;
-    k_sweep_node<<<dim3(grid_for(nc), L->members), 256, 0, st>>>(Th, FIo, FEo, FIn, FEn, tau, L->plan->d_ndeg, nc,
-                                                                 dt, row, phys_of(L->prm), L->ms());
-    MLSDC_LAUNCHED("k_sweep_node");
+    MLSDC_LAUNCH("k_sweep_node",
+                 launch_k(k_sweep_node, dim3((nc + kNodeCoefs - 1) / kNodeCoefs, L->members), dim3(3 * kNodeCoefs),
+                          0, st, Th, FIo, FEo, FIn, FEn, tau, (const int*)L->plan->d_ndeg, nc, dt, row,
+                          phys_of(L->prm), L->ms()));
     L->launches++;
     return MLSDC_OK;
 }
 
 static mlsdc_status launch_bcast(sdc_level_t L, const double2* src, double2* dst, int n3, int count, size_t ms_src,
                                  size_t ms_dst, cudaStream_t st) {
-    k_broadcast<<<dim3(grid_for(n3), L->members), 256, 0, st>>>(src, dst, n3, count, ms_src, ms_dst);
-    MLSDC_LAUNCHED("k_broadcast");
+    MLSDC_LAUNCH("k_broadcast", launch_k(k_broadcast, dim3(grid_for(n3), L->members), dim3(256), 0, st, src, dst, n3,
+                                         count, ms_src, ms_dst));
     L->launches++;
     return MLSDC_OK;
 }
@@ -665,22 +682,25 @@ size_t build_mlsdc_ops(mlsdc_t ml, double2* state, double dt, int n_iter, int n_
         o.ms_dst = L->ms();
         ops.push_back(o);
     };
-    auto fi = [&](sdc_level_t L, double2* x, double2* f) {
+    auto fi = [&](sdc_level_t L, double2* x, double2* f, int nodes = 0) {
         Op o{OpK::FI};
         o.L = L;
         o.p[0] = x;
         o.p[1] = f;
+        o.nodes = nodes;
         ops.push_back(o);
     };
-    auto fe = [&](sdc_level_t L, double2* x, double2* f) {
+    auto fe = [&](sdc_level_t L, double2* x, double2* f, int nodes = 0) {
         Op o{OpK::FE};
         o.L = L;
         o.p[0] = x;
         o.p[1] = f;
+        o.nodes = nodes;
         o.tape_off = tape;
-        tape += (size_t)L->members * L->node();
+        tape += (size_t)(nodes > 0 ? nodes : L->members) * L->node();
         ops.push_back(o);
     };
+    const bool batch_b = B == 1 && ncn > 2 && C->plan->max_members >= ncn - 1;
     auto sweep_ops = [&](sdc_level_t L, double2* FIo, double2* FEo, double2* FIn, double2* FEn, double2* tau) {
         for (int m = 0; m < L->n - 1; ++m) {
             Op o{OpK::Node};
@@ -728,11 +748,18 @@ size_t build_mlsdc_ops(mlsdc_t ml, double2* state, double dt, int n_iter, int n_
         // A) fine sweep
         sweep_ops(F, F->FI[cf], F->FE[cf], F->FI[1 - cf], F->FE[1 - cf], nullptr);
         cf = 1 - cf;
-        // B) restrict nodes 1..Mc, evaluate, save
+        // B) restrict nodes 1..Mc, evaluate, save.  The evaluations at the
+        // coarse nodes are independent: with one member and a coarse plan
+        // sized for them, all Mc nodes go in one launch per stage.
         restrict_ops(1, ncn);
-        for (int i = 1; i < ncn; ++i) {
-            fi(C, C->Th + i * nodec, C->FI[cc] + i * nodec);
-            fe(C, C->Th + i * nodec, C->FE[cc] + i * nodec);
+        if (batch_b) {
+            fi(C, C->Th + nodec, C->FI[cc] + nodec, ncn - 1);
+            fe(C, C->Th + nodec, C->FE[cc] + nodec, ncn - 1);
+        } else {
+            for (int i = 1; i < ncn; ++i) {
+                fi(C, C->Th + i * nodec, C->FI[cc] + i * nodec);
+                fe(C, C->Th + i * nodec, C->FE[cc] + i * nodec);
+            }
         }
         const size_t bytes = (size_t)B * C->ms() * sizeof(double2);
         copy(ml->Ts, C->Th, bytes);
@@ -788,38 +815,41 @@ mlsdc_status run_ops(mlsdc_t ml, const std::vector<Op>& ops, cudaStream_t st, in
                 s = launch_bcast(o.L, o.p[0], o.p[1], o.n3, o.count, o.ms_src, o.ms_dst, st);
                 break;
             case OpK::FI:
-                s = eval_FI(o.L, o.p[0], o.p[1], st);
+                s = eval_FI(o.L, o.p[0], o.p[1], st, o.nodes);
                 break;
             case OpK::FE:
-                if (tape) {
+                if (tape && o.nodes > 0) {
+                    MLSDC_CUDA(cudaMemcpyAsync(tape + o.tape_off, o.p[0], (size_t)o.nodes * o.L->node() * sizeof(double2),
+                                               cudaMemcpyDeviceToDevice, st));
+                } else if (tape) {
                     const size_t w = o.L->node() * sizeof(double2);
                     MLSDC_CUDA(cudaMemcpy2DAsync(tape + o.tape_off, w, o.p[0], o.L->ms() * sizeof(double2), w,
                                                  (size_t)o.L->members, cudaMemcpyDeviceToDevice, st));
                 }
-                s = eval_FE(o.L, o.p[0], o.p[1], st);
+                s = eval_FE(o.L, o.p[0], o.p[1], st, o.nodes);
                 break;
             case OpK::Node:
                 s = launch_node(o.L, o.dt, o.row, o.p[0], o.p[1], o.p[2], o.p[3], o.p[4], o.p[5], st);
                 break;
             case OpK::Restrict:
-                k_restrict<<<gt, 256, 0, st>>>(o.p[0], o.p[1], ml->d_c2f, ncf, ncc, nfn, o.i0, o.i1, ml->Pcf, msf,
-                                               msc);
-                MLSDC_LAUNCHED("k_restrict");
+                MLSDC_LAUNCH("k_restrict", launch_k(k_restrict, gt, dim3(256), 0, st, o.p[0], o.p[1],
+                                                    (const int*)ml->d_c2f, ncf, ncc, nfn, o.i0, o.i1, ml->Pcf, msf,
+                                                    msc));
                 own++;
                 break;
             case OpK::Copy:
                 MLSDC_CUDA(cudaMemcpyAsync(o.p[1], o.p[0], o.bytes, cudaMemcpyDeviceToDevice, st));
                 break;
             case OpK::Fas:
-                k_fas_tau<<<gt, 256, 0, st>>>(o.p[0], o.p[1], o.p[2], o.p[3], o.p[4], o.p[5], o.p[6], ml->d_c2f,
-                                              ncf, ncc, o.dt, fa, msf, msc);
-                MLSDC_LAUNCHED("k_fas_tau");
+                MLSDC_LAUNCH("k_fas_tau", launch_k(k_fas_tau, gt, dim3(256), 0, st, o.p[0], o.p[1], o.p[2], o.p[3],
+                                                   o.p[4], o.p[5], o.p[6], (const int*)ml->d_c2f, ncf, ncc, o.dt,
+                                                   fa, msf, msc));
                 own++;
                 break;
             case OpK::Interp:
-                k_interp<<<gt, 256, 0, st>>>(o.p[0], o.p[1], o.p[2], o.p[3], o.p[4], o.p[5], o.p[6], o.p[7], o.p[8],
-                                             ml->d_c2f, ncf, ncc, nfn, ncn, ml->Pfc, msf, msc);
-                MLSDC_LAUNCHED("k_interp");
+                MLSDC_LAUNCH("k_interp", launch_k(k_interp, gt, dim3(256), 0, st, o.p[0], o.p[1], o.p[2], o.p[3],
+                                                  o.p[4], o.p[5], o.p[6], o.p[7], o.p[8], (const int*)ml->d_c2f, ncf,
+                                                  ncc, nfn, ncn, ml->Pfc, msf, msc));
                 own++;
                 break;
             case OpK::CopyLast: {

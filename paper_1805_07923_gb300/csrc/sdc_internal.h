@@ -14,6 +14,7 @@
 namespace mlsdc {
 
 constexpr int kMaxNodes = 9;
+constexpr int kNodeCoefs = 64;  // coefficients per CTA of the node update (3 x 64 threads)
 
 struct Phys {
     double inv_a2, phibar, nu;
@@ -66,6 +67,8 @@ struct Op {
     double dt = 0.0;                 // Node, Fas
     NodeRow row{};                   // Node
     size_t tape_off = 0;             // FE: offset of its linearisation point in a step's tape (complex)
+    int nodes = 0;                   // FI / FE: > 0 = that many consecutive nodes of a one-member level
+                                     // in one launch (the nodes as the batch); 0 = one node of every member
 };
 
 inline Phys phys_of(const swe_params& p) { return Phys{1.0 / (p.a * p.a), p.phibar, p.nu}; }

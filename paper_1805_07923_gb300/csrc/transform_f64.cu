@@ -126,20 +126,25 @@ mlsdc_status rhs_explicit_f64(sh_plan_t p, const swe_params* prm, const double* 
     const size_t fs = (size_t)p->J * (R + 1);
     const MemberStrides ms{b.state_ms, 4 * fs, 5 * fs, b.fe_ms};
     if (stage == 0 || stage < 0) {
-        k_synth_rhs<double><<<dim3(p->n_synth, b.members), 32 * kSynthWarps, synth_smem<double>(R), st>>>(
-            (const double2*)state, p->d_P, p->d_H, p->d_synth, R, p->J2, p->nc, prm->a, p->d_four_in, ms);
-        MLSDC_LAUNCHED("k_synth_rhs<double>");
+        MLSDC_LAUNCH("k_synth_rhs<double>",
+                     launch_k(k_synth_rhs<double>, dim3(p->n_synth, b.members), dim3(32 * kSynthWarps),
+                              synth_smem<double>(R), st, (const double2*)state, (const double*)p->d_P,
+                              (const double*)p->d_H, (const Chunk*)p->d_synth, R, p->J2, p->nc, prm->a,
+                              p->d_four_in, ms));
     }
     if (stage == 1 || stage < 0) {
-        k_grid_rhs<double><<<dim3(p->J, b.members), 256, sizeof(double2) * 9 * (p->I / 2), st>>>(
-            p->d_four_in, p->d_four_out, p->d_mu, p->d_w, p->d_tw, R, p->I, p->logI, p->J, 2.0 * prm->omega, ms);
-        MLSDC_LAUNCHED("k_grid_rhs<double>");
+        MLSDC_LAUNCH("k_grid_rhs<double>",
+                     launch_k(k_grid_rhs<double>, dim3(p->J, b.members), dim3(256), sizeof(double2) * 9 * (p->I / 2),
+                              st, (const double2*)p->d_four_in, p->d_four_out, (const double*)p->d_mu,
+                              (const double*)p->d_w, (const double2*)p->d_tw, R, p->I, p->logI, p->J,
+                              2.0 * prm->omega, ms));
     }
     if (stage == 2 || stage < 0) {
-        k_anal_rhs<double><<<dim3(p->n_anal, b.members), 32 * anal_warps(p->J2), 0, st>>>(
-            p->d_four_out, p->d_P, p->d_H, p->d_anal, R, p->J2, p->nc, prm->a, (double2*)FE,
-            (const double2*)state, 0.0, p->d_cor, ms);
-        MLSDC_LAUNCHED("k_anal_rhs<double>");
+        MLSDC_LAUNCH("k_anal_rhs<double>",
+                     launch_k(k_anal_rhs<double>, dim3(p->n_anal, b.members), dim3(32 * anal_warps(p->J2)), 0, st,
+                              (const double2*)p->d_four_out, (const double*)p->d_P, (const double*)p->d_H,
+                              (const Chunk*)p->d_anal, R, p->J2, p->nc, prm->a, (double2*)FE, (const double2*)state,
+                              0.0, (const double*)p->d_cor, ms));
     }
     if (launches) *launches += stage < 0 ? 3 : 1;
     return MLSDC_OK;

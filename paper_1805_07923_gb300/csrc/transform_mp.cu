@@ -84,24 +84,28 @@ mlsdc_status rhs_explicit_mp(sh_plan_t p, const swe_params* prm, const double* s
         if (tc) {
             if ((s = tc_synth(p, state, prm->a, b, st)) != MLSDC_OK) return s;
         } else {
-            k_synth_rhs<float><<<dim3(p->n_synth, b.members), 32 * kSynthWarps, synth_smem<float>(R), st>>>(
-                (const double2*)state, t.P32, t.H32, p->d_synth, R, p->J2, p->nc, prm->a, t.four_in, ms);
-            MLSDC_LAUNCHED("k_synth_rhs<float>");
+            MLSDC_LAUNCH("k_synth_rhs<float>",
+                         launch_k(k_synth_rhs<float>, dim3(p->n_synth, b.members), dim3(32 * kSynthWarps),
+                                  synth_smem<float>(R), st, (const double2*)state, (const float*)t.P32,
+                                  (const float*)t.H32, (const Chunk*)p->d_synth, R, p->J2, p->nc, prm->a, t.four_in,
+                                  ms));
         }
     }
     if (stage == 1 || stage < 0) {
-        k_grid_rhs<float><<<dim3(p->J, b.members), 256, sizeof(float2) * 9 * (p->I / 2), st>>>(
-            t.four_in, t.four_out, p->d_mu, p->d_w, t.tw32, R, p->I, p->logI, p->J, 0.0, ms);
-        MLSDC_LAUNCHED("k_grid_rhs<float>");
+        MLSDC_LAUNCH("k_grid_rhs<float>",
+                     launch_k(k_grid_rhs<float>, dim3(p->J, b.members), dim3(256), sizeof(float2) * 9 * (p->I / 2), st,
+                              (const float2*)t.four_in, t.four_out, (const double*)p->d_mu, (const double*)p->d_w,
+                              (const float2*)t.tw32, R, p->I, p->logI, p->J, 0.0, ms));
     }
     if (stage == 2 || stage < 0) {
         if (tc) {
             if ((s = tc_anal(p, prm->a, FE, state, 2.0 * prm->omega, b, st)) != MLSDC_OK) return s;
         } else {
-            k_anal_rhs<float><<<dim3(p->n_anal, b.members), 32 * anal_warps(p->J2), 0, st>>>(
-                t.four_out, t.P32, t.H32, p->d_anal, R, p->J2, p->nc, prm->a, (double2*)FE, (const double2*)state,
-                2.0 * prm->omega, p->d_cor, ms);
-            MLSDC_LAUNCHED("k_anal_rhs<float>");
+            MLSDC_LAUNCH("k_anal_rhs<float>",
+                         launch_k(k_anal_rhs<float>, dim3(p->n_anal, b.members), dim3(32 * anal_warps(p->J2)), 0, st,
+                                  (const float2*)t.four_out, (const float*)t.P32, (const float*)t.H32,
+                                  (const Chunk*)p->d_anal, R, p->J2, p->nc, prm->a, (double2*)FE,
+                                  (const double2*)state, 2.0 * prm->omega, (const double*)p->d_cor, ms));
         }
     }
     if (launches) *launches += stage < 0 ? 3 : 1;
