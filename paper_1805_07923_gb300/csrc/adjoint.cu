@@ -154,16 +154,18 @@ __global__ void __launch_bounds__(256) k_grid_ad(const double2* __restrict__ fou
                                                  const double2* __restrict__ tw, int R, int I, int logI, int J,
                                                  double two_omega) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    double2* sx = reinterpret_cast<double2*>(smem_raw);  // [9][I/2]
+    double2* sx = reinterpret_cast<double2*>(smem_raw);  // [9][I/2], then [I/2] twiddles
     const int j = blockIdx.x;
     const int Hn = I >> 1, logH = logI - 1;
+    double2* stw = sx + 9 * Hn;
+    for (int k = threadIdx.x; k < Hn; k += blockDim.x) stw[k] = tw[k];
     const size_t fs = (size_t)J * (R + 1);
     for (int t = threadIdx.x; t < 9 * Hn; t += blockDim.x) {
         const int f = t >> logH, k = t & (Hn - 1);
         sx[f * Hn + k] = irfft_pack(four_in + f * fs + (size_t)j * (R + 1), k, R, Hn, tw);
     }
     __syncthreads();
-    fft_dif(sx, 9, Hn, logH, tw, true);
+    fft4_dif(sx, 9, Hn, logH, stw, I, true);
     const double muj = mu[j];
     const double f = two_omega * muj;
     const double rc = 1.0 / (1.0 - muj * muj);
@@ -188,7 +190,7 @@ __global__ void __launch_bounds__(256) k_grid_ad(const double2* __restrict__ fou
         for (int k = 0; k < 4; ++k) sx[k * Hn + q] = make_double2(o[k][0], o[k][1]);
     }
     __syncthreads();
-    fft_dit(sx, 4, Hn, logH, tw, false);
+    fft4_dit(sx, 4, Hn, logH, stw, I, false);
     for (int t = threadIdx.x; t < 4 * (R + 1); t += blockDim.x) {
         const int fld = t / (R + 1);
         const int m = t - fld * (R + 1);
@@ -286,7 +288,7 @@ __global__ void __launch_bounds__(32 * kAnalWarpsMax) k_anal_ad(const double2* _
 static size_t synth_ad_smem(int R) {
     return std::max(sizeof(double2) * kAdSynthWarps * kAdSums * 32, sizeof(double2) * 8 * (R + 1));
 }
-static size_t grid_ad_smem(int I) { return sizeof(double2) * 9 * (I / 2); }
+static size_t grid_ad_smem(int I) { return sizeof(double2) * 10 * (I / 2); }
 
 // Shared-memory limits of the F_E adjoint kernels for a plan (outside any
 // stream capture).

@@ -87,6 +87,100 @@ __device__ void fft_dif(C* x, int narr, int Hn, int logH, const C* __restrict__ 
     }
 }
 
+// Mixed radix-4 (and one radix-2 stage when log2 N is odd) versions of the
+// same pair: fft4_dif takes natural-order input to an output in the
+// base-4 digit-reversed order of its stages, fft4_dit takes that order back
+// to natural order, so the two compose with any pointwise stage between them
+// exactly as the radix-2 pair does, in half the barriers.  N = I/2 complex
+// points per array, `narr` arrays back to back; tw[k] = exp(-2 pi i k / I)
+// for k < I/2 (shared or global memory), exp(-2 pi i k / I) = -tw[k - I/2]
+// above.  DIF stage of span L (quarter Q = L/4), butterfly (a, b, c, d) at
+// (i0, i0 + Q, i0 + 2Q, i0 + 3Q), s = -i (forward) or +i (inverse):
+//   (a + c) + (b + d),  [(a - c) + s (b - d)] w^j,  [(a + c) - (b + d)] w^2j,  [(a - c) - s (b - d)] w^3j
+// with w = exp(-/+ 2 pi i / L); the DIT stage applies the twiddles first.
+template <class C> __device__ __forceinline__ C tw_at(const C* tw, int k, int half) {
+    if (k < half) return tw[k];
+    const C w = tw[k - half];
+    return mkc(-w.x, -w.y);
+}
+template <class C> __device__ __forceinline__ C times_s(C z, bool inverse) {  // s z, s = +i or -i
+    return inverse ? mkc(-z.y, z.x) : mkc(z.y, -z.x);
+}
+template <class C> __device__ __forceinline__ C maybe_conj(C w, bool inverse) { return inverse ? cconj(w) : w; }
+
+template <class C>
+__device__ void fft4_dif(C* x, int narr, int N, int logN, const C* tw, int I, bool inverse) {
+    const int half = I >> 1;
+    int L = N, logL = logN;
+    if (logN & 1) {
+        const int H = N >> 1;
+        for (int t = threadIdx.x; t < narr * H; t += blockDim.x) {
+            const int ar = t >> (logN - 1), j = t & (H - 1);
+            C* xa = x + ar * N;
+            const C w = maybe_conj(tw[2 * j], inverse);
+            const C u = xa[j], v = xa[j + H];
+            xa[j] = cadd(u, v);
+            xa[j + H] = cmul(csub(u, v), w);
+        }
+        __syncthreads();
+        L >>= 1;
+        --logL;
+    }
+    for (; L >= 4; L >>= 2, logL -= 2) {
+        const int Q = L >> 2, logQ = logL - 2;
+        const int st = I >> logL;
+        for (int t = threadIdx.x; t < narr * (N >> 2); t += blockDim.x) {
+            const int ar = t >> (logN - 2), r = t & ((N >> 2) - 1);
+            const int g = r >> logQ, j = r & (Q - 1);
+            C* xa = x + ar * N + g * L + j;
+            const C a = xa[0], b = xa[Q], c = xa[2 * Q], d = xa[3 * Q];
+            const C apc = cadd(a, c), amc = csub(a, c), bpd = cadd(b, d), sbmd = times_s(csub(b, d), inverse);
+            xa[0] = cadd(apc, bpd);
+            xa[Q] = cmul(cadd(amc, sbmd), maybe_conj(tw_at(tw, j * st, half), inverse));
+            xa[2 * Q] = cmul(csub(apc, bpd), maybe_conj(tw_at(tw, 2 * j * st, half), inverse));
+            xa[3 * Q] = cmul(csub(amc, sbmd), maybe_conj(tw_at(tw, 3 * j * st, half), inverse));
+        }
+        __syncthreads();
+    }
+}
+
+template <class C>
+__device__ void fft4_dit(C* x, int narr, int N, int logN, const C* tw, int I, bool inverse) {
+    const int half = I >> 1;
+    const int top = (logN & 1) ? logN - 1 : logN;
+    for (int logL = 2; logL <= top; logL += 2) {
+        const int L = 1 << logL, Q = L >> 2, logQ = logL - 2;
+        const int st = I >> logL;
+        for (int t = threadIdx.x; t < narr * (N >> 2); t += blockDim.x) {
+            const int ar = t >> (logN - 2), r = t & ((N >> 2) - 1);
+            const int g = r >> logQ, j = r & (Q - 1);
+            C* xa = x + ar * N + g * L + j;
+            const C a = xa[0];
+            const C b = cmul(xa[Q], maybe_conj(tw_at(tw, j * st, half), inverse));
+            const C c = cmul(xa[2 * Q], maybe_conj(tw_at(tw, 2 * j * st, half), inverse));
+            const C d = cmul(xa[3 * Q], maybe_conj(tw_at(tw, 3 * j * st, half), inverse));
+            const C apc = cadd(a, c), amc = csub(a, c), bpd = cadd(b, d), sbmd = times_s(csub(b, d), inverse);
+            xa[0] = cadd(apc, bpd);
+            xa[Q] = cadd(amc, sbmd);
+            xa[2 * Q] = csub(apc, bpd);
+            xa[3 * Q] = csub(amc, sbmd);
+        }
+        __syncthreads();
+    }
+    if (logN & 1) {
+        const int H = N >> 1;
+        for (int t = threadIdx.x; t < narr * H; t += blockDim.x) {
+            const int ar = t >> (logN - 1), j = t & (H - 1);
+            C* xa = x + ar * N;
+            const C w = maybe_conj(tw[2 * j], inverse);
+            const C u = xa[j], v = cmul(xa[j + H], w);
+            xa[j] = cadd(u, v);
+            xa[j + H] = csub(u, v);
+        }
+        __syncthreads();
+    }
+}
+
 // Real DFTs of length I through complex DFTs of length I/2 over the packed
 // samples z_k = x_{2k} + i x_{2k+1} of ONE real row (packing two different
 // fields would tie the smaller field's rounding error to the larger one).

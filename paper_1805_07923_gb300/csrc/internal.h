@@ -48,8 +48,8 @@ inline int nc_of(int R) { return (R + 1) * (R + 2) / 2; }
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
-// Whether launches use programmatic stream serialisation (on unless the
-// environment sets MLSDC_PDL=0, e.g. to time the difference).
+// Whether launches use programmatic stream serialisation (off unless the
+// environment sets MLSDC_PDL=1).
 bool pdl_enabled();
 
 template <typename... KArgs, typename... Args>

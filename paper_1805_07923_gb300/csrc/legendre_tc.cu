@@ -63,7 +63,8 @@ struct TcState {
     int* d_err = nullptr;
     int2* d_tiles = nullptr;
     int n_tiles = 0;
-    int chunk = 1;  // members per CTA (autotuned)
+    int chunk = 1;   // members per CTA (autotuned)
+    int stages = 0;  // K pipeline depth (autotuned; 0 = the deepest that fits)
 };
 
 // ---------------------------------------------------------------- PTX helpers
@@ -684,7 +685,7 @@ TcArgs base_args(sh_plan_t p, TcState* s, double a, int members) {
     g.J2p = s->J2p;
     g.members = members;
     g.chunk = std::min(s->chunk, members);
-    g.stages = stages_for(s->mode, g.chunk);
+    g.stages = s->stages > 0 ? s->stages : stages_for(s->mode, g.chunk);
     g.a = a;
     g.four_in = p->mp.four_in;
     g.four_out = p->mp.four_out;
@@ -695,15 +696,13 @@ TcArgs base_args(sh_plan_t p, TcState* s, double a, int members) {
 }
 
 // Autotuner: time the synthesis and analysis for a full batch of members
-// with each feasible member chunk (1, 2, 4, 8, 16 members per CTA) and keep
-// the fastest.  Runs once per plan, on zero inputs, at plan creation.
+// with each feasible member chunk (1, 2, 4, 8, 16 members per CTA) and K
+// pipeline depth (two stages, or one, which leaves room for more CTAs per
+// SM) and keep the fastest.  Runs once per plan, on zero inputs, at plan
+// creation.
 template <int MODE>
 mlsdc_status autotune(sh_plan_t p, TcState* s) {
     const int B = p->max_members;
-    if (B == 1) {
-        s->chunk = 1;
-        return MLSDC_OK;
-    }
     const size_t n = (size_t)B * 3 * p->nc;
     double2 *x = nullptr, *fe = nullptr;
     MLSDC_CUDA(cudaMalloc((void**)&x, n * sizeof(double2)));
@@ -713,11 +712,13 @@ mlsdc_status autotune(sh_plan_t p, TcState* s) {
     MLSDC_CUDA(cudaEventCreate(&e0));
     MLSDC_CUDA(cudaEventCreate(&e1));
     float best = 1e30f;
-    int best_chunk = 1;
+    int best_chunk = 1, best_stages = 0;
     mlsdc_status rs = MLSDC_OK;
-    for (int chunk = 1; chunk <= 16 && chunk <= B && rs == MLSDC_OK; chunk *= 2) {
-        if (stages_for(MODE, chunk) == 0) continue;
+    for (int cfg = 0; cfg < 10 && rs == MLSDC_OK; ++cfg) {
+        const int chunk = 1 << (cfg >> 1), stages = 2 - (cfg & 1);
+        if (chunk > B || cta_smem_bytes(MODE, chunk, stages) > kSmemBudget) continue;
         s->chunk = chunk;
+        s->stages = stages;
         TcArgs g = base_args(p, s, 6.37122e6, B);
         g.state = x;
         g.state_ms = (size_t)3 * p->nc;
@@ -735,6 +736,7 @@ mlsdc_status autotune(sh_plan_t p, TcState* s) {
         if (rs == MLSDC_OK && ms < best) {
             best = ms;
             best_chunk = chunk;
+            best_stages = stages;
         }
     }
     cudaEventDestroy(e0);
@@ -742,6 +744,7 @@ mlsdc_status autotune(sh_plan_t p, TcState* s) {
     cudaFree(x);
     cudaFree(fe);
     s->chunk = best_chunk;
+    s->stages = best_stages;
     return rs;
 }
 

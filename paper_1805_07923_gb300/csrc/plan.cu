@@ -19,9 +19,12 @@ void set_error(const char* where, cudaError_t e) {
 void set_error_text(const std::string& s) { g_last_error = s; }
 
 bool pdl_enabled() {
+    // Off by default: measured inside the step's CUDA graph on GB300, the
+    // programmatic edges made the step slower (565 -> 465 steps/s split-BF16,
+    // 199 -> 115 float64), although isolated back-to-back launches gained.
     static const bool on = [] {
         const char* v = std::getenv("MLSDC_PDL");
-        return !(v && v[0] == '0');
+        return v && v[0] == '1';
     }();
     return on;
 }

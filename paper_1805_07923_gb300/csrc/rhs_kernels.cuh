@@ -131,20 +131,23 @@ __global__ void __launch_bounds__(256) k_grid_rhs(const C_t<T>* __restrict__ fou
     using C = C_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* sx = reinterpret_cast<C*>(smem_raw);  // [9][I/2]: zeta, Phi', U, V packed rows, then A..E
+    const int Hn = I >> 1, logH = logI - 1;
+    C* stw = sx + 9 * Hn;                     // [I/2] twiddles
+    for (int k = threadIdx.x; k < Hn; k += blockDim.x) stw[k] = tw[k];  // constant table
     pdl_wait();
     pdl_launch();
     four_in += blockIdx.y * ms.four_in;
     four_out += blockIdx.y * ms.four_out;
     const int j = blockIdx.x;
-    const int Hn = I >> 1, logH = logI - 1;
     const size_t fs = (size_t)J * (R + 1);
     for (int t = threadIdx.x; t < 4 * Hn; t += blockDim.x) {
         const int f = t >> logH, k = t & (Hn - 1);
         sx[f * Hn + k] = irfft_pack(four_in + f * fs + (size_t)j * (R + 1), k, R, Hn, tw);
     }
     __syncthreads();
-    // inverse by decimation in frequency: slot q now holds the longitude pair bitrev(q)
-    fft_dif(sx, 4, Hn, logH, tw, true);
+    // inverse by decimation in frequency: slot q now holds the longitude pair
+    // at the digit-reversed position of q
+    fft4_dif(sx, 4, Hn, logH, stw, I, true);
     const double muj = mu[j];
     const T f = T(two_omega * muj);
     const T rc = T(1.0 / (1.0 - muj * muj));
@@ -162,8 +165,8 @@ __global__ void __launch_bounds__(256) k_grid_rhs(const C_t<T>* __restrict__ fou
                             T(0.5) * (u.y * u.y + v.y * v.y) * rc);
     }
     __syncthreads();
-    // forward by decimation in time from the bit-reversed slots: natural order out
-    fft_dit(y, 5, Hn, logH, tw, false);
+    // forward by decimation in time from the digit-reversed slots: natural order out
+    fft4_dit(y, 5, Hn, logH, stw, I, false);
     const T sAD = T(w[j] / (1.0 - muj * muj) / I);
     const T sE = T(w[j] / I);
     for (int t = threadIdx.x; t < 5 * (R + 1); t += blockDim.x) {
@@ -318,6 +321,10 @@ __global__ void __launch_bounds__(32 * kAnalWarpsMax) k_anal_rhs(const C_t<T>* _
 }
 
 // Launch helpers shared by both precisions.
+template <class T>
+inline size_t grid_smem(int I) {
+    return sizeof(C_t<T>) * 10 * (size_t)(I / 2);  // nine rows and the twiddles
+}
 template <class T>
 inline size_t synth_smem(int R) {
     const size_t coef = sizeof(C_t<T>) * 4 * (R + 1);

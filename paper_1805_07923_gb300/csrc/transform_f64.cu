@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(32) k_anal_scalar_f64(const double2* __restric
 
 mlsdc_status f64_prepare(sh_plan_t p) {
     mlsdc_status s;
-    if ((s = raise_smem_limit((const void*)k_grid_rhs<double>, sizeof(double2) * 9 * (p->I / 2))) != MLSDC_OK) return s;
+    if ((s = raise_smem_limit((const void*)k_grid_rhs<double>, grid_smem<double>(p->I))) != MLSDC_OK) return s;
     if ((s = raise_smem_limit((const void*)k_synth_rhs<double>, synth_smem<double>(p->R))) != MLSDC_OK) return s;
     return MLSDC_OK;
 }
@@ -134,7 +134,7 @@ mlsdc_status rhs_explicit_f64(sh_plan_t p, const swe_params* prm, const double* 
     }
     if (stage == 1 || stage < 0) {
         MLSDC_LAUNCH("k_grid_rhs<double>",
-                     launch_k(k_grid_rhs<double>, dim3(p->J, b.members), dim3(256), sizeof(double2) * 9 * (p->I / 2),
+                     launch_k(k_grid_rhs<double>, dim3(p->J, b.members), dim3(256), grid_smem<double>(p->I),
                               st, (const double2*)p->d_four_in, p->d_four_out, (const double*)p->d_mu,
                               (const double*)p->d_w, (const double2*)p->d_tw, R, p->I, p->logI, p->J,
                               2.0 * prm->omega, ms));

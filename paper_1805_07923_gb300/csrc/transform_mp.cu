@@ -53,8 +53,7 @@ mlsdc_status mp_init(sh_plan_t p) {
     k_round_c32<<<8, 256>>>(p->d_tw, t.tw32, p->I / 2);
     MLSDC_LAUNCHED("k_round_f32");
     MLSDC_CUDA(cudaDeviceSynchronize());
-    const size_t grid_smem = sizeof(float2) * 9 * (p->I / 2);
-    mlsdc_status rs = raise_smem_limit((const void*)k_grid_rhs<float>, grid_smem);
+    mlsdc_status rs = raise_smem_limit((const void*)k_grid_rhs<float>, grid_smem<float>(p->I));
     if (rs != MLSDC_OK) return rs;
     if (p->precision == MLSDC_TF32 || p->precision == MLSDC_BF16X3) return tc_init(p);
     return MLSDC_OK;
@@ -93,7 +92,7 @@ mlsdc_status rhs_explicit_mp(sh_plan_t p, const swe_params* prm, const double* s
     }
     if (stage == 1 || stage < 0) {
         MLSDC_LAUNCH("k_grid_rhs<float>",
-                     launch_k(k_grid_rhs<float>, dim3(p->J, b.members), dim3(256), sizeof(float2) * 9 * (p->I / 2), st,
+                     launch_k(k_grid_rhs<float>, dim3(p->J, b.members), dim3(256), grid_smem<float>(p->I), st,
                               (const float2*)t.four_in, t.four_out, (const double*)p->d_mu, (const double*)p->d_w,
                               (const float2*)t.tw32, R, p->I, p->logI, p->J, 0.0, ms));
     }
