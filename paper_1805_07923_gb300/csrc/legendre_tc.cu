@@ -212,6 +212,7 @@ struct TcArgs {
     const double* cor;
     const int2* tiles;
     int* err;
+    NodeFuse nf;  // the next node's update, run in the analysis epilogue (nf.on)
 };
 
 // Stage buffers, barriers and tensor memory of one CTA.
@@ -540,6 +541,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_anal(const __grid_constant
         FE[off + k] = f0;
         FE[g.nc + off + k] = f1;
         FE[2 * g.nc + off + k] = f2;
+        if (g.nf.on) node_update_coef(g.nf, g.nc, off + k, (size_t)(b0 + b) * g.nf.ms);
     }
     cta_release(c, tmem, ncols);
 }
@@ -799,9 +801,10 @@ mlsdc_status tc_synth(sh_plan_t p, const double* state, double a, RhsBatch b, cu
 }
 
 mlsdc_status tc_anal(sh_plan_t p, double a, double* FE, const double* state, double two_omega, RhsBatch b,
-                     cudaStream_t st) {
+                     cudaStream_t st, const NodeFuse* nf) {
     TcState* s = st_of(p);
     TcArgs g = base_args(p, s, a, b.members);
+    if (nf) g.nf = *nf;
     g.state = (const double2*)state;
     g.state_ms = b.state_ms;
     g.two_omega = two_omega;

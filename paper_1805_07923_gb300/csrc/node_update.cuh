@@ -1,0 +1,132 @@
+// The per-coefficient SDC node update (Sec. 4.2, Eq.
+// update_equation_sdcq_discrete_form; with tau the coarse-level form, Eq.
+// modified_update_equation_sdcq_discrete_form), the implicit solve and
+// F_I at the new node (Sec. 4.4), as device functions shared by the node
+// kernel (sdc.cu) and the analysis kernels that run the update of the next
+// node in their epilogue (rhs_kernels.cuh, legendre_tc.cu).  All float64.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace mlsdc {
+
+constexpr int kMaxNodes = 9;
+
+struct Phys {
+    double inv_a2, phibar, nu;
+};
+
+// Row m+1 of the SDC matrices for one node update.
+struct NodeRow {
+    double qe[kMaxNodes], qi[kMaxNodes], q[kMaxNodes];
+    double qimm;
+    int m;    // updating node m+1
+    int M;    // nodes 0..M
+};
+
+__device__ __forceinline__ double2 cax(double2 acc, double s, double2 x) {
+    return make_double2(fma(s, x.x, acc.x), fma(s, x.y, acc.y));
+}
+
+// F_I = [ -Phibar delta + nu L Phi', nu L zeta, -L Phi' + nu L delta ], L = -n(n+1)/a^2
+__device__ __forceinline__ void implicit_rhs_coef(double L, const Phys& ph, double2 p, double2 z, double2 d,
+                                                  double2& fp, double2& fz, double2& fd) {
+    const double nl = ph.nu * L;
+    fp = make_double2(-ph.phibar * d.x + nl * p.x, -ph.phibar * d.y + nl * p.y);
+    fz = make_double2(nl * z.x, nl * z.y);
+    fd = make_double2(-L * p.x + nl * d.x, -L * p.y + nl * d.y);
+}
+
+// x - alpha F_I(x) = b, diagonal per coefficient (Sec. 4.4).
+__device__ __forceinline__ void implicit_solve_coef(double L, double alpha, const Phys& ph, double2 bp,
+                                                    double2 bz, double2 bd, double2& p, double2& z,
+                                                    double2& d) {
+    const double c = 1.0 - alpha * ph.nu * L;
+    const double ic = 1.0 / c;
+    const double den = 1.0 / (c * c - alpha * alpha * ph.phibar * L);
+    z = make_double2(bz.x * ic, bz.y * ic);
+    p = make_double2((c * bp.x - alpha * ph.phibar * bd.x) * den, (c * bp.y - alpha * ph.phibar * bd.y) * den);
+    d = make_double2((bd.x - alpha * L * p.x) * ic, (bd.y - alpha * L * p.y) * ic);
+}
+
+// The right-hand side b of the node update at one (field, coefficient)
+// offset o of a member's node arrays ([M+1][3][nc], node = 3 nc):
+//   b = Th[0] + sum_{j=1..m} dt (qE_j (FEn_j - FEo_j) + qI_j (FIn_j - FIo_j))
+//       - dt qI_{m+1,m+1} FIo_{m+1} + sum_{j=0..M} dt q_j (FIo_j + FEo_j) [+ tau_{m+1}]
+__device__ __forceinline__ double2 node_rhs(const double2* Th, const double2* FIo, const double2* FEo,
+                                            const double2* FIn, const double2* FEn, const double2* tau,
+                                            size_t node, size_t o, double dt, const NodeRow& row) {
+    const int m = row.m;
+    double2 acc = Th[o];  // Theta^n (node 0)
+    for (int j = 1; j <= m; ++j) {
+        const size_t oj = j * node + o;
+        const double2 de = make_double2(FEn[oj].x - FEo[oj].x, FEn[oj].y - FEo[oj].y);
+        const double2 di = make_double2(FIn[oj].x - FIo[oj].x, FIn[oj].y - FIo[oj].y);
+        acc = cax(acc, dt * row.qe[j], de);
+        acc = cax(acc, dt * row.qi[j], di);
+    }
+    acc = cax(acc, -dt * row.qimm, FIo[(m + 1) * node + o]);
+    for (int j = 0; j <= row.M; ++j) {
+        const size_t oj = j * node + o;
+        const double2 s = make_double2(FIo[oj].x + FEo[oj].x, FIo[oj].y + FEo[oj].y);
+        acc = cax(acc, dt * row.q[j], s);
+    }
+    if (tau) {
+        const double2 t = tau[(m + 1) * node + o];
+        acc = make_double2(acc.x + t.x, acc.y + t.y);
+    }
+    return acc;
+}
+
+// A node update to run right after an F_E evaluation, at the same
+// coefficients, by the thread that computed them (on = 0: none).  Pointers
+// are member 0's node arrays; member b is ms complex values further on.
+struct NodeFuse {
+    double2* Th;
+    const double2 *FIo, *FEo;
+    double2 *FIn, *FEn;
+    const double2* tau;
+    const int* ndeg;
+    double dt;
+    NodeRow row;
+    Phys ph;
+    size_t ms;
+    int on;
+};
+
+// The whole update of node row.m + 1 at coefficient c of member offset mo:
+// the three fields' right-hand sides, the coupled solve, F_I.  The m = 0
+// update also copies node 0 of the old F arrays into the new ones.
+__device__ __forceinline__ void node_update_coef(const NodeFuse& f, int nc, int c, size_t mo) {
+    const size_t node = (size_t)3 * nc;
+    const double2* Th0 = f.Th + mo;
+    const double2 *FIo = f.FIo + mo, *FEo = f.FEo + mo;
+    const double2 *FIn = f.FIn + mo, *FEn = f.FEn + mo;
+    const double2* tau = f.tau ? f.tau + mo : nullptr;
+    double2 b[3];
+    for (int q = 0; q < 3; ++q) b[q] = node_rhs(Th0, FIo, FEo, FIn, FEn, tau, node, (size_t)q * nc + c, f.dt, f.row);
+    const double n = f.ndeg[c];
+    const double L = -n * (n + 1.0) * f.ph.inv_a2;
+    double2 p, z, d;
+    implicit_solve_coef(L, f.dt * f.row.qimm, f.ph, b[0], b[1], b[2], p, z, d);
+    double2 fp, fz, fd;
+    implicit_rhs_coef(L, f.ph, p, z, d, fp, fz, fd);
+    const size_t om = (f.row.m + 1) * node + c;
+    double2* Th = f.Th + mo;
+    double2* FInw = f.FIn + mo;
+    Th[om] = p;
+    Th[om + nc] = z;
+    Th[om + 2 * nc] = d;
+    FInw[om] = fp;
+    FInw[om + nc] = fz;
+    FInw[om + 2 * nc] = fd;
+    if (f.row.m == 0) {
+        double2* FEnw = f.FEn + mo;
+        for (int q = 0; q < 3; ++q) {
+            FInw[(size_t)q * nc + c] = FIo[(size_t)q * nc + c];
+            FEnw[(size_t)q * nc + c] = FEo[(size_t)q * nc + c];
+        }
+    }
+}
+
+}  // namespace mlsdc

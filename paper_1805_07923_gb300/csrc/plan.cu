@@ -29,6 +29,14 @@ bool pdl_enabled() {
     return on;
 }
 
+bool node_fusion_enabled() {
+    static const bool on = [] {
+        const char* v = std::getenv("MLSDC_FUSE_NODE");
+        return !(v && v[0] == '0');
+    }();
+    return on;
+}
+
 mlsdc_status raise_smem_limit(const void* fn, size_t bytes) {
     static std::mutex mu;
     if (bytes <= 48 * 1024) return MLSDC_OK;

@@ -19,31 +19,6 @@
 namespace mlsdc {
 
 
-__device__ __forceinline__ double2 cax(double2 acc, double s, double2 x) {
-    return make_double2(fma(s, x.x, acc.x), fma(s, x.y, acc.y));
-}
-
-// F_I = [ -Phibar delta + nu L Phi', nu L zeta, -L Phi' + nu L delta ], L = -n(n+1)/a^2
-__device__ __forceinline__ void implicit_rhs_coef(double L, const Phys& ph, double2 p, double2 z, double2 d,
-                                                  double2& fp, double2& fz, double2& fd) {
-    const double nl = ph.nu * L;
-    fp = make_double2(-ph.phibar * d.x + nl * p.x, -ph.phibar * d.y + nl * p.y);
-    fz = make_double2(nl * z.x, nl * z.y);
-    fd = make_double2(-L * p.x + nl * d.x, -L * p.y + nl * d.y);
-}
-
-// x - alpha F_I(x) = b, diagonal per coefficient (Sec. 4.4).
-__device__ __forceinline__ void implicit_solve_coef(double L, double alpha, const Phys& ph, double2 bp,
-                                                    double2 bz, double2 bd, double2& p, double2& z,
-                                                    double2& d) {
-    const double c = 1.0 - alpha * ph.nu * L;
-    const double ic = 1.0 / c;
-    const double den = 1.0 / (c * c - alpha * alpha * ph.phibar * L);
-    z = make_double2(bz.x * ic, bz.y * ic);
-    p = make_double2((c * bp.x - alpha * ph.phibar * bd.x) * den, (c * bp.y - alpha * ph.phibar * bd.y) * den);
-    d = make_double2((bd.x - alpha * L * p.x) * ic, (bd.y - alpha * L * p.y) * ic);
-}
-
 __global__ void k_implicit_rhs(const double2* __restrict__ x, double2* __restrict__ F,
                                const int* __restrict__ ndeg, int nc, Phys ph, size_t ms_x, size_t ms_f) {
     pdl_wait();
@@ -102,27 +77,7 @@ __global__ void __launch_bounds__(3 * kNodeCoefs) k_sweep_node(double2* Th, cons
     const int c = blockIdx.x * kNodeCoefs + cl;
     const bool live = c < nc;
     const size_t o = (size_t)f * nc + c;
-    if (live) {
-        double2 acc = Th[o];  // Theta^n (node 0)
-        for (int j = 1; j <= m; ++j) {
-            const size_t oj = j * node + o;
-            const double2 de = make_double2(FEn[oj].x - FEo[oj].x, FEn[oj].y - FEo[oj].y);
-            const double2 di = make_double2(FIn[oj].x - FIo[oj].x, FIn[oj].y - FIo[oj].y);
-            acc = cax(acc, dt * row.qe[j], de);
-            acc = cax(acc, dt * row.qi[j], di);
-        }
-        acc = cax(acc, -dt * row.qimm, FIo[(m + 1) * node + o]);
-        for (int j = 0; j <= row.M; ++j) {
-            const size_t oj = j * node + o;
-            const double2 s = make_double2(FIo[oj].x + FEo[oj].x, FIo[oj].y + FEo[oj].y);
-            acc = cax(acc, dt * row.q[j], s);
-        }
-        if (tau) {
-            const double2 t = tau[(m + 1) * node + o];
-            acc = make_double2(acc.x + t.x, acc.y + t.y);
-        }
-        sb[f][cl] = acc;
-    }
+    if (live) sb[f][cl] = node_rhs(Th, FIo, FEo, FIn, FEn, tau, node, o, dt, row);
     __syncthreads();
     if (!live) return;
     const double n = ndeg[c];
@@ -364,13 +319,14 @@ namespace mlsdc {
 // F_E at one node of every member (x and FE point at that node of member 0),
 // or, with nodes > 0 on a one-member level, at `nodes` consecutive nodes in
 // one launch per stage (the nodes are the batch).
-static mlsdc_status eval_FE(sdc_level_t L, const double2* x, double2* FE, cudaStream_t st, int nodes = 0) {
+static mlsdc_status eval_FE(sdc_level_t L, const double2* x, double2* FE, cudaStream_t st, int nodes = 0,
+                            const NodeFuse* nf = nullptr) {
     RhsBatch b;
     b.members = nodes > 0 ? nodes : L->members;
     b.state_ms = b.fe_ms = nodes > 0 ? L->node() : L->ms();
     if (L->plan->precision == MLSDC_FP64)
-        return rhs_explicit_f64(L->plan, &L->prm, (const double*)x, (double*)FE, st, &L->launches, -1, b);
-    return rhs_explicit_mp(L->plan, &L->prm, (const double*)x, (double*)FE, st, &L->launches, -1, b);
+        return rhs_explicit_f64(L->plan, &L->prm, (const double*)x, (double*)FE, st, &L->launches, -1, b, nf);
+    return rhs_explicit_mp(L->plan, &L->prm, (const double*)x, (double*)FE, st, &L->launches, -1, b, nf);
 }
 
 static mlsdc_status eval_FI(sdc_level_t L, const double2* x, double2* FI, cudaStream_t st, int nodes = 0) {
@@ -793,7 +749,8 @@ size_t build_mlsdc_ops(mlsdc_t ml, double2* state, double dt, int n_iter, int n_
     return tape;
 }
 
-mlsdc_status run_ops(mlsdc_t ml, const std::vector<Op>& ops, cudaStream_t st, int64_t* launches, double2* tape) {
+mlsdc_status run_ops(mlsdc_t ml, const std::vector<Op>& ops, cudaStream_t st, int64_t* launches, double2* tape,
+                     bool fuse_node) {
     sdc_level_t F = ml->f, C = ml->c;
     const int ncf = F->plan->nc, ncc = C->plan->nc;
     const int nfn = F->n, ncn = C->n;
@@ -809,7 +766,8 @@ mlsdc_status run_ops(mlsdc_t ml, const std::vector<Op>& ops, cudaStream_t st, in
     for (int i = 0; i < ncn * ncn; ++i) fa.Qc[i] = C->Q[i];
     for (int i = 0; i < ncn * nfn; ++i) fa.Pcf[i] = ml->Pcf.a[i];
     mlsdc_status s = MLSDC_OK;
-    for (const Op& o : ops) {
+    for (size_t oi = 0; oi < ops.size(); ++oi) {
+        const Op& o = ops[oi];
         switch (o.k) {
             case OpK::Bcast:
                 s = launch_bcast(o.L, o.p[0], o.p[1], o.n3, o.count, o.ms_src, o.ms_dst, st);
@@ -826,7 +784,29 @@ mlsdc_status run_ops(mlsdc_t ml, const std::vector<Op>& ops, cudaStream_t st, in
                     MLSDC_CUDA(cudaMemcpy2DAsync(tape + o.tape_off, w, o.p[0], o.L->ms() * sizeof(double2), w,
                                                  (size_t)o.L->members, cudaMemcpyDeviceToDevice, st));
                 }
-                s = eval_FE(o.L, o.p[0], o.p[1], st, o.nodes);
+                if (fuse_node && o.nodes == 0 && oi + 1 < ops.size() && ops[oi + 1].k == OpK::Node &&
+                    ops[oi + 1].L == o.L) {
+                    // the next node's update runs in the analysis epilogue, per
+                    // coefficient, right after F_E there (same arithmetic as k_sweep_node)
+                    const Op& n = ops[oi + 1];
+                    NodeFuse nf{};
+                    nf.Th = n.p[0];
+                    nf.FIo = n.p[1];
+                    nf.FEo = n.p[2];
+                    nf.FIn = n.p[3];
+                    nf.FEn = n.p[4];
+                    nf.tau = n.p[5];
+                    nf.ndeg = n.L->plan->d_ndeg;
+                    nf.dt = n.dt;
+                    nf.row = n.row;
+                    nf.ph = phys_of(n.L->prm);
+                    nf.ms = n.L->ms();
+                    nf.on = 1;
+                    s = eval_FE(o.L, o.p[0], o.p[1], st, 0, &nf);
+                    ++oi;
+                } else {
+                    s = eval_FE(o.L, o.p[0], o.p[1], st, o.nodes);
+                }
                 break;
             case OpK::Node:
                 s = launch_node(o.L, o.dt, o.row, o.p[0], o.p[1], o.p[2], o.p[3], o.p[4], o.p[5], st);

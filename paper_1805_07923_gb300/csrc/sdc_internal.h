@@ -10,23 +10,11 @@
 #include <vector>
 
 #include "internal.h"
+#include "node_update.cuh"
 
 namespace mlsdc {
 
-constexpr int kMaxNodes = 9;
 constexpr int kNodeCoefs = 64;  // coefficients per CTA of the node update (3 x 64 threads)
-
-struct Phys {
-    double inv_a2, phibar, nu;
-};
-
-// Row m+1 of the SDC matrices for one node update.
-struct NodeRow {
-    double qe[kMaxNodes], qi[kMaxNodes], q[kMaxNodes];
-    double qimm;
-    int m;    // updating node m+1
-    int M;    // nodes 0..M
-};
 
 // Time interpolation matrix between two node sets (Sec. 4.3.3).
 struct TransferMat {
@@ -73,6 +61,10 @@ struct Op {
 
 inline Phys phys_of(const swe_params& p) { return Phys{1.0 / (p.a * p.a), p.phibar, p.nu}; }
 
+// Whether node updates are fused into the preceding F_E analysis kernel (on
+// unless the environment sets MLSDC_FUSE_NODE=0, e.g. to compare).
+bool node_fusion_enabled();
+
 inline int grid_for(int n) {
     int b = (n + 255) / 256;
     return b < 1 ? 1 : (b > 152 * 8 ? 152 * 8 : b);
@@ -114,7 +106,11 @@ namespace mlsdc {
 size_t build_mlsdc_ops(mlsdc_t ml, double2* state, double dt, int n_iter, int n_c, std::vector<Op>& ops);
 
 // Launch the operations in order on `st`.  With `tape`, each FE operation
-// first copies its input to tape + tape_off.
-mlsdc_status run_ops(mlsdc_t ml, const std::vector<Op>& ops, cudaStream_t st, int64_t* launches, double2* tape);
+// first copies its input to tape + tape_off.  With fuse_node, an FE
+// operation directly followed by a node update on the same level runs that
+// update in its analysis kernel's epilogue (one launch fewer, same
+// arithmetic).
+mlsdc_status run_ops(mlsdc_t ml, const std::vector<Op>& ops, cudaStream_t st, int64_t* launches, double2* tape,
+                     bool fuse_node = node_fusion_enabled());
 
 }  // namespace mlsdc

@@ -122,17 +122,30 @@ for prec in ("fp64", "bf16x3"):
         M.mlsdc_step(ml, x, 300.0, 4, 2, use_graph=True)
     torch.cuda.synchronize()
     out[prec] = x.cpu().numpy().view(np.float64).tolist()
+# three ensemble members in lockstep (member-batched kernels)
+pf, pc = M.Plan(42, 128, 64, "fp32", 3), M.Plan(21, 64, 32, "fp32", 3)
+ml = M.MLSDC(M.Level(pf, 5, members=3), M.Level(pc, 3, members=3))
+base = inputs.initial_state(42)
+x = torch.from_numpy(np.stack([inputs.perturbed_member(base, 42, 42, k) for k in range(3)])).cuda()
+for _ in range(2):
+    M.mlsdc_step(ml, x, 300.0, 3, 2, use_graph=False)
+torch.cuda.synchronize()
+out["ens_fp32"] = x.cpu().numpy().view(np.float64).tolist()
 print(json.dumps(out))
 """
 
 
-def test_programmatic_dependent_launch_does_not_change_results():
+def test_launch_modes_do_not_change_results():
+    """Programmatic dependent launch (MLSDC_PDL=1) and fusing each node update
+    into the preceding analysis kernel (on unless MLSDC_FUSE_NODE=0) change
+    only how the same arithmetic is launched: results are bitwise equal."""
     res = {}
-    for pdl in ("1", "0"):
-        env = dict(os.environ, MLSDC_PDL=pdl)
+    for name, env_add in (("default", {}), ("pdl", {"MLSDC_PDL": "1"}), ("unfused", {"MLSDC_FUSE_NODE": "0"})):
+        env = dict(os.environ, **env_add)
         r = subprocess.run([sys.executable, "-c", _CHILD, ROOT], env=env, capture_output=True, text=True,
                            timeout=600)
         assert r.returncode == 0, r.stderr[-2000:]
-        res[pdl] = json.loads(r.stdout.strip().splitlines()[-1])
-    for prec in ("fp64", "bf16x3"):
-        assert np.array_equal(np.array(res["1"][prec]), np.array(res["0"][prec])), prec
+        res[name] = json.loads(r.stdout.strip().splitlines()[-1])
+    for name in ("pdl", "unfused"):
+        for key in ("fp64", "bf16x3", "ens_fp32"):
+            assert np.array_equal(np.array(res[name][key]), np.array(res["default"][key])), (name, key)
