@@ -450,15 +450,24 @@ __global__ void k_restrict_ad(double2* __restrict__ Tfb, double2* __restrict__ T
 
 // transpose of tau[i] = Tc[i] - dt sum_l Qc[i][l] (FIc+FEc)[l] - sum_j Pcf[i][j] Af[j],
 // Af[j] = Tf[j] - dt sum_l Qf[j][l] (FIf+FEf)[l]  (fine values at the coarse modes)
+// and of the saved copies Ts, FIs, FEs = Tc, FIc, FEc made in the same pass
 __global__ void k_fas_ad(double2* __restrict__ Tfb, double2* __restrict__ FIfb, double2* __restrict__ FEfb,
                          double2* __restrict__ Tcb, double2* __restrict__ FIcb, double2* __restrict__ FEcb,
-                         double2* __restrict__ taub, const int* __restrict__ c2f, int ncf, int ncc, double dt,
+                         double2* __restrict__ taub, double2* __restrict__ Tsb, double2* __restrict__ FIsb,
+                         double2* __restrict__ FEsb, const int* __restrict__ c2f, int ncf, int ncc, double dt,
                          FasArgs A) {
     const int total = 3 * ncc;
     const size_t nf3 = (size_t)3 * ncf, nc3 = (size_t)3 * ncc;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
         const int f = t / ncc, k = t - f * ncc;
         const size_t of = (size_t)f * ncf + c2f[k];
+        for (int i = 0; i < A.ncn; ++i) {
+            const size_t oc = i * nc3 + t;
+            Tcb[oc] = cadd(Tcb[oc], Tsb[oc]);
+            FIcb[oc] = cadd(FIcb[oc], FIsb[oc]);
+            FEcb[oc] = cadd(FEcb[oc], FEsb[oc]);
+            Tsb[oc] = FIsb[oc] = FEsb[oc] = make_double2(0.0, 0.0);
+        }
         double2 tb[kMaxNodes], Afb[kMaxNodes];
         for (int i = 0; i < A.ncn; ++i) {
             tb[i] = taub[i * nc3 + t];
@@ -591,7 +600,7 @@ double2* adj_of(mlsdc_adjoint_t A, const double2* p) {
 
 mlsdc_status check_op_ptrs(mlsdc_adjoint_t A) {
     for (const Op& o : A->ops) {
-        const int np = o.k == OpK::Node ? 6 : o.k == OpK::Fas ? 7 : o.k == OpK::Interp ? 9 : 2;
+        const int np = o.k == OpK::Node ? 6 : o.k == OpK::Fas ? 10 : o.k == OpK::Interp ? 9 : 2;
         for (int i = 0; i < np; ++i)
             if (o.p[i] && !adj_of(A, o.p[i])) {
                 set_error_text("mlsdc_adjoint: an operand has no adjoint buffer");
@@ -667,7 +676,8 @@ mlsdc_status reverse_step(mlsdc_adjoint_t A, const double2* tape, cudaStream_t s
             case OpK::Fas:
                 k_fas_ad<<<gt, 256, 0, st>>>(adj_of(A, o.p[0]), adj_of(A, o.p[1]), adj_of(A, o.p[2]),
                                             adj_of(A, o.p[3]), adj_of(A, o.p[4]), adj_of(A, o.p[5]),
-                                            adj_of(A, o.p[6]), ml->d_c2f, ncf, ncc, o.dt, fa);
+                                            adj_of(A, o.p[6]), adj_of(A, o.p[7]), adj_of(A, o.p[8]),
+                                            adj_of(A, o.p[9]), ml->d_c2f, ncf, ncc, o.dt, fa);
                 MLSDC_LAUNCHED("k_fas_ad");
                 break;
             case OpK::Interp:

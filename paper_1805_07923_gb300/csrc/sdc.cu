@@ -132,11 +132,14 @@ __global__ void k_restrict(const double2* __restrict__ Tf, double2* __restrict__
 
 
 // tau_c = A_c(R Theta_f) - R A_f(Theta_f), A(Theta) = Theta - dt (Q x I) F
-// (Eq. tau_term_level_l+1 with tau_f = 0; Eq. collocation_problem).
+// (Eq. tau_term_level_l+1 with tau_f = 0; Eq. collocation_problem).  The
+// same pass saves the restricted coarse values Theta_c, F_I,c, F_E,c
+// (Algorithm 1 step B) into Ts, FIs, FEs for step D.
 __global__ void k_fas_tau(const double2* __restrict__ Tf, const double2* __restrict__ FIf,
                           const double2* __restrict__ FEf, const double2* __restrict__ Tc,
                           const double2* __restrict__ FIc, const double2* __restrict__ FEc,
-                          double2* __restrict__ tau, const int* __restrict__ c2f, int ncf, int ncc,
+                          double2* __restrict__ tau, double2* __restrict__ Ts, double2* __restrict__ FIs,
+                          double2* __restrict__ FEs, const int* __restrict__ c2f, int ncf, int ncc,
                           double dt, FasArgs A, size_t msf, size_t msc) {
     pdl_wait();
     pdl_launch();
@@ -148,6 +151,9 @@ __global__ void k_fas_tau(const double2* __restrict__ Tf, const double2* __restr
     FIc += oc_m;
     FEc += oc_m;
     tau += oc_m;
+    Ts += oc_m;
+    FIs += oc_m;
+    FEs += oc_m;
     const int total = 3 * ncc;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
         const int f = t / ncc, k = t - f * ncc;
@@ -162,6 +168,11 @@ __global__ void k_fas_tau(const double2* __restrict__ Tf, const double2* __restr
                 acc = cax(acc, -dt * A.Qf[j * A.nfn + l], s);
             }
             Af[j] = acc;
+        }
+        for (int i = 0; i < A.ncn; ++i) {
+            Ts[i * nc3 + t] = Tc[i * nc3 + t];
+            FIs[i * nc3 + t] = FIc[i * nc3 + t];
+            FEs[i * nc3 + t] = FEc[i * nc3 + t];
         }
         for (int i = 0; i < A.ncn; ++i) {
             double2 acc = Tc[i * nc3 + t];
@@ -682,14 +693,6 @@ size_t build_mlsdc_ops(mlsdc_t ml, double2* state, double dt, int n_iter, int n_
         o.i1 = i1;
         ops.push_back(o);
     };
-    auto copy = [&](double2* dst, const double2* src, size_t bytes) {
-        Op o{OpK::Copy};
-        o.L = C;
-        o.p[0] = const_cast<double2*>(src);
-        o.p[1] = dst;
-        o.bytes = bytes;
-        ops.push_back(o);
-    };
     int cf = F->cur, cc = C->cur;
     // initialisation: fine spread; coarse node 0 = restriction of Theta^n, evaluated once
     bcast(F, state, F->Th, nfn, nodef);
@@ -717,15 +720,13 @@ size_t build_mlsdc_ops(mlsdc_t ml, double2* state, double dt, int n_iter, int n_
                 fe(C, C->Th + i * nodec, C->FE[cc] + i * nodec);
             }
         }
-        const size_t bytes = (size_t)B * C->ms() * sizeof(double2);
-        copy(ml->Ts, C->Th, bytes);
-        copy(ml->FIs, C->FI[cc], bytes);
-        copy(ml->FEs, C->FE[cc], bytes);
-        // C) FAS correction, coarse sweeps
+        // C) FAS correction (its pass also saves the restricted values of
+        // step B), coarse sweeps
         Op fa{OpK::Fas};
         fa.L = C;
-        double2* fas[7] = {F->Th, F->FI[cf], F->FE[cf], C->Th, C->FI[cc], C->FE[cc], ml->tau};
-        std::copy(fas, fas + 7, fa.p);
+        double2* fas[10] = {F->Th, F->FI[cf], F->FE[cf], C->Th, C->FI[cc], C->FE[cc], ml->tau,
+                            ml->Ts, ml->FIs, ml->FEs};
+        std::copy(fas, fas + 10, fa.p);
         fa.dt = dt;
         ops.push_back(fa);
         for (int k = 0; k < n_c; ++k) {
@@ -822,8 +823,8 @@ mlsdc_status run_ops(mlsdc_t ml, const std::vector<Op>& ops, cudaStream_t st, in
                 break;
             case OpK::Fas:
                 MLSDC_LAUNCH("k_fas_tau", launch_k(k_fas_tau, gt, dim3(256), 0, st, o.p[0], o.p[1], o.p[2], o.p[3],
-                                                   o.p[4], o.p[5], o.p[6], (const int*)ml->d_c2f, ncf, ncc, o.dt,
-                                                   fa, msf, msc));
+                                                   o.p[4], o.p[5], o.p[6], o.p[7], o.p[8], o.p[9],
+                                                   (const int*)ml->d_c2f, ncf, ncc, o.dt, fa, msf, msc));
                 own++;
                 break;
             case OpK::Interp:

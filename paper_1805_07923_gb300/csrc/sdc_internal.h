@@ -39,7 +39,7 @@ enum class OpK : int {
     Node,      // k_sweep_node: node m+1 update, solve, F_I     (p: Th FIo FEo FIn FEn tau)
     Restrict,  // coarse p[1][i] = D(sum_j Pcf[i][j] p[0][j]), i in [i0, i1)
     Copy,      // p[1] = p[0], `bytes` bytes
-    Fas,       // tau (p[6]) from fine (p[0..2]) and coarse (p[3..5]) nodes
+    Fas,       // tau (p[6]) from fine (p[0..2]) and coarse (p[3..5]) nodes; saves p[3..5] to p[7..9]
     Interp,    // fine p[0..2] += P(Pfc (coarse p[3..5] - saved p[6..8]))
     CopyLast,  // p[1] (the state) = last fine node p[0], every member
 };
@@ -47,7 +47,7 @@ enum class OpK : int {
 struct Op {
     OpK k;
     sdc_level_t L = nullptr;         // the level the operation runs on
-    double2* p[9] = {};              // operands, by kind (above)
+    double2* p[10] = {};             // operands, by kind (above)
     int n3 = 0, count = 0;           // Bcast
     size_t ms_src = 0, ms_dst = 0;   // Bcast member strides
     int i0 = 0, i1 = 0;              // Restrict
@@ -61,8 +61,8 @@ struct Op {
 
 inline Phys phys_of(const swe_params& p) { return Phys{1.0 / (p.a * p.a), p.phibar, p.nu}; }
 
-// Whether node updates are fused into the preceding F_E analysis kernel (on
-// unless the environment sets MLSDC_FUSE_NODE=0, e.g. to compare).
+// Whether node updates are fused into the preceding F_E analysis kernel (off
+// unless the environment sets MLSDC_FUSE_NODE=1).
 bool node_fusion_enabled();
 
 inline int grid_for(int n) {

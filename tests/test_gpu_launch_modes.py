@@ -137,15 +137,15 @@ print(json.dumps(out))
 
 def test_launch_modes_do_not_change_results():
     """Programmatic dependent launch (MLSDC_PDL=1) and fusing each node update
-    into the preceding analysis kernel (on unless MLSDC_FUSE_NODE=0) change
-    only how the same arithmetic is launched: results are bitwise equal."""
+    into the preceding analysis kernel (MLSDC_FUSE_NODE=1) change only how
+    the same arithmetic is launched: results are bitwise equal."""
     res = {}
-    for name, env_add in (("default", {}), ("pdl", {"MLSDC_PDL": "1"}), ("unfused", {"MLSDC_FUSE_NODE": "0"})):
+    for name, env_add in (("default", {}), ("pdl", {"MLSDC_PDL": "1"}), ("fused", {"MLSDC_FUSE_NODE": "1"})):
         env = dict(os.environ, **env_add)
         r = subprocess.run([sys.executable, "-c", _CHILD, ROOT], env=env, capture_output=True, text=True,
                            timeout=600)
         assert r.returncode == 0, r.stderr[-2000:]
         res[name] = json.loads(r.stdout.strip().splitlines()[-1])
-    for name in ("pdl", "unfused"):
+    for name in ("pdl", "fused"):
         for key in ("fp64", "bf16x3", "ens_fp32"):
             assert np.array_equal(np.array(res[name][key]), np.array(res["default"][key])), (name, key)
