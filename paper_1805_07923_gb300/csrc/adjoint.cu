@@ -157,20 +157,21 @@ __global__ void __launch_bounds__(256) k_grid_ad(const double2* __restrict__ fou
     double2* sx = reinterpret_cast<double2*>(smem_raw);  // [9][I/2], then [I/2] twiddles
     const int j = blockIdx.x;
     const int Hn = I >> 1, logH = logI - 1;
-    double2* stw = sx + 9 * Hn;
-    for (int k = threadIdx.x; k < Hn; k += blockDim.x) stw[k] = tw[k];
+    double2* stab = sx + 9 * Hn;
+    fft4_stage_twiddles(stab, tw, Hn, logH, I);
     const size_t fs = (size_t)J * (R + 1);
     for (int t = threadIdx.x; t < 9 * Hn; t += blockDim.x) {
         const int f = t >> logH, k = t & (Hn - 1);
-        sx[f * Hn + k] = irfft_pack(four_in + f * fs + (size_t)j * (R + 1), k, R, Hn, tw);
+        sx[f * Hn + swz(k)] = irfft_pack(four_in + f * fs + (size_t)j * (R + 1), k, R, Hn, tw);
     }
     __syncthreads();
-    fft4_dif(sx, 9, Hn, logH, stw, I, true);
+    fft4_dif(sx, 9, Hn, logH, stab, true);
     const double muj = mu[j];
     const double f = two_omega * muj;
     const double rc = 1.0 / (1.0 - muj * muj);
     const double sAD = w[j] * rc / I, sE = w[j] / I;
-    for (int q = threadIdx.x; q < Hn; q += blockDim.x) {
+    for (int q0 = threadIdx.x; q0 < Hn; q0 += blockDim.x) {
+        const int q = swz(q0);
         double2 v9[9];
         for (int k = 0; k < 9; ++k) v9[k] = sx[k * Hn + q];
         // .x and .y are two longitudes of one packed pair: pointwise in both
@@ -190,11 +191,11 @@ __global__ void __launch_bounds__(256) k_grid_ad(const double2* __restrict__ fou
         for (int k = 0; k < 4; ++k) sx[k * Hn + q] = make_double2(o[k][0], o[k][1]);
     }
     __syncthreads();
-    fft4_dit(sx, 4, Hn, logH, stw, I, false);
+    fft4_dit(sx, 4, Hn, logH, stab, false);
     for (int t = threadIdx.x; t < 4 * (R + 1); t += blockDim.x) {
         const int fld = t / (R + 1);
         const int m = t - fld * (R + 1);
-        const double2 X = rfft_unpack(sx + fld * Hn, m, Hn, tw);
+        const double2 X = rfft_unpack_sw(sx + fld * Hn, m, Hn, tw);
         four_out[(size_t)fld * fs + (size_t)j * (R + 1) + m] = cscale(X, m == 0 ? 1.0 : 2.0);
     }
 }

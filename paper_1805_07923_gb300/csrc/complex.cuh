@@ -92,12 +92,24 @@ __device__ void fft_dif(C* x, int narr, int Hn, int logH, const C* __restrict__ 
 // base-4 digit-reversed order of its stages, fft4_dit takes that order back
 // to natural order, so the two compose with any pointwise stage between them
 // exactly as the radix-2 pair does, in half the barriers.  N = I/2 complex
-// points per array, `narr` arrays back to back; tw[k] = exp(-2 pi i k / I)
-// for k < I/2 (shared or global memory), exp(-2 pi i k / I) = -tw[k - I/2]
-// above.  DIF stage of span L (quarter Q = L/4), butterfly (a, b, c, d) at
-// (i0, i0 + Q, i0 + 2Q, i0 + 3Q), s = -i (forward) or +i (inverse):
+// points per array, `narr` arrays back to back.  DIF stage of span L
+// (quarter Q = L/4), butterfly (a, b, c, d) at (i0, i0 + Q, i0 + 2Q, i0 + 3Q),
+// s = -i (forward) or +i (inverse):
 //   (a + c) + (b + d),  [(a - c) + s (b - d)] w^j,  [(a + c) - (b + d)] w^2j,  [(a - c) - s (b - d)] w^3j
 // with w = exp(-/+ 2 pi i / L); the DIT stage applies the twiddles first.
+//
+// Storage: element a of an array sits at swz(a), an XOR swizzle inside each
+// aligned group of 16 that spreads every stage's access pattern (runs of
+// 16 consecutive indices, or groups of 4 at strides 4 and 16) over distinct
+// shared-memory banks; every access of these arrays goes through swz.
+// Twiddles come from a per-stage table (fft4_stage_twiddles) laid out
+// [radix-2 stage: w^2j, j < N/2][each radix-4 stage of span L, largest
+// first: w^j, w^2j, w^3j for j < L/4], N - 1 entries, so a stage reads
+// consecutive entries.
+__device__ __forceinline__ int swz(int a) {
+    const int s = (a >> 4) & 3;
+    return a ^ (s | (s << 2));
+}
 template <class C> __device__ __forceinline__ C tw_at(const C* tw, int k, int half) {
     if (k < half) return tw[k];
     const C w = tw[k - half];
@@ -108,62 +120,89 @@ template <class C> __device__ __forceinline__ C times_s(C z, bool inverse) {  //
 }
 template <class C> __device__ __forceinline__ C maybe_conj(C w, bool inverse) { return inverse ? cconj(w) : w; }
 
+// Fill the stage table (N - 1 entries) from tw[k] = exp(-2 pi i k / I),
+// k < I/2 (any memory space); the caller synchronises before use.
 template <class C>
-__device__ void fft4_dif(C* x, int narr, int N, int logN, const C* tw, int I, bool inverse) {
+__device__ void fft4_stage_twiddles(C* tab, const C* __restrict__ tw, int N, int logN, int I) {
     const int half = I >> 1;
-    int L = N, logL = logN;
+    int off = 0;
+    if (logN & 1) {
+        const int H = N >> 1;
+        for (int j = threadIdx.x; j < H; j += blockDim.x) tab[j] = tw[2 * j];
+        off = H;
+    }
+    for (int logL = (logN & 1) ? logN - 1 : logN; logL >= 2; logL -= 2) {
+        const int Q = 1 << (logL - 2), st = I >> logL;
+        for (int e = threadIdx.x; e < 3 * Q; e += blockDim.x) {
+            const int q = e / Q + 1, j = e - (q - 1) * Q;
+            tab[off + e] = tw_at(tw, q * j * st, half);
+        }
+        off += 3 * Q;
+    }
+}
+
+template <class C>
+__device__ void fft4_dif(C* x, int narr, int N, int logN, const C* tab, bool inverse) {
+    int L = N, logL = logN, off = 0;
     if (logN & 1) {
         const int H = N >> 1;
         for (int t = threadIdx.x; t < narr * H; t += blockDim.x) {
             const int ar = t >> (logN - 1), j = t & (H - 1);
             C* xa = x + ar * N;
-            const C w = maybe_conj(tw[2 * j], inverse);
-            const C u = xa[j], v = xa[j + H];
-            xa[j] = cadd(u, v);
-            xa[j + H] = cmul(csub(u, v), w);
+            const C w = maybe_conj(tab[j], inverse);
+            const C u = xa[swz(j)], v = xa[swz(j + H)];
+            xa[swz(j)] = cadd(u, v);
+            xa[swz(j + H)] = cmul(csub(u, v), w);
         }
         __syncthreads();
+        off = H;
         L >>= 1;
         --logL;
     }
     for (; L >= 4; L >>= 2, logL -= 2) {
         const int Q = L >> 2, logQ = logL - 2;
-        const int st = I >> logL;
+        const C* tq = tab + off;
         for (int t = threadIdx.x; t < narr * (N >> 2); t += blockDim.x) {
             const int ar = t >> (logN - 2), r = t & ((N >> 2) - 1);
             const int g = r >> logQ, j = r & (Q - 1);
-            C* xa = x + ar * N + g * L + j;
-            const C a = xa[0], b = xa[Q], c = xa[2 * Q], d = xa[3 * Q];
+            C* xa = x + ar * N;
+            const int i0 = g * L + j;
+            const C a = xa[swz(i0)], b = xa[swz(i0 + Q)], c = xa[swz(i0 + 2 * Q)], d = xa[swz(i0 + 3 * Q)];
             const C apc = cadd(a, c), amc = csub(a, c), bpd = cadd(b, d), sbmd = times_s(csub(b, d), inverse);
-            xa[0] = cadd(apc, bpd);
-            xa[Q] = cmul(cadd(amc, sbmd), maybe_conj(tw_at(tw, j * st, half), inverse));
-            xa[2 * Q] = cmul(csub(apc, bpd), maybe_conj(tw_at(tw, 2 * j * st, half), inverse));
-            xa[3 * Q] = cmul(csub(amc, sbmd), maybe_conj(tw_at(tw, 3 * j * st, half), inverse));
+            xa[swz(i0)] = cadd(apc, bpd);
+            xa[swz(i0 + Q)] = cmul(cadd(amc, sbmd), maybe_conj(tq[j], inverse));
+            xa[swz(i0 + 2 * Q)] = cmul(csub(apc, bpd), maybe_conj(tq[Q + j], inverse));
+            xa[swz(i0 + 3 * Q)] = cmul(csub(amc, sbmd), maybe_conj(tq[2 * Q + j], inverse));
         }
         __syncthreads();
+        off += 3 * Q;
     }
 }
 
 template <class C>
-__device__ void fft4_dit(C* x, int narr, int N, int logN, const C* tw, int I, bool inverse) {
-    const int half = I >> 1;
+__device__ void fft4_dit(C* x, int narr, int N, int logN, const C* tab, bool inverse) {
     const int top = (logN & 1) ? logN - 1 : logN;
+    const int r2 = (logN & 1) ? (N >> 1) : 0;  // entries of the radix-2 stage
     for (int logL = 2; logL <= top; logL += 2) {
         const int L = 1 << logL, Q = L >> 2, logQ = logL - 2;
-        const int st = I >> logL;
+        // the table holds the radix-4 stages largest first: skip the larger spans
+        int off = r2;
+        for (int l2 = top; l2 > logL; l2 -= 2) off += 3 * (1 << (l2 - 2));
+        const C* tq = tab + off;
         for (int t = threadIdx.x; t < narr * (N >> 2); t += blockDim.x) {
             const int ar = t >> (logN - 2), r = t & ((N >> 2) - 1);
             const int g = r >> logQ, j = r & (Q - 1);
-            C* xa = x + ar * N + g * L + j;
-            const C a = xa[0];
-            const C b = cmul(xa[Q], maybe_conj(tw_at(tw, j * st, half), inverse));
-            const C c = cmul(xa[2 * Q], maybe_conj(tw_at(tw, 2 * j * st, half), inverse));
-            const C d = cmul(xa[3 * Q], maybe_conj(tw_at(tw, 3 * j * st, half), inverse));
+            C* xa = x + ar * N;
+            const int i0 = g * L + j;
+            const C a = xa[swz(i0)];
+            const C b = cmul(xa[swz(i0 + Q)], maybe_conj(tq[j], inverse));
+            const C c = cmul(xa[swz(i0 + 2 * Q)], maybe_conj(tq[Q + j], inverse));
+            const C d = cmul(xa[swz(i0 + 3 * Q)], maybe_conj(tq[2 * Q + j], inverse));
             const C apc = cadd(a, c), amc = csub(a, c), bpd = cadd(b, d), sbmd = times_s(csub(b, d), inverse);
-            xa[0] = cadd(apc, bpd);
-            xa[Q] = cadd(amc, sbmd);
-            xa[2 * Q] = csub(apc, bpd);
-            xa[3 * Q] = csub(amc, sbmd);
+            xa[swz(i0)] = cadd(apc, bpd);
+            xa[swz(i0 + Q)] = cadd(amc, sbmd);
+            xa[swz(i0 + 2 * Q)] = csub(apc, bpd);
+            xa[swz(i0 + 3 * Q)] = csub(amc, sbmd);
         }
         __syncthreads();
     }
@@ -172,10 +211,10 @@ __device__ void fft4_dit(C* x, int narr, int N, int logN, const C* tw, int I, bo
         for (int t = threadIdx.x; t < narr * H; t += blockDim.x) {
             const int ar = t >> (logN - 1), j = t & (H - 1);
             C* xa = x + ar * N;
-            const C w = maybe_conj(tw[2 * j], inverse);
-            const C u = xa[j], v = cmul(xa[j + H], w);
-            xa[j] = cadd(u, v);
-            xa[j + H] = csub(u, v);
+            const C w = maybe_conj(tab[j], inverse);
+            const C u = xa[swz(j)], v = cmul(xa[swz(j + H)], w);
+            xa[swz(j)] = cadd(u, v);
+            xa[swz(j + H)] = csub(u, v);
         }
         __syncthreads();
     }
@@ -209,6 +248,17 @@ template <class C> __device__ __forceinline__ C rfft_unpack(const C* z, int m, i
     using T = decltype(z[0].x);
     const C Z = z[m];
     const C Zc = cconj(z[(Hn - m) & (Hn - 1)]);
+    const C E = mkc(T(0.5) * (Z.x + Zc.x), T(0.5) * (Z.y + Zc.y));
+    const C dz = csub(Z, Zc);
+    const C O = mkc(T(0.5) * dz.y, T(-0.5) * dz.x);
+    return cadd(E, cmul(__ldg(&tw[m]), O));
+}
+
+// rfft_unpack for an array stored through swz (the fft4 storage).
+template <class C> __device__ __forceinline__ C rfft_unpack_sw(const C* z, int m, int Hn, const C* __restrict__ tw) {
+    using T = decltype(z[0].x);
+    const C Z = z[swz(m)];
+    const C Zc = cconj(z[swz((Hn - m) & (Hn - 1))]);
     const C E = mkc(T(0.5) * (Z.x + Zc.x), T(0.5) * (Z.y + Zc.y));
     const C dz = csub(Z, Zc);
     const C O = mkc(T(0.5) * dz.y, T(-0.5) * dz.x);

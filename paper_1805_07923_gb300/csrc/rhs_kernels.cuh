@@ -132,8 +132,8 @@ __global__ void __launch_bounds__(256) k_grid_rhs(const C_t<T>* __restrict__ fou
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* sx = reinterpret_cast<C*>(smem_raw);  // [9][I/2]: zeta, Phi', U, V packed rows, then A..E
     const int Hn = I >> 1, logH = logI - 1;
-    C* stw = sx + 9 * Hn;                     // [I/2] twiddles
-    for (int k = threadIdx.x; k < Hn; k += blockDim.x) stw[k] = tw[k];  // constant table
+    C* stab = sx + 9 * Hn;                    // stage twiddles (I/2 - 1 entries)
+    fft4_stage_twiddles(stab, tw, Hn, logH, I);  // constant table
     pdl_wait();
     pdl_launch();
     four_in += blockIdx.y * ms.four_in;
@@ -142,19 +142,20 @@ __global__ void __launch_bounds__(256) k_grid_rhs(const C_t<T>* __restrict__ fou
     const size_t fs = (size_t)J * (R + 1);
     for (int t = threadIdx.x; t < 4 * Hn; t += blockDim.x) {
         const int f = t >> logH, k = t & (Hn - 1);
-        sx[f * Hn + k] = irfft_pack(four_in + f * fs + (size_t)j * (R + 1), k, R, Hn, tw);
+        sx[f * Hn + swz(k)] = irfft_pack(four_in + f * fs + (size_t)j * (R + 1), k, R, Hn, tw);
     }
     __syncthreads();
     // inverse by decimation in frequency: slot q now holds the longitude pair
     // at the digit-reversed position of q
-    fft4_dif(sx, 4, Hn, logH, stw, I, true);
+    fft4_dif(sx, 4, Hn, logH, stab, true);
     const double muj = mu[j];
     const T f = T(two_omega * muj);
     const T rc = T(1.0 / (1.0 - muj * muj));
     C* y = sx + 4 * Hn;
-    for (int q = threadIdx.x; q < Hn; q += blockDim.x) {
+    for (int q0 = threadIdx.x; q0 < Hn; q0 += blockDim.x) {
         // .x and .y hold the two longitudes of one packed pair; products are
-        // pointwise, so they stay in the same (bit-reversed) slot
+        // pointwise, so they stay in the same (permuted, swizzled) slot
+        const int q = swz(q0);
         const C z = sx[q], p = sx[Hn + q], u = sx[2 * Hn + q], v = sx[3 * Hn + q];
         const T zf0 = z.x + f, zf1 = z.y + f;
         y[q] = mkc(zf0 * u.x, zf1 * u.y);                                        // A
@@ -166,13 +167,13 @@ __global__ void __launch_bounds__(256) k_grid_rhs(const C_t<T>* __restrict__ fou
     }
     __syncthreads();
     // forward by decimation in time from the digit-reversed slots: natural order out
-    fft4_dit(y, 5, Hn, logH, stw, I, false);
+    fft4_dit(y, 5, Hn, logH, stab, false);
     const T sAD = T(w[j] / (1.0 - muj * muj) / I);
     const T sE = T(w[j] / I);
     for (int t = threadIdx.x; t < 5 * (R + 1); t += blockDim.x) {
         const int fld = t / (R + 1);
         const int m = t - fld * (R + 1);
-        const C X = rfft_unpack(y + fld * Hn, m, Hn, tw);
+        const C X = rfft_unpack_sw(y + fld * Hn, m, Hn, tw);
         four_out[(size_t)fld * fs + (size_t)j * (R + 1) + m] = cscale(X, fld < 4 ? sAD : sE);
     }
 }

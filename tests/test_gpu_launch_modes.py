@@ -8,8 +8,10 @@ schedule.
   step is bitwise the unbatched one; the tensor-core kernels pack the entries
   along N of one MMA (equal to 1e-12).  The batched float64 step also matches
   the oracle per step to 1e-12, and its adjoint the oracle's adjoint.
-- Programmatic dependent launch (on by default, MLSDC_PDL=0 switches it off)
-  changes only when kernels start, never what they compute: bitwise equal.
+- Programmatic dependent launch (MLSDC_PDL=1) and fusing each node update
+  into the preceding analysis kernel (MLSDC_FUSE_NODE=1), both off by
+  default, change only how kernels start, never what they compute: bitwise
+  equal.
 """
 import json
 import os
