@@ -161,7 +161,9 @@ __device__ __forceinline__ uint32_t to_tf32(float x) {
 
 // Store one B-operand value (row r of N rows, column k of one K block) in the
 // plain K-major layout: byte offset (k / kc) * lbo + (r / 8) * 128 + (r % 8) * 16
-// + (k % kc) * esz, kc = 16 / esz elements per core-matrix row, lbo = 16 N.
+// + (k % kc) * esz, kc = 16 / esz elements per core-matrix row, lbo = 16 N + 16
+// (lbo_for): the extra 16 bytes shift consecutive K groups by four banks, so a
+// warp writing one column for 32 consecutive k hits distinct banks.
 template <int MODE>
 __device__ __forceinline__ void put_b(unsigned char* hi, unsigned char* lo, int r, int k, float v, uint32_t lbo) {
     if (MODE == MODE_TF32) {
@@ -187,9 +189,13 @@ struct Shape {
 
 // One pipeline stage: the A tiles of one K block, then the B tiles of the
 // two column groups (P, H) for `chunk` members (16 rows each) and each part.
+__host__ __device__ inline uint32_t lbo_for(int N) { return 16u * (uint32_t)N + 16u; }
+// one B tile (8 core-matrix columns along K) for up to `chunk` members
+__host__ __device__ inline size_t btile_bytes(int chunk) { return (size_t)8 * lbo_for(16 * chunk); }
 __host__ __device__ inline size_t stage_bytes(int mode, int chunk) {
     const int nt = mode == MODE_TF32 ? 2 : 4, npart = mode == MODE_TF32 ? 1 : 2;
-    return (size_t)nt * kTileBytes + (size_t)2 * npart * (16 * chunk) * 128;
+    const size_t b = (size_t)nt * kTileBytes + (size_t)2 * npart * btile_bytes(chunk);
+    return (b + 1023) & ~(size_t)1023;  // the next stage's A tiles need 1024-byte alignment (128-byte swizzle)
 }
 __host__ __device__ inline size_t cta_smem_bytes(int mode, int chunk, int stages) {
     return 1024 + (size_t)stages * stage_bytes(mode, chunk) + 128;
@@ -257,7 +263,7 @@ __device__ __forceinline__ unsigned char* a_tile(const Cta& c, int st, int t) {
 template <int MODE>
 __device__ __forceinline__ unsigned char* b_tile(const Cta& c, int st, int grp, int part, int chunk) {
     using S = Shape<MODE>;
-    return c.smem + st * c.stage_sz + (size_t)S::NT * kTileBytes + (size_t)(grp * S::NPART + part) * (16 * chunk) * 128;
+    return c.smem + st * c.stage_sz + (size_t)S::NT * kTileBytes + (size_t)(grp * S::NPART + part) * btile_bytes(chunk);
 }
 
 // Issue the four MMA steps of one K block for both column groups.
@@ -265,7 +271,7 @@ template <int MODE>
 __device__ __forceinline__ void mma_block(const Cta& c, int st, int chunk, uint32_t tmem, int N, uint32_t idesc,
                                           bool first) {
     using S = Shape<MODE>;
-    const uint32_t lbo = 16u * N;
+    const uint32_t lbo = lbo_for(N);
     for (int s = 0; s < S::KB / S::KSTEP; ++s) {
         const uint32_t acc = (!first || s > 0) ? 1u : 0u;
         for (int grp = 0; grp < 2; ++grp) {
@@ -372,7 +378,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_synth(const __grid_constan
     const uint32_t ncols = tmem_cols_for(2 * N);
     const Cta c = cta_setup<MODE>(smem_raw, g.chunk, g.stages, ncols);
     const uint32_t tmem = *c.tslot;
-    const uint32_t lbo = 16u * N;
+    const uint32_t lbo = lbo_for(N);
     const double sa2 = -g.a * g.a;
     auto load_a = [&](int st, int kb) {
         mbar_expect_tx(sa(&c.bars[st]), (uint32_t)(S::NT * kTileBytes));
@@ -461,7 +467,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_anal(const __grid_constant
     const uint32_t ncols = tmem_cols_for(2 * N);
     const Cta c = cta_setup<MODE>(smem_raw, g.chunk, g.stages, ncols);
     const uint32_t tmem = *c.tslot;
-    const uint32_t lbo = 16u * N;
+    const uint32_t lbo = lbo_for(N);
     const int J = 2 * g.J2;
     const size_t fs = (size_t)J * (R + 1);
     auto load_a = [&](int st, int kb) {
