@@ -1,0 +1,61 @@
+"""Run the explicit right-hand side F_E (or its adjoint) of one truncation for
+a batch of members, for profiling one stage kernel in a chosen configuration.
+
+    python -m paper_1805_07923_gb300.profile_rhs --R 170 --nlon 512 --nlat 256 \\
+        --precision bf16x3 --members 16 --reps 3
+
+The plan is created (and, for the tensor-core precisions, autotuned) first;
+the `reps` evaluations that follow run inside the NVTX range
+"mlsdc_profile", so a profiler can select exactly them, e.g.
+ncu --nvtx --nvtx-include "mlsdc_profile/" -k regex:k_tc_anal ...
+Prints the mean stage times measured with CUDA events.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+
+import numpy as np
+import torch
+
+from . import inputs
+from . import mlsdc as M
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--R", type=int, default=170)
+    ap.add_argument("--nlon", type=int, default=512)
+    ap.add_argument("--nlat", type=int, default=256)
+    ap.add_argument("--precision", default="bf16x3", choices=list(M.PRECISIONS))
+    ap.add_argument("--members", type=int, default=1)
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--adjoint", action="store_true", help="the float64 F_E adjoint instead of F_E")
+    a = ap.parse_args(argv)
+    plan = M.Plan(a.R, a.nlon, a.nlat, "fp64" if a.adjoint else a.precision, a.members)
+    prm = M.swe_params()
+    base = inputs.initial_state(a.R)
+    x = torch.from_numpy(np.stack([inputs.perturbed_member(base, a.R, a.R, k) for k in range(a.members)])).cuda()
+    fe = torch.empty_like(x)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("mlsdc_profile")
+    for _ in range(a.reps):
+        if a.adjoint:
+            for b in range(a.members):
+                lam = x[b].clone()
+                M.swe_explicit_rhs_adjoint(plan, prm, x[b], lam, fe[b])
+        else:
+            M.swe_explicit_rhs_batched(plan, prm, x, fe, a.members)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    if a.adjoint:
+        ms = M.mlsdc_profile_rhs_adjoint(plan, prm, x[0], x[0].clone(), fe[0], reps=20)
+    else:
+        ms = M.mlsdc_profile_rhs(plan, prm, x, fe, reps=20, members=a.members)
+    print(json.dumps({"R": a.R, "nlon": a.nlon, "nlat": a.nlat, "precision": a.precision, "members": a.members,
+                      "adjoint": a.adjoint, "stage_ms": ms, "tc_chunk": plan.tc_chunk()
+                      if hasattr(plan, "tc_chunk") else None}))
+
+
+if __name__ == "__main__":
+    main()
