@@ -60,18 +60,20 @@ __global__ void __launch_bounds__(32 * kAdSynthWarps) k_synth_ad(const double2* 
                                                                  const double2* __restrict__ lam,
                                                                  const double* __restrict__ P,
                                                                  const double* __restrict__ H,
+                                                                 const double* __restrict__ invnn,
                                                                  const Chunk* __restrict__ chunks, int R, int J2,
-                                                                 int nc, double a, double2* __restrict__ four) {
+                                                                 int nc, double a, double ia,
+                                                                 double2* __restrict__ four) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double2* sc = reinterpret_cast<double2*>(smem_raw);  // [nm][8], then the reduction
     const Chunk ch = chunks[blockIdx.x];
     const int m = ch.m;
     const int nm = R + 1 - m;
     const int off = m * (R + 1) - m * (m - 1) / 2;
-    const double ia2 = 1.0 / (a * a);
+    const double ia2 = ia * ia;
     for (int k = threadIdx.x; k < nm; k += blockDim.x) {
         const int n = m + k;
-        const double s = n > 0 ? -a * a / (n * (n + 1.0)) : 0.0;
+        const double s = -a * a * invnn[n];  // -a^2/(n(n+1)), 0 for n = 0
         const double2 ph = x[off + k], ze = x[nc + off + k], de = x[2 * nc + off + k];
         double2 lp = lam[off + k], lz = lam[nc + off + k], ld = lam[2 * nc + off + k];
         if (m == 0) lp.y = lz.y = ld.y = 0.0;  // Im of m = 0 is not a degree of freedom
@@ -130,7 +132,7 @@ __global__ void __launch_bounds__(32 * kAdSynthWarps) k_synth_ad(const double2* 
         N[q] = cadd(e, o);
         S[q] = isH[q] ? csub(o, e) : csub(e, o);
     }
-    const double ia = 1.0 / a, dm = (double)m;
+    const double dm = (double)m;
     const double cm = m == 0 ? 1.0 : 0.5;  // transpose of the Hermitian inverse FFT
     const int J = 2 * J2;
     const size_t fs = (size_t)J * (R + 1);
@@ -150,9 +152,8 @@ __global__ void __launch_bounds__(32 * kAdSynthWarps) k_synth_ad(const double2* 
 }
 
 __global__ void __launch_bounds__(256) k_grid_ad(const double2* __restrict__ four_in, double2* __restrict__ four_out,
-                                                 const double* __restrict__ mu, const double* __restrict__ w,
-                                                 const double2* __restrict__ tw, int R, int I, int logI, int J,
-                                                 double two_omega) {
+                                                 const double* __restrict__ lat, const double2* __restrict__ tw,
+                                                 int R, int I, int logI, int J, double two_omega) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double2* sx = reinterpret_cast<double2*>(smem_raw);  // [9][I/2], then [I/2] twiddles
     const int j = blockIdx.x;
@@ -166,10 +167,10 @@ __global__ void __launch_bounds__(256) k_grid_ad(const double2* __restrict__ fou
     }
     __syncthreads();
     fft4_dif(sx, 9, Hn, logH, stab, true);
-    const double muj = mu[j];
-    const double f = two_omega * muj;
-    const double rc = 1.0 / (1.0 - muj * muj);
-    const double sAD = w[j] * rc / I, sE = w[j] / I;
+    // lat[j] = (mu, 1/(1-mu^2), w/((1-mu^2) I), w/I)
+    const double f = two_omega * lat[4 * j];
+    const double rc = lat[4 * j + 1];
+    const double sAD = lat[4 * j + 2], sE = lat[4 * j + 3];
     for (int q0 = threadIdx.x; q0 < Hn; q0 += blockDim.x) {
         const int q = swz(q0);
         double2 v9[9];
@@ -203,9 +204,10 @@ __global__ void __launch_bounds__(256) k_grid_ad(const double2* __restrict__ fou
 __global__ void __launch_bounds__(32 * kAnalWarpsMax) k_anal_ad(const double2* __restrict__ four,
                                                                 const double* __restrict__ P,
                                                                 const double* __restrict__ H,
+                                                                const double* __restrict__ invnn,
                                                                 const Chunk* __restrict__ chunks, int R, int J2,
-                                                                int nc, double a, double2* __restrict__ xb,
-                                                                double2* __restrict__ lam) {
+                                                                int nc, double a, double ia,
+                                                                double2* __restrict__ xb, double2* __restrict__ lam) {
     constexpr int TW = 32;
     __shared__ double2 sG[kAnalWarpsMax][TW][4][2];  // per warp: [lat][zeta_b, Phi_b, U_b, V_b][even, odd]
     __shared__ double2 red[kAnalWarpsMax - 1][6][32];
@@ -267,8 +269,8 @@ __global__ void __launch_bounds__(32 * kAnalWarpsMax) k_anal_ad(const double2* _
         hV = cadd(hV, red[w2 - 1][5][lane]);
     }
     const int n = m + k;
-    const double ia = 1.0 / a, dm = (double)m;
-    const double sn = n > 0 ? -a * a / (n * (n + 1.0)) : 0.0;
+    const double dm = (double)m;
+    const double sn = -a * a * invnn[n];  // -a^2/(n(n+1)), 0 for n = 0
     // psi_b = (1/a)(-H U_b - i m P V_b), chi_b = (1/a)(-i m P U_b + H V_b)
     const double2 psib = cscale(csub(make_double2(-hU.x, -hU.y), cim(dm, aV)), ia);
     const double2 chib = cscale(csub(hV, cim(dm, aU)), ia);
@@ -303,14 +305,14 @@ static mlsdc_status fe_adjoint(sh_plan_t p, const swe_params* prm, const double2
                                cudaStream_t st, int64_t* launches) {
     const int R = p->R;
     const size_t ss = synth_ad_smem(R), gs = grid_ad_smem(p->I);
-    k_synth_ad<<<p->n_synth, 32 * kAdSynthWarps, ss, st>>>(x, lam, p->d_P, p->d_H, p->d_synth, R, p->J2, p->nc,
-                                                          prm->a, p->d_four_in);
+    k_synth_ad<<<p->n_synth, 32 * kAdSynthWarps, ss, st>>>(x, lam, p->d_P, p->d_H, p->d_invnn, p->d_synth, R, p->J2,
+                                                          p->nc, prm->a, 1.0 / prm->a, p->d_four_in);
     MLSDC_LAUNCHED("k_synth_ad");
-    k_grid_ad<<<p->J, 256, gs, st>>>(p->d_four_in, p->d_four_out, p->d_mu, p->d_w, p->d_tw, R, p->I, p->logI, p->J,
+    k_grid_ad<<<p->J, 256, gs, st>>>(p->d_four_in, p->d_four_out, p->d_lat, p->d_tw, R, p->I, p->logI, p->J,
                                      2.0 * prm->omega);
     MLSDC_LAUNCHED("k_grid_ad");
-    k_anal_ad<<<p->n_anal, 32 * anal_warps(p->J2), 0, st>>>(p->d_four_out, p->d_P, p->d_H, p->d_anal, R, p->J2,
-                                                           p->nc, prm->a, xb, lam);
+    k_anal_ad<<<p->n_anal, 32 * anal_warps(p->J2), 0, st>>>(p->d_four_out, p->d_P, p->d_H, p->d_invnn, p->d_anal, R,
+                                                           p->J2, p->nc, prm->a, 1.0 / prm->a, xb, lam);
     MLSDC_LAUNCHED("k_anal_ad");
     if (launches) *launches += 3;
     return MLSDC_OK;
@@ -923,14 +925,15 @@ extern "C" mlsdc_status mlsdc_profile_rhs_adjoint(sh_plan_t p, const swe_params*
     double2* xb = (double2*)state_bar;
     auto stage = [&](int k) -> mlsdc_status {
         if (k == 0)
-            k_synth_ad<<<p->n_synth, 32 * kAdSynthWarps, ss, st>>>(x, lam, p->d_P, p->d_H, p->d_synth, R, p->J2,
-                                                                  p->nc, prm->a, p->d_four_in);
+            k_synth_ad<<<p->n_synth, 32 * kAdSynthWarps, ss, st>>>(x, lam, p->d_P, p->d_H, p->d_invnn, p->d_synth, R,
+                                                                  p->J2, p->nc, prm->a, 1.0 / prm->a, p->d_four_in);
         else if (k == 1)
-            k_grid_ad<<<p->J, 256, gs, st>>>(p->d_four_in, p->d_four_out, p->d_mu, p->d_w, p->d_tw, R, p->I,
-                                             p->logI, p->J, 2.0 * prm->omega);
+            k_grid_ad<<<p->J, 256, gs, st>>>(p->d_four_in, p->d_four_out, p->d_lat, p->d_tw, R, p->I, p->logI, p->J,
+                                             2.0 * prm->omega);
         else
-            k_anal_ad<<<p->n_anal, 32 * anal_warps(p->J2), 0, st>>>(p->d_four_out, p->d_P, p->d_H, p->d_anal, R,
-                                                                   p->J2, p->nc, prm->a, xb, lam);
+            k_anal_ad<<<p->n_anal, 32 * anal_warps(p->J2), 0, st>>>(p->d_four_out, p->d_P, p->d_H, p->d_invnn,
+                                                                   p->d_anal, R, p->J2, p->nc, prm->a, 1.0 / prm->a,
+                                                                   xb, lam);
         MLSDC_LAUNCHED("profile_rhs_adjoint");
         return MLSDC_OK;
     };

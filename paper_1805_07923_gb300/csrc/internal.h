@@ -98,6 +98,8 @@ struct MPTables {
     float2* tw32 = nullptr;      // [I/2] float32 twiddles
     float2* four_in = nullptr;   // [4][J][R+1]
     float2* four_out = nullptr;  // [5][J][R+1]
+    float* lat32 = nullptr;      // [J][4] float32 copy of the plan's d_lat
+    float* invnn32 = nullptr;    // [R+1] float32 copy of d_invnn
     // tensor-core state (legendre_tc.cu): operand tables, tensor maps, error flag
     void* tc = nullptr;
     int64_t tc_bytes = 0;
@@ -117,6 +119,10 @@ struct sh_plan_s {
     double2* d_tw = nullptr;          // [I/2] exp(-2 pi i k / I)
     int* d_ndeg = nullptr;            // [nc] total degree n of each coefficient
     double* d_cor = nullptr;          // [nc][5] Coriolis recurrence factors (coriolis_linear)
+    // Per-latitude and per-degree constants, computed on the host in float64
+    // so no kernel divides in float64 (about 1/64 of the float32 rate here):
+    double* d_lat = nullptr;          // [J][4] mu, 1/(1-mu^2), w/((1-mu^2) I), w/I
+    double* d_invnn = nullptr;        // [R+1] 1/(n(n+1)), 0 for n = 0
     mlsdc::Chunk* d_synth = nullptr;  // synthesis work items, largest first
     mlsdc::Chunk* d_anal = nullptr;   // analysis work items, largest first
     int n_synth = 0, n_anal = 0;

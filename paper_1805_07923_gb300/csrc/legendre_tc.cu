@@ -219,6 +219,10 @@ struct TcArgs {
     const int2* tiles;
     int* err;
     NodeFuse nf;  // the next node's update, run in the analysis epilogue (nf.on)
+    // host-computed constants (no float64 division in the kernels)
+    double ia, a2, c_cor;    // 1/a, a^2, 2 Omega / a^2
+    float ia_f, na2_f;       // 1/a, -a^2
+    const float* invnn;      // [R+1] 1/(n(n+1)), 0 for n = 0
 };
 
 // Stage buffers, barriers and tensor memory of one CTA.
@@ -379,7 +383,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_synth(const __grid_constan
     const Cta c = cta_setup<MODE>(smem_raw, g.chunk, g.stages, ncols);
     const uint32_t tmem = *c.tslot;
     const uint32_t lbo = lbo_for(N);
-    const double sa2 = -g.a * g.a;
     auto load_a = [&](int st, int kb) {
         mbar_expect_tx(sa(&c.bars[st]), (uint32_t)(S::NT * kTileBytes));
         for (int t = 0; t < S::NT; ++t)
@@ -397,14 +400,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_synth(const __grid_constan
             const int kk = kb * S::KB + k;
             float pv[8] = {0, 0, 0, 0, 0, 0, 0, 0};
             if (kk < nm) {
-                const int n = m + kk;
-                const double s = n > 0 ? sa2 / (n * (n + 1.0)) : 0.0;
+                const float s = g.na2_f * g.invnn[m + kk];  // psi, chi = -a^2/(n(n+1)) (zeta, delta)
                 const double2* x = g.state + (size_t)(b0 + b) * g.state_ms + off + kk;
                 const double2 ph = x[0], ze = x[g.nc], de = x[2 * g.nc];
                 pv[0] = (float)ze.x; pv[1] = (float)ze.y;
                 pv[2] = (float)ph.x; pv[3] = (float)ph.y;
-                pv[4] = (float)(de.x * s); pv[5] = (float)(de.y * s);
-                pv[6] = (float)(ze.x * s); pv[7] = (float)(ze.y * s);
+                pv[4] = (float)de.x * s; pv[5] = (float)de.y * s;
+                pv[6] = (float)ze.x * s; pv[7] = (float)ze.y * s;
             }
             const int par = kk & 1;
             for (int col = 0; col < 16; ++col) {
@@ -428,7 +430,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_synth(const __grid_constan
         tmem_ld16(lane_base + N + 16 * b, vH);
         if (!ok || j >= g.J2) continue;
         float2* four = g.four_in + (size_t)(b0 + b) * 4 * fs;
-        const float ia = (float)(1.0 / g.a), dm = (float)m;
+        const float ia = g.ia_f, dm = (float)m;
         auto cx = [&](const float* v, int q) { return make_float2(v[q], v[q + 1]); };
         // even parts at columns q, odd parts at q + 8
         const float2 zN = cadd(cx(vP, 0), cx(vP, 8)), zS = csub(cx(vP, 0), cx(vP, 8));
@@ -527,19 +529,22 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_anal(const __grid_constant
         const int par = k & 1;
         const float* P8 = vP + 8 * par;        // C, A, B, E at this row's parity
         const float* H8 = vH + 8 * (par ^ 1);  // D, B, A at the opposite parity
-        const double2 sC{P8[0], P8[1]}, sA{P8[2], P8[3]}, sB{P8[4], P8[5]}, sE{P8[6], P8[7]};
-        const double2 hD{H8[0], H8[1]}, hB{H8[2], H8[3]}, hA{H8[4], H8[5]};
+        const float2 sC{P8[0], P8[1]}, sA{P8[2], P8[3]}, sB{P8[4], P8[5]}, sE{P8[6], P8[7]};
+        const float2 hD{H8[0], H8[1]}, hB{H8[2], H8[3]}, hA{H8[4], H8[5]};
         const int n = m + k;
-        const double ia = 1.0 / g.a, dm = (double)m;
-        const double2 divCD = cscale(csub(cim(dm, sC), hD), ia);
-        const double2 divAB = cscale(csub(cim(dm, sA), hB), ia);
-        const double2 curlAB = cscale(cadd(cim(dm, sB), hA), ia);
-        const double lap = n * (n + 1.0) * ia * ia;
-        double2 f0 = make_double2(-divCD.x, -divCD.y);
-        double2 f1 = make_double2(-divAB.x, -divAB.y);
-        double2 f2 = make_double2(curlAB.x + lap * sE.x, curlAB.y + lap * sE.y);
+        // the nonlinear part from the float32 sums, combined in float32 (its
+        // rounding is far below the operands' split-BF16 / TF32 rounding)
+        const float ia = g.ia_f, dm = (float)m;
+        const float2 divCD = cscale(csub(cim(dm, sC), hD), ia);
+        const float2 divAB = cscale(csub(cim(dm, sA), hB), ia);
+        const float2 curlAB = cscale(cadd(cim(dm, sB), hA), ia);
+        const float lap = (float)n * (float)(n + 1) * ia * ia;
+        double2 f0 = make_double2(-(double)divCD.x, -(double)divCD.y);
+        double2 f1 = make_double2(-(double)divAB.x, -(double)divAB.y);
+        double2 f2 = make_double2((double)(curlAB.x + lap * sE.x), (double)(curlAB.y + lap * sE.y));
         double2 dz, dd;  // the Coriolis part, exactly in float64 (grid products carry no f)
-        coriolis_linear(g.state + (size_t)(b0 + b) * g.state_ms, g.cor, g.nc, R, m, n, off, g.a, g.two_omega, dz, dd);
+        coriolis_linear(g.state + (size_t)(b0 + b) * g.state_ms, g.cor, g.nc, R, m, n, off, g.a2, g.two_omega,
+                        g.c_cor, dz, dd);
         f1 = cadd(f1, dz);
         f2 = cadd(f2, dd);
         if (m == 0) f0.y = f1.y = f2.y = 0.0;
@@ -695,6 +700,11 @@ TcArgs base_args(sh_plan_t p, TcState* s, double a, int members) {
     g.chunk = std::min(s->chunk, members);
     g.stages = s->stages > 0 ? s->stages : stages_for(s->mode, g.chunk);
     g.a = a;
+    g.ia = 1.0 / a;
+    g.a2 = a * a;
+    g.ia_f = (float)(1.0 / a);
+    g.na2_f = (float)(-a * a);
+    g.invnn = p->mp.invnn32;
     g.four_in = p->mp.four_in;
     g.four_out = p->mp.four_out;
     g.cor = p->d_cor;
@@ -814,6 +824,7 @@ mlsdc_status tc_anal(sh_plan_t p, double a, double* FE, const double* state, dou
     g.state = (const double2*)state;
     g.state_ms = b.state_ms;
     g.two_omega = two_omega;
+    g.c_cor = two_omega / (a * a);
     g.FE = (double2*)FE;
     g.fe_ms = b.fe_ms;
     return s->mode == MODE_TF32 ? launch_anal<MODE_TF32>(p, s, g, st) : launch_anal<MODE_BF16X3>(p, s, g, st);

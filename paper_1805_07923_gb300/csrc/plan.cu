@@ -159,6 +159,8 @@ static void free_plan(sh_plan_t p) {
     cudaFree(p->d_tw);
     cudaFree(p->d_ndeg);
     cudaFree(p->d_cor);
+    cudaFree(p->d_lat);
+    cudaFree(p->d_invnn);
     cudaFree(p->d_synth);
     cudaFree(p->d_anal);
     cudaFree(p->d_four_in);
@@ -252,6 +254,19 @@ mlsdc_status mlsdc::create_plan(int R, int nlon, int nlat, int precision, int ma
             c[4] = inv(n);
         }
 
+    // Latitude constants of the grid products and the Fourier weights
+    // (Eq. fourier_transform's 1/I and Eq. legendre_transform's w_j), and
+    // the inverse Laplacian factors of the Helmholtz step.
+    std::vector<double> lat((size_t)4 * nlat), invnn(R + 1);
+    for (int j = 0; j < nlat; ++j) {
+        const double mu = p->mu[j], w = p->w[j];
+        lat[4 * j + 0] = mu;
+        lat[4 * j + 1] = 1.0 / (1.0 - mu * mu);
+        lat[4 * j + 2] = w / (1.0 - mu * mu) / nlon;
+        lat[4 * j + 3] = w / nlon;
+    }
+    for (int n = 0; n <= R; ++n) invnn[n] = n > 0 ? 1.0 / (n * (n + 1.0)) : 0.0;
+
     // Legendre work items, largest first so the block scheduler balances them.
     std::vector<Chunk> cs, ca;
     for (int m = 0; m <= R; ++m)
@@ -274,6 +289,8 @@ mlsdc_status mlsdc::create_plan(int R, int nlon, int nlat, int precision, int ma
     TRY(dev_alloc(&p->d_tw, tw.size(), &p->bytes));
     TRY(dev_alloc(&p->d_ndeg, ndeg.size(), &p->bytes));
     TRY(dev_alloc(&p->d_cor, cor.size(), &p->bytes));
+    TRY(dev_alloc(&p->d_lat, lat.size(), &p->bytes));
+    TRY(dev_alloc(&p->d_invnn, invnn.size(), &p->bytes));
     TRY(dev_alloc(&p->d_synth, cs.size(), &p->bytes));
     TRY(dev_alloc(&p->d_anal, ca.size(), &p->bytes));
     TRY(dev_alloc(&p->d_four_in, nfour, &p->bytes));
@@ -289,6 +306,8 @@ mlsdc_status mlsdc::create_plan(int R, int nlon, int nlat, int precision, int ma
     H2D(p->d_tw, tw.data(), tw.size());
     H2D(p->d_ndeg, ndeg.data(), ndeg.size());
     H2D(p->d_cor, cor.data(), cor.size());
+    H2D(p->d_lat, lat.data(), lat.size());
+    H2D(p->d_invnn, invnn.data(), invnn.size());
     H2D(p->d_synth, cs.data(), cs.size());
     H2D(p->d_anal, ca.data(), ca.size());
 #undef H2D

@@ -38,8 +38,9 @@ struct MemberStrides {
 template <class T>
 __global__ void __launch_bounds__(32 * kSynthWarps) k_synth_rhs(const double2* __restrict__ state,
                                                                 const T* __restrict__ P, const T* __restrict__ H,
+                                                                const T* __restrict__ invnn,
                                                                 const Chunk* __restrict__ chunks, int R, int J2,
-                                                                int nc, double a, C_t<T>* __restrict__ four,
+                                                                int nc, double na2, double ia, C_t<T>* __restrict__ four,
                                                                 MemberStrides ms) {
     using C = C_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -53,15 +54,15 @@ __global__ void __launch_bounds__(32 * kSynthWarps) k_synth_rhs(const double2* _
     const int nm = R + 1 - m;
     const int off = m * (R + 1) - m * (m - 1) / 2;
     for (int k = threadIdx.x; k < nm; k += blockDim.x) {
-        const int n = m + k;
-        const double s = n > 0 ? -a * a / (n * (n + 1.0)) : 0.0;
+        // psi, chi = -a^2/(n(n+1)) (zeta, delta), the factor from the plan's table
+        const T s = T(na2) * invnn[m + k];
         const double2 ph = state[off + k];
         const double2 ze = state[nc + off + k];
         const double2 de = state[2 * nc + off + k];
         sc[4 * k + 0] = mkc(T(ze.x), T(ze.y));
         sc[4 * k + 1] = mkc(T(ph.x), T(ph.y));
-        sc[4 * k + 2] = mkc(T(de.x * s), T(de.y * s));
-        sc[4 * k + 3] = mkc(T(ze.x * s), T(ze.y * s));
+        sc[4 * k + 2] = mkc(T(de.x) * s, T(de.y) * s);
+        sc[4 * k + 3] = mkc(T(ze.x) * s, T(ze.y) * s);
     }
     __syncthreads();
     const int lane = threadIdx.x & 31;
@@ -101,7 +102,7 @@ __global__ void __launch_bounds__(32 * kSynthWarps) k_synth_rhs(const double2* _
         e[q] = cadd(red[(0 * 6 + q) * 32 + lane], red[(2 * 6 + q) * 32 + lane]);
         o[q] = cadd(red[(1 * 6 + q) * 32 + lane], red[(3 * 6 + q) * 32 + lane]);
     }
-    const T ia = T(1.0 / a);
+    const T iaT = T(ia);
     const T dm = T(m);
     const int J = 2 * J2;
     const int jS = J - 1 - j;
@@ -117,16 +118,16 @@ __global__ void __launch_bounds__(32 * kSynthWarps) k_synth_rhs(const double2* _
     four[0 * fs + (size_t)jS * (R + 1) + m] = zS;
     four[1 * fs + (size_t)j * (R + 1) + m] = pN;
     four[1 * fs + (size_t)jS * (R + 1) + m] = pS;
-    four[2 * fs + (size_t)j * (R + 1) + m] = cscale(csub(cim(dm, xPN), sHN), ia);
-    four[2 * fs + (size_t)jS * (R + 1) + m] = cscale(csub(cim(dm, xPS), sHS), ia);
-    four[3 * fs + (size_t)j * (R + 1) + m] = cscale(cadd(cim(dm, sPN), xHN), ia);
-    four[3 * fs + (size_t)jS * (R + 1) + m] = cscale(cadd(cim(dm, sPS), xHS), ia);
+    four[2 * fs + (size_t)j * (R + 1) + m] = cscale(csub(cim(dm, xPN), sHN), iaT);
+    four[2 * fs + (size_t)jS * (R + 1) + m] = cscale(csub(cim(dm, xPS), sHS), iaT);
+    four[3 * fs + (size_t)j * (R + 1) + m] = cscale(cadd(cim(dm, sPN), xHN), iaT);
+    four[3 * fs + (size_t)jS * (R + 1) + m] = cscale(cadd(cim(dm, sPS), xHS), iaT);
 }
 
 template <class T>
 __global__ void __launch_bounds__(256) k_grid_rhs(const C_t<T>* __restrict__ four_in, C_t<T>* __restrict__ four_out,
-                                                  const double* __restrict__ mu, const double* __restrict__ w,
-                                                  const C_t<T>* __restrict__ tw, int R, int I, int logI, int J,
+                                                  const T* __restrict__ lat, const C_t<T>* __restrict__ tw,
+                                                  int R, int I, int logI, int J,
                                                   double two_omega, MemberStrides ms) {
     using C = C_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -148,9 +149,9 @@ __global__ void __launch_bounds__(256) k_grid_rhs(const C_t<T>* __restrict__ fou
     // inverse by decimation in frequency: slot q now holds the longitude pair
     // at the digit-reversed position of q
     fft4_dif(sx, 4, Hn, logH, stab, true);
-    const double muj = mu[j];
-    const T f = T(two_omega * muj);
-    const T rc = T(1.0 / (1.0 - muj * muj));
+    // lat[j] = (mu, 1/(1-mu^2), w/((1-mu^2) I), w/I): no float64 division here
+    const T f = T(two_omega) * lat[4 * j];
+    const T rc = lat[4 * j + 1];
     C* y = sx + 4 * Hn;
     for (int q0 = threadIdx.x; q0 < Hn; q0 += blockDim.x) {
         // .x and .y hold the two longitudes of one packed pair; products are
@@ -168,8 +169,8 @@ __global__ void __launch_bounds__(256) k_grid_rhs(const C_t<T>* __restrict__ fou
     __syncthreads();
     // forward by decimation in time from the digit-reversed slots: natural order out
     fft4_dit(y, 5, Hn, logH, stab, false);
-    const T sAD = T(w[j] / (1.0 - muj * muj) / I);
-    const T sE = T(w[j] / I);
+    const T sAD = lat[4 * j + 2];
+    const T sE = lat[4 * j + 3];
     for (int t = threadIdx.x; t < 5 * (R + 1); t += blockDim.x) {
         const int fld = t / (R + 1);
         const int m = t - fld * (R + 1);
@@ -193,9 +194,10 @@ __global__ void __launch_bounds__(256) k_grid_rhs(const C_t<T>* __restrict__ fou
 // with inv_n = -1/(n(n+1)) (0 for n = 0; times a^2 here) and eps zero outside
 // m <= n <= R (precomputed per plan: float64 square roots and divisions are
 // slow on this GPU).
+// a2 = a^2 and c = 2 Omega / a^2 are computed once on the host.
 __device__ inline void coriolis_linear(const double2* __restrict__ state, const double* __restrict__ cor, int nc,
-                                       int R, int m, int n, int off, double a, double two_omega, double2& dz,
-                                       double2& dd) {
+                                       int R, int m, int n, int off, double a2, double two_omega, double c,
+                                       double2& dz, double2& dd) {
     const int k = n - m;
     const double2* z = state + nc + off;
     const double2* d = state + 2 * nc + off;
@@ -203,7 +205,6 @@ __device__ inline void coriolis_linear(const double2* __restrict__ state, const 
     if (n - 1 >= m) { zl = z[k - 1]; dl = d[k - 1]; }
     if (n + 1 <= R) { zu = z[k + 1]; du = d[k + 1]; }
     const double* c5 = cor + 5 * (size_t)(off + k);
-    const double a2 = a * a;
     const double en = c5[0], en1 = c5[1], cl = c5[2] * a2, cu = c5[3] * a2, in = c5[4] * a2;
     const double2 muD = make_double2(en * dl.x + en1 * du.x, en * dl.y + en1 * du.y);
     const double2 muZ = make_double2(en * zl.x + en1 * zu.x, en * zl.y + en1 * zu.y);
@@ -211,7 +212,7 @@ __device__ inline void coriolis_linear(const double2* __restrict__ state, const 
     const double2 Hpsi = make_double2(cl * zl.x + cu * zu.x, cl * zl.y + cu * zu.y);
     const double2 psi = make_double2(in * z[k].x, in * z[k].y);
     const double2 chi = make_double2(in * d[k].x, in * d[k].y);
-    const double c = two_omega / (a * a), dm = (double)m;
+    const double dm = (double)m;
     dz = make_double2(-two_omega * muD.x - c * (-dm * psi.y + Hchi.x), -two_omega * muD.y - c * (dm * psi.x + Hchi.y));
     dd = make_double2(two_omega * muZ.x - c * (-dm * chi.y - Hpsi.x), two_omega * muZ.y - c * (dm * chi.x - Hpsi.y));
 }
@@ -224,7 +225,7 @@ template <class T>
 __global__ void __launch_bounds__(32 * kAnalWarpsMax) k_anal_rhs(const C_t<T>* __restrict__ four_out,
                                                                  const T* __restrict__ P, const T* __restrict__ H,
                                                                  const Chunk* __restrict__ chunks, int R, int J2,
-                                                                 int nc, double a, double2* __restrict__ FE,
+                                                                 int nc, double ia, double a2, double2* __restrict__ FE,
                                                                  const double2* __restrict__ state,
                                                                  double two_omega_lin, const double* __restrict__ cor,
                                                                  MemberStrides ms, NodeFuse nf) {
@@ -300,7 +301,6 @@ __global__ void __launch_bounds__(32 * kAnalWarpsMax) k_anal_rhs(const C_t<T>* _
             s[q].y += (double)red[w2 - 1][q][lane].y;
         }
     const int n = m + k;
-    const double ia = 1.0 / a;
     const double dm = (double)m;
     const double2 divCD = cscale(csub(cim(dm, s[0]), s[4]), ia);
     const double2 divAB = cscale(csub(cim(dm, s[1]), s[5]), ia);
@@ -311,7 +311,7 @@ __global__ void __launch_bounds__(32 * kAnalWarpsMax) k_anal_rhs(const C_t<T>* _
     double2 f2 = make_double2(curlAB.x + lap * s[3].x, curlAB.y + lap * s[3].y);
     if (two_omega_lin != 0.0) {
         double2 dz, dd;
-        coriolis_linear(state, cor, nc, R, m, n, off, a, two_omega_lin, dz, dd);
+        coriolis_linear(state, cor, nc, R, m, n, off, a2, two_omega_lin, two_omega_lin * ia * ia, dz, dd);
         f1 = cadd(f1, dz);
         f2 = cadd(f2, dd);
     }

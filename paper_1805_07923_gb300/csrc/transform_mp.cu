@@ -43,7 +43,9 @@ mlsdc_status mp_init(sh_plan_t p) {
     bool ok = alloc((void**)&t.P32, ntab * sizeof(float)) && alloc((void**)&t.H32, ntab * sizeof(float)) &&
               alloc((void**)&t.tw32, (p->I / 2) * sizeof(float2)) &&
               alloc((void**)&t.four_in, 4 * nfour * p->max_members * sizeof(float2)) &&
-              alloc((void**)&t.four_out, 5 * nfour * p->max_members * sizeof(float2));
+              alloc((void**)&t.four_out, 5 * nfour * p->max_members * sizeof(float2)) &&
+              alloc((void**)&t.lat32, (size_t)4 * p->J * sizeof(float)) &&
+              alloc((void**)&t.invnn32, (size_t)(p->R + 1) * sizeof(float));
     if (!ok) {
         set_error("cudaMalloc (mixed-precision tables)", cudaGetLastError());
         return MLSDC_ERR_ALLOC;
@@ -51,6 +53,8 @@ mlsdc_status mp_init(sh_plan_t p) {
     k_round_f32<<<1024, 256>>>(p->d_P, t.P32, ntab);
     k_round_f32<<<1024, 256>>>(p->d_H, t.H32, ntab);
     k_round_c32<<<8, 256>>>(p->d_tw, t.tw32, p->I / 2);
+    k_round_f32<<<8, 256>>>(p->d_lat, t.lat32, (size_t)4 * p->J);
+    k_round_f32<<<8, 256>>>(p->d_invnn, t.invnn32, (size_t)(p->R + 1));
     MLSDC_LAUNCHED("k_round_f32");
     MLSDC_CUDA(cudaDeviceSynchronize());
     mlsdc_status rs = raise_smem_limit((const void*)k_grid_rhs<float>, grid_smem<float>(p->I));
@@ -67,6 +71,8 @@ void mp_free(sh_plan_t p) {
     cudaFree(t.tw32);
     cudaFree(t.four_in);
     cudaFree(t.four_out);
+    cudaFree(t.lat32);
+    cudaFree(t.invnn32);
     t = MPTables();
 }
 
@@ -88,15 +94,15 @@ mlsdc_status rhs_explicit_mp(sh_plan_t p, const swe_params* prm, const double* s
             MLSDC_LAUNCH("k_synth_rhs<float>",
                          launch_k(k_synth_rhs<float>, dim3(p->n_synth, b.members), dim3(32 * kSynthWarps),
                                   synth_smem<float>(R), st, (const double2*)state, (const float*)t.P32,
-                                  (const float*)t.H32, (const Chunk*)p->d_synth, R, p->J2, p->nc, prm->a, t.four_in,
-                                  ms));
+                                  (const float*)t.H32, (const float*)t.invnn32, (const Chunk*)p->d_synth, R, p->J2,
+                                  p->nc, -prm->a * prm->a, 1.0 / prm->a, t.four_in, ms));
         }
     }
     if (stage == 1 || stage < 0) {
         MLSDC_LAUNCH("k_grid_rhs<float>",
                      launch_k(k_grid_rhs<float>, dim3(p->J, b.members), dim3(256), grid_smem<float>(p->I), st,
-                              (const float2*)t.four_in, t.four_out, (const double*)p->d_mu, (const double*)p->d_w,
-                              (const float2*)t.tw32, R, p->I, p->logI, p->J, 0.0, ms));
+                              (const float2*)t.four_in, t.four_out, (const float*)t.lat32, (const float2*)t.tw32, R,
+                              p->I, p->logI, p->J, 0.0, ms));
     }
     if (stage == 2 || stage < 0) {
         if (tc) {
@@ -105,8 +111,9 @@ mlsdc_status rhs_explicit_mp(sh_plan_t p, const swe_params* prm, const double* s
             MLSDC_LAUNCH("k_anal_rhs<float>",
                          launch_k(k_anal_rhs<float>, dim3(p->n_anal, b.members), dim3(32 * anal_warps(p->J2)), 0, st,
                                   (const float2*)t.four_out, (const float*)t.P32, (const float*)t.H32,
-                                  (const Chunk*)p->d_anal, R, p->J2, p->nc, prm->a, (double2*)FE,
-                                  (const double2*)state, 2.0 * prm->omega, (const double*)p->d_cor, ms, fuse));
+                                  (const Chunk*)p->d_anal, R, p->J2, p->nc, 1.0 / prm->a, prm->a * prm->a,
+                                  (double2*)FE, (const double2*)state, 2.0 * prm->omega, (const double*)p->d_cor, ms,
+                                  fuse));
         }
     }
     if (launches) *launches += stage < 0 ? 3 : 1;
