@@ -357,11 +357,11 @@ __device__ __forceinline__ void implicit_rhs_t(double L, const Phys& ph, double2
 
 // transpose of the implicit solve: (I - alpha F_I^t) y = g, with c = 1 - alpha nu L
 // [[c, 0, alpha L], [0, c, 0], [alpha Phibar, 0, c]] y = g
-__device__ __forceinline__ void implicit_solve_t(double L, double alpha, const Phys& ph, double2 gp, double2 gz,
-                                                 double2 gd, double2& p, double2& z, double2& d) {
+// with the same two reciprocals r = solve_recips(L, alpha, ph) as the forward solve
+__device__ __forceinline__ void implicit_solve_t(double L, double alpha, const Phys& ph, double2 r, double2 gp,
+                                                 double2 gz, double2 gd, double2& p, double2& z, double2& d) {
     const double c = 1.0 - alpha * ph.nu * L;
-    const double ic = 1.0 / c;
-    const double den = 1.0 / (c * c - alpha * alpha * ph.phibar * L);
+    const double ic = r.x, den = r.y;
     z = make_double2(gz.x * ic, gz.y * ic);
     p = make_double2((c * gp.x - alpha * L * gd.x) * den, (c * gp.y - alpha * L * gd.y) * den);
     d = make_double2((gd.x - alpha * ph.phibar * p.x) * ic, (gd.y - alpha * ph.phibar * p.y) * ic);
@@ -386,7 +386,8 @@ __global__ void k_fi_ad(double2* __restrict__ xb, double2* __restrict__ Fb, cons
 //       - dt qI_mm FIo_{m+1} + sum_{j=0..M} dt q_j (FIo_j + FEo_j) [+ tau_{m+1}]
 //   Th[m+1] = solve(b);  FIn[m+1] = F_I(Th[m+1]);  (m = 0: FIn[0] = FIo[0], FEn[0] = FEo[0])
 __global__ void k_node_ad(double2* Thb, double2* FIob, double2* FEob, double2* FInb, double2* FEnb, double2* taub,
-                          const int* __restrict__ ndeg, int nc, double dt, NodeRow row, Phys ph) {
+                          const int* __restrict__ ndeg, const double2* __restrict__ recips, int nc, double dt,
+                          NodeRow row, Phys ph) {
     const size_t node = (size_t)3 * nc;
     const int m = row.m;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) {
@@ -397,7 +398,8 @@ __global__ void k_node_ad(double2* Thb, double2* FIob, double2* FEob, double2* F
                 FEob[o] = cadd(FEob[o], FEnb[o]);
                 FInb[o] = FEnb[o] = make_double2(0.0, 0.0);
             }
-        const double n = ndeg[c];
+        const int nd = ndeg[c];
+        const double n = nd;
         const double L = -n * (n + 1.0) * ph.inv_a2;
         const size_t om = (m + 1) * node + c;
         double2 gp, gz, gd;
@@ -407,7 +409,7 @@ __global__ void k_node_ad(double2* Thb, double2* FIob, double2* FEob, double2* F
         gd = cadd(gd, Thb[om + 2 * nc]);
         for (int f = 0; f < 3; ++f) Thb[om + f * nc] = FInb[om + f * nc] = make_double2(0.0, 0.0);
         double2 b[3];
-        implicit_solve_t(L, dt * row.qimm, ph, gp, gz, gd, b[0], b[1], b[2]);
+        implicit_solve_t(L, dt * row.qimm, ph, recips[nd], gp, gz, gd, b[0], b[1], b[2]);
         for (int f = 0; f < 3; ++f) {
             const size_t o = (size_t)f * nc + c;
             const double2 bb = b[f];
@@ -603,7 +605,8 @@ double2* adj_of(mlsdc_adjoint_t A, const double2* p) {
 
 mlsdc_status check_op_ptrs(mlsdc_adjoint_t A) {
     for (const Op& o : A->ops) {
-        const int np = o.k == OpK::Node ? 6 : o.k == OpK::Fas ? 10 : o.k == OpK::Interp ? 9 : 2;
+        const int np = o.k == OpK::Node ? 6 : o.k == OpK::Fas ? 10 : o.k == OpK::Interp ? 9
+                                                                    : o.k == OpK::SolveCoefs ? 0 : 2;
         for (int i = 0; i < np; ++i)
             if (o.p[i] && !adj_of(A, o.p[i])) {
                 set_error_text("mlsdc_adjoint: an operand has no adjoint buffer");
@@ -668,8 +671,13 @@ mlsdc_status reverse_step(mlsdc_adjoint_t A, const double2* tape, cudaStream_t s
                 k_node_ad<<<grid_for(L->plan->nc), 256, 0, st>>>(adj_of(A, o.p[0]), adj_of(A, o.p[1]),
                                                                 adj_of(A, o.p[2]), adj_of(A, o.p[3]),
                                                                 adj_of(A, o.p[4]), adj_of(A, o.p[5]), L->plan->d_ndeg,
+                                                                L->d_recips + (size_t)o.row.m * (L->plan->R + 1),
                                                                 L->plan->nc, o.dt, o.row, phys_of(L->prm));
                 MLSDC_LAUNCHED("k_node_ad");
+                break;
+            case OpK::SolveCoefs:
+                // constant coefficients of the step, recomputed by its forward ops: nothing to transpose
+                n--;
                 break;
             case OpK::Restrict:
                 k_restrict_ad<<<gt, 256, 0, st>>>(adj_of(A, o.p[0]), adj_of(A, o.p[1]), ml->d_c2f, ncf, ncc, nfn, o.i0,

@@ -49,6 +49,25 @@ __device__ __forceinline__ void implicit_solve_coef(double L, double alpha, cons
     d = make_double2((bd.x - alpha * L * p.x) * ic, (bd.y - alpha * L * p.y) * ic);
 }
 
+// The two reciprocals of the solve, per degree n: with c = 1 - alpha nu L,
+// (1/c, 1 / (c^2 - alpha^2 Phibar L)).  They depend only on the degree and on
+// alpha = dt q~I_{m+1,m+1}, so a step computes them once per level and node
+// (k_solve_coefs) instead of per coefficient and update.
+__device__ __forceinline__ double2 solve_recips(double L, double alpha, const Phys& ph) {
+    const double c = 1.0 - alpha * ph.nu * L;
+    return make_double2(1.0 / c, 1.0 / (c * c - alpha * alpha * ph.phibar * L));
+}
+
+// implicit_solve_coef with the reciprocals r = solve_recips(L, alpha, ph).
+__device__ __forceinline__ void implicit_solve_tab(double L, double alpha, const Phys& ph, double2 r, double2 bp,
+                                                   double2 bz, double2 bd, double2& p, double2& z, double2& d) {
+    const double c = 1.0 - alpha * ph.nu * L;
+    const double ic = r.x, den = r.y;
+    z = make_double2(bz.x * ic, bz.y * ic);
+    p = make_double2((c * bp.x - alpha * ph.phibar * bd.x) * den, (c * bp.y - alpha * ph.phibar * bd.y) * den);
+    d = make_double2((bd.x - alpha * L * p.x) * ic, (bd.y - alpha * L * p.y) * ic);
+}
+
 // The right-hand side b of the node update at one (field, coefficient)
 // offset o of a member's node arrays ([M+1][3][nc], node = 3 nc):
 //   b = Th[0] + sum_{j=1..m} dt (qE_j (FEn_j - FEo_j) + qI_j (FIn_j - FIo_j))
@@ -87,6 +106,7 @@ struct NodeFuse {
     double2 *FIn, *FEn;
     const double2* tau;
     const int* ndeg;
+    const double2* recips;  // [R+1] solve_recips of this node, by degree
     double dt;
     NodeRow row;
     Phys ph;
@@ -105,10 +125,11 @@ __device__ __forceinline__ void node_update_coef(const NodeFuse& f, int nc, int 
     const double2* tau = f.tau ? f.tau + mo : nullptr;
     double2 b[3];
     for (int q = 0; q < 3; ++q) b[q] = node_rhs(Th0, FIo, FEo, FIn, FEn, tau, node, (size_t)q * nc + c, f.dt, f.row);
-    const double n = f.ndeg[c];
+    const int nd = f.ndeg[c];
+    const double n = nd;
     const double L = -n * (n + 1.0) * f.ph.inv_a2;
     double2 p, z, d;
-    implicit_solve_coef(L, f.dt * f.row.qimm, f.ph, b[0], b[1], b[2], p, z, d);
+    implicit_solve_tab(L, f.dt * f.row.qimm, f.ph, f.recips[nd], b[0], b[1], b[2], p, z, d);
     double2 fp, fz, fd;
     implicit_rhs_coef(L, f.ph, p, z, d, fp, fz, fd);
     const size_t om = (f.row.m + 1) * node + c;

@@ -49,6 +49,20 @@ __global__ void k_implicit_solve(const double2* __restrict__ b, double2* __restr
     }
 }
 
+// The solve reciprocals of every node update of a sweep at time step dt,
+// tab[m][n] = solve_recips(L_n, dt q~I_{m+1,m+1}) for m < M, n <= R.
+struct QiDiag {
+    double v[kMaxNodes];
+};
+__global__ void k_solve_coefs(double2* __restrict__ tab, int R, int M, QiDiag qd, double dt, Phys ph) {
+    pdl_wait();
+    pdl_launch();
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < M * (R + 1); t += gridDim.x * blockDim.x) {
+        const int m = t / (R + 1), n = t - m * (R + 1);
+        tab[t] = solve_recips(-n * (n + 1.0) * ph.inv_a2, dt * qd.v[m], ph);
+    }
+}
+
 // One SDC node update (Eq. update_equation_sdcq_discrete_form, plus tau on a
 // coarse level), the implicit solve, and F_I at the new node.  Node arrays
 // are [M+1][3][nc] complex per member (member stride ms); `node` = 3 nc
@@ -59,7 +73,8 @@ __global__ void k_implicit_solve(const double2* __restrict__ b, double2* __restr
 __global__ void __launch_bounds__(3 * kNodeCoefs) k_sweep_node(double2* Th, const double2* __restrict__ FIo,
                                                              const double2* __restrict__ FEo, double2* FIn,
                                                              double2* FEn, const double2* __restrict__ tau,
-                                                             const int* __restrict__ ndeg, int nc, double dt,
+                                                             const int* __restrict__ ndeg,
+                                                             const double2* __restrict__ recips, int nc, double dt,
                                                              NodeRow row, Phys ph, size_t ms) {
     __shared__ double2 sb[3][kNodeCoefs];
     pdl_wait();
@@ -80,10 +95,11 @@ __global__ void __launch_bounds__(3 * kNodeCoefs) k_sweep_node(double2* Th, cons
     if (live) sb[f][cl] = node_rhs(Th, FIo, FEo, FIn, FEn, tau, node, o, dt, row);
     __syncthreads();
     if (!live) return;
-    const double n = ndeg[c];
+    const int nd = ndeg[c];
+    const double n = nd;
     const double L = -n * (n + 1.0) * ph.inv_a2;
     double2 p, z, d;
-    implicit_solve_coef(L, dt * row.qimm, ph, sb[0][cl], sb[1][cl], sb[2][cl], p, z, d);
+    implicit_solve_tab(L, dt * row.qimm, ph, recips[nd], sb[0][cl], sb[1][cl], sb[2][cl], p, z, d);
     double2 fp, fz, fd;
     implicit_rhs_coef(L, ph, p, z, d, fp, fz, fd);
     const size_t om = (m + 1) * node + o;
@@ -371,7 +387,8 @@ static mlsdc_status launch_node(sdc_level_t L, double dt, const NodeRow& row, do
     const int nc = L->plan->nc;
     MLSDC_LAUNCH("k_sweep_node",
                  launch_k(k_sweep_node, dim3((nc + kNodeCoefs - 1) / kNodeCoefs, L->members), dim3(3 * kNodeCoefs),
-                          0, st, Th, FIo, FEo, FIn, FEn, tau, (const int*)L->plan->d_ndeg, nc, dt, row,
+                          0, st, Th, FIo, FEo, FIn, FEn, tau, (const int*)L->plan->d_ndeg,
+                          (const double2*)(L->d_recips + (size_t)row.m * (L->plan->R + 1)), nc, dt, row,
                           phys_of(L->prm), L->ms()));
     L->launches++;
     return MLSDC_OK;
@@ -385,10 +402,24 @@ static mlsdc_status launch_bcast(sdc_level_t L, const double2* src, double2* dst
     return MLSDC_OK;
 }
 
+// The solve reciprocals of the level's node updates at step size dt.
+static mlsdc_status launch_solve_coefs(sdc_level_t L, double dt, cudaStream_t st) {
+    QiDiag qd;
+    std::memset(&qd, 0, sizeof(qd));
+    for (int m = 0; m + 1 < L->n; ++m) qd.v[m] = L->QI[(m + 1) * L->n + m + 1];
+    const int R = L->plan->R;
+    MLSDC_LAUNCH("k_solve_coefs", launch_k(k_solve_coefs, dim3(grid_for((L->n - 1) * (R + 1))), dim3(256), 0, st,
+                                           L->d_recips, R, L->n - 1, qd, dt, phys_of(L->prm)));
+    L->launches++;
+    return MLSDC_OK;
+}
+
 // One sweep on explicit buffers ([members][n][3][nc] each).
 static mlsdc_status sweep(sdc_level_t L, double dt, double2* Th, const double2* FIo, const double2* FEo,
                           double2* FIn, double2* FEn, const double2* tau, cudaStream_t st) {
     const size_t node = L->node();
+    mlsdc_status s0 = launch_solve_coefs(L, dt, st);
+    if (s0 != MLSDC_OK) return s0;
     for (int m = 0; m < L->n - 1; ++m) {
         mlsdc_status s = launch_node(L, dt, node_row(L, m), Th, FIo, FEo, FIn, FEn, tau, st);
         if (s != MLSDC_OK) return s;
@@ -517,7 +548,8 @@ extern "C" mlsdc_status sdc_level_create_batched(sh_plan_t plan, const swe_param
         for (int c = 0; c < k; ++c) L->QI[(r + 1) * n + (c + 1)] = U[c * k + r];
 
     const size_t cnt = (size_t)members * L->ms();
-    bool ok = cudaMalloc((void**)&L->Th, cnt * sizeof(double2)) == cudaSuccess;
+    bool ok = cudaMalloc((void**)&L->Th, cnt * sizeof(double2)) == cudaSuccess &&
+              cudaMalloc((void**)&L->d_recips, (size_t)n * (plan->R + 1) * sizeof(double2)) == cudaSuccess;
     for (int b = 0; b < 2 && ok; ++b) {
         ok = ok && cudaMalloc((void**)&L->FI[b], cnt * sizeof(double2)) == cudaSuccess;
         ok = ok && cudaMalloc((void**)&L->FE[b], cnt * sizeof(double2)) == cudaSuccess;
@@ -538,6 +570,7 @@ extern "C" mlsdc_status sdc_level_create(sh_plan_t plan, const swe_params* prm, 
 extern "C" mlsdc_status sdc_level_destroy(sdc_level_t L) {
     if (!L) return MLSDC_ERR_INVALID;
     cudaFree(L->Th);
+    cudaFree(L->d_recips);
     for (int b = 0; b < 2; ++b) {
         cudaFree(L->FI[b]);
         cudaFree(L->FE[b]);
@@ -694,6 +727,13 @@ size_t build_mlsdc_ops(mlsdc_t ml, double2* state, double dt, int n_iter, int n_
         ops.push_back(o);
     };
     int cf = F->cur, cc = C->cur;
+    // the implicit-solve reciprocals of both levels at this dt
+    for (sdc_level_t L : {F, C}) {
+        Op o{OpK::SolveCoefs};
+        o.L = L;
+        o.dt = dt;
+        ops.push_back(o);
+    }
     // initialisation: fine spread; coarse node 0 = restriction of Theta^n, evaluated once
     bcast(F, state, F->Th, nfn, nodef);
     fi(F, F->Th, F->FI[cf]);
@@ -798,6 +838,7 @@ mlsdc_status run_ops(mlsdc_t ml, const std::vector<Op>& ops, cudaStream_t st, in
                     nf.FEn = n.p[4];
                     nf.tau = n.p[5];
                     nf.ndeg = n.L->plan->d_ndeg;
+                    nf.recips = n.L->d_recips + (size_t)n.row.m * (n.L->plan->R + 1);
                     nf.dt = n.dt;
                     nf.row = n.row;
                     nf.ph = phys_of(n.L->prm);
@@ -832,6 +873,9 @@ mlsdc_status run_ops(mlsdc_t ml, const std::vector<Op>& ops, cudaStream_t st, in
                                                   o.p[4], o.p[5], o.p[6], o.p[7], o.p[8], (const int*)ml->d_c2f, ncf,
                                                   ncc, nfn, ncn, ml->Pfc, msf, msc));
                 own++;
+                break;
+            case OpK::SolveCoefs:
+                s = launch_solve_coefs(o.L, o.dt, st);
                 break;
             case OpK::CopyLast: {
                 const size_t w = o.L->node() * sizeof(double2);

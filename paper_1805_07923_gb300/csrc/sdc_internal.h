@@ -42,6 +42,7 @@ enum class OpK : int {
     Fas,       // tau (p[6]) from fine (p[0..2]) and coarse (p[3..5]) nodes; saves p[3..5] to p[7..9]
     Interp,    // fine p[0..2] += P(Pfc (coarse p[3..5] - saved p[6..8]))
     CopyLast,  // p[1] (the state) = last fine node p[0], every member
+    SolveCoefs,  // the level's implicit-solve reciprocals at dt (no state operands)
 };
 
 struct Op {
@@ -81,6 +82,7 @@ struct sdc_level_s {
     double2* Th = nullptr;  // [members][n][3][nc]
     double2* FI[2] = {nullptr, nullptr};
     double2* FE[2] = {nullptr, nullptr};
+    double2* d_recips = nullptr;  // [n][R+1] solve reciprocals of the node updates (k_solve_coefs)
     int cur = 0;
     int64_t launches = 0;
     size_t node() const { return (size_t)3 * plan->nc; }
