@@ -31,6 +31,55 @@ mlsdc_status tc_synth(sh_plan_t p, const double* state, double a, RhsBatch b, cu
 mlsdc_status tc_anal(sh_plan_t p, double a, double* FE, const double* state, double two_omega, RhsBatch b,
                      cudaStream_t st, const NodeFuse* nf);
 
+// For each Legendre stage of a tensor-core plan, time the tcgen05 kernel and
+// the float32 CUDA-core kernel on a full batch of members (zero state, Earth
+// constants; timing only) and keep the faster.  The CUDA-core kernels are at
+// least as accurate (float32 operands instead of split-BF16 / TF32), so the
+// choice never loosens the plan's accuracy.  With one member the tensor core
+// has 16 columns to fill and the CUDA-core synthesis can win; batched, the
+// tensor cores win.
+static mlsdc_status choose_stage_kernels(sh_plan_t p) {
+    const int B = p->max_members;
+    const size_t n = (size_t)B * 3 * p->nc;
+    double2 *x = nullptr, *fe = nullptr;
+    MLSDC_CUDA(cudaMalloc((void**)&x, n * sizeof(double2)));
+    MLSDC_CUDA(cudaMalloc((void**)&fe, n * sizeof(double2)));
+    MLSDC_CUDA(cudaMemset(x, 0, n * sizeof(double2)));
+    const swe_params prm{6.37122e6, 7.292e-5, 9.80616, 9.80616e4, 1.0e5};
+    RhsBatch b;
+    b.members = B;
+    b.state_ms = b.fe_ms = (size_t)3 * p->nc;
+    cudaEvent_t e0, e1;
+    MLSDC_CUDA(cudaEventCreate(&e0));
+    MLSDC_CUDA(cudaEventCreate(&e1));
+    mlsdc_status rs = rhs_explicit_mp(p, &prm, (const double*)x, (double*)fe, 0, nullptr, -1, b);
+    for (int stage = 0; stage <= 2 && rs == MLSDC_OK; stage += 2) {
+        float best = 1e30f;
+        int best_tc = 1;
+        for (int use_tc = 1; use_tc >= 0 && rs == MLSDC_OK; --use_tc) {
+            (stage == 0 ? p->mp.synth_tc : p->mp.anal_tc) = use_tc;
+            for (int rep = 0; rep < 6 && rs == MLSDC_OK; ++rep) {
+                if (rep == 1) cudaEventRecord(e0);
+                rs = rhs_explicit_mp(p, &prm, (const double*)x, (double*)fe, 0, nullptr, stage, b);
+            }
+            cudaEventRecord(e1);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) {
+                best = ms;
+                best_tc = use_tc;
+            }
+        }
+        (stage == 0 ? p->mp.synth_tc : p->mp.anal_tc) = best_tc;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(x);
+    cudaFree(fe);
+    return rs;
+}
+
 mlsdc_status mp_init(sh_plan_t p) {
     MPTables& t = p->mp;
     const size_t ntab = (size_t)p->nc * p->J2;
@@ -59,7 +108,11 @@ mlsdc_status mp_init(sh_plan_t p) {
     MLSDC_CUDA(cudaDeviceSynchronize());
     mlsdc_status rs = raise_smem_limit((const void*)k_grid_rhs<float>, grid_smem<float>(p->I));
     if (rs != MLSDC_OK) return rs;
-    if (p->precision == MLSDC_TF32 || p->precision == MLSDC_BF16X3) return tc_init(p);
+    if (p->precision == MLSDC_TF32 || p->precision == MLSDC_BF16X3) {
+        rs = tc_init(p);
+        if (rs == MLSDC_OK) rs = choose_stage_kernels(p);
+        return rs;
+    }
     return MLSDC_OK;
 }
 
@@ -88,7 +141,7 @@ mlsdc_status rhs_explicit_mp(sh_plan_t p, const swe_params* prm, const double* s
     const MemberStrides ms{b.state_ms, 4 * fs, 5 * fs, b.fe_ms};
     mlsdc_status s;
     if (stage == 0 || stage < 0) {
-        if (tc) {
+        if (tc && t.synth_tc) {
             if ((s = tc_synth(p, state, prm->a, b, st)) != MLSDC_OK) return s;
         } else {
             MLSDC_LAUNCH("k_synth_rhs<float>",
@@ -105,7 +158,7 @@ mlsdc_status rhs_explicit_mp(sh_plan_t p, const swe_params* prm, const double* s
                               p->I, p->logI, p->J, 0.0, ms));
     }
     if (stage == 2 || stage < 0) {
-        if (tc) {
+        if (tc && t.anal_tc) {
             if ((s = tc_anal(p, prm->a, FE, state, 2.0 * prm->omega, b, st, nf)) != MLSDC_OK) return s;
         } else {
             MLSDC_LAUNCH("k_anal_rhs<float>",
@@ -121,3 +174,18 @@ mlsdc_status rhs_explicit_mp(sh_plan_t p, const swe_params* prm, const double* s
 }
 
 }  // namespace mlsdc
+
+extern "C" mlsdc_status sh_plan_stage_kernels(sh_plan_t p, int* synth_tc, int* anal_tc) {
+    if (!p) return MLSDC_ERR_INVALID;
+    const bool tc = p->precision == MLSDC_TF32 || p->precision == MLSDC_BF16X3;
+    if (synth_tc) *synth_tc = tc ? p->mp.synth_tc : 0;
+    if (anal_tc) *anal_tc = tc ? p->mp.anal_tc : 0;
+    return MLSDC_OK;
+}
+
+extern "C" mlsdc_status sh_plan_set_stage_kernels(sh_plan_t p, int synth_tc, int anal_tc) {
+    if (!p || !(p->precision == MLSDC_TF32 || p->precision == MLSDC_BF16X3)) return MLSDC_ERR_INVALID;
+    p->mp.synth_tc = synth_tc ? 1 : 0;
+    p->mp.anal_tc = anal_tc ? 1 : 0;
+    return MLSDC_OK;
+}

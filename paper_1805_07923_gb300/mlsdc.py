@@ -66,6 +66,8 @@ _SIGS = {
     "mlsdc_profile_rhs": ([_VP, ctypes.POINTER(SweParams), _DP, _DP, _I, ctypes.POINTER(ctypes.c_float), _VP], _I),
     "mlsdc_profile_rhs_batched": ([_VP, ctypes.POINTER(SweParams), _DP, _DP, _I, _I, ctypes.POINTER(ctypes.c_float),
                                    _VP], _I),
+    "sh_plan_stage_kernels": ([_VP, ctypes.POINTER(_I), ctypes.POINTER(_I)], _I),
+    "sh_plan_set_stage_kernels": ([_VP, _I, _I], _I),
     "swe_explicit_rhs_adjoint": ([_VP, ctypes.POINTER(SweParams), _DP, _DP, _DP, _VP], _I),
     "mlsdc_phi_misfit": ([_VP, _DP, _DP, _DP, _DP, _VP], _I),
     "mlsdc_adjoint_create": ([_VP, _I, _I, _D, _I, _I, ctypes.POINTER(_VP)], _I),
@@ -183,6 +185,15 @@ class Plan:
         b = ctypes.c_int64()
         _check(lib().sh_plan_device_bytes(self.h, ctypes.byref(b)), "sh_plan_device_bytes")
         return b.value
+
+    def stage_kernels(self) -> tuple[bool, bool]:
+        """(synthesis on tensor cores, analysis on tensor cores)."""
+        a, b = ctypes.c_int(), ctypes.c_int()
+        _check(lib().sh_plan_stage_kernels(self.h, ctypes.byref(a), ctypes.byref(b)), "sh_plan_stage_kernels")
+        return bool(a.value), bool(b.value)
+
+    def set_stage_kernels(self, synth_tc: bool, anal_tc: bool):
+        _check(lib().sh_plan_set_stage_kernels(self.h, int(synth_tc), int(anal_tc)), "sh_plan_set_stage_kernels")
 
 
 def sh_inverse(plan: Plan, spec: torch.Tensor, grid: torch.Tensor, nf: int, stream=None):
