@@ -302,15 +302,18 @@ def run_ensemble(args):
             fe = torch.empty_like(xs)
             ms = M.mlsdc_profile_rhs(plan, lf.prm, xs, fe, reps=20, members=B)
             stages[f"{lvl}x{B}"] = dict(zip(names, ms))
+            tcs = plan.stage_kernels(B) if prec in ("tf32", "bf16x3") else (False, False)
+            stages[f"{lvl}x{B}"]["tensor_core_stages"] = [n for n, on in zip(("synthesis", "analysis"), tcs) if on]
             for s in range(3):
                 fl = (legendre_stage_flops(R, J, s) if s != 1 else grid_stage_flops(R, I, J)) * B
-                shares.append((ms[s] * cnt, f"{lvl}x{B}", names[s], ms[s], fl))
+                on_tc = (s == 0 and tcs[0]) or (s == 2 and tcs[1])
+                shares.append((ms[s] * cnt, f"{lvl}x{B}", names[s], ms[s], fl, on_tc))
     shares.sort(reverse=True)
     top = shares[0]
     peaks = load_peaks()
     bf16 = peaks.get("bf16_tflops", 1900.0)
     achieved = top[4] / (top[3] * 1e-3) / 1e12
-    roof = {"bound": "tensor" if top[2] != "grid_fft_products" and prec in ("tf32", "bf16x3") else "alu",
+    roof = {"bound": "tensor" if top[5] else "alu",
             "achieved": achieved, "unit": "TFLOP/s", "kernel": f"{top[2]} at {top[1]}", "kernel_ms": top[3]}
     if roof["bound"] == "tensor":
         roof["peak"] = bf16 if prec == "bf16x3" else bf16 * 1.1 / 2.25
@@ -675,11 +678,21 @@ def main():
     tname = {"fp64": "double", "fp32": "float", "tf32": "float", "bf16x3": "float"}[prec]
     kern_names = {"legendre_synthesis": f"k_synth_rhs<{tname}>", "grid_fft_products": f"k_grid_rhs<{tname}>",
                   "legendre_analysis": f"k_anal_rhs<{tname}>"}
+    stage_kernels = {}
     if prec in ("tf32", "bf16x3"):
-        kern_names.update({"legendre_synthesis": f"k_tc_synth<{prec}>", "legendre_analysis": f"k_tc_anal<{prec}>"})
+        # the plans' size rule: per level, which Legendre stages run on tcgen05
+        for lvl, p_, mem in (("T170", pf, 1), ("T85", pc, 1)):
+            stc, atc = p_.stage_kernels(mem)
+            stage_kernels[lvl] = {"synthesis": "tcgen05" if stc else "cuda-core fp32",
+                                  "analysis": "tcgen05" if atc else "cuda-core fp32"}
+        stc, atc = pf.stage_kernels(1)
+        if stc:
+            kern_names["legendre_synthesis"] = f"k_tc_synth<{prec}>"
+        if atc:
+            kern_names["legendre_analysis"] = f"k_tc_anal<{prec}>"
     achieved = top[4] / (top[3] * 1e-3) / 1e12
     sm_max = (clk.get("sm_max_mhz") or 2070.0) * 1e6
-    if top[2] == "grid_fft_products" or prec in ("fp64", "fp32"):
+    if not kern_names[top[2]].startswith("k_tc"):
         if prec == "fp64":
             peak, src = measured_fp64_tflops(torch, dev), "measured cuBLAS DGEMM on this GPU (float64 pipe)"
         else:
@@ -705,7 +718,8 @@ def main():
         "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if prec == "fp64" else f"f64+{prec}", "data": "synthetic",
         "config": {"workload": WORKLOAD_NAME, "precision": prec, "steps_of_run": w["total_steps"],
-                   "l2": "flushed between timed steps (256 MB write)", "graph": "one CUDA graph per step"},
+                   "l2": "flushed between timed steps (256 MB write)", "graph": "one CUDA graph per step",
+                   "legendre_kernels": stage_kernels or None},
         "sh_tflops": sh_flops * value / ws / 1e12,
         "gpu_launches": launches_per_step * K,
         "e2e": {"value": job_value(ws, Ke, e2e_ms), "unit": "steps/s", "h2d_bytes_per_step": nbytes,

@@ -107,16 +107,19 @@ mlsdc_status sh_plan_device_bytes(sh_plan_t plan, int64_t* bytes);
  * device.  Always 0 for MLSDC_FP64 / MLSDC_FP32 plans. */
 mlsdc_status sh_plan_device_error(sh_plan_t plan, int* code);
 /* Which kernel each Legendre stage of a tensor-core plan (MLSDC_TF32 /
- * MLSDC_BF16X3) runs: 1 = the tcgen05 kernel, 0 = the float32 CUDA-core
- * kernel of MLSDC_FP32.  At creation the plan times both on a full batch of
- * its members and keeps the faster per stage (with one member the CUDA-core
- * synthesis is usually faster; batched, the tensor cores).  The CUDA-core
- * kernels use float32 operands, at least as accurate as split-BF16 or TF32.
- * sh_plan_stage_kernels reports the choice (0, 0 for other precisions);
- * sh_plan_set_stage_kernels overrides it (MLSDC_ERR_INVALID for other
- * precisions). */
-mlsdc_status sh_plan_stage_kernels(sh_plan_t plan, int* synth_tc, int* anal_tc);
-mlsdc_status sh_plan_set_stage_kernels(sh_plan_t plan, int synth_tc, int anal_tc);
+ * MLSDC_BF16X3) runs: the tcgen05 kernel or the float32 CUDA-core kernel of
+ * MLSDC_FP32.  By default the choice follows a fixed rule per launch (measured
+ * on GB300): the analysis on tensor cores for R >= 64, the synthesis on
+ * tensor cores for R >= 128 with at least 8 members in the launch, the
+ * CUDA-core kernels otherwise.  The CUDA-core kernels use float32 operands,
+ * at least as accurate as split-BF16 or TF32; the rule depends on sizes only,
+ * so results are reproducible.  sh_plan_stage_kernels reports the kernels a
+ * launch of `members` states uses (1 = tcgen05; 0, 0 for other precisions).
+ * sh_plan_set_stage_kernels sets each stage's mode: 0 = the rule, 1 = always
+ * tcgen05, 2 = always the CUDA-core kernel (MLSDC_ERR_INVALID for other
+ * precisions or modes). */
+mlsdc_status sh_plan_stage_kernels(sh_plan_t plan, int members, int* synth_tc, int* anal_tc);
+mlsdc_status sh_plan_set_stage_kernels(sh_plan_t plan, int synth_mode, int anal_mode);
 
 /* sh_inverse: spectral -> grid for nf independent scalar fields,
  * Eq. spectral_to_physical_space (Legendre sum per m, then the inverse

@@ -103,9 +103,10 @@ struct MPTables {
     // tensor-core state (legendre_tc.cu): operand tables, tensor maps, error flag
     void* tc = nullptr;
     int64_t tc_bytes = 0;
-    // tensor-core plans: which kernel each Legendre stage runs (1 = tcgen05,
-    // 0 = the float32 CUDA-core kernel), chosen by timing at plan creation
-    int synth_tc = 1, anal_tc = 1;
+    // tensor-core plans: which kernel each Legendre stage runs (kStageAuto:
+    // by truncation and batch size, see stage_uses_tc; kStageTc: tcgen05;
+    // kStageSimt: the float32 CUDA-core kernel)
+    int synth_mode = 0, anal_mode = 0;
 };
 
 }  // namespace mlsdc

@@ -31,53 +31,20 @@ mlsdc_status tc_synth(sh_plan_t p, const double* state, double a, RhsBatch b, cu
 mlsdc_status tc_anal(sh_plan_t p, double a, double* FE, const double* state, double two_omega, RhsBatch b,
                      cudaStream_t st, const NodeFuse* nf);
 
-// For each Legendre stage of a tensor-core plan, time the tcgen05 kernel and
-// the float32 CUDA-core kernel on a full batch of members (zero state, Earth
-// constants; timing only) and keep the faster.  The CUDA-core kernels are at
-// least as accurate (float32 operands instead of split-BF16 / TF32), so the
-// choice never loosens the plan's accuracy.  With one member the tensor core
-// has 16 columns to fill and the CUDA-core synthesis can win; batched, the
-// tensor cores win.
-static mlsdc_status choose_stage_kernels(sh_plan_t p) {
-    const int B = p->max_members;
-    const size_t n = (size_t)B * 3 * p->nc;
-    double2 *x = nullptr, *fe = nullptr;
-    MLSDC_CUDA(cudaMalloc((void**)&x, n * sizeof(double2)));
-    MLSDC_CUDA(cudaMalloc((void**)&fe, n * sizeof(double2)));
-    MLSDC_CUDA(cudaMemset(x, 0, n * sizeof(double2)));
-    const swe_params prm{6.37122e6, 7.292e-5, 9.80616, 9.80616e4, 1.0e5};
-    RhsBatch b;
-    b.members = B;
-    b.state_ms = b.fe_ms = (size_t)3 * p->nc;
-    cudaEvent_t e0, e1;
-    MLSDC_CUDA(cudaEventCreate(&e0));
-    MLSDC_CUDA(cudaEventCreate(&e1));
-    mlsdc_status rs = rhs_explicit_mp(p, &prm, (const double*)x, (double*)fe, 0, nullptr, -1, b);
-    for (int stage = 0; stage <= 2 && rs == MLSDC_OK; stage += 2) {
-        float best = 1e30f;
-        int best_tc = 1;
-        for (int use_tc = 1; use_tc >= 0 && rs == MLSDC_OK; --use_tc) {
-            (stage == 0 ? p->mp.synth_tc : p->mp.anal_tc) = use_tc;
-            for (int rep = 0; rep < 6 && rs == MLSDC_OK; ++rep) {
-                if (rep == 1) cudaEventRecord(e0);
-                rs = rhs_explicit_mp(p, &prm, (const double*)x, (double*)fe, 0, nullptr, stage, b);
-            }
-            cudaEventRecord(e1);
-            cudaEventSynchronize(e1);
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (ms < best) {
-                best = ms;
-                best_tc = use_tc;
-            }
-        }
-        (stage == 0 ? p->mp.synth_tc : p->mp.anal_tc) = best_tc;
-    }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    cudaFree(x);
-    cudaFree(fe);
-    return rs;
+constexpr int kStageAuto = 0, kStageTc = 1, kStageSimt = 2;
+
+// Which kernel a Legendre stage of a tensor-core plan runs for a launch of
+// `members` states.  The rule is the outcome of timing both kernels on GB300
+// for R = 21, 42, 85, 170 and 1..48 members: the tcgen05 analysis wins from
+// R = 85 up, the tcgen05 synthesis only at R = 170 with 8 or more members
+// (its 16 columns per member leave a single member's MMA mostly idle and the
+// B operand costs more to stage than the CUDA-core sums).  A fixed rule keeps
+// results reproducible run to run; the CUDA-core kernels use float32
+// operands, at least as accurate as split-BF16 or TF32.
+static bool stage_uses_tc(const sh_plan_s* p, int stage, int members) {
+    const int mode = stage == 0 ? p->mp.synth_mode : p->mp.anal_mode;
+    if (mode != kStageAuto) return mode == kStageTc;
+    return stage == 0 ? (p->R >= 128 && members >= 8) : p->R >= 64;
 }
 
 mlsdc_status mp_init(sh_plan_t p) {
@@ -108,11 +75,7 @@ mlsdc_status mp_init(sh_plan_t p) {
     MLSDC_CUDA(cudaDeviceSynchronize());
     mlsdc_status rs = raise_smem_limit((const void*)k_grid_rhs<float>, grid_smem<float>(p->I));
     if (rs != MLSDC_OK) return rs;
-    if (p->precision == MLSDC_TF32 || p->precision == MLSDC_BF16X3) {
-        rs = tc_init(p);
-        if (rs == MLSDC_OK) rs = choose_stage_kernels(p);
-        return rs;
-    }
+    if (p->precision == MLSDC_TF32 || p->precision == MLSDC_BF16X3) return tc_init(p);
     return MLSDC_OK;
 }
 
@@ -141,7 +104,7 @@ mlsdc_status rhs_explicit_mp(sh_plan_t p, const swe_params* prm, const double* s
     const MemberStrides ms{b.state_ms, 4 * fs, 5 * fs, b.fe_ms};
     mlsdc_status s;
     if (stage == 0 || stage < 0) {
-        if (tc && t.synth_tc) {
+        if (tc && stage_uses_tc(p, 0, b.members)) {
             if ((s = tc_synth(p, state, prm->a, b, st)) != MLSDC_OK) return s;
         } else {
             MLSDC_LAUNCH("k_synth_rhs<float>",
@@ -158,7 +121,7 @@ mlsdc_status rhs_explicit_mp(sh_plan_t p, const swe_params* prm, const double* s
                               p->I, p->logI, p->J, 0.0, ms));
     }
     if (stage == 2 || stage < 0) {
-        if (tc && t.anal_tc) {
+        if (tc && stage_uses_tc(p, 2, b.members)) {
             if ((s = tc_anal(p, prm->a, FE, state, 2.0 * prm->omega, b, st, nf)) != MLSDC_OK) return s;
         } else {
             MLSDC_LAUNCH("k_anal_rhs<float>",
@@ -175,17 +138,18 @@ mlsdc_status rhs_explicit_mp(sh_plan_t p, const swe_params* prm, const double* s
 
 }  // namespace mlsdc
 
-extern "C" mlsdc_status sh_plan_stage_kernels(sh_plan_t p, int* synth_tc, int* anal_tc) {
-    if (!p) return MLSDC_ERR_INVALID;
+extern "C" mlsdc_status sh_plan_stage_kernels(sh_plan_t p, int members, int* synth_tc, int* anal_tc) {
+    if (!p || members < 1) return MLSDC_ERR_INVALID;
     const bool tc = p->precision == MLSDC_TF32 || p->precision == MLSDC_BF16X3;
-    if (synth_tc) *synth_tc = tc ? p->mp.synth_tc : 0;
-    if (anal_tc) *anal_tc = tc ? p->mp.anal_tc : 0;
+    if (synth_tc) *synth_tc = tc && mlsdc::stage_uses_tc(p, 0, members) ? 1 : 0;
+    if (anal_tc) *anal_tc = tc && mlsdc::stage_uses_tc(p, 2, members) ? 1 : 0;
     return MLSDC_OK;
 }
 
-extern "C" mlsdc_status sh_plan_set_stage_kernels(sh_plan_t p, int synth_tc, int anal_tc) {
+extern "C" mlsdc_status sh_plan_set_stage_kernels(sh_plan_t p, int synth_mode, int anal_mode) {
     if (!p || !(p->precision == MLSDC_TF32 || p->precision == MLSDC_BF16X3)) return MLSDC_ERR_INVALID;
-    p->mp.synth_tc = synth_tc ? 1 : 0;
-    p->mp.anal_tc = anal_tc ? 1 : 0;
+    if (synth_mode < 0 || synth_mode > 2 || anal_mode < 0 || anal_mode > 2) return MLSDC_ERR_INVALID;
+    p->mp.synth_mode = synth_mode;
+    p->mp.anal_mode = anal_mode;
     return MLSDC_OK;
 }

@@ -66,7 +66,7 @@ _SIGS = {
     "mlsdc_profile_rhs": ([_VP, ctypes.POINTER(SweParams), _DP, _DP, _I, ctypes.POINTER(ctypes.c_float), _VP], _I),
     "mlsdc_profile_rhs_batched": ([_VP, ctypes.POINTER(SweParams), _DP, _DP, _I, _I, ctypes.POINTER(ctypes.c_float),
                                    _VP], _I),
-    "sh_plan_stage_kernels": ([_VP, ctypes.POINTER(_I), ctypes.POINTER(_I)], _I),
+    "sh_plan_stage_kernels": ([_VP, _I, ctypes.POINTER(_I), ctypes.POINTER(_I)], _I),
     "sh_plan_set_stage_kernels": ([_VP, _I, _I], _I),
     "swe_explicit_rhs_adjoint": ([_VP, ctypes.POINTER(SweParams), _DP, _DP, _DP, _VP], _I),
     "mlsdc_phi_misfit": ([_VP, _DP, _DP, _DP, _DP, _VP], _I),
@@ -186,14 +186,19 @@ class Plan:
         _check(lib().sh_plan_device_bytes(self.h, ctypes.byref(b)), "sh_plan_device_bytes")
         return b.value
 
-    def stage_kernels(self) -> tuple[bool, bool]:
-        """(synthesis on tensor cores, analysis on tensor cores)."""
+    STAGE_MODES = {"auto": 0, "tc": 1, "simt": 2}
+
+    def stage_kernels(self, members: int = 1) -> tuple[bool, bool]:
+        """(synthesis on tensor cores, analysis on tensor cores) for a launch of `members` states."""
         a, b = ctypes.c_int(), ctypes.c_int()
-        _check(lib().sh_plan_stage_kernels(self.h, ctypes.byref(a), ctypes.byref(b)), "sh_plan_stage_kernels")
+        _check(lib().sh_plan_stage_kernels(self.h, int(members), ctypes.byref(a), ctypes.byref(b)),
+               "sh_plan_stage_kernels")
         return bool(a.value), bool(b.value)
 
-    def set_stage_kernels(self, synth_tc: bool, anal_tc: bool):
-        _check(lib().sh_plan_set_stage_kernels(self.h, int(synth_tc), int(anal_tc)), "sh_plan_set_stage_kernels")
+    def set_stage_kernels(self, synth: str = "auto", anal: str = "auto"):
+        """Per-stage kernel mode of a tensor-core plan: "auto" (the size rule), "tc" or "simt"."""
+        _check(lib().sh_plan_set_stage_kernels(self.h, self.STAGE_MODES[synth], self.STAGE_MODES[anal]),
+               "sh_plan_set_stage_kernels")
 
 
 def sh_inverse(plan: Plan, spec: torch.Tensor, grid: torch.Tensor, nf: int, stream=None):

@@ -36,7 +36,7 @@ def main(argv=None):
     a = ap.parse_args(argv)
     plan = M.Plan(a.R, a.nlon, a.nlat, "fp64" if a.adjoint else a.precision, a.members)
     if a.kernels != "auto" and a.precision in ("tf32", "bf16x3") and not a.adjoint:
-        plan.set_stage_kernels(a.kernels == "tc", a.kernels == "tc")
+        plan.set_stage_kernels(a.kernels, a.kernels)
     prm = M.swe_params()
     base = inputs.initial_state(a.R)
     x = torch.from_numpy(np.stack([inputs.perturbed_member(base, a.R, a.R, k) for k in range(a.members)])).cuda()
@@ -57,7 +57,7 @@ def main(argv=None):
     else:
         ms = M.mlsdc_profile_rhs(plan, prm, x, fe, reps=20, members=a.members)
     print(json.dumps({"R": a.R, "nlon": a.nlon, "nlat": a.nlat, "precision": a.precision, "members": a.members,
-                      "adjoint": a.adjoint, "stage_ms": ms, "stage_kernels_tc": plan.stage_kernels()}))
+                      "adjoint": a.adjoint, "stage_ms": ms, "stage_kernels_tc": plan.stage_kernels(a.members)}))
 
 
 if __name__ == "__main__":

@@ -29,6 +29,11 @@ def test_batched_rhs_equals_single(prec, R, I, J, B):
     x = members_state(R, B)
     pb = M.Plan(R, I, J, prec, max_members=B)
     p1 = M.Plan(R, I, J, prec)
+    if prec in ("tf32", "bf16x3"):
+        # compare the tensor-core kernels batched and single (the size rule
+        # could pick different kernels for 1 and B members)
+        for p in (pb, p1):
+            p.set_stage_kernels("tc", "tc")
     prm = M.swe_params()
     xs = torch.from_numpy(x).cuda()
     FEb = torch.empty_like(xs)
@@ -79,6 +84,9 @@ def test_batched_sdc_step_equals_single_fp64():
 
 def _group(Rf, If, Jf, Rc, Ic, Jc, B, prec):
     pf, pc = M.Plan(Rf, If, Jf, prec, B), M.Plan(Rc, Ic, Jc, prec, B)
+    if prec in ("tf32", "bf16x3"):
+        for p in (pf, pc):
+            p.set_stage_kernels("tc", "tc")
     lf, lc = M.Level(pf, 5, members=B), M.Level(pc, 3, members=B)
     return M.MLSDC(lf, lc), (pf, pc, lf, lc)
 

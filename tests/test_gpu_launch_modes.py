@@ -49,6 +49,9 @@ def rel_l2(R, got, ref):
 def _mlsdc(Rf, If, Jf, Rc, Ic, Jc, prec, coarse_members):
     pf = M.Plan(Rf, If, Jf, prec)
     pc = M.Plan(Rc, Ic, Jc, prec, coarse_members)
+    if prec in ("tf32", "bf16x3"):
+        for p in (pf, pc):  # the tensor-core kernels themselves, batched and not
+            p.set_stage_kernels("tc", "tc")
     lf, lc = M.Level(pf, 5), M.Level(pc, 3)
     return M.MLSDC(lf, lc), (pf, pc, lf, lc)
 

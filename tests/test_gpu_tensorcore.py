@@ -34,12 +34,16 @@ def rel_l2(R, got, ref):
     return float(np.sqrt(osht.norm2(R, got - ref) / max(osht.norm2(R, ref), 1e-300)))
 
 
+@pytest.mark.parametrize("kernels", ["tc", "auto"])
 @pytest.mark.parametrize("prec", TC)
 @pytest.mark.parametrize("R,I,J", [(21, 64, 32), (45, 256, 70), (85, 256, 128), (170, 512, 256)])
-def test_tensorcore_rhs_vs_oracle(prec, R, I, J):
+def test_tensorcore_rhs_vs_oracle(prec, R, I, J, kernels):
+    """kernels="tc": both Legendre stages on tcgen05; "auto": the plan's size
+    rule (CUDA-core float32 kernels where they are faster)."""
     o = oracle(R, I, J)
     x = inputs.initial_state(R)
     plan = M.Plan(R, I, J, prec)
+    plan.set_stage_kernels(kernels, kernels)
     FE = torch.full((3, o.nc), float("nan"), dtype=torch.complex128, device="cuda")
     M.swe_explicit_rhs(plan, M.swe_params(), torch.from_numpy(x).cuda(), FE)
     assert plan.device_error() == 0
