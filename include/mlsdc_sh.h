@@ -264,12 +264,13 @@ mlsdc_status mlsdc_ensemble_step(mlsdc_ensemble_t ens, double* const* states, do
                                  int n_coarse_sweeps, int use_graph, void* stream);
 mlsdc_status mlsdc_ensemble_launch_count(mlsdc_ensemble_t ens, int64_t* launches);
 
-/* Stage timing of swe_explicit_rhs for roofline reporting: launches each of
- * the plan's F_E stage kernels `reps` times back to back on `stream`, timed
- * with CUDA events on that stream, and writes the mean milliseconds per
- * launch of [0] the Legendre synthesis, [1] the longitude FFT / grid-product
- * kernel, [2] the Legendre analysis to ms_host[3] (synchronises the stream).
- * Not a paper operation: a measurement utility over the same kernels. */
+/* Stage timing of swe_explicit_rhs for roofline reporting: captures `reps`
+ * back-to-back launches of each of the plan's F_E stage kernels into a CUDA
+ * graph (as the step runs them), replays it once to warm up and once timed
+ * with CUDA events on `stream`, and writes the mean milliseconds per launch of
+ * [0] the Legendre synthesis, [1] the longitude FFT / grid-product kernel,
+ * [2] the Legendre analysis to ms_host[3] (synchronises the stream).  Not a
+ * paper operation: a measurement utility over the same kernels. */
 mlsdc_status mlsdc_profile_rhs(sh_plan_t plan, const swe_params* prm, const double* state, double* FE,
                                int reps, float* ms_host, void* stream);
 /* The same for a batch of `members` states ([members][3][N_c]) per launch. */

@@ -931,15 +931,15 @@ extern "C" mlsdc_status mlsdc_profile_rhs_adjoint(sh_plan_t p, const swe_params*
     const double2* x = (const double2*)state;
     double2* lam = (double2*)lambda;
     double2* xb = (double2*)state_bar;
-    auto stage = [&](int k) -> mlsdc_status {
+    auto stage = [&](int k, cudaStream_t cs) -> mlsdc_status {
         if (k == 0)
-            k_synth_ad<<<p->n_synth, 32 * kAdSynthWarps, ss, st>>>(x, lam, p->d_P, p->d_H, p->d_invnn, p->d_synth, R,
+            k_synth_ad<<<p->n_synth, 32 * kAdSynthWarps, ss, cs>>>(x, lam, p->d_P, p->d_H, p->d_invnn, p->d_synth, R,
                                                                   p->J2, p->nc, prm->a, 1.0 / prm->a, p->d_four_in);
         else if (k == 1)
-            k_grid_ad<<<p->J, 256, gs, st>>>(p->d_four_in, p->d_four_out, p->d_lat, p->d_tw, R, p->I, p->logI, p->J,
+            k_grid_ad<<<p->J, 256, gs, cs>>>(p->d_four_in, p->d_four_out, p->d_lat, p->d_tw, R, p->I, p->logI, p->J,
                                              2.0 * prm->omega);
         else
-            k_anal_ad<<<p->n_anal, 32 * anal_warps(p->J2), 0, st>>>(p->d_four_out, p->d_P, p->d_H, p->d_invnn,
+            k_anal_ad<<<p->n_anal, 32 * anal_warps(p->J2), 0, cs>>>(p->d_four_out, p->d_P, p->d_H, p->d_invnn,
                                                                    p->d_anal, R, p->J2, p->nc, prm->a, 1.0 / prm->a,
                                                                    xb, lam);
         MLSDC_LAUNCHED("profile_rhs_adjoint");
@@ -947,20 +947,8 @@ extern "C" mlsdc_status mlsdc_profile_rhs_adjoint(sh_plan_t p, const swe_params*
     };
     // one full evaluation first so every stage reads valid inputs
     if ((s = fe_adjoint(p, prm, x, lam, xb, st, nullptr)) != MLSDC_OK) return s;
-    cudaEvent_t e0, e1;
-    MLSDC_CUDA(cudaEventCreate(&e0));
-    MLSDC_CUDA(cudaEventCreate(&e1));
-    for (int k = 0; k < 3 && s == MLSDC_OK; ++k) {
-        MLSDC_CUDA(cudaEventRecord(e0, st));
-        for (int r = 0; r < reps && s == MLSDC_OK; ++r) s = stage(k);
-        MLSDC_CUDA(cudaEventRecord(e1, st));
-        MLSDC_CUDA(cudaEventSynchronize(e1));
-        float ms = 0.f;
-        MLSDC_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-        ms_host[k] = ms / reps;
-    }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    for (int k = 0; k < 3 && s == MLSDC_OK; ++k)
+        s = time_in_graph(st, reps, &ms_host[k], [&](cudaStream_t cs) { return stage(k, cs); });
     return s;
 }
 

@@ -78,6 +78,47 @@ inline cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, siz
         }                                                 \
     } while (0)
 
+// Stage timing for the measurement entry points: `enqueue(stream)` issued
+// `reps` times is captured into one CUDA graph, replayed once to warm up and
+// once timed with CUDA events on `st`; *ms = milliseconds per enqueue.
+// Inside a graph the per-launch cost is the device's (about 1.1 us per
+// dependent kernel here), not the host's launch rate, as in the step graphs.
+template <class Enqueue>
+inline mlsdc_status time_in_graph(cudaStream_t st, int reps, float* ms, Enqueue enqueue) {
+    cudaStream_t cap = nullptr;
+    MLSDC_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    mlsdc_status s = MLSDC_OK;
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    for (int r = 0; r < reps && s == MLSDC_OK && e == cudaSuccess; ++r) s = enqueue(cap);
+    cudaError_t e2 = cudaStreamEndCapture(cap, &g);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess && s == MLSDC_OK) e = cudaGraphInstantiate(&ge, g, 0);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (e == cudaSuccess && s == MLSDC_OK) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess && s == MLSDC_OK) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess && s == MLSDC_OK) e = cudaGraphLaunch(ge, st);
+    if (e == cudaSuccess && s == MLSDC_OK) e = cudaEventRecord(e0, st);
+    if (e == cudaSuccess && s == MLSDC_OK) e = cudaGraphLaunch(ge, st);
+    if (e == cudaSuccess && s == MLSDC_OK) e = cudaEventRecord(e1, st);
+    if (e == cudaSuccess && s == MLSDC_OK) e = cudaEventSynchronize(e1);
+    float t = 0.f;
+    if (e == cudaSuccess && s == MLSDC_OK) e = cudaEventElapsedTime(&t, e0, e1);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (ge) cudaGraphExecDestroy(ge);
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cap);
+    if (s != MLSDC_OK) return s;
+    if (e != cudaSuccess) {
+        set_error("time_in_graph", e);
+        return MLSDC_ERR_CUDA;
+    }
+    *ms = t / reps;
+    return MLSDC_OK;
+}
+
 // Raise (never lower) a kernel's dynamic shared-memory limit.  The attribute
 // belongs to the kernel, not to a plan, so a plan needing less must not undo
 // the setting another live plan relies on.

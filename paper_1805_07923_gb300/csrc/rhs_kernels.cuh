@@ -292,23 +292,22 @@ __global__ void __launch_bounds__(32 * kAnalWarpsMax) k_anal_rhs(const C_t<T>* _
     }
     __syncthreads();
     if (wid != 0 || !live) return;
-    double2 s[7] = {{(double)aC.x, (double)aC.y}, {(double)aA.x, (double)aA.y}, {(double)aB.x, (double)aB.y},
-                    {(double)aE.x, (double)aE.y}, {(double)hD.x, (double)hD.y}, {(double)hB.x, (double)hB.y},
-                    {(double)hA.x, (double)hA.y}};
+    // The sums of the other warps, then div, curl and the kinetic-energy
+    // term in the working precision T: float64 on the float64 path; float32
+    // on the mixed path, whose sums are float32 already (and float64 runs at
+    // a small fraction of the float32 rate on this GPU).
+    C s[7] = {aC, aA, aB, aE, hD, hB, hA};
     for (int w2 = 1; w2 < nw; ++w2)
-        for (int q = 0; q < 7; ++q) {
-            s[q].x += (double)red[w2 - 1][q][lane].x;
-            s[q].y += (double)red[w2 - 1][q][lane].y;
-        }
+        for (int q = 0; q < 7; ++q) s[q] = cadd(s[q], red[w2 - 1][q][lane]);
     const int n = m + k;
-    const double dm = (double)m;
-    const double2 divCD = cscale(csub(cim(dm, s[0]), s[4]), ia);
-    const double2 divAB = cscale(csub(cim(dm, s[1]), s[5]), ia);
-    const double2 curlAB = cscale(cadd(cim(dm, s[2]), s[6]), ia);
-    const double lap = n * (n + 1.0) * ia * ia;
-    double2 f0 = make_double2(-divCD.x, -divCD.y);
-    double2 f1 = make_double2(-divAB.x, -divAB.y);
-    double2 f2 = make_double2(curlAB.x + lap * s[3].x, curlAB.y + lap * s[3].y);
+    const T dm = T(m), iaT = T(ia);
+    const C divCD = cscale(csub(cim(dm, s[0]), s[4]), iaT);
+    const C divAB = cscale(csub(cim(dm, s[1]), s[5]), iaT);
+    const C curlAB = cscale(cadd(cim(dm, s[2]), s[6]), iaT);
+    const T lap = T(n) * T(n + 1) * iaT * iaT;
+    double2 f0 = make_double2(-(double)divCD.x, -(double)divCD.y);
+    double2 f1 = make_double2(-(double)divAB.x, -(double)divAB.y);
+    double2 f2 = make_double2((double)(curlAB.x + lap * s[3].x), (double)(curlAB.y + lap * s[3].y));
     if (two_omega_lin != 0.0) {
         double2 dz, dd;
         coriolis_linear(state, cor, nc, R, m, n, off, a2, two_omega_lin, two_omega_lin * ia * ia, dz, dd);

@@ -217,26 +217,14 @@ extern "C" mlsdc_status mlsdc_profile_rhs_batched(sh_plan_t p, const swe_params*
     RhsBatch b;
     b.members = members;
     b.state_ms = b.fe_ms = (size_t)3 * p->nc;
-    auto run = [&](int stage) {
-        return p->precision == MLSDC_FP64 ? rhs_explicit_f64(p, prm, state, FE, st, nullptr, stage, b)
-                                          : rhs_explicit_mp(p, prm, state, FE, st, nullptr, stage, b);
+    auto run = [&](int stage, cudaStream_t s) {
+        return p->precision == MLSDC_FP64 ? rhs_explicit_f64(p, prm, state, FE, s, nullptr, stage, b)
+                                          : rhs_explicit_mp(p, prm, state, FE, s, nullptr, stage, b);
     };
     // one full evaluation first so every stage reads valid inputs
-    mlsdc_status s = run(-1);
+    mlsdc_status s = run(-1, st);
     if (s != MLSDC_OK) return s;
-    cudaEvent_t e0, e1;
-    MLSDC_CUDA(cudaEventCreate(&e0));
-    MLSDC_CUDA(cudaEventCreate(&e1));
-    for (int stage = 0; stage < 3 && s == MLSDC_OK; ++stage) {
-        MLSDC_CUDA(cudaEventRecord(e0, st));
-        for (int r = 0; r < reps && s == MLSDC_OK; ++r) s = run(stage);
-        MLSDC_CUDA(cudaEventRecord(e1, st));
-        MLSDC_CUDA(cudaEventSynchronize(e1));
-        float ms = 0.f;
-        MLSDC_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-        ms_host[stage] = ms / reps;
-    }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    for (int stage = 0; stage < 3 && s == MLSDC_OK; ++stage)
+        s = time_in_graph(st, reps, &ms_host[stage], [&](cudaStream_t cs) { return run(stage, cs); });
     return s;
 }
