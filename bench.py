@@ -676,15 +676,17 @@ def main():
     top = shares[0]
     peaks = load_peaks()
     tname = {"fp64": "double", "fp32": "float", "tf32": "float", "bf16x3": "float"}[prec]
-    kern_names = {"legendre_synthesis": f"k_synth_rhs<{tname}>", "grid_fft_products": f"k_grid_rhs<{tname}>",
+    kern_names = {"legendre_synthesis": f"k_synth_rhs<{tname}>", "grid_fft_products": f"k_grid_rhs<{tname}, 1>",
                   "legendre_analysis": f"k_anal_rhs<{tname}>"}
     stage_kernels = {}
     if prec in ("tf32", "bf16x3"):
         # the plans' size rule: per level, which Legendre stages run on tcgen05
         for lvl, p_, mem in (("T170", pf, 1), ("T85", pc, 1)):
             stc, atc = p_.stage_kernels(mem)
+            cpc, nst = p_.tc_config()
             stage_kernels[lvl] = {"synthesis": "tcgen05" if stc else "cuda-core fp32",
-                                  "analysis": "tcgen05" if atc else "cuda-core fp32"}
+                                  "analysis": "tcgen05" if atc else "cuda-core fp32",
+                                  "tc_members_per_cta": cpc, "tc_stages": nst}
         stc, atc = pf.stage_kernels(1)
         if stc:
             kern_names["legendre_synthesis"] = f"k_tc_synth<{prec}>"

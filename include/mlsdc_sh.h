@@ -120,6 +120,12 @@ mlsdc_status sh_plan_device_error(sh_plan_t plan, int* code);
  * precisions or modes). */
 mlsdc_status sh_plan_stage_kernels(sh_plan_t plan, int members, int* synth_tc, int* anal_tc);
 mlsdc_status sh_plan_set_stage_kernels(sh_plan_t plan, int synth_mode, int anal_mode);
+/* The tensor-core kernels' launch configuration, chosen at plan creation by
+ * timing each feasible choice on a full batch of the plan's max_members:
+ * members per CTA (1, 2, 4, 8 or 16; the members form the MMA's N dimension,
+ * 16 columns each) and the depth of the shared-memory pipeline over K (1 or
+ * 2 stages).  0, 0 for MLSDC_FP64 / MLSDC_FP32 plans.  Pointers may be NULL. */
+mlsdc_status sh_plan_tc_config(sh_plan_t plan, int* members_per_cta, int* stages);
 
 /* sh_inverse: spectral -> grid for nf independent scalar fields,
  * Eq. spectral_to_physical_space (Legendre sum per m, then the inverse

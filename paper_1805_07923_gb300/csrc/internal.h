@@ -138,7 +138,7 @@ struct MPTables {
     float* H32 = nullptr;        // [nc][J2]
     float2* tw32 = nullptr;      // [I/2] float32 twiddles
     float2* four_in = nullptr;   // [4][J][R+1]
-    float2* four_out = nullptr;  // [5][J][R+1]
+    float2* four_out = nullptr;  // [5][R+1][J] (latitude-contiguous)
     float* lat32 = nullptr;      // [J][4] float32 copy of the plan's d_lat
     float* invnn32 = nullptr;    // [R+1] float32 copy of d_invnn
     // tensor-core state (legendre_tc.cu): operand tables, tensor maps, error flag
@@ -205,6 +205,9 @@ mlsdc_status rhs_explicit_mp(sh_plan_t p, const swe_params* prm, const double* s
                              cudaStream_t st, int64_t* launches, int stage = -1, RhsBatch b = RhsBatch(),
                              const NodeFuse* nf = nullptr);
 mlsdc_status create_plan(int R, int nlon, int nlat, int precision, int max_members, sh_plan_t* out);
+// whether a Legendre stage (0 synthesis, 2 analysis) of a tensor-core plan
+// runs the tcgen05 kernel for a launch of `members` states (transform_mp.cu)
+bool stage_uses_tc(const sh_plan_s* p, int stage, int members);
 // pointwise float64 kernels (sdc.cu)
 mlsdc_status implicit_rhs_launch(sh_plan_t p, const swe_params* prm, const double* state, double* FI,
                                  cudaStream_t st);

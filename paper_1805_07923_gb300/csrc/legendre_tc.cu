@@ -178,6 +178,31 @@ __device__ __forceinline__ void put_b(unsigned char* hi, unsigned char* lo, int 
     }
 }
 
+// put_b for the KV = 16 / esz consecutive K values k = KV g ... KV g + KV - 1
+// of row r, stored as one 16-byte word per part (same layout and rounding).
+// Eight lanes storing one row for consecutive groups g hit distinct banks
+// (the 16-byte shift of lbo_for).
+template <int MODE>
+__device__ __forceinline__ void put_bv(unsigned char* hi, unsigned char* lo, int r, int g, const float* v,
+                                       uint32_t lbo) {
+    const uint32_t off = (uint32_t)g * lbo + (r >> 3) * 128 + (r & 7) * 16;
+    if (MODE == MODE_TF32) {
+        *reinterpret_cast<uint4*>(hi + off) = make_uint4(to_tf32(v[0]), to_tf32(v[1]), to_tf32(v[2]), to_tf32(v[3]));
+    } else {
+        uint32_t h[4], l[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const __nv_bfloat162 hv = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
+            const float2 hf = __bfloat1622float2(hv);
+            const __nv_bfloat162 lv = __floats2bfloat162_rn(v[2 * q] - hf.x, v[2 * q + 1] - hf.y);
+            h[q] = *reinterpret_cast<const uint32_t*>(&hv);
+            l[q] = *reinterpret_cast<const uint32_t*>(&lv);
+        }
+        *reinterpret_cast<uint4*>(hi + off) = make_uint4(h[0], h[1], h[2], h[3]);
+        *reinterpret_cast<uint4*>(lo + off) = make_uint4(l[0], l[1], l[2], l[3]);
+    }
+}
+
 // ------------------------------------------------------------ shared layout
 template <int MODE>
 struct Shape {
@@ -185,6 +210,7 @@ struct Shape {
     static constexpr int KSTEP = MODE == MODE_TF32 ? 8 : 16;   // K per MMA
     static constexpr int NT = MODE == MODE_TF32 ? 2 : 4;       // A tables (P, H) or (P hi, P lo, H hi, H lo)
     static constexpr int NPART = MODE == MODE_TF32 ? 1 : 2;    // B parts (hi, lo)
+    static constexpr int KV = MODE == MODE_TF32 ? 4 : 8;       // K values per 16-byte B word
 };
 
 // One pipeline stage: the A tiles of one K block, then the B tiles of the
@@ -213,6 +239,7 @@ struct TcArgs {
     size_t state_ms;      // member stride of the state (complex values)
     float2* four_in;      // synthesis output, member stride 4 J (R+1)
     const float2* four_out;  // analysis input, member stride 5 J (R+1)
+    FourStride fo;           // layout of each four_out field
     double2* FE;
     size_t fe_ms;
     const double* cor;
@@ -390,31 +417,64 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_synth(const __grid_constan
     };
     // B columns per member b: P group (zeta, Phi', chi, psi) x (re, im) + 8 x parity,
     // H group (psi, chi) x (re, im) + 8 x parity (4..7 and 12..15 zero).
+    // One work item per (member, group of KV degrees, quantity q = zeta,
+    // Phi', chi, psi): KV consecutive coefficients, each target column
+    // stored as one 16-byte word per part (K groups start at multiples of KV,
+    // so the even columns take the even v and the odd columns the odd v).
+    constexpr int KV = S::KV, NG = S::KB / S::KV;
+    if (threadIdx.x < 2 * bc) {  // the always-zero H columns, written once per stage buffer
+        const float z[KV] = {};
+        const int b = threadIdx.x >> 1, col = (threadIdx.x & 1) ? 12 : 4;
+        for (int st = 0; st < g.stages; ++st)
+            for (int gg = 0; gg < NG; ++gg)
+                for (int cc = 0; cc < 4; ++cc)
+                    put_bv<MODE>(b_tile<MODE>(c, st, 1, 0, g.chunk), b_tile<MODE>(c, st, 1, S::NPART - 1, g.chunk),
+                                 16 * b + col + cc, gg, z, lbo);
+    }
     auto build_b = [&](int st, int kb) {
         unsigned char* P0 = b_tile<MODE>(c, st, 0, 0, g.chunk);
         unsigned char* P1 = b_tile<MODE>(c, st, 0, S::NPART - 1, g.chunk);
         unsigned char* H0 = b_tile<MODE>(c, st, 1, 0, g.chunk);
         unsigned char* H1 = b_tile<MODE>(c, st, 1, S::NPART - 1, g.chunk);
-        for (int it = threadIdx.x; it < bc * S::KB; it += kTcThreads) {
-            const int b = it / S::KB, k = it - b * S::KB;
-            const int kk = kb * S::KB + k;
-            float pv[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-            if (kk < nm) {
-                const float s = g.na2_f * g.invnn[m + kk];  // psi, chi = -a^2/(n(n+1)) (zeta, delta)
-                const double2* x = g.state + (size_t)(b0 + b) * g.state_ms + off + kk;
-                const double2 ph = x[0], ze = x[g.nc], de = x[2 * g.nc];
-                pv[0] = (float)ze.x; pv[1] = (float)ze.y;
-                pv[2] = (float)ph.x; pv[3] = (float)ph.y;
-                pv[4] = (float)de.x * s; pv[5] = (float)de.y * s;
-                pv[6] = (float)ze.x * s; pv[7] = (float)ze.y * s;
+        for (int it = threadIdx.x; it < bc * 4 * NG; it += kTcThreads) {
+            const int gg = it % NG, qb = it / NG;
+            const int q = qb & 3, b = qb >> 2;
+            const int k0 = kb * S::KB + gg * KV;
+            // state fields: Phi' at 0, zeta at nc, delta at 2 nc
+            const double2* x =
+                g.state + (size_t)(b0 + b) * g.state_ms + (q == 1 ? 0 : q == 2 ? 2 * g.nc : g.nc) + off;
+            float er[KV], ei[KV], orr[KV], oi[KV];
+#pragma unroll
+            for (int v = 0; v < KV; ++v) {
+                const int kk = k0 + v;
+                float xr = 0.f, xi = 0.f;
+                if (kk < nm) {
+                    const double2 z = x[kk];
+                    xr = (float)z.x;
+                    xi = (float)z.y;
+                    if (q >= 2) {  // psi, chi = -a^2/(n(n+1)) (zeta, delta)
+                        const float sc = g.na2_f * g.invnn[m + kk];
+                        xr *= sc;
+                        xi *= sc;
+                    }
+                }
+                const bool odd = v & 1;
+                er[v] = odd ? 0.f : xr;
+                ei[v] = odd ? 0.f : xi;
+                orr[v] = odd ? xr : 0.f;
+                oi[v] = odd ? xi : 0.f;
             }
-            const int par = kk & 1;
-            for (int col = 0; col < 16; ++col) {
-                const int comp = col & 7, cpar = col >> 3;
-                const float vP = cpar == par ? pv[comp] : 0.f;
-                const float vH = (cpar == par && comp < 4) ? pv[comp < 2 ? comp + 6 : comp + 2] : 0.f;
-                put_b<MODE>(P0, P1, 16 * b + col, k, vP, lbo);
-                put_b<MODE>(H0, H1, 16 * b + col, k, vH, lbo);
+            const int r = 16 * b + 2 * q;
+            put_bv<MODE>(P0, P1, r, gg, er, lbo);
+            put_bv<MODE>(P0, P1, r + 1, gg, ei, lbo);
+            put_bv<MODE>(P0, P1, r + 8, gg, orr, lbo);
+            put_bv<MODE>(P0, P1, r + 9, gg, oi, lbo);
+            if (q >= 2) {  // H columns: psi at 0, 1; chi at 2, 3
+                const int rh = 16 * b + (q == 3 ? 0 : 2);
+                put_bv<MODE>(H0, H1, rh, gg, er, lbo);
+                put_bv<MODE>(H0, H1, rh + 1, gg, ei, lbo);
+                put_bv<MODE>(H0, H1, rh + 8, gg, orr, lbo);
+                put_bv<MODE>(H0, H1, rh + 9, gg, oi, lbo);
             }
         }
     };
@@ -424,6 +484,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_synth(const __grid_constan
     const int j = 32 * warp + lane;
     const int J = 2 * g.J2, jS = J - 1 - j;
     const size_t fs = (size_t)J * (R + 1);
+    const size_t iN = (size_t)j * (R + 1) + m, iS = (size_t)jS * (R + 1) + m;
     for (int b = 0; b < bc; ++b) {
         float vP[16], vH[16];
         tmem_ld16(lane_base + 16 * b, vP);
@@ -439,14 +500,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_synth(const __grid_constan
         const float2 sPN = cadd(cx(vP, 6), cx(vP, 14)), sPS = csub(cx(vP, 6), cx(vP, 14));
         const float2 sHN = cadd(cx(vH, 0), cx(vH, 8)), sHS = csub(cx(vH, 8), cx(vH, 0));
         const float2 xHN = cadd(cx(vH, 2), cx(vH, 10)), xHS = csub(cx(vH, 10), cx(vH, 2));
-        four[0 * fs + (size_t)j * (R + 1) + m] = zN;
-        four[0 * fs + (size_t)jS * (R + 1) + m] = zS;
-        four[1 * fs + (size_t)j * (R + 1) + m] = pN;
-        four[1 * fs + (size_t)jS * (R + 1) + m] = pS;
-        four[2 * fs + (size_t)j * (R + 1) + m] = cscale(csub(cim(dm, xPN), sHN), ia);
-        four[2 * fs + (size_t)jS * (R + 1) + m] = cscale(csub(cim(dm, xPS), sHS), ia);
-        four[3 * fs + (size_t)j * (R + 1) + m] = cscale(cadd(cim(dm, sPN), xHN), ia);
-        four[3 * fs + (size_t)jS * (R + 1) + m] = cscale(cadd(cim(dm, sPS), xHS), ia);
+        four[0 * fs + iN] = zN;
+        four[0 * fs + iS] = zS;
+        four[1 * fs + iN] = pN;
+        four[1 * fs + iS] = pS;
+        four[2 * fs + iN] = cscale(csub(cim(dm, xPN), sHN), ia);
+        four[2 * fs + iS] = cscale(csub(cim(dm, xPS), sHS), ia);
+        four[3 * fs + iN] = cscale(cadd(cim(dm, sPN), xHN), ia);
+        four[3 * fs + iS] = cscale(cadd(cim(dm, sPS), xHS), ia);
     }
     cta_release(c, tmem, ncols);
 }
@@ -480,40 +541,116 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_anal(const __grid_constant
     // B columns per member over latitudes: P group (C, A, B, E) x (re, im) + 8 x parity,
     // H group (D, B, A) x (re, im) + 8 x parity (6, 7, 14, 15 zero);
     // even = north + south, odd = north - south.
+    // m-contiguous input (launches of one or two members): one item per
+    // (member, latitude), one value per store, 64 threads busy per member.
+    // Latitude-contiguous input (more members): one item per (member, group
+    // of KV latitudes, field), two runs of KV latitudes (north and the
+    // mirrored south) read as 16-byte words, each target column stored as
+    // one 16-byte word per part; the eight lanes of a quarter warp take
+    // consecutive latitude groups, which the K-group stride (16 N + 16 bytes)
+    // puts in distinct banks.  With few members the longer per-item work of
+    // the second form measured slower; with many its fewer loads and stores win.
+    const FourStride fx = g.fo;
+    const bool lat_contig = fx.sj == 1;
+    constexpr int KV = S::KV, NG = S::KB / S::KV;
+    if (lat_contig && threadIdx.x < 2 * bc) {  // the always-zero H columns, written once per stage buffer
+        const float z[KV] = {};
+        const int b = threadIdx.x >> 1, col = (threadIdx.x & 1) ? 14 : 6;
+        for (int st = 0; st < g.stages; ++st)
+            for (int gg = 0; gg < NG; ++gg)
+                for (int cc = 0; cc < 2; ++cc)
+                    put_bv<MODE>(b_tile<MODE>(c, st, 1, 0, g.chunk), b_tile<MODE>(c, st, 1, S::NPART - 1, g.chunk),
+                                 16 * b + col + cc, gg, z, lbo);
+    }
     auto build_b = [&](int st, int kb) {
         unsigned char* P0 = b_tile<MODE>(c, st, 0, 0, g.chunk);
         unsigned char* P1 = b_tile<MODE>(c, st, 0, S::NPART - 1, g.chunk);
         unsigned char* H0 = b_tile<MODE>(c, st, 1, 0, g.chunk);
         unsigned char* H1 = b_tile<MODE>(c, st, 1, S::NPART - 1, g.chunk);
-        for (int it = threadIdx.x; it < bc * S::KB; it += kTcThreads) {
-            const int b = it / S::KB, k = it - b * S::KB;
-            const int j = kb * S::KB + k;
-            float2 e[5], o[5];
-            const float2* F = g.four_out + (size_t)(b0 + b) * 5 * fs;
-            for (int f = 0; f < 5; ++f) {
-                if (j < g.J2) {
-                    const float2 gN = F[(size_t)f * fs + (size_t)j * (R + 1) + m];
-                    const float2 gS = F[(size_t)f * fs + (size_t)(J - 1 - j) * (R + 1) + m];
-                    e[f] = cadd(gN, gS);
-                    o[f] = csub(gN, gS);
-                } else {
-                    e[f] = o[f] = make_float2(0.f, 0.f);
+        if (!lat_contig) {  // one (member, latitude) item per thread, one bf16/tf32 value per store
+            for (int it = threadIdx.x; it < bc * S::KB; it += kTcThreads) {
+                const int b = it / S::KB, k = it - b * S::KB;
+                const int j = kb * S::KB + k;
+                float2 e[5], o[5];
+                const float2* F = g.four_out + (size_t)(b0 + b) * 5 * fs;  // m-contiguous
+                for (int f = 0; f < 5; ++f) {
+                    if (j < g.J2) {
+                        const float2 gN = F[(size_t)f * fs + (size_t)j * (R + 1) + m];
+                        const float2 gS = F[(size_t)f * fs + (size_t)(J - 1 - j) * (R + 1) + m];
+                        e[f] = cadd(gN, gS);
+                        o[f] = csub(gN, gS);
+                    } else {
+                        e[f] = o[f] = make_float2(0.f, 0.f);
+                    }
+                }
+                const int pf[4] = {2, 0, 1, 4};  // C, A, B, E in four_out order A, B, C, D, E
+                const int hf[3] = {3, 1, 0};     // D, B, A
+                for (int col = 0; col < 16; ++col) {
+                    const int comp = col & 7, cpar = col >> 3;
+                    const float2* src = cpar ? o : e;
+                    const float2 zp = src[pf[comp >> 1]];
+                    const float vP = (comp & 1) ? zp.y : zp.x;
+                    float vH = 0.f;
+                    if (comp < 6) {
+                        const float2 zh = src[hf[comp >> 1]];
+                        vH = (comp & 1) ? zh.y : zh.x;
+                    }
+                    put_b<MODE>(P0, P1, 16 * b + col, k, vP, lbo);
+                    put_b<MODE>(H0, H1, 16 * b + col, k, vH, lbo);
                 }
             }
-            const int pf[4] = {2, 0, 1, 4};  // C, A, B, E in four_out order A, B, C, D, E
-            const int hf[3] = {3, 1, 0};     // D, B, A
-            for (int col = 0; col < 16; ++col) {
-                const int comp = col & 7, cpar = col >> 3;
-                const float2* src = cpar ? o : e;
-                const float2 zp = src[pf[comp >> 1]];
-                const float vP = (comp & 1) ? zp.y : zp.x;
-                float vH = 0.f;
-                if (comp < 6) {
-                    const float2 zh = src[hf[comp >> 1]];
-                    vH = (comp & 1) ? zh.y : zh.x;
+            return;
+        }
+        for (int it = threadIdx.x; it < bc * 5 * NG; it += kTcThreads) {
+            const int gg = it % NG, q = it / NG;
+            const int f = q % 5, b = q / 5;
+            const int j0 = kb * S::KB + gg * KV;
+            const float2* F = g.four_out + (size_t)(b0 + b) * 5 * fs + (size_t)f * fs + fx.at(0, m);
+            float2 gN[KV], gS[KV];
+            if (j0 + KV <= g.J2) {
+                // north j0 .. j0 + KV - 1 and south J - j0 - KV .. J - 1 - j0 (reversed)
+                const float4* pn = reinterpret_cast<const float4*>(F + j0);
+                const float4* ps = reinterpret_cast<const float4*>(F + (J - j0 - KV));
+#pragma unroll
+                for (int v = 0; v < KV / 2; ++v) {
+                    const float4 a = pn[v], z = ps[v];
+                    gN[2 * v] = make_float2(a.x, a.y);
+                    gN[2 * v + 1] = make_float2(a.z, a.w);
+                    gS[KV - 1 - 2 * v] = make_float2(z.x, z.y);
+                    gS[KV - 2 - 2 * v] = make_float2(z.z, z.w);
                 }
-                put_b<MODE>(P0, P1, 16 * b + col, k, vP, lbo);
-                put_b<MODE>(H0, H1, 16 * b + col, k, vH, lbo);
+            } else {
+#pragma unroll
+                for (int v = 0; v < KV; ++v) {
+                    const int j = j0 + v;
+                    gN[v] = j < g.J2 ? F[j] : make_float2(0.f, 0.f);
+                    gS[v] = j < g.J2 ? F[J - 1 - j] : make_float2(0.f, 0.f);
+                }
+            }
+            float er[KV], ei[KV], orr[KV], oi[KV];
+#pragma unroll
+            for (int v = 0; v < KV; ++v) {
+                const float2 e = cadd(gN[v], gS[v]), o = csub(gN[v], gS[v]);
+                er[v] = e.x;
+                ei[v] = e.y;
+                orr[v] = o.x;
+                oi[v] = o.y;
+            }
+            // four_out fields A, B, C, D, E -> (group, first column): A: P 2, H 4; B: P 4, H 2;
+            // C: P 0; D: H 0; E: P 6
+            const int cP = f == 0 ? 2 : f == 1 ? 4 : f == 2 ? 0 : f == 4 ? 6 : -1;
+            const int cH = f == 0 ? 4 : f == 1 ? 2 : f == 3 ? 0 : -1;
+#pragma unroll
+            for (int grp = 0; grp < 2; ++grp) {
+                const int c0 = grp == 0 ? cP : cH;
+                if (c0 < 0) continue;
+                unsigned char* t0 = grp == 0 ? P0 : H0;
+                unsigned char* t1 = grp == 0 ? P1 : H1;
+                const int r = 16 * b + c0;
+                put_bv<MODE>(t0, t1, r, gg, er, lbo);
+                put_bv<MODE>(t0, t1, r + 1, gg, ei, lbo);
+                put_bv<MODE>(t0, t1, r + 8, gg, orr, lbo);
+                put_bv<MODE>(t0, t1, r + 9, gg, oi, lbo);
             }
         }
     };
@@ -526,9 +663,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_anal(const __grid_constant
         tmem_ld16(lane_base + 16 * b, vP);
         tmem_ld16(lane_base + N + 16 * b, vH);
         if (!ok || k >= nm) continue;
-        const int par = k & 1;
-        const float* P8 = vP + 8 * par;        // C, A, B, E at this row's parity
-        const float* H8 = vH + 8 * (par ^ 1);  // D, B, A at the opposite parity
+        const bool par = k & 1;
+        float P8[8], H8[8];  // C, A, B, E at this row's parity; D, B, A at the opposite one
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            P8[i] = par ? vP[8 + i] : vP[i];
+            H8[i] = par ? vH[i] : vH[8 + i];
+        }
         const float2 sC{P8[0], P8[1]}, sA{P8[2], P8[3]}, sB{P8[4], P8[5]}, sE{P8[6], P8[7]};
         const float2 hD{H8[0], H8[1]}, hB{H8[2], H8[3]}, hA{H8[4], H8[5]};
         const int n = m + k;
@@ -707,33 +848,41 @@ TcArgs base_args(sh_plan_t p, TcState* s, double a, int members) {
     g.invnn = p->mp.invnn32;
     g.four_in = p->mp.four_in;
     g.four_out = p->mp.four_out;
+    g.fo = four_out_layout(p->J, p->R, members >= kLatContigMembers);
     g.cor = p->d_cor;
     g.tiles = s->d_tiles;
     g.err = s->d_err;
     return g;
 }
 
-// Autotuner: time the synthesis and analysis for a full batch of members
-// with each feasible member chunk (1, 2, 4, 8, 16 members per CTA) and K
-// pipeline depth (two stages, or one, which leaves room for more CTAs per
-// SM) and keep the fastest.  Runs once per plan, on zero inputs, at plan
-// creation.
+// Autotuner: for a full batch of members, time the stages the plan's size
+// rule runs on tensor cores at that batch (both when it runs neither, so a
+// forced choice still gets a tuned configuration) with each feasible member
+// chunk (1, 2, 4, 8, 16 members per CTA) and K pipeline depth (two stages,
+// or one, which leaves room for more CTAs per SM), and keep the fastest.
+// Each candidate is timed inside a CUDA graph of kTuneReps launches per
+// stage (the launch cost of the step graphs, not the host's launch rate);
+// a deeper or wider candidate must win by 1 % to replace a shallower one,
+// so near-ties do not flip between runs.  Runs once per plan, on zero
+// inputs, at plan creation.
+constexpr int kTuneReps = 10;
 template <int MODE>
 mlsdc_status autotune(sh_plan_t p, TcState* s) {
     const int B = p->max_members;
+    bool syn = stage_uses_tc(p, 0, B), ana = stage_uses_tc(p, 2, B);
+    if (!syn && !ana) syn = ana = true;
     const size_t n = (size_t)B * 3 * p->nc;
     double2 *x = nullptr, *fe = nullptr;
     MLSDC_CUDA(cudaMalloc((void**)&x, n * sizeof(double2)));
     MLSDC_CUDA(cudaMalloc((void**)&fe, n * sizeof(double2)));
     MLSDC_CUDA(cudaMemset(x, 0, n * sizeof(double2)));
-    cudaEvent_t e0, e1;
-    MLSDC_CUDA(cudaEventCreate(&e0));
-    MLSDC_CUDA(cudaEventCreate(&e1));
+    cudaStream_t st = nullptr;
+    MLSDC_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
     float best = 1e30f;
     int best_chunk = 1, best_stages = 0;
     mlsdc_status rs = MLSDC_OK;
     for (int cfg = 0; cfg < 10 && rs == MLSDC_OK; ++cfg) {
-        const int chunk = 1 << (cfg >> 1), stages = 2 - (cfg & 1);
+        const int chunk = 1 << (cfg >> 1), stages = 1 + (cfg & 1);  // (1,1), (1,2), (2,1), ...
         if (chunk > B || cta_smem_bytes(MODE, chunk, stages) > kSmemBudget) continue;
         s->chunk = chunk;
         s->stages = stages;
@@ -742,23 +891,23 @@ mlsdc_status autotune(sh_plan_t p, TcState* s) {
         g.state_ms = (size_t)3 * p->nc;
         g.FE = fe;
         g.fe_ms = (size_t)3 * p->nc;
-        for (int rep = 0; rep < 4 && rs == MLSDC_OK; ++rep) {
-            if (rep == 1) cudaEventRecord(e0);
-            rs = launch_synth<MODE>(p, s, g, 0);
-            if (rs == MLSDC_OK) rs = launch_anal<MODE>(p, s, g, 0);
-        }
-        cudaEventRecord(e1);
-        cudaEventSynchronize(e1);
+        auto enqueue = [&](cudaStream_t q) -> mlsdc_status {
+            mlsdc_status r = MLSDC_OK;
+            if (syn) r = launch_synth<MODE>(p, s, g, q);
+            if (r == MLSDC_OK && ana) r = launch_anal<MODE>(p, s, g, q);
+            return r;
+        };
+        rs = enqueue(st);  // outside the capture: sets the kernels' shared-memory limits
+        if (rs == MLSDC_OK) MLSDC_CUDA(cudaStreamSynchronize(st));
         float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (rs == MLSDC_OK && ms < best) {
+        if (rs == MLSDC_OK) rs = time_in_graph(st, kTuneReps, &ms, enqueue);
+        if (rs == MLSDC_OK && ms < 0.99f * best) {
             best = ms;
             best_chunk = chunk;
             best_stages = stages;
         }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    cudaStreamDestroy(st);
     cudaFree(x);
     cudaFree(fe);
     s->chunk = best_chunk;
@@ -817,7 +966,7 @@ mlsdc_status tc_synth(sh_plan_t p, const double* state, double a, RhsBatch b, cu
 }
 
 mlsdc_status tc_anal(sh_plan_t p, double a, double* FE, const double* state, double two_omega, RhsBatch b,
-                     cudaStream_t st, const NodeFuse* nf) {
+                     FourStride fo, cudaStream_t st, const NodeFuse* nf) {
     TcState* s = st_of(p);
     TcArgs g = base_args(p, s, a, b.members);
     if (nf) g.nf = *nf;
@@ -827,7 +976,15 @@ mlsdc_status tc_anal(sh_plan_t p, double a, double* FE, const double* state, dou
     g.c_cor = two_omega / (a * a);
     g.FE = (double2*)FE;
     g.fe_ms = b.fe_ms;
+    g.fo = fo;
     return s->mode == MODE_TF32 ? launch_anal<MODE_TF32>(p, s, g, st) : launch_anal<MODE_BF16X3>(p, s, g, st);
+}
+
+mlsdc_status tc_config(sh_plan_t p, int* chunk, int* stages) {
+    TcState* s = st_of(p);
+    if (chunk) *chunk = s ? s->chunk : 0;
+    if (stages) *stages = s ? (s->stages > 0 ? s->stages : stages_for(s->mode, s->chunk)) : 0;
+    return MLSDC_OK;
 }
 
 mlsdc_status tc_error(sh_plan_t p, int* code) {

@@ -13,10 +13,16 @@
 //   k_grid_rhs<T>   per latitude: real inverse FFTs, the grid products
 //                   A = (zeta+f)U, B = (zeta+f)V, C = Phi'U, D = Phi'V,
 //                   E = (U^2+V^2)/(2(1-mu^2)), real forward FFTs, weights
-//                   w/(1-mu^2)/I (A..D) or w/I (E)        -> four_out[5][J][R+1]
+//                   w/(1-mu^2)/I (A..D) or w/I (E)        -> four_out[5][..]
 //   k_anal_rhs<T>   per (m, 32 degrees), latitude tiles split over warps:
 //                   Gaussian sums with even/odd combinations, then in float64
 //                   F_E = [-div(C,D), -div(A,B), curl(A,B) + n(n+1)/a^2 E].
+// four_in is [field][J][R+1] (m contiguous).  four_out is [field][J][R+1]
+// or, chosen per launch (FourStride), [field][R+1][J] (latitudes
+// contiguous): the analysis kernels work per m over latitudes and then read
+// whole cache lines, while the FFT kernel, one latitude per CTA, writes its
+// row with stride J.  That costs the FFT kernel about 1 us at T170 and pays
+// only when a launch carries several members (measured on GB300: from three).
 #pragma once
 
 #include "complex.cuh"
@@ -25,6 +31,18 @@
 namespace mlsdc {
 
 constexpr int kSynthWarps = 4;
+
+// Element strides of latitude j and wavenumber m in one field of four_out:
+// (R + 1, 1) m-contiguous or (1, J) latitude-contiguous.
+struct FourStride {
+    int sj, sm;
+    __host__ __device__ size_t at(int j, int m) const { return (size_t)j * sj + (size_t)m * sm; }
+};
+inline FourStride four_out_layout(int J, int R, bool lat_contig) {
+    return lat_contig ? FourStride{1, J} : FourStride{R + 1, 1};
+}
+// float32 path: latitude-contiguous four_out from this many members per launch
+constexpr int kLatContigMembers = 3;
 constexpr int kAnalWarpsMax = 4;
 
 // Ensemble batching: blockIdx.y selects the member, and each array advances
@@ -107,6 +125,7 @@ __global__ void __launch_bounds__(32 * kSynthWarps) k_synth_rhs(const double2* _
     const int J = 2 * J2;
     const int jS = J - 1 - j;
     const size_t fs = (size_t)J * (R + 1);
+    const size_t iN = (size_t)j * (R + 1) + m, iS = (size_t)jS * (R + 1) + m;
     // north: P-sums e + o, H-sums e + o; south: P-sums e - o, H-sums o - e
     const C zN = cadd(e[0], o[0]), zS = csub(e[0], o[0]);
     const C pN = cadd(e[1], o[1]), pS = csub(e[1], o[1]);
@@ -114,68 +133,100 @@ __global__ void __launch_bounds__(32 * kSynthWarps) k_synth_rhs(const double2* _
     const C sPN = cadd(e[3], o[3]), sPS = csub(e[3], o[3]);
     const C sHN = cadd(e[4], o[4]), sHS = csub(o[4], e[4]);
     const C xHN = cadd(e[5], o[5]), xHS = csub(o[5], e[5]);
-    four[0 * fs + (size_t)j * (R + 1) + m] = zN;
-    four[0 * fs + (size_t)jS * (R + 1) + m] = zS;
-    four[1 * fs + (size_t)j * (R + 1) + m] = pN;
-    four[1 * fs + (size_t)jS * (R + 1) + m] = pS;
-    four[2 * fs + (size_t)j * (R + 1) + m] = cscale(csub(cim(dm, xPN), sHN), iaT);
-    four[2 * fs + (size_t)jS * (R + 1) + m] = cscale(csub(cim(dm, xPS), sHS), iaT);
-    four[3 * fs + (size_t)j * (R + 1) + m] = cscale(cadd(cim(dm, sPN), xHN), iaT);
-    four[3 * fs + (size_t)jS * (R + 1) + m] = cscale(cadd(cim(dm, sPS), xHS), iaT);
+    four[0 * fs + iN] = zN;
+    four[0 * fs + iS] = zS;
+    four[1 * fs + iN] = pN;
+    four[1 * fs + iS] = pS;
+    four[2 * fs + iN] = cscale(csub(cim(dm, xPN), sHN), iaT);
+    four[2 * fs + iS] = cscale(csub(cim(dm, xPS), sHS), iaT);
+    four[3 * fs + iN] = cscale(cadd(cim(dm, sPN), xHN), iaT);
+    four[3 * fs + iS] = cscale(cadd(cim(dm, sPS), xHS), iaT);
 }
 
-template <class T>
+// LPB latitudes per CTA (1, or 2 adjacent ones for latitude-contiguous
+// output: the two values of a (field, m) pair then leave in one store).
+template <class T, int LPB>
 __global__ void __launch_bounds__(256) k_grid_rhs(const C_t<T>* __restrict__ four_in, C_t<T>* __restrict__ four_out,
                                                   const T* __restrict__ lat, const C_t<T>* __restrict__ tw,
                                                   int R, int I, int logI, int J,
-                                                  double two_omega, MemberStrides ms) {
+                                                  double two_omega, MemberStrides ms, FourStride fx) {
     using C = C_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* sx = reinterpret_cast<C*>(smem_raw);  // [9][I/2]: zeta, Phi', U, V packed rows, then A..E
+    // [LPB][4][I/2]: zeta, Phi', U, V packed rows; then [LPB][5][I/2]: A..E; then the twiddles
+    C* sx = reinterpret_cast<C*>(smem_raw);
     const int Hn = I >> 1, logH = logI - 1;
-    C* stab = sx + 9 * Hn;                    // stage twiddles (I/2 - 1 entries)
+    C* stab = sx + 9 * LPB * Hn;                 // stage twiddles (I/2 - 1 entries)
     fft4_stage_twiddles(stab, tw, Hn, logH, I);  // constant table
     pdl_wait();
     pdl_launch();
     four_in += blockIdx.y * ms.four_in;
     four_out += blockIdx.y * ms.four_out;
-    const int j = blockIdx.x;
+    const int j0 = blockIdx.x * LPB;
     const size_t fs = (size_t)J * (R + 1);
-    for (int t = threadIdx.x; t < 4 * Hn; t += blockDim.x) {
-        const int f = t >> logH, k = t & (Hn - 1);
-        sx[f * Hn + swz(k)] = irfft_pack(four_in + f * fs + (size_t)j * (R + 1), k, R, Hn, tw);
+    for (int t = threadIdx.x; t < 4 * LPB * Hn; t += blockDim.x) {
+        const int r = t >> logH, k = t & (Hn - 1);  // row r = 4 l + f
+        const int l = r >> 2, f = r & 3;
+        sx[r * Hn + swz(k)] = irfft_pack(four_in + f * fs + (size_t)(j0 + l) * (R + 1), k, R, Hn, tw);
     }
     __syncthreads();
     // inverse by decimation in frequency: slot q now holds the longitude pair
     // at the digit-reversed position of q
-    fft4_dif(sx, 4, Hn, logH, stab, true);
+    fft4_dif(sx, 4 * LPB, Hn, logH, stab, true);
+    C* y = sx + 4 * LPB * Hn;
     // lat[j] = (mu, 1/(1-mu^2), w/((1-mu^2) I), w/I): no float64 division here
-    const T f = T(two_omega) * lat[4 * j];
-    const T rc = lat[4 * j + 1];
-    C* y = sx + 4 * Hn;
-    for (int q0 = threadIdx.x; q0 < Hn; q0 += blockDim.x) {
+    T fl[LPB], rcl[LPB];
+#pragma unroll
+    for (int l = 0; l < LPB; ++l) {
+        fl[l] = T(two_omega) * lat[4 * (j0 + l)];
+        rcl[l] = lat[4 * (j0 + l) + 1];
+    }
+    for (int t = threadIdx.x; t < LPB * Hn; t += blockDim.x) {
+        const int l = LPB == 1 ? 0 : t >> logH;
+        const C* xl = sx + 4 * l * Hn;
+        C* yl = y + 5 * l * Hn;
+        const T f = LPB == 1 ? fl[0] : (l ? fl[LPB - 1] : fl[0]);
+        const T rc = LPB == 1 ? rcl[0] : (l ? rcl[LPB - 1] : rcl[0]);
         // .x and .y hold the two longitudes of one packed pair; products are
         // pointwise, so they stay in the same (permuted, swizzled) slot
-        const int q = swz(q0);
-        const C z = sx[q], p = sx[Hn + q], u = sx[2 * Hn + q], v = sx[3 * Hn + q];
+        const int q = swz(t & (Hn - 1));
+        const C z = xl[q], p = xl[Hn + q], u = xl[2 * Hn + q], v = xl[3 * Hn + q];
         const T zf0 = z.x + f, zf1 = z.y + f;
-        y[q] = mkc(zf0 * u.x, zf1 * u.y);                                        // A
-        y[Hn + q] = mkc(zf0 * v.x, zf1 * v.y);                                   // B
-        y[2 * Hn + q] = mkc(p.x * u.x, p.y * u.y);                               // C
-        y[3 * Hn + q] = mkc(p.x * v.x, p.y * v.y);                               // D
-        y[4 * Hn + q] = mkc(T(0.5) * (u.x * u.x + v.x * v.x) * rc,               // E
-                            T(0.5) * (u.y * u.y + v.y * v.y) * rc);
+        yl[q] = mkc(zf0 * u.x, zf1 * u.y);                                        // A
+        yl[Hn + q] = mkc(zf0 * v.x, zf1 * v.y);                                   // B
+        yl[2 * Hn + q] = mkc(p.x * u.x, p.y * u.y);                               // C
+        yl[3 * Hn + q] = mkc(p.x * v.x, p.y * v.y);                               // D
+        yl[4 * Hn + q] = mkc(T(0.5) * (u.x * u.x + v.x * v.x) * rc,               // E
+                             T(0.5) * (u.y * u.y + v.y * v.y) * rc);
     }
     __syncthreads();
     // forward by decimation in time from the digit-reversed slots: natural order out
-    fft4_dit(y, 5, Hn, logH, stab, false);
-    const T sAD = lat[4 * j + 2];
-    const T sE = lat[4 * j + 3];
+    fft4_dit(y, 5 * LPB, Hn, logH, stab, false);
+    T sAD[LPB], sE[LPB];  // w/((1-mu^2) I) for A..D, w/I for E
+#pragma unroll
+    for (int l = 0; l < LPB; ++l) {
+        sAD[l] = lat[4 * (j0 + l) + 2];
+        sE[l] = lat[4 * (j0 + l) + 3];
+    }
     for (int t = threadIdx.x; t < 5 * (R + 1); t += blockDim.x) {
         const int fld = t / (R + 1);
         const int m = t - fld * (R + 1);
-        const C X = rfft_unpack_sw(y + fld * Hn, m, Hn, tw);
-        four_out[(size_t)fld * fs + (size_t)j * (R + 1) + m] = cscale(X, fld < 4 ? sAD : sE);
+        if (LPB == 1) {
+            const C X = rfft_unpack_sw(y + fld * Hn, m, Hn, tw);
+            four_out[(size_t)fld * fs + fx.at(j0, m)] = cscale(X, fld < 4 ? sAD[0] : sE[0]);
+        } else {
+            C X[LPB];
+#pragma unroll
+            for (int l = 0; l < LPB; ++l)
+                X[l] = cscale(rfft_unpack_sw(y + (5 * l + fld) * Hn, m, Hn, tw), fld < 4 ? sAD[l] : sE[l]);
+            C* dst = four_out + (size_t)fld * fs + fx.at(j0, m);
+            if (sizeof(C) == 8 && fx.sj == 1) {
+                // two adjacent latitudes: one 16-byte store (j0, J even: aligned)
+                *reinterpret_cast<float4*>(dst) = make_float4(X[0].x, X[0].y, X[1].x, X[1].y);
+            } else {
+#pragma unroll
+                for (int l = 0; l < LPB; ++l) dst[(size_t)l * fx.sj] = X[l];
+            }
+        }
     }
 }
 
@@ -228,7 +279,7 @@ __global__ void __launch_bounds__(32 * kAnalWarpsMax) k_anal_rhs(const C_t<T>* _
                                                                  int nc, double ia, double a2, double2* __restrict__ FE,
                                                                  const double2* __restrict__ state,
                                                                  double two_omega_lin, const double* __restrict__ cor,
-                                                                 MemberStrides ms, NodeFuse nf) {
+                                                                 MemberStrides ms, FourStride fx, NodeFuse nf) {
     using C = C_t<T>;
     constexpr int TW = 32;                    // latitudes per tile
     pdl_wait();
@@ -257,13 +308,14 @@ __global__ void __launch_bounds__(32 * kAnalWarpsMax) k_anal_rhs(const C_t<T>* _
     const T* Hrow = H + (size_t)(off + (live ? k : k0)) * J2;
     for (int jt = wid * TW; jt < J2; jt += nw * TW) {
         const int nl = min(TW, J2 - jt);
-        for (int t = lane; t < nl * 5; t += 32) {
-            const int jj = t / 5, f = t - jj * 5;
-            const int jn = jt + jj, js = J - 1 - jn;
-            const C gN = four_out[(size_t)f * fs + (size_t)jn * (R + 1) + m];
-            const C gS = four_out[(size_t)f * fs + (size_t)js * (R + 1) + m];
-            sG[wid][jj][f][0] = cadd(gN, gS);
-            sG[wid][jj][f][1] = csub(gN, gS);
+        if (lane < nl) {
+            const int jn = jt + lane, js = J - 1 - jn;  // consecutive lanes: consecutive latitudes
+            for (int f = 0; f < 5; ++f) {
+                const C gN = four_out[(size_t)f * fs + fx.at(jn, m)];
+                const C gS = four_out[(size_t)f * fs + fx.at(js, m)];
+                sG[wid][lane][f][0] = cadd(gN, gS);
+                sG[wid][lane][f][1] = csub(gN, gS);
+            }
         }
         __syncwarp();
         if (live) {
@@ -323,8 +375,8 @@ __global__ void __launch_bounds__(32 * kAnalWarpsMax) k_anal_rhs(const C_t<T>* _
 
 // Launch helpers shared by both precisions.
 template <class T>
-inline size_t grid_smem(int I) {
-    return sizeof(C_t<T>) * 10 * (size_t)(I / 2);  // nine rows and the twiddles
+inline size_t grid_smem(int I, int lpb = 1) {
+    return sizeof(C_t<T>) * (9 * lpb + 1) * (size_t)(I / 2);  // nine rows per latitude and the twiddles
 }
 template <class T>
 inline size_t synth_smem(int R) {

@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(32) k_anal_scalar_f64(const double2* __restric
 
 mlsdc_status f64_prepare(sh_plan_t p) {
     mlsdc_status s;
-    if ((s = raise_smem_limit((const void*)k_grid_rhs<double>, grid_smem<double>(p->I))) != MLSDC_OK) return s;
+    if ((s = raise_smem_limit((const void*)k_grid_rhs<double, 1>, grid_smem<double>(p->I))) != MLSDC_OK) return s;
     if ((s = raise_smem_limit((const void*)k_synth_rhs<double>, synth_smem<double>(p->R))) != MLSDC_OK) return s;
     return MLSDC_OK;
 }
@@ -127,6 +127,7 @@ mlsdc_status rhs_explicit_f64(sh_plan_t p, const swe_params* prm, const double* 
     const NodeFuse& fuse = nf ? *nf : none;
     const size_t fs = (size_t)p->J * (R + 1);
     const MemberStrides ms{b.state_ms, 4 * fs, 5 * fs, b.fe_ms};
+    const FourStride fo = four_out_layout(p->J, R, false);  // float64 path: m-contiguous
     if (stage == 0 || stage < 0) {
         MLSDC_LAUNCH("k_synth_rhs<double>",
                      launch_k(k_synth_rhs<double>, dim3(p->n_synth, b.members), dim3(32 * kSynthWarps),
@@ -136,16 +137,16 @@ mlsdc_status rhs_explicit_f64(sh_plan_t p, const swe_params* prm, const double* 
     }
     if (stage == 1 || stage < 0) {
         MLSDC_LAUNCH("k_grid_rhs<double>",
-                     launch_k(k_grid_rhs<double>, dim3(p->J, b.members), dim3(256), grid_smem<double>(p->I),
+                     launch_k(k_grid_rhs<double, 1>, dim3(p->J, b.members), dim3(256), grid_smem<double>(p->I),
                               st, (const double2*)p->d_four_in, p->d_four_out, (const double*)p->d_lat,
-                              (const double2*)p->d_tw, R, p->I, p->logI, p->J, 2.0 * prm->omega, ms));
+                              (const double2*)p->d_tw, R, p->I, p->logI, p->J, 2.0 * prm->omega, ms, fo));
     }
     if (stage == 2 || stage < 0) {
         MLSDC_LAUNCH("k_anal_rhs<double>",
                      launch_k(k_anal_rhs<double>, dim3(p->n_anal, b.members), dim3(32 * anal_warps(p->J2)), 0, st,
                               (const double2*)p->d_four_out, (const double*)p->d_P, (const double*)p->d_H,
                               (const Chunk*)p->d_anal, R, p->J2, p->nc, 1.0 / prm->a, prm->a * prm->a, (double2*)FE,
-                              (const double2*)state, 0.0, (const double*)p->d_cor, ms, fuse));
+                              (const double2*)state, 0.0, (const double*)p->d_cor, ms, fo, fuse));
     }
     if (launches) *launches += stage < 0 ? 3 : 1;
     return MLSDC_OK;

@@ -26,10 +26,11 @@ __global__ void k_round_c32(const double2* __restrict__ x, float2* __restrict__ 
 }
 
 mlsdc_status tc_init(sh_plan_t p);   // legendre_tc.cu
+mlsdc_status tc_config(sh_plan_t p, int* chunk, int* stages);
 void tc_free(sh_plan_t p);
 mlsdc_status tc_synth(sh_plan_t p, const double* state, double a, RhsBatch b, cudaStream_t st);
 mlsdc_status tc_anal(sh_plan_t p, double a, double* FE, const double* state, double two_omega, RhsBatch b,
-                     cudaStream_t st, const NodeFuse* nf);
+                     FourStride fo, cudaStream_t st, const NodeFuse* nf);
 
 constexpr int kStageAuto = 0, kStageTc = 1, kStageSimt = 2;
 
@@ -41,7 +42,7 @@ constexpr int kStageAuto = 0, kStageTc = 1, kStageSimt = 2;
 // B operand costs more to stage than the CUDA-core sums).  A fixed rule keeps
 // results reproducible run to run; the CUDA-core kernels use float32
 // operands, at least as accurate as split-BF16 or TF32.
-static bool stage_uses_tc(const sh_plan_s* p, int stage, int members) {
+bool stage_uses_tc(const sh_plan_s* p, int stage, int members) {
     const int mode = stage == 0 ? p->mp.synth_mode : p->mp.anal_mode;
     if (mode != kStageAuto) return mode == kStageTc;
     return stage == 0 ? (p->R >= 128 && members >= 8) : p->R >= 64;
@@ -73,7 +74,8 @@ mlsdc_status mp_init(sh_plan_t p) {
     k_round_f32<<<8, 256>>>(p->d_invnn, t.invnn32, (size_t)(p->R + 1));
     MLSDC_LAUNCHED("k_round_f32");
     MLSDC_CUDA(cudaDeviceSynchronize());
-    mlsdc_status rs = raise_smem_limit((const void*)k_grid_rhs<float>, grid_smem<float>(p->I));
+    mlsdc_status rs = raise_smem_limit((const void*)k_grid_rhs<float, 1>, grid_smem<float>(p->I));
+    if (rs == MLSDC_OK) rs = raise_smem_limit((const void*)k_grid_rhs<float, 2>, grid_smem<float>(p->I, 2));
     if (rs != MLSDC_OK) return rs;
     if (p->precision == MLSDC_TF32 || p->precision == MLSDC_BF16X3) return tc_init(p);
     return MLSDC_OK;
@@ -102,6 +104,7 @@ mlsdc_status rhs_explicit_mp(sh_plan_t p, const swe_params* prm, const double* s
     const bool tc = p->precision == MLSDC_TF32 || p->precision == MLSDC_BF16X3;
     const size_t fs = (size_t)p->J * (R + 1);
     const MemberStrides ms{b.state_ms, 4 * fs, 5 * fs, b.fe_ms};
+    const FourStride fo = four_out_layout(p->J, R, b.members >= kLatContigMembers);
     mlsdc_status s;
     if (stage == 0 || stage < 0) {
         if (tc && stage_uses_tc(p, 0, b.members)) {
@@ -115,21 +118,28 @@ mlsdc_status rhs_explicit_mp(sh_plan_t p, const swe_params* prm, const double* s
         }
     }
     if (stage == 1 || stage < 0) {
-        MLSDC_LAUNCH("k_grid_rhs<float>",
-                     launch_k(k_grid_rhs<float>, dim3(p->J, b.members), dim3(256), grid_smem<float>(p->I), st,
-                              (const float2*)t.four_in, t.four_out, (const float*)t.lat32, (const float2*)t.tw32, R,
-                              p->I, p->logI, p->J, 0.0, ms));
+        if (fo.sj == 1) {  // latitude-contiguous output: two adjacent latitudes per CTA
+            MLSDC_LAUNCH("k_grid_rhs<float, 2>",
+                         launch_k(k_grid_rhs<float, 2>, dim3(p->J / 2, b.members), dim3(256),
+                                  grid_smem<float>(p->I, 2), st, (const float2*)t.four_in, t.four_out,
+                                  (const float*)t.lat32, (const float2*)t.tw32, R, p->I, p->logI, p->J, 0.0, ms, fo));
+        } else {
+            MLSDC_LAUNCH("k_grid_rhs<float, 1>",
+                         launch_k(k_grid_rhs<float, 1>, dim3(p->J, b.members), dim3(256), grid_smem<float>(p->I), st,
+                                  (const float2*)t.four_in, t.four_out, (const float*)t.lat32,
+                                  (const float2*)t.tw32, R, p->I, p->logI, p->J, 0.0, ms, fo));
+        }
     }
     if (stage == 2 || stage < 0) {
         if (tc && stage_uses_tc(p, 2, b.members)) {
-            if ((s = tc_anal(p, prm->a, FE, state, 2.0 * prm->omega, b, st, nf)) != MLSDC_OK) return s;
+            if ((s = tc_anal(p, prm->a, FE, state, 2.0 * prm->omega, b, fo, st, nf)) != MLSDC_OK) return s;
         } else {
             MLSDC_LAUNCH("k_anal_rhs<float>",
                          launch_k(k_anal_rhs<float>, dim3(p->n_anal, b.members), dim3(32 * anal_warps(p->J2)), 0, st,
                                   (const float2*)t.four_out, (const float*)t.P32, (const float*)t.H32,
                                   (const Chunk*)p->d_anal, R, p->J2, p->nc, 1.0 / prm->a, prm->a * prm->a,
                                   (double2*)FE, (const double2*)state, 2.0 * prm->omega, (const double*)p->d_cor, ms,
-                                  fuse));
+                                  fo, fuse));
         }
     }
     if (launches) *launches += stage < 0 ? 3 : 1;
@@ -144,6 +154,11 @@ extern "C" mlsdc_status sh_plan_stage_kernels(sh_plan_t p, int members, int* syn
     if (synth_tc) *synth_tc = tc && mlsdc::stage_uses_tc(p, 0, members) ? 1 : 0;
     if (anal_tc) *anal_tc = tc && mlsdc::stage_uses_tc(p, 2, members) ? 1 : 0;
     return MLSDC_OK;
+}
+
+extern "C" mlsdc_status sh_plan_tc_config(sh_plan_t p, int* members_per_cta, int* stages) {
+    if (!p) return MLSDC_ERR_INVALID;
+    return mlsdc::tc_config(p, members_per_cta, stages);
 }
 
 extern "C" mlsdc_status sh_plan_set_stage_kernels(sh_plan_t p, int synth_mode, int anal_mode) {

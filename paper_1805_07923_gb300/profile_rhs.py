@@ -57,7 +57,8 @@ def main(argv=None):
     else:
         ms = M.mlsdc_profile_rhs(plan, prm, x, fe, reps=20, members=a.members)
     print(json.dumps({"R": a.R, "nlon": a.nlon, "nlat": a.nlat, "precision": a.precision, "members": a.members,
-                      "adjoint": a.adjoint, "stage_ms": ms, "stage_kernels_tc": plan.stage_kernels(a.members)}))
+                      "adjoint": a.adjoint, "stage_ms": ms, "stage_kernels_tc": plan.stage_kernels(a.members),
+                      "tc_config": plan.tc_config()}))
 
 
 if __name__ == "__main__":
