@@ -163,7 +163,7 @@ struct sh_plan_s {
     double* d_H = nullptr;            // [nc][J2]
     double2* d_tw = nullptr;          // [I/2] exp(-2 pi i k / I)
     int* d_ndeg = nullptr;            // [nc] total degree n of each coefficient
-    double* d_cor = nullptr;          // [nc][5] Coriolis recurrence factors (coriolis_linear)
+    double* d_cor = nullptr;          // [nc][4] Coriolis factors alpha, beta, gamma, 0 (coriolis_add)
     // Per-latitude and per-degree constants, computed on the host in float64
     // so no kernel divides in float64 (about 1/64 of the float32 rate here):
     double* d_lat = nullptr;          // [J][4] mu, 1/(1-mu^2), w/((1-mu^2) I), w/I

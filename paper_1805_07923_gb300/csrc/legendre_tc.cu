@@ -234,7 +234,7 @@ __host__ __device__ inline uint32_t tmem_cols_for(int ncols) {
 
 struct TcArgs {
     int R, J2, nc, J2p, members, chunk, stages;
-    double a, two_omega;
+    double two_omega;
     const double2* state;
     size_t state_ms;      // member stride of the state (complex values)
     float2* four_in;      // synthesis output, member stride 4 J (R+1)
@@ -247,7 +247,6 @@ struct TcArgs {
     int* err;
     NodeFuse nf;  // the next node's update, run in the analysis epilogue (nf.on)
     // host-computed constants (no float64 division in the kernels)
-    double ia, a2, c_cor;    // 1/a, a^2, 2 Omega / a^2
     float ia_f, na2_f;       // 1/a, -a^2
     const float* invnn;      // [R+1] 1/(n(n+1)), 0 for n = 0
 };
@@ -683,11 +682,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_anal(const __grid_constant
         double2 f0 = make_double2(-(double)divCD.x, -(double)divCD.y);
         double2 f1 = make_double2(-(double)divAB.x, -(double)divAB.y);
         double2 f2 = make_double2((double)(curlAB.x + lap * sE.x), (double)(curlAB.y + lap * sE.y));
-        double2 dz, dd;  // the Coriolis part, exactly in float64 (grid products carry no f)
-        coriolis_linear(g.state + (size_t)(b0 + b) * g.state_ms, g.cor, g.nc, R, m, n, off, g.a2, g.two_omega,
-                        g.c_cor, dz, dd);
-        f1 = cadd(f1, dz);
-        f2 = cadd(f2, dd);
+        // the Coriolis part, exactly in float64 (grid products carry no f)
+        coriolis_add(g.state + (size_t)(b0 + b) * g.state_ms, g.cor, g.nc, R, m, n, off, g.two_omega, f1, f2);
         if (m == 0) f0.y = f1.y = f2.y = 0.0;
         double2* FE = g.FE + (size_t)(b0 + b) * g.fe_ms;
         FE[off + k] = f0;
@@ -840,9 +836,6 @@ TcArgs base_args(sh_plan_t p, TcState* s, double a, int members) {
     g.members = members;
     g.chunk = std::min(s->chunk, members);
     g.stages = s->stages > 0 ? s->stages : stages_for(s->mode, g.chunk);
-    g.a = a;
-    g.ia = 1.0 / a;
-    g.a2 = a * a;
     g.ia_f = (float)(1.0 / a);
     g.na2_f = (float)(-a * a);
     g.invnn = p->mp.invnn32;
@@ -973,7 +966,6 @@ mlsdc_status tc_anal(sh_plan_t p, double a, double* FE, const double* state, dou
     g.state = (const double2*)state;
     g.state_ms = b.state_ms;
     g.two_omega = two_omega;
-    g.c_cor = two_omega / (a * a);
     g.FE = (double2*)FE;
     g.fe_ms = b.fe_ms;
     g.fo = fo;

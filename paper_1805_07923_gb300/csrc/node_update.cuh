@@ -24,6 +24,19 @@ struct NodeRow {
     int M;    // nodes 0..M
 };
 
+// The row with every coefficient multiplied by dt, formed on the host: the
+// node kernels take it so that no thread repeats the uniform products (the
+// same float64 products, so the results do not change).
+__host__ __device__ inline NodeRow dt_scaled(NodeRow r, double dt) {
+    for (int j = 0; j < kMaxNodes; ++j) {
+        r.qe[j] *= dt;
+        r.qi[j] *= dt;
+        r.q[j] *= dt;
+    }
+    r.qimm *= dt;
+    return r;
+}
+
 __device__ __forceinline__ double2 cax(double2 acc, double s, double2 x) {
     return make_double2(fma(s, x.x, acc.x), fma(s, x.y, acc.y));
 }
@@ -68,27 +81,53 @@ __device__ __forceinline__ void implicit_solve_tab(double L, double alpha, const
     d = make_double2((bd.x - alpha * L * p.x) * ic, (bd.y - alpha * L * p.y) * ic);
 }
 
+// Field f (0 Phi', 1 zeta, 2 delta) of implicit_solve_tab followed by
+// implicit_rhs_coef: the new value th and its F_I, by the same expressions,
+// without the other fields' work (zeta needs only its own right-hand side;
+// Phi' and delta need both p and d).
+__device__ __forceinline__ void node_solve_field(int f, double L, double alpha, const Phys& ph, double2 r,
+                                                 double2 bp, double2 bz, double2 bd, double2& th, double2& fi) {
+    const double ic = r.x, den = r.y;
+    const double nl = ph.nu * L;
+    if (f == 1) {
+        th = make_double2(bz.x * ic, bz.y * ic);
+        fi = make_double2(nl * th.x, nl * th.y);
+        return;
+    }
+    const double c = 1.0 - alpha * ph.nu * L;
+    const double2 p = make_double2((c * bp.x - alpha * ph.phibar * bd.x) * den, (c * bp.y - alpha * ph.phibar * bd.y) * den);
+    const double2 d = make_double2((bd.x - alpha * L * p.x) * ic, (bd.y - alpha * L * p.y) * ic);
+    if (f == 0) {
+        th = p;
+        fi = make_double2(-ph.phibar * d.x + nl * p.x, -ph.phibar * d.y + nl * p.y);
+    } else {
+        th = d;
+        fi = make_double2(-L * p.x + nl * d.x, -L * p.y + nl * d.y);
+    }
+}
+
 // The right-hand side b of the node update at one (field, coefficient)
 // offset o of a member's node arrays ([M+1][3][nc], node = 3 nc):
 //   b = Th[0] + sum_{j=1..m} dt (qE_j (FEn_j - FEo_j) + qI_j (FIn_j - FIo_j))
 //       - dt qI_{m+1,m+1} FIo_{m+1} + sum_{j=0..M} dt q_j (FIo_j + FEo_j) [+ tau_{m+1}]
+// `row` is dt_scaled.
 __device__ __forceinline__ double2 node_rhs(const double2* Th, const double2* FIo, const double2* FEo,
                                             const double2* FIn, const double2* FEn, const double2* tau,
-                                            size_t node, size_t o, double dt, const NodeRow& row) {
+                                            size_t node, size_t o, const NodeRow& row) {
     const int m = row.m;
     double2 acc = Th[o];  // Theta^n (node 0)
     for (int j = 1; j <= m; ++j) {
         const size_t oj = j * node + o;
         const double2 de = make_double2(FEn[oj].x - FEo[oj].x, FEn[oj].y - FEo[oj].y);
         const double2 di = make_double2(FIn[oj].x - FIo[oj].x, FIn[oj].y - FIo[oj].y);
-        acc = cax(acc, dt * row.qe[j], de);
-        acc = cax(acc, dt * row.qi[j], di);
+        acc = cax(acc, row.qe[j], de);
+        acc = cax(acc, row.qi[j], di);
     }
-    acc = cax(acc, -dt * row.qimm, FIo[(m + 1) * node + o]);
+    acc = cax(acc, -row.qimm, FIo[(m + 1) * node + o]);
     for (int j = 0; j <= row.M; ++j) {
         const size_t oj = j * node + o;
         const double2 s = make_double2(FIo[oj].x + FEo[oj].x, FIo[oj].y + FEo[oj].y);
-        acc = cax(acc, dt * row.q[j], s);
+        acc = cax(acc, row.q[j], s);
     }
     if (tau) {
         const double2 t = tau[(m + 1) * node + o];
@@ -107,8 +146,7 @@ struct NodeFuse {
     const double2* tau;
     const int* ndeg;
     const double2* recips;  // [R+1] solve_recips of this node, by degree
-    double dt;
-    NodeRow row;
+    NodeRow row;            // dt_scaled
     Phys ph;
     size_t ms;
     int on;
@@ -124,12 +162,12 @@ __device__ __forceinline__ void node_update_coef(const NodeFuse& f, int nc, int 
     const double2 *FIn = f.FIn + mo, *FEn = f.FEn + mo;
     const double2* tau = f.tau ? f.tau + mo : nullptr;
     double2 b[3];
-    for (int q = 0; q < 3; ++q) b[q] = node_rhs(Th0, FIo, FEo, FIn, FEn, tau, node, (size_t)q * nc + c, f.dt, f.row);
+    for (int q = 0; q < 3; ++q) b[q] = node_rhs(Th0, FIo, FEo, FIn, FEn, tau, node, (size_t)q * nc + c, f.row);
     const int nd = f.ndeg[c];
     const double n = nd;
     const double L = -n * (n + 1.0) * f.ph.inv_a2;
     double2 p, z, d;
-    implicit_solve_tab(L, f.dt * f.row.qimm, f.ph, f.recips[nd], b[0], b[1], b[2], p, z, d);
+    implicit_solve_tab(L, f.row.qimm, f.ph, f.recips[nd], b[0], b[1], b[2], p, z, d);
     double2 fp, fz, fd;
     implicit_rhs_coef(L, f.ph, p, z, d, fp, fz, fd);
     const size_t om = (f.row.m + 1) * node + c;

@@ -237,21 +237,23 @@ mlsdc_status mlsdc::create_plan(int R, int nlon, int nlat, int precision, int ma
     std::vector<int> ndeg(p->nc);
     for (int m = 0; m <= R; ++m)
         for (int n = m; n <= R; ++n) ndeg[moff(R, m) + n - m] = n;
-    // Coriolis recurrence factors per coefficient (see coriolis_linear):
-    // eps_n, eps_{n+1}, -(n-1) eps_n inv_{n-1}, (n+2) eps_{n+1} inv_{n+1}, inv_n
-    // with inv_n = -1/(n(n+1)); the radius is a call parameter, so the last
-    // three are stored for a = 1 and multiplied by a^2 on the device.
-    std::vector<double> cor((size_t)5 * p->nc);
+    // Coriolis factors per coefficient (see coriolis_add): with
+    // inv_n = -1/(n(n+1)) (0 for n = 0) and eps zero outside m <= n <= R,
+    //   alpha = eps_n - (n-1) eps_n inv_{n-1}   (factor of x_{n-1})
+    //   beta  = eps_{n+1} + (n+2) eps_{n+1} inv_{n+1}   (factor of x_{n+1})
+    //   gamma = m inv_n
+    // (the radius cancels: psi, chi carry a^2 and the H term 1/a^2), padded
+    // to four doubles.
+    std::vector<double> cor((size_t)4 * p->nc);
     for (int m = 0; m <= R; ++m)
         for (int n = m; n <= R; ++n) {
             auto inv = [](int nn) { return nn > 0 ? -1.0 / (nn * (nn + 1.0)) : 0.0; };
             const double en = eps_mn(m, n), en1 = (n + 1 <= R) ? eps_mn(m, n + 1) : 0.0;
-            double* c = &cor[(size_t)5 * (moff(R, m) + n - m)];
-            c[0] = en;
-            c[1] = en1;
-            c[2] = -(n - 1.0) * en * inv(n - 1);
-            c[3] = (n + 2.0) * en1 * inv(n + 1);
-            c[4] = inv(n);
+            double* c = &cor[(size_t)4 * (moff(R, m) + n - m)];
+            c[0] = en - (n - 1.0) * en * inv(n - 1);
+            c[1] = en1 + (n + 2.0) * en1 * inv(n + 1);
+            c[2] = m * inv(n);
+            c[3] = 0.0;
         }
 
     // Latitude constants of the grid products and the Fourier weights

@@ -238,34 +238,32 @@ __global__ void __launch_bounds__(256) k_grid_rhs(const C_t<T>* __restrict__ fou
 //   (mu x)_n = eps_n x_{n-1} + eps_{n+1} x_{n+1},
 //   (H x)_n  = -(n-1) eps_n x_{n-1} + (n+2) eps_{n+1} x_{n+1},
 // from mu P_n = eps_{n+1} P_{n+1} + eps_n P_{n-1} and H_n = (1 - mu^2) dP_n/dmu,
-// projected on n <= R; psi, chi = -a^2/(n(n+1)) (zeta, delta).  The
-// mixed-precision paths add this term in float64 and send only the nonlinear
-// part of the products through the reduced-precision transforms.
-// cor[5 * idx .. +4] = (eps_n, eps_{n+1}, -(n-1) eps_n inv_{n-1}, (n+2) eps_{n+1} inv_{n+1}, inv_n)
-// with inv_n = -1/(n(n+1)) (0 for n = 0; times a^2 here) and eps zero outside
-// m <= n <= R (precomputed per plan: float64 square roots and divisions are
-// slow on this GPU).
-// a2 = a^2 and c = 2 Omega / a^2 are computed once on the host.
-__device__ inline void coriolis_linear(const double2* __restrict__ state, const double* __restrict__ cor, int nc,
-                                       int R, int m, int n, int off, double a2, double two_omega, double c,
-                                       double2& dz, double2& dd) {
+// projected on n <= R; psi, chi = -a^2/(n(n+1)) (zeta, delta).  Collecting
+// the factors of each neighbour (the a^2 of psi, chi cancels the 1/a^2):
+//   dzeta  = -2 Omega [ alpha delta_{n-1} + beta delta_{n+1} + gamma i zeta_n ]
+//   ddelta =  2 Omega [ alpha zeta_{n-1}  + beta zeta_{n+1}  - gamma i delta_n ]
+// with the plan's per-coefficient factors cor[4 idx .. +2] = (alpha, beta,
+// gamma): 16 float64 operations per coefficient (float64 runs at a small
+// fraction of the float32 rate on this GPU).  The mixed-precision paths add
+// this term in float64 and send only the nonlinear part of the products
+// through the reduced-precision transforms.  Adds dzeta to f1 and ddelta to f2.
+__device__ inline void coriolis_add(const double2* __restrict__ state, const double* __restrict__ cor, int nc, int R,
+                                    int m, int n, int off, double two_omega, double2& f1, double2& f2) {
     const int k = n - m;
     const double2* z = state + nc + off;
     const double2* d = state + 2 * nc + off;
     double2 zl{0, 0}, zu{0, 0}, dl{0, 0}, du{0, 0};
     if (n - 1 >= m) { zl = z[k - 1]; dl = d[k - 1]; }
     if (n + 1 <= R) { zu = z[k + 1]; du = d[k + 1]; }
-    const double* c5 = cor + 5 * (size_t)(off + k);
-    const double en = c5[0], en1 = c5[1], cl = c5[2] * a2, cu = c5[3] * a2, in = c5[4] * a2;
-    const double2 muD = make_double2(en * dl.x + en1 * du.x, en * dl.y + en1 * du.y);
-    const double2 muZ = make_double2(en * zl.x + en1 * zu.x, en * zl.y + en1 * zu.y);
-    const double2 Hchi = make_double2(cl * dl.x + cu * du.x, cl * dl.y + cu * du.y);
-    const double2 Hpsi = make_double2(cl * zl.x + cu * zu.x, cl * zl.y + cu * zu.y);
-    const double2 psi = make_double2(in * z[k].x, in * z[k].y);
-    const double2 chi = make_double2(in * d[k].x, in * d[k].y);
-    const double dm = (double)m;
-    dz = make_double2(-two_omega * muD.x - c * (-dm * psi.y + Hchi.x), -two_omega * muD.y - c * (dm * psi.x + Hchi.y));
-    dd = make_double2(two_omega * muZ.x - c * (-dm * chi.y - Hpsi.x), two_omega * muZ.y - c * (dm * chi.x - Hpsi.y));
+    const double2 zk = z[k], dk = d[k];
+    const double2 ab = *reinterpret_cast<const double2*>(cor + 4 * (size_t)(off + k));
+    const double al = ab.x, be = ab.y, ga = cor[4 * (size_t)(off + k) + 2];
+    const double ux = fma(al, dl.x, fma(be, du.x, -ga * zk.y)), uy = fma(al, dl.y, fma(be, du.y, ga * zk.x));
+    const double vx = fma(al, zl.x, fma(be, zu.x, ga * dk.y)), vy = fma(al, zl.y, fma(be, zu.y, -ga * dk.x));
+    f1.x = fma(-two_omega, ux, f1.x);
+    f1.y = fma(-two_omega, uy, f1.y);
+    f2.x = fma(two_omega, vx, f2.x);
+    f2.y = fma(two_omega, vy, f2.y);
 }
 
 // div(X,Y)^m_n = (1/a) sum_j [ i m X' P - Y' H ], curl(X,Y)^m_n = (1/a) sum_j [ i m Y' P + X' H ]
@@ -276,7 +274,7 @@ template <class T>
 __global__ void __launch_bounds__(32 * kAnalWarpsMax) k_anal_rhs(const C_t<T>* __restrict__ four_out,
                                                                  const T* __restrict__ P, const T* __restrict__ H,
                                                                  const Chunk* __restrict__ chunks, int R, int J2,
-                                                                 int nc, double ia, double a2, double2* __restrict__ FE,
+                                                                 int nc, double ia, double2* __restrict__ FE,
                                                                  const double2* __restrict__ state,
                                                                  double two_omega_lin, const double* __restrict__ cor,
                                                                  MemberStrides ms, FourStride fx, NodeFuse nf) {
@@ -360,12 +358,7 @@ __global__ void __launch_bounds__(32 * kAnalWarpsMax) k_anal_rhs(const C_t<T>* _
     double2 f0 = make_double2(-(double)divCD.x, -(double)divCD.y);
     double2 f1 = make_double2(-(double)divAB.x, -(double)divAB.y);
     double2 f2 = make_double2((double)(curlAB.x + lap * s[3].x), (double)(curlAB.y + lap * s[3].y));
-    if (two_omega_lin != 0.0) {
-        double2 dz, dd;
-        coriolis_linear(state, cor, nc, R, m, n, off, a2, two_omega_lin, two_omega_lin * ia * ia, dz, dd);
-        f1 = cadd(f1, dz);
-        f2 = cadd(f2, dd);
-    }
+    if (two_omega_lin != 0.0) coriolis_add(state, cor, nc, R, m, n, off, two_omega_lin, f1, f2);
     if (m == 0) f0.y = f1.y = f2.y = 0.0;
     FE[off + k] = f0;
     FE[nc + off + k] = f1;

@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(3 * kNodeCoefs) k_sweep_node(double2* Th, cons
                                                              const double2* __restrict__ FEo, double2* FIn,
                                                              double2* FEn, const double2* __restrict__ tau,
                                                              const int* __restrict__ ndeg,
-                                                             const double2* __restrict__ recips, int nc, double dt,
+                                                             const double2* __restrict__ recips, int nc,
                                                              NodeRow row, Phys ph, size_t ms) {
     __shared__ double2 sb[3][kNodeCoefs];
     pdl_wait();
@@ -92,19 +92,17 @@ __global__ void __launch_bounds__(3 * kNodeCoefs) k_sweep_node(double2* Th, cons
     const int c = blockIdx.x * kNodeCoefs + cl;
     const bool live = c < nc;
     const size_t o = (size_t)f * nc + c;
-    if (live) sb[f][cl] = node_rhs(Th, FIo, FEo, FIn, FEn, tau, node, o, dt, row);
+    if (live) sb[f][cl] = node_rhs(Th, FIo, FEo, FIn, FEn, tau, node, o, row);
     __syncthreads();
     if (!live) return;
     const int nd = ndeg[c];
     const double n = nd;
     const double L = -n * (n + 1.0) * ph.inv_a2;
-    double2 p, z, d;
-    implicit_solve_tab(L, dt * row.qimm, ph, recips[nd], sb[0][cl], sb[1][cl], sb[2][cl], p, z, d);
-    double2 fp, fz, fd;
-    implicit_rhs_coef(L, ph, p, z, d, fp, fz, fd);
+    double2 th, fi;  // each thread only its own field (warp-uniform f)
+    node_solve_field(f, L, row.qimm, ph, recips[nd], sb[0][cl], sb[1][cl], sb[2][cl], th, fi);
     const size_t om = (m + 1) * node + o;
-    Th[om] = f == 0 ? p : (f == 1 ? z : d);
-    FIn[om] = f == 0 ? fp : (f == 1 ? fz : fd);
+    Th[om] = th;
+    FIn[om] = fi;
     if (m == 0) {
         FIn[o] = FIo[o];
         FEn[o] = FEo[o];
@@ -127,36 +125,38 @@ __global__ void k_broadcast(const double2* __restrict__ src, double2* __restrict
 
 
 // Restriction (Eqs. two_step_restriction, time_restriction, space_restriction):
-// Theta_c[i] = D( sum_j Pi^c_f[i][j] Theta_f[j] ) for i in [i0, i1).
+// Theta_c[i] = D( sum_j Pi^c_f[i][j] Theta_f[j] ) for i in [i0, i1); one
+// thread per (coarse node, field, coarse coefficient).
 __global__ void k_restrict(const double2* __restrict__ Tf, double2* __restrict__ Tc, const int* __restrict__ c2f,
                            int ncf, int ncc, int nf_nodes, int i0, int i1, TransferMat Pcf, size_t msf, size_t msc) {
     pdl_wait();
     pdl_launch();
     Tf += blockIdx.y * msf;
     Tc += blockIdx.y * msc;
-    const int total = 3 * ncc;
+    const int nc3 = 3 * ncc;
+    const int total = (i1 - i0) * nc3;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
-        const int f = t / ncc, k = t - f * ncc;
+        const int i = i0 + t / nc3, r = t % nc3;
+        const int f = r / ncc, k = r - f * ncc;
         const size_t of = (size_t)f * ncf + c2f[k];
-        for (int i = i0; i < i1; ++i) {
-            double2 acc{0.0, 0.0};
-            for (int j = 0; j < nf_nodes; ++j) acc = cax(acc, Pcf.a[i * nf_nodes + j], Tf[(size_t)j * 3 * ncf + of]);
-            Tc[(size_t)i * 3 * ncc + t] = acc;
-        }
+        double2 acc{0.0, 0.0};
+        for (int j = 0; j < nf_nodes; ++j) acc = cax(acc, Pcf.a[i * nf_nodes + j], Tf[(size_t)j * 3 * ncf + of]);
+        Tc[(size_t)i * nc3 + r] = acc;
     }
 }
 
 
 // tau_c = A_c(R Theta_f) - R A_f(Theta_f), A(Theta) = Theta - dt (Q x I) F
-// (Eq. tau_term_level_l+1 with tau_f = 0; Eq. collocation_problem).  The
-// same pass saves the restricted coarse values Theta_c, F_I,c, F_E,c
-// (Algorithm 1 step B) into Ts, FIs, FEs for step D.
+// (Eq. tau_term_level_l+1 with tau_f = 0; Eq. collocation_problem), in the
+// folded form of FasFwd; one thread per (coarse node i, field, coarse
+// coefficient).  The same pass saves the restricted coarse values Theta_c,
+// F_I,c, F_E,c (Algorithm 1 step B) into Ts, FIs, FEs for step D.
 __global__ void k_fas_tau(const double2* __restrict__ Tf, const double2* __restrict__ FIf,
                           const double2* __restrict__ FEf, const double2* __restrict__ Tc,
                           const double2* __restrict__ FIc, const double2* __restrict__ FEc,
                           double2* __restrict__ tau, double2* __restrict__ Ts, double2* __restrict__ FIs,
                           double2* __restrict__ FEs, const int* __restrict__ c2f, int ncf, int ncc,
-                          double dt, FasArgs A, size_t msf, size_t msc) {
+                          FasFwd A, size_t msf, size_t msc) {
     pdl_wait();
     pdl_launch();
     const size_t of_m = blockIdx.y * msf, oc_m = blockIdx.y * msc;
@@ -170,41 +170,38 @@ __global__ void k_fas_tau(const double2* __restrict__ Tf, const double2* __restr
     Ts += oc_m;
     FIs += oc_m;
     FEs += oc_m;
-    const int total = 3 * ncc;
+    const int nc3 = 3 * ncc;
+    const size_t nf3 = (size_t)3 * ncf;
+    const int total = A.ncn * nc3;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
-        const int f = t / ncc, k = t - f * ncc;
+        const int i = t / nc3, r = t - i * nc3;
+        const int f = r / ncc, k = r - f * ncc;
         const size_t of = (size_t)f * ncf + c2f[k];
-        const size_t nf3 = (size_t)3 * ncf, nc3 = (size_t)3 * ncc;
-        double2 Af[kMaxNodes];
+        const size_t oc = (size_t)i * nc3 + r;
+        const double2 tc = Tc[oc];
+        Ts[oc] = tc;
+        FIs[oc] = FIc[oc];
+        FEs[oc] = FEc[oc];
+        double2 acc = tc;
         for (int j = 0; j < A.nfn; ++j) {
-            double2 acc = Tf[j * nf3 + of];
-            for (int l = 0; l < A.nfn; ++l) {
-                const double2 s = make_double2(FIf[l * nf3 + of].x + FEf[l * nf3 + of].x,
-                                               FIf[l * nf3 + of].y + FEf[l * nf3 + of].y);
-                acc = cax(acc, -dt * A.Qf[j * A.nfn + l], s);
-            }
-            Af[j] = acc;
+            const size_t oj = (size_t)j * nf3 + of;
+            const double2 sf = make_double2(FIf[oj].x + FEf[oj].x, FIf[oj].y + FEf[oj].y);
+            acc = cax(acc, -A.Pcf[i * A.nfn + j], Tf[oj]);
+            acc = cax(acc, A.dPQf[i * A.nfn + j], sf);
         }
-        for (int i = 0; i < A.ncn; ++i) {
-            Ts[i * nc3 + t] = Tc[i * nc3 + t];
-            FIs[i * nc3 + t] = FIc[i * nc3 + t];
-            FEs[i * nc3 + t] = FEc[i * nc3 + t];
+        for (int l = 0; l < A.ncn; ++l) {
+            const size_t ol = (size_t)l * nc3 + r;
+            const double2 sc = make_double2(FIc[ol].x + FEc[ol].x, FIc[ol].y + FEc[ol].y);
+            acc = cax(acc, -A.dQc[i * A.ncn + l], sc);
         }
-        for (int i = 0; i < A.ncn; ++i) {
-            double2 acc = Tc[i * nc3 + t];
-            for (int l = 0; l < A.ncn; ++l) {
-                const double2 s = make_double2(FIc[l * nc3 + t].x + FEc[l * nc3 + t].x,
-                                               FIc[l * nc3 + t].y + FEc[l * nc3 + t].y);
-                acc = cax(acc, -dt * A.Qc[i * A.ncn + l], s);
-            }
-            for (int j = 0; j < A.nfn; ++j) acc = cax(acc, -A.Pcf[i * A.nfn + j], Af[j]);
-            tau[i * nc3 + t] = acc;
-        }
+        tau[oc] = acc;
     }
 }
 
 // Step D: X_f[m] += P( sum_i Pi^f_c[m][i] (X_c[i] - X_s[i]) ), m = 1..M_f,
-// for X = Theta, F_I, F_E (zero-padding leaves the fine-only modes unchanged).
+// for X = Theta, F_I, F_E (zero-padding leaves the fine-only modes
+// unchanged); one thread per (fine node m, field, coarse coefficient), the
+// zero weights (fine nodes that are coarse nodes) skipped.
 __global__ void k_interp(double2* __restrict__ Tf, double2* __restrict__ FIf, double2* __restrict__ FEf,
                          const double2* __restrict__ Tc, const double2* __restrict__ FIc,
                          const double2* __restrict__ FEc, const double2* __restrict__ Ts,
@@ -223,31 +220,26 @@ __global__ void k_interp(double2* __restrict__ Tf, double2* __restrict__ FIf, do
     Ts += oc_m;
     FIs += oc_m;
     FEs += oc_m;
-    const int total = 3 * ncc;
-    const size_t nf3 = (size_t)3 * ncf, nc3 = (size_t)3 * ncc;
+    const int nc3 = 3 * ncc;
+    const size_t nf3 = (size_t)3 * ncf;
+    const int total = (nfn - 1) * nc3;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
-        const int f = t / ncc, k = t - f * ncc;
+        const int m = 1 + t / nc3, r = t % nc3;
+        const int f = r / ncc, k = r - f * ncc;
         const size_t of = (size_t)f * ncf + c2f[k];
-        double2 dT[kMaxNodes], dI[kMaxNodes], dE[kMaxNodes];
+        double2 aT{0, 0}, aI{0, 0}, aE{0, 0};
         for (int i = 0; i < ncn; ++i) {
-            const size_t oc = i * nc3 + t;
-            dT[i] = make_double2(Tc[oc].x - Ts[oc].x, Tc[oc].y - Ts[oc].y);
-            dI[i] = make_double2(FIc[oc].x - FIs[oc].x, FIc[oc].y - FIs[oc].y);
-            dE[i] = make_double2(FEc[oc].x - FEs[oc].x, FEc[oc].y - FEs[oc].y);
+            const double w = Pfc.a[m * ncn + i];
+            if (w == 0.0) continue;
+            const size_t oc = (size_t)i * nc3 + r;
+            aT = cax(aT, w, make_double2(Tc[oc].x - Ts[oc].x, Tc[oc].y - Ts[oc].y));
+            aI = cax(aI, w, make_double2(FIc[oc].x - FIs[oc].x, FIc[oc].y - FIs[oc].y));
+            aE = cax(aE, w, make_double2(FEc[oc].x - FEs[oc].x, FEc[oc].y - FEs[oc].y));
         }
-        for (int m = 1; m < nfn; ++m) {
-            double2 aT{0, 0}, aI{0, 0}, aE{0, 0};
-            for (int i = 0; i < ncn; ++i) {
-                const double w = Pfc.a[m * ncn + i];
-                aT = cax(aT, w, dT[i]);
-                aI = cax(aI, w, dI[i]);
-                aE = cax(aE, w, dE[i]);
-            }
-            const size_t o = m * nf3 + of;
-            Tf[o] = make_double2(Tf[o].x + aT.x, Tf[o].y + aT.y);
-            FIf[o] = make_double2(FIf[o].x + aI.x, FIf[o].y + aI.y);
-            FEf[o] = make_double2(FEf[o].x + aE.x, FEf[o].y + aE.y);
-        }
+        const size_t o = (size_t)m * nf3 + of;
+        Tf[o] = make_double2(Tf[o].x + aT.x, Tf[o].y + aT.y);
+        FIf[o] = make_double2(FIf[o].x + aI.x, FIf[o].y + aI.y);
+        FEf[o] = make_double2(FEf[o].x + aE.x, FEf[o].y + aE.y);
     }
 }
 
@@ -388,8 +380,8 @@ static mlsdc_status launch_node(sdc_level_t L, double dt, const NodeRow& row, do
     MLSDC_LAUNCH("k_sweep_node",
                  launch_k(k_sweep_node, dim3((nc + kNodeCoefs - 1) / kNodeCoefs, L->members), dim3(3 * kNodeCoefs),
                           0, st, Th, FIo, FEo, FIn, FEn, tau, (const int*)L->plan->d_ndeg,
-                          (const double2*)(L->d_recips + (size_t)row.m * (L->plan->R + 1)), nc, dt, row,
-                          phys_of(L->prm), L->ms()));
+                          (const double2*)(L->d_recips + (size_t)row.m * (L->plan->R + 1)), nc,
+                          dt_scaled(row, dt), phys_of(L->prm), L->ms()));
     L->launches++;
     return MLSDC_OK;
 }
@@ -796,7 +788,7 @@ mlsdc_status run_ops(mlsdc_t ml, const std::vector<Op>& ops, cudaStream_t st, in
     const int ncf = F->plan->nc, ncc = C->plan->nc;
     const int nfn = F->n, ncn = C->n;
     const size_t msf = F->ms(), msc = C->ms();
-    const dim3 gt(grid_for(3 * ncc), F->members);
+    auto gt = [&](int threads) { return dim3(grid_for(threads), F->members); };
     F->launches = C->launches = 0;
     int64_t own = 0;
     FasArgs fa;
@@ -839,8 +831,7 @@ mlsdc_status run_ops(mlsdc_t ml, const std::vector<Op>& ops, cudaStream_t st, in
                     nf.tau = n.p[5];
                     nf.ndeg = n.L->plan->d_ndeg;
                     nf.recips = n.L->d_recips + (size_t)n.row.m * (n.L->plan->R + 1);
-                    nf.dt = n.dt;
-                    nf.row = n.row;
+                    nf.row = dt_scaled(n.row, n.dt);
                     nf.ph = phys_of(n.L->prm);
                     nf.ms = n.L->ms();
                     nf.on = 1;
@@ -854,24 +845,39 @@ mlsdc_status run_ops(mlsdc_t ml, const std::vector<Op>& ops, cudaStream_t st, in
                 s = launch_node(o.L, o.dt, o.row, o.p[0], o.p[1], o.p[2], o.p[3], o.p[4], o.p[5], st);
                 break;
             case OpK::Restrict:
-                MLSDC_LAUNCH("k_restrict", launch_k(k_restrict, gt, dim3(256), 0, st, o.p[0], o.p[1],
-                                                    (const int*)ml->d_c2f, ncf, ncc, nfn, o.i0, o.i1, ml->Pcf, msf,
-                                                    msc));
+                MLSDC_LAUNCH("k_restrict",
+                             launch_k(k_restrict, gt((o.i1 - o.i0) * 3 * ncc), dim3(256), 0, st, o.p[0], o.p[1],
+                                      (const int*)ml->d_c2f, ncf, ncc, nfn, o.i0, o.i1, ml->Pcf, msf, msc));
                 own++;
                 break;
             case OpK::Copy:
                 MLSDC_CUDA(cudaMemcpyAsync(o.p[1], o.p[0], o.bytes, cudaMemcpyDeviceToDevice, st));
                 break;
-            case OpK::Fas:
-                MLSDC_LAUNCH("k_fas_tau", launch_k(k_fas_tau, gt, dim3(256), 0, st, o.p[0], o.p[1], o.p[2], o.p[3],
-                                                   o.p[4], o.p[5], o.p[6], o.p[7], o.p[8], o.p[9],
-                                                   (const int*)ml->d_c2f, ncf, ncc, o.dt, fa, msf, msc));
+            case OpK::Fas: {
+                FasFwd fw;
+                std::memset(&fw, 0, sizeof(fw));
+                fw.nfn = nfn;
+                fw.ncn = ncn;
+                for (int i = 0; i < ncn; ++i) {
+                    for (int j = 0; j < nfn; ++j) {
+                        double pq = 0.0;
+                        for (int l = 0; l < nfn; ++l) pq += fa.Pcf[i * nfn + l] * fa.Qf[l * nfn + j];
+                        fw.Pcf[i * nfn + j] = fa.Pcf[i * nfn + j];
+                        fw.dPQf[i * nfn + j] = o.dt * pq;
+                    }
+                    for (int l = 0; l < ncn; ++l) fw.dQc[i * ncn + l] = o.dt * fa.Qc[i * ncn + l];
+                }
+                MLSDC_LAUNCH("k_fas_tau", launch_k(k_fas_tau, gt(ncn * 3 * ncc), dim3(256), 0, st, o.p[0], o.p[1],
+                                                   o.p[2], o.p[3], o.p[4], o.p[5], o.p[6], o.p[7], o.p[8], o.p[9],
+                                                   (const int*)ml->d_c2f, ncf, ncc, fw, msf, msc));
                 own++;
                 break;
+            }
             case OpK::Interp:
-                MLSDC_LAUNCH("k_interp", launch_k(k_interp, gt, dim3(256), 0, st, o.p[0], o.p[1], o.p[2], o.p[3],
-                                                  o.p[4], o.p[5], o.p[6], o.p[7], o.p[8], (const int*)ml->d_c2f, ncf,
-                                                  ncc, nfn, ncn, ml->Pfc, msf, msc));
+                MLSDC_LAUNCH("k_interp",
+                             launch_k(k_interp, gt((nfn - 1) * 3 * ncc), dim3(256), 0, st, o.p[0], o.p[1], o.p[2],
+                                      o.p[3], o.p[4], o.p[5], o.p[6], o.p[7], o.p[8], (const int*)ml->d_c2f, ncf, ncc,
+                                      nfn, ncn, ml->Pfc, msf, msc));
                 own++;
                 break;
             case OpK::SolveCoefs:

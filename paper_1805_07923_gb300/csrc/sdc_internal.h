@@ -28,6 +28,18 @@ struct FasArgs {
     int nfn, ncn;
 };
 
+// The forward FAS pass's matrices for one step size dt, formed on the host:
+// Pcf, dt Q_c and dt Pcf Q_f, so that
+//   tau_i = Theta_c,i - sum_j Pcf_ij Theta_f,j - sum_l (dt Q_c)_il F_c,l + sum_j (dt Pcf Q_f)_ij F_f,j
+// (F = F_I + F_E; the same value as A_c(R Theta_f) - R A_f(Theta_f) with the
+// fine sums folded through Pcf).
+struct FasFwd {
+    double Pcf[kMaxNodes * kMaxNodes];   // [ncn][nfn]
+    double dQc[kMaxNodes * kMaxNodes];   // [ncn][ncn]
+    double dPQf[kMaxNodes * kMaxNodes];  // [ncn][nfn]
+    int nfn, ncn;
+};
+
 // One operation of an MLSDC step.  A step is a fixed, straight-line list of
 // these (built on the host from the schedule of Algorithm 1), run in order
 // by the forward step and walked backwards by the adjoint.  Every operation

@@ -145,7 +145,7 @@ mlsdc_status rhs_explicit_f64(sh_plan_t p, const swe_params* prm, const double* 
         MLSDC_LAUNCH("k_anal_rhs<double>",
                      launch_k(k_anal_rhs<double>, dim3(p->n_anal, b.members), dim3(32 * anal_warps(p->J2)), 0, st,
                               (const double2*)p->d_four_out, (const double*)p->d_P, (const double*)p->d_H,
-                              (const Chunk*)p->d_anal, R, p->J2, p->nc, 1.0 / prm->a, prm->a * prm->a, (double2*)FE,
+                              (const Chunk*)p->d_anal, R, p->J2, p->nc, 1.0 / prm->a, (double2*)FE,
                               (const double2*)state, 0.0, (const double*)p->d_cor, ms, fo, fuse));
     }
     if (launches) *launches += stage < 0 ? 3 : 1;

@@ -137,7 +137,7 @@ mlsdc_status rhs_explicit_mp(sh_plan_t p, const swe_params* prm, const double* s
             MLSDC_LAUNCH("k_anal_rhs<float>",
                          launch_k(k_anal_rhs<float>, dim3(p->n_anal, b.members), dim3(32 * anal_warps(p->J2)), 0, st,
                                   (const float2*)t.four_out, (const float*)t.P32, (const float*)t.H32,
-                                  (const Chunk*)p->d_anal, R, p->J2, p->nc, 1.0 / prm->a, prm->a * prm->a,
+                                  (const Chunk*)p->d_anal, R, p->J2, p->nc, 1.0 / prm->a,
                                   (double2*)FE, (const double2*)state, 2.0 * prm->omega, (const double*)p->d_cor, ms,
                                   fo, fuse));
         }
