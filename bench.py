@@ -53,6 +53,62 @@ def grid_stage_flops(R, I, J):
     return 9 * J * 2.5 * I * math.log2(I)
 
 
+def stage_bytes(R, I, J, stage, prec, members=1):
+    """Algorithmic bytes of one launch of an F_E stage kernel (0 synthesis,
+    1 FFT/products, 2 analysis) for `members` members: each table read once
+    per launch, each member's operands read once and results written once.
+    Tables in the form the kernel reads them: 8 bytes per value (float64), 4
+    (float32, tf32, bf16 hi + lo); Fourier arrays complex float64 or float32;
+    state and F_E complex float64.  The mixed paths' analysis also reads
+    zeta, delta and the per-coefficient factors of the float64 Coriolis term."""
+    nc = (R + 1) * (R + 2) // 2
+    four = J * (R + 1)
+    cb = 16 if prec == "fp64" else 8
+    if stage == 1:
+        return members * 9 * four * cb
+    tab = 2 * nc * (J // 2) * (8 if prec == "fp64" else 4)
+    if stage == 0:
+        return tab + members * (3 * nc * 16 + 4 * four * cb)
+    cor = 0 if prec == "fp64" else nc * 32
+    per = 5 * four * cb + 3 * nc * 16 + (0 if prec == "fp64" else 2 * nc * 16)
+    return tab + cor + members * per
+
+
+def stage_roofline(prec, flops, nbytes, ms, on_tc, peaks, fp64_peak):
+    """Roofline of one stage kernel: the bound is whichever of memory (the
+    algorithmic bytes at the measured HBM copy rate) and compute (the
+    algorithmic flops at the kernel's arithmetic peak) takes longer;
+    achieved = that quantity / the measured launch time."""
+    t = ms * 1e-3
+    hbm = peaks.get("hbm_gbs")
+    hbm_src = "measured HBM copy (MEASURED_PEAKS.json)" if hbm else "fallback 6800 GB/s"
+    hbm = hbm or 6800.0
+    if on_tc:
+        bf16 = peaks.get("bf16_tflops", 1900.0)
+        cpeak = bf16 if prec == "bf16x3" else bf16 * 1.1 / 2.25
+        csrc = "measured bf16 burst peak" + (" x 1.1/2.25 (tf32)" if prec == "tf32" else
+                                             "; bf16 hi/lo operands, 3 tensor products per algorithmic one")
+        cflops = flops * (3 if prec == "bf16x3" else 1)
+        cbound = "tensor"
+    elif prec == "fp64":
+        cpeak, csrc, cflops, cbound = fp64_peak(), "measured cuBLAS DGEMM (float64 pipe)", flops, "alu"
+    else:
+        cpeak = 152 * 128 * 2 * (peaks.get("sm_max_mhz") or 2070.0) * 1e6 / 1e12
+        csrc, cflops, cbound = "float32 CUDA-core FMA: 152 SMs x 128 lanes x 2 x max SM clock", flops, "alu"
+    t_mem, t_comp = nbytes / (hbm * 1e9), cflops / (cpeak * 1e12)
+    if t_mem >= t_comp:
+        roof = {"bound": "hbm", "achieved": nbytes / t / 1e9, "peak": hbm, "unit": "GB/s", "peak_source": hbm_src}
+    else:
+        roof = {"bound": cbound, "achieved": cflops / t / 1e12, "peak": cpeak, "unit": "TFLOP/s",
+                "peak_source": csrc}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["algorithmic_bytes"] = nbytes
+    roof["algorithmic_flops"] = flops
+    roof["memory_time_floor_ms"] = t_mem * 1e3
+    roof["compute_time_floor_ms"] = t_comp * 1e3
+    return roof
+
+
 def evals_per_step(w):
     f = 1 + w["n_iter"] * (w["nf"] - 1)
     c = 1 + w["n_iter"] * ((w["nc"] - 1) + w["n_coarse"] * (w["nc"] - 1))
@@ -307,23 +363,15 @@ def run_ensemble(args):
             for s in range(3):
                 fl = (legendre_stage_flops(R, J, s) if s != 1 else grid_stage_flops(R, I, J)) * B
                 on_tc = (s == 0 and tcs[0]) or (s == 2 and tcs[1])
-                shares.append((ms[s] * cnt, f"{lvl}x{B}", names[s], ms[s], fl, on_tc))
+                shares.append((ms[s] * cnt, f"{lvl}x{B}", names[s], ms[s], fl, on_tc,
+                               stage_bytes(R, I, J, s, prec, B)))
     shares.sort(reverse=True)
     top = shares[0]
-    peaks = load_peaks()
-    bf16 = peaks.get("bf16_tflops", 1900.0)
-    achieved = top[4] / (top[3] * 1e-3) / 1e12
-    roof = {"bound": "tensor" if top[5] else "alu",
-            "achieved": achieved, "unit": "TFLOP/s", "kernel": f"{top[2]} at {top[1]}", "kernel_ms": top[3]}
-    if roof["bound"] == "tensor":
-        roof["peak"] = bf16 if prec == "bf16x3" else bf16 * 1.1 / 2.25
-        roof["peak_source"] = "measured bf16 burst peak" + (" x 1.1/2.25 (tf32)" if prec == "tf32" else "")
-        if prec == "bf16x3":
-            roof["tensor_products_per_flop"] = 3
-    else:
-        roof["peak"] = measured_fp64_tflops(torch, dev) if prec == "fp64" else 152 * 128 * 2 * 2.07e9 / 1e12
-        roof["peak_source"] = "measured DGEMM" if prec == "fp64" else "float32 CUDA-core FMA rate"
-    roof["frac"] = roof["achieved"] / roof["peak"]
+    fp64_cache = []
+    fp64_peak = lambda: fp64_cache[0] if fp64_cache else fp64_cache.append(measured_fp64_tflops(torch, dev)) or fp64_cache[0]
+    roof = stage_roofline(prec, top[4], top[6], top[3], top[5], load_peaks(), fp64_peak)
+    roof["kernel"] = f"{top[2]} at {top[1]}"
+    roof["kernel_ms"] = top[3]
     roof["traffic"] = None
     line = {"metric": "ensemble member-steps/s (MLSDC-SH); SH TFLOP/s", "value": value, "unit": "member-steps/s",
             "n_gpus": 1, "steps": K, "warmup": 3, "ms_per_step": total_ms / K, "higher_is_better": True,
@@ -692,23 +740,11 @@ def main():
             kern_names["legendre_synthesis"] = f"k_tc_synth<{prec}>"
         if atc:
             kern_names["legendre_analysis"] = f"k_tc_anal<{prec}>"
-    achieved = top[4] / (top[3] * 1e-3) / 1e12
-    sm_max = (clk.get("sm_max_mhz") or 2070.0) * 1e6
-    if not kern_names[top[2]].startswith("k_tc"):
-        if prec == "fp64":
-            peak, src = measured_fp64_tflops(torch, dev), "measured cuBLAS DGEMM on this GPU (float64 pipe)"
-        else:
-            peak = 152 * 128 * 2 * sm_max / 1e12
-            src = "float32 CUDA-core FMA: 152 SMs x 128 lanes x 2 flops x max SM clock"
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "peak_source": src}
-    else:
-        bf16 = peaks.get("bf16_tflops", 1900.0)
-        if prec == "tf32":
-            peak, src = bf16 * 1.1 / 2.25, "measured bf16 burst peak x nominal tf32/bf16 ratio (1.1/2.25)"
-        else:
-            peak, src = bf16, "measured bf16 burst peak (bf16 hi/lo operands; 3 tensor products per algorithmic one)"
-        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "peak_source": src}
-    roof["frac"] = roof["achieved"] / roof["peak"]
+    lvl_dims = {"T170": (w["Rf"], w["If"], w["Jf"]), "T85": (w["Rc"], w["Ic"], w["Jc"])}
+    R_, I_, J_ = lvl_dims[top[1]]
+    on_tc = kern_names[top[2]].startswith("k_tc")
+    roof = stage_roofline(prec, top[4], stage_bytes(R_, I_, J_, names.index(top[2]), prec), top[3], on_tc, peaks,
+                          lambda: measured_fp64_tflops(torch, dev))
     roof["traffic"] = traffic_for(f"{top[1]}:{kern_names[top[2]]}")
     roof["kernel"] = f"{top[2]} ({kern_names[top[2]]}) at {top[1]}"
     roof["kernel_ms"] = top[3]
