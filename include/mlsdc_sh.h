@@ -124,8 +124,13 @@ mlsdc_status sh_plan_set_stage_kernels(sh_plan_t plan, int synth_mode, int anal_
  * timing each feasible choice on a full batch of the plan's max_members:
  * members per CTA (1, 2, 4, 8 or 16; the members form the MMA's N dimension,
  * 16 columns each) and the depth of the shared-memory pipeline over K (1 or
- * 2 stages).  0, 0 for MLSDC_FP64 / MLSDC_FP32 plans.  Pointers may be NULL. */
+ * 2 stages).  sh_plan_tc_config reports it (0, 0 for MLSDC_FP64 / MLSDC_FP32
+ * plans; pointers may be NULL); sh_plan_set_tc_config replaces it (results
+ * are the same to rounding; MLSDC_ERR_INVALID for other precisions, a member
+ * count that is not a power of two up to min(16, max_members), a depth other
+ * than 1 or 2, or a choice whose shared memory does not fit a CTA). */
 mlsdc_status sh_plan_tc_config(sh_plan_t plan, int* members_per_cta, int* stages);
+mlsdc_status sh_plan_set_tc_config(sh_plan_t plan, int members_per_cta, int stages);
 
 /* sh_inverse: spectral -> grid for nf independent scalar fields,
  * Eq. spectral_to_physical_space (Legendre sum per m, then the inverse

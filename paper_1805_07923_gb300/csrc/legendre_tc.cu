@@ -979,6 +979,19 @@ mlsdc_status tc_config(sh_plan_t p, int* chunk, int* stages) {
     return MLSDC_OK;
 }
 
+mlsdc_status tc_set_config(sh_plan_t p, int chunk, int stages) {
+    TcState* s = st_of(p);
+    if (!s) return MLSDC_ERR_INVALID;
+    const bool pow2 = chunk >= 1 && chunk <= 16 && (chunk & (chunk - 1)) == 0;
+    if (!pow2 || chunk > p->max_members || stages < 1 || stages > kMaxStages ||
+        cta_smem_bytes(s->mode, chunk, stages) > kSmemBudget)
+        return MLSDC_ERR_INVALID;
+    s->chunk = chunk;
+    s->stages = stages;
+    p->tc_chunk = chunk;
+    return MLSDC_OK;
+}
+
 mlsdc_status tc_error(sh_plan_t p, int* code) {
     TcState* s = st_of(p);
     *code = 0;

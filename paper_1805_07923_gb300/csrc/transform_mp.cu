@@ -27,6 +27,7 @@ __global__ void k_round_c32(const double2* __restrict__ x, float2* __restrict__ 
 
 mlsdc_status tc_init(sh_plan_t p);   // legendre_tc.cu
 mlsdc_status tc_config(sh_plan_t p, int* chunk, int* stages);
+mlsdc_status tc_set_config(sh_plan_t p, int chunk, int stages);
 void tc_free(sh_plan_t p);
 mlsdc_status tc_synth(sh_plan_t p, const double* state, double a, RhsBatch b, cudaStream_t st);
 mlsdc_status tc_anal(sh_plan_t p, double a, double* FE, const double* state, double two_omega, RhsBatch b,
@@ -159,6 +160,11 @@ extern "C" mlsdc_status sh_plan_stage_kernels(sh_plan_t p, int members, int* syn
 extern "C" mlsdc_status sh_plan_tc_config(sh_plan_t p, int* members_per_cta, int* stages) {
     if (!p) return MLSDC_ERR_INVALID;
     return mlsdc::tc_config(p, members_per_cta, stages);
+}
+
+extern "C" mlsdc_status sh_plan_set_tc_config(sh_plan_t p, int members_per_cta, int stages) {
+    if (!p || !(p->precision == MLSDC_TF32 || p->precision == MLSDC_BF16X3)) return MLSDC_ERR_INVALID;
+    return mlsdc::tc_set_config(p, members_per_cta, stages);
 }
 
 extern "C" mlsdc_status sh_plan_set_stage_kernels(sh_plan_t p, int synth_mode, int anal_mode) {

@@ -69,6 +69,7 @@ _SIGS = {
     "sh_plan_stage_kernels": ([_VP, _I, ctypes.POINTER(_I), ctypes.POINTER(_I)], _I),
     "sh_plan_set_stage_kernels": ([_VP, _I, _I], _I),
     "sh_plan_tc_config": ([_VP, ctypes.POINTER(_I), ctypes.POINTER(_I)], _I),
+    "sh_plan_set_tc_config": ([_VP, _I, _I], _I),
     "swe_explicit_rhs_adjoint": ([_VP, ctypes.POINTER(SweParams), _DP, _DP, _DP, _VP], _I),
     "mlsdc_phi_misfit": ([_VP, _DP, _DP, _DP, _DP, _VP], _I),
     "mlsdc_adjoint_create": ([_VP, _I, _I, _D, _I, _I, ctypes.POINTER(_VP)], _I),
@@ -197,10 +198,14 @@ class Plan:
         return bool(a.value), bool(b.value)
 
     def tc_config(self) -> tuple[int, int]:
-        """(members per CTA, K-pipeline stages) the tensor-core autotuner chose; (0, 0) otherwise."""
+        """(members per CTA, K-pipeline stages) of the tensor-core kernels; (0, 0) otherwise."""
         a, b = ctypes.c_int(), ctypes.c_int()
         _check(lib().sh_plan_tc_config(self.h, ctypes.byref(a), ctypes.byref(b)), "sh_plan_tc_config")
         return a.value, b.value
+
+    def set_tc_config(self, members_per_cta: int, stages: int):
+        """Replace the autotuned tensor-core configuration (tensor-core plans only)."""
+        _check(lib().sh_plan_set_tc_config(self.h, int(members_per_cta), int(stages)), "sh_plan_set_tc_config")
 
     def set_stage_kernels(self, synth: str = "auto", anal: str = "auto"):
         """Per-stage kernel mode of a tensor-core plan: "auto" (the size rule), "tc" or "simt"."""

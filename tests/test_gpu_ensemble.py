@@ -127,3 +127,40 @@ def test_uneven_ensemble_in_one_graph_equals_members_alone(prec):
                 assert rel(got[b], ref) <= 1e-12, (Rf, b, rel(got[b], ref))
         for p in k1[:2]:
             assert p.device_error() == 0
+
+
+@pytest.mark.parametrize("prec", ["tf32", "bf16x3"])
+def test_tensor_core_configs_agree(prec):
+    """Every feasible tensor-core launch configuration (members per CTA, K
+    stages) reproduces the single-member results to 1e-12.  T85 on 256 x 160
+    has two (bf16) or four (tf32) K blocks of latitudes per tile, so one-stage
+    configurations refill their stage within a tile; 17 members leave a ragged
+    last member chunk for every chunk size."""
+    R, I, J, B = 85, 256, 160, 17
+    x = members_state(R, B)
+    prm = M.swe_params()
+    xs = torch.from_numpy(x).cuda()
+    p1 = M.Plan(R, I, J, prec)
+    p1.set_stage_kernels("tc", "tc")
+    refs = []
+    for b in range(B):
+        FE1 = torch.empty_like(xs[b])
+        M.swe_explicit_rhs(p1, prm, xs[b].contiguous(), FE1)
+        refs.append(FE1.cpu().numpy())
+    pb = M.Plan(R, I, J, prec, max_members=B)
+    pb.set_stage_kernels("tc", "tc")
+    tried = 0
+    for cfg in [(1, 1), (1, 2), (2, 1), (2, 2), (4, 1), (4, 2), (8, 1), (16, 1)]:
+        try:
+            pb.set_tc_config(*cfg)
+        except RuntimeError:
+            continue  # shared memory of this choice does not fit a CTA
+        assert pb.tc_config() == cfg
+        FEb = torch.full_like(xs, float("nan"))
+        M.swe_explicit_rhs_batched(pb, prm, xs, FEb, B)
+        got = FEb.cpu().numpy()
+        assert pb.device_error() == 0, cfg
+        for b in range(B):
+            assert rel(got[b], refs[b]) <= 1e-12, (prec, cfg, b, rel(got[b], refs[b]))
+        tried += 1
+    assert tried >= 5
