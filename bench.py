@@ -578,6 +578,10 @@ def run_reference(args):
     ws, rank, local = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0
     if rank != 0:
         return
+    if args.workload != "headline":
+        print(json.dumps({"impl": "reference", "unavailable": "the oracle arm times the headline workload; the "
+                          "ensemble and adjoint lines carry their own cpu_baseline from the oracle"}), flush=True)
+        return
     from oracle import sdc as osdc
     from oracle.swe import SWE, Params
     from paper_1805_07923_gb300 import inputs
@@ -586,10 +590,13 @@ def run_reference(args):
     coarse = osdc.Level(SWE(w["Rc"], w["Ic"], w["Jc"], Params()), w["nc"])
     u = inputs.initial_state(w["Rf"])
     # bounded sample: each timed "step" is one full oracle MLSDC step; the
-    # number of steps is capped so the run ends within a few minutes
+    # warm-up steps are the requested ones and the timed steps are capped so
+    # the run ends within a few minutes
+    nw = max(1, args.warmup)
     t = time.perf_counter()
-    u = osdc.mlsdc_step(fine, coarse, u, w["dt"], w["n_iter"], w["n_coarse"])
-    first = time.perf_counter() - t
+    for _ in range(nw):
+        u = osdc.mlsdc_step(fine, coarse, u, w["dt"], w["n_iter"], w["n_coarse"])
+    first = (time.perf_counter() - t) / nw
     k = max(1, min(args.steps, int(90.0 / max(first, 1e-3))))
     t = time.perf_counter()
     for _ in range(k):
@@ -597,11 +604,11 @@ def run_reference(args):
     el = time.perf_counter() - t
     v = k / el
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "steps/s", "n_gpus": args.gpus,
-            "steps": k, "warmup": 1, "ms_per_step": 1e3 * el / k, "higher_is_better": True,
+            "steps": k, "warmup": nw, "ms_per_step": 1e3 * el / k, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD_NAME, "sample": f"{k} of {args.steps} requested steps"},
             "cpu_baseline": {"value": v, "unit": "steps/s", "cores": os.cpu_count(), "kind": "oracle",
-                             "sample": f"{k} oracle MLSDC steps after 1 warm-up step"},
+                             "sample": f"{k} oracle MLSDC steps after {nw} warm-up steps"},
             "e2e": {"value": v, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
