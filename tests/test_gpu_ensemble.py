@@ -5,8 +5,9 @@ Float64 and float32 batched kernels do each member's arithmetic in the same
 order, so the results are bitwise equal; the tensor-core results are compared
 within 1e-12 relative (the MMA columns are independent).  A launch with
 several members also stores the analysis input latitude-contiguous (one
-member: m-contiguous); T45 on 70 latitudes (35 per hemisphere, not a multiple
-of the tensor-core kernels' latitude groups) covers the ragged tail."""
+member: m-contiguous); T45 on 70 latitudes and T13 on 22 (35 and 11 per
+hemisphere, not multiples of the tensor-core kernels' latitude groups) cover
+the ragged tail, R = 1 on 16 x 4 the smallest legal plan."""
 import numpy as np
 import pytest
 import torch
@@ -27,7 +28,8 @@ def rel(a, b):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32", "bf16x3"])
-@pytest.mark.parametrize("R,I,J,B", [(21, 64, 32, 5), (45, 256, 70, 3), (85, 256, 128, 17)])
+@pytest.mark.parametrize("R,I,J,B", [(1, 16, 4, 3), (13, 64, 22, 4), (21, 64, 32, 5), (45, 256, 70, 3),
+                                     (85, 256, 128, 17)])
 def test_batched_rhs_equals_single(prec, R, I, J, B):
     x = members_state(R, B)
     pb = M.Plan(R, I, J, prec, max_members=B)

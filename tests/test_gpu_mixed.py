@@ -45,7 +45,8 @@ def total_phi_rel(R, got, ref, phibar=9.80616e4):
 
 
 @pytest.mark.parametrize("prec", MP)
-@pytest.mark.parametrize("R,I,J", [(21, 64, 32), (45, 256, 70), (85, 256, 128), (170, 512, 256)])
+@pytest.mark.parametrize("R,I,J", [(1, 16, 4), (13, 64, 22), (21, 64, 32), (45, 256, 70), (85, 256, 128),
+                                   (170, 512, 256)])
 def test_mixed_explicit_rhs_vs_oracle(prec, R, I, J):
     o = oracle(R, I, J)
     x = inputs.initial_state(R)

@@ -36,7 +36,8 @@ def rel_l2(R, got, ref):
 
 @pytest.mark.parametrize("kernels", ["tc", "auto"])
 @pytest.mark.parametrize("prec", TC)
-@pytest.mark.parametrize("R,I,J", [(21, 64, 32), (45, 256, 70), (85, 256, 128), (170, 512, 256)])
+@pytest.mark.parametrize("R,I,J", [(1, 16, 4), (13, 64, 22), (21, 64, 32), (45, 256, 70), (85, 256, 128),
+                                   (170, 512, 256)])
 def test_tensorcore_rhs_vs_oracle(prec, R, I, J, kernels):
     """kernels="tc": both Legendre stages on tcgen05; "auto": the plan's size
     rule (CUDA-core float32 kernels where they are faster)."""
