@@ -102,10 +102,18 @@ mlsdc_status sh_plan_grid(sh_plan_t plan, double* mu_host, double* w_host);
 mlsdc_status sh_plan_device_bytes(sh_plan_t plan, int64_t* bytes);
 /* Device-side error code recorded by the plan's tensor-core kernels (0 = none;
  * 1 = a TMA wait gave up, 2 = an MMA completion wait gave up).  Every such
- * wait is bounded: on timeout the kernel records the code, releases its
- * tensor memory and returns without writing results.  Synchronises the
- * device.  Always 0 for MLSDC_FP64 / MLSDC_FP32 plans. */
+ * wait is bounded (2 s of the global timer): on timeout the kernel records
+ * the code, releases its tensor memory and returns without writing results.
+ * Synchronises the device.  Always 0 for MLSDC_FP64 / MLSDC_FP32 plans. */
 mlsdc_status sh_plan_device_error(sh_plan_t plan, int* code);
+/* Check of the bounded device-side wait used by the tensor-core kernels:
+ * one CTA waits on an mbarrier that nothing completes, with the same wait
+ * loop (polls bounded by the global timer) and a limit of timeout_ms
+ * (1..2000); the wait must give up and the kernel records 2 (the code of a
+ * gave-up MMA wait) and returns, leaving the context usable.  *code is the
+ * recorded value (0 would mean the barrier completed).  Synchronises the
+ * device.  MLSDC_ERR_INVALID for a null pointer or a limit out of range. */
+mlsdc_status mlsdc_selftest_wait_timeout(int timeout_ms, int* code);
 /* Which kernel each Legendre stage of a tensor-core plan (MLSDC_TF32 /
  * MLSDC_BF16X3) runs: the tcgen05 kernel or the float32 CUDA-core kernel of
  * MLSDC_FP32.  By default the choice follows a fixed rule per launch (measured

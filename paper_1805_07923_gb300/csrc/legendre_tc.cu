@@ -44,7 +44,11 @@ constexpr int kTcThreads = 128;
 constexpr int kTileRows = 128;   // MMA M
 constexpr int kMaxKS = 192;      // synthesis K limit (R + 1 <= 192)
 constexpr int kTileBytes = 16384;  // 128 rows x 128 B
-constexpr uint32_t kSpinLimit = 1u << 24;
+// Every mbarrier wait is bounded in time (the waits of these kernels complete
+// in microseconds): after kWaitNs of the global timer the wait gives up, with
+// an iteration cap as a second bound.
+constexpr uint64_t kWaitNs = 2000000000ull;
+constexpr uint32_t kSpinLimit = 1u << 30;
 constexpr int kErrTmaTimeout = 1, kErrMmaTimeout = 2;
 
 enum { MODE_TF32 = 0, MODE_BF16X3 = 1 };
@@ -87,9 +91,18 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-    for (uint32_t i = 0; i < kSpinLimit; ++i)
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint64_t limit_ns = kWaitNs) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (uint32_t i = 1; i < kSpinLimit; ++i) {
         if (mbar_try_wait(bar, parity)) return true;
+        if ((i & 255) == 0 && global_ns() - t0 > limit_ns) return false;
+    }
     return false;
 }
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
@@ -989,6 +1002,36 @@ mlsdc_status tc_set_config(sh_plan_t p, int chunk, int stages) {
     s->chunk = chunk;
     s->stages = stages;
     p->tc_chunk = chunk;
+    return MLSDC_OK;
+}
+
+// One CTA waits on an mbarrier that nothing completes, with the kernels'
+// bounded wait and a limit of limit_ns: the wait must give up and the kernel
+// record kErrMmaTimeout and return (the check behind mlsdc_selftest_wait_timeout).
+__global__ void k_wait_selftest(uint64_t limit_ns, int* code) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(sa(&bar), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *code = mbar_wait(sa(&bar), 0, limit_ns) ? 0 : kErrMmaTimeout;
+}
+
+mlsdc_status wait_selftest(int timeout_ms, int* code) {
+    int* d = nullptr;
+    MLSDC_CUDA(cudaMalloc((void**)&d, sizeof(int)));
+    cudaError_t e = cudaMemset(d, 0xff, sizeof(int));
+    if (e == cudaSuccess) {
+        k_wait_selftest<<<1, 32>>>((uint64_t)timeout_ms * 1000000ull, d);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(code, d, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) {
+        set_error("k_wait_selftest", e);
+        return MLSDC_ERR_CUDA;
+    }
     return MLSDC_OK;
 }
 

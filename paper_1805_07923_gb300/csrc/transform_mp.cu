@@ -28,6 +28,7 @@ __global__ void k_round_c32(const double2* __restrict__ x, float2* __restrict__ 
 mlsdc_status tc_init(sh_plan_t p);   // legendre_tc.cu
 mlsdc_status tc_config(sh_plan_t p, int* chunk, int* stages);
 mlsdc_status tc_set_config(sh_plan_t p, int chunk, int stages);
+mlsdc_status wait_selftest(int timeout_ms, int* code);
 void tc_free(sh_plan_t p);
 mlsdc_status tc_synth(sh_plan_t p, const double* state, double a, RhsBatch b, cudaStream_t st);
 mlsdc_status tc_anal(sh_plan_t p, double a, double* FE, const double* state, double two_omega, RhsBatch b,
@@ -160,6 +161,11 @@ extern "C" mlsdc_status sh_plan_stage_kernels(sh_plan_t p, int members, int* syn
 extern "C" mlsdc_status sh_plan_tc_config(sh_plan_t p, int* members_per_cta, int* stages) {
     if (!p) return MLSDC_ERR_INVALID;
     return mlsdc::tc_config(p, members_per_cta, stages);
+}
+
+extern "C" mlsdc_status mlsdc_selftest_wait_timeout(int timeout_ms, int* code) {
+    if (!code || timeout_ms < 1 || timeout_ms > 2000) return MLSDC_ERR_INVALID;
+    return mlsdc::wait_selftest(timeout_ms, code);
 }
 
 extern "C" mlsdc_status sh_plan_set_tc_config(sh_plan_t p, int members_per_cta, int stages) {

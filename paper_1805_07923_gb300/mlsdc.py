@@ -70,6 +70,7 @@ _SIGS = {
     "sh_plan_set_stage_kernels": ([_VP, _I, _I], _I),
     "sh_plan_tc_config": ([_VP, ctypes.POINTER(_I), ctypes.POINTER(_I)], _I),
     "sh_plan_set_tc_config": ([_VP, _I, _I], _I),
+    "mlsdc_selftest_wait_timeout": ([_I, ctypes.POINTER(_I)], _I),
     "swe_explicit_rhs_adjoint": ([_VP, ctypes.POINTER(SweParams), _DP, _DP, _DP, _VP], _I),
     "mlsdc_phi_misfit": ([_VP, _DP, _DP, _DP, _DP, _VP], _I),
     "mlsdc_adjoint_create": ([_VP, _I, _I, _D, _I, _I, ctypes.POINTER(_VP)], _I),
@@ -211,6 +212,14 @@ class Plan:
         """Per-stage kernel mode of a tensor-core plan: "auto" (the size rule), "tc" or "simt"."""
         _check(lib().sh_plan_set_stage_kernels(self.h, self.STAGE_MODES[synth], self.STAGE_MODES[anal]),
                "sh_plan_set_stage_kernels")
+
+
+def selftest_wait_timeout(timeout_ms: int = 20) -> int:
+    """Run the bounded-wait check (one CTA waiting on an mbarrier nothing completes);
+    returns the code the kernel recorded (2: the wait gave up, as it must)."""
+    c = ctypes.c_int()
+    _check(lib().mlsdc_selftest_wait_timeout(int(timeout_ms), ctypes.byref(c)), "mlsdc_selftest_wait_timeout")
+    return c.value
 
 
 def sh_inverse(plan: Plan, spec: torch.Tensor, grid: torch.Tensor, nf: int, stream=None):

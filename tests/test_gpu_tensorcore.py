@@ -83,3 +83,29 @@ def test_tensorcore_headline_run_total_geopotential(prec):
     # split BF16 meets the 1e-6 bar; TF32 (10-bit mantissa operands) does not
     # and is reported with its own bound, never as the headline variant
     assert err <= RUN_TOL[prec]
+
+
+def test_bounded_wait_gives_up_and_context_survives():
+    """Failure detection without a fault: one CTA waits on an mbarrier that
+    nothing completes, with the tensor-core kernels' bounded wait and a 20 ms
+    limit.  The wait must give up (code 2) within a bounded time, and the
+    context must stay usable: a tensor-core F_E evaluation afterwards still
+    matches the oracle and records no device error."""
+    import time
+    t0 = time.perf_counter()
+    assert M.selftest_wait_timeout(20) == 2
+    assert time.perf_counter() - t0 < 10.0
+    R, I, J = 21, 64, 32
+    o = oracle(R, I, J)
+    x = inputs.initial_state(R)
+    plan = M.Plan(R, I, J, "bf16x3")
+    plan.set_stage_kernels("tc", "tc")
+    FE = torch.empty((3, o.nc), dtype=torch.complex128, device="cuda")
+    M.swe_explicit_rhs(plan, M.swe_params(), torch.from_numpy(x).cuda(), FE)
+    assert plan.device_error() == 0
+    got = FE.cpu().numpy()
+    ref = o.explicit_rhs(x)
+    for k in range(3):
+        assert rel_l2(R, got[k], ref[k]) <= PER_EVAL_TOL["bf16x3"][k]
+    with pytest.raises(M.MlsdcError):
+        M.selftest_wait_timeout(0)
