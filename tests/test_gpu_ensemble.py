@@ -28,8 +28,8 @@ def rel(a, b):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32", "bf16x3"])
-@pytest.mark.parametrize("R,I,J,B", [(1, 16, 4, 3), (13, 64, 22, 4), (21, 64, 32, 5), (45, 256, 70, 3),
-                                     (85, 256, 128, 17)])
+@pytest.mark.parametrize("R,I,J,B", [(1, 16, 4, 3), (13, 64, 22, 4), (13, 64, 22, 9), (21, 64, 32, 5),
+                                     (45, 256, 70, 3), (85, 256, 128, 17)])
 def test_batched_rhs_equals_single(prec, R, I, J, B):
     x = members_state(R, B)
     pb = M.Plan(R, I, J, prec, max_members=B)
