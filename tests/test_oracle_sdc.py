@@ -9,6 +9,8 @@ Algorithm 1) against closed forms and exact solutions:
     iteration (derived: tau vanishes, restriction is the identity);
   - MLSDC iterated to convergence reaches the fine collocation solution (the
     FAS property shown after Eq. tau_term_level_l+1);
+  - MLSDC(5,3,N,1/2) on the linearised system: observed order near 4 for
+    N = 4 and near 8 for N = 12 (the behaviour Sec. 5 reports);
   - the mean geopotential is conserved."""
 import numpy as np
 import pytest
@@ -187,3 +189,33 @@ def test_mean_geopotential_conserved_over_steps():
         u = sdc.mlsdc_step(fine, coarse, u, 600.0, 2, 1)
     assert abs(u[0, 0] - 50.0) < 1e-12 * 50.0
     assert abs(u[2, 0]) < 1e-20
+
+
+@pytest.mark.parametrize("n_iter,lo,hi", [(4, 3.2, 4.6), (12, 7.4, 8.8)])
+def test_mlsdc_order_with_spatial_coarsening(n_iter, lo, hi):
+    """Sec. 5: MLSDC(5,3,4,1/2) converges at fourth order in the range of small
+    time steps (spatial coarsening limits the coarse correction), and more
+    iterations recover the eighth order of the fine collocation solution.  On
+    the linearised rotating system, fine T6 and coarse T3 (spatial and
+    temporal coarsening), against the exact solution by matrix exponential:
+    4 iterations give an observed order near 4, 12 iterations near 8.  A
+    wrong FAS term or transfer moves the fixed point away from the fine
+    collocation solution and caps the second."""
+    Rf, Rc = 6, 3
+    pf = LinearSWE(Rf, 32, 16, Params())
+    pc = LinearSWE(Rc, 16, 8, Params())
+    u0 = inputs.initial_state(Rf, seed=99, rms=(3e3, 1e-5, 1e-5))
+    A = _linear_operator(pf)
+    T = 7200.0
+    exact = _cplx(scipy_linalg.expm(T * A) @ _real(u0), pf.nc)
+    fine, coarse = sdc.Level(pf, 5), sdc.Level(pc, 3)
+    errs = []
+    for nsteps in (1, 2):
+        dt = T / nsteps
+        u = u0.copy()
+        for _ in range(nsteps):
+            u = sdc.mlsdc_step(fine, coarse, u, dt, n_iter, 1)
+        errs.append(np.sqrt(sht.norm2(Rf, (u - exact)[0]) / sht.norm2(Rf, exact[0])))
+    observed = np.log2(errs[0] / errs[1])
+    assert errs[1] > 1e-14
+    assert lo < observed < hi, (errs, observed)
