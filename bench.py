@@ -738,10 +738,10 @@ def main():
         # the plans' size rule: per level, which Legendre stages run on tcgen05
         for lvl, p_, mem in (("T170", pf, 1), ("T85", pc, 1)):
             stc, atc = p_.stage_kernels(mem)
-            cpc, nst = p_.tc_config()
             stage_kernels[lvl] = {"synthesis": "tcgen05" if stc else "cuda-core fp32",
                                   "analysis": "tcgen05" if atc else "cuda-core fp32",
-                                  "tc_members_per_cta": cpc, "tc_stages": nst}
+                                  "tc_config_synthesis": list(p_.tc_config("synthesis")),
+                                  "tc_config_analysis": list(p_.tc_config("analysis"))}
         stc, atc = pf.stage_kernels(1)
         if stc:
             kern_names["legendre_synthesis"] = f"k_tc_synth<{prec}>"

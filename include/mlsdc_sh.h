@@ -128,17 +128,25 @@ mlsdc_status mlsdc_selftest_wait_timeout(int timeout_ms, int* code);
  * precisions or modes). */
 mlsdc_status sh_plan_stage_kernels(sh_plan_t plan, int members, int* synth_tc, int* anal_tc);
 mlsdc_status sh_plan_set_stage_kernels(sh_plan_t plan, int synth_mode, int anal_mode);
-/* The tensor-core kernels' launch configuration, chosen at plan creation by
- * timing each feasible choice on a full batch of the plan's max_members:
- * members per CTA (1, 2, 4, 8 or 16; the members form the MMA's N dimension,
- * 16 columns each) and the depth of the shared-memory pipeline over K (1 or
- * 2 stages).  sh_plan_tc_config reports it (0, 0 for MLSDC_FP64 / MLSDC_FP32
- * plans; pointers may be NULL); sh_plan_set_tc_config replaces it (results
- * are the same to rounding; MLSDC_ERR_INVALID for other precisions, a member
- * count that is not a power of two up to min(16, max_members), a depth other
- * than 1 or 2, or a choice whose shared memory does not fit a CTA). */
-mlsdc_status sh_plan_tc_config(sh_plan_t plan, int* members_per_cta, int* stages);
-mlsdc_status sh_plan_set_tc_config(sh_plan_t plan, int members_per_cta, int stages);
+/* The launch configuration of each tensor-core Legendre stage (stage 0: the
+ * synthesis, 2: the analysis), chosen at plan creation by timing each
+ * feasible choice of that stage alone on a full batch of the plan's
+ * max_members: members per CTA (1, 2, 4, 8 or 16; the members form the
+ * MMA's N dimension, 16 columns each), the depth of the shared-memory
+ * pipeline over K (1 or 2 stages) and, for the analysis of launches of 3 or
+ * more members, whether it runs the warp-specialised kernel (1: persistent
+ * CTAs of two warpgroups, one staging operands and issuing the MMAs, one
+ * running the epilogue of the previous tile from a second accumulator buffer
+ * in tensor memory; up to 8 members per CTA).  sh_plan_tc_config reports it
+ * (zeros for MLSDC_FP64 / MLSDC_FP32 plans; pointers may be NULL);
+ * sh_plan_set_tc_config replaces it (results are the same to rounding;
+ * MLSDC_ERR_INVALID for other precisions or stages, a member count that is
+ * not a power of two up to min(16, max_members), a depth other than 1 or 2,
+ * warp specialisation for the synthesis or with more than 8 members per CTA,
+ * or a choice whose shared memory does not fit a CTA). */
+mlsdc_status sh_plan_tc_config(sh_plan_t plan, int stage, int* members_per_cta, int* stages, int* warp_specialised);
+mlsdc_status sh_plan_set_tc_config(sh_plan_t plan, int stage, int members_per_cta, int stages,
+                                   int warp_specialised);
 
 /* sh_inverse: spectral -> grid for nf independent scalar fields,
  * Eq. spectral_to_physical_space (Legendre sum per m, then the inverse

@@ -155,7 +155,6 @@ struct MPTables {
 struct sh_plan_s {
     int R, I, J, J2, nc, logI, precision;
     int max_members = 1;              // ensemble members one F_E launch may carry
-    int tc_chunk = 1;                 // members per tensor-core CTA (autotuned)
     std::vector<double> mu, w;        // host copies, north to south, length J
     double* d_mu = nullptr;           // [J]
     double* d_w = nullptr;            // [J]

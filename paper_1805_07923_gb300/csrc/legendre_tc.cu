@@ -67,8 +67,12 @@ struct TcState {
     int* d_err = nullptr;
     int2* d_tiles = nullptr;
     int n_tiles = 0;
-    int chunk = 1;   // members per CTA (autotuned)
-    int stages = 0;  // K pipeline depth (autotuned; 0 = the deepest that fits)
+    // launch configuration per Legendre stage ([0] synthesis, [1] analysis;
+    // autotuned): members per CTA, K pipeline depth, and for the analysis
+    // whether batched launches run the warp-specialised kernel
+    struct Cfg {
+        int chunk = 1, stages = 0, ws = 0;
+    } cfg[2];
 };
 
 // ---------------------------------------------------------------- PTX helpers
@@ -257,6 +261,7 @@ struct TcArgs {
     size_t fe_ms;
     const double* cor;
     const int2* tiles;
+    int n_tiles;
     int* err;
     NodeFuse nf;  // the next node's update, run in the analysis epilogue (nf.on)
     // host-computed constants (no float64 division in the kernels)
@@ -707,6 +712,239 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_anal(const __grid_constant
     cta_release(c, tmem, ncols);
 }
 
+// ------------------------------------------------ analysis, warp-specialised
+// For batched launches (latitude-contiguous input, up to 8 members per CTA):
+// 256 threads, persistent over the (m, 128 degrees) tiles blockIdx.x,
+// blockIdx.x + gridDim.x, ...  Warpgroup 0 (threads 0..127) builds the B
+// operand of each K block while thread 0 issues the block's TMA loads and
+// MMAs into one of two accumulator buffers in tensor memory (the tile's
+// parity) and, after the tile's last block, commits to acc_full[buffer].
+// Warpgroup 1 (threads 128..255) waits for acc_full, reads the accumulators
+// (warp w reads lanes 32 (w % 4) .. 32 (w % 4) + 31), runs the epilogue of
+// k_tc_anal and arrives on acc_empty[buffer]; thread 0 waits for that before
+// the first MMA into the buffer two tiles later.  The epilogue of one tile
+// thus runs while the next tile is loaded, built and multiplied.  Warpgroup
+// 0 synchronises on named barrier 1 and checks the abort flag only after it,
+// so its threads never diverge around the barrier; every wait is bounded.
+constexpr int kWsThreads = 256;
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void producer_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
+template <int MODE>
+__global__ void __launch_bounds__(kWsThreads, 1) k_tc_anal_ws(const __grid_constant__ Maps maps, const TcArgs g) {
+    using S = Shape<MODE>;
+    extern __shared__ unsigned char smem_raw[];
+    const int b0 = blockIdx.y * g.chunk;
+    const int bc = min(g.chunk, g.members - b0);
+    const int N = 16 * bc;
+    const int R = g.R;
+    const int nkb = (g.J2p + S::KB - 1) / S::KB;
+    const int stages = g.stages;
+    const uint32_t ncols = tmem_cols_for(4 * N);  // two accumulator buffers of 2N columns
+    const Cta c = cta_setup<MODE>(smem_raw, g.chunk, stages, ncols);
+    uint64_t* acc_full = reinterpret_cast<uint64_t*>(c.smem + stages * c.stage_sz + 64);
+    uint64_t* acc_empty = acc_full + 2;
+    if (threadIdx.x == 0) {
+        mbar_init(sa(&acc_full[0]), 1);
+        mbar_init(sa(&acc_full[1]), 1);
+        mbar_init(sa(&acc_empty[0]), 4);  // one arrival per epilogue warp
+        mbar_init(sa(&acc_empty[1]), 4);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const uint32_t tmem = *c.tslot;
+    const uint32_t lbo = lbo_for(N);
+    const uint32_t idesc = idesc_for<MODE>(N);
+    const int J = 2 * g.J2;
+    const size_t fs = (size_t)J * (R + 1);
+    constexpr int KV = S::KV, NG = S::KB / S::KV;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    bool ok = true;
+    // thread 0's TMA loads not yet waited for (stages 0, 1) and last committed K block
+    int pend0 = -1, pend1 = -1, q_commit = -1;
+    pdl_wait();
+    if (threadIdx.x < 128) {
+        // ------------------------------------------------ producer warpgroup
+        if (threadIdx.x < 2 * bc) {  // the always-zero H columns, written once per stage buffer
+            const float z[KV] = {};
+            const int b = threadIdx.x >> 1, col = (threadIdx.x & 1) ? 14 : 6;
+            for (int st = 0; st < stages; ++st)
+                for (int gg = 0; gg < NG; ++gg)
+                    for (int cc = 0; cc < 2; ++cc)
+                        put_bv<MODE>(b_tile<MODE>(c, st, 1, 0, g.chunk), b_tile<MODE>(c, st, 1, S::NPART - 1, g.chunk),
+                                     16 * b + col + cc, gg, z, lbo);
+        }
+        int q = 0, tcount = 0;
+        for (int tile = blockIdx.x; tile < g.n_tiles; tile += gridDim.x, ++tcount) {
+            const int2 tl = g.tiles[tile];
+            const int m = tl.x, t = tl.y;
+            const int row = m * (R + 1) - m * (m - 1) / 2 + t * kTileRows;
+            const int buf = tcount & 1;
+            for (int kb = 0; kb < nkb; ++kb, ++q) {
+                const int st = q % stages;
+                // the MMAs that last read this stage must have completed
+                if (q >= stages && !mbar_wait(sa(&c.bars[kMaxStages + st]), (uint32_t)(q / stages - 1) & 1)) {
+                    atomicExch(g.err, kErrMmaTimeout);
+                    *c.abort = 1;
+                }
+                if (threadIdx.x == 0) {
+                    mbar_expect_tx(sa(&c.bars[st]), (uint32_t)(S::NT * kTileBytes));
+                    for (int i = 0; i < S::NT; ++i)
+                        tma_load_2d(sa(a_tile<MODE>(c, st, i)), &maps.m[i], kb * S::KB, row, sa(&c.bars[st]));
+                    if (st == 0) pend0 = q;
+                    else pend1 = q;
+                }
+                unsigned char* P0 = b_tile<MODE>(c, st, 0, 0, g.chunk);
+                unsigned char* P1 = b_tile<MODE>(c, st, 0, S::NPART - 1, g.chunk);
+                unsigned char* H0 = b_tile<MODE>(c, st, 1, 0, g.chunk);
+                unsigned char* H1 = b_tile<MODE>(c, st, 1, S::NPART - 1, g.chunk);
+                for (int it = threadIdx.x; it < bc * 5 * NG; it += 128) {
+                    const int gg = it % NG, qq = it / NG;
+                    const int f = qq % 5, b = qq / 5;
+                    const int j0 = kb * S::KB + gg * KV;
+                    const float2* F = g.four_out + (size_t)(b0 + b) * 5 * fs + (size_t)f * fs + (size_t)m * J;
+                    float2 gN[KV], gS[KV];
+                    if (j0 + KV <= g.J2) {
+                        const float4* pn = reinterpret_cast<const float4*>(F + j0);
+                        const float4* ps = reinterpret_cast<const float4*>(F + (J - j0 - KV));
+#pragma unroll
+                        for (int v = 0; v < KV / 2; ++v) {
+                            const float4 a = pn[v], z = ps[v];
+                            gN[2 * v] = make_float2(a.x, a.y);
+                            gN[2 * v + 1] = make_float2(a.z, a.w);
+                            gS[KV - 1 - 2 * v] = make_float2(z.x, z.y);
+                            gS[KV - 2 - 2 * v] = make_float2(z.z, z.w);
+                        }
+                    } else {
+#pragma unroll
+                        for (int v = 0; v < KV; ++v) {
+                            const int j = j0 + v;
+                            gN[v] = j < g.J2 ? F[j] : make_float2(0.f, 0.f);
+                            gS[v] = j < g.J2 ? F[J - 1 - j] : make_float2(0.f, 0.f);
+                        }
+                    }
+                    float er[KV], ei[KV], orr[KV], oi[KV];
+#pragma unroll
+                    for (int v = 0; v < KV; ++v) {
+                        const float2 e = cadd(gN[v], gS[v]), o = csub(gN[v], gS[v]);
+                        er[v] = e.x;
+                        ei[v] = e.y;
+                        orr[v] = o.x;
+                        oi[v] = o.y;
+                    }
+                    const int cP = f == 0 ? 2 : f == 1 ? 4 : f == 2 ? 0 : f == 4 ? 6 : -1;
+                    const int cH = f == 0 ? 4 : f == 1 ? 2 : f == 3 ? 0 : -1;
+#pragma unroll
+                    for (int grp = 0; grp < 2; ++grp) {
+                        const int c0 = grp == 0 ? cP : cH;
+                        if (c0 < 0) continue;
+                        unsigned char* t0 = grp == 0 ? P0 : H0;
+                        unsigned char* t1 = grp == 0 ? P1 : H1;
+                        const int r = 16 * b + c0;
+                        put_bv<MODE>(t0, t1, r, gg, er, lbo);
+                        put_bv<MODE>(t0, t1, r + 1, gg, ei, lbo);
+                        put_bv<MODE>(t0, t1, r + 8, gg, orr, lbo);
+                        put_bv<MODE>(t0, t1, r + 9, gg, oi, lbo);
+                    }
+                }
+                fence_async_smem();
+                tc_fence_before();
+                producer_sync();
+                tc_fence_after();
+                if (*c.abort) {  // read after the barrier: the same value in every producer thread
+                    ok = false;
+                    break;
+                }
+                if (threadIdx.x == 0) {
+                    // before the tile's first MMA: the epilogue of the tile two back has drained the buffer
+                    if (kb == 0 && tcount >= 2 &&
+                        !mbar_wait(sa(&acc_empty[buf]), (uint32_t)(tcount / 2 - 1) & 1)) {
+                        atomicExch(g.err, kErrMmaTimeout);
+                        *c.abort = 1;
+                    } else if (!mbar_wait(sa(&c.bars[st]), (uint32_t)(q / stages) & 1)) {
+                        atomicExch(g.err, kErrTmaTimeout);
+                        *c.abort = 1;
+                    } else {
+                        if (st == 0) pend0 = -1;
+                        else pend1 = -1;
+                        tc_fence_after();
+                        mma_block<MODE>(c, st, g.chunk, tmem + (uint32_t)(buf * 2 * N), N, idesc, kb == 0);
+                        mma_commit(sa(&c.bars[kMaxStages + st]));
+                        if (kb == nkb - 1) mma_commit(sa(&acc_full[buf]));
+                        q_commit = q;
+                    }
+                }
+            }
+            if (!ok) break;
+        }
+        if (threadIdx.x == 0 && (!ok || *c.abort)) {
+            // a wait gave up: wait (bounded) for this CTA's loads and MMAs in flight
+            if (pend0 >= 0) mbar_wait(sa(&c.bars[0]), (uint32_t)(pend0 / stages) & 1);
+            if (pend1 >= 0) mbar_wait(sa(&c.bars[1]), (uint32_t)(pend1 / stages) & 1);
+            if (q_commit >= 0)
+                mbar_wait(sa(&c.bars[kMaxStages + q_commit % stages]), (uint32_t)(q_commit / stages) & 1);
+        }
+    } else {
+        // ------------------------------------------------ epilogue warpgroup
+        const uint32_t lane_rows = (uint32_t)(32 * (warp & 3)) << 16;
+        int tcount = 0;
+        for (int tile = blockIdx.x; tile < g.n_tiles; tile += gridDim.x, ++tcount) {
+            const int buf = tcount & 1;
+            if (!mbar_wait(sa(&acc_full[buf]), (uint32_t)(tcount / 2) & 1)) {
+                if (lane == 0) atomicExch(g.err, kErrMmaTimeout);
+                *c.abort = 1;
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            const int2 tl = g.tiles[tile];
+            const int m = tl.x, t = tl.y;
+            const int nm = R + 1 - m;
+            const int off = m * (R + 1) - m * (m - 1) / 2;
+            const int k = t * kTileRows + 32 * (warp & 3) + lane;
+            const uint32_t base = tmem + lane_rows + (uint32_t)(buf * 2 * N);
+            for (int b = 0; b < bc; ++b) {
+                float vP[16], vH[16];
+                tmem_ld16(base + 16 * b, vP);
+                tmem_ld16(base + N + 16 * b, vH);
+                if (k >= nm) continue;
+                const bool par = k & 1;
+                float P8[8], H8[8];  // C, A, B, E at this row's parity; D, B, A at the opposite one
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    P8[i] = par ? vP[8 + i] : vP[i];
+                    H8[i] = par ? vH[i] : vH[8 + i];
+                }
+                const float2 sC{P8[0], P8[1]}, sA{P8[2], P8[3]}, sB{P8[4], P8[5]}, sE{P8[6], P8[7]};
+                const float2 hD{H8[0], H8[1]}, hB{H8[2], H8[3]}, hA{H8[4], H8[5]};
+                const int n = m + k;
+                const float ia = g.ia_f, dm = (float)m;
+                const float2 divCD = cscale(csub(cim(dm, sC), hD), ia);
+                const float2 divAB = cscale(csub(cim(dm, sA), hB), ia);
+                const float2 curlAB = cscale(cadd(cim(dm, sB), hA), ia);
+                const float lap = (float)n * (float)(n + 1) * ia * ia;
+                double2 f0 = make_double2(-(double)divCD.x, -(double)divCD.y);
+                double2 f1 = make_double2(-(double)divAB.x, -(double)divAB.y);
+                double2 f2 = make_double2((double)(curlAB.x + lap * sE.x), (double)(curlAB.y + lap * sE.y));
+                coriolis_add(g.state + (size_t)(b0 + b) * g.state_ms, g.cor, g.nc, R, m, n, off, g.two_omega, f1, f2);
+                if (m == 0) f0.y = f1.y = f2.y = 0.0;
+                double2* FE = g.FE + (size_t)(b0 + b) * g.fe_ms;
+                FE[off + k] = f0;
+                FE[g.nc + off + k] = f1;
+                FE[2 * g.nc + off + k] = f2;
+            }
+            // this warp's reads of the buffer are complete (tcgen05.wait::ld)
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(sa(&acc_empty[buf]));
+        }
+    }
+    cta_release(c, tmem, ncols);
+}
+
 // ---------------------------------------------------------- table builders
 // Synthesis tables, K-major in n: row (m, lat) of length KS.
 template <int MODE>
@@ -829,8 +1067,32 @@ mlsdc_status launch_synth(sh_plan_t p, TcState* s, const TcArgs& g, cudaStream_t
     return MLSDC_OK;
 }
 
+// The warp-specialised analysis applies to latitude-contiguous launches of
+// up to 8 members per CTA (two accumulator buffers of 2 x 16 x chunk
+// columns in the 512 of tensor memory) without a fused node update.
+inline bool ws_applies(const TcArgs& g) { return g.fo.sj == 1 && g.chunk <= 8 && !g.nf.on; }
+inline int cfg_index(int stage) { return stage == 0 ? 0 : 1; }
+
+template <int MODE>
+mlsdc_status launch_anal_ws(sh_plan_t p, TcState* s, const TcArgs& g, cudaStream_t st) {
+    const int nchunks = (g.members + g.chunk - 1) / g.chunk;
+    const size_t smem = cta_smem_bytes(MODE, g.chunk, g.stages);
+    mlsdc_status rs = raise_smem_limit((const void*)k_tc_anal_ws<MODE>, smem);
+    if (rs != MLSDC_OK) return rs;
+    int per_sm = 0, sms = 0, dev = 0;
+    MLSDC_CUDA(cudaGetDevice(&dev));
+    MLSDC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    MLSDC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tc_anal_ws<MODE>, kWsThreads, smem));
+    // one wave of persistent CTAs, shared by the member chunks
+    const int nx = std::min(s->n_tiles, std::max(1, per_sm * sms / nchunks));
+    MLSDC_LAUNCH("k_tc_anal_ws",
+                 launch_k(k_tc_anal_ws<MODE>, dim3(nx, nchunks), dim3(kWsThreads), smem, st, s->map_ana, g));
+    return MLSDC_OK;
+}
+
 template <int MODE>
 mlsdc_status launch_anal(sh_plan_t p, TcState* s, const TcArgs& g, cudaStream_t st) {
+    if (s->cfg[1].ws && ws_applies(g)) return launch_anal_ws<MODE>(p, s, g, st);
     const int nchunks = (g.members + g.chunk - 1) / g.chunk;
     const size_t smem = cta_smem_bytes(MODE, g.chunk, g.stages);
     mlsdc_status rs = raise_smem_limit((const void*)k_tc_anal<MODE>, smem);
@@ -840,15 +1102,17 @@ mlsdc_status launch_anal(sh_plan_t p, TcState* s, const TcArgs& g, cudaStream_t 
     return MLSDC_OK;
 }
 
-TcArgs base_args(sh_plan_t p, TcState* s, double a, int members) {
+// stage 0: the synthesis's configuration, 2: the analysis's
+TcArgs base_args(sh_plan_t p, TcState* s, double a, int members, int stage) {
+    const TcState::Cfg& cf = s->cfg[cfg_index(stage)];
     TcArgs g{};
     g.R = p->R;
     g.J2 = p->J2;
     g.nc = p->nc;
     g.J2p = s->J2p;
     g.members = members;
-    g.chunk = std::min(s->chunk, members);
-    g.stages = s->stages > 0 ? s->stages : stages_for(s->mode, g.chunk);
+    g.chunk = std::min(cf.chunk, members);
+    g.stages = cf.stages > 0 ? cf.stages : stages_for(s->mode, g.chunk);
     g.ia_f = (float)(1.0 / a);
     g.na2_f = (float)(-a * a);
     g.invnn = p->mp.invnn32;
@@ -857,20 +1121,22 @@ TcArgs base_args(sh_plan_t p, TcState* s, double a, int members) {
     g.fo = four_out_layout(p->J, p->R, members >= kLatContigMembers);
     g.cor = p->d_cor;
     g.tiles = s->d_tiles;
+    g.n_tiles = s->n_tiles;
     g.err = s->d_err;
     return g;
 }
 
-// Autotuner: for a full batch of members, time the stages the plan's size
-// rule runs on tensor cores at that batch (both when it runs neither, so a
-// forced choice still gets a tuned configuration) with each feasible member
-// chunk (1, 2, 4, 8, 16 members per CTA) and K pipeline depth (two stages,
-// or one, which leaves room for more CTAs per SM), and keep the fastest.
-// Each candidate is timed inside a CUDA graph of kTuneReps launches per
-// stage (the launch cost of the step graphs, not the host's launch rate);
-// a deeper or wider candidate must win by 1 % to replace a shallower one,
-// so near-ties do not flip between runs.  Runs once per plan, on zero
-// inputs, at plan creation.
+// Autotuner: for a full batch of members, time each Legendre stage that the
+// plan's size rule runs on tensor cores at that batch (both when it runs
+// neither, so a forced choice still gets a tuned configuration), on its own,
+// with each feasible member chunk (1, 2, 4, 8, 16 members per CTA), K
+// pipeline depth (two stages, or one, which leaves room for more CTAs per
+// SM) and, for the analysis of batched launches, the warp-specialised
+// kernel, and keep each stage's fastest.  Each candidate is timed inside a
+// CUDA graph of kTuneReps launches (the launch cost of the step graphs, not
+// the host's launch rate); a later candidate must win by 1 % to replace an
+// earlier one, so near-ties do not flip between runs.  Runs once per plan,
+// on zero inputs, at plan creation.
 constexpr int kTuneReps = 10;
 template <int MODE>
 mlsdc_status autotune(sh_plan_t p, TcState* s) {
@@ -884,40 +1150,42 @@ mlsdc_status autotune(sh_plan_t p, TcState* s) {
     MLSDC_CUDA(cudaMemset(x, 0, n * sizeof(double2)));
     cudaStream_t st = nullptr;
     MLSDC_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
-    float best = 1e30f;
-    int best_chunk = 1, best_stages = 0;
     mlsdc_status rs = MLSDC_OK;
-    for (int cfg = 0; cfg < 10 && rs == MLSDC_OK; ++cfg) {
-        const int chunk = 1 << (cfg >> 1), stages = 1 + (cfg & 1);  // (1,1), (1,2), (2,1), ...
-        if (chunk > B || cta_smem_bytes(MODE, chunk, stages) > kSmemBudget) continue;
-        s->chunk = chunk;
-        s->stages = stages;
-        TcArgs g = base_args(p, s, 6.37122e6, B);
-        g.state = x;
-        g.state_ms = (size_t)3 * p->nc;
-        g.FE = fe;
-        g.fe_ms = (size_t)3 * p->nc;
-        auto enqueue = [&](cudaStream_t q) -> mlsdc_status {
-            mlsdc_status r = MLSDC_OK;
-            if (syn) r = launch_synth<MODE>(p, s, g, q);
-            if (r == MLSDC_OK && ana) r = launch_anal<MODE>(p, s, g, q);
-            return r;
-        };
-        rs = enqueue(st);  // outside the capture: sets the kernels' shared-memory limits
-        if (rs == MLSDC_OK) MLSDC_CUDA(cudaStreamSynchronize(st));
-        float ms = 0.f;
-        if (rs == MLSDC_OK) rs = time_in_graph(st, kTuneReps, &ms, enqueue);
-        if (rs == MLSDC_OK && ms < 0.99f * best) {
-            best = ms;
-            best_chunk = chunk;
-            best_stages = stages;
+    for (int stage = 0; stage <= 2 && rs == MLSDC_OK; stage += 2) {
+        if (stage == 0 ? !syn : !ana) continue;
+        TcState::Cfg& cf = s->cfg[cfg_index(stage)];
+        TcState::Cfg best_cf = cf;
+        float best = 1e30f;
+        for (int k = 0; k < 20 && rs == MLSDC_OK; ++k) {
+            // (chunk, stages, ws) = (1,1,0), (1,1,1), (1,2,0), (1,2,1), (2,1,0), ...
+            const int chunk = 1 << (k >> 2), stages = 1 + ((k >> 1) & 1), ws = k & 1;
+            if (chunk > B || cta_smem_bytes(MODE, chunk, stages) > kSmemBudget) continue;
+            if (ws && !(stage == 2 && B >= kLatContigMembers && chunk <= 8)) continue;  // where the ws kernel applies
+            cf.chunk = chunk;
+            cf.stages = stages;
+            cf.ws = ws;
+            TcArgs g = base_args(p, s, 6.37122e6, B, stage);
+            g.state = x;
+            g.state_ms = (size_t)3 * p->nc;
+            g.FE = fe;
+            g.fe_ms = (size_t)3 * p->nc;
+            auto enqueue = [&](cudaStream_t q) -> mlsdc_status {
+                return stage == 0 ? launch_synth<MODE>(p, s, g, q) : launch_anal<MODE>(p, s, g, q);
+            };
+            rs = enqueue(st);  // outside the capture: sets the kernel's shared-memory limit
+            if (rs == MLSDC_OK) MLSDC_CUDA(cudaStreamSynchronize(st));
+            float ms = 0.f;
+            if (rs == MLSDC_OK) rs = time_in_graph(st, kTuneReps, &ms, enqueue);
+            if (rs == MLSDC_OK && ms < 0.99f * best) {
+                best = ms;
+                best_cf = cf;
+            }
         }
+        cf = best_cf;
     }
     cudaStreamDestroy(st);
     cudaFree(x);
     cudaFree(fe);
-    s->chunk = best_chunk;
-    s->stages = best_stages;
     return rs;
 }
 
@@ -945,7 +1213,6 @@ mlsdc_status tc_init(sh_plan_t p) {
     if (rs != MLSDC_OK) return rs;
     rs = s->mode == MODE_TF32 ? autotune<MODE_TF32>(p, s) : autotune<MODE_BF16X3>(p, s);
     if (rs != MLSDC_OK) return rs;
-    p->tc_chunk = s->chunk;
     MLSDC_CUDA(cudaMemset(s->d_err, 0, sizeof(int)));
     return MLSDC_OK;
 }
@@ -965,7 +1232,7 @@ void tc_free(sh_plan_t p) {
 
 mlsdc_status tc_synth(sh_plan_t p, const double* state, double a, RhsBatch b, cudaStream_t st) {
     TcState* s = st_of(p);
-    TcArgs g = base_args(p, s, a, b.members);
+    TcArgs g = base_args(p, s, a, b.members, 0);
     g.state = (const double2*)state;
     g.state_ms = b.state_ms;
     return s->mode == MODE_TF32 ? launch_synth<MODE_TF32>(p, s, g, st) : launch_synth<MODE_BF16X3>(p, s, g, st);
@@ -974,7 +1241,7 @@ mlsdc_status tc_synth(sh_plan_t p, const double* state, double a, RhsBatch b, cu
 mlsdc_status tc_anal(sh_plan_t p, double a, double* FE, const double* state, double two_omega, RhsBatch b,
                      FourStride fo, cudaStream_t st, const NodeFuse* nf) {
     TcState* s = st_of(p);
-    TcArgs g = base_args(p, s, a, b.members);
+    TcArgs g = base_args(p, s, a, b.members, 2);
     if (nf) g.nf = *nf;
     g.state = (const double2*)state;
     g.state_ms = b.state_ms;
@@ -985,23 +1252,27 @@ mlsdc_status tc_anal(sh_plan_t p, double a, double* FE, const double* state, dou
     return s->mode == MODE_TF32 ? launch_anal<MODE_TF32>(p, s, g, st) : launch_anal<MODE_BF16X3>(p, s, g, st);
 }
 
-mlsdc_status tc_config(sh_plan_t p, int* chunk, int* stages) {
+mlsdc_status tc_config(sh_plan_t p, int stage, int* chunk, int* stages, int* ws) {
     TcState* s = st_of(p);
-    if (chunk) *chunk = s ? s->chunk : 0;
-    if (stages) *stages = s ? (s->stages > 0 ? s->stages : stages_for(s->mode, s->chunk)) : 0;
+    if (stage != 0 && stage != 2) return MLSDC_ERR_INVALID;
+    const TcState::Cfg* cf = s ? &s->cfg[cfg_index(stage)] : nullptr;
+    if (chunk) *chunk = cf ? cf->chunk : 0;
+    if (stages) *stages = cf ? (cf->stages > 0 ? cf->stages : stages_for(s->mode, cf->chunk)) : 0;
+    if (ws) *ws = cf ? cf->ws : 0;
     return MLSDC_OK;
 }
 
-mlsdc_status tc_set_config(sh_plan_t p, int chunk, int stages) {
+mlsdc_status tc_set_config(sh_plan_t p, int stage, int chunk, int stages, int ws) {
     TcState* s = st_of(p);
-    if (!s) return MLSDC_ERR_INVALID;
+    if (!s || (stage != 0 && stage != 2)) return MLSDC_ERR_INVALID;
     const bool pow2 = chunk >= 1 && chunk <= 16 && (chunk & (chunk - 1)) == 0;
-    if (!pow2 || chunk > p->max_members || stages < 1 || stages > kMaxStages ||
-        cta_smem_bytes(s->mode, chunk, stages) > kSmemBudget)
+    if (!pow2 || chunk > p->max_members || stages < 1 || stages > kMaxStages || ws < 0 || ws > 1 ||
+        (ws && (stage == 0 || chunk > 8)) || cta_smem_bytes(s->mode, chunk, stages) > kSmemBudget)
         return MLSDC_ERR_INVALID;
-    s->chunk = chunk;
-    s->stages = stages;
-    p->tc_chunk = chunk;
+    TcState::Cfg& cf = s->cfg[cfg_index(stage)];
+    cf.chunk = chunk;
+    cf.stages = stages;
+    cf.ws = ws;
     return MLSDC_OK;
 }
 

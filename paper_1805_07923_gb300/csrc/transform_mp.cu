@@ -26,8 +26,8 @@ __global__ void k_round_c32(const double2* __restrict__ x, float2* __restrict__ 
 }
 
 mlsdc_status tc_init(sh_plan_t p);   // legendre_tc.cu
-mlsdc_status tc_config(sh_plan_t p, int* chunk, int* stages);
-mlsdc_status tc_set_config(sh_plan_t p, int chunk, int stages);
+mlsdc_status tc_config(sh_plan_t p, int stage, int* chunk, int* stages, int* ws);
+mlsdc_status tc_set_config(sh_plan_t p, int stage, int chunk, int stages, int ws);
 mlsdc_status wait_selftest(int timeout_ms, int* code);
 void tc_free(sh_plan_t p);
 mlsdc_status tc_synth(sh_plan_t p, const double* state, double a, RhsBatch b, cudaStream_t st);
@@ -158,9 +158,10 @@ extern "C" mlsdc_status sh_plan_stage_kernels(sh_plan_t p, int members, int* syn
     return MLSDC_OK;
 }
 
-extern "C" mlsdc_status sh_plan_tc_config(sh_plan_t p, int* members_per_cta, int* stages) {
+extern "C" mlsdc_status sh_plan_tc_config(sh_plan_t p, int stage, int* members_per_cta, int* stages,
+                                          int* warp_specialised) {
     if (!p) return MLSDC_ERR_INVALID;
-    return mlsdc::tc_config(p, members_per_cta, stages);
+    return mlsdc::tc_config(p, stage, members_per_cta, stages, warp_specialised);
 }
 
 extern "C" mlsdc_status mlsdc_selftest_wait_timeout(int timeout_ms, int* code) {
@@ -168,9 +169,10 @@ extern "C" mlsdc_status mlsdc_selftest_wait_timeout(int timeout_ms, int* code) {
     return mlsdc::wait_selftest(timeout_ms, code);
 }
 
-extern "C" mlsdc_status sh_plan_set_tc_config(sh_plan_t p, int members_per_cta, int stages) {
+extern "C" mlsdc_status sh_plan_set_tc_config(sh_plan_t p, int stage, int members_per_cta, int stages,
+                                              int warp_specialised) {
     if (!p || !(p->precision == MLSDC_TF32 || p->precision == MLSDC_BF16X3)) return MLSDC_ERR_INVALID;
-    return mlsdc::tc_set_config(p, members_per_cta, stages);
+    return mlsdc::tc_set_config(p, stage, members_per_cta, stages, warp_specialised);
 }
 
 extern "C" mlsdc_status sh_plan_set_stage_kernels(sh_plan_t p, int synth_mode, int anal_mode) {

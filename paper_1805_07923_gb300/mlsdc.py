@@ -68,8 +68,8 @@ _SIGS = {
                                    _VP], _I),
     "sh_plan_stage_kernels": ([_VP, _I, ctypes.POINTER(_I), ctypes.POINTER(_I)], _I),
     "sh_plan_set_stage_kernels": ([_VP, _I, _I], _I),
-    "sh_plan_tc_config": ([_VP, ctypes.POINTER(_I), ctypes.POINTER(_I)], _I),
-    "sh_plan_set_tc_config": ([_VP, _I, _I], _I),
+    "sh_plan_tc_config": ([_VP, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)], _I),
+    "sh_plan_set_tc_config": ([_VP, _I, _I, _I, _I], _I),
     "mlsdc_selftest_wait_timeout": ([_I, ctypes.POINTER(_I)], _I),
     "swe_explicit_rhs_adjoint": ([_VP, ctypes.POINTER(SweParams), _DP, _DP, _DP, _VP], _I),
     "mlsdc_phi_misfit": ([_VP, _DP, _DP, _DP, _DP, _VP], _I),
@@ -198,15 +198,20 @@ class Plan:
                "sh_plan_stage_kernels")
         return bool(a.value), bool(b.value)
 
-    def tc_config(self) -> tuple[int, int]:
-        """(members per CTA, K-pipeline stages) of the tensor-core kernels; (0, 0) otherwise."""
-        a, b = ctypes.c_int(), ctypes.c_int()
-        _check(lib().sh_plan_tc_config(self.h, ctypes.byref(a), ctypes.byref(b)), "sh_plan_tc_config")
-        return a.value, b.value
+    TC_STAGES = {"synthesis": 0, "analysis": 2}
 
-    def set_tc_config(self, members_per_cta: int, stages: int):
-        """Replace the autotuned tensor-core configuration (tensor-core plans only)."""
-        _check(lib().sh_plan_set_tc_config(self.h, int(members_per_cta), int(stages)), "sh_plan_set_tc_config")
+    def tc_config(self, stage: str = "analysis") -> tuple[int, int, int]:
+        """(members per CTA, K-pipeline stages, warp-specialised batched analysis) of one
+        tensor-core Legendre stage; zeros for other precisions."""
+        a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(lib().sh_plan_tc_config(self.h, self.TC_STAGES[stage], ctypes.byref(a), ctypes.byref(b),
+                                       ctypes.byref(c)), "sh_plan_tc_config")
+        return a.value, b.value, c.value
+
+    def set_tc_config(self, members_per_cta: int, stages: int, warp_specialised: int = 0, stage: str = "analysis"):
+        """Replace the autotuned configuration of one tensor-core Legendre stage."""
+        _check(lib().sh_plan_set_tc_config(self.h, self.TC_STAGES[stage], int(members_per_cta), int(stages),
+                                           int(warp_specialised)), "sh_plan_set_tc_config")
 
     def set_stage_kernels(self, synth: str = "auto", anal: str = "auto"):
         """Per-stage kernel mode of a tensor-core plan: "auto" (the size rule), "tc" or "simt"."""

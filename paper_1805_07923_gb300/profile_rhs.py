@@ -31,12 +31,17 @@ def main(argv=None):
     ap.add_argument("--members", type=int, default=1)
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--adjoint", action="store_true", help="the float64 F_E adjoint instead of F_E")
+    ap.add_argument("--tc-config", default=None,
+                    help="members_per_cta,stages,warp_specialised: replace the analysis's autotuned tensor-core "
+                         "configuration (the synthesis keeps its own)")
     ap.add_argument("--kernels", default="auto", choices=["auto", "tc", "simt"],
                     help="tensor-core plans: the plan's choice, or both Legendre stages on tcgen05 / CUDA cores")
     a = ap.parse_args(argv)
     plan = M.Plan(a.R, a.nlon, a.nlat, "fp64" if a.adjoint else a.precision, a.members)
     if a.kernels != "auto" and a.precision in ("tf32", "bf16x3") and not a.adjoint:
         plan.set_stage_kernels(a.kernels, a.kernels)
+    if a.tc_config and a.precision in ("tf32", "bf16x3") and not a.adjoint:
+        plan.set_tc_config(*[int(v) for v in a.tc_config.split(",")])
     prm = M.swe_params()
     base = inputs.initial_state(a.R)
     x = torch.from_numpy(np.stack([inputs.perturbed_member(base, a.R, a.R, k) for k in range(a.members)])).cuda()
@@ -58,7 +63,8 @@ def main(argv=None):
         ms = M.mlsdc_profile_rhs(plan, prm, x, fe, reps=20, members=a.members)
     print(json.dumps({"R": a.R, "nlon": a.nlon, "nlat": a.nlat, "precision": a.precision, "members": a.members,
                       "adjoint": a.adjoint, "stage_ms": ms, "stage_kernels_tc": plan.stage_kernels(a.members),
-                      "tc_config": plan.tc_config()}))
+                      "tc_config": {"synthesis": plan.tc_config("synthesis"),
+                                    "analysis": plan.tc_config("analysis")}}))
 
 
 if __name__ == "__main__":

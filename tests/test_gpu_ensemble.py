@@ -134,10 +134,12 @@ def test_uneven_ensemble_in_one_graph_equals_members_alone(prec):
 @pytest.mark.parametrize("prec", ["tf32", "bf16x3"])
 def test_tensor_core_configs_agree(prec):
     """Every feasible tensor-core launch configuration (members per CTA, K
-    stages) reproduces the single-member results to 1e-12.  T85 on 256 x 160
-    has two (bf16) or four (tf32) K blocks of latitudes per tile, so one-stage
-    configurations refill their stage within a tile; 17 members leave a ragged
-    last member chunk for every chunk size."""
+    stages, warp-specialised batched analysis) reproduces the single-member
+    results to 1e-12.  T85 on 256 x 160 has two (bf16) or four (tf32) K blocks
+    of latitudes per tile, so one-stage configurations refill their stage
+    within a tile; 17 members leave a ragged last member chunk for every chunk
+    size; the warp-specialised CTAs loop over several tiles each, alternating
+    their two accumulator buffers."""
     R, I, J, B = 85, 256, 160, 17
     x = members_state(R, B)
     prm = M.swe_params()
@@ -152,12 +154,14 @@ def test_tensor_core_configs_agree(prec):
     pb = M.Plan(R, I, J, prec, max_members=B)
     pb.set_stage_kernels("tc", "tc")
     tried = 0
-    for cfg in [(1, 1), (1, 2), (2, 1), (2, 2), (4, 1), (4, 2), (8, 1), (16, 1)]:
+    for cfg in [(1, 1, 0), (1, 2, 0), (2, 1, 0), (2, 2, 0), (4, 1, 0), (4, 2, 0), (8, 1, 0), (16, 1, 0),
+                (1, 1, 1), (1, 2, 1), (2, 2, 1), (4, 1, 1), (4, 2, 1), (8, 1, 1)]:
         try:
-            pb.set_tc_config(*cfg)
+            pb.set_tc_config(cfg[0], cfg[1], 0, stage="synthesis")
+            pb.set_tc_config(*cfg, stage="analysis")
         except RuntimeError:
             continue  # shared memory of this choice does not fit a CTA
-        assert pb.tc_config() == cfg
+        assert pb.tc_config("analysis") == cfg and pb.tc_config("synthesis") == (cfg[0], cfg[1], 0)
         FEb = torch.full_like(xs, float("nan"))
         M.swe_explicit_rhs_batched(pb, prm, xs, FEb, B)
         got = FEb.cpu().numpy()
