@@ -343,7 +343,25 @@ def run_ensemble(args):
     clocks.start()
     time.sleep(0.3)
     total_ms, ens, groups, keep, states = timed(prec, K)
+    # end to end through the public API with host buffers: every member's state
+    # from pinned memory, the ensemble step, every state back, every step
+    hosts_in = [x.cpu().pin_memory() for x in states]
+    hosts_out = [torch.empty_like(h).pin_memory() for h in hosts_in]
+    Ke = min(K, 100)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(Ke):
+        for x, h in zip(states, hosts_in):
+            x.copy_(h, non_blocking=True)
+        M.mlsdc_ensemble_step(ens, states, w["dt"], w["n_iter"], w["n_coarse"], use_graph=True)
+        for x, h in zip(states, hosts_out):
+            h.copy_(x, non_blocking=True)
+    e1.record(stream)
+    e1.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
     clk = clocks.stop()
+    nbytes = sum(h.numel() * h.element_size() for h in hosts_in)
     members = sum(g[-1] for g in ENSEMBLE)
     value = members * K / (total_ms * 1e-3)
     nfe, nce = evals_per_step(w)
@@ -380,7 +398,11 @@ def run_ensemble(args):
                                             "l2": "flushed between timed steps (256 MB write)"},
             "sh_tflops": flops * K / (total_ms * 1e-3) / 1e12, "gpu_launches": ens.launch_count() * K,
             "roofline": roof, "stage_ms": stages, "clocks": clk,
+            "e2e": {"value": members * Ke / (e2e_ms * 1e-3), "unit": "member-steps/s", "h2d_bytes_per_step": nbytes,
+                    "d2h_bytes_per_step": nbytes},
             }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_ensemble()
     if prec != "fp64":
         del ens, groups, keep, states
         K64 = max(3, min(K, 10))
@@ -572,6 +594,28 @@ def cpu_baseline(steps_cap_s: float = 25.0):
         n += 1
     return {"value": n / t, "unit": "steps/s", "cores": os.cpu_count(), "kind": "oracle",
             "sample": f"{n} MLSDC steps of the same workload (float64 numpy oracle, setup {setup:.1f} s untimed)"}
+
+
+def cpu_baseline_ensemble():
+    """The float64 oracle on a bounded sample of the ensemble: one MLSDC step of
+    one member per truncation group, weighted by the group sizes."""
+    from oracle import sdc as osdc
+    from oracle.swe import SWE, Params
+    from paper_1805_07923_gb300 import inputs
+    w = WORKLOAD
+    base = inputs.initial_state(170)
+    secs = 0.0
+    for (Rf, If, Jf, Rc, Ic, Jc, B) in ENSEMBLE:
+        fine = osdc.Level(SWE(Rf, If, Jf, Params()), w["nf"])
+        coarse = osdc.Level(SWE(Rc, Ic, Jc, Params()), w["nc"])
+        u = inputs.perturbed_member(base, 170, Rf, 0)
+        t = time.perf_counter()
+        osdc.mlsdc_step(fine, coarse, u, w["dt"], w["n_iter"], w["n_coarse"])
+        secs += B * (time.perf_counter() - t)
+    members = sum(g[-1] for g in ENSEMBLE)
+    return {"value": members / secs, "unit": "member-steps/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": "one oracle MLSDC step of one member per truncation group (T42/T21, T85/T42, T170/T85), "
+                      "weighted by the group sizes (32, 48, 16)"}
 
 
 def run_reference(args):
