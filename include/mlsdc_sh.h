@@ -343,7 +343,7 @@ mlsdc_status mlsdc_phi_misfit(sh_plan_t plan, const double* state, const double*
  * time, recording that segment's F_E inputs, then walks it backwards.  Device
  * memory: the checkpoints, checkpoint_every steps of F_E inputs, and one
  * adjoint copy of every buffer a step uses.  The MLSDC object (float64 plans,
- * one member) must outlive the driver and shares its buffers: order calls
+ * one member) must outlive the adjoint object and shares its buffers: order calls
  * on one stream. */
 mlsdc_status mlsdc_adjoint_create(mlsdc_t ml, int n_steps, int checkpoint_every, double dt, int n_iter,
                                   int n_coarse_sweeps, mlsdc_adjoint_t* out);

@@ -4,7 +4,7 @@ implicit solve) against the float64 oracle and the float64 GPU path.
 Bars: per F_E evaluation, relative L2 per field within a bound derived from
 float32 rounding (u = 6e-8) times the cancellation of each tendency (the
 vorticity and divergence tendencies cancel to ~1e-2 of their parts); per run,
-the benchmark spec criterion: relative L2 of the total geopotential Phibar + Phi'
+the acceptance criterion: relative L2 of the total geopotential Phibar + Phi'
 <= 1e-6 after the 400-step headline run, against the float64 path (itself
 parity-pinned to the oracle per step at 1e-12)."""
 import numpy as np
