@@ -21,14 +21,18 @@ coefficient.  With L = -n(n+1)/a^2 and c = 1 - alpha nu L:
   c Phi' + alpha Phibar delta = b_Phi ;  alpha L Phi' + c delta = b_delta
   Phi'  = (c b_Phi - alpha Phibar b_delta) / (c^2 - alpha^2 Phibar L)
   delta = (b_delta - alpha L Phi') / c
+SWECoriolisImplicit is the alternative split with L_F moved into F_I; its
+implicit system couples degrees n - 1, n, n + 1 and is solved densely per m.
 """
 from __future__ import annotations
 
-from dataclasses import dataclass
+from dataclasses import dataclass, replace
+from functools import lru_cache
 
 import numpy as np
 
-from .sht import Grid, truncate, zero_pad, zero_m0_imag
+from . import legendre
+from .sht import Grid, spec_mn, m_slice, truncate, zero_pad, zero_m0_imag
 
 
 @dataclass(frozen=True)
@@ -106,3 +110,103 @@ class SWE:
         tot = ref[0].copy()
         tot[0] += np.sqrt(2.0) * self.p.phibar
         return float(np.sqrt(norm2(self.R, x[0] - ref[0]) / norm2(self.R, tot)))
+
+
+@lru_cache(maxsize=None)
+def _eps_neighbours(R: int):
+    """Per stored coefficient (m, n): eps^m_n (0 for n = m) and eps^m_{n+1}
+    (0 for n = R), the factors of the n - 1 and n + 1 neighbours."""
+    m, n = spec_mn(R)
+    e_lo = np.array([legendre.eps(mm, nn) for mm, nn in zip(m, n)])
+    e_hi = np.array([legendre.eps(mm, nn + 1) if nn + 1 <= R else 0.0 for mm, nn in zip(m, n)])
+    return n, e_lo, e_hi
+
+
+def _lower(x: np.ndarray) -> np.ndarray:
+    """x[k - 1] at k (0 at k = 0); used only where eps^m_n masks the m boundary."""
+    return np.concatenate([np.zeros(1, x.dtype), x[:-1]])
+
+
+def _upper(x: np.ndarray) -> np.ndarray:
+    """x[k + 1] at k (0 at the end); used only where eps^m_{n+1} masks n = R."""
+    return np.concatenate([x[1:], np.zeros(1, x.dtype)])
+
+
+def mu_times(x: np.ndarray, R: int) -> np.ndarray:
+    """Spectral coefficients of mu times a field, projected on n <= R: from the
+    recurrence mu P^m_n = eps^m_{n+1} P^m_{n+1} + eps^m_n P^m_{n-1} (Sec. 3),
+    (mu f)^m_n = eps^m_n f^m_{n-1} + eps^m_{n+1} f^m_{n+1}."""
+    _, e_lo, e_hi = _eps_neighbours(R)
+    return e_lo * _lower(x) + e_hi * _upper(x)
+
+
+def h_times(x: np.ndarray, R: int) -> np.ndarray:
+    """Spectral coefficients of (1 - mu^2) d f / d mu, projected on n <= R: from
+    H^m_n = -n eps^m_{n+1} P^m_{n+1} + (n+1) eps^m_n P^m_{n-1},
+    (H f)^m_n = -(n-1) eps^m_n f^m_{n-1} + (n+2) eps^m_{n+1} f^m_{n+1}."""
+    n, e_lo, e_hi = _eps_neighbours(R)
+    return -(n - 1) * e_lo * _lower(x) + (n + 2) * e_hi * _upper(x)
+
+
+class SWECoriolisImplicit(SWE):
+    """The alternative splitting of Sec. 4.1 with the Coriolis terms treated
+    implicitly: F_I = L_G + L_F, F_E = N (the paper keeps L_F explicit; this
+    variant moves it).
+
+    L_F is the linear Coriolis part of F_E, written in closed spectral form
+    from Sec. 2's equations with f = 2 Omega mu and V = k x grad psi + grad chi:
+      -div(f V)  = -f delta - V.grad f  = -2 Omega mu delta - (2 Omega / a^2)(i m psi + H chi)
+       curl(f V) =  f zeta  + k.(grad f x V) = 2 Omega mu zeta - (2 Omega / a^2)(i m chi - H psi)
+    with mu times a field and H = (1 - mu^2) d/dmu applied through the
+    Legendre recurrences (mu_times, h_times), both projected on n <= R.
+    N = F_E with Omega = 0 (the nonlinear terms alone).
+
+    The implicit system x - alpha F_I(x) = b no longer decouples per
+    coefficient: the Coriolis terms couple degrees n - 1, n, n + 1 of the same
+    zonal wavenumber m.  It is solved as it stands, per m, as a dense complex
+    linear system over the 3 (R + 1 - m) unknowns (Phi', zeta, delta) of that
+    m (the blocks of F_I on each m are formed once, by applying F_I to unit
+    vectors)."""
+
+    def __init__(self, R: int, I: int, J: int, params: Params = Params()):
+        super().__init__(R, I, J, params)
+        self._no_rotation = SWE(R, I, J, replace(params, omega=0.0))
+        self._blocks = None
+
+    def coriolis(self, x: np.ndarray) -> np.ndarray:
+        p, R = self.p, self.R
+        phi, zeta, delta = x
+        psi, chi = self.inverse_laplacian(zeta), self.inverse_laplacian(delta)
+        m, _ = spec_mn(R)
+        tw, ia2 = 2.0 * p.omega, 1.0 / (p.a * p.a)
+        lz = -tw * mu_times(delta, R) - tw * ia2 * (1j * m * psi + h_times(chi, R))
+        ld = tw * mu_times(zeta, R) - tw * ia2 * (1j * m * chi - h_times(psi, R))
+        return np.stack([np.zeros_like(phi), lz, ld])
+
+    def explicit_rhs(self, x: np.ndarray) -> np.ndarray:
+        return self._no_rotation.explicit_rhs(x)
+
+    def implicit_rhs(self, x: np.ndarray) -> np.ndarray:
+        return SWE.implicit_rhs(self, x) + self.coriolis(x)
+
+    def _implicit_blocks(self):
+        if self._blocks is None:
+            self._blocks = []
+            for m in range(self.R + 1):
+                sl = m_slice(self.R, m)
+                nm = sl.stop - sl.start
+                A = np.zeros((3 * nm, 3 * nm), complex)
+                for col in range(3 * nm):
+                    e = np.zeros((3, self.nc), complex)
+                    e[col // nm, sl.start + col % nm] = 1.0
+                    A[:, col] = self.implicit_rhs(e)[:, sl].ravel()
+                self._blocks.append(A)
+        return self._blocks
+
+    def implicit_solve(self, b: np.ndarray, alpha: float) -> np.ndarray:
+        x = np.zeros_like(b)
+        for m, A in enumerate(self._implicit_blocks()):
+            sl = m_slice(self.R, m)
+            nm = sl.stop - sl.start
+            x[:, sl] = np.linalg.solve(np.eye(3 * nm) - alpha * A, b[:, sl].ravel()).reshape(3, nm)
+        return x

@@ -5,6 +5,7 @@ import pytest
 
 from oracle import quadrature, sdc, sht, swe
 
+import test_oracle_coriolis_implicit as T_ci
 import test_oracle_quadrature as T_q
 import test_oracle_sdc as T_sdc
 import test_oracle_sht as T_sht
@@ -188,3 +189,23 @@ def test_adjoint_missing_kinetic_energy_weight_is_caught(monkeypatch):
         return orig_t(g, s) * (1.0 - g.mu[:, None] ** 2)
     monkeypatch.setattr(oad, "analysis_t", bad)
     _fails(T_ad.test_explicit_rhs_adjoint_dot_product)
+
+
+def test_coriolis_closed_form_sign_mistake_is_caught(monkeypatch):
+    def coriolis(self, x):
+        p, R = self.p, self.R
+        _, zeta, delta = x
+        psi, chi = self.inverse_laplacian(zeta), self.inverse_laplacian(delta)
+        m, _ = sht.spec_mn(R)
+        tw, ia2 = 2.0 * p.omega, 1.0 / (p.a * p.a)
+        lz = -tw * swe.mu_times(delta, R) - tw * ia2 * (1j * m * psi + swe.h_times(chi, R))
+        ld = tw * swe.mu_times(zeta, R) - tw * ia2 * (1j * m * chi + swe.h_times(psi, R))   # sign of H psi
+        return np.stack([np.zeros_like(zeta), lz, ld])
+    monkeypatch.setattr(swe.SWECoriolisImplicit, "coriolis", coriolis)
+    _fails(T_ci.test_closed_form_coriolis_is_the_transform_linear_part, 10, 32, 16)
+
+
+def test_coupled_solve_without_coriolis_is_caught(monkeypatch):
+    monkeypatch.setattr(swe.SWECoriolisImplicit, "implicit_solve", swe.SWE.implicit_solve)
+    _fails(T_ci.test_coupled_solve_residual_against_transform_coriolis, 3.0e3)
+    _fails(T_ci.test_fully_implicit_linear_sweeps_reach_collocation)
