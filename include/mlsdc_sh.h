@@ -210,6 +210,33 @@ mlsdc_status swe_implicit_rhs(sh_plan_t plan, const swe_params* prm, const doubl
 mlsdc_status swe_implicit_solve(sh_plan_t plan, const swe_params* prm, double alpha,
                                 const double* b, double* x, void* stream);
 
+/* Options of the splitting F = F_I + F_E (Sec. 4.1).  0: the paper's split,
+ * F_I = L_G, F_E = L_F + N.  MLSDC_CORIOLIS_IMPLICIT: the alternative with
+ * the Coriolis terms implicit, F_I = L_G + L_F, F_E = N; L_F is the exact
+ * spectral Coriolis operator (tridiagonal in n for each m, from the mu and
+ * (1 - mu^2) d/dmu recurrences of the Legendre functions), and F_E is then
+ * swe_explicit_rhs with Omega = 0. */
+#define MLSDC_CORIOLIS_IMPLICIT 1
+
+/* swe_implicit_rhs_ex: F_I of the splitting `options` (0: swe_implicit_rhs;
+ * MLSDC_CORIOLIS_IMPLICIT: L_G + L_F).  state, FI: [3][N_c] float64; FI must
+ * not alias state with MLSDC_CORIOLIS_IMPLICIT (L_F reads the neighbouring
+ * degrees).  Unknown option bits: MLSDC_ERR_INVALID. */
+mlsdc_status swe_implicit_rhs_ex(sh_plan_t plan, const swe_params* prm, const double* state,
+                                 double* FI, int options, void* stream);
+
+/* swe_implicit_solve_ex: x - alpha F_I(x) = b for the splitting `options`.
+ * With MLSDC_CORIOLIS_IMPLICIT the system couples degrees n - 1, n, n + 1 of
+ * each zonal wavenumber m: Phi' is eliminated per coefficient, and the rest
+ * is two complex tridiagonal systems per m, (zeta_m, delta_{m+1}, zeta_{m+2}, ...)
+ * and (delta_m, zeta_{m+1}, ...), factored by the Thomas algorithm (no
+ * pivoting: the systems are diagonally dominant while 2 Omega alpha stays
+ * well below 1, i.e. alpha below about 3000 s) and substituted by warp-wide
+ * scans.  alpha >= 0; b, x: [3][N_c]; x may alias b.  Always float64; the
+ * factor table is a stream-ordered allocation freed before return. */
+mlsdc_status swe_implicit_solve_ex(sh_plan_t plan, const swe_params* prm, double alpha,
+                                   const double* b, double* x, int options, void* stream);
+
 /* ---------------------------------------------------------------------------
  * sdc_level: one space-time level: a plan, the physics, and n_nodes
  * Gauss-Lobatto nodes on [0, 1] with the collocation matrix Q (Sec. 4.2,
@@ -224,6 +251,14 @@ mlsdc_status sdc_level_create(sh_plan_t plan, const swe_params* prm, int n_nodes
  * arrays of sdc_sweep are [members][M+1][3][N_c]. */
 mlsdc_status sdc_level_create_batched(sh_plan_t plan, const swe_params* prm, int n_nodes, int members,
                                       sdc_level_t* out);
+/* sdc_level_create_ex: sdc_level_create_batched with a splitting `options`
+ * (0 or MLSDC_CORIOLIS_IMPLICIT, see swe_implicit_solve_ex).  An
+ * implicit-Coriolis level evaluates F_E with Omega = 0 and F_I = L_G + L_F;
+ * its node updates solve the coupled system per wavenumber, with the chains
+ * factored once per step size and node.  Both levels of an mlsdc_t must use
+ * the same options; the adjoint (mlsdc_adjoint_create) accepts only 0. */
+mlsdc_status sdc_level_create_ex(sh_plan_t plan, const swe_params* prm, int n_nodes, int members, int options,
+                                 sdc_level_t* out);
 mlsdc_status sdc_level_destroy(sdc_level_t lev);
 /* Host copies of the node times t[n_nodes] and row-major Q, QE, QI [n_nodes^2]
  * (any pointer may be NULL). */

@@ -767,6 +767,10 @@ extern "C" mlsdc_status mlsdc_adjoint_create(mlsdc_t ml, int n_steps, int checkp
         set_error_text("mlsdc_adjoint_create: needs one member and float64 plans");
         return MLSDC_ERR_INVALID;
     }
+    if (F->options || C->options) {
+        set_error_text("mlsdc_adjoint_create: the implicit-Coriolis splitting has no adjoint");
+        return MLSDC_ERR_INVALID;
+    }
     mlsdc_adjoint_t A = new mlsdc_adjoint_s();
     A->ml = ml;
     A->n_steps = n_steps;

@@ -123,7 +123,7 @@ inline mlsdc_status time_in_graph(cudaStream_t st, int reps, float* ms, Enqueue 
 // belongs to the kernel, not to a plan, so a plan needing less must not undo
 // the setting another live plan relies on.
 mlsdc_status raise_smem_limit(const void* fn, size_t bytes);
-inline int moff(int R, int m) { return m * (R + 1) - m * (m - 1) / 2; }
+__host__ __device__ inline int moff(int R, int m) { return m * (R + 1) - m * (m - 1) / 2; }
 
 // Work item of a Legendre kernel: zonal wavenumber m and the first
 // latitude (synthesis) or the first degree offset n - m (analysis).

@@ -230,42 +230,6 @@ __global__ void __launch_bounds__(256) k_grid_rhs(const C_t<T>* __restrict__ fou
     }
 }
 
-// The Coriolis (linear) part of F_E at coefficient (m, n), exactly, in
-// float64 spectral arithmetic.  With f = 2 Omega mu, -div(f V) and curl(f V)
-// are tridiagonal in n for each m:
-//   dzeta  = -2 Omega (mu delta)_n - (2 Omega / a^2) [ i m psi_n + (H chi)_n ]
-//   ddelta =  2 Omega (mu zeta)_n  - (2 Omega / a^2) [ i m chi_n - (H psi)_n ]
-//   (mu x)_n = eps_n x_{n-1} + eps_{n+1} x_{n+1},
-//   (H x)_n  = -(n-1) eps_n x_{n-1} + (n+2) eps_{n+1} x_{n+1},
-// from mu P_n = eps_{n+1} P_{n+1} + eps_n P_{n-1} and H_n = (1 - mu^2) dP_n/dmu,
-// projected on n <= R; psi, chi = -a^2/(n(n+1)) (zeta, delta).  Collecting
-// the factors of each neighbour (the a^2 of psi, chi cancels the 1/a^2):
-//   dzeta  = -2 Omega [ alpha delta_{n-1} + beta delta_{n+1} + gamma i zeta_n ]
-//   ddelta =  2 Omega [ alpha zeta_{n-1}  + beta zeta_{n+1}  - gamma i delta_n ]
-// with the plan's per-coefficient factors cor[4 idx .. +2] = (alpha, beta,
-// gamma): 16 float64 operations per coefficient (float64 runs at a small
-// fraction of the float32 rate on this GPU).  The mixed-precision paths add
-// this term in float64 and send only the nonlinear part of the products
-// through the reduced-precision transforms.  Adds dzeta to f1 and ddelta to f2.
-__device__ inline void coriolis_add(const double2* __restrict__ state, const double* __restrict__ cor, int nc, int R,
-                                    int m, int n, int off, double two_omega, double2& f1, double2& f2) {
-    const int k = n - m;
-    const double2* z = state + nc + off;
-    const double2* d = state + 2 * nc + off;
-    double2 zl{0, 0}, zu{0, 0}, dl{0, 0}, du{0, 0};
-    if (n - 1 >= m) { zl = z[k - 1]; dl = d[k - 1]; }
-    if (n + 1 <= R) { zu = z[k + 1]; du = d[k + 1]; }
-    const double2 zk = z[k], dk = d[k];
-    const double2 ab = *reinterpret_cast<const double2*>(cor + 4 * (size_t)(off + k));
-    const double al = ab.x, be = ab.y, ga = cor[4 * (size_t)(off + k) + 2];
-    const double ux = fma(al, dl.x, fma(be, du.x, -ga * zk.y)), uy = fma(al, dl.y, fma(be, du.y, ga * zk.x));
-    const double vx = fma(al, zl.x, fma(be, zu.x, ga * dk.y)), vy = fma(al, zl.y, fma(be, zu.y, -ga * dk.x));
-    f1.x = fma(-two_omega, ux, f1.x);
-    f1.y = fma(-two_omega, uy, f1.y);
-    f2.x = fma(two_omega, vx, f2.x);
-    f2.y = fma(two_omega, vy, f2.y);
-}
-
 // div(X,Y)^m_n = (1/a) sum_j [ i m X' P - Y' H ], curl(X,Y)^m_n = (1/a) sum_j [ i m Y' P + X' H ]
 // with X', Y' the weighted Fourier coefficients (integration by parts of the
 // mu-derivatives); E^m_n = sum_j E' P.  With two_omega_lin != 0 the grid

@@ -344,13 +344,14 @@ static mlsdc_status eval_FE(sdc_level_t L, const double2* x, double2* FE, cudaSt
     b.members = nodes > 0 ? nodes : L->members;
     b.state_ms = b.fe_ms = nodes > 0 ? L->node() : L->ms();
     if (L->plan->precision == MLSDC_FP64)
-        return rhs_explicit_f64(L->plan, &L->prm, (const double*)x, (double*)FE, st, &L->launches, -1, b, nf);
-    return rhs_explicit_mp(L->plan, &L->prm, (const double*)x, (double*)FE, st, &L->launches, -1, b, nf);
+        return rhs_explicit_f64(L->plan, &L->prm_fe, (const double*)x, (double*)FE, st, &L->launches, -1, b, nf);
+    return rhs_explicit_mp(L->plan, &L->prm_fe, (const double*)x, (double*)FE, st, &L->launches, -1, b, nf);
 }
 
 static mlsdc_status eval_FI(sdc_level_t L, const double2* x, double2* FI, cudaStream_t st, int nodes = 0) {
     const int nc = L->plan->nc;
     const size_t ms = nodes > 0 ? L->node() : L->ms();
+    if (L->options & MLSDC_CORIOLIS_IMPLICIT) return cor_fi_launch(L, x, FI, nodes > 0 ? nodes : L->members, ms, st);
     MLSDC_LAUNCH("k_implicit_rhs", launch_k(k_implicit_rhs, dim3(grid_for(nc), nodes > 0 ? nodes : L->members),
                                             dim3(256), 0, st, x, FI, (const int*)L->plan->d_ndeg, nc,
                                             phys_of(L->prm), ms, ms));
@@ -376,6 +377,7 @@ static NodeRow node_row(sdc_level_t L, int m) {
 static mlsdc_status launch_node(sdc_level_t L, double dt, const NodeRow& row, double2* Th, const double2* FIo,
                                 const double2* FEo, double2* FIn, double2* FEn, const double2* tau,
                                 cudaStream_t st) {
+    if (L->options & MLSDC_CORIOLIS_IMPLICIT) return cor_node_launch(L, dt_scaled(row, dt), Th, FIo, FEo, FIn, FEn, tau, st);
     const int nc = L->plan->nc;
     MLSDC_LAUNCH("k_sweep_node",
                  launch_k(k_sweep_node, dim3((nc + kNodeCoefs - 1) / kNodeCoefs, L->members), dim3(3 * kNodeCoefs),
@@ -394,8 +396,10 @@ static mlsdc_status launch_bcast(sdc_level_t L, const double2* src, double2* dst
     return MLSDC_OK;
 }
 
-// The solve reciprocals of the level's node updates at step size dt.
+// The solve reciprocals of the level's node updates at step size dt (with
+// implicit Coriolis: the factored chains instead).
 static mlsdc_status launch_solve_coefs(sdc_level_t L, double dt, cudaStream_t st) {
+    if (L->options & MLSDC_CORIOLIS_IMPLICIT) return cor_factor_launch(L, dt, st);
     QiDiag qd;
     std::memset(&qd, 0, sizeof(qd));
     for (int m = 0; m + 1 < L->n; ++m) qd.v[m] = L->QI[(m + 1) * L->n + m + 1];
@@ -494,13 +498,17 @@ extern "C" mlsdc_status mlsdc_check_finite(const double* state, int64_t n, int* 
     return MLSDC_OK;
 }
 
-extern "C" mlsdc_status sdc_level_create_batched(sh_plan_t plan, const swe_params* prm, int n_nodes, int members,
-                                                 sdc_level_t* out) {
+extern "C" mlsdc_status sdc_level_create_ex(sh_plan_t plan, const swe_params* prm, int n_nodes, int members,
+                                            int options, sdc_level_t* out) {
     if (!plan || !prm || !out || n_nodes < 2 || n_nodes > kMaxNodes) return MLSDC_ERR_INVALID;
     if (members < 1 || members > plan->max_members) return MLSDC_ERR_INVALID;
+    if (options & ~MLSDC_CORIOLIS_IMPLICIT) return MLSDC_ERR_INVALID;
     sdc_level_t L = new sdc_level_s();
     L->plan = plan;
     L->prm = *prm;
+    L->prm_fe = *prm;
+    L->options = options;
+    if (options & MLSDC_CORIOLIS_IMPLICIT) L->prm_fe.omega = 0.0;  // F_E = N
     L->n = n_nodes;
     L->members = members;
     const int n = n_nodes;
@@ -542,6 +550,13 @@ extern "C" mlsdc_status sdc_level_create_batched(sh_plan_t plan, const swe_param
     const size_t cnt = (size_t)members * L->ms();
     bool ok = cudaMalloc((void**)&L->Th, cnt * sizeof(double2)) == cudaSuccess &&
               cudaMalloc((void**)&L->d_recips, (size_t)n * (plan->R + 1) * sizeof(double2)) == cudaSuccess;
+    if (ok && (options & MLSDC_CORIOLIS_IMPLICIT)) {
+        ok = cudaMalloc((void**)&L->d_cfac, (size_t)(n - 1) * 2 * plan->nc * sizeof(CorFac)) == cudaSuccess;
+        if (ok && cor_smem_limits(plan->R) != MLSDC_OK) {
+            sdc_level_destroy(L);
+            return MLSDC_ERR_CUDA;
+        }
+    }
     for (int b = 0; b < 2 && ok; ++b) {
         ok = ok && cudaMalloc((void**)&L->FI[b], cnt * sizeof(double2)) == cudaSuccess;
         ok = ok && cudaMalloc((void**)&L->FE[b], cnt * sizeof(double2)) == cudaSuccess;
@@ -555,14 +570,20 @@ extern "C" mlsdc_status sdc_level_create_batched(sh_plan_t plan, const swe_param
     return MLSDC_OK;
 }
 
+extern "C" mlsdc_status sdc_level_create_batched(sh_plan_t plan, const swe_params* prm, int n_nodes, int members,
+                                                 sdc_level_t* out) {
+    return sdc_level_create_ex(plan, prm, n_nodes, members, 0, out);
+}
+
 extern "C" mlsdc_status sdc_level_create(sh_plan_t plan, const swe_params* prm, int n_nodes, sdc_level_t* out) {
-    return sdc_level_create_batched(plan, prm, n_nodes, 1, out);
+    return sdc_level_create_ex(plan, prm, n_nodes, 1, 0, out);
 }
 
 extern "C" mlsdc_status sdc_level_destroy(sdc_level_t L) {
     if (!L) return MLSDC_ERR_INVALID;
     cudaFree(L->Th);
     cudaFree(L->d_recips);
+    cudaFree(L->d_cfac);
     for (int b = 0; b < 2; ++b) {
         cudaFree(L->FI[b]);
         cudaFree(L->FE[b]);
@@ -608,6 +629,7 @@ extern "C" mlsdc_status sdc_step(sdc_level_t L, double* state, double dt, int n_
 extern "C" mlsdc_status mlsdc_create(sdc_level_t fine, sdc_level_t coarse, mlsdc_t* out) {
     if (!fine || !coarse || !out) return MLSDC_ERR_INVALID;
     if (coarse->plan->R > fine->plan->R || coarse->members != fine->members) return MLSDC_ERR_INVALID;
+    if (coarse->options != fine->options) return MLSDC_ERR_INVALID;  // one splitting on both levels
     mlsdc_t ml = new mlsdc_s();
     ml->f = fine;
     ml->c = coarse;
@@ -817,8 +839,8 @@ mlsdc_status run_ops(mlsdc_t ml, const std::vector<Op>& ops, cudaStream_t st, in
                     MLSDC_CUDA(cudaMemcpy2DAsync(tape + o.tape_off, w, o.p[0], o.L->ms() * sizeof(double2), w,
                                                  (size_t)o.L->members, cudaMemcpyDeviceToDevice, st));
                 }
-                if (fuse_node && o.nodes == 0 && oi + 1 < ops.size() && ops[oi + 1].k == OpK::Node &&
-                    ops[oi + 1].L == o.L) {
+                if (fuse_node && o.nodes == 0 && !o.L->options && oi + 1 < ops.size() &&
+                    ops[oi + 1].k == OpK::Node && ops[oi + 1].L == o.L) {
                     // the next node's update runs in the analysis epilogue, per
                     // coefficient, right after F_E there (same arithmetic as k_sweep_node)
                     const Op& n = ops[oi + 1];

@@ -74,6 +74,23 @@ struct Op {
 
 inline Phys phys_of(const swe_params& p) { return Phys{1.0 / (p.a * p.a), p.phibar, p.nu}; }
 
+// One element of a factored Coriolis chain (coriolis_implicit.cu): the
+// Thomas elimination's multiplier l, the pivot's reciprocal iw and the
+// scaled super-diagonal u = c iw, and 1/(1 - alpha nu L_n) of its degree.
+struct CorFac {
+    double2 l, iw, u;
+    double ic, pad;
+};
+
+// The implicit-Coriolis splitting (coriolis_implicit.cu).  Levels created
+// with MLSDC_CORIOLIS_IMPLICIT evaluate F_E with Omega = 0 and F_I with the
+// Coriolis terms; their node updates solve the coupled system per m.
+mlsdc_status cor_smem_limits(int R);  // once per level, outside any graph capture
+mlsdc_status cor_factor_launch(sdc_level_t L, double dt, cudaStream_t st);
+mlsdc_status cor_fi_launch(sdc_level_t L, const double2* x, double2* FI, int batch, size_t ms, cudaStream_t st);
+mlsdc_status cor_node_launch(sdc_level_t L, const NodeRow& row_dt, double2* Th, const double2* FIo,
+                             const double2* FEo, double2* FIn, double2* FEn, const double2* tau, cudaStream_t st);
+
 // Whether node updates are fused into the preceding F_E analysis kernel (off
 // unless the environment sets MLSDC_FUSE_NODE=1).
 bool node_fusion_enabled();
@@ -88,6 +105,8 @@ inline int grid_for(int n) {
 struct sdc_level_s {
     sh_plan_t plan;
     swe_params prm;
+    swe_params prm_fe;  // the parameters F_E is evaluated with (Omega = 0 with implicit Coriolis)
+    int options = 0;    // MLSDC_CORIOLIS_IMPLICIT
     int n;        // nodes
     int members;  // ensemble members advanced together
     std::vector<double> t, Q, QE, QI;
@@ -95,6 +114,7 @@ struct sdc_level_s {
     double2* FI[2] = {nullptr, nullptr};
     double2* FE[2] = {nullptr, nullptr};
     double2* d_recips = nullptr;  // [n][R+1] solve reciprocals of the node updates (k_solve_coefs)
+    mlsdc::CorFac* d_cfac = nullptr;  // [n-1][2][nc] factored Coriolis chains (implicit Coriolis only)
     int cur = 0;
     int64_t launches = 0;
     size_t node() const { return (size_t)3 * plan->nc; }

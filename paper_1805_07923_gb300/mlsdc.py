@@ -39,6 +39,9 @@ _SIGS = {
     "sh_plan_batched": ([_I, _I, _I, _I, _I, ctypes.POINTER(_VP)], _I),
     "swe_explicit_rhs_batched": ([_VP, ctypes.POINTER(SweParams), _DP, _DP, _I, _VP], _I),
     "sdc_level_create_batched": ([_VP, ctypes.POINTER(SweParams), _I, _I, ctypes.POINTER(_VP)], _I),
+    "sdc_level_create_ex": ([_VP, ctypes.POINTER(SweParams), _I, _I, _I, ctypes.POINTER(_VP)], _I),
+    "swe_implicit_rhs_ex": ([_VP, ctypes.POINTER(SweParams), _DP, _DP, _I, _VP], _I),
+    "swe_implicit_solve_ex": ([_VP, ctypes.POINTER(SweParams), _D, _DP, _DP, _I, _VP], _I),
     "mlsdc_ensemble_create": ([ctypes.POINTER(_VP), _I, ctypes.POINTER(_VP)], _I),
     "mlsdc_ensemble_destroy": ([_VP], _I),
     "mlsdc_ensemble_step": ([_VP, ctypes.POINTER(_VP), _D, _I, _I, _I, _VP], _I),
@@ -256,26 +259,38 @@ def swe_explicit_rhs_batched(plan: Plan, prm: SweParams, states: torch.Tensor, F
                                           _stream(stream)), "swe_explicit_rhs_batched")
 
 
-def swe_implicit_rhs(plan: Plan, prm: SweParams, state: torch.Tensor, FI: torch.Tensor, stream=None):
-    _check(lib().swe_implicit_rhs(plan.h, ctypes.byref(prm), _ptr(state, 6 * plan.nc), _ptr(FI, 6 * plan.nc),
-                                  _stream(stream)), "swe_implicit_rhs")
+# option bit of the splitting (include/mlsdc_sh.h): the Coriolis terms in F_I
+CORIOLIS_IMPLICIT = 1
 
 
-def swe_implicit_solve(plan: Plan, prm: SweParams, alpha: float, b: torch.Tensor, x: torch.Tensor, stream=None):
-    _check(lib().swe_implicit_solve(plan.h, ctypes.byref(prm), float(alpha), _ptr(b, 6 * plan.nc),
-                                    _ptr(x, 6 * plan.nc), _stream(stream)), "swe_implicit_solve")
+def swe_implicit_rhs(plan: Plan, prm: SweParams, state: torch.Tensor, FI: torch.Tensor, stream=None,
+                     coriolis_implicit: bool = False):
+    _check(lib().swe_implicit_rhs_ex(plan.h, ctypes.byref(prm), _ptr(state, 6 * plan.nc), _ptr(FI, 6 * plan.nc),
+                                     CORIOLIS_IMPLICIT if coriolis_implicit else 0, _stream(stream)),
+           "swe_implicit_rhs_ex")
+
+
+def swe_implicit_solve(plan: Plan, prm: SweParams, alpha: float, b: torch.Tensor, x: torch.Tensor, stream=None,
+                       coriolis_implicit: bool = False):
+    _check(lib().swe_implicit_solve_ex(plan.h, ctypes.byref(prm), float(alpha), _ptr(b, 6 * plan.nc),
+                                       _ptr(x, 6 * plan.nc), CORIOLIS_IMPLICIT if coriolis_implicit else 0,
+                                       _stream(stream)), "swe_implicit_solve_ex")
 
 
 class Level:
-    """sdc_level: a plan, the physics and n Gauss-Lobatto nodes."""
+    """sdc_level: a plan, the physics and n Gauss-Lobatto nodes (with
+    coriolis_implicit: the splitting with the Coriolis terms in F_I)."""
 
-    def __init__(self, plan: Plan, n_nodes: int, prm: SweParams | None = None, members: int = 1):
+    def __init__(self, plan: Plan, n_nodes: int, prm: SweParams | None = None, members: int = 1,
+                 coriolis_implicit: bool = False):
         self.plan = plan
         self.prm = prm if prm is not None else swe_params()
         h = ctypes.c_void_p()
-        _check(lib().sdc_level_create_batched(plan.h, ctypes.byref(self.prm), n_nodes, int(members), ctypes.byref(h)),
-               "sdc_level_create_batched")
+        opts = CORIOLIS_IMPLICIT if coriolis_implicit else 0
+        _check(lib().sdc_level_create_ex(plan.h, ctypes.byref(self.prm), n_nodes, int(members), opts, ctypes.byref(h)),
+               "sdc_level_create_ex")
         self.h, self.n, self.members = h, n_nodes, members
+        self.coriolis_implicit = bool(coriolis_implicit)
 
     def close(self):
         if self.h:
