@@ -338,6 +338,14 @@ mlsdc_status mlsdc_profile_rhs(sh_plan_t plan, const swe_params* prm, const doub
 /* The same for a batch of `members` states ([members][3][N_c]) per launch. */
 mlsdc_status mlsdc_profile_rhs_batched(sh_plan_t plan, const swe_params* prm, const double* states, double* FE,
                                        int members, int reps, float* ms_host, void* stream);
+/* mlsdc_profile_node: device time of each node update of a level (the
+ * update, implicit solve and F_I of node m + 1, Sec. 4.2 and Sec. 4.4; with
+ * MLSDC_CORIOLIS_IMPLICIT the coupled per-wavenumber solve), on the level's
+ * own node arrays as the last sweep left them: ms_out[m], m = 0..n_nodes-2,
+ * is the mean of `reps` back-to-back launches timed with CUDA events on
+ * `stream`.  Overwrites nodes 1..M of the level's current arrays (no step's
+ * result lives there).  Synchronises the stream. */
+mlsdc_status mlsdc_profile_node(sdc_level_t lev, double dt, int reps, float* ms_out, void* stream);
 
 /* ---------------------------------------------------------------------------
  * Adjoint (reverse mode) of the MLSDC time step with respect to its initial

@@ -25,7 +25,8 @@
 
 namespace mlsdc {
 
-constexpr int kCorThreads = 128;  // per wavenumber: warps 0 and 1 solve the two chains
+constexpr int kCorThreads = 256;      // standalone solve and F_I: per wavenumber, warps 0 and 1 solve the chains
+constexpr int kCorNodeThreads = 128;  // node update: per (wavenumber, chain), warp 0 solves
 
 __device__ __forceinline__ double2 zmul(double2 a, double2 b) {
     return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
@@ -85,6 +86,54 @@ __device__ __forceinline__ void warp_recurrence(int n, int lane, PQ pq, Put put)
     }
 }
 
+// The same recurrence over all warps of the CTA (blockDim.x threads, a
+// multiple of 32): thread t takes positions [t s, t s + s) of the recurrence
+// order (k ascending for Fwd, descending otherwise), s = ceil(n / blockDim.x);
+// each warp scans its lanes' maps, warp totals meet in shared memory
+// (wsum[2 * warps]), and every thread then runs its segment from its carry.
+// pq(k, p, q) is called once per k (the first pass keeps p in pbuf[k]);
+// called by every thread of the CTA (it synchronises).
+template <bool Fwd, class PQ, class Put>
+__device__ __forceinline__ void block_recurrence(int n, PQ pq, Put put, double2* pbuf, double2* wsum) {
+    const int T = blockDim.x, t = threadIdx.x, lane = t & 31, warp = t >> 5, nw = T >> 5;
+    const int s = (n + T - 1) / T;
+    const int j0 = min(n, t * s), j1 = min(n, j0 + s);
+    double2 A = make_double2(1.0, 0.0), B = make_double2(0.0, 0.0);
+    for (int j = j0; j < j1; ++j) {
+        const int k = Fwd ? j : n - 1 - j;
+        double2 p, q;
+        pq(k, p, q);
+        pbuf[k] = p;
+        B = zfma(q, B, p);
+        A = zmul(q, A);
+    }
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const double2 A1 = zshfl_up(A, d), B1 = zshfl_up(B, d);
+        if (lane >= d) {
+            B = zfma(A, B1, B);
+            A = zmul(A, A1);
+        }
+    }
+    if (lane == 31) {
+        wsum[warp] = A;
+        wsum[nw + warp] = B;
+    }
+    __syncthreads();
+    double2 z = make_double2(0.0, 0.0);  // the value before this warp's first position
+    for (int w = 0; w < warp; ++w) z = zfma(wsum[w], z, wsum[nw + w]);
+    double2 Ae = zshfl_up(A, 1), Be = zshfl_up(B, 1);
+    if (lane > 0) z = zfma(Ae, z, Be);
+    for (int j = j0; j < j1; ++j) {
+        const int k = Fwd ? j : n - 1 - j;
+        double2 p, q;
+        pq(k, p, q);
+        z = zfma(q, z, pbuf[k]);
+        put(k, z);
+    }
+    __syncthreads();
+}
+
 // Factor the chains of every node update of a level at step size dt (or of
 // one solve: nodes = 1, dt = 1, qd.v[0] = alpha).  fac[(i 2 + c) nc + off + k]
 // is element k of chain c of wavenumber m (offset off) for node update i;
@@ -126,7 +175,7 @@ __global__ void k_cor_factor(CorFac* __restrict__ fac, const double* __restrict_
         e.iw = iw;
         e.u = make_double2(sup * iw.x, sup * iw.y);
         e.ic = ic;
-        e.pad = 0.0;
+        e.aLc = alpha * L * ic;
         F[k] = e;
         iw_prev = iw;
         sup_prev = sup;
@@ -135,16 +184,17 @@ __global__ void k_cor_factor(CorFac* __restrict__ fac, const double* __restrict_
 
 // Solve the two chains of wavenumber m (nm = R + 1 - m unknowns each) from
 // the right-hand sides sb[f][k] (f = 0 Phi', 1 zeta, 2 delta; row stride ld)
-// into sx[0][k] = zeta_{m+k}, sx[1][k] = delta_{m+k}.  F0 points at element
-// (chain 0, k = 0) of this node update's factors, chain 1 is nc further.
-// Warps 0 and 1 of the CTA take chains 0 and 1; the caller synchronises.
-__device__ __forceinline__ void cor_solve_chains(const double2* sb, double2* sx, int ld, const CorFac* F0, int nc,
-                                                 int m, double alpha, const Phys& ph) {
+// into sx[0][k] = zeta_{m+k}, sx[1][k] = delta_{m+k}.  sf holds this node
+// update's factors of chain 0 (sf[k]) and chain 1 (sf[ld + k]) in shared
+// memory.  Warps 0 and 1 of the CTA take chains 0 and 1; the caller
+// synchronises.
+__device__ __forceinline__ void cor_solve_chains(const double2* sb, double2* sx, int ld, const CorFac* sf, int m,
+                                                 double alpha, const Phys& ph) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (warp > 1) return;
     const int c = warp;
     const int nm = ld - m;  // ld = R + 1
-    const CorFac* F = F0 + (size_t)c * nc;
+    const CorFac* F = sf + c * ld;
     // forward substitution y_k = r_k - l_k y_{k-1}; y is kept where x goes
     warp_recurrence<true>(
         nm, lane,
@@ -170,69 +220,116 @@ __device__ __forceinline__ void cor_solve_chains(const double2* sb, double2* sx,
         [&](int k, double2 x) { sx[(((k + c) & 1) ? ld : 0) + k] = x; });
 }
 
+// Copy this wavenumber's factors of both chains (global fac: chain 0 at
+// F0[k], chain 1 at F0[nc + k]) into shared memory sf[c ld + k], 16 bytes per
+// thread and step.
+__device__ __forceinline__ void cor_stage_factors(CorFac* sf, const CorFac* __restrict__ F0, int nc, int ld, int nm) {
+    constexpr int kV = sizeof(CorFac) / sizeof(double2);
+    for (int t = threadIdx.x; t < 2 * nm * kV; t += blockDim.x) {
+        const int c = t / (nm * kV), r = t - c * nm * kV;
+        reinterpret_cast<double2*>(sf + c * ld)[r] = reinterpret_cast<const double2*>(F0 + (size_t)c * nc)[r];
+    }
+}
+
 // Phi'_n from the solved delta_n.
 __device__ __forceinline__ double2 cor_phi(double2 bp, double2 d, double alpha, const Phys& ph, double ic) {
     return make_double2((bp.x - alpha * ph.phibar * d.x) * ic, (bp.y - alpha * ph.phibar * d.y) * ic);
 }
 
-// F_I = L_G + L_F at the coefficients of wavenumber m from the solved values
-// in shared memory (sp = Phi', sx = zeta, delta as cor_solve_chains leaves them).
-__device__ __forceinline__ void cor_fi_coef(const double2* sx, int ld, const double* cor, int off, int m, int k,
-                                            double2 p, const Phys& ph, double two_omega, double2& fp, double2& fz,
-                                            double2& fd) {
-    const int nm = ld - m, n = m + k;
-    const double L = -n * (n + 1.0) * ph.inv_a2;
-    const double2 zero = make_double2(0.0, 0.0);
-    const double2 zk = sx[k], dk = sx[ld + k];
-    implicit_rhs_coef(L, ph, p, zk, dk, fp, fz, fd);
-    const double2 zl = k > 0 ? sx[k - 1] : zero, dl = k > 0 ? sx[ld + k - 1] : zero;
-    const double2 zu = k + 1 < nm ? sx[k + 1] : zero, du = k + 1 < nm ? sx[ld + k + 1] : zero;
-    coriolis_terms(cor + 4 * (size_t)(off + k), zl, zk, zu, dl, dk, du, two_omega, fz, fd);
-}
-
 // The node update of an implicit-Coriolis level: right-hand sides b of node
 // row.m + 1 (node_rhs, Eq. update_equation_sdcq_discrete_form), the coupled
-// solve, and F_I at the new node.  One CTA per (wavenumber m, member).
-__global__ void __launch_bounds__(kCorThreads) k_sweep_node_cor(double2* Th, const double2* __restrict__ FIo,
-                                                              const double2* __restrict__ FEo, double2* FIn,
-                                                              double2* FEn, const double2* __restrict__ tau,
-                                                              const CorFac* __restrict__ fac,
-                                                              const double* __restrict__ cor, int R, int nc,
-                                                              NodeRow row, Phys ph, double two_omega, size_t ms) {
+// solve, and F_I at the new node.  One CTA per (wavenumber m, chain c,
+// member): chain c holds zeta_{m+k} for k + c even and delta_{m+k} for k + c
+// odd, and every value the outputs of its elements need is in the chain
+// (F_I of zeta_n uses delta_{n-1}, delta_{n+1}; F_I of delta_n and Phi'_n use
+// zeta_{n-1}, zeta_{n+1} and Phi'_n, which comes from delta_n), so the two
+// chains of a wavenumber run on different SMs without exchanging anything.
+__global__ void __launch_bounds__(kCorNodeThreads) k_sweep_node_cor(double2* Th, const double2* __restrict__ FIo,
+                                                                  const double2* __restrict__ FEo, double2* FIn,
+                                                                  double2* FEn, const double2* __restrict__ tau,
+                                                                  const CorFac* __restrict__ fac,
+                                                                  const double* __restrict__ cor, int R, int nc,
+                                                                  NodeRow row, Phys ph, double two_omega, size_t ms) {
     extern __shared__ double2 cor_sm[];
     pdl_wait();
     pdl_launch();
-    const size_t mo = blockIdx.y * ms;
+    const size_t mo = blockIdx.z * ms;
     Th += mo;
     FIo += mo;
     FEo += mo;
     FIn += mo;
     FEn += mo;
     if (tau) tau += mo;
-    const int m = blockIdx.x, ld = R + 1, nm = ld - m, off = moff(R, m);
+    const int m = blockIdx.x, c = blockIdx.y, ld = R + 1, nm = ld - m, off = moff(R, m);
     const size_t node = (size_t)3 * nc;
-    double2* sb = cor_sm;           // [3][R+1]
-    double2* sx = cor_sm + 3 * ld;  // [2][R+1]
-    for (int t = threadIdx.x; t < 3 * nm; t += blockDim.x) {
-        const int f = t / nm, k = t - f * nm;
-        sb[f * ld + k] = node_rhs(Th, FIo, FEo, FIn, FEn, tau, node, (size_t)f * nc + off + k, row);
+    const double alpha = row.qimm;
+    double2* sr = cor_sm;                                     // [R+1] b_zeta or b_delta of element k
+    double2* sp = cor_sm + ld;                                // [R+1] b_Phi at the delta elements
+    double2* sx = cor_sm + 2 * ld;                            // [R+1] the chain's solution
+    double2* pb = cor_sm + 3 * ld;                            // [R+1] the recurrences' p_k
+    double2* ws = cor_sm + 4 * ld;                            // [2 warps] warp totals
+    CorFac* sf = reinterpret_cast<CorFac*>(cor_sm + 4 * ld + 2 * (kCorNodeThreads / 32));  // [R+1] factors
+    {
+        constexpr int kV = sizeof(CorFac) / sizeof(double2);
+        const double2* src = reinterpret_cast<const double2*>(fac + (size_t)c * nc + off);
+        for (int t = threadIdx.x; t < nm * kV; t += blockDim.x) reinterpret_cast<double2*>(sf)[t] = src[t];
+    }
+    for (int t = threadIdx.x; t < 2 * nm; t += blockDim.x) {
+        const int k = t >> 1, second = t & 1;
+        const bool zeta = ((k + c) & 1) == 0;
+        if (zeta && second) continue;
+        const int f = zeta ? 1 : (second ? 0 : 2);
+        const double2 b = node_rhs(Th, FIo, FEo, FIn, FEn, tau, node, (size_t)f * nc + off + k, row);
+        (second ? sp : sr)[k] = b;
     }
     __syncthreads();
-    const CorFac* F0 = fac + off;
-    cor_solve_chains(sb, sx, ld, F0, nc, m, row.qimm, ph);
-    __syncthreads();
+    // forward substitution y_k = r_k - l_k y_{k-1} (the delta rows with Phi'
+    // eliminated: r = b_delta - alpha L_n b_Phi / c_n), then back substitution
+    // x_k = iw_k y_k - u_k x_{k+1}; y and x are kept in sx
+    block_recurrence<true>(
+        nm,
+        [&](int k, double2& p, double2& q) {
+            if (((k + c) & 1) == 0) {
+                p = sr[k];
+            } else {
+                const double aL = sf[k].aLc;
+                p = make_double2(fma(-aL, sp[k].x, sr[k].x), fma(-aL, sp[k].y, sr[k].y));
+            }
+            q = zneg(sf[k].l);
+        },
+        [&](int k, double2 y) { sx[k] = y; }, pb, ws);
+    block_recurrence<false>(
+        nm,
+        [&](int k, double2& p, double2& q) {
+            p = zmul(sf[k].iw, sx[k]);
+            q = zneg(sf[k].u);
+        },
+        [&](int k, double2 x) { sx[k] = x; }, pb, ws);
     const size_t om = (size_t)(row.m + 1) * node + off;
+    const double2 zero = make_double2(0.0, 0.0);
     for (int k = threadIdx.x; k < nm; k += blockDim.x) {
-        const double2 p = cor_phi(sb[k], sx[ld + k], row.qimm, ph, F0[k].ic);
-        double2 fp, fz, fd;
-        cor_fi_coef(sx, ld, cor, off, m, k, p, ph, two_omega, fp, fz, fd);
-        Th[om + k] = p;
-        Th[om + nc + k] = sx[k];
-        Th[om + 2 * nc + k] = sx[ld + k];
-        FIn[om + k] = fp;
-        FIn[om + nc + k] = fz;
-        FIn[om + 2 * nc + k] = fd;
-        if (row.m == 0) {
+        const int n = m + k;
+        const double L = -n * (n + 1.0) * ph.inv_a2;
+        const double nl = ph.nu * L;
+        const double* cf = cor + 4 * (size_t)(off + k);
+        const double2 v = sx[k];
+        const double2 lo = k > 0 ? sx[k - 1] : zero, hi = k + 1 < nm ? sx[k + 1] : zero;
+        if (((k + c) & 1) == 0) {  // zeta_n: nu L zeta + L_F (delta_{n-1}, zeta_n, delta_{n+1})
+            double2 fz = make_double2(nl * v.x, nl * v.y);
+            coriolis_zeta_row(cf, lo, v, hi, two_omega, fz);
+            Th[om + nc + k] = v;
+            FIn[om + nc + k] = fz;
+        } else {  // delta_n and Phi'_n: L_G, and L_F (zeta_{n-1}, delta_n, zeta_{n+1})
+            const double2 p = cor_phi(sp[k], v, alpha, ph, sf[k].ic);
+            const double2 fp = make_double2(-ph.phibar * v.x + nl * p.x, -ph.phibar * v.y + nl * p.y);
+            double2 fd = make_double2(-L * p.x + nl * v.x, -L * p.y + nl * v.y);
+            coriolis_delta_row(cf, lo, v, hi, two_omega, fd);
+            Th[om + k] = p;
+            Th[om + 2 * nc + k] = v;
+            FIn[om + k] = fp;
+            FIn[om + 2 * nc + k] = fd;
+        }
+        if (row.m == 0 && c == 0) {
             for (int f = 0; f < 3; ++f) {
                 const size_t o = (size_t)f * nc + off + k;
                 FIn[o] = FIo[o];
@@ -254,16 +351,17 @@ __global__ void __launch_bounds__(kCorThreads) k_cor_solve(const double2* b, dou
     const int m = blockIdx.x, ld = R + 1, nm = ld - m, off = moff(R, m);
     double2* sb = cor_sm;
     double2* sx = cor_sm + 3 * ld;
+    CorFac* sf = reinterpret_cast<CorFac*>(cor_sm + 5 * ld);
+    cor_stage_factors(sf, fac + off, nc, ld, nm);
     for (int t = threadIdx.x; t < 3 * nm; t += blockDim.x) {
         const int f = t / nm, k = t - f * nm;
         sb[f * ld + k] = b[(size_t)f * nc + off + k];
     }
     __syncthreads();
-    const CorFac* F0 = fac + off;
-    cor_solve_chains(sb, sx, ld, F0, nc, m, alpha, ph);
+    cor_solve_chains(sb, sx, ld, sf, m, alpha, ph);
     __syncthreads();
     for (int k = threadIdx.x; k < nm; k += blockDim.x) {
-        x[off + k] = cor_phi(sb[k], sx[ld + k], alpha, ph, F0[k].ic);
+        x[off + k] = cor_phi(sb[k], sx[ld + k], alpha, ph, sf[k].ic);
         x[nc + off + k] = sx[k];
         x[2 * nc + off + k] = sx[ld + k];
     }
@@ -293,23 +391,42 @@ __global__ void __launch_bounds__(kCorThreads) k_implicit_rhs_cor(const double2*
     }
 }
 
-static size_t cor_smem(int R) { return (size_t)5 * (R + 1) * sizeof(double2); }
+// standalone solve: right-hand sides [3][R+1], solution [2][R+1], factors [2][R+1]
+static size_t cor_smem(int R) { return (size_t)5 * (R + 1) * sizeof(double2) + (size_t)2 * (R + 1) * sizeof(CorFac); }
+// node update, one chain: r, b_Phi, solution, p [R+1] each, warp totals, factors [R+1]
+static size_t cor_node_smem(int R) {
+    return (size_t)(4 * (R + 1) + 2 * (kCorNodeThreads / 32)) * sizeof(double2) + (size_t)(R + 1) * sizeof(CorFac);
+}
 
 mlsdc_status cor_smem_limits(int R) {
-    mlsdc_status s = raise_smem_limit((const void*)k_sweep_node_cor, cor_smem(R));
+    mlsdc_status s = raise_smem_limit((const void*)k_sweep_node_cor, cor_node_smem(R));
     if (s == MLSDC_OK) s = raise_smem_limit((const void*)k_cor_solve, cor_smem(R));
     return s;
 }
 
-mlsdc_status cor_factor_launch(sdc_level_t L, double dt, cudaStream_t st) {
+mlsdc_status cor_factors(sdc_level_t L, double dt, cudaStream_t st, const CorFac** out) {
+    for (const auto& e : L->cfac)
+        if (e.first == dt) {
+            *out = e.second;
+            return MLSDC_OK;
+        }
+    CorFac* buf = nullptr;
+    MLSDC_CUDA(cudaMalloc((void**)&buf, (size_t)(L->n - 1) * 2 * L->plan->nc * sizeof(CorFac)));
+    L->cfac.emplace_back(dt, buf);
     QiDiagC qd{};
     for (int m = 0; m + 1 < L->n; ++m) qd.v[m] = L->QI[(m + 1) * L->n + m + 1];
     const int R = L->plan->R, threads = (L->n - 1) * (R + 1) * 2;
-    MLSDC_LAUNCH("k_cor_factor", launch_k(k_cor_factor, dim3((threads + 127) / 128), dim3(128), 0, st, L->d_cfac,
+    MLSDC_LAUNCH("k_cor_factor", launch_k(k_cor_factor, dim3((threads + 127) / 128), dim3(128), 0, st, buf,
                                           (const double*)L->plan->d_cor, R, L->plan->nc, L->n - 1, qd, dt,
                                           phys_of(L->prm), 2.0 * L->prm.omega));
     L->launches++;
+    *out = buf;
     return MLSDC_OK;
+}
+
+mlsdc_status cor_factor_launch(sdc_level_t L, double dt, cudaStream_t st) {
+    const CorFac* f = nullptr;
+    return cor_factors(L, dt, st, &f);
 }
 
 mlsdc_status cor_fi_launch(sdc_level_t L, const double2* x, double2* FI, int batch, size_t ms, cudaStream_t st) {
@@ -321,13 +438,16 @@ mlsdc_status cor_fi_launch(sdc_level_t L, const double2* x, double2* FI, int bat
     return MLSDC_OK;
 }
 
-mlsdc_status cor_node_launch(sdc_level_t L, const NodeRow& row_dt, double2* Th, const double2* FIo,
+mlsdc_status cor_node_launch(sdc_level_t L, double dt, const NodeRow& row_dt, double2* Th, const double2* FIo,
                              const double2* FEo, double2* FIn, double2* FEn, const double2* tau, cudaStream_t st) {
     const int R = L->plan->R, nc = L->plan->nc;  // shared-memory limit raised at level creation
+    const CorFac* fac = nullptr;
+    mlsdc_status s = cor_factors(L, dt, st, &fac);
+    if (s != MLSDC_OK) return s;
     MLSDC_LAUNCH("k_sweep_node_cor",
-                 launch_k(k_sweep_node_cor, dim3(R + 1, L->members), dim3(kCorThreads), cor_smem(R), st, Th, FIo, FEo,
-                          FIn, FEn, tau, (const CorFac*)(L->d_cfac + (size_t)row_dt.m * 2 * nc),
-                          (const double*)L->plan->d_cor, R, nc, row_dt, phys_of(L->prm), 2.0 * L->prm.omega, L->ms()));
+                 launch_k(k_sweep_node_cor, dim3(R + 1, 2, L->members), dim3(kCorNodeThreads), cor_node_smem(R), st,
+                          Th, FIo, FEo, FIn, FEn, tau, fac + (size_t)row_dt.m * 2 * nc, (const double*)L->plan->d_cor,
+                          R, nc, row_dt, phys_of(L->prm), 2.0 * L->prm.omega, L->ms()));
     L->launches++;
     return MLSDC_OK;
 }

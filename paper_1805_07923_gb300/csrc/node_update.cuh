@@ -126,17 +126,29 @@ __device__ __forceinline__ void node_solve_field(int f, double L, double alpha, 
 // (coriolis_implicit.cu) adds it to F_I instead.  Adds dzeta to f1 and ddelta to f2.
 // coriolis_terms takes the neighbours' values (zero outside m <= n <= R);
 // coriolis_add reads them from a state [3][nc] in global memory.
-__device__ __forceinline__ void coriolis_terms(const double* __restrict__ cf, double2 zl, double2 zk, double2 zu,
-                                               double2 dl, double2 dk, double2 du, double two_omega, double2& f1,
-                                               double2& f2) {
+// The vorticity row alone (needs delta_{n-1}, zeta_n, delta_{n+1}) and the
+// divergence row alone (zeta_{n-1}, delta_n, zeta_{n+1}).
+__device__ __forceinline__ void coriolis_zeta_row(const double* __restrict__ cf, double2 dl, double2 zk, double2 du,
+                                                  double two_omega, double2& f1) {
     const double2 ab = *reinterpret_cast<const double2*>(cf);
     const double al = ab.x, be = ab.y, ga = cf[2];
     const double ux = fma(al, dl.x, fma(be, du.x, -ga * zk.y)), uy = fma(al, dl.y, fma(be, du.y, ga * zk.x));
-    const double vx = fma(al, zl.x, fma(be, zu.x, ga * dk.y)), vy = fma(al, zl.y, fma(be, zu.y, -ga * dk.x));
     f1.x = fma(-two_omega, ux, f1.x);
     f1.y = fma(-two_omega, uy, f1.y);
+}
+__device__ __forceinline__ void coriolis_delta_row(const double* __restrict__ cf, double2 zl, double2 dk, double2 zu,
+                                                   double two_omega, double2& f2) {
+    const double2 ab = *reinterpret_cast<const double2*>(cf);
+    const double al = ab.x, be = ab.y, ga = cf[2];
+    const double vx = fma(al, zl.x, fma(be, zu.x, ga * dk.y)), vy = fma(al, zl.y, fma(be, zu.y, -ga * dk.x));
     f2.x = fma(two_omega, vx, f2.x);
     f2.y = fma(two_omega, vy, f2.y);
+}
+__device__ __forceinline__ void coriolis_terms(const double* __restrict__ cf, double2 zl, double2 zk, double2 zu,
+                                               double2 dl, double2 dk, double2 du, double two_omega, double2& f1,
+                                               double2& f2) {
+    coriolis_zeta_row(cf, dl, zk, du, two_omega, f1);
+    coriolis_delta_row(cf, zl, dk, zu, two_omega, f2);
 }
 
 __device__ inline void coriolis_add(const double2* __restrict__ state, const double* __restrict__ cor, int nc, int R,

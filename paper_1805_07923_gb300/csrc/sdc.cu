@@ -377,7 +377,8 @@ static NodeRow node_row(sdc_level_t L, int m) {
 static mlsdc_status launch_node(sdc_level_t L, double dt, const NodeRow& row, double2* Th, const double2* FIo,
                                 const double2* FEo, double2* FIn, double2* FEn, const double2* tau,
                                 cudaStream_t st) {
-    if (L->options & MLSDC_CORIOLIS_IMPLICIT) return cor_node_launch(L, dt_scaled(row, dt), Th, FIo, FEo, FIn, FEn, tau, st);
+    if (L->options & MLSDC_CORIOLIS_IMPLICIT)
+        return cor_node_launch(L, dt, dt_scaled(row, dt), Th, FIo, FEo, FIn, FEn, tau, st);
     const int nc = L->plan->nc;
     MLSDC_LAUNCH("k_sweep_node",
                  launch_k(k_sweep_node, dim3((nc + kNodeCoefs - 1) / kNodeCoefs, L->members), dim3(3 * kNodeCoefs),
@@ -550,12 +551,9 @@ extern "C" mlsdc_status sdc_level_create_ex(sh_plan_t plan, const swe_params* pr
     const size_t cnt = (size_t)members * L->ms();
     bool ok = cudaMalloc((void**)&L->Th, cnt * sizeof(double2)) == cudaSuccess &&
               cudaMalloc((void**)&L->d_recips, (size_t)n * (plan->R + 1) * sizeof(double2)) == cudaSuccess;
-    if (ok && (options & MLSDC_CORIOLIS_IMPLICIT)) {
-        ok = cudaMalloc((void**)&L->d_cfac, (size_t)(n - 1) * 2 * plan->nc * sizeof(CorFac)) == cudaSuccess;
-        if (ok && cor_smem_limits(plan->R) != MLSDC_OK) {
-            sdc_level_destroy(L);
-            return MLSDC_ERR_CUDA;
-        }
+    if (ok && (options & MLSDC_CORIOLIS_IMPLICIT) && cor_smem_limits(plan->R) != MLSDC_OK) {
+        sdc_level_destroy(L);
+        return MLSDC_ERR_CUDA;
     }
     for (int b = 0; b < 2 && ok; ++b) {
         ok = ok && cudaMalloc((void**)&L->FI[b], cnt * sizeof(double2)) == cudaSuccess;
@@ -583,7 +581,7 @@ extern "C" mlsdc_status sdc_level_destroy(sdc_level_t L) {
     if (!L) return MLSDC_ERR_INVALID;
     cudaFree(L->Th);
     cudaFree(L->d_recips);
-    cudaFree(L->d_cfac);
+    for (auto& e : L->cfac) cudaFree(e.second);
     for (int b = 0; b < 2; ++b) {
         cudaFree(L->FI[b]);
         cudaFree(L->FE[b]);
@@ -624,6 +622,23 @@ extern "C" mlsdc_status sdc_step(sdc_level_t L, double* state, double dt, int n_
         L->cur = 1 - c;
     }
     return copy_last_node(L, state, st);
+}
+
+extern "C" mlsdc_status mlsdc_profile_node(sdc_level_t L, double dt, int reps, float* ms_out, void* stream) {
+    if (!L || !ms_out || reps < 1 || !(dt > 0.0)) return MLSDC_ERR_INVALID;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int c = L->cur;
+    mlsdc_status s = launch_solve_coefs(L, dt, st);
+    // a node update reads Theta^0 and the old F arrays and writes node m + 1
+    // only, so the repeated launches all do the same work; timed as a graph
+    // of `reps` launches, as the step runs them
+    for (int m = 0; m < L->n - 1 && s == MLSDC_OK; ++m) {
+        const NodeRow row = node_row(L, m);
+        s = time_in_graph(st, reps, &ms_out[m], [&](cudaStream_t cs) {
+            return launch_node(L, dt, row, L->Th, L->FI[c], L->FE[c], L->FI[1 - c], L->FE[1 - c], nullptr, cs);
+        });
+    }
+    return s;
 }
 
 extern "C" mlsdc_status mlsdc_create(sdc_level_t fine, sdc_level_t coarse, mlsdc_t* out) {
@@ -918,6 +933,18 @@ mlsdc_status run_ops(mlsdc_t ml, const std::vector<Op>& ops, cudaStream_t st, in
     return MLSDC_OK;
 }
 
+// Work a step at dt needs done once, outside any graph capture: the
+// factored Coriolis chains of implicit-Coriolis levels.
+static mlsdc_status prepare_levels(mlsdc_t ml, double dt, cudaStream_t st) {
+    for (sdc_level_t L : {ml->f, ml->c})
+        if (L->options & MLSDC_CORIOLIS_IMPLICIT) {
+            const CorFac* f = nullptr;
+            mlsdc_status s = cor_factors(L, dt, st, &f);
+            if (s != MLSDC_OK) return s;
+        }
+    return MLSDC_OK;
+}
+
 static mlsdc_status mlsdc_enqueue(mlsdc_t ml, double* state, double dt, int n_iter, int n_c, cudaStream_t st) {
     std::vector<Op> ops;
     build_mlsdc_ops(ml, (double2*)state, dt, n_iter, n_c, ops);
@@ -954,6 +981,8 @@ extern "C" mlsdc_status mlsdc_step(mlsdc_t ml, double* state, double dt, int n_i
                                    int use_graph, void* stream) {
     if (!ml || !state || n_iter < 0 || n_coarse_sweeps < 0) return MLSDC_ERR_INVALID;
     cudaStream_t st = (cudaStream_t)stream;
+    mlsdc_status sp = prepare_levels(ml, dt, st);
+    if (sp != MLSDC_OK) return sp;
     if (!use_graph) return mlsdc_enqueue(ml, state, dt, n_iter, n_coarse_sweeps, st);
     auto key = std::make_tuple(state, dt, n_iter, n_coarse_sweeps);
     auto it = ml->graphs.find(key);
@@ -1050,6 +1079,10 @@ extern "C" mlsdc_status mlsdc_ensemble_step(mlsdc_ensemble_t e, double* const* s
     for (double* p : sv)
         if (!p) return MLSDC_ERR_INVALID;
     cudaStream_t st = (cudaStream_t)stream;
+    for (mlsdc_t ml : e->groups) {
+        mlsdc_status sp = prepare_levels(ml, dt, st);
+        if (sp != MLSDC_OK) return sp;
+    }
     if (!use_graph) return ensemble_enqueue(e, sv, dt, n_iter, n_coarse_sweeps, st);
     auto key = std::make_tuple(sv, dt, n_iter, n_coarse_sweeps);
     auto it = e->graphs.find(key);

@@ -76,19 +76,25 @@ inline Phys phys_of(const swe_params& p) { return Phys{1.0 / (p.a * p.a), p.phib
 
 // One element of a factored Coriolis chain (coriolis_implicit.cu): the
 // Thomas elimination's multiplier l, the pivot's reciprocal iw and the
-// scaled super-diagonal u = c iw, and 1/(1 - alpha nu L_n) of its degree.
+// scaled super-diagonal u = c iw; ic = 1/c_n with c_n = 1 - alpha nu L_n, and
+// aLc = alpha L_n / c_n (the factor of b_Phi in a delta row's right-hand side).
 struct CorFac {
     double2 l, iw, u;
-    double ic, pad;
+    double ic, aLc;
 };
 
 // The implicit-Coriolis splitting (coriolis_implicit.cu).  Levels created
 // with MLSDC_CORIOLIS_IMPLICIT evaluate F_E with Omega = 0 and F_I with the
 // Coriolis terms; their node updates solve the coupled system per m.
+// The factored chains depend only on the level and dt: a level keeps one
+// set per step size it has seen (cor_factors computes a new one on `st`;
+// the step entry points call it before any graph capture, so a captured step
+// only reads them).
 mlsdc_status cor_smem_limits(int R);  // once per level, outside any graph capture
+mlsdc_status cor_factors(sdc_level_t L, double dt, cudaStream_t st, const CorFac** out);
 mlsdc_status cor_factor_launch(sdc_level_t L, double dt, cudaStream_t st);
 mlsdc_status cor_fi_launch(sdc_level_t L, const double2* x, double2* FI, int batch, size_t ms, cudaStream_t st);
-mlsdc_status cor_node_launch(sdc_level_t L, const NodeRow& row_dt, double2* Th, const double2* FIo,
+mlsdc_status cor_node_launch(sdc_level_t L, double dt, const NodeRow& row_dt, double2* Th, const double2* FIo,
                              const double2* FEo, double2* FIn, double2* FEn, const double2* tau, cudaStream_t st);
 
 // Whether node updates are fused into the preceding F_E analysis kernel (off
@@ -114,7 +120,8 @@ struct sdc_level_s {
     double2* FI[2] = {nullptr, nullptr};
     double2* FE[2] = {nullptr, nullptr};
     double2* d_recips = nullptr;  // [n][R+1] solve reciprocals of the node updates (k_solve_coefs)
-    mlsdc::CorFac* d_cfac = nullptr;  // [n-1][2][nc] factored Coriolis chains (implicit Coriolis only)
+    // implicit Coriolis only: per step size dt, the factored chains [n-1][2][nc]
+    std::vector<std::pair<double, mlsdc::CorFac*>> cfac;
     int cur = 0;
     int64_t launches = 0;
     size_t node() const { return (size_t)3 * plan->nc; }

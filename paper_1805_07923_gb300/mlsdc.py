@@ -39,6 +39,7 @@ _SIGS = {
     "sh_plan_batched": ([_I, _I, _I, _I, _I, ctypes.POINTER(_VP)], _I),
     "swe_explicit_rhs_batched": ([_VP, ctypes.POINTER(SweParams), _DP, _DP, _I, _VP], _I),
     "sdc_level_create_batched": ([_VP, ctypes.POINTER(SweParams), _I, _I, ctypes.POINTER(_VP)], _I),
+    "mlsdc_profile_node": ([_VP, _D, _I, ctypes.POINTER(ctypes.c_float), _VP], _I),
     "sdc_level_create_ex": ([_VP, ctypes.POINTER(SweParams), _I, _I, _I, ctypes.POINTER(_VP)], _I),
     "swe_implicit_rhs_ex": ([_VP, ctypes.POINTER(SweParams), _DP, _DP, _I, _VP], _I),
     "swe_implicit_solve_ex": ([_VP, ctypes.POINTER(SweParams), _D, _DP, _DP, _I, _VP], _I),
@@ -310,6 +311,13 @@ class Level:
         args = [a.ctypes.data_as(ctypes.c_void_p) for a in (t, Q, QE, QI)]
         _check(lib().sdc_level_matrices(self.h, *args), "sdc_level_matrices")
         return t, Q.reshape(n, n), QE.reshape(n, n), QI.reshape(n, n)
+
+
+def mlsdc_profile_node(level: Level, dt: float, reps: int = 20, stream=None) -> list[float]:
+    """Device milliseconds of each node update m = 0..n-2 of the level."""
+    out = (ctypes.c_float * (level.n - 1))()
+    _check(lib().mlsdc_profile_node(level.h, float(dt), int(reps), out, _stream(stream)), "mlsdc_profile_node")
+    return list(out)
 
 
 def sdc_sweep(level: Level, dt: float, Theta, FI_old, FE_old, FI_new, FE_new, tau=None, stream=None):

@@ -9,6 +9,11 @@ the `reps` evaluations that follow run inside the NVTX range
 "mlsdc_profile", so a profiler can select exactly them, e.g.
 ncu --nvtx --nvtx-include "mlsdc_profile/" -k regex:k_tc_anal ...
 Prints the mean stage times measured with CUDA events.
+
+With --node, the node updates of one SDC level instead (update, implicit
+solve, F_I; --coriolis-implicit for the coupled per-wavenumber solve): one
+SDC step fills the level's arrays, then `reps` rounds of the node updates
+run inside the NVTX range, and the mean time of each is printed.
 """
 from __future__ import annotations
 
@@ -36,7 +41,13 @@ def main(argv=None):
                          "configuration (the synthesis keeps its own)")
     ap.add_argument("--kernels", default="auto", choices=["auto", "tc", "simt"],
                     help="tensor-core plans: the plan's choice, or both Legendre stages on tcgen05 / CUDA cores")
+    ap.add_argument("--node", action="store_true", help="the node updates of an SDC level instead of F_E")
+    ap.add_argument("--nodes", type=int, default=5, help="--node: Lobatto nodes of the level")
+    ap.add_argument("--coriolis-implicit", action="store_true", help="--node: the implicit-Coriolis splitting")
+    ap.add_argument("--dt", type=float, default=150.0)
     a = ap.parse_args(argv)
+    if a.node:
+        return node_main(a)
     plan = M.Plan(a.R, a.nlon, a.nlat, "fp64" if a.adjoint else a.precision, a.members)
     if a.kernels != "auto" and a.precision in ("tf32", "bf16x3") and not a.adjoint:
         plan.set_stage_kernels(a.kernels, a.kernels)
@@ -65,6 +76,23 @@ def main(argv=None):
                       "adjoint": a.adjoint, "stage_ms": ms, "stage_kernels_tc": plan.stage_kernels(a.members),
                       "tc_config": {"synthesis": plan.tc_config("synthesis"),
                                     "analysis": plan.tc_config("analysis")}}))
+
+
+def node_main(a):
+    plan = M.Plan(a.R, a.nlon, a.nlat, "fp64", a.members)
+    lev = M.Level(plan, a.nodes, members=a.members, coriolis_implicit=a.coriolis_implicit)
+    base = inputs.initial_state(a.R)
+    x = torch.from_numpy(np.stack([inputs.perturbed_member(base, a.R, a.R, k) for k in range(a.members)])).cuda()
+    if a.members == 1:
+        x = x[0].contiguous()
+    M.sdc_step(lev, x, a.dt, 1)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("mlsdc_profile")
+    ms = M.mlsdc_profile_node(lev, a.dt, reps=a.reps)
+    torch.cuda.nvtx.range_pop()
+    ms20 = M.mlsdc_profile_node(lev, a.dt, reps=20)
+    print(json.dumps({"R": a.R, "nodes": a.nodes, "members": a.members, "coriolis_implicit": a.coriolis_implicit,
+                      "node_ms": ms20}))
 
 
 if __name__ == "__main__":
