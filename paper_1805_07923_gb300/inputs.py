@@ -1,7 +1,9 @@
 """Seeded synthetic inputs shared by the CUDA path's tests/bench and the oracle.
 
 This module holds no arithmetic of the method: it only draws reproducible
-random spectral coefficients in the library's storage layout.
+random spectral coefficients in the library's storage layout, and evaluates
+the analytic Gaussian-dome initial condition at grid points the caller gives
+(each side then analyses that grid field with its own transform).
 
 Storage layout (the C-ABI layout): a spectral field of triangular truncation R
 holds N_c = (R+1)(R+2)/2 complex coefficients xi^m_n, 0 <= m <= n <= R, stored
@@ -110,3 +112,36 @@ def to_real(x: np.ndarray) -> np.ndarray:
 def from_real(x: np.ndarray) -> np.ndarray:
     """float64[..., 2N] interleaved -> complex128[..., N]."""
     return np.ascontiguousarray(x).view(np.complex128)
+
+
+# The Gaussian dome of the paper's unsteady test (Sec. 5, Eq. gaussian_bump):
+# u = v = 0 and h = h_bar + A exp(-alpha (d / a)^2), with d the straight-line
+# (chord) distance between the point and the centre (lambda_c, phi_c) =
+# (pi, pi/4) for points on the sphere of radius a, h_bar = 29400 m, A = 6000 m.
+# The paper does not give alpha; DOME_ALPHA is this library's choice.
+DOME_H_BAR = 29400.0
+DOME_A = 6000.0
+DOME_ALPHA = 10.0
+DOME_CENTRE = (np.pi, np.pi / 4.0)
+
+
+def dome_chord(lam: np.ndarray, mu: np.ndarray, centre=DOME_CENTRE) -> np.ndarray:
+    """d / a on the unit sphere for longitudes lam (radians) and mu = sin(phi),
+    broadcast against each other: sqrt(x^2 + y^2 + z^2) with x, y, z the
+    Cartesian differences to the centre."""
+    lc, pc = centre
+    cphi = np.sqrt(1.0 - mu * mu)
+    x = np.cos(lam) * cphi - np.cos(lc) * np.cos(pc)
+    y = np.sin(lam) * cphi - np.sin(lc) * np.cos(pc)
+    z = mu - np.sin(pc)
+    return np.sqrt(x * x + y * y + z * z)
+
+
+def gaussian_dome_grid(lam: np.ndarray, mu: np.ndarray, g: float = 9.80616, alpha: float = DOME_ALPHA,
+                       h_bar: float = DOME_H_BAR, amp: float = DOME_A) -> tuple[np.ndarray, float]:
+    """The dome's geopotential deviation Phi' = g A exp(-alpha (d/a)^2) on the
+    grid lam[None, :] x mu[:, None] ([J][I], latitudes as given), and the mean
+    geopotential Phibar = g h_bar the model takes as a parameter.  The
+    vorticity and divergence of the dome are zero (u = v = 0)."""
+    d = dome_chord(np.asarray(lam)[None, :], np.asarray(mu)[:, None])
+    return g * amp * np.exp(-alpha * d * d), g * h_bar
