@@ -152,3 +152,78 @@ def mlsdc_step(fine: Level, coarse: Level, u0, dt: float, n_iter: int, n_coarse_
     if return_nodes:
         return Th_f, FI_f, FE_f
     return Th_f[-1]
+
+
+def mlsdc_step_levels(levels: list, u0, dt: float, n_iter: int, n_coarse_sweeps: int = 1,
+                      return_nodes: bool = False):
+    """One time step of MLSDC on L >= 2 space-time levels (levels[0] finest).
+
+    The paper treats two levels (Algorithm 1) and leaves more for future work;
+    it calls the iteration a V-cycle from the fine level to the coarse level and
+    back, and writes the FAS term for a general pair of levels (Eq.
+    tau_term_level_l+1: tau_{l+1} = A_{l+1}(R Theta_l) - R A_l(Theta_l) + R tau_l).
+    Reading for L levels:
+      A) one sweep on level 0;
+      down, for l = 0..L-2: restrict level l's nodes 1..M_{l+1} to level l+1,
+         evaluate F there and save copies (step B), form tau_{l+1} with the
+         restricted tau_l, and do n_coarse_sweeps sweeps on level l+1 (step C);
+      up, for l = L-2..0: add the interpolated corrections of level l+1 (its
+         values minus the saved copies) to level l's nodes 1..M_l (step D),
+         then, on an intermediate level (l > 0), one sweep with tau_l.
+    Initialisation as in Algorithm 1: Theta^n on every fine node; node 0 of
+    each coarser level is the restriction of the level above's node 0,
+    evaluated once.  With two levels this is mlsdc_step."""
+    L = len(levels)
+    probs = [lv.prob for lv in levels]
+    down = [quadrature.lagrange_matrix(levels[l].t, levels[l + 1].t) for l in range(L - 1)]
+    up = [quadrature.lagrange_matrix(levels[l + 1].t, levels[l].t) for l in range(L - 1)]
+
+    def restrict(l, vals, i):
+        return probs[l].restrict(sum(down[l][i, j] * vals[j] for j in range(levels[l].M + 1)), probs[l + 1])
+
+    def interpolate(l, dvals, m):
+        return probs[l].interpolate(sum(up[l][m, i] * dvals[i] for i in range(levels[l + 1].M + 1)), probs[l + 1])
+
+    Th, FI, FE = [None] * L, [None] * L, [None] * L
+    Th[0], FI[0], FE[0] = spread(levels[0], u0)
+    for l in range(1, L):
+        u0l = restrict(l - 1, Th[l - 1], 0)
+        n = levels[l].M + 1
+        Th[l] = [u0l] * n
+        FI[l] = [probs[l].implicit_rhs(u0l)] * n
+        FE[l] = [probs[l].explicit_rhs(u0l)] * n
+    tau = [None] * L
+    saved = [None] * L
+    for _ in range(n_iter):
+        Th[0], FI[0], FE[0] = sweep(levels[0], dt, Th[0], FI[0], FE[0])
+        for l in range(L - 1):
+            c = l + 1
+            Th[c], FI[c], FE[c] = list(Th[c]), list(FI[c]), list(FE[c])
+            for m in range(1, levels[c].M + 1):
+                Th[c][m] = restrict(l, Th[l], m)
+                FI[c][m] = probs[c].implicit_rhs(Th[c][m])
+                FE[c][m] = probs[c].explicit_rhs(Th[c][m])
+            saved[c] = (list(Th[c]), list(FI[c]), list(FE[c]))
+            A_c = collocation_operator(levels[c], dt, Th[c], FI[c], FE[c])
+            A_f = collocation_operator(levels[l], dt, Th[l], FI[l], FE[l])
+            tau[c] = [A_c[i] - restrict(l, A_f, i) for i in range(levels[c].M + 1)]
+            if tau[l] is not None:
+                tau[c] = [tau[c][i] + restrict(l, tau[l], i) for i in range(levels[c].M + 1)]
+            for _s in range(n_coarse_sweeps):
+                Th[c], FI[c], FE[c] = sweep(levels[c], dt, Th[c], FI[c], FE[c], tau[c])
+        for l in range(L - 2, -1, -1):
+            c = l + 1
+            Ts, Is, Es = saved[c]
+            dT = [Th[c][i] - Ts[i] for i in range(levels[c].M + 1)]
+            dI = [FI[c][i] - Is[i] for i in range(levels[c].M + 1)]
+            dE = [FE[c][i] - Es[i] for i in range(levels[c].M + 1)]
+            Th[l], FI[l], FE[l] = list(Th[l]), list(FI[l]), list(FE[l])
+            for m in range(1, levels[l].M + 1):
+                Th[l][m] = Th[l][m] + interpolate(l, dT, m)
+                FI[l][m] = FI[l][m] + interpolate(l, dI, m)
+                FE[l][m] = FE[l][m] + interpolate(l, dE, m)
+            if l > 0:
+                Th[l], FI[l], FE[l] = sweep(levels[l], dt, Th[l], FI[l], FE[l], tau[l])
+    if return_nodes:
+        return Th[0], FI[0], FE[0]
+    return Th[0][-1]

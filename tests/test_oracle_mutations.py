@@ -209,3 +209,16 @@ def test_coupled_solve_without_coriolis_is_caught(monkeypatch):
     monkeypatch.setattr(swe.SWECoriolisImplicit, "implicit_solve", swe.SWE.implicit_solve)
     _fails(T_ci.test_coupled_solve_residual_against_transform_coriolis, 3.0e3)
     _fails(T_ci.test_fully_implicit_linear_sweeps_reach_collocation)
+
+
+def test_dropped_restricted_tau_in_three_levels_is_caught(monkeypatch):
+    import inspect
+    import test_oracle_mlsdc_levels as T_lv
+    src = inspect.getsource(sdc.mlsdc_step_levels)
+    planted = src.replace("            if tau[l] is not None:\n"
+                          "                tau[c] = [tau[c][i] + restrict(l, tau[l], i) for i in range(levels[c].M + 1)]\n", "")
+    assert planted != src
+    ns = dict(vars(sdc))
+    exec(planted, ns)
+    monkeypatch.setattr(sdc, "mlsdc_step_levels", ns["mlsdc_step_levels"])
+    _fails(T_lv.test_three_levels_reach_the_fine_collocation_solution)
