@@ -74,6 +74,7 @@ typedef struct sdc_level_s* sdc_level_t;
 typedef struct mlsdc_s* mlsdc_t;
 typedef struct mlsdc_ensemble_s* mlsdc_ensemble_t;
 typedef struct mlsdc_adjoint_s* mlsdc_adjoint_t;
+typedef struct mlsdc_levels_s* mlsdc_levels_t;
 
 /* Text of a status code, and the last CUDA error message seen by this thread. */
 const char* mlsdc_status_string(mlsdc_status s);
@@ -310,6 +311,26 @@ mlsdc_status mlsdc_step(mlsdc_t ml, double* state, double dt, int n_iter, int n_
 /* Kernel launches issued by the last mlsdc_step / sdc_step call made without
  * a graph replay (a count of this library's kernels, for reporting). */
 mlsdc_status mlsdc_launch_count(mlsdc_t ml, int64_t* launches);
+
+/* ---------------------------------------------------------------------------
+ * MLSDC on 2 <= L <= 8 space-time levels (levels[0] the finest; truncations
+ * non-increasing, equal member counts and splitting options, no level twice).
+ * The paper treats two levels (Algorithm 1) and leaves more for future work;
+ * it describes the iteration as a V-cycle and writes the FAS term for any
+ * pair of levels (Eq. tau_term_level_l+1, tau_{l+1} = A_{l+1}(R Theta_l)
+ * - R A_l(Theta_l) + R tau_l).  One iteration here: a sweep on level 0; down,
+ * for each pair, Algorithm 1's steps B and C (restrict nodes 1..M, evaluate,
+ * save; FAS term with the restricted tau of the finer level; n_coarse_sweeps
+ * sweeps); up, step D for each pair (interpolated corrections of Theta, F_I,
+ * F_E), followed by one sweep on every intermediate level.  With two levels
+ * this is exactly mlsdc_step.  The object keeps a level pair (the
+ * mlsdc_create data) per consecutive levels; the levels must outlive it.
+ * state: [members][3][N_c] of levels[0], in place; use_graph as mlsdc_step. */
+mlsdc_status mlsdc_levels_create(const sdc_level_t* levels, int n_levels, mlsdc_levels_t* out);
+mlsdc_status mlsdc_levels_destroy(mlsdc_levels_t h);
+mlsdc_status mlsdc_levels_step(mlsdc_levels_t h, double* state, double dt, int n_iter, int n_coarse_sweeps,
+                               int use_graph, void* stream);
+mlsdc_status mlsdc_levels_launch_count(mlsdc_levels_t h, int64_t* launches);
 
 /* ---------------------------------------------------------------------------
  * Ensembles of uneven truncation: one MLSDC object per truncation group

@@ -146,8 +146,8 @@ __global__ void k_restrict(const double2* __restrict__ Tf, double2* __restrict__
 }
 
 
-// tau_c = A_c(R Theta_f) - R A_f(Theta_f), A(Theta) = Theta - dt (Q x I) F
-// (Eq. tau_term_level_l+1 with tau_f = 0; Eq. collocation_problem), in the
+// tau_c = A_c(R Theta_f) - R A_f(Theta_f) [+ R tau_f], A(Theta) = Theta - dt (Q x I) F
+// (Eq. tau_term_level_l+1; tau_f = 0 on the finest level; Eq. collocation_problem), in the
 // folded form of FasFwd; one thread per (coarse node i, field, coarse
 // coefficient).  The same pass saves the restricted coarse values Theta_c,
 // F_I,c, F_E,c (Algorithm 1 step B) into Ts, FIs, FEs for step D.
@@ -155,14 +155,15 @@ __global__ void k_fas_tau(const double2* __restrict__ Tf, const double2* __restr
                           const double2* __restrict__ FEf, const double2* __restrict__ Tc,
                           const double2* __restrict__ FIc, const double2* __restrict__ FEc,
                           double2* __restrict__ tau, double2* __restrict__ Ts, double2* __restrict__ FIs,
-                          double2* __restrict__ FEs, const int* __restrict__ c2f, int ncf, int ncc,
-                          FasFwd A, size_t msf, size_t msc) {
+                          double2* __restrict__ FEs, const double2* __restrict__ tauf,
+                          const int* __restrict__ c2f, int ncf, int ncc, FasFwd A, size_t msf, size_t msc) {
     pdl_wait();
     pdl_launch();
     const size_t of_m = blockIdx.y * msf, oc_m = blockIdx.y * msc;
     Tf += of_m;
     FIf += of_m;
     FEf += of_m;
+    if (tauf) tauf += of_m;
     Tc += oc_m;
     FIc += oc_m;
     FEc += oc_m;
@@ -194,6 +195,8 @@ __global__ void k_fas_tau(const double2* __restrict__ Tf, const double2* __restr
             const double2 sc = make_double2(FIc[ol].x + FEc[ol].x, FIc[ol].y + FEc[ol].y);
             acc = cax(acc, -A.dQc[i * A.ncn + l], sc);
         }
+        if (tauf)  // + R tau_f on a level below the finest (Eq. tau_term_level_l+1)
+            for (int j = 0; j < A.nfn; ++j) acc = cax(acc, A.Pcf[i * A.nfn + j], tauf[(size_t)j * nf3 + of]);
         tau[oc] = acc;
     }
 }
@@ -692,12 +695,11 @@ extern "C" mlsdc_status mlsdc_destroy(mlsdc_t ml) {
 namespace mlsdc {
 
 // The schedule of one MLSDC step (Sec. 4.3.2 initialisation, then Algorithm 1
-// steps A-D per iteration) as a list of operations.
-size_t build_mlsdc_ops(mlsdc_t ml, double2* state, double dt, int n_iter, int n_c, std::vector<Op>& ops) {
-    sdc_level_t F = ml->f, C = ml->c;
-    const size_t nodef = F->node(), nodec = C->node();
-    const int nfn = F->n, ncn = C->n;
-    const int B = F->members;
+// steps A-D per iteration) as a list of operations, for L >= 2 levels as the
+// V-cycle of mlsdc_step_levels.
+size_t build_levels_ops(const std::vector<sdc_level_t>& Lv, const std::vector<mlsdc_t>& pairs, double2* state,
+                        double dt, int n_iter, int n_c, std::vector<Op>& ops) {
+    const int NL = (int)Lv.size();
     size_t tape = 0;
     ops.clear();
     auto bcast = [&](sdc_level_t L, const double2* src, double2* dst, int count, size_t ms_src) {
@@ -729,7 +731,6 @@ size_t build_mlsdc_ops(mlsdc_t ml, double2* state, double dt, int n_iter, int n_
         tape += (size_t)(nodes > 0 ? nodes : L->members) * L->node();
         ops.push_back(o);
     };
-    const bool batch_b = B == 1 && ncn > 2 && C->plan->max_members >= ncn - 1;
     auto sweep_ops = [&](sdc_level_t L, double2* FIo, double2* FEo, double2* FIn, double2* FEn, double2* tau) {
         for (int m = 0; m < L->n - 1; ++m) {
             Op o{OpK::Node};
@@ -746,98 +747,124 @@ size_t build_mlsdc_ops(mlsdc_t ml, double2* state, double dt, int n_iter, int n_
             fe(L, L->Th + (m + 1) * L->node(), FEn + (m + 1) * L->node());
         }
     };
-    auto restrict_ops = [&](int i0, int i1) {
+    auto restrict_ops = [&](int l, int i0, int i1) {  // level l -> l + 1, coarse nodes [i0, i1)
         Op o{OpK::Restrict};
-        o.L = C;
-        o.p[0] = F->Th;
-        o.p[1] = C->Th;
+        o.L = Lv[l + 1];
+        o.pair = pairs[l];
+        o.p[0] = Lv[l]->Th;
+        o.p[1] = Lv[l + 1]->Th;
         o.i0 = i0;
         o.i1 = i1;
         ops.push_back(o);
     };
-    int cf = F->cur, cc = C->cur;
-    // the implicit-solve reciprocals of both levels at this dt
-    for (sdc_level_t L : {F, C}) {
+    std::vector<int> cur(NL);
+    for (int l = 0; l < NL; ++l) cur[l] = Lv[l]->cur;
+    auto FIc = [&](int l) { return Lv[l]->FI[cur[l]]; };
+    auto FEc = [&](int l) { return Lv[l]->FE[cur[l]]; };
+    auto sweep_level = [&](int l, double2* tau) {
+        sdc_level_t L = Lv[l];
+        sweep_ops(L, L->FI[cur[l]], L->FE[cur[l]], L->FI[1 - cur[l]], L->FE[1 - cur[l]], tau);
+        cur[l] = 1 - cur[l];
+    };
+    // the implicit-solve reciprocals (or factored chains) of every level at this dt
+    for (sdc_level_t L : Lv) {
         Op o{OpK::SolveCoefs};
         o.L = L;
         o.dt = dt;
         ops.push_back(o);
     }
-    // initialisation: fine spread; coarse node 0 = restriction of Theta^n, evaluated once
-    bcast(F, state, F->Th, nfn, nodef);
-    fi(F, F->Th, F->FI[cf]);
-    fe(F, F->Th, F->FE[cf]);
-    bcast(F, F->FI[cf], F->FI[cf] + nodef, nfn - 1, F->ms());
-    bcast(F, F->FE[cf], F->FE[cf] + nodef, nfn - 1, F->ms());
-    restrict_ops(0, 1);
-    fi(C, C->Th, C->FI[cc]);
-    fe(C, C->Th, C->FE[cc]);
+    // initialisation: fine spread; node 0 of each coarser level = restriction of
+    // the level above's node 0, evaluated once
+    sdc_level_t F = Lv[0];
+    bcast(F, state, F->Th, F->n, F->node());
+    fi(F, F->Th, FIc(0));
+    fe(F, F->Th, FEc(0));
+    bcast(F, FIc(0), FIc(0) + F->node(), F->n - 1, F->ms());
+    bcast(F, FEc(0), FEc(0) + F->node(), F->n - 1, F->ms());
+    for (int l = 1; l < NL; ++l) {
+        restrict_ops(l - 1, 0, 1);
+        fi(Lv[l], Lv[l]->Th, FIc(l));
+        fe(Lv[l], Lv[l]->Th, FEc(l));
+    }
     for (int it = 0; it < n_iter; ++it) {
         // A) fine sweep
-        sweep_ops(F, F->FI[cf], F->FE[cf], F->FI[1 - cf], F->FE[1 - cf], nullptr);
-        cf = 1 - cf;
-        // B) restrict nodes 1..Mc, evaluate, save.  The evaluations at the
-        // coarse nodes are independent: with one member and a coarse plan
-        // sized for them, all Mc nodes go in one launch per stage.
-        restrict_ops(1, ncn);
-        if (batch_b) {
-            fi(C, C->Th + nodec, C->FI[cc] + nodec, ncn - 1);
-            fe(C, C->Th + nodec, C->FE[cc] + nodec, ncn - 1);
-        } else {
-            for (int i = 1; i < ncn; ++i) {
-                fi(C, C->Th + i * nodec, C->FI[cc] + i * nodec);
-                fe(C, C->Th + i * nodec, C->FE[cc] + i * nodec);
+        sweep_level(0, nullptr);
+        for (int l = 0; l + 1 < NL; ++l) {
+            const int c = l + 1;
+            sdc_level_t C = Lv[c];
+            const size_t nodec = C->node();
+            const int ncn = C->n;
+            // B) restrict nodes 1..Mc, evaluate, save.  The evaluations at the
+            // coarse nodes are independent: with one member and a coarse plan
+            // sized for them, all Mc nodes go in one launch per stage.
+            restrict_ops(l, 1, ncn);
+            if (C->members == 1 && ncn > 2 && C->plan->max_members >= ncn - 1) {
+                fi(C, C->Th + nodec, FIc(c) + nodec, ncn - 1);
+                fe(C, C->Th + nodec, FEc(c) + nodec, ncn - 1);
+            } else {
+                for (int i = 1; i < ncn; ++i) {
+                    fi(C, C->Th + i * nodec, FIc(c) + i * nodec);
+                    fe(C, C->Th + i * nodec, FEc(c) + i * nodec);
+                }
             }
+            // C) FAS correction (its pass also saves the restricted values of
+            // step B), coarse sweeps
+            mlsdc_t P = pairs[l];
+            Op fa{OpK::Fas};
+            fa.L = C;
+            fa.pair = P;
+            fa.tauf = l > 0 ? pairs[l - 1]->tau : nullptr;
+            double2* fas[10] = {Lv[l]->Th, FIc(l), FEc(l), C->Th, FIc(c), FEc(c), P->tau, P->Ts, P->FIs, P->FEs};
+            std::copy(fas, fas + 10, fa.p);
+            fa.dt = dt;
+            ops.push_back(fa);
+            for (int k = 0; k < n_c; ++k) sweep_level(c, P->tau);
         }
-        // C) FAS correction (its pass also saves the restricted values of
-        // step B), coarse sweeps
-        Op fa{OpK::Fas};
-        fa.L = C;
-        double2* fas[10] = {F->Th, F->FI[cf], F->FE[cf], C->Th, C->FI[cc], C->FE[cc], ml->tau,
-                            ml->Ts, ml->FIs, ml->FEs};
-        std::copy(fas, fas + 10, fa.p);
-        fa.dt = dt;
-        ops.push_back(fa);
-        for (int k = 0; k < n_c; ++k) {
-            sweep_ops(C, C->FI[cc], C->FE[cc], C->FI[1 - cc], C->FE[1 - cc], ml->tau);
-            cc = 1 - cc;
+        // D) back up: interpolate each level's corrections to the level above,
+        // one sweep on every intermediate level
+        for (int l = NL - 2; l >= 0; --l) {
+            const int c = l + 1;
+            mlsdc_t P = pairs[l];
+            Op ip{OpK::Interp};
+            ip.L = Lv[c];
+            ip.pair = P;
+            double2* ipp[9] = {Lv[l]->Th, FIc(l), FEc(l), Lv[c]->Th, FIc(c), FEc(c), P->Ts, P->FIs, P->FEs};
+            std::copy(ipp, ipp + 9, ip.p);
+            ops.push_back(ip);
+            if (l > 0) sweep_level(l, pairs[l - 1]->tau);
         }
-        // D) interpolate the coarse corrections to fine nodes 1..Mf
-        Op ip{OpK::Interp};
-        ip.L = C;
-        double2* ipp[9] = {F->Th, F->FI[cf], F->FE[cf], C->Th, C->FI[cc], C->FE[cc], ml->Ts, ml->FIs, ml->FEs};
-        std::copy(ipp, ipp + 9, ip.p);
-        ops.push_back(ip);
     }
     Op last{OpK::CopyLast};
     last.L = F;
-    last.p[0] = F->Th + (nfn - 1) * nodef;
+    last.p[0] = F->Th + (F->n - 1) * F->node();
     last.p[1] = state;
     ops.push_back(last);
-    F->cur = cf;
-    C->cur = cc;
+    for (int l = 0; l < NL; ++l) Lv[l]->cur = cur[l];
     return tape;
+}
+
+size_t build_mlsdc_ops(mlsdc_t ml, double2* state, double dt, int n_iter, int n_c, std::vector<Op>& ops) {
+    return build_levels_ops({ml->f, ml->c}, {ml}, state, dt, n_iter, n_c, ops);
 }
 
 mlsdc_status run_ops(mlsdc_t ml, const std::vector<Op>& ops, cudaStream_t st, int64_t* launches, double2* tape,
                      bool fuse_node) {
-    sdc_level_t F = ml->f, C = ml->c;
-    const int ncf = F->plan->nc, ncc = C->plan->nc;
-    const int nfn = F->n, ncn = C->n;
-    const size_t msf = F->ms(), msc = C->ms();
-    auto gt = [&](int threads) { return dim3(grid_for(threads), F->members); };
-    F->launches = C->launches = 0;
+    // every level the operations touch (launch accounting)
+    std::vector<sdc_level_t> lv;
+    for (const Op& o : ops)
+        if (o.L && std::find(lv.begin(), lv.end(), o.L) == lv.end()) lv.push_back(o.L);
+    for (sdc_level_t L : lv) L->launches = 0;
     int64_t own = 0;
-    FasArgs fa;
-    std::memset(&fa, 0, sizeof(fa));
-    fa.nfn = nfn;
-    fa.ncn = ncn;
-    for (int i = 0; i < nfn * nfn; ++i) fa.Qf[i] = F->Q[i];
-    for (int i = 0; i < ncn * ncn; ++i) fa.Qc[i] = C->Q[i];
-    for (int i = 0; i < ncn * nfn; ++i) fa.Pcf[i] = ml->Pcf.a[i];
     mlsdc_status s = MLSDC_OK;
     for (size_t oi = 0; oi < ops.size(); ++oi) {
         const Op& o = ops[oi];
+        // the level pair of a transfer operation (the two-level object by default)
+        const mlsdc_s* P = o.pair ? o.pair : ml;
+        sdc_level_t F = P->f, C = P->c;
+        const int ncf = F->plan->nc, ncc = C->plan->nc;
+        const int nfn = F->n, ncn = C->n;
+        const size_t msf = F->ms(), msc = C->ms();
+        auto gt = [&](int threads) { return dim3(grid_for(threads), F->members); };
         switch (o.k) {
             case OpK::Bcast:
                 s = launch_bcast(o.L, o.p[0], o.p[1], o.n3, o.count, o.ms_src, o.ms_dst, st);
@@ -884,7 +911,7 @@ mlsdc_status run_ops(mlsdc_t ml, const std::vector<Op>& ops, cudaStream_t st, in
             case OpK::Restrict:
                 MLSDC_LAUNCH("k_restrict",
                              launch_k(k_restrict, gt((o.i1 - o.i0) * 3 * ncc), dim3(256), 0, st, o.p[0], o.p[1],
-                                      (const int*)ml->d_c2f, ncf, ncc, nfn, o.i0, o.i1, ml->Pcf, msf, msc));
+                                      (const int*)P->d_c2f, ncf, ncc, nfn, o.i0, o.i1, P->Pcf, msf, msc));
                 own++;
                 break;
             case OpK::Copy:
@@ -898,23 +925,24 @@ mlsdc_status run_ops(mlsdc_t ml, const std::vector<Op>& ops, cudaStream_t st, in
                 for (int i = 0; i < ncn; ++i) {
                     for (int j = 0; j < nfn; ++j) {
                         double pq = 0.0;
-                        for (int l = 0; l < nfn; ++l) pq += fa.Pcf[i * nfn + l] * fa.Qf[l * nfn + j];
-                        fw.Pcf[i * nfn + j] = fa.Pcf[i * nfn + j];
+                        for (int l = 0; l < nfn; ++l) pq += P->Pcf.a[i * nfn + l] * F->Q[l * nfn + j];
+                        fw.Pcf[i * nfn + j] = P->Pcf.a[i * nfn + j];
                         fw.dPQf[i * nfn + j] = o.dt * pq;
                     }
-                    for (int l = 0; l < ncn; ++l) fw.dQc[i * ncn + l] = o.dt * fa.Qc[i * ncn + l];
+                    for (int l = 0; l < ncn; ++l) fw.dQc[i * ncn + l] = o.dt * C->Q[i * ncn + l];
                 }
                 MLSDC_LAUNCH("k_fas_tau", launch_k(k_fas_tau, gt(ncn * 3 * ncc), dim3(256), 0, st, o.p[0], o.p[1],
                                                    o.p[2], o.p[3], o.p[4], o.p[5], o.p[6], o.p[7], o.p[8], o.p[9],
-                                                   (const int*)ml->d_c2f, ncf, ncc, fw, msf, msc));
+                                                   (const double2*)o.tauf, (const int*)P->d_c2f, ncf, ncc, fw, msf,
+                                                   msc));
                 own++;
                 break;
             }
             case OpK::Interp:
                 MLSDC_LAUNCH("k_interp",
                              launch_k(k_interp, gt((nfn - 1) * 3 * ncc), dim3(256), 0, st, o.p[0], o.p[1], o.p[2],
-                                      o.p[3], o.p[4], o.p[5], o.p[6], o.p[7], o.p[8], (const int*)ml->d_c2f, ncf, ncc,
-                                      nfn, ncn, ml->Pfc, msf, msc));
+                                      o.p[3], o.p[4], o.p[5], o.p[6], o.p[7], o.p[8], (const int*)P->d_c2f, ncf, ncc,
+                                      nfn, ncn, P->Pfc, msf, msc));
                 own++;
                 break;
             case OpK::SolveCoefs:
@@ -929,7 +957,10 @@ mlsdc_status run_ops(mlsdc_t ml, const std::vector<Op>& ops, cudaStream_t st, in
         }
         if (s != MLSDC_OK) return s;
     }
-    if (launches) *launches = own + F->launches + C->launches;
+    if (launches) {
+        *launches = own;
+        for (sdc_level_t L : lv) *launches += L->launches;
+    }
     return MLSDC_OK;
 }
 
@@ -1002,6 +1033,90 @@ extern "C" mlsdc_status mlsdc_step(mlsdc_t ml, double* state, double dt, int n_i
         ml->c->cur = 0;
     }
     MLSDC_CUDA(cudaGraphLaunch(it->second, st));
+    return MLSDC_OK;
+}
+
+// ------------------------------------------------------- three or more levels
+struct mlsdc_levels_s {
+    std::vector<sdc_level_t> levels;
+    std::vector<mlsdc_t> pairs;  // pairs[l] joins levels l and l + 1 (owned)
+    cudaStream_t cap = nullptr;
+    std::map<std::tuple<double*, double, int, int>, cudaGraphExec_t> graphs;
+    int64_t launches = 0;
+};
+
+extern "C" mlsdc_status mlsdc_levels_destroy(mlsdc_levels_t h) {
+    if (!h) return MLSDC_ERR_INVALID;
+    for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
+    for (mlsdc_t p : h->pairs) mlsdc_destroy(p);
+    if (h->cap) cudaStreamDestroy(h->cap);
+    delete h;
+    return MLSDC_OK;
+}
+
+extern "C" mlsdc_status mlsdc_levels_create(const sdc_level_t* levels, int n_levels, mlsdc_levels_t* out) {
+    if (!levels || !out || n_levels < 2 || n_levels > 8) return MLSDC_ERR_INVALID;
+    for (int l = 0; l < n_levels; ++l) {
+        if (!levels[l]) return MLSDC_ERR_INVALID;
+        for (int k = 0; k < l; ++k)
+            if (levels[k] == levels[l]) return MLSDC_ERR_INVALID;  // each level's node arrays are its own
+    }
+    mlsdc_levels_t h = new mlsdc_levels_s();
+    h->levels.assign(levels, levels + n_levels);
+    for (int l = 0; l + 1 < n_levels; ++l) {
+        mlsdc_t p = nullptr;
+        mlsdc_status s = mlsdc_create(levels[l], levels[l + 1], &p);
+        if (s != MLSDC_OK) {
+            mlsdc_levels_destroy(h);
+            return s;
+        }
+        h->pairs.push_back(p);
+    }
+    if (cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess) {
+        set_error("mlsdc_levels_create", cudaGetLastError());
+        mlsdc_levels_destroy(h);
+        return MLSDC_ERR_CUDA;
+    }
+    *out = h;
+    return MLSDC_OK;
+}
+
+namespace mlsdc {
+static mlsdc_status levels_enqueue(mlsdc_levels_t h, double* state, double dt, int n_iter, int n_c, cudaStream_t st) {
+    std::vector<Op> ops;
+    build_levels_ops(h->levels, h->pairs, (double2*)state, dt, n_iter, n_c, ops);
+    return run_ops(h->pairs[0], ops, st, &h->launches, nullptr);
+}
+}  // namespace mlsdc
+
+extern "C" mlsdc_status mlsdc_levels_step(mlsdc_levels_t h, double* state, double dt, int n_iter, int n_coarse_sweeps,
+                                          int use_graph, void* stream) {
+    if (!h || !state || n_iter < 0 || n_coarse_sweeps < 0) return MLSDC_ERR_INVALID;
+    cudaStream_t st = (cudaStream_t)stream;
+    for (mlsdc_t p : h->pairs) {
+        mlsdc_status sp = prepare_levels(p, dt, st);
+        if (sp != MLSDC_OK) return sp;
+    }
+    if (!use_graph) return levels_enqueue(h, state, dt, n_iter, n_coarse_sweeps, st);
+    auto key = std::make_tuple(state, dt, n_iter, n_coarse_sweeps);
+    auto it = h->graphs.find(key);
+    if (it == h->graphs.end()) {
+        for (sdc_level_t L : h->levels) L->cur = 0;  // the same buffer parity at capture and every replay
+        cudaGraphExec_t ex = nullptr;
+        mlsdc_status s = capture(h->cap, &ex, [&](cudaStream_t cs) {
+            return levels_enqueue(h, state, dt, n_iter, n_coarse_sweeps, cs);
+        });
+        if (s != MLSDC_OK) return s;
+        it = h->graphs.emplace(key, ex).first;
+        for (sdc_level_t L : h->levels) L->cur = 0;
+    }
+    MLSDC_CUDA(cudaGraphLaunch(it->second, st));
+    return MLSDC_OK;
+}
+
+extern "C" mlsdc_status mlsdc_levels_launch_count(mlsdc_levels_t h, int64_t* launches) {
+    if (!h || !launches) return MLSDC_ERR_INVALID;
+    *launches = h->launches;
     return MLSDC_OK;
 }
 

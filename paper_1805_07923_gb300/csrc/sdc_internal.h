@@ -70,6 +70,8 @@ struct Op {
     size_t tape_off = 0;             // FE: offset of its linearisation point in a step's tape (complex)
     int nodes = 0;                   // FI / FE: > 0 = that many consecutive nodes of a one-member level
                                      // in one launch (the nodes as the batch); 0 = one node of every member
+    mlsdc_t pair = nullptr;          // Restrict / Fas / Interp: the level pair (fine, coarse) they join
+    double2* tauf = nullptr;         // Fas: the finer level's own tau (null on the finest pair)
 };
 
 inline Phys phys_of(const swe_params& p) { return Phys{1.0 / (p.a * p.a), p.phibar, p.nu}; }
@@ -145,6 +147,13 @@ namespace mlsdc {
 // current buffer parities, which it advances as the step will.  Returns the
 // number of complex values one step's F_E linearisation points take.
 size_t build_mlsdc_ops(mlsdc_t ml, double2* state, double dt, int n_iter, int n_c, std::vector<Op>& ops);
+
+// The same for L >= 2 levels (levels[0] finest), pairs[l] joining levels l
+// and l + 1: the V-cycle of mlsdc_step_levels (down: restrict, evaluate,
+// FAS with the restricted finer tau, n_c sweeps; up: interpolate, one sweep
+// on each intermediate level).  With two levels the list is build_mlsdc_ops's.
+size_t build_levels_ops(const std::vector<sdc_level_t>& levels, const std::vector<mlsdc_t>& pairs, double2* state,
+                        double dt, int n_iter, int n_c, std::vector<Op>& ops);
 
 // Launch the operations in order on `st`.  With `tape`, each FE operation
 // first copies its input to tape + tape_off.  With fuse_node, an FE

@@ -39,6 +39,10 @@ _SIGS = {
     "sh_plan_batched": ([_I, _I, _I, _I, _I, ctypes.POINTER(_VP)], _I),
     "swe_explicit_rhs_batched": ([_VP, ctypes.POINTER(SweParams), _DP, _DP, _I, _VP], _I),
     "sdc_level_create_batched": ([_VP, ctypes.POINTER(SweParams), _I, _I, ctypes.POINTER(_VP)], _I),
+    "mlsdc_levels_create": ([ctypes.POINTER(_VP), _I, ctypes.POINTER(_VP)], _I),
+    "mlsdc_levels_destroy": ([_VP], _I),
+    "mlsdc_levels_step": ([_VP, _DP, _D, _I, _I, _I, _VP], _I),
+    "mlsdc_levels_launch_count": ([_VP, ctypes.POINTER(_I64)], _I),
     "mlsdc_profile_node": ([_VP, _D, _I, ctypes.POINTER(ctypes.c_float), _VP], _I),
     "sdc_level_create_ex": ([_VP, ctypes.POINTER(SweParams), _I, _I, _I, ctypes.POINTER(_VP)], _I),
     "swe_implicit_rhs_ex": ([_VP, ctypes.POINTER(SweParams), _DP, _DP, _I, _VP], _I),
@@ -361,6 +365,40 @@ def mlsdc_step(ml: MLSDC, state: torch.Tensor, dt: float, n_iter: int, n_coarse_
                stream=None):
     _check(lib().mlsdc_step(ml.h, _ptr(state, 6 * ml.fine.plan.nc * ml.fine.members), float(dt), int(n_iter), int(n_coarse_sweeps),
                             1 if use_graph else 0, _stream(stream)), "mlsdc_step")
+
+
+class MLSDCLevels:
+    """MLSDC on two or more levels (levels[0] finest; the levels must outlive it)."""
+
+    def __init__(self, levels: list[Level]):
+        self.levels = list(levels)
+        arr = (ctypes.c_void_p * len(levels))(*[lv.h.value for lv in levels])
+        h = ctypes.c_void_p()
+        _check(lib().mlsdc_levels_create(arr, len(levels), ctypes.byref(h)), "mlsdc_levels_create")
+        self.h = h
+
+    def close(self):
+        if self.h:
+            lib().mlsdc_levels_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def launch_count(self) -> int:
+        v = ctypes.c_int64()
+        _check(lib().mlsdc_levels_launch_count(self.h, ctypes.byref(v)), "mlsdc_levels_launch_count")
+        return v.value
+
+
+def mlsdc_levels_step(ml: MLSDCLevels, state: torch.Tensor, dt: float, n_iter: int, n_coarse_sweeps: int,
+                      use_graph: bool = False, stream=None):
+    f = ml.levels[0]
+    _check(lib().mlsdc_levels_step(ml.h, _ptr(state, 6 * f.plan.nc * f.members), float(dt), int(n_iter),
+                                   int(n_coarse_sweeps), 1 if use_graph else 0, _stream(stream)), "mlsdc_levels_step")
 
 
 def mlsdc_check_finite(x: torch.Tensor, stream=None) -> bool:
