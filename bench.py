@@ -119,6 +119,30 @@ def evals_per_step(w):
     return f, c
 
 
+# --levels 3: a third level below the headline's coarse level (T42 on 128 x 64
+# with 2 Lobatto nodes); the V-cycle adds one sweep on the middle level per
+# iteration (mlsdc_levels_step)
+THIRD_LEVEL = dict(R=42, I=128, J=64, n=2)
+
+
+def evals_per_step_levels(w):
+    """F_E evaluations per step on each of the three levels: node 0 once per
+    level; per iteration the fine sweep, and on each coarser level the
+    restricted nodes and n_coarse sweeps, plus one up-sweep on the middle level."""
+    n = [w["nf"], w["nc"], THIRD_LEVEL["n"]]
+    N, nc = w["n_iter"], w["n_coarse"]
+    return (1 + N * (n[0] - 1), 1 + N * ((n[1] - 1) * (1 + nc + 1)), 1 + N * ((n[2] - 1) * (1 + nc)))
+
+
+def do_step(M, ml, state):
+    """One step of the workload through the library's public step call."""
+    w = WORKLOAD
+    if isinstance(ml, M.MLSDCLevels):
+        M.mlsdc_levels_step(ml, state, w["dt"], w["n_iter"], w["n_coarse"], use_graph=True)
+    else:
+        M.mlsdc_step(ml, state, w["dt"], w["n_iter"], w["n_coarse"], use_graph=True)
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
 
@@ -263,13 +287,13 @@ def timed_steps(torch, M, ml, state, K, flush, stream) -> float:
     for k in range(K):
         flush.zero_()
         ev[k][0].record(stream)
-        M.mlsdc_step(ml, state, w["dt"], w["n_iter"], w["n_coarse"], use_graph=True)
+        do_step(M, ml, state)
         ev[k][1].record(stream)
     torch.cuda.synchronize()
     return sum(a.elapsed_time(b) for a, b in ev)
 
 
-def build_mlsdc(M, prec, coriolis_implicit=False):
+def build_mlsdc(M, prec, coriolis_implicit=False, levels=2):
     w = WORKLOAD
     pf = M.Plan(w["Rf"], w["If"], w["Jf"], prec)
     # the coarse plan holds scratch for M_c states: step B's coarse evaluations
@@ -277,6 +301,11 @@ def build_mlsdc(M, prec, coriolis_implicit=False):
     pc = M.Plan(w["Rc"], w["Ic"], w["Jc"], prec, w["nc"] - 1)
     lf = M.Level(pf, w["nf"], coriolis_implicit=coriolis_implicit)
     lc = M.Level(pc, w["nc"], coriolis_implicit=coriolis_implicit)
+    if levels == 3:
+        t = THIRD_LEVEL
+        p3 = M.Plan(t["R"], t["I"], t["J"], prec)
+        l3 = M.Level(p3, t["n"], coriolis_implicit=coriolis_implicit)
+        return M.MLSDCLevels([lf, lc, l3]), (pf, pc, lf, lc, p3, l3)
     return M.MLSDC(lf, lc), (pf, pc, lf, lc)
 
 
@@ -596,7 +625,7 @@ def cpu_baseline_adjoint(n_sample: int = 2):
                       f"{a['n_steps'] // n_sample}"}
 
 
-def cpu_baseline(steps_cap_s: float = 25.0, coriolis_implicit: bool = False):
+def cpu_baseline(steps_cap_s: float = 25.0, coriolis_implicit: bool = False, levels: int = 2):
     """The float64 oracle as it stands, timed on this host for a bounded sample."""
     from oracle import sdc as osdc
     from oracle.swe import SWE, SWECoriolisImplicit, Params
@@ -609,12 +638,16 @@ def cpu_baseline(steps_cap_s: float = 25.0, coriolis_implicit: bool = False):
         pf.implicit_solve(inputs.initial_state(w["Rf"]), 1.0)
         pc.implicit_solve(inputs.initial_state(w["Rc"]), 1.0)
     fine, coarse = osdc.Level(pf, w["nf"]), osdc.Level(pc, w["nc"])
+    lv = [fine, coarse]
+    if levels == 3:
+        t3 = THIRD_LEVEL
+        lv.append(osdc.Level(cls(t3["R"], t3["I"], t3["J"], Params()), t3["n"]))
     setup = time.perf_counter() - t0
     u = inputs.initial_state(w["Rf"])
     n, t = 0, 0.0
     while n == 0 or (t < steps_cap_s and n < 8):
         t1 = time.perf_counter()
-        u = osdc.mlsdc_step(fine, coarse, u, w["dt"], w["n_iter"], w["n_coarse"])
+        u = osdc.mlsdc_step_levels(lv, u, w["dt"], w["n_iter"], w["n_coarse"])
         t += time.perf_counter() - t1
         n += 1
     return {"value": n / t, "unit": "steps/s", "cores": os.cpu_count(), "kind": "oracle",
@@ -691,6 +724,8 @@ def main():
                     help="Legendre/FFT arithmetic; bf16x3 (the fastest variant within 1e-6) by default")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--levels", type=int, default=2, choices=[2, 3],
+                    help="space-time levels of the headline workload: 2 (the paper's) or 3 (a T42 level added)")
     ap.add_argument("--coriolis", default="explicit", choices=["explicit", "implicit"],
                     help="splitting of the headline workload: the paper's (Coriolis in F_E) or Coriolis in F_I")
     ap.add_argument("--workload", default="headline", choices=["headline", "ensemble", "adjoint"],
@@ -717,14 +752,15 @@ def main():
     w = WORKLOAD
     prec = args.precision
     cor_impl = args.coriolis == "implicit"
-    ml, (pf, pc, lf, lc) = build_mlsdc(M, prec, cor_impl)
+    ml, objs = build_mlsdc(M, prec, cor_impl, args.levels)
+    pf, pc, lf, lc = objs[:4]
     u0 = inputs.initial_state(w["Rf"], seed=replica_seed(rank))
     state = torch.from_numpy(u0).to(dev)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     for _ in range(args.warmup):
-        M.mlsdc_step(ml, state, w["dt"], w["n_iter"], w["n_coarse"], use_graph=True)
+        do_step(M, ml, state)
     torch.cuda.synchronize()
     launches_per_step = ml.launch_count()
 
@@ -747,7 +783,7 @@ def main():
     e0.record(stream)
     for _ in range(Ke):
         state.copy_(host_in, non_blocking=True)
-        M.mlsdc_step(ml, state, w["dt"], w["n_iter"], w["n_coarse"], use_graph=True)
+        do_step(M, ml, state)
         host_out.copy_(state, non_blocking=True)
     e1.record(stream)
     e1.synchronize()
@@ -764,17 +800,17 @@ def main():
     # the accuracy of this precision after the full 400-step run against it
     comparison = None
     if prec != "fp64":
-        ml64, keep64 = build_mlsdc(M, "fp64", cor_impl)
+        ml64, keep64 = build_mlsdc(M, "fp64", cor_impl, args.levels)
         s64 = torch.from_numpy(u0).to(dev)
         for _ in range(3):
-            M.mlsdc_step(ml64, s64, w["dt"], w["n_iter"], w["n_coarse"], use_graph=True)
+            do_step(M, ml64, s64)
         K64 = min(K, 100)
         v64 = K64 / (timed_steps(torch, M, ml64, s64, K64, flush, stream) * 1e-3)
         a = torch.from_numpy(u0).to(dev)
         b = torch.from_numpy(u0).to(dev)
         for _ in range(w["total_steps"]):
-            M.mlsdc_step(ml, a, w["dt"], w["n_iter"], w["n_coarse"], use_graph=True)
-            M.mlsdc_step(ml64, b, w["dt"], w["n_iter"], w["n_coarse"], use_graph=True)
+            do_step(M, ml, a)
+            do_step(M, ml64, b)
         torch.cuda.synchronize()
         err = total_phi_rel_l2(a.cpu().numpy(), b.cpu().numpy())
         comparison = {"fp64_gpu_steps_per_s": v64, "speedup_vs_fp64_gpu": value / ws / v64,
@@ -791,7 +827,7 @@ def main():
     fine_ms = M.mlsdc_profile_rhs(pf, lf.prm, x0, FE, reps=50)
     coarse_ms = M.mlsdc_profile_rhs(pc, lc.prm, torch.from_numpy(np.ascontiguousarray(inputs.truncate(u0, w["Rf"], w["Rc"]))).to(dev),
                                     torch.empty((3, pc.nc), dtype=torch.complex128, device=dev), reps=50)
-    nfe, nce = evals_per_step(w)
+    nfe, nce = evals_per_step(w) if args.levels == 2 else evals_per_step_levels(w)[:2]
     names = ["legendre_synthesis", "grid_fft_products", "legendre_analysis"]
     shares = []
     for lvl, ms, (R, I, J), cnt in (("T170", fine_ms, (w["Rf"], w["If"], w["Jf"]), nfe),
@@ -834,9 +870,10 @@ def main():
     # device time of each node update on the level's arrays after the timed run
     node = {"kernel": "k_sweep_node_cor" if cor_impl else "k_sweep_node", "levels": {}}
     node_ms_step = 0.0
+    up = 1 if args.levels == 3 else 0  # the V-cycle's up-sweep on the middle level
     for lvl, lev, (R, I, J), nn, per_step in (("T170", lf, (w["Rf"], w["If"], w["Jf"]), w["nf"], w["n_iter"]),
                                               ("T85", lc, (w["Rc"], w["Ic"], w["Jc"]), w["nc"],
-                                               w["n_iter"] * w["n_coarse"])):
+                                               w["n_iter"] * (w["n_coarse"] + up))):
         ms = M.mlsdc_profile_node(lev, w["dt"], reps=20)
         nbytes_m = [node_update_bytes(R, nn, m, cor_impl) for m in range(nn - 1)]
         gbs = sum(nbytes_m) / (sum(ms) * 1e-3) / 1e9
@@ -850,12 +887,20 @@ def main():
                     "these kernels, not HBM")
 
     sh_flops = nfe * sh_flops_per_eval(w["Rf"], w["If"], w["Jf"]) + nce * sh_flops_per_eval(w["Rc"], w["Ic"], w["Jc"])
+    if args.levels == 3:
+        t3 = THIRD_LEVEL
+        e0, e1, e2 = evals_per_step_levels(w)
+        sh_flops = (e0 * sh_flops_per_eval(w["Rf"], w["If"], w["Jf"]) + e1 * sh_flops_per_eval(w["Rc"], w["Ic"], w["Jc"])
+                    + e2 * sh_flops_per_eval(t3["R"], t3["I"], t3["J"]))
     line = {
         "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": ws, "steps": K, "warmup": args.warmup,
         "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if prec == "fp64" else f"f64+{prec}", "data": "synthetic",
         "config": {"workload": WORKLOAD_NAME + (", Coriolis terms implicit (F_I = L_G + L_F, F_E = N)"
-                                                if cor_impl else ""),
+                                                if cor_impl else "")
+                   + (", a third level T42 128x64 with 2 Lobatto nodes (V-cycle, one up-sweep on T85)"
+                      if args.levels == 3 else ""),
+                   "levels": args.levels,
                    "splitting": "coriolis_implicit" if cor_impl else "paper (Coriolis explicit)",
                    "precision": prec, "steps_of_run": w["total_steps"],
                    "l2": "flushed between timed steps (256 MB write)", "graph": "one CUDA graph per step",
@@ -872,7 +917,7 @@ def main():
     if comparison is not None:
         line["vs_fp64_gpu_path"] = comparison
     if ws == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(coriolis_implicit=cor_impl)
+        line["cpu_baseline"] = cpu_baseline(coriolis_implicit=cor_impl, levels=args.levels)
     print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
