@@ -10,7 +10,8 @@ Schemes, in the paper's notation: SDC(M+1, K) is the single-level scheme with
 M+1 Gauss-Lobatto nodes and K sweeps per step; MLSDC(M_f+1, M_c+1, N, 1/2) is
 the two-level scheme with the coarse truncation R_c (half of R by default),
 N iterations of one fine and one coarse sweep (the paper's choice of one
-coarse sweep per iteration).  Cases: `dome` (the Gaussian dome of Eq.
+coarse sweep per iteration); MLSDC(5,3,2,N) adds a third level at R_3 (a
+quarter of R by default) with 2 nodes (the V-cycle of mlsdc_levels_step).  Cases: `dome` (the Gaussian dome of Eq.
 gaussian_bump, at rest, with the mean geopotential g h_bar = g 29400 m) and
 `spectra` (the seeded n^-3/2 state of the benchmarks).  Errors are L_inf
 norms over the Gaussian grid of Phi' and of zeta (the difference
@@ -31,27 +32,37 @@ from . import inputs
 from . import mlsdc as M
 
 SCHEMES = {
-    # name: (fine nodes, sweeps or iterations, coarse nodes or None)
-    "SDC(3,4)": (3, 4, None),
-    "MLSDC(3,2,2,1/2)": (3, 2, 2),
-    "SDC(5,8)": (5, 8, None),
-    "MLSDC(5,3,4,1/2)": (5, 4, 3),
+    # name: (nodes per level, finest first; sweeps (one level) or iterations)
+    "SDC(3,4)": ((3,), 4),
+    "MLSDC(3,2,2,1/2)": ((3, 2), 2),
+    "SDC(5,8)": ((5,), 8),
+    "MLSDC(5,3,4,1/2)": ((5, 3), 4),
 }
+EXTRA_SCHEMES = {  # run on request (--schemes)
+    "MLSDC(5,3,7,1/2)": ((5, 3), 7),
+    "MLSDC(5,3,2,4)": ((5, 3, 2), 4),
+}
+ALL_SCHEMES = {**SCHEMES, **EXTRA_SCHEMES}
 
 
-def fe_evals_per_step(scheme: str) -> tuple[int, int]:
-    """F_E evaluations per step on the fine and the coarse level: the spread
-    evaluates node 0 once; a sweep evaluates every node after the first; an
-    MLSDC iteration adds the restricted coarse nodes 1..M_c and one coarse
-    sweep."""
-    nf, k, nc = SCHEMES[scheme]
-    if nc is None:
-        return 1 + k * (nf - 1), 0
-    return 1 + k * (nf - 1), 1 + k * 2 * (nc - 1)
+def fe_evals_per_step(scheme: str) -> list[int]:
+    """F_E evaluations per step on each level: the spread evaluates node 0
+    once per level; a sweep evaluates every node after the first; an MLSDC
+    iteration adds, on each coarser level, the restricted nodes and one
+    sweep, and on an intermediate level one more sweep going up."""
+    nodes, k = ALL_SCHEMES[scheme]
+    if len(nodes) == 1:
+        return [1 + k * (nodes[0] - 1)]
+    out = [1 + k * (nodes[0] - 1)]
+    for l in range(1, len(nodes)):
+        sweeps = 1 + (1 if l < len(nodes) - 1 else 0)
+        out.append(1 + k * (nodes[l] - 1) * (1 + sweeps))
+    return out
 
 
 class Study:
-    def __init__(self, case: str, R: int, I: int, J: int, Rc: int, Ic: int, Jc: int, omega: float | None = None):
+    def __init__(self, case: str, R: int, I: int, J: int, Rc: int, Ic: int, Jc: int, omega: float | None = None,
+                 third: tuple[int, int, int] | None = None):
         self.case, self.R, self.Rc = case, R, Rc
         g = 9.80616
         if case == "dome":
@@ -62,6 +73,8 @@ class Study:
             self.prm.omega = omega
         self.pf = M.Plan(R, I, J, "fp64")
         self.pc = M.Plan(Rc, Ic, Jc, "fp64", 2)
+        R3, I3, J3 = third if third else (Rc // 2, Ic // 2, Jc // 2)
+        self.p3 = M.Plan(R3, I3, J3, "fp64")
         self.x0 = self._initial_state()
         self.buf = torch.empty_like(self.x0)  # one state buffer, so each step size captures one graph
         self._levels = {}
@@ -82,14 +95,23 @@ class Study:
 
     def _runner(self, scheme: str):
         if scheme not in self._levels:
-            nf, k, nc = SCHEMES[scheme]
-            lf = M.Level(self.pf, nf, self.prm)
-            if nc is None:
-                self._levels[scheme] = (lf,)
+            nodes, k = ALL_SCHEMES[scheme]
+            levels = [M.Level(p, n, self.prm) for p, n in zip((self.pf, self.pc, self.p3), nodes)]
+            if len(levels) == 1:
+                self._levels[scheme] = (levels[0],)
+            elif len(levels) == 2:
+                self._levels[scheme] = (levels, M.MLSDC(*levels))
             else:
-                lc = M.Level(self.pc, nc, self.prm)
-                self._levels[scheme] = (lf, lc, M.MLSDC(lf, lc))
+                self._levels[scheme] = (levels, M.MLSDCLevels(levels))
         return self._levels[scheme]
+
+    def _step(self, scheme, objs, x, dt, k):
+        if len(objs) == 1:
+            M.sdc_step(objs[0], x, dt, k)
+        elif isinstance(objs[1], M.MLSDC):
+            M.mlsdc_step(objs[1], x, dt, k, 1, use_graph=True)
+        else:
+            M.mlsdc_levels_step(objs[1], x, dt, k, 1, use_graph=True)
 
     def run(self, scheme: str, dt: float, seconds: float) -> tuple[torch.Tensor, float, int]:
         """The state after `seconds` of simulated time (a whole number of steps
@@ -97,12 +119,12 @@ class Study:
         steps = int(round(seconds / dt))
         if abs(steps * dt - seconds) > 1e-9 * seconds:
             raise ValueError(f"{seconds} s is not a whole number of steps of {dt} s")
-        nf, k, nc = SCHEMES[scheme]
+        nodes, k = ALL_SCHEMES[scheme]
         objs = self._runner(scheme)
         x = self.buf
-        if nc is not None and (scheme, dt) not in self._captured:
+        if len(nodes) > 1 and (scheme, dt) not in self._captured:
             x.copy_(self.x0)  # capture this step size's graph outside the timed region
-            M.mlsdc_step(objs[2], x, dt, k, 1, use_graph=True)
+            self._step(scheme, objs, x, dt, k)
             self._captured.add((scheme, dt))
         x.copy_(self.x0)
         st = torch.cuda.current_stream()
@@ -110,10 +132,7 @@ class Study:
         torch.cuda.synchronize()
         e0.record(st)
         for _ in range(steps):
-            if nc is None:
-                M.sdc_step(objs[0], x, dt, k)
-            else:
-                M.mlsdc_step(objs[2], x, dt, k, 1, use_graph=True)
+            self._step(scheme, objs, x, dt, k)
         e1.record(st)
         e1.synchronize()
         return x.clone(), e0.elapsed_time(e1), steps
@@ -159,21 +178,21 @@ def main(argv=None):
             d = x - ref
             errs_phi.append(s.linf(d, 0) / norms[0])
             errs_zeta.append(s.linf(d, 1) / norms[1])
-            ff, fc = fe_evals_per_step(scheme)
             rows.append({"scheme": scheme, "dt": dt, "steps": steps, "err_phi": errs_phi[-1],
-                         "err_zeta": errs_zeta[-1], "ms": ms, "fe_fine": ff * steps, "fe_coarse": fc * steps})
+                         "err_zeta": errs_zeta[-1], "ms": ms,
+                         "fe_per_level": [v * steps for v in fe_evals_per_step(scheme)]})
         for r, op, oz in zip(rows[-len(dts):], observed_orders(dts, errs_phi), observed_orders(dts, errs_zeta)):
             r["order_phi"], r["order_zeta"] = op, oz
     out = {"case": a.case, "R": a.R, "grid": [a.nlon, a.nlat], "Rc": a.Rc, "hours": a.hours,
            "reference": {"scheme": "SDC(5,8)", "dt": a.ref_dt, "steps": ref_steps, "ms": ref_ms},
            "phibar": s.prm.phibar, "rows": rows}
     print(json.dumps(out))
-    print(f"| scheme | dt (s) | L_inf err Phi' | order | L_inf err zeta | order | F_E fine/coarse | GPU ms |")
+    print(f"| scheme | dt (s) | L_inf err Phi' | order | L_inf err zeta | order | F_E per level | GPU ms |")
     print("|---|---|---|---|---|---|---|---|")
     for r in rows:
         fo = lambda v: "" if v is None else f"{v:.2f}"
         print(f"| {r['scheme']} | {r['dt']:g} | {r['err_phi']:.2e} | {fo(r['order_phi'])} | {r['err_zeta']:.2e} | "
-              f"{fo(r['order_zeta'])} | {r['fe_fine']}/{r['fe_coarse']} | {r['ms']:.1f} |")
+              f"{fo(r['order_zeta'])} | {' / '.join(str(v) for v in r['fe_per_level'])} | {r['ms']:.1f} |")
 
 
 if __name__ == "__main__":
