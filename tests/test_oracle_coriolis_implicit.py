@@ -150,3 +150,18 @@ def test_mlsdc_order_with_implicit_coriolis(n_iter, lo, hi):
     observed = np.log2(errs[0] / errs[1])
     assert errs[1] > 1e-14
     assert lo < observed < hi, (errs, observed)
+
+
+def test_mean_geopotential_conserved_with_implicit_coriolis():
+    """Phi'^0_0 has no tendency (div V has zero mean and delta^0_0 = 0; L_F
+    and the coupled solve leave the n = 0 row alone): an MLSDC step keeps it."""
+    R, Rc = 10, 5
+    pf, pc = SWECoriolisImplicit(R, 32, 16, P0), SWECoriolisImplicit(Rc, 16, 8, P0)
+    u = inputs.initial_state(R, seed=13)
+    u[0, 0] = 55.0
+    fine, coarse = sdc.Level(pf, 5), sdc.Level(pc, 3)
+    for _ in range(3):
+        u = sdc.mlsdc_step(fine, coarse, u, 600.0, 2, 2)
+    assert abs(u[0, 0] - 55.0) <= 1e-13 * 55.0
+    # delta^0_0 stays zero to the rounding of the dense per-m solve
+    assert abs(u[2, 0]) <= 1e-15 * np.max(np.abs(u[2]))
