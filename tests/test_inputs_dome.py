@@ -36,3 +36,18 @@ def test_peak_symmetry_and_mean():
     # the far side of the sphere (d = 2 a at the antipode) is flat to exp(-4 alpha)
     anti, _ = inputs.gaussian_dome_grid(np.array([lc - np.pi]), np.array([-np.sin(pc)]))
     assert abs(anti[0, 0] - G * inputs.DOME_A * np.exp(-4.0 * inputs.DOME_ALPHA)) < 1e-12 * G * inputs.DOME_A
+
+
+def test_dome_spectrum_closed_forms():
+    """Through the oracle's analysis: the n = 0 coefficient is sqrt(2) times
+    the area mean, which for exp(-alpha (d/a)^2) with (d/a)^2 = 2 (1 - cos
+    theta) is (1 - exp(-4 alpha)) / (4 alpha); the mirror symmetry about the
+    meridian lambda_c = pi makes every coefficient real."""
+    from oracle.sht import Grid
+    exact = np.sqrt(2.0) * G * inputs.DOME_A * (1.0 - np.exp(-4.0 * inputs.DOME_ALPHA)) / (4.0 * inputs.DOME_ALPHA)
+    for R, I, J in [(21, 64, 32), (42, 128, 64)]:
+        grid = Grid(R, I, J)
+        phi, _ = inputs.gaussian_dome_grid(grid.lam, grid.mu)
+        s = grid.analysis(phi)
+        assert abs(s[0] - exact) <= 1e-14 * exact
+        assert np.max(np.abs(s.imag)) <= 1e-12 * np.max(np.abs(s))
