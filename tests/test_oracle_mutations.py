@@ -222,3 +222,84 @@ def test_dropped_restricted_tau_in_three_levels_is_caught(monkeypatch):
     exec(planted, ns)
     monkeypatch.setattr(sdc, "mlsdc_step_levels", ns["mlsdc_step_levels"])
     _fails(T_lv.test_three_levels_reach_the_fine_collocation_solution)
+
+
+# ---- F_I's terms (tests/test_oracle_implicit_terms.py) ----------------------
+import test_oracle_implicit_terms as T_fi  # noqa: E402
+
+
+def test_consistent_anti_diffusion_is_caught(monkeypatch):
+    """-nu lap in F_I and the matching solve (c = 1 + alpha nu L): the solve
+    still inverts its F_I, so only the forward pins of F_I's terms can see it."""
+    def rhs(self, x):
+        p, L = self.p, self.L
+        phi, zeta, delta = x
+        return np.stack([-p.phibar * delta - p.nu * L * phi,
+                         -p.nu * L * zeta,
+                         -L * phi - p.nu * L * delta])
+
+    def solve(self, b, alpha):
+        p, L = self.p, self.L
+        c = 1.0 + alpha * p.nu * L
+        zeta = b[1] / c
+        phi = (c * b[0] - alpha * p.phibar * b[2]) / (c * c - alpha * alpha * p.phibar * L)
+        delta = (b[2] - alpha * L * phi) / c
+        return np.stack([phi, zeta, delta])
+    monkeypatch.setattr(swe.SWE, "implicit_rhs", rhs)
+    monkeypatch.setattr(swe.SWE, "implicit_solve", solve)
+    T_swe.test_implicit_solve_matches_dense_solve()       # consistent: the solve pin passes
+    _fails(T_fi.test_diffusion_is_nu_div_grad, 10, 32, 16)
+    _fails(T_fi.test_full_tendency_matches_the_grid_form, 10, 32, 16)
+    _fails(T_fi.test_diffusion_decay_rate, 3, 4)
+
+
+def test_consistent_flip_of_the_mean_geopotential_flux_is_caught(monkeypatch):
+    """+Phibar delta in the Phi' row of F_I and the matching solve."""
+    def rhs(self, x):
+        p, L = self.p, self.L
+        phi, zeta, delta = x
+        return np.stack([p.phibar * delta + p.nu * L * phi,
+                         p.nu * L * zeta,
+                         -L * phi + p.nu * L * delta])
+
+    def solve(self, b, alpha):
+        p, L = self.p, self.L
+        c = 1.0 - alpha * p.nu * L
+        zeta = b[1] / c
+        phi = (c * b[0] + alpha * p.phibar * b[2]) / (c * c + alpha * alpha * p.phibar * L)
+        delta = (b[2] - alpha * L * phi) / c
+        return np.stack([phi, zeta, delta])
+    monkeypatch.setattr(swe.SWE, "implicit_rhs", rhs)
+    monkeypatch.setattr(swe.SWE, "implicit_solve", solve)
+    T_swe.test_implicit_solve_matches_dense_solve()
+    _fails(T_fi.test_gravity_wave_dispersion_relation, 2, 3)
+    _fails(T_fi.test_full_tendency_matches_the_grid_form, 10, 32, 16)
+
+
+def test_flipped_pressure_gradient_term_is_caught(monkeypatch):
+    """+lap Phi' in the delta row of F_I (and the matching solve): the wave
+    equation's product of the two coupling terms changes sign."""
+    def rhs(self, x):
+        p, L = self.p, self.L
+        phi, zeta, delta = x
+        return np.stack([-p.phibar * delta + p.nu * L * phi,
+                         p.nu * L * zeta,
+                         L * phi + p.nu * L * delta])
+    monkeypatch.setattr(swe.SWE, "implicit_rhs", rhs)
+    _fails(T_fi.test_gravity_wave_dispersion_relation, 2, 3)
+    _fails(T_fi.test_full_tendency_matches_the_grid_form, 10, 32, 16)
+
+
+def test_wrong_nu_value_is_caught(monkeypatch):
+    orig = swe.SWE.implicit_rhs
+
+    def rhs(self, x):
+        p = self.p
+        self.p = swe.Params(p.a, p.omega, p.g, p.phibar, p.nu * 2.0)
+        try:
+            return orig(self, x)
+        finally:
+            self.p = p
+    monkeypatch.setattr(swe.SWE, "implicit_rhs", rhs)
+    _fails(T_fi.test_diffusion_is_nu_div_grad, 10, 32, 16)
+    _fails(T_fi.test_diffusion_decay_rate, 0, 2)
