@@ -23,7 +23,9 @@
  * Node arrays ("space-time vectors", Sec. 4.2): [M+1][3][N_c] complex.
  *
  * Memory: every data pointer is a DEVICE pointer owned by the caller, 16-byte
- * aligned, contiguous.  Plans, levels and MLSDC objects own their tables and
+ * aligned, contiguous.  The entry points that take complex arrays refuse a
+ * pointer that is not 16-byte aligned with MLSDC_ERR_INVALID (the argument
+ * named in mlsdc_last_error()) before any launch.  Plans, levels and MLSDC objects own their tables and
  * scratch (allocated at creation, freed at destroy).  Calls are asynchronous
  * on the given CUDA stream (NULL = legacy default stream); calls that share a
  * plan, level or MLSDC object must be ordered on one stream, since they share
@@ -169,10 +171,16 @@ mlsdc_status sh_inverse(sh_plan_t plan, const double* spec, double* grid, int nf
  * nlat even, nlat >= (3R+1)/2, nlat <= 2048), 1 <= nf <= 16, and
  * nf * nlat * (R+1) <= 261120 (e.g. nf <= 5 at T170 on 512 x 256); larger
  * requests return MLSDC_ERR_INVALID with the limit in mlsdc_last_error().
- * spec: [nf][N_c] complex, grid: [nf][nlat][nlon] (caller-owned device memory).
- * The first call on each device looks up the static array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call before
- * any stream capture.  All calls share the one array and it keeps the last
+ * spec: [nf][N_c] complex, grid: [nf][nlat][nlon] (caller-owned device memory,
+ * both 16-byte aligned: a pointer at an odd double offset is refused with
+ * MLSDC_ERR_INVALID before any launch).  Every invalid argument sets a
+ * message in mlsdc_last_error().
+ * Every call made outside stream capture looks up the static array's device
+ * address (cudaGetSymbolAddress) with the current device, so the address stays
+ * right after a cudaDeviceReset reloads the module; a call under capture
+ * reuses the address found by the last uncaptured call on that device, so
+ * make a first call on each device before any stream capture (and again after
+ * a device reset, before capturing).  All calls share the one array and it keeps the last
  * call's contents; every value a call reads from it is written earlier in
  * the same call, so nothing needs clearing, but calls that overlap on the GPU
  * (different streams, or different host threads, at the same time) race on

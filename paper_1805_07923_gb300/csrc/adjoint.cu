@@ -853,6 +853,7 @@ extern "C" mlsdc_status mlsdc_adjoint_destroy(mlsdc_adjoint_t A) {
 extern "C" mlsdc_status mlsdc_adjoint_forward(mlsdc_adjoint_t A, const double* state0, double* state_T, int use_graph,
                                               void* stream) {
     if (!A || !state0 || !state_T) return MLSDC_ERR_INVALID;
+    MLSDC_ALIGNED("mlsdc_adjoint_forward", {"state0", state0}, {"state_T", state_T});
     cudaStream_t st = (cudaStream_t)stream;
     const size_t bytes = A->ml->f->node() * sizeof(double2);
     MLSDC_CUDA(cudaMemcpyAsync(A->work, state0, bytes, cudaMemcpyDeviceToDevice, st));
@@ -871,6 +872,7 @@ extern "C" mlsdc_status mlsdc_adjoint_forward(mlsdc_adjoint_t A, const double* s
 extern "C" mlsdc_status mlsdc_adjoint_backward(mlsdc_adjoint_t A, const double* lambda_T, double* lambda_0,
                                                int use_graph, void* stream) {
     if (!A || !lambda_T || !lambda_0) return MLSDC_ERR_INVALID;
+    MLSDC_ALIGNED("mlsdc_adjoint_backward", {"lambda_T", lambda_T}, {"lambda_0", lambda_0});
     if (!A->have_forward) {
         set_error_text("mlsdc_adjoint_backward: no forward run has stored the checkpoints");
         return MLSDC_ERR_INVALID;
@@ -913,6 +915,7 @@ extern "C" mlsdc_status mlsdc_adjoint_launch_count(mlsdc_adjoint_t A, int64_t* f
 extern "C" mlsdc_status swe_explicit_rhs_adjoint(sh_plan_t p, const swe_params* prm, const double* state,
                                                  double* lambda, double* state_bar, void* stream) {
     if (!p || !prm || !state || !lambda || !state_bar) return MLSDC_ERR_INVALID;
+    MLSDC_ALIGNED("swe_explicit_rhs_adjoint", {"state", state}, {"lambda", lambda}, {"state_bar", state_bar});
     if (p->precision != MLSDC_FP64 || state_bar == lambda || state_bar == state || lambda == state)
         return MLSDC_ERR_INVALID;
     mlsdc_status s = fe_adjoint_prepare(p);
@@ -925,6 +928,7 @@ extern "C" mlsdc_status mlsdc_profile_rhs_adjoint(sh_plan_t p, const swe_params*
                                                   double* lambda, double* state_bar, int reps, float* ms_host,
                                                   void* stream) {
     if (!p || !prm || !state || !lambda || !state_bar || reps < 1 || !ms_host) return MLSDC_ERR_INVALID;
+    MLSDC_ALIGNED("mlsdc_profile_rhs_adjoint", {"state", state}, {"lambda", lambda}, {"state_bar", state_bar});
     if (p->precision != MLSDC_FP64 || state_bar == lambda || state_bar == state || lambda == state)
         return MLSDC_ERR_INVALID;
     cudaStream_t st = (cudaStream_t)stream;
@@ -959,6 +963,7 @@ extern "C" mlsdc_status mlsdc_profile_rhs_adjoint(sh_plan_t p, const swe_params*
 extern "C" mlsdc_status mlsdc_phi_misfit(sh_plan_t p, const double* state, const double* phi_target, double* J,
                                          double* lambda, void* stream) {
     if (!p || !state || !phi_target || !J || !lambda) return MLSDC_ERR_INVALID;
+    MLSDC_ALIGNED("mlsdc_phi_misfit", {"state", state}, {"phi_target", phi_target}, {"lambda", lambda});
     k_misfit<<<1, 1024, 0, (cudaStream_t)stream>>>((const double2*)state, (const double2*)phi_target, p->R, p->nc, J,
                                                    (double2*)lambda);
     MLSDC_LAUNCHED("k_misfit");

@@ -459,6 +459,7 @@ using namespace mlsdc;
 extern "C" mlsdc_status swe_implicit_rhs_ex(sh_plan_t p, const swe_params* prm, const double* state, double* FI,
                                             int options, void* stream) {
     if (!p || !prm || !state || !FI || (options & ~MLSDC_CORIOLIS_IMPLICIT)) return MLSDC_ERR_INVALID;
+    MLSDC_ALIGNED("swe_implicit_rhs_ex", {"state", state}, {"FI", FI});
     if (!(options & MLSDC_CORIOLIS_IMPLICIT)) return swe_implicit_rhs(p, prm, state, FI, stream);
     k_implicit_rhs_cor<<<dim3(p->R + 1, 1), kCorThreads, 0, (cudaStream_t)stream>>>(
         (const double2*)state, (double2*)FI, p->d_cor, p->R, p->nc, phys_of(*prm), 2.0 * prm->omega, 0);
@@ -469,6 +470,7 @@ extern "C" mlsdc_status swe_implicit_rhs_ex(sh_plan_t p, const swe_params* prm, 
 extern "C" mlsdc_status swe_implicit_solve_ex(sh_plan_t p, const swe_params* prm, double alpha, const double* b,
                                               double* x, int options, void* stream) {
     if (!p || !prm || !b || !x || !(alpha >= 0.0) || (options & ~MLSDC_CORIOLIS_IMPLICIT)) return MLSDC_ERR_INVALID;
+    MLSDC_ALIGNED("swe_implicit_solve_ex", {"b", b}, {"x", x});
     if (!(options & MLSDC_CORIOLIS_IMPLICIT)) return swe_implicit_solve(p, prm, alpha, b, x, stream);
     cudaStream_t st = (cudaStream_t)stream;
     mlsdc_status s = cor_smem_limits(p->R);

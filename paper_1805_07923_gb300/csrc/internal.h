@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <initializer_list>
 #include <string>
 #include <utility>
 #include <vector>
@@ -16,6 +17,21 @@ namespace mlsdc {
 // thread-local text of the last CUDA error
 void set_error(const char* where, cudaError_t e);
 void set_error_text(const std::string& s);
+
+// Record why an argument was refused; returns MLSDC_ERR_INVALID.
+mlsdc_status invalid_arg(const std::string& why);
+
+// The kernels read complex arrays as 16-byte double2 words, so a device
+// pointer at an odd double offset (a flat float64 view sliced at [1:], say)
+// would fault on the GPU.  Entry points refuse such pointers before any
+// launch: MLSDC_ERR_INVALID with the offending argument named.  Null
+// pointers pass here (each entry point checks those itself).
+mlsdc_status check_aligned16(const char* where, std::initializer_list<std::pair<const char*, const void*>> ptrs);
+#define MLSDC_ALIGNED(where, ...)                                          \
+    do {                                                                   \
+        mlsdc_status s_ = ::mlsdc::check_aligned16(where, {__VA_ARGS__});  \
+        if (s_ != MLSDC_OK) return s_;                                     \
+    } while (0)
 
 #define MLSDC_CUDA(call)                                  \
     do {                                                  \

@@ -18,6 +18,18 @@ void set_error(const char* where, cudaError_t e) {
 }
 void set_error_text(const std::string& s) { g_last_error = s; }
 
+mlsdc_status invalid_arg(const std::string& why) {
+    g_last_error = why;
+    return MLSDC_ERR_INVALID;
+}
+
+mlsdc_status check_aligned16(const char* where, std::initializer_list<std::pair<const char*, const void*>> ptrs) {
+    for (const auto& pr : ptrs)
+        if (((uintptr_t)pr.second & 15u) != 0)
+            return invalid_arg(std::string(where) + ": " + pr.first + " is not 16-byte aligned");
+    return MLSDC_OK;
+}
+
 bool pdl_enabled() {
     // Off by default: measured inside the step's CUDA graph on GB300, the
     // programmatic edges made the step slower (565 -> 465 steps/s split-BF16,

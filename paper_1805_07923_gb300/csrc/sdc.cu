@@ -474,12 +474,14 @@ struct mlsdc_ensemble_s {
 extern "C" mlsdc_status swe_implicit_rhs(sh_plan_t p, const swe_params* prm, const double* state, double* FI,
                                          void* stream) {
     if (!p || !prm || !state || !FI) return MLSDC_ERR_INVALID;
+    MLSDC_ALIGNED("swe_implicit_rhs", {"state", state}, {"FI", FI});
     return implicit_rhs_launch(p, prm, state, FI, (cudaStream_t)stream);
 }
 
 extern "C" mlsdc_status swe_implicit_solve(sh_plan_t p, const swe_params* prm, double alpha, const double* b,
                                            double* x, void* stream) {
     if (!p || !prm || !b || !x || !(alpha >= 0.0)) return MLSDC_ERR_INVALID;
+    MLSDC_ALIGNED("swe_implicit_solve", {"b", b}, {"x", x});
     k_implicit_solve<<<grid_for(p->nc), 256, 0, (cudaStream_t)stream>>>((const double2*)b, (double2*)x, p->d_ndeg,
                                                                        p->nc, alpha, phys_of(*prm));
     MLSDC_LAUNCHED("k_implicit_solve");
@@ -608,12 +610,15 @@ extern "C" mlsdc_status sdc_sweep(sdc_level_t L, double dt, double* Theta, const
                                   void* stream) {
     if (!L || !Theta || !FI_old || !FE_old || !FI_new || !FE_new) return MLSDC_ERR_INVALID;
     if (FI_old == FI_new || FE_old == FE_new) return MLSDC_ERR_INVALID;
+    MLSDC_ALIGNED("sdc_sweep", {"Theta", Theta}, {"FI_old", FI_old}, {"FE_old", FE_old}, {"FI_new", FI_new},
+                  {"FE_new", FE_new}, {"tau", tau});
     return sweep(L, dt, (double2*)Theta, (const double2*)FI_old, (const double2*)FE_old, (double2*)FI_new,
                  (double2*)FE_new, (const double2*)tau, (cudaStream_t)stream);
 }
 
 extern "C" mlsdc_status sdc_step(sdc_level_t L, double* state, double dt, int n_sweeps, void* stream) {
     if (!L || !state || n_sweeps < 0) return MLSDC_ERR_INVALID;
+    MLSDC_ALIGNED("sdc_step", {"state", state});
     cudaStream_t st = (cudaStream_t)stream;
     L->launches = 0;
     mlsdc_status s;
@@ -1011,6 +1016,7 @@ static mlsdc_status capture(cudaStream_t cap, cudaGraphExec_t* out, Enqueue enqu
 extern "C" mlsdc_status mlsdc_step(mlsdc_t ml, double* state, double dt, int n_iter, int n_coarse_sweeps,
                                    int use_graph, void* stream) {
     if (!ml || !state || n_iter < 0 || n_coarse_sweeps < 0) return MLSDC_ERR_INVALID;
+    MLSDC_ALIGNED("mlsdc_step", {"state", state});
     cudaStream_t st = (cudaStream_t)stream;
     mlsdc_status sp = prepare_levels(ml, dt, st);
     if (sp != MLSDC_OK) return sp;
@@ -1092,6 +1098,7 @@ static mlsdc_status levels_enqueue(mlsdc_levels_t h, double* state, double dt, i
 extern "C" mlsdc_status mlsdc_levels_step(mlsdc_levels_t h, double* state, double dt, int n_iter, int n_coarse_sweeps,
                                           int use_graph, void* stream) {
     if (!h || !state || n_iter < 0 || n_coarse_sweeps < 0) return MLSDC_ERR_INVALID;
+    MLSDC_ALIGNED("mlsdc_levels_step", {"state", state});
     cudaStream_t st = (cudaStream_t)stream;
     for (mlsdc_t p : h->pairs) {
         mlsdc_status sp = prepare_levels(p, dt, st);
@@ -1191,8 +1198,10 @@ extern "C" mlsdc_status mlsdc_ensemble_step(mlsdc_ensemble_t e, double* const* s
                                             int n_coarse_sweeps, int use_graph, void* stream) {
     if (!e || !states || n_iter < 0 || n_coarse_sweeps < 0) return MLSDC_ERR_INVALID;
     std::vector<double*> sv(states, states + e->groups.size());
-    for (double* p : sv)
+    for (double* p : sv) {
         if (!p) return MLSDC_ERR_INVALID;
+        MLSDC_ALIGNED("mlsdc_ensemble_step", {"states[i]", p});
+    }
     cudaStream_t st = (cudaStream_t)stream;
     for (mlsdc_t ml : e->groups) {
         mlsdc_status sp = prepare_levels(ml, dt, st);

@@ -7,6 +7,7 @@
 // FFTs) lives in the file-scope device array g_static_scratch below.  That
 // array is part of the loaded module: every GPU that loads this library holds
 // its kStaticScratchBytes until the process exits.
+#include <cfloat>
 #include <cmath>
 #include <mutex>
 
@@ -25,8 +26,10 @@ constexpr size_t kStaticFourierMax = (kStaticScratchBytes - kStaticLatDoubles * 
 
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
-// Host-side device addresses of g_static_scratch, one per device, filled on
-// the first call made on that device.
+// Host-side device addresses of g_static_scratch, one per device.  Outside
+// stream capture every call looks the address up again (a cudaDeviceReset
+// reloads the module, and the array may then sit elsewhere); under capture
+// the address recorded by the last uncaptured call on that device is used.
 std::mutex g_static_mu;
 void* g_static_ptr[kStaticMaxDevices] = {nullptr};
 
@@ -52,7 +55,9 @@ __global__ void k_static_latitudes(double* lat, int J) {
         dp = J * (x * p1 - p0) / (x * x - 1.0);
         const double dx = p1 / dp;
         x -= dx;
-        if (fabs(dx) < 1e-16) break;
+        // relative stop: near the poles one ulp of x is ~1.1e-16, so an
+        // absolute 1e-16 test could run every iteration of the O(J) loop
+        if (fabs(dx) <= 4.0 * DBL_EPSILON * fabs(x)) break;
     }
     p0 = 1.0;
     p1 = x;
@@ -150,17 +155,26 @@ __global__ void k_static_irfft(const double2* __restrict__ four, double* __restr
     for (int k = threadIdx.x; k < Hn; k += blockDim.x) g[k] = sz[k];
 }
 
-// The device address of g_static_scratch on the current device (set-up on
-// the first call per device).
-mlsdc_status static_scratch(void** out) {
+// The device address of g_static_scratch on the current device.  Looked up
+// (cudaGetSymbolAddress, with the device current) on every call made
+// outside stream capture; a call under capture reuses the address of the
+// last uncaptured call on that device and fails if there was none.
+mlsdc_status static_scratch(cudaStream_t st, void** out) {
     int dev = 0;
     MLSDC_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= kStaticMaxDevices) return MLSDC_ERR_INVALID;
+    if (dev < 0 || dev >= kStaticMaxDevices)
+        return invalid_arg("sh_inverse_static: device ordinal beyond " + std::to_string(kStaticMaxDevices));
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    const cudaError_t qe = cudaStreamIsCapturing(st, &cs);
+    if (qe != cudaSuccess) (void)cudaGetLastError();  // not this call's launch error; treated as capture
+    const bool capturing = qe != cudaSuccess || cs != cudaStreamCaptureStatusNone;
     std::lock_guard<std::mutex> lock(g_static_mu);
-    if (!g_static_ptr[dev]) {
+    if (!capturing) {
         void* p = nullptr;
         MLSDC_CUDA(cudaGetSymbolAddress(&p, g_static_scratch));
         g_static_ptr[dev] = p;
+    } else if (!g_static_ptr[dev]) {
+        return invalid_arg("sh_inverse_static: the first call on a device must be made outside stream capture");
     }
     *out = g_static_ptr[dev];
     return MLSDC_OK;
@@ -173,20 +187,25 @@ using namespace mlsdc;
 
 extern "C" mlsdc_status sh_inverse_static(int R, int nlon, int nlat, const double* spec, double* grid, int nf,
                                           void* stream) {
-    if (!spec || !grid || nf < 1 || nf > kMaxFields) return MLSDC_ERR_INVALID;
-    if (R < 1 || nlon < 16 || nlon > 1024 || (nlon & (nlon - 1)) != 0 || nlon < 3 * R + 1) return MLSDC_ERR_INVALID;
-    if (nlat < 2 || nlat % 2 != 0 || 2 * nlat < 3 * R + 1 || nlat / 2 > kStaticMaxHalfLat) return MLSDC_ERR_INVALID;
-    if ((size_t)nf * nlat * (R + 1) > kStaticFourierMax) {
-        set_error_text("sh_inverse_static: nf * nlat * (R+1) exceeds the static scratch of " +
-                       std::to_string(kStaticFourierMax) + " complex values");
-        return MLSDC_ERR_INVALID;
-    }
+    if (!spec || !grid) return invalid_arg("sh_inverse_static: spec and grid must not be null");
+    if (nf < 1 || nf > kMaxFields)
+        return invalid_arg("sh_inverse_static: nf must be in [1, " + std::to_string(kMaxFields) + "]");
+    if (R < 1) return invalid_arg("sh_inverse_static: R must be >= 1");
+    if (nlon < 16 || nlon > 1024 || (nlon & (nlon - 1)) != 0 || nlon < 3 * R + 1)
+        return invalid_arg("sh_inverse_static: nlon must be a power of two in [16, 1024] and >= 3R+1");
+    if (nlat < 2 || nlat % 2 != 0 || 2 * nlat < 3 * R + 1 || nlat / 2 > kStaticMaxHalfLat)
+        return invalid_arg("sh_inverse_static: nlat must be even, >= (3R+1)/2 and <= " +
+                           std::to_string(2 * kStaticMaxHalfLat));
+    if ((size_t)nf * nlat * (R + 1) > kStaticFourierMax)
+        return invalid_arg("sh_inverse_static: nf * nlat * (R+1) exceeds the static scratch of " +
+                           std::to_string(kStaticFourierMax) + " complex values");
+    MLSDC_ALIGNED("sh_inverse_static", {"spec", spec}, {"grid", grid});
+    cudaStream_t st = (cudaStream_t)stream;
     void* base = nullptr;
-    mlsdc_status s = static_scratch(&base);
+    mlsdc_status s = static_scratch(st, &base);
     if (s != MLSDC_OK) return s;
     double* lat = (double*)base;
     double2* four = (double2*)((double*)base + kStaticLatDoubles);
-    cudaStream_t st = (cudaStream_t)stream;
     const int J2 = nlat / 2;
     const int nc = nc_of(R);
     k_static_latitudes<<<(J2 + 63) / 64, 64, 0, st>>>(lat, nlat);

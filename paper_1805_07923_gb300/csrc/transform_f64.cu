@@ -158,6 +158,7 @@ using namespace mlsdc;
 
 extern "C" mlsdc_status sh_inverse(sh_plan_t p, const double* spec, double* grid, int nf, void* stream) {
     if (!p || !spec || !grid || nf < 1 || nf > kMaxFields) return MLSDC_ERR_INVALID;
+    MLSDC_ALIGNED("sh_inverse", {"spec", spec}, {"grid", grid});
     cudaStream_t st = (cudaStream_t)stream;
     const int R = p->R;
     dim3 gs(p->n_synth, nf);
@@ -173,6 +174,7 @@ extern "C" mlsdc_status sh_inverse(sh_plan_t p, const double* spec, double* grid
 
 extern "C" mlsdc_status sh_forward(sh_plan_t p, const double* grid, double* spec, int nf, void* stream) {
     if (!p || !spec || !grid || nf < 1 || nf > kMaxFields) return MLSDC_ERR_INVALID;
+    MLSDC_ALIGNED("sh_forward", {"grid", grid}, {"spec", spec});
     cudaStream_t st = (cudaStream_t)stream;
     const int R = p->R;
     const int rows = nf * p->J;
@@ -188,6 +190,7 @@ extern "C" mlsdc_status sh_forward(sh_plan_t p, const double* grid, double* spec
 extern "C" mlsdc_status swe_explicit_rhs(sh_plan_t p, const swe_params* prm, const double* state, double* FE,
                                          void* stream) {
     if (!p || !prm || !state || !FE || state == FE) return MLSDC_ERR_INVALID;
+    MLSDC_ALIGNED("swe_explicit_rhs", {"state", state}, {"FE", FE});
     cudaStream_t st = (cudaStream_t)stream;
     if (p->precision == MLSDC_FP64) return rhs_explicit_f64(p, prm, state, FE, st, nullptr, -1);
     return rhs_explicit_mp(p, prm, state, FE, st, nullptr, -1);
@@ -197,6 +200,7 @@ extern "C" mlsdc_status swe_explicit_rhs_batched(sh_plan_t p, const swe_params* 
                                                  int members, void* stream) {
     if (!p || !prm || !states || !FE || states == FE || members < 1 || members > p->max_members)
         return MLSDC_ERR_INVALID;
+    MLSDC_ALIGNED("swe_explicit_rhs_batched", {"states", states}, {"FE", FE});
     RhsBatch b;
     b.members = members;
     b.state_ms = b.fe_ms = (size_t)3 * p->nc;
@@ -213,6 +217,7 @@ extern "C" mlsdc_status mlsdc_profile_rhs(sh_plan_t p, const swe_params* prm, co
 extern "C" mlsdc_status mlsdc_profile_rhs_batched(sh_plan_t p, const swe_params* prm, const double* state, double* FE,
                                                   int members, int reps, float* ms_host, void* stream) {
     if (!p || !prm || !state || !FE || state == FE || reps < 1 || !ms_host) return MLSDC_ERR_INVALID;
+    MLSDC_ALIGNED("mlsdc_profile_rhs", {"state", state}, {"FE", FE});
     if (members < 1 || members > p->max_members) return MLSDC_ERR_INVALID;
     cudaStream_t st = (cudaStream_t)stream;
     RhsBatch b;

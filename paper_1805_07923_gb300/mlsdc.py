@@ -131,6 +131,8 @@ def _ptr(t: torch.Tensor | None, numel_f64: int | None = None):
         raise MlsdcError(f"tensor must be float64 or complex128, got {t.dtype}")
     if not t.is_contiguous():
         raise MlsdcError("tensor must be contiguous")
+    if t.data_ptr() % 16 != 0:
+        raise MlsdcError("tensor data must be 16-byte aligned (complex values are read as 16-byte words)")
     if numel_f64 is not None:
         n = t.numel() * (2 if t.dtype == torch.complex128 else 1)
         if n < numel_f64:

@@ -59,3 +59,41 @@ def test_invalid_sizes_are_rejected_without_a_gpu(lib_path):
     assert lib.sh_plan(21, 64, 32, 7, ctypes.byref(h)) == -1         # precision
     lib.mlsdc_status_string.restype = ctypes.c_char_p
     assert lib.mlsdc_status_string(-1) == b"invalid argument"
+
+
+def test_static_inverse_argument_errors_name_the_problem(lib_path):
+    """sh_inverse_static refuses bad sizes and pointers that are not 16-byte
+    aligned before any CUDA call, each with its own message (the pointers
+    here are never dereferenced)."""
+    lib = ctypes.CDLL(lib_path)
+    lib.mlsdc_last_error.restype = ctypes.c_char_p
+    f = lib.sh_inverse_static
+    f.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                  ctypes.c_void_p]
+    good, odd = 0x10000, 0x10008
+    assert f(21, 60, 32, good, good, 1, None) == -1
+    assert b"nlon" in lib.mlsdc_last_error()
+    assert f(21, 64, 31, good, good, 1, None) == -1
+    assert b"nlat" in lib.mlsdc_last_error()
+    assert f(21, 64, 32, good, good, 0, None) == -1
+    assert b"nf" in lib.mlsdc_last_error()
+    assert f(21, 64, 32, None, good, 1, None) == -1
+    assert b"null" in lib.mlsdc_last_error()
+    assert f(21, 64, 32, odd, good, 1, None) == -1
+    assert b"spec is not 16-byte aligned" in lib.mlsdc_last_error()
+    assert f(21, 64, 32, good, odd, 1, None) == -1
+    assert b"grid is not 16-byte aligned" in lib.mlsdc_last_error()
+
+
+def test_planned_entry_points_refuse_misaligned_pointers(lib_path):
+    """The alignment check runs before the plan is touched, so a fake plan
+    handle is never dereferenced either."""
+    lib = ctypes.CDLL(lib_path)
+    lib.mlsdc_last_error.restype = ctypes.c_char_p
+    fake_plan, good, odd = 0x20000, 0x10000, 0x10008
+    lib.sh_inverse.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
+    assert lib.sh_inverse(fake_plan, odd, good, 1, None) == -1
+    assert b"sh_inverse: spec is not 16-byte aligned" in lib.mlsdc_last_error()
+    lib.sh_forward.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
+    assert lib.sh_forward(fake_plan, good, odd, 1, None) == -1
+    assert b"sh_forward: spec is not 16-byte aligned" in lib.mlsdc_last_error()

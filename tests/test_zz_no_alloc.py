@@ -29,7 +29,8 @@ def _c_call(R, I, J, spec, grid, nf):
     return lib.sh_inverse_static(R, I, J, ctypes.c_void_p(spec.data_ptr()), ctypes.c_void_p(grid.data_ptr()), nf, st)
 
 
-@pytest.mark.parametrize("R,I,J,nf", [(21, 64, 32, 3), (170, 512, 256, 5), (45, 256, 70, 2)])
+# (169, 512, 384, 4): nf * nlat * (R+1) = 261120, exactly the scratch's capacity
+@pytest.mark.parametrize("R,I,J,nf", [(21, 64, 32, 3), (170, 512, 256, 5), (45, 256, 70, 2), (169, 512, 384, 4)])
 def test_static_inverse_matches_planned_inverse_twice(R, I, J, nf):
     plan = M.Plan(R, I, J)
     for call in range(2):
@@ -46,8 +47,29 @@ def test_static_inverse_matches_planned_inverse_twice(R, I, J, nf):
 
 
 def test_static_inverse_rejects_requests_beyond_its_scratch():
-    R, I, J, nf = 170, 512, 256, 6          # 6 * 256 * 171 > 261120 complex values
-    spec = torch.zeros((nf, M.n_coeffs(R)), dtype=torch.complex128, device="cuda")
-    grid = torch.zeros((nf, J, I), dtype=torch.float64, device="cuda")
-    assert _c_call(R, I, J, spec, grid, nf) == -1
-    assert b"static scratch" in M.lib().mlsdc_last_error()
+    for R, I, J, nf in [(170, 512, 256, 6),     # 6 * 256 * 171 > 261120 complex values
+                        (169, 512, 386, 4)]:    # 4 * 386 * 170 = 262480, just beyond
+        spec = torch.zeros((nf, M.n_coeffs(R)), dtype=torch.complex128, device="cuda")
+        grid = torch.zeros((nf, J, I), dtype=torch.float64, device="cuda")
+        assert _c_call(R, I, J, spec, grid, nf) == -1
+        assert b"static scratch" in M.lib().mlsdc_last_error()
+
+
+def test_static_inverse_allocates_nothing():
+    """After a first call (which loads the module and its static array), a
+    call changes neither the device's free memory nor torch's allocator."""
+    R, I, J, nf = 85, 256, 128, 3
+    spec = torch.from_numpy(np.stack([inputs.spectrum(R, 700 + k, k, 1.0) for k in range(nf)])).cuda()
+    grid = torch.empty((nf, J, I), dtype=torch.float64, device="cuda")
+    assert _c_call(R, I, J, spec, grid, nf) == 0
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    stats0 = torch.cuda.memory_stats()
+    for _ in range(3):
+        assert _c_call(R, I, J, spec, grid, nf) == 0
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    stats1 = torch.cuda.memory_stats()
+    assert free1 == free0
+    for key in ("allocation.all.allocated", "segment.all.allocated"):
+        assert stats1.get(key, 0) == stats0.get(key, 0), key
