@@ -303,3 +303,55 @@ def test_wrong_nu_value_is_caught(monkeypatch):
     monkeypatch.setattr(swe.SWE, "implicit_rhs", rhs)
     _fails(T_fi.test_diffusion_is_nu_div_grad, 10, 32, 16)
     _fails(T_fi.test_diffusion_decay_rate, 0, 2)
+
+
+# ---- PFASST (tests/test_oracle_pfasst.py) ------------------------------------
+import test_oracle_pfasst as T_pf  # noqa: E402
+from oracle import pfasst as opf  # noqa: E402
+
+
+def _planted_pfasst(monkeypatch, old, new):
+    import inspect
+    src = inspect.getsource(opf.pfasst)
+    assert old in src
+    ns = dict(vars(opf))
+    exec(src.replace(old, new), ns)
+    monkeypatch.setattr(opf, "pfasst", ns["pfasst"])
+
+
+def _pf_fixtures():
+    from oracle import sdc as osdc
+    from oracle.swe import SWE, Params
+    from paper_1805_07923_gb300 import inputs
+    fine = osdc.Level(SWE(T_pf.RF, 32, 16, Params()), 3)
+    coarse = osdc.Level(SWE(T_pf.RC, 16, 8, Params()), 2)
+    u, seq = inputs.initial_state(T_pf.RF), []
+    for _ in range(T_pf.P):
+        u = osdc.sdc_step(fine, u, T_pf.DT, 60)
+        seq.append(u)
+    return (fine, coarse), seq
+
+
+def test_pfasst_without_coarse_initial_value_is_caught(monkeypatch):
+    _planted_pfasst(monkeypatch, "            if p >= 1:\n                Th_c, FI_c, FE_c = with_node0(coarse, Th_c, "
+                    "FI_c, FE_c, coarse_end)\n", "")
+    lv, seq = _pf_fixtures()
+    _fails(T_pf.test_identical_levels_one_iteration_is_serial_collocation, lv, seq)
+
+
+def test_pfasst_without_fine_initial_value_is_caught(monkeypatch):
+    _planted_pfasst(monkeypatch, "            if p >= 1 and k >= 1:\n", "            if False:\n")
+    lv, seq = _pf_fixtures()
+    _fails(T_pf.test_converges_to_serial_collocation, lv, seq)
+
+
+def test_pfasst_without_tau_is_caught(monkeypatch):
+    _planted_pfasst(monkeypatch, "sweep(coarse, dt, Th_c, FI_c, FE_c, tau)", "sweep(coarse, dt, Th_c, FI_c, FE_c)")
+    lv, _ = _pf_fixtures()
+    _fails(T_pf.test_one_slice_is_mlsdc, lv)
+
+
+def test_pfasst_without_F_interpolation_is_caught(monkeypatch):
+    _planted_pfasst(monkeypatch, "                FE_f[m] = FE_f[m] + interpolate_node(dE, m)\n", "")
+    lv, _ = _pf_fixtures()
+    _fails(T_pf.test_first_slice_is_mlsdc, lv)
