@@ -12,11 +12,11 @@ Predictor.  Every slice's fine nodes start as u0 spread.  The coarse level is
 run serially over the slices: slice 0 starts from R(u0), slice p from slice
 p-1's coarse end value, each spread and swept n_predictor_sweeps times (no
 tau; by default n_coarse_sweeps; with 0 every slice starts from u0).
-For p >= 1 the fine nodes then become u0 plus the interpolated coarse
-correction (Th_c[p] - R(u0)) at every fine node 0..M_f, with F_I and F_E
-re-evaluated there.  Slice 0's fine nodes stay u0 (its coarse predictor
-values are overwritten by the first restriction), so slice 0 is exactly
-MLSDC.
+For p >= 1 the fine nodes then become the spread of u0 plus the zero-padded
+coarse correction of the slice's initial value, v_p = u0 + (D^c_f)^T
+(Th_c[p][0] - R(u0)), with F_I and F_E evaluated there.  Slice 0's fine nodes
+stay u0 (its coarse predictor values are overwritten by the first
+restriction), so slice 0 is exactly MLSDC.
 
 Iteration k (per slice, in slice order, which is the pipeline's data flow):
   A) for p >= 1 and k >= 2: fine node 0 = slice p-1's fine end value at the
@@ -73,10 +73,7 @@ def pfasst(fine: Level, coarse: Level, u0, dt: float, P: int, n_iter: int, n_coa
         coarse_nodes.append((Th_c, FI_c, FE_c))
         cu = Th_c[-1]
     for p in range(1, P):
-        Th_c = coarse_nodes[p][0]
-        d = [Th_c[i] - Ru0 for i in range(Mc + 1)]
-        Th = [u0 + interpolate_node(d, m) for m in range(Mf + 1)]
-        fine_nodes[p] = (Th, [pf.implicit_rhs(t) for t in Th], [pf.explicit_rhs(t) for t in Th])
+        fine_nodes[p] = spread(fine, u0 + pf.interpolate(coarse_nodes[p][0][0] - Ru0, pc))
 
     end_prev = None
     for k in range(n_iter):
