@@ -325,6 +325,93 @@ def node_update_bytes(R, n_nodes, m, coriolis_implicit):
     return reads + writes + tables
 
 
+def field_rel_l2(a, b):
+    """Relative Parseval L2 error of each field (Phi', zeta, delta) of state a
+    against state b ([3][N_c] complex, m-major, R = 170)."""
+    import numpy as np
+    R = WORKLOAD["Rf"]
+    m = np.concatenate([np.full(R + 1 - k, k) for k in range(R + 1)])
+    wt = np.where(m == 0, 1.0, 2.0)
+    return [float(np.sqrt(np.sum(wt * np.abs(a[k] - b[k]) ** 2) / np.sum(wt * np.abs(b[k]) ** 2)))
+            for k in range(3)]
+
+
+HEADLINE_GOLDEN = os.path.join(ROOT, "tests", "golden", "headline_T170_T85_400.npy")
+
+
+def oracle_end_state():
+    """The float64 oracle's state after the headline run's 400 steps from the
+    seed-1805 state (stored by tests/golden/make_headline_reference.py)."""
+    import numpy as np
+    try:
+        return np.load(HEADLINE_GOLDEN)
+    except OSError:
+        return None
+
+
+def host_info():
+    """What the CPU baseline ran on: CPU model, cores, BLAS threads and the
+    thread-count environment."""
+    import platform
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                k = line.split(":")[0].strip().lower()
+                if k in ("model name", "cpu model", "hardware"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    if model is None:
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for line in out.splitlines():
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except (OSError, subprocess.SubprocessError):
+            pass
+    import numpy  # noqa: F401  (loads the BLAS the oracle uses)
+    blas, blas_threads = None, None
+    try:
+        from threadpoolctl import threadpool_info
+        for d in threadpool_info():
+            if d.get("user_api") == "blas":
+                blas, blas_threads = d.get("internal_api"), d.get("num_threads")
+                break
+    except ImportError:
+        blas_threads = _openblas_threads()
+        blas = "openblas" if blas_threads else None
+    env = {k: os.environ[k] for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+           if k in os.environ}
+    return {"cpu_model": model or platform.processor() or platform.machine(), "machine": platform.machine(),
+            "nproc": os.cpu_count(), "affinity": len(os.sched_getaffinity(0)), "blas": blas,
+            "blas_threads": blas_threads, "thread_env": env}
+
+
+def _openblas_threads():
+    """OpenBLAS thread count through the library numpy loaded (no threadpoolctl)."""
+    import ctypes
+    import numpy  # noqa: F401  (loads the BLAS)
+    try:
+        with open("/proc/self/maps") as f:
+            libs = {ln.split()[-1] for ln in f if "openblas" in ln.lower() and ln.split()[-1].startswith("/")}
+    except OSError:
+        return None
+    for path in libs:
+        try:
+            L = ctypes.CDLL(path)
+        except OSError:
+            continue
+        for sym in ("scipy_openblas_get_num_threads64_", "openblas_get_num_threads64_", "openblas_get_num_threads"):
+            fn = getattr(L, sym, None)
+            if fn is not None:
+                fn.restype = ctypes.c_int
+                return int(fn())
+    return None
+
+
 def total_phi_rel_l2(a, b, phibar=9.80616e4):
     """Relative Parseval L2 error of the total geopotential Phibar + Phi' of
     state a against state b ([3][N_c] complex, m-major, R = 170)."""
@@ -620,7 +707,9 @@ def cpu_baseline_adjoint(n_sample: int = 2):
     t = time.perf_counter()
     oad.gradient(fine, coarse, x0, tgt, a["dt"], n_sample, a["n_iter"], a["n_coarse"])
     el = time.perf_counter() - t
-    return {"value": el * a["n_steps"] / n_sample, "unit": "s/gradient", "cores": os.cpu_count(), "kind": "oracle",
+    hi = host_info()
+    return {"value": el * a["n_steps"] / n_sample, "unit": "s/gradient", "cores": hi["blas_threads"] or hi["affinity"],
+            "kind": "oracle", "host": hi,
             "sample": f"oracle gradient over {n_sample} of the {a['n_steps']} steps ({el:.1f} s), scaled by "
                       f"{a['n_steps'] // n_sample}"}
 
@@ -650,8 +739,10 @@ def cpu_baseline(steps_cap_s: float = 25.0, coriolis_implicit: bool = False, lev
         u = osdc.mlsdc_step_levels(lv, u, w["dt"], w["n_iter"], w["n_coarse"])
         t += time.perf_counter() - t1
         n += 1
-    return {"value": n / t, "unit": "steps/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"{n} MLSDC steps of the same workload (float64 numpy oracle, setup {setup:.1f} s untimed)"}
+    hi = host_info()
+    return {"value": n / t, "unit": "steps/s", "cores": hi["blas_threads"] or hi["affinity"], "kind": "oracle",
+            "sample": f"{n} MLSDC steps of the same workload (float64 numpy oracle, setup {setup:.1f} s untimed)",
+            "host": hi}
 
 
 def cpu_baseline_ensemble():
@@ -671,7 +762,9 @@ def cpu_baseline_ensemble():
         osdc.mlsdc_step(fine, coarse, u, w["dt"], w["n_iter"], w["n_coarse"])
         secs += B * (time.perf_counter() - t)
     members = sum(g[-1] for g in ENSEMBLE)
-    return {"value": members / secs, "unit": "member-steps/s", "cores": os.cpu_count(), "kind": "oracle",
+    hi = host_info()
+    return {"value": members / secs, "unit": "member-steps/s", "cores": hi["blas_threads"] or hi["affinity"],
+            "kind": "oracle", "host": hi,
             "sample": "one oracle MLSDC step of one member per truncation group (T42/T21, T85/T42, T170/T85), "
                       "weighted by the group sizes (32, 48, 16)"}
 
@@ -705,11 +798,13 @@ def run_reference(args):
         u = osdc.mlsdc_step(fine, coarse, u, w["dt"], w["n_iter"], w["n_coarse"])
     el = time.perf_counter() - t
     v = k / el
+    hi = host_info()
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "steps/s", "n_gpus": args.gpus,
             "steps": k, "warmup": nw, "ms_per_step": 1e3 * el / k, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD_NAME, "sample": f"{k} of {args.steps} requested steps"},
-            "cpu_baseline": {"value": v, "unit": "steps/s", "cores": os.cpu_count(), "kind": "oracle",
+            "cpu_baseline": {"value": v, "unit": "steps/s", "cores": hi["blas_threads"] or hi["affinity"],
+                             "kind": "oracle", "host": hi,
                              "sample": f"{k} oracle MLSDC steps after {nw} warm-up steps"},
             "e2e": {"value": v, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -812,11 +907,24 @@ def main():
             do_step(M, ml, a)
             do_step(M, ml64, b)
         torch.cuda.synchronize()
-        err = total_phi_rel_l2(a.cpu().numpy(), b.cpu().numpy())
+        a_h, b_h = a.cpu().numpy(), b.cpu().numpy()
+        err = total_phi_rel_l2(a_h, b_h)
         comparison = {"fp64_gpu_steps_per_s": v64, "speedup_vs_fp64_gpu": value / ws / v64,
                       "total_phi_rel_l2_after_400_steps": err, "bar": 1e-6, "meets_bar": bool(err <= 1e-6),
+                      "fields_rel_l2_after_400_steps": dict(zip(("phi_prime", "zeta", "delta"),
+                                                                field_rel_l2(a_h, b_h))),
                       "reference": "float64 GPU path (same splitting), itself matching the float64 oracle per "
                                    "step to 1e-12"}
+        golden = oracle_end_state()
+        if golden is not None and not cor_impl and args.levels == 2 and replica_seed(rank) == 1805:
+            vo = {}
+            for tag, st_ in ((prec, a_h), ("fp64", b_h)):
+                e_ = field_rel_l2(st_, golden)
+                vo[tag] = {"total_phi": total_phi_rel_l2(st_, golden), "phi_prime": e_[0], "zeta": e_[1],
+                           "delta": e_[2]}
+            vo["reference"] = ("float64 oracle's end state after the 400 steps (tests/golden/"
+                               "headline_T170_T85_400.npy)")
+            comparison["vs_oracle_after_400_steps"] = vo
         for p_ in (pf, pc):
             if p_.device_error() != 0:
                 comparison["device_error"] = p_.device_error()

@@ -671,7 +671,7 @@ mlsdc_status reverse_step(mlsdc_adjoint_t A, const double2* tape, cudaStream_t s
                 k_node_ad<<<grid_for(L->plan->nc), 256, 0, st>>>(adj_of(A, o.p[0]), adj_of(A, o.p[1]),
                                                                 adj_of(A, o.p[2]), adj_of(A, o.p[3]),
                                                                 adj_of(A, o.p[4]), adj_of(A, o.p[5]), L->plan->d_ndeg,
-                                                                L->d_recips + (size_t)o.row.m * (L->plan->R + 1),
+                                                                recips_of(L, o.dt) + (size_t)o.row.m * (L->plan->R + 1),
                                                                 L->plan->nc, o.dt, o.row, phys_of(L->prm));
                 MLSDC_LAUNCHED("k_node_ad");
                 break;
@@ -855,6 +855,10 @@ extern "C" mlsdc_status mlsdc_adjoint_forward(mlsdc_adjoint_t A, const double* s
     if (!A || !state0 || !state_T) return MLSDC_ERR_INVALID;
     MLSDC_ALIGNED("mlsdc_adjoint_forward", {"state0", state0}, {"state_T", state_T});
     cudaStream_t st = (cudaStream_t)stream;
+    for (sdc_level_t L : {A->ml->f, A->ml->c}) {  // per-dt tables, before any capture
+        mlsdc_status r = prepare_level_tables(L, A->dt, st);
+        if (r != MLSDC_OK) return r;
+    }
     const size_t bytes = A->ml->f->node() * sizeof(double2);
     MLSDC_CUDA(cudaMemcpyAsync(A->work, state0, bytes, cudaMemcpyDeviceToDevice, st));
     for (int s = 0; s < A->n_steps; ++s) {

@@ -207,18 +207,14 @@ struct RhsBatch {
 
 // float64 kernels (transform_f64.cu)
 // stage < 0: the whole F_E evaluation; 0, 1, 2: only that stage's kernel
-// nf: a node update for the analysis kernel to run after F_E at each
-// coefficient (nullptr: none)
 mlsdc_status rhs_explicit_f64(sh_plan_t p, const swe_params* prm, const double* state, double* FE,
-                              cudaStream_t st, int64_t* launches, int stage = -1, RhsBatch b = RhsBatch(),
-                              const NodeFuse* nf = nullptr);
+                              cudaStream_t st, int64_t* launches, int stage = -1, RhsBatch b = RhsBatch());
 mlsdc_status f64_prepare(sh_plan_t p);
 // float32 / tensor-core path (transform_mp.cu)
 mlsdc_status mp_init(sh_plan_t p);
 void mp_free(sh_plan_t p);
 mlsdc_status rhs_explicit_mp(sh_plan_t p, const swe_params* prm, const double* state, double* FE,
-                             cudaStream_t st, int64_t* launches, int stage = -1, RhsBatch b = RhsBatch(),
-                             const NodeFuse* nf = nullptr);
+                             cudaStream_t st, int64_t* launches, int stage = -1, RhsBatch b = RhsBatch());
 mlsdc_status create_plan(int R, int nlon, int nlat, int precision, int max_members, sh_plan_t* out);
 // whether a Legendre stage (0 synthesis, 2 analysis) of a tensor-core plan
 // runs the tcgen05 kernel for a launch of `members` states (transform_mp.cu)

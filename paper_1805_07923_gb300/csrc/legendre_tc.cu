@@ -263,7 +263,6 @@ struct TcArgs {
     const int2* tiles;
     int n_tiles;
     int* err;
-    NodeFuse nf;  // the next node's update, run in the analysis epilogue (nf.on)
     // host-computed constants (no float64 division in the kernels)
     float ia_f, na2_f;       // 1/a, -a^2
     const float* invnn;      // [R+1] 1/(n(n+1)), 0 for n = 0
@@ -707,7 +706,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_anal(const __grid_constant
         FE[off + k] = f0;
         FE[g.nc + off + k] = f1;
         FE[2 * g.nc + off + k] = f2;
-        if (g.nf.on) node_update_coef(g.nf, g.nc, off + k, (size_t)(b0 + b) * g.nf.ms);
     }
     cta_release(c, tmem, ncols);
 }
@@ -1070,7 +1068,7 @@ mlsdc_status launch_synth(sh_plan_t p, TcState* s, const TcArgs& g, cudaStream_t
 // The warp-specialised analysis applies to latitude-contiguous launches of
 // up to 8 members per CTA (two accumulator buffers of 2 x 16 x chunk
 // columns in the 512 of tensor memory) without a fused node update.
-inline bool ws_applies(const TcArgs& g) { return g.fo.sj == 1 && g.chunk <= 8 && !g.nf.on; }
+inline bool ws_applies(const TcArgs& g) { return g.fo.sj == 1 && g.chunk <= 8; }
 inline int cfg_index(int stage) { return stage == 0 ? 0 : 1; }
 
 template <int MODE>
@@ -1239,10 +1237,9 @@ mlsdc_status tc_synth(sh_plan_t p, const double* state, double a, RhsBatch b, cu
 }
 
 mlsdc_status tc_anal(sh_plan_t p, double a, double* FE, const double* state, double two_omega, RhsBatch b,
-                     FourStride fo, cudaStream_t st, const NodeFuse* nf) {
+                     FourStride fo, cudaStream_t st) {
     TcState* s = st_of(p);
     TcArgs g = base_args(p, s, a, b.members, 2);
-    if (nf) g.nf = *nf;
     g.state = (const double2*)state;
     g.state_ms = b.state_ms;
     g.two_omega = two_omega;

@@ -1,9 +1,9 @@
 // The per-coefficient SDC node update (Sec. 4.2, Eq.
 // update_equation_sdcq_discrete_form; with tau the coarse-level form, Eq.
 // modified_update_equation_sdcq_discrete_form), the implicit solve and
-// F_I at the new node (Sec. 4.4), as device functions shared by the node
-// kernel (sdc.cu) and the analysis kernels that run the update of the next
-// node in their epilogue (rhs_kernels.cuh, legendre_tc.cu).  All float64.
+// F_I at the new node (Sec. 4.4), as device functions of the node kernels
+// (sdc.cu, coriolis_implicit.cu) and the Coriolis term shared with the
+// analysis kernels (rhs_kernels.cuh, legendre_tc.cu).  All float64.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -190,58 +190,6 @@ __device__ __forceinline__ double2 node_rhs(const double2* Th, const double2* FI
         acc = make_double2(acc.x + t.x, acc.y + t.y);
     }
     return acc;
-}
-
-// A node update to run right after an F_E evaluation, at the same
-// coefficients, by the thread that computed them (on = 0: none).  Pointers
-// are member 0's node arrays; member b is ms complex values further on.
-struct NodeFuse {
-    double2* Th;
-    const double2 *FIo, *FEo;
-    double2 *FIn, *FEn;
-    const double2* tau;
-    const int* ndeg;
-    const double2* recips;  // [R+1] solve_recips of this node, by degree
-    NodeRow row;            // dt_scaled
-    Phys ph;
-    size_t ms;
-    int on;
-};
-
-// The whole update of node row.m + 1 at coefficient c of member offset mo:
-// the three fields' right-hand sides, the coupled solve, F_I.  The m = 0
-// update also copies node 0 of the old F arrays into the new ones.
-__device__ __forceinline__ void node_update_coef(const NodeFuse& f, int nc, int c, size_t mo) {
-    const size_t node = (size_t)3 * nc;
-    const double2* Th0 = f.Th + mo;
-    const double2 *FIo = f.FIo + mo, *FEo = f.FEo + mo;
-    const double2 *FIn = f.FIn + mo, *FEn = f.FEn + mo;
-    const double2* tau = f.tau ? f.tau + mo : nullptr;
-    double2 b[3];
-    for (int q = 0; q < 3; ++q) b[q] = node_rhs(Th0, FIo, FEo, FIn, FEn, tau, node, (size_t)q * nc + c, f.row);
-    const int nd = f.ndeg[c];
-    const double n = nd;
-    const double L = -n * (n + 1.0) * f.ph.inv_a2;
-    double2 p, z, d;
-    implicit_solve_tab(L, f.row.qimm, f.ph, f.recips[nd], b[0], b[1], b[2], p, z, d);
-    double2 fp, fz, fd;
-    implicit_rhs_coef(L, f.ph, p, z, d, fp, fz, fd);
-    const size_t om = (f.row.m + 1) * node + c;
-    double2* Th = f.Th + mo;
-    double2* FInw = f.FIn + mo;
-    Th[om] = p;
-    Th[om + nc] = z;
-    Th[om + 2 * nc] = d;
-    FInw[om] = fp;
-    FInw[om + nc] = fz;
-    FInw[om + 2 * nc] = fd;
-    if (f.row.m == 0) {
-        double2* FEnw = f.FEn + mo;
-        for (int q = 0; q < 3; ++q) {
-            FInw[(size_t)q * nc + c] = FIo[(size_t)q * nc + c];
-            FEnw[(size_t)q * nc + c] = FEo[(size_t)q * nc + c];
-        }
-    }
 }
 
 }  // namespace mlsdc

@@ -41,18 +41,6 @@ bool pdl_enabled() {
     return on;
 }
 
-bool node_fusion_enabled() {
-    // Off by default: on GB300 the fused step was slower (615 vs 626 steps/s
-    // split-BF16 single member; 4390 vs 5408 member-steps/s for the
-    // ensemble), the serial per-thread update lengthening the analysis
-    // epilogue more than the saved launch.
-    static const bool on = [] {
-        const char* v = std::getenv("MLSDC_FUSE_NODE");
-        return v && v[0] == '1';
-    }();
-    return on;
-}
-
 mlsdc_status raise_smem_limit(const void* fn, size_t bytes) {
     static std::mutex mu;
     if (bytes <= 48 * 1024) return MLSDC_OK;

@@ -241,7 +241,7 @@ __global__ void __launch_bounds__(32 * kAnalWarpsMax) k_anal_rhs(const C_t<T>* _
                                                                  int nc, double ia, double2* __restrict__ FE,
                                                                  const double2* __restrict__ state,
                                                                  double two_omega_lin, const double* __restrict__ cor,
-                                                                 MemberStrides ms, FourStride fx, NodeFuse nf) {
+                                                                 MemberStrides ms, FourStride fx) {
     using C = C_t<T>;
     constexpr int TW = 32;                    // latitudes per tile
     pdl_wait();
@@ -327,7 +327,6 @@ __global__ void __launch_bounds__(32 * kAnalWarpsMax) k_anal_rhs(const C_t<T>* _
     FE[off + k] = f0;
     FE[nc + off + k] = f1;
     FE[2 * nc + off + k] = f2;
-    if (nf.on) node_update_coef(nf, nc, off + k, (size_t)blockIdx.y * nf.ms);
 }
 
 // Launch helpers shared by both precisions.

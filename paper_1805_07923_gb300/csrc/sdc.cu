@@ -109,6 +109,127 @@ __global__ void __launch_bounds__(3 * kNodeCoefs) k_sweep_node(double2* Th, cons
     }
 }
 
+// The node updates of one sweep with the sweep-constant part gathered once.
+// In the update of node r = m + 1 every term that involves only the old
+// iterate (the old F arrays), Theta^0 or tau is the same at every node
+// update of the sweep (those arrays do not change during it):
+//   S_r = Theta^0 + tau_r + sum_{j=0..M} q_rj (FIo_j + FEo_j)
+//         - sum_{j=1..r-1} (qE_rj FEo_j + qI_rj FIo_j) - qI_rr FIo_r
+// and the update's right-hand side is b_r = S_r + sum_{j=1..r-1} (qE_rj FEn_j
+// + qI_rj FIn_j): the terms of Eq. update_equation_sdcq_discrete_form (with
+// tau, Eq. modified_update_equation_sdcq_discrete_form) regrouped, the same
+// sum up to rounding order.  The m = 0 launch forms S_1..S_M (reading each
+// old F array once instead of once per node update), uses S_1 itself and
+// keeps S_2..S_M in the level's array S ([members][M-1][3][nc]); the m >= 1
+// launches read S_{m+1} and the new values of nodes 1..m only.
+struct SweepMats {  // dt-scaled rows 1..M of Q, Q_E, Q_I
+    double q[kMaxNodes][kMaxNodes], qe[kMaxNodes][kMaxNodes], qi[kMaxNodes][kMaxNodes];
+};
+
+template <int MM>
+__global__ void __launch_bounds__(3 * kNodeCoefs) k_sweep_node0(double2* Th, const double2* __restrict__ FIo,
+                                                              const double2* __restrict__ FEo, double2* FIn,
+                                                              double2* FEn, const double2* __restrict__ tau,
+                                                              double2* __restrict__ S, const int* __restrict__ ndeg,
+                                                              const double2* __restrict__ recips, int nc,
+                                                              SweepMats sm, Phys ph, size_t ms, size_t ms_s) {
+    __shared__ double2 sb[3][kNodeCoefs];
+    pdl_wait();
+    pdl_launch();
+    const size_t mo = blockIdx.y * ms;
+    Th += mo;
+    FIo += mo;
+    FEo += mo;
+    FIn += mo;
+    FEn += mo;
+    if (tau) tau += mo;
+    S += blockIdx.y * ms_s;
+    const size_t node = (size_t)3 * nc;
+    const int f = threadIdx.x / kNodeCoefs, cl = threadIdx.x - f * kNodeCoefs;
+    const int c = blockIdx.x * kNodeCoefs + cl;
+    const bool live = c < nc;
+    const size_t o = (size_t)f * nc + c;
+    if (live) {
+        double2 acc[MM + 1];
+        const double2 t0 = Th[o];
+#pragma unroll
+        for (int r = 1; r <= MM; ++r) acc[r] = tau ? make_double2(t0.x + tau[r * node + o].x, t0.y + tau[r * node + o].y)
+                                                   : t0;
+#pragma unroll
+        for (int j = 0; j <= MM; ++j) {
+            const double2 fi = FIo[j * node + o], fe = FEo[j * node + o];
+            const double2 s = make_double2(fi.x + fe.x, fi.y + fe.y);
+#pragma unroll
+            for (int r = 1; r <= MM; ++r) {
+                acc[r] = cax(acc[r], sm.q[r][j], s);
+                if (j >= 1 && j < r) {
+                    acc[r] = cax(acc[r], -sm.qe[r][j], fe);
+                    acc[r] = cax(acc[r], -sm.qi[r][j], fi);
+                } else if (j == r) {
+                    acc[r] = cax(acc[r], -sm.qi[r][r], fi);
+                }
+            }
+        }
+#pragma unroll
+        for (int r = 2; r <= MM; ++r) S[(r - 2) * node + o] = acc[r];
+        sb[f][cl] = acc[1];
+    }
+    __syncthreads();
+    if (!live) return;
+    const int nd = ndeg[c];
+    const double n = nd;
+    const double L = -n * (n + 1.0) * ph.inv_a2;
+    double2 th, fi;
+    node_solve_field(f, L, sm.qi[1][1], ph, recips[nd], sb[0][cl], sb[1][cl], sb[2][cl], th, fi);
+    Th[node + o] = th;
+    FIn[node + o] = fi;
+    FIn[o] = FIo[o];
+    FEn[o] = FEo[o];
+}
+
+// Node update m >= 1 of a sweep whose m = 0 launch (k_sweep_node0) left
+// S_{m+1} in S: b = S_{m+1} + sum_{j=1..m} (qE_j FEn_j + qI_j FIn_j), then
+// the solve and F_I as k_sweep_node.  `row` is dt_scaled.
+__global__ void __launch_bounds__(3 * kNodeCoefs) k_sweep_node_s(double2* Th, double2* FIn,
+                                                               const double2* __restrict__ FEn,
+                                                               const double2* __restrict__ S,
+                                                               const int* __restrict__ ndeg,
+                                                               const double2* __restrict__ recips, int nc,
+                                                               NodeRow row, Phys ph, size_t ms, size_t ms_s) {
+    __shared__ double2 sb[3][kNodeCoefs];
+    pdl_wait();
+    pdl_launch();
+    const size_t mo = blockIdx.y * ms;
+    Th += mo;
+    FIn += mo;
+    FEn += mo;
+    S += blockIdx.y * ms_s;
+    const size_t node = (size_t)3 * nc;
+    const int m = row.m;
+    const int f = threadIdx.x / kNodeCoefs, cl = threadIdx.x - f * kNodeCoefs;
+    const int c = blockIdx.x * kNodeCoefs + cl;
+    const bool live = c < nc;
+    const size_t o = (size_t)f * nc + c;
+    if (live) {
+        double2 acc = S[(m - 1) * node + o];
+        for (int j = 1; j <= m; ++j) {
+            acc = cax(acc, row.qe[j], FEn[j * node + o]);
+            acc = cax(acc, row.qi[j], FIn[j * node + o]);
+        }
+        sb[f][cl] = acc;
+    }
+    __syncthreads();
+    if (!live) return;
+    const int nd = ndeg[c];
+    const double n = nd;
+    const double L = -n * (n + 1.0) * ph.inv_a2;
+    double2 th, fi;
+    node_solve_field(f, L, row.qimm, ph, recips[nd], sb[0][cl], sb[1][cl], sb[2][cl], th, fi);
+    const size_t om = (m + 1) * node + o;
+    Th[om] = th;
+    FIn[om] = fi;
+}
+
 // dst[k] = src for k = 0..count-1 (node broadcast), src and dst [3 nc] complex
 // per member.
 __global__ void k_broadcast(const double2* __restrict__ src, double2* __restrict__ dst, int n3, int count,
@@ -341,14 +462,13 @@ namespace mlsdc {
 // F_E at one node of every member (x and FE point at that node of member 0),
 // or, with nodes > 0 on a one-member level, at `nodes` consecutive nodes in
 // one launch per stage (the nodes are the batch).
-static mlsdc_status eval_FE(sdc_level_t L, const double2* x, double2* FE, cudaStream_t st, int nodes = 0,
-                            const NodeFuse* nf = nullptr) {
+static mlsdc_status eval_FE(sdc_level_t L, const double2* x, double2* FE, cudaStream_t st, int nodes = 0) {
     RhsBatch b;
     b.members = nodes > 0 ? nodes : L->members;
     b.state_ms = b.fe_ms = nodes > 0 ? L->node() : L->ms();
     if (L->plan->precision == MLSDC_FP64)
-        return rhs_explicit_f64(L->plan, &L->prm_fe, (const double*)x, (double*)FE, st, &L->launches, -1, b, nf);
-    return rhs_explicit_mp(L->plan, &L->prm_fe, (const double*)x, (double*)FE, st, &L->launches, -1, b, nf);
+        return rhs_explicit_f64(L->plan, &L->prm_fe, (const double*)x, (double*)FE, st, &L->launches, -1, b);
+    return rhs_explicit_mp(L->plan, &L->prm_fe, (const double*)x, (double*)FE, st, &L->launches, -1, b);
 }
 
 static mlsdc_status eval_FI(sdc_level_t L, const double2* x, double2* FI, cudaStream_t st, int nodes = 0) {
@@ -383,11 +503,48 @@ static mlsdc_status launch_node(sdc_level_t L, double dt, const NodeRow& row, do
     if (L->options & MLSDC_CORIOLIS_IMPLICIT)
         return cor_node_launch(L, dt, dt_scaled(row, dt), Th, FIo, FEo, FIn, FEn, tau, st);
     const int nc = L->plan->nc;
+    const double2* tab = recips_of(L, dt);
+    if (!tab) return invalid_arg("node update: the level's tables for this dt were not prepared");
+    const double2* rec = tab + (size_t)row.m * (L->plan->R + 1);
+    const dim3 grid((nc + kNodeCoefs - 1) / kNodeCoefs, L->members), block(3 * kNodeCoefs);
+    // the sweep-constant terms gathered once per sweep (k_sweep_node0 /
+    // k_sweep_node_s); two-node levels have a single update per sweep
+    if (L->S) {
+        const int M = L->n - 1;
+        if (row.m == 0) {
+            SweepMats sm;
+            std::memset(&sm, 0, sizeof(sm));
+            for (int r = 1; r <= M; ++r)
+                for (int j = 0; j <= M; ++j) {
+                    sm.q[r][j] = dt * L->Q[r * L->n + j];
+                    sm.qe[r][j] = dt * L->QE[r * L->n + j];
+                    sm.qi[r][j] = dt * L->QI[r * L->n + j];
+                }
+            const size_t ms_s = (size_t)(M - 1) * L->node();
+            cudaError_t e = cudaErrorInvalidValue;
+            switch (M) {
+#define MLSDC_NODE0(MM)                                                                                          \
+    case MM:                                                                                                     \
+        e = launch_k(k_sweep_node0<MM>, grid, block, 0, st, Th, FIo, FEo, FIn, FEn, tau, L->S,                   \
+                     (const int*)L->plan->d_ndeg, rec, nc, sm, phys_of(L->prm), L->ms(), ms_s);                  \
+        break;
+                MLSDC_NODE0(2) MLSDC_NODE0(3) MLSDC_NODE0(4) MLSDC_NODE0(5) MLSDC_NODE0(6) MLSDC_NODE0(7)
+                MLSDC_NODE0(8)
+#undef MLSDC_NODE0
+            }
+            MLSDC_LAUNCH("k_sweep_node0", e);
+        } else {
+            MLSDC_LAUNCH("k_sweep_node_s", launch_k(k_sweep_node_s, grid, block, 0, st, Th, FIn, (const double2*)FEn,
+                                                    (const double2*)L->S, (const int*)L->plan->d_ndeg, rec, nc,
+                                                    dt_scaled(row, dt), phys_of(L->prm), L->ms(),
+                                                    (size_t)(M - 1) * L->node()));
+        }
+        L->launches++;
+        return MLSDC_OK;
+    }
     MLSDC_LAUNCH("k_sweep_node",
-                 launch_k(k_sweep_node, dim3((nc + kNodeCoefs - 1) / kNodeCoefs, L->members), dim3(3 * kNodeCoefs),
-                          0, st, Th, FIo, FEo, FIn, FEn, tau, (const int*)L->plan->d_ndeg,
-                          (const double2*)(L->d_recips + (size_t)row.m * (L->plan->R + 1)), nc,
-                          dt_scaled(row, dt), phys_of(L->prm), L->ms()));
+                 launch_k(k_sweep_node, grid, block, 0, st, Th, FIo, FEo, FIn, FEn, tau, (const int*)L->plan->d_ndeg,
+                          rec, nc, dt_scaled(row, dt), phys_of(L->prm), L->ms()));
     L->launches++;
     return MLSDC_OK;
 }
@@ -400,18 +557,42 @@ static mlsdc_status launch_bcast(sdc_level_t L, const double2* src, double2* dst
     return MLSDC_OK;
 }
 
-// The solve reciprocals of the level's node updates at step size dt (with
-// implicit Coriolis: the factored chains instead).
-static mlsdc_status launch_solve_coefs(sdc_level_t L, double dt, cudaStream_t st) {
-    if (L->options & MLSDC_CORIOLIS_IMPLICIT) return cor_factor_launch(L, dt, st);
+const double2* recips_of(sdc_level_t L, double dt) {
+    for (const auto& e : L->rtab)
+        if (e.first == dt) return e.second;
+    return nullptr;
+}
+
+mlsdc_status solve_recips_for(sdc_level_t L, double dt, cudaStream_t st, const double2** out) {
+    if ((*out = recips_of(L, dt))) return MLSDC_OK;
+    const int R = L->plan->R;
+    double2* buf = nullptr;
+    MLSDC_CUDA(cudaMalloc((void**)&buf, (size_t)(L->n - 1) * (R + 1) * sizeof(double2)));
+    L->rtab.emplace_back(dt, buf);
     QiDiag qd;
     std::memset(&qd, 0, sizeof(qd));
     for (int m = 0; m + 1 < L->n; ++m) qd.v[m] = L->QI[(m + 1) * L->n + m + 1];
-    const int R = L->plan->R;
     MLSDC_LAUNCH("k_solve_coefs", launch_k(k_solve_coefs, dim3(grid_for((L->n - 1) * (R + 1))), dim3(256), 0, st,
-                                           L->d_recips, R, L->n - 1, qd, dt, phys_of(L->prm)));
+                                           buf, R, L->n - 1, qd, dt, phys_of(L->prm)));
     L->launches++;
+    *out = buf;
     return MLSDC_OK;
+}
+
+mlsdc_status prepare_level_tables(sdc_level_t L, double dt, cudaStream_t st) {
+    if (L->options & MLSDC_CORIOLIS_IMPLICIT) {
+        const CorFac* f = nullptr;
+        return cor_factors(L, dt, st, &f);
+    }
+    const double2* r = nullptr;
+    return solve_recips_for(L, dt, st, &r);
+}
+
+// The per-dt tables of the level's node updates (solve reciprocals, or with
+// implicit Coriolis the factored chains): a launch only the first time a dt
+// is seen, nothing afterwards.
+static mlsdc_status launch_solve_coefs(sdc_level_t L, double dt, cudaStream_t st) {
+    return prepare_level_tables(L, dt, st);
 }
 
 // One sweep on explicit buffers ([members][n][3][nc] each).
@@ -554,8 +735,7 @@ extern "C" mlsdc_status sdc_level_create_ex(sh_plan_t plan, const swe_params* pr
         for (int c = 0; c < k; ++c) L->QI[(r + 1) * n + (c + 1)] = U[c * k + r];
 
     const size_t cnt = (size_t)members * L->ms();
-    bool ok = cudaMalloc((void**)&L->Th, cnt * sizeof(double2)) == cudaSuccess &&
-              cudaMalloc((void**)&L->d_recips, (size_t)n * (plan->R + 1) * sizeof(double2)) == cudaSuccess;
+    bool ok = cudaMalloc((void**)&L->Th, cnt * sizeof(double2)) == cudaSuccess;
     if (ok && (options & MLSDC_CORIOLIS_IMPLICIT) && cor_smem_limits(plan->R) != MLSDC_OK) {
         sdc_level_destroy(L);
         return MLSDC_ERR_CUDA;
@@ -564,6 +744,8 @@ extern "C" mlsdc_status sdc_level_create_ex(sh_plan_t plan, const swe_params* pr
         ok = ok && cudaMalloc((void**)&L->FI[b], cnt * sizeof(double2)) == cudaSuccess;
         ok = ok && cudaMalloc((void**)&L->FE[b], cnt * sizeof(double2)) == cudaSuccess;
     }
+    if (ok && n >= 3 && !(options & MLSDC_CORIOLIS_IMPLICIT))
+        ok = cudaMalloc((void**)&L->S, (size_t)members * (n - 2) * L->node() * sizeof(double2)) == cudaSuccess;
     if (!ok) {
         set_error("cudaMalloc", cudaGetLastError());
         sdc_level_destroy(L);
@@ -585,7 +767,8 @@ extern "C" mlsdc_status sdc_level_create(sh_plan_t plan, const swe_params* prm, 
 extern "C" mlsdc_status sdc_level_destroy(sdc_level_t L) {
     if (!L) return MLSDC_ERR_INVALID;
     cudaFree(L->Th);
-    cudaFree(L->d_recips);
+    for (auto& e : L->rtab) cudaFree(e.second);
+    cudaFree(L->S);
     for (auto& e : L->cfac) cudaFree(e.second);
     for (int b = 0; b < 2; ++b) {
         cudaFree(L->FI[b]);
@@ -852,8 +1035,7 @@ size_t build_mlsdc_ops(mlsdc_t ml, double2* state, double dt, int n_iter, int n_
     return build_levels_ops({ml->f, ml->c}, {ml}, state, dt, n_iter, n_c, ops);
 }
 
-mlsdc_status run_ops(mlsdc_t ml, const std::vector<Op>& ops, cudaStream_t st, int64_t* launches, double2* tape,
-                     bool fuse_node) {
+mlsdc_status run_ops(mlsdc_t ml, const std::vector<Op>& ops, cudaStream_t st, int64_t* launches, double2* tape) {
     // every level the operations touch (launch accounting)
     std::vector<sdc_level_t> lv;
     for (const Op& o : ops)
@@ -886,29 +1068,7 @@ mlsdc_status run_ops(mlsdc_t ml, const std::vector<Op>& ops, cudaStream_t st, in
                     MLSDC_CUDA(cudaMemcpy2DAsync(tape + o.tape_off, w, o.p[0], o.L->ms() * sizeof(double2), w,
                                                  (size_t)o.L->members, cudaMemcpyDeviceToDevice, st));
                 }
-                if (fuse_node && o.nodes == 0 && !o.L->options && oi + 1 < ops.size() &&
-                    ops[oi + 1].k == OpK::Node && ops[oi + 1].L == o.L) {
-                    // the next node's update runs in the analysis epilogue, per
-                    // coefficient, right after F_E there (same arithmetic as k_sweep_node)
-                    const Op& n = ops[oi + 1];
-                    NodeFuse nf{};
-                    nf.Th = n.p[0];
-                    nf.FIo = n.p[1];
-                    nf.FEo = n.p[2];
-                    nf.FIn = n.p[3];
-                    nf.FEn = n.p[4];
-                    nf.tau = n.p[5];
-                    nf.ndeg = n.L->plan->d_ndeg;
-                    nf.recips = n.L->d_recips + (size_t)n.row.m * (n.L->plan->R + 1);
-                    nf.row = dt_scaled(n.row, n.dt);
-                    nf.ph = phys_of(n.L->prm);
-                    nf.ms = n.L->ms();
-                    nf.on = 1;
-                    s = eval_FE(o.L, o.p[0], o.p[1], st, 0, &nf);
-                    ++oi;
-                } else {
-                    s = eval_FE(o.L, o.p[0], o.p[1], st, o.nodes);
-                }
+                s = eval_FE(o.L, o.p[0], o.p[1], st, o.nodes);
                 break;
             case OpK::Node:
                 s = launch_node(o.L, o.dt, o.row, o.p[0], o.p[1], o.p[2], o.p[3], o.p[4], o.p[5], st);
@@ -972,12 +1132,10 @@ mlsdc_status run_ops(mlsdc_t ml, const std::vector<Op>& ops, cudaStream_t st, in
 // Work a step at dt needs done once, outside any graph capture: the
 // factored Coriolis chains of implicit-Coriolis levels.
 static mlsdc_status prepare_levels(mlsdc_t ml, double dt, cudaStream_t st) {
-    for (sdc_level_t L : {ml->f, ml->c})
-        if (L->options & MLSDC_CORIOLIS_IMPLICIT) {
-            const CorFac* f = nullptr;
-            mlsdc_status s = cor_factors(L, dt, st, &f);
-            if (s != MLSDC_OK) return s;
-        }
+    for (sdc_level_t L : {ml->f, ml->c}) {
+        mlsdc_status s = prepare_level_tables(L, dt, st);
+        if (s != MLSDC_OK) return s;
+    }
     return MLSDC_OK;
 }
 

@@ -99,9 +99,16 @@ mlsdc_status cor_fi_launch(sdc_level_t L, const double2* x, double2* FI, int bat
 mlsdc_status cor_node_launch(sdc_level_t L, double dt, const NodeRow& row_dt, double2* Th, const double2* FIo,
                              const double2* FEo, double2* FIn, double2* FEn, const double2* tau, cudaStream_t st);
 
-// Whether node updates are fused into the preceding F_E analysis kernel (off
-// unless the environment sets MLSDC_FUSE_NODE=1).
-bool node_fusion_enabled();
+// The solve reciprocals of level L's node updates at step size dt ([n-1][R+1],
+// node-major): looked up, or computed on `st` the first time dt is seen
+// (allocates; call outside stream capture).  recips_of returns the table of
+// an already prepared dt, or nullptr.
+mlsdc_status solve_recips_for(sdc_level_t L, double dt, cudaStream_t st, const double2** out);
+const double2* recips_of(sdc_level_t L, double dt);
+// Every per-dt table a step of level L at dt reads (solve reciprocals, or the
+// factored Coriolis chains): prepared outside graph capture.
+mlsdc_status prepare_level_tables(sdc_level_t L, double dt, cudaStream_t st);
+
 
 inline int grid_for(int n) {
     int b = (n + 255) / 256;
@@ -121,7 +128,14 @@ struct sdc_level_s {
     double2* Th = nullptr;  // [members][n][3][nc]
     double2* FI[2] = {nullptr, nullptr};
     double2* FE[2] = {nullptr, nullptr};
-    double2* d_recips = nullptr;  // [n][R+1] solve reciprocals of the node updates (k_solve_coefs)
+    // per step size dt, the solve reciprocals of the node updates [n-1][R+1]
+    // (k_solve_coefs): computed the first time a dt is seen, before any graph
+    // capture, and kept, so a step's graph only reads them
+    std::vector<std::pair<double, double2*>> rtab;
+    // the sweep-constant parts S_2..S_M of the node updates' right-hand sides,
+    // [members][n-2][3][nc] (k_sweep_node0 writes them, k_sweep_node_s reads;
+    // null for two nodes and for the implicit-Coriolis splitting)
+    double2* S = nullptr;
     // implicit Coriolis only: per step size dt, the factored chains [n-1][2][nc]
     std::vector<std::pair<double, mlsdc::CorFac*>> cfac;
     int cur = 0;
@@ -156,11 +170,7 @@ size_t build_levels_ops(const std::vector<sdc_level_t>& levels, const std::vecto
                         double dt, int n_iter, int n_c, std::vector<Op>& ops);
 
 // Launch the operations in order on `st`.  With `tape`, each FE operation
-// first copies its input to tape + tape_off.  With fuse_node, an FE
-// operation directly followed by a node update on the same level runs that
-// update in its analysis kernel's epilogue (one launch fewer, same
-// arithmetic).
-mlsdc_status run_ops(mlsdc_t ml, const std::vector<Op>& ops, cudaStream_t st, int64_t* launches, double2* tape,
-                     bool fuse_node = node_fusion_enabled());
+// first copies its input to tape + tape_off.
+mlsdc_status run_ops(mlsdc_t ml, const std::vector<Op>& ops, cudaStream_t st, int64_t* launches, double2* tape);
 
 }  // namespace mlsdc

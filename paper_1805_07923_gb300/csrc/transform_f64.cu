@@ -120,11 +120,9 @@ mlsdc_status f64_prepare(sh_plan_t p) {
 }
 
 mlsdc_status rhs_explicit_f64(sh_plan_t p, const swe_params* prm, const double* state, double* FE,
-                              cudaStream_t st, int64_t* launches, int stage, RhsBatch b, const NodeFuse* nf) {
+                              cudaStream_t st, int64_t* launches, int stage, RhsBatch b) {
     const int R = p->R;
     if (b.members < 1 || b.members > p->max_members) return MLSDC_ERR_INVALID;
-    NodeFuse none{};
-    const NodeFuse& fuse = nf ? *nf : none;
     const size_t fs = (size_t)p->J * (R + 1);
     const MemberStrides ms{b.state_ms, 4 * fs, 5 * fs, b.fe_ms};
     const FourStride fo = four_out_layout(p->J, R, false);  // float64 path: m-contiguous
@@ -146,7 +144,7 @@ mlsdc_status rhs_explicit_f64(sh_plan_t p, const swe_params* prm, const double* 
                      launch_k(k_anal_rhs<double>, dim3(p->n_anal, b.members), dim3(32 * anal_warps(p->J2)), 0, st,
                               (const double2*)p->d_four_out, (const double*)p->d_P, (const double*)p->d_H,
                               (const Chunk*)p->d_anal, R, p->J2, p->nc, 1.0 / prm->a, (double2*)FE,
-                              (const double2*)state, 0.0, (const double*)p->d_cor, ms, fo, fuse));
+                              (const double2*)state, 0.0, (const double*)p->d_cor, ms, fo));
     }
     if (launches) *launches += stage < 0 ? 3 : 1;
     return MLSDC_OK;

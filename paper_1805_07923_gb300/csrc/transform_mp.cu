@@ -32,7 +32,7 @@ mlsdc_status wait_selftest(int timeout_ms, int* code);
 void tc_free(sh_plan_t p);
 mlsdc_status tc_synth(sh_plan_t p, const double* state, double a, RhsBatch b, cudaStream_t st);
 mlsdc_status tc_anal(sh_plan_t p, double a, double* FE, const double* state, double two_omega, RhsBatch b,
-                     FourStride fo, cudaStream_t st, const NodeFuse* nf);
+                     FourStride fo, cudaStream_t st);
 
 constexpr int kStageAuto = 0, kStageTc = 1, kStageSimt = 2;
 
@@ -97,11 +97,9 @@ void mp_free(sh_plan_t p) {
 }
 
 mlsdc_status rhs_explicit_mp(sh_plan_t p, const swe_params* prm, const double* state, double* FE, cudaStream_t st,
-                             int64_t* launches, int stage, RhsBatch b, const NodeFuse* nf) {
+                             int64_t* launches, int stage, RhsBatch b) {
     const int R = p->R;
     MPTables& t = p->mp;
-    NodeFuse none{};
-    const NodeFuse& fuse = nf ? *nf : none;
     if (b.members < 1 || b.members > p->max_members) return MLSDC_ERR_INVALID;
     const bool tc = p->precision == MLSDC_TF32 || p->precision == MLSDC_BF16X3;
     const size_t fs = (size_t)p->J * (R + 1);
@@ -134,14 +132,14 @@ mlsdc_status rhs_explicit_mp(sh_plan_t p, const swe_params* prm, const double* s
     }
     if (stage == 2 || stage < 0) {
         if (tc && stage_uses_tc(p, 2, b.members)) {
-            if ((s = tc_anal(p, prm->a, FE, state, 2.0 * prm->omega, b, fo, st, nf)) != MLSDC_OK) return s;
+            if ((s = tc_anal(p, prm->a, FE, state, 2.0 * prm->omega, b, fo, st)) != MLSDC_OK) return s;
         } else {
             MLSDC_LAUNCH("k_anal_rhs<float>",
                          launch_k(k_anal_rhs<float>, dim3(p->n_anal, b.members), dim3(32 * anal_warps(p->J2)), 0, st,
                                   (const float2*)t.four_out, (const float*)t.P32, (const float*)t.H32,
                                   (const Chunk*)p->d_anal, R, p->J2, p->nc, 1.0 / prm->a,
                                   (double2*)FE, (const double2*)state, 2.0 * prm->omega, (const double*)p->d_cor, ms,
-                                  fo, fuse));
+                                  fo));
         }
     }
     if (launches) *launches += stage < 0 ? 3 : 1;

@@ -9,7 +9,11 @@ the seeded state (seed 1805).
 Bars: the float64 path matches per step to 1e-12 (test_gpu_parity); over 400
 steps rounding differences grow, and the end state must agree to 1e-9 per
 field.  The mixed-precision variants that carry the headline must meet the
-1e-6 relative L2 bound on the total geopotential against the oracle."""
+1e-6 relative L2 bound on the total geopotential against the oracle.  Their
+per-field errors (Phi', zeta, delta), which the total geopotential's mean
+hides (Phibar is ~1e3 times the rms of Phi'), are bounded too, at three
+times the values measured on GB300 (split-BF16: 3.9e-6, 7.3e-6, 1.25e-4;
+float32: 3.0e-7, 2.4e-7, 9.8e-6): a regression in any field fails."""
 import os
 
 import numpy as np
@@ -57,10 +61,16 @@ def test_fp64_run_matches_oracle_end_state(oracle_end):
     assert max(errs) <= 1e-9
 
 
+FIELD_TOL = {"bf16x3": (1.2e-5, 2.2e-5, 3.8e-4), "fp32": (9e-7, 7e-7, 3e-5)}
+
+
 @pytest.mark.parametrize("prec", ["bf16x3", "fp32"])
 def test_mixed_run_meets_total_geopotential_bar_vs_oracle(prec, oracle_end):
     got = _run(prec)
     err = _total_phi(got, oracle_end)
+    fields = [_rel(got[k], oracle_end[k]) for k in range(3)]
     print(f"{prec} 400-step total-Phi rel L2 vs oracle: {err:.3e}; fields "
-          f"{[round(_rel(got[k], oracle_end[k]), 10) for k in range(3)]}")
+          f"{[round(f, 10) for f in fields]}")
     assert err <= 1e-6
+    for k in range(3):
+        assert fields[k] <= FIELD_TOL[prec][k], (prec, k, fields[k])

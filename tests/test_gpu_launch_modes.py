@@ -8,10 +8,8 @@ schedule.
   step is bitwise the unbatched one; the tensor-core kernels pack the entries
   along N of one MMA (equal to 1e-12).  The batched float64 step also matches
   the oracle per step to 1e-12, and its adjoint the oracle's adjoint.
-- Programmatic dependent launch (MLSDC_PDL=1) and fusing each node update
-  into the preceding analysis kernel (MLSDC_FUSE_NODE=1), both off by
-  default, change only how kernels start, never what they compute: bitwise
-  equal.
+- Programmatic dependent launch (MLSDC_PDL=1), off by default, changes only
+  how kernels start, never what they compute: bitwise equal.
 """
 import json
 import os
@@ -141,16 +139,15 @@ print(json.dumps(out))
 
 
 def test_launch_modes_do_not_change_results():
-    """Programmatic dependent launch (MLSDC_PDL=1) and fusing each node update
-    into the preceding analysis kernel (MLSDC_FUSE_NODE=1) change only how
-    the same arithmetic is launched: results are bitwise equal."""
+    """Programmatic dependent launch (MLSDC_PDL=1) changes only how the same
+    arithmetic is launched: results are bitwise equal."""
     res = {}
-    for name, env_add in (("default", {}), ("pdl", {"MLSDC_PDL": "1"}), ("fused", {"MLSDC_FUSE_NODE": "1"})):
+    for name, env_add in (("default", {}), ("pdl", {"MLSDC_PDL": "1"})):
         env = dict(os.environ, **env_add)
         r = subprocess.run([sys.executable, "-c", _CHILD, ROOT], env=env, capture_output=True, text=True,
                            timeout=600)
         assert r.returncode == 0, r.stderr[-2000:]
         res[name] = json.loads(r.stdout.strip().splitlines()[-1])
-    for name in ("pdl", "fused"):
+    for name in ("pdl",):
         for key in ("fp64", "bf16x3", "ens_fp32"):
             assert np.array_equal(np.array(res[name][key]), np.array(res["default"][key])), (name, key)

@@ -1,7 +1,8 @@
 """Tensor-core (tcgen05, TMA-fed) Legendre contractions: TF32 and split-BF16
 (hi/lo, three products) against the float64 oracle per F_E evaluation, and
 the run-level criterion on the headline workload: total-geopotential relative
-L2 <= 1e-6 after 400 steps against the float64 GPU path."""
+L2 <= 1e-6 after 400 steps against the float64 GPU path (split-BF16; TF32
+does not meet it and is reported only)."""
 import numpy as np
 import pytest
 import torch
@@ -18,8 +19,11 @@ TC = ["tf32", "bf16x3"]
 # bf16 hi+lo: 2^-16 relative per product) times the cancellation of each
 # tendency, with margin over the largest error measured on T21..T170.
 PER_EVAL_TOL = {"tf32": (5e-3, 1e-1, 3e-1), "bf16x3": (2e-4, 5e-3, 2e-2)}
-# Run-level bound on the total geopotential after 400 steps.
-RUN_TOL = {"bf16x3": 1e-6, "tf32": 1e-5}
+# Run-level bound on the total geopotential after 400 steps: the 1e-6 bar
+# for split BF16.  TF32 (10-bit operand mantissas) fails that bar (about
+# 5e-6 on GB300); its run is reported, never bounded by a looser number and
+# never the headline variant.
+RUN_TOL = {"bf16x3": 1e-6}
 
 _or = {}
 
@@ -80,9 +84,8 @@ def test_tensorcore_headline_run_total_geopotential(prec):
     print(f"{prec}: total Phi rel L2 after 400 steps = {err:.3e}; Phi' {rel_l2(170, got[0], ref[0]):.2e} "
           f"zeta {rel_l2(170, got[1], ref[1]):.2e} delta {rel_l2(170, got[2], ref[2]):.2e}")
     assert np.all(np.isfinite(got))
-    # split BF16 meets the 1e-6 bar; TF32 (10-bit mantissa operands) does not
-    # and is reported with its own bound, never as the headline variant
-    assert err <= RUN_TOL[prec]
+    if prec in RUN_TOL:
+        assert err <= RUN_TOL[prec]
 
 
 def test_bounded_wait_gives_up_and_context_survives():
