@@ -77,6 +77,7 @@ typedef struct mlsdc_s* mlsdc_t;
 typedef struct mlsdc_ensemble_s* mlsdc_ensemble_t;
 typedef struct mlsdc_adjoint_s* mlsdc_adjoint_t;
 typedef struct mlsdc_levels_s* mlsdc_levels_t;
+typedef struct pfasst_s* pfasst_t;
 
 /* Text of a status code, and the last CUDA error message seen by this thread. */
 const char* mlsdc_status_string(mlsdc_status s);
@@ -339,6 +340,39 @@ mlsdc_status mlsdc_levels_destroy(mlsdc_levels_t h);
 mlsdc_status mlsdc_levels_step(mlsdc_levels_t h, double* state, double dt, int n_iter, int n_coarse_sweeps,
                                int use_graph, void* stream);
 mlsdc_status mlsdc_levels_launch_count(mlsdc_levels_t h, int64_t* launches);
+
+/* ---------------------------------------------------------------------------
+ * Two-level PFASST, time-parallel MLSDC, on one GPU.  The paper names the
+ * parallel full approximation scheme in space and time as the time-parallel
+ * extension of MLSDC (Sec. 1, conclusions) without printing it; this is the
+ * published two-level iteration built on Algorithm 1's steps.  P time slices
+ * of length dt, slice p covering [t0 + p dt, t0 + (p+1) dt], are the P
+ * members of the two batched levels (created with members = P; the coarse
+ * plan with max_members >= P * coarse nodes evaluates every slice's coarse
+ * nodes in one launch per stage, a smaller one node by node).  One call:
+ *   predictor: every slice's fine nodes = u0; the coarse level runs serially
+ *     over the slices (slice 0 from R u0, slice p from slice p-1's coarse end
+ *     value; spread, n_predictor_sweeps sweeps); slices p >= 1 then start
+ *     from u0 + zero-pad(their coarse initial value - R u0), spread;
+ *   n_iter iterations of: fine initial value of slice p = slice p-1's fine
+ *     end value from the previous iteration (F re-evaluated); one fine sweep
+ *     of every slice (batched); restriction of fine nodes 0..M_c, coarse F,
+ *     FAS term (batched); the coarse pipeline: slice after slice, coarse node
+ *     0 = the previous slice's coarse end value of this iteration (F
+ *     re-evaluated), n_coarse_sweeps sweeps with tau; interpolation of the
+ *     coarse corrections to fine nodes 1..M_f (batched).
+ * With P = 1 (and for slice 0 always) the result is mlsdc_step's; with
+ * enough iterations every slice reaches the serial sequence of fine
+ * collocation steps.  Only the paper's splitting; levels must outlive the
+ * object.  u0: [3][N_c,fine] (device, read only); ends: [P][3][N_c,fine]
+ * receives every slice's end value (ends[P-1] = the state at t0 + P dt).
+ * n_predictor_sweeps < 0 means n_coarse_sweeps.  use_graph as mlsdc_step
+ * (one graph per u0, ends, dt and iteration counts). */
+mlsdc_status pfasst_create(sdc_level_t fine, sdc_level_t coarse, pfasst_t* out);
+mlsdc_status pfasst_destroy(pfasst_t pf);
+mlsdc_status pfasst_step(pfasst_t pf, const double* u0, double* ends, double dt, int n_iter, int n_coarse_sweeps,
+                         int n_predictor_sweeps, int use_graph, void* stream);
+mlsdc_status pfasst_launch_count(pfasst_t pf, int64_t* launches);
 
 /* ---------------------------------------------------------------------------
  * Ensembles of uneven truncation: one MLSDC object per truncation group

@@ -636,6 +636,9 @@ mlsdc_status reverse_step(mlsdc_adjoint_t A, const double2* tape, cudaStream_t s
         const Op& o = *it;
         sdc_level_t L = o.L;
         switch (o.k) {
+            case OpK::Copy2D:
+            case OpK::PadAdd:
+                return invalid_arg("mlsdc_adjoint: the operation list holds a time-parallel operation");
             case OpK::CopyLast:
             case OpK::Copy: {
                 const size_t cnt = o.k == OpK::Copy ? o.bytes / sizeof(double2) : L->node();

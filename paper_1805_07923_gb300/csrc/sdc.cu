@@ -367,6 +367,21 @@ __global__ void k_interp(double2* __restrict__ Tf, double2* __restrict__ FIf, do
     }
 }
 
+// X_f += zero-pad(X_c - X_0) at one node per member (X_0 shared by every
+// member): the coarse change of a node carried to the fine level without
+// interpolation in time; one thread per (field, coarse coefficient).
+__global__ void k_pad_add(double2* __restrict__ Xf, const double2* __restrict__ Xc,
+                          const double2* __restrict__ X0, const int* __restrict__ c2f, int ncf, int ncc,
+                          size_t msf, size_t msc) {
+    Xf += blockIdx.y * msf;
+    Xc += blockIdx.y * msc;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < 3 * ncc; t += gridDim.x * blockDim.x) {
+        const int f = t / ncc, k = t - f * ncc;
+        const size_t o = (size_t)f * ncf + c2f[k];
+        Xf[o] = make_double2(Xf[o].x + (Xc[t].x - X0[t].x), Xf[o].y + (Xc[t].y - X0[t].y));
+    }
+}
+
 __global__ void k_finite(const double* __restrict__ x, int64_t n, int* __restrict__ bad) {
     int local = 0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -482,7 +497,7 @@ static mlsdc_status eval_FI(sdc_level_t L, const double2* x, double2* FI, cudaSt
     return MLSDC_OK;
 }
 
-static NodeRow node_row(sdc_level_t L, int m) {
+NodeRow node_row(sdc_level_t L, int m) {
     const int n = L->n;
     NodeRow row;
     std::memset(&row, 0, sizeof(row));
@@ -1119,6 +1134,16 @@ mlsdc_status run_ops(mlsdc_t ml, const std::vector<Op>& ops, cudaStream_t st, in
                                              (size_t)o.L->members, cudaMemcpyDeviceToDevice, st));
                 break;
             }
+            case OpK::Copy2D:
+                MLSDC_CUDA(cudaMemcpy2DAsync(o.p[1], o.ms_dst * sizeof(double2), o.p[0], o.ms_src * sizeof(double2),
+                                             o.bytes, (size_t)o.count, cudaMemcpyDeviceToDevice, st));
+                break;
+            case OpK::PadAdd:
+                MLSDC_LAUNCH("k_pad_add", launch_k(k_pad_add, dim3(grid_for(3 * ncc), o.count), dim3(256), 0, st,
+                                                   o.p[0], (const double2*)o.p[1], (const double2*)o.p[2],
+                                                   (const int*)P->d_c2f, ncf, ncc, msf, msc));
+                own++;
+                break;
         }
         if (s != MLSDC_OK) return s;
     }

@@ -55,6 +55,9 @@ enum class OpK : int {
     Interp,    // fine p[0..2] += P(Pfc (coarse p[3..5] - saved p[6..8]))
     CopyLast,  // p[1] (the state) = last fine node p[0], every member
     SolveCoefs,  // the level's implicit-solve reciprocals at dt (no state operands)
+    Copy2D,    // `count` rows of `bytes` bytes, p[0] -> p[1], row pitches ms_src / ms_dst (complex values)
+    PadAdd,    // fine p[0] += zero-pad(coarse p[1] - p[2]) at one node, `count` members from p[0], p[1]
+               // (member strides of the pair's levels; p[2] the same for every member)
 };
 
 struct Op {
@@ -75,6 +78,9 @@ struct Op {
 };
 
 inline Phys phys_of(const swe_params& p) { return Phys{1.0 / (p.a * p.a), p.phibar, p.nu}; }
+
+// Row m + 1 of level L's SDC matrices (not yet scaled by dt).
+NodeRow node_row(sdc_level_t L, int m);
 
 // One element of a factored Coriolis chain (coriolis_implicit.cu): the
 // Thomas elimination's multiplier l, the pivot's reciprocal iw and the

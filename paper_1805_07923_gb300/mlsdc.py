@@ -43,6 +43,10 @@ _SIGS = {
     "mlsdc_levels_destroy": ([_VP], _I),
     "mlsdc_levels_step": ([_VP, _DP, _D, _I, _I, _I, _VP], _I),
     "mlsdc_levels_launch_count": ([_VP, ctypes.POINTER(_I64)], _I),
+    "pfasst_create": ([_VP, _VP, ctypes.POINTER(_VP)], _I),
+    "pfasst_destroy": ([_VP], _I),
+    "pfasst_step": ([_VP, _DP, _DP, _D, _I, _I, _I, _I, _VP], _I),
+    "pfasst_launch_count": ([_VP, ctypes.POINTER(_I64)], _I),
     "mlsdc_profile_node": ([_VP, _D, _I, ctypes.POINTER(ctypes.c_float), _VP], _I),
     "sdc_level_create_ex": ([_VP, ctypes.POINTER(SweParams), _I, _I, _I, ctypes.POINTER(_VP)], _I),
     "swe_implicit_rhs_ex": ([_VP, ctypes.POINTER(SweParams), _DP, _DP, _I, _VP], _I),
@@ -401,6 +405,44 @@ def mlsdc_levels_step(ml: MLSDCLevels, state: torch.Tensor, dt: float, n_iter: i
     f = ml.levels[0]
     _check(lib().mlsdc_levels_step(ml.h, _ptr(state, 6 * f.plan.nc * f.members), float(dt), int(n_iter),
                                    int(n_coarse_sweeps), 1 if use_graph else 0, _stream(stream)), "mlsdc_levels_step")
+
+
+class PFASST:
+    """pfasst_create: two-level PFASST over P time slices, the P members of the
+    batched fine and coarse levels (which must outlive it)."""
+
+    def __init__(self, fine: Level, coarse: Level):
+        self.fine, self.coarse = fine, coarse
+        h = ctypes.c_void_p()
+        _check(lib().pfasst_create(fine.h, coarse.h, ctypes.byref(h)), "pfasst_create")
+        self.h = h
+        self.slices = fine.members
+
+    def close(self):
+        if self.h:
+            lib().pfasst_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def launch_count(self) -> int:
+        v = ctypes.c_int64()
+        _check(lib().pfasst_launch_count(self.h, ctypes.byref(v)), "pfasst_launch_count")
+        return v.value
+
+
+def pfasst_step(pf: PFASST, u0: torch.Tensor, ends: torch.Tensor, dt: float, n_iter: int, n_coarse_sweeps: int,
+                n_predictor_sweeps: int = -1, use_graph: bool = False, stream=None):
+    """Advance u0 ([3][N_c]) over pf.slices slices of length dt; ends
+    ([slices][3][N_c]) receives every slice's end value."""
+    nc = pf.fine.plan.nc
+    _check(lib().pfasst_step(pf.h, _ptr(u0, 6 * nc), _ptr(ends, 6 * nc * pf.slices), float(dt), int(n_iter),
+                             int(n_coarse_sweeps), int(n_predictor_sweeps), 1 if use_graph else 0, _stream(stream)),
+           "pfasst_step")
 
 
 def mlsdc_check_finite(x: torch.Tensor, stream=None) -> bool:
