@@ -549,6 +549,116 @@ def run_ensemble(args):
     print(json.dumps(line), flush=True)
 
 
+PFASST = dict(P=4, n_iter=4, n_coarse=2)
+PFASST_NAME = ("two-level PFASST over 4 time slices of dt 150 s (the slices as the members of batched levels): "
+               "fine T170 512x256 5 Lobatto nodes / coarse T85 256x128 3 nodes, 4 iterations of one fine sweep "
+               "of every slice and a serial coarse pipeline of 2 sweeps per slice, seeded n^-3/2 spectra")
+
+
+def run_pfasst(args):
+    """Time steps per second of PFASST over 4 slices on one GPU, with the
+    accuracy of every slice against the serial MLSDC steps of the headline
+    schedule (same dt, same fine and coarse levels)."""
+    import numpy as np
+    import torch
+
+    from paper_1805_07923_gb300 import inputs
+    from paper_1805_07923_gb300 import mlsdc as M
+    dev = torch.device("cuda", 0)
+    w, pw = WORKLOAD, PFASST
+    P, prec = pw["P"], args.precision
+    pf_ = M.Plan(w["Rf"], w["If"], w["Jf"], prec, max_members=P)
+    pc_ = M.Plan(w["Rc"], w["Ic"], w["Jc"], prec, max_members=P * w["nc"])
+    lf, lc = M.Level(pf_, w["nf"], members=P), M.Level(pc_, w["nc"], members=P)
+    pf = M.PFASST(lf, lc)
+    u0 = inputs.initial_state(w["Rf"])
+    x = torch.from_numpy(u0).to(dev)
+    ends = torch.empty((P,) + tuple(x.shape), dtype=torch.complex128, device=dev)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def call():
+        M.pfasst_step(pf, x, ends, w["dt"], pw["n_iter"], pw["n_coarse"], -1, True)
+
+    for _ in range(max(3, args.warmup)):
+        call()
+    torch.cuda.synchronize()
+    K = args.steps
+    clocks = ClockSampler(0)
+    clocks.start()
+    time.sleep(0.3)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    for k in range(K):
+        flush.zero_()
+        ev[k][0].record(stream)
+        call()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    total_ms = sum(a.elapsed_time(b) for a, b in ev)
+    # end to end through the public API: u0 from pinned host memory, every slice's end value back
+    host_in = torch.from_numpy(u0).pin_memory()
+    host_out = torch.empty(tuple(ends.shape), dtype=ends.dtype).pin_memory()
+    Ke = min(K, 50)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(Ke):
+        x.copy_(host_in, non_blocking=True)
+        call()
+        host_out.copy_(ends, non_blocking=True)
+    e1.record(stream)
+    e1.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    got = ends.cpu().numpy()
+    # the serial reference: P MLSDC steps of the same schedule, this precision and float64
+    acc = {}
+    for tag in sorted({prec, "fp64"}):
+        sf, sc = M.Plan(w["Rf"], w["If"], w["Jf"], tag), M.Plan(w["Rc"], w["Ic"], w["Jc"], tag, w["nc"] - 1)
+        ml = M.MLSDC(M.Level(sf, w["nf"]), M.Level(sc, w["nc"]))
+        y = torch.from_numpy(u0).to(dev)
+        ser = []
+        for _ in range(P):
+            M.mlsdc_step(ml, y, w["dt"], w["n_iter"], w["n_coarse"], use_graph=True)
+            ser.append(y.cpu().numpy())
+        if tag == "fp64":
+            acc["vs_serial_mlsdc_fp64"] = [dict(zip(("phi_prime", "zeta", "delta"), field_rel_l2(got[p], ser[p])),
+                                                total_phi=total_phi_rel_l2(got[p], ser[p])) for p in range(P)]
+        # serial MLSDC time steps per second of the same precision, for comparison
+        for _ in range(3):
+            M.mlsdc_step(ml, y, w["dt"], w["n_iter"], w["n_coarse"], use_graph=True)
+        Ks = min(K * P, 200)
+        acc[f"serial_mlsdc_{tag}_steps_per_s"] = Ks / (timed_steps(torch, M, ml, y, Ks, flush, stream) * 1e-3)
+    value = P * K / (total_ms * 1e-3)
+    nbytes = host_in.numel() * host_in.element_size()
+    line = {"metric": "PFASST time steps/s at T170/T85 (4 slices on one GPU)", "value": value, "unit": "steps/s",
+            "n_gpus": 1, "steps": K, "warmup": max(3, args.warmup), "ms_per_step": total_ms / K,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if prec == "fp64" else f"f64+{prec}", "data": "synthetic",
+            "config": {"workload": PFASST_NAME, "precision": prec, "slices": P, "iterations": pw["n_iter"],
+                       "l2": "flushed between timed calls (256 MB write)", "graph": "one CUDA graph per call",
+                       "step": "one pfasst_step call = 4 time steps"},
+            "gpu_launches": pf.launch_count() * K, "clocks": clk, "accuracy": acc,
+            "e2e": {"value": P * Ke / (e2e_ms * 1e-3), "unit": "steps/s", "h2d_bytes_per_step": nbytes,
+                    "d2h_bytes_per_step": nbytes * P}}
+    if not args.no_cpu_baseline:
+        from oracle import pfasst as opf
+        from oracle import sdc as osdc
+        from oracle.swe import SWE, Params
+        fine = osdc.Level(SWE(w["Rf"], w["If"], w["Jf"], Params()), w["nf"])
+        coarse = osdc.Level(SWE(w["Rc"], w["Ic"], w["Jc"], Params()), w["nc"])
+        t = time.perf_counter()
+        opf.pfasst(fine, coarse, u0, w["dt"], P, 1, pw["n_coarse"])
+        el = time.perf_counter() - t
+        hi = host_info()
+        # one iteration sampled; the predictor is about one more iteration's coarse work
+        line["cpu_baseline"] = {"value": P / (el * pw["n_iter"]), "unit": "steps/s",
+                                "cores": hi["blas_threads"] or hi["affinity"], "kind": "oracle", "host": hi,
+                                "sample": f"oracle PFASST call with 1 of the {pw['n_iter']} iterations ({el:.1f} s), "
+                                          f"scaled to {pw['n_iter']} iterations"}
+    print(json.dumps(line), flush=True)
+
+
 ADJOINT = dict(Rf=85, If=256, Jf=128, Rc=42, Ic=128, Jc=64, nf=5, nc=3, n_iter=4, n_coarse=2, dt=300.0,
                n_steps=48, every=8)
 ADJOINT_NAME = ("gradient of J = 1/2 ||Phi'(T) - Phi_t||^2 w.r.t. the initial state: 48 steps of MLSDC(5,3) "
@@ -823,9 +933,10 @@ def main():
                     help="space-time levels of the headline workload: 2 (the paper's) or 3 (a T42 level added)")
     ap.add_argument("--coriolis", default="explicit", choices=["explicit", "implicit"],
                     help="splitting of the headline workload: the paper's (Coriolis in F_E) or Coriolis in F_I")
-    ap.add_argument("--workload", default="headline", choices=["headline", "ensemble", "adjoint"],
+    ap.add_argument("--workload", default="headline", choices=["headline", "ensemble", "adjoint", "pfasst"],
                     help="headline: one T170/T85 member; ensemble: the 96-member uneven-truncation ensemble; "
-                         "adjoint: the 48-step T85/T42 gradient")
+                         "adjoint: the 48-step T85/T42 gradient; pfasst: 4 time slices of the headline "
+                         "schedule advanced by PFASST")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -833,6 +944,8 @@ def main():
         return run_ensemble(args)
     if args.workload == "adjoint":
         return run_adjoint(args)
+    if args.workload == "pfasst":
+        return run_pfasst(args)
     args.warmup = max(3, args.warmup)
 
     import numpy as np
