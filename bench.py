@@ -549,9 +549,93 @@ def run_ensemble(args):
     print(json.dumps(line), flush=True)
 
 
+SMALL = {  # the two smaller configurations of the parity workloads, timed for the results table
+    "sdc_t21": dict(name="single-level SDC(3,4) T21 64x32, dt 600 s, seeded n^-3/2 spectra", R=21, I=64, J=32,
+                    nodes=3, sweeps=4, dt=600.0),
+    "mlsdc_t85": dict(name="MLSDC(5,3,4,1/2) fine T85 256x128 / coarse T42 128x64, 1 fine + 2 coarse sweeps, "
+                           "dt 300 s, seeded n^-3/2 spectra", Rf=85, If=256, Jf=128, Rc=42, Ic=128, Jc=64, nf=5,
+                      nc=3, n_iter=4, n_coarse=2, dt=300.0),
+}
+
+
+def run_small(args):
+    """Steps/s of a smaller workload on the GPU (float64 and the requested
+    precision) and of the oracle on the host cores."""
+    import numpy as np
+    import torch
+
+    from paper_1805_07923_gb300 import inputs
+    from paper_1805_07923_gb300 import mlsdc as M
+    cfg = SMALL[args.workload]
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    R = cfg.get("R", cfg.get("Rf"))
+    u0 = inputs.initial_state(R)
+
+    def gpu_rate(prec):
+        if args.workload == "sdc_t21":
+            lev = M.Level(M.Plan(cfg["R"], cfg["I"], cfg["J"], prec), cfg["nodes"])
+            step = lambda x: M.sdc_step(lev, x, cfg["dt"], cfg["sweeps"])
+            keep = lev
+        else:
+            pf = M.Plan(cfg["Rf"], cfg["If"], cfg["Jf"], prec)
+            pc = M.Plan(cfg["Rc"], cfg["Ic"], cfg["Jc"], prec, cfg["nc"] - 1)
+            ml = M.MLSDC(M.Level(pf, cfg["nf"]), M.Level(pc, cfg["nc"]))
+            step = lambda x: M.mlsdc_step(ml, x, cfg["dt"], cfg["n_iter"], cfg["n_coarse"], use_graph=True)
+            keep = ml
+        x = torch.from_numpy(u0).to(dev)
+        for _ in range(max(3, args.warmup)):
+            step(x)
+        torch.cuda.synchronize()
+        K = args.steps
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        for k in range(K):
+            flush.zero_()
+            ev[k][0].record(stream)
+            step(x)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        del keep
+        return K / (sum(a.elapsed_time(b) for a, b in ev) * 1e-3)
+
+    clocks = ClockSampler(0)
+    clocks.start()
+    time.sleep(0.3)
+    rates = {p: gpu_rate(p) for p in sorted({"fp64", args.precision})}
+    clk = clocks.stop()
+    value = rates[args.precision]
+    line = {"metric": f"{args.workload} steps/s", "value": value, "unit": "steps/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": 1e3 / value, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else f"f64+{args.precision}",
+            "data": "synthetic", "config": {"workload": cfg["name"], "precision": args.precision,
+                                            "l2": "flushed between timed steps (256 MB write)"},
+            "gpu_steps_per_s": rates, "clocks": clk}
+    if not args.no_cpu_baseline:
+        from oracle import sdc as osdc
+        from oracle.swe import SWE, Params
+        if args.workload == "sdc_t21":
+            lev = osdc.Level(SWE(cfg["R"], cfg["I"], cfg["J"], Params()), cfg["nodes"])
+            ostep = lambda u: osdc.sdc_step(lev, u, cfg["dt"], cfg["sweeps"])
+        else:
+            fine = osdc.Level(SWE(cfg["Rf"], cfg["If"], cfg["Jf"], Params()), cfg["nf"])
+            coarse = osdc.Level(SWE(cfg["Rc"], cfg["Ic"], cfg["Jc"], Params()), cfg["nc"])
+            ostep = lambda u: osdc.mlsdc_step(fine, coarse, u, cfg["dt"], cfg["n_iter"], cfg["n_coarse"])
+        u, n, t = u0, 0, 0.0
+        while n == 0 or (t < 15.0 and n < 50):
+            t1 = time.perf_counter()
+            u = ostep(u)
+            t += time.perf_counter() - t1
+            n += 1
+        hi = host_info()
+        line["cpu_baseline"] = {"value": n / t, "unit": "steps/s", "cores": hi["blas_threads"] or hi["affinity"],
+                                "kind": "oracle", "host": hi, "sample": f"{n} oracle steps of the same workload"}
+    print(json.dumps(line), flush=True)
+
+
 PFASST = dict(P=4, n_iter=4, n_coarse=2)
 PFASST_NAME = ("two-level PFASST over 4 time slices of dt 150 s (the slices as the members of batched levels): "
-               "fine T170 512x256 5 Lobatto nodes / coarse T85 256x128 3 nodes, 4 iterations of one fine sweep "
+               "fine T170 512x256 5 Lobatto nodes / coarse T85 256x128 3 nodes, {K} iterations of one fine sweep "
                "of every slice and a serial coarse pipeline of 2 sweeps per slice, seeded n^-3/2 spectra")
 
 
@@ -565,7 +649,9 @@ def run_pfasst(args):
     from paper_1805_07923_gb300 import inputs
     from paper_1805_07923_gb300 import mlsdc as M
     dev = torch.device("cuda", 0)
-    w, pw = WORKLOAD, PFASST
+    w, pw = WORKLOAD, dict(PFASST)
+    if args.pfasst_iters:
+        pw["n_iter"] = args.pfasst_iters
     P, prec = pw["P"], args.precision
     pf_ = M.Plan(w["Rf"], w["If"], w["Jf"], prec, max_members=P)
     pc_ = M.Plan(w["Rc"], w["Ic"], w["Jc"], prec, max_members=P * w["nc"])
@@ -635,7 +721,8 @@ def run_pfasst(args):
             "n_gpus": 1, "steps": K, "warmup": max(3, args.warmup), "ms_per_step": total_ms / K,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if prec == "fp64" else f"f64+{prec}", "data": "synthetic",
-            "config": {"workload": PFASST_NAME, "precision": prec, "slices": P, "iterations": pw["n_iter"],
+            "config": {"workload": PFASST_NAME.format(K=pw["n_iter"]), "precision": prec, "slices": P,
+                       "iterations": pw["n_iter"],
                        "l2": "flushed between timed calls (256 MB write)", "graph": "one CUDA graph per call",
                        "step": "one pfasst_step call = 4 time steps"},
             "gpu_launches": pf.launch_count() * K, "clocks": clk, "accuracy": acc,
@@ -933,10 +1020,12 @@ def main():
                     help="space-time levels of the headline workload: 2 (the paper's) or 3 (a T42 level added)")
     ap.add_argument("--coriolis", default="explicit", choices=["explicit", "implicit"],
                     help="splitting of the headline workload: the paper's (Coriolis in F_E) or Coriolis in F_I")
-    ap.add_argument("--workload", default="headline", choices=["headline", "ensemble", "adjoint", "pfasst"],
+    ap.add_argument("--workload", default="headline",
+                    choices=["headline", "ensemble", "adjoint", "pfasst", "sdc_t21", "mlsdc_t85"],
                     help="headline: one T170/T85 member; ensemble: the 96-member uneven-truncation ensemble; "
                          "adjoint: the 48-step T85/T42 gradient; pfasst: 4 time slices of the headline "
-                         "schedule advanced by PFASST")
+                         "schedule advanced by PFASST; sdc_t21 / mlsdc_t85: the smaller parity workloads")
+    ap.add_argument("--pfasst-iters", type=int, default=None, help="pfasst: iterations (default 4)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -946,6 +1035,8 @@ def main():
         return run_adjoint(args)
     if args.workload == "pfasst":
         return run_pfasst(args)
+    if args.workload in SMALL:
+        return run_small(args)
     args.warmup = max(3, args.warmup)
 
     import numpy as np

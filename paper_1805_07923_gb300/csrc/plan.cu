@@ -41,6 +41,17 @@ bool pdl_enabled() {
     return on;
 }
 
+void set_carveout_once(const void* kernel) {
+    static std::mutex mu;
+    static std::vector<const void*> done;
+    std::lock_guard<std::mutex> lock(mu);
+    if (std::find(done.begin(), done.end(), kernel) != done.end()) return;
+    done.push_back(kernel);
+    // a hint: ignore a refusal (the kernel then runs with the driver's choice)
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, kCarveoutPct) != cudaSuccess)
+        (void)cudaGetLastError();
+}
+
 mlsdc_status raise_smem_limit(const void* fn, size_t bytes) {
     static std::mutex mu;
     if (bytes <= 48 * 1024) return MLSDC_OK;
