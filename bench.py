@@ -311,17 +311,27 @@ def build_mlsdc(M, prec, coriolis_implicit=False, levels=2):
 
 def node_update_bytes(R, n_nodes, m, coriolis_implicit):
     """Algorithmic bytes of node update m (node m + 1 of a level with n_nodes
-    Lobatto nodes, no tau) for one member: reads Theta^0, the old F_I and F_E
-    at every node, the new F_I and F_E at nodes 1..m; writes Theta and F_I at
-    node m + 1 (and, for m = 0, node 0 of the new F arrays); plus the solve's
-    tables (per degree reciprocals and the degree of each coefficient, or
-    with implicit Coriolis the factored chains, 2 x 64 B per coefficient, and
-    the Coriolis factors, 32 B per coefficient).  Complex float64 values."""
+    Lobatto nodes, no tau) for one member, complex float64 values.
+    Paper splitting, the sweep-constant parts formed once per sweep: m = 0
+    reads Theta^0 and the old F_I, F_E at every node and writes the
+    n_nodes - 2 sweep-constant arrays S_2..S_M; m >= 1 reads S_{m+1} and the
+    new F_I, F_E at nodes 1..m.  Implicit Coriolis: every update reads
+    Theta^0, the old F_I, F_E at every node and the new ones at nodes 1..m.
+    Both write Theta and F_I at node m + 1 (and, for m = 0, node 0 of the new
+    F arrays), plus the solve's tables (per degree reciprocals and the degree
+    of each coefficient, or with implicit Coriolis the factored chains, 2 x 64
+    B per coefficient, and the Coriolis factors, 32 B per coefficient)."""
     nc = (R + 1) * (R + 2) // 2
     field3 = 3 * nc * 16
-    reads = field3 * (1 + 2 * n_nodes + 2 * m)
     writes = field3 * (2 + (2 if m == 0 else 0))
-    tables = nc * (128 + 32) if coriolis_implicit else (R + 1) * 16 + nc * 4
+    if coriolis_implicit:
+        reads = field3 * (1 + 2 * n_nodes + 2 * m)
+        tables = nc * (128 + 32)
+    else:
+        reads = field3 * ((1 + 2 * n_nodes) if m == 0 else (1 + 2 * m))
+        if m == 0 and n_nodes >= 3:
+            writes += field3 * (n_nodes - 2)
+        tables = (R + 1) * 16 + nc * 4
     return reads + writes + tables
 
 

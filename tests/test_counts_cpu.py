@@ -47,8 +47,11 @@ def test_node_update_bytes():
     R, n = 3, 5
     nc = (R + 1) * (R + 2) // 2
     field3 = 3 * nc * 16
-    # m = 0: Theta^0, old F_I and F_E at 5 nodes; writes Theta, F_I at node 1 and node 0 of the new F
-    assert bench.node_update_bytes(R, n, 0, False) == field3 * 11 + field3 * 4 + (R + 1) * 16 + nc * 4
+    # m = 0: Theta^0, old F_I and F_E at 5 nodes; writes Theta, F_I at node 1, node 0 of the new F
+    # and the sweep-constant arrays S_2..S_4
+    assert bench.node_update_bytes(R, n, 0, False) == field3 * 11 + field3 * 7 + (R + 1) * 16 + nc * 4
+    # m = 2: S_3 and the new F_I, F_E at nodes 1..2; writes Theta, F_I at node 3
+    assert bench.node_update_bytes(R, n, 2, False) == field3 * 5 + field3 * 2 + (R + 1) * 16 + nc * 4
     # m = 2 with implicit Coriolis: also new F_I, F_E at nodes 1..2, and the chains' tables
     assert bench.node_update_bytes(R, n, 2, True) == field3 * 15 + field3 * 2 + nc * 160
     assert math.isclose(bench.node_update_bytes(170, 5, 0, True) / 1e6, 12.94128, rel_tol=1e-6)
