@@ -20,8 +20,6 @@
 // solve then runs the two substitutions, each a first-order linear
 // recurrence, as a warp-wide scan of affine maps: one warp per chain, a
 // contiguous segment of the chain per lane.  All float64.
-#include <cooperative_groups.h>
-
 #include "internal.h"
 #include "sdc_internal.h"
 
@@ -394,204 +392,14 @@ __global__ void __launch_bounds__(kCorThreads) k_implicit_rhs_cor(const double2*
 }
 
 // standalone solve: right-hand sides [3][R+1], solution [2][R+1], factors [2][R+1]
-// ---------------------------------------------------------------- cluster split
-// The same node update with each chain split over a cluster of kCorCluster
-// CTAs (distributed shared memory): CTA rank r takes the contiguous segment
-// [r s, r s + s) of the chain, s = ceil(nm / kCorCluster), for the right-hand
-// sides, both substitutions and the outputs, so a long chain (small m, up to
-// R + 1 elements) is spread over several SMs.  A substitution is a
-// composition of affine maps z -> p + q z: every CTA first composes its
-// segment (a block scan, as block_recurrence), the segment maps meet across
-// the cluster (each CTA reads the maps of the segments before it in the
-// recurrence's order from their CTAs' shared memory), and every CTA then runs
-// its segment from that carry.  The outputs of a segment's end elements need
-// the neighbouring solution values, read from the neighbouring CTA.  Every
-// CTA reaches every cluster barrier (empty segments included); there is no
-// other wait.
-constexpr int kCorCluster = 4;
-constexpr int kCorClusterMinLen = 64;  // chains of at least this many elements (R + 1) use the cluster split
-namespace cg = cooperative_groups;
-
-// One substitution over the cluster: positions k of this CTA's segment
-// [k0, k1) of a chain of nm elements, in ascending k (Fwd) or descending k
-// (!Fwd) order.  pq(k, p, q) is called once per k (p is kept in pbuf[k]),
-// put(k, z) receives the result.  seg[0..1] of every CTA holds its segment's
-// map (A, B); wsum holds the warp maps.
-template <bool Fwd, class PQ, class Put>
-__device__ __forceinline__ void cluster_recurrence(cg::cluster_group& cl, int k0, int k1, PQ pq, Put put,
-                                                   double2* pbuf, double2* wsum, double2* seg) {
-    const int T = blockDim.x, t = threadIdx.x, lane = t & 31, warp = t >> 5, nw = T >> 5;
-    const int n = k1 - k0;
-    const int s = (n + T - 1) / T;
-    const int j0 = min(n, t * s), j1 = min(n, j0 + s);
-    double2 A = make_double2(1.0, 0.0), B = make_double2(0.0, 0.0);
-    for (int j = j0; j < j1; ++j) {
-        const int k = Fwd ? k0 + j : k1 - 1 - j;
-        double2 p, q;
-        pq(k, p, q);
-        pbuf[k] = p;
-        B = zfma(q, B, p);
-        A = zmul(q, A);
-    }
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const double2 A1 = zshfl_up(A, d), B1 = zshfl_up(B, d);
-        if (lane >= d) {
-            B = zfma(A, B1, B);
-            A = zmul(A, A1);
-        }
-    }
-    if (lane == 31) {
-        wsum[warp] = A;
-        wsum[nw + warp] = B;
-    }
-    __syncthreads();
-    if (t == 0) {  // this segment's map: the warp maps in order
-        double2 SA = make_double2(1.0, 0.0), SB = make_double2(0.0, 0.0);
-        for (int w = 0; w < nw; ++w) {
-            SB = zfma(wsum[w], SB, wsum[nw + w]);
-            SA = zmul(wsum[w], SA);
-        }
-        seg[0] = SA;
-        seg[1] = SB;
-    }
-    cl.sync();
-    // the value before this segment: the earlier segments' maps applied to 0
-    const int r = (int)cl.block_rank(), R = (int)cl.num_blocks();
-    double2 z = make_double2(0.0, 0.0);
-    for (int i = 0; i < R; ++i) {
-        const int q = Fwd ? i : R - 1 - i;
-        if (Fwd ? q >= r : q <= r) break;
-        const double2* ps = cl.map_shared_rank(seg, q);
-        z = zfma(ps[0], z, ps[1]);
-    }
-    for (int w = 0; w < warp; ++w) z = zfma(wsum[w], z, wsum[nw + w]);
-    const double2 Ae = zshfl_up(A, 1), Be = zshfl_up(B, 1);
-    if (lane > 0) z = zfma(Ae, z, Be);
-    for (int j = j0; j < j1; ++j) {
-        const int k = Fwd ? k0 + j : k1 - 1 - j;
-        double2 p, q;
-        pq(k, p, q);
-        z = zfma(q, z, pbuf[k]);
-        put(k, z);
-    }
-    cl.sync();  // seg and wsum are reused; the results are complete across the cluster
-}
-
-__global__ void __launch_bounds__(kCorNodeThreads) k_sweep_node_cor_cl(double2* Th, const double2* __restrict__ FIo,
-                                                                     const double2* __restrict__ FEo, double2* FIn,
-                                                                     double2* FEn, const double2* __restrict__ tau,
-                                                                     const CorFac* __restrict__ fac,
-                                                                     const double* __restrict__ cor, int R, int nc,
-                                                                     NodeRow row, Phys ph, double two_omega,
-                                                                     size_t ms) {
-    extern __shared__ double2 cor_sm[];
-    cg::cluster_group cl = cg::this_cluster();
-    pdl_wait();
-    pdl_launch();
-    const size_t mo = blockIdx.z * ms;
-    Th += mo;
-    FIo += mo;
-    FEo += mo;
-    FIn += mo;
-    FEn += mo;
-    if (tau) tau += mo;
-    const int rank = (int)cl.block_rank(), CS = (int)cl.num_blocks();
-    const int m = blockIdx.x / CS, c = blockIdx.y, ld = R + 1, nm = ld - m, off = moff(R, m);
-    const int s = (nm + CS - 1) / CS, k0 = min(nm, rank * s), k1 = min(nm, k0 + s);
-    const size_t node = (size_t)3 * nc;
-    const double alpha = row.qimm;
-    double2* sr = cor_sm;                                     // [R+1] b_zeta or b_delta of element k
-    double2* sp = cor_sm + ld;                                // [R+1] b_Phi at the delta elements
-    double2* sx = cor_sm + 2 * ld;                            // [R+1] the chain's solution
-    double2* pb = cor_sm + 3 * ld;                            // [R+1] the recurrences' p_k
-    double2* ws = cor_sm + 4 * ld;                            // [2 warps] warp maps
-    double2* sg = ws + 2 * (kCorNodeThreads / 32);            // [2] this segment's map
-    CorFac* sf = reinterpret_cast<CorFac*>(sg + 2);           // [R+1] factors (this segment's)
-    {
-        constexpr int kV = sizeof(CorFac) / sizeof(double2);
-        const double2* src = reinterpret_cast<const double2*>(fac + (size_t)c * nc + off + k0);
-        double2* dst = reinterpret_cast<double2*>(sf + k0);
-        for (int t = threadIdx.x; t < (k1 - k0) * kV; t += blockDim.x) dst[t] = src[t];
-    }
-    for (int t = threadIdx.x; t < 2 * (k1 - k0); t += blockDim.x) {
-        const int k = k0 + (t >> 1), second = t & 1;
-        const bool zeta = ((k + c) & 1) == 0;
-        if (zeta && second) continue;
-        const int f = zeta ? 1 : (second ? 0 : 2);
-        const double2 b = node_rhs(Th, FIo, FEo, FIn, FEn, tau, node, (size_t)f * nc + off + k, row);
-        (second ? sp : sr)[k] = b;
-    }
-    __syncthreads();
-    cluster_recurrence<true>(
-        cl, k0, k1,
-        [&](int k, double2& p, double2& q) {
-            if (((k + c) & 1) == 0) {
-                p = sr[k];
-            } else {
-                const double aL = sf[k].aLc;
-                p = make_double2(fma(-aL, sp[k].x, sr[k].x), fma(-aL, sp[k].y, sr[k].y));
-            }
-            q = zneg(sf[k].l);
-        },
-        [&](int k, double2 y) { sx[k] = y; }, pb, ws, sg);
-    cluster_recurrence<false>(
-        cl, k0, k1,
-        [&](int k, double2& p, double2& q) {
-            p = zmul(sf[k].iw, sx[k]);
-            q = zneg(sf[k].u);
-        },
-        [&](int k, double2 x) { sx[k] = x; }, pb, ws, sg);
-    // the neighbours across the segment ends (the last cl.sync made them final)
-    const double2 zero = make_double2(0.0, 0.0);
-    double2 before = zero, after = zero;
-    if (k0 < k1) {
-        if (k0 > 0) before = cl.map_shared_rank(sx, rank - 1)[k0 - 1];
-        if (k1 < nm) after = cl.map_shared_rank(sx, rank + 1)[k1];
-    }
-    const size_t om = (size_t)(row.m + 1) * node + off;
-    for (int k = k0 + (int)threadIdx.x; k < k1; k += blockDim.x) {
-        const int n = m + k;
-        const double L = -n * (n + 1.0) * ph.inv_a2;
-        const double nl = ph.nu * L;
-        const double* cf = cor + 4 * (size_t)(off + k);
-        const double2 v = sx[k];
-        const double2 lo = k > k0 ? sx[k - 1] : before, hi = k + 1 < k1 ? sx[k + 1] : after;
-        if (((k + c) & 1) == 0) {
-            double2 fz = make_double2(nl * v.x, nl * v.y);
-            coriolis_zeta_row(cf, lo, v, hi, two_omega, fz);
-            Th[om + nc + k] = v;
-            FIn[om + nc + k] = fz;
-        } else {
-            const double2 p = cor_phi(sp[k], v, alpha, ph, sf[k].ic);
-            const double2 fp = make_double2(-ph.phibar * v.x + nl * p.x, -ph.phibar * v.y + nl * p.y);
-            double2 fd = make_double2(-L * p.x + nl * v.x, -L * p.y + nl * v.y);
-            coriolis_delta_row(cf, lo, v, hi, two_omega, fd);
-            Th[om + k] = p;
-            Th[om + 2 * nc + k] = v;
-            FIn[om + k] = fp;
-            FIn[om + 2 * nc + k] = fd;
-        }
-        if (row.m == 0 && c == 0) {
-            for (int f = 0; f < 3; ++f) {
-                const size_t o = (size_t)f * nc + off + k;
-                FIn[o] = FIo[o];
-                FEn[o] = FEo[o];
-            }
-        }
-    }
-    cl.sync();  // no CTA leaves while a neighbour may still read its shared memory
-}
-
 static size_t cor_smem(int R) { return (size_t)5 * (R + 1) * sizeof(double2) + (size_t)2 * (R + 1) * sizeof(CorFac); }
 // node update, one chain: r, b_Phi, solution, p [R+1] each, warp totals, factors [R+1]
 static size_t cor_node_smem(int R) {
-    return (size_t)(4 * (R + 1) + 2 * (kCorNodeThreads / 32) + 2) * sizeof(double2) + (size_t)(R + 1) * sizeof(CorFac);
+    return (size_t)(4 * (R + 1) + 2 * (kCorNodeThreads / 32)) * sizeof(double2) + (size_t)(R + 1) * sizeof(CorFac);
 }
 
 mlsdc_status cor_smem_limits(int R) {
     mlsdc_status s = raise_smem_limit((const void*)k_sweep_node_cor, cor_node_smem(R));
-    if (s == MLSDC_OK) s = raise_smem_limit((const void*)k_sweep_node_cor_cl, cor_node_smem(R));
     if (s == MLSDC_OK) s = raise_smem_limit((const void*)k_cor_solve, cor_smem(R));
     return s;
 }
@@ -636,27 +444,6 @@ mlsdc_status cor_node_launch(sdc_level_t L, double dt, const NodeRow& row_dt, do
     const CorFac* fac = nullptr;
     mlsdc_status s = cor_factors(L, dt, st, &fac);
     if (s != MLSDC_OK) return s;
-    if (R + 1 >= kCorClusterMinLen) {  // long chains: each over a cluster of kCorCluster CTAs
-        set_carveout_once((const void*)k_sweep_node_cor_cl);
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3(kCorCluster * (R + 1), 2, L->members);
-        cfg.blockDim = dim3(kCorNodeThreads);
-        cfg.dynamicSmemBytes = cor_node_smem(R);
-        cfg.stream = st;
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = kCorCluster;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        MLSDC_LAUNCH("k_sweep_node_cor_cl",
-                     cudaLaunchKernelEx(&cfg, k_sweep_node_cor_cl, Th, FIo, FEo, FIn, FEn, tau,
-                                        (const CorFac*)(fac + (size_t)row_dt.m * 2 * nc), (const double*)L->plan->d_cor,
-                                        R, nc, row_dt, phys_of(L->prm), 2.0 * L->prm.omega, L->ms()));
-        L->launches++;
-        return MLSDC_OK;
-    }
     MLSDC_LAUNCH("k_sweep_node_cor",
                  launch_k(k_sweep_node_cor, dim3(R + 1, 2, L->members), dim3(kCorNodeThreads), cor_node_smem(R), st,
                           Th, FIo, FEo, FIn, FEn, tau, fac + (size_t)row_dt.m * 2 * nc, (const double*)L->plan->d_cor,
