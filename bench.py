@@ -251,9 +251,11 @@ def load_peaks():
         return {}
 
 
-def traffic_for(kernel: str):
+def traffic_for(kernel: str, key: str = "bytes_per_launch"):
     """DRAM bytes per launch from a committed ncu capture, if the kernel's
-    sources have not changed since (profiles/traffic.json)."""
+    sources have not changed since (profiles/traffic.json): `bytes_per_launch`
+    with the caches kept between launches (as in the step's graph),
+    `cold_bytes_per_launch` with them flushed before the launch."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             d = json.load(f)
@@ -264,7 +266,7 @@ def traffic_for(kernel: str):
         return None
     if ent.get("src_sha") != sources_sha():
         return None
-    return ent.get("bytes_per_launch")
+    return ent.get(key)
 
 
 def sources_sha() -> str:
@@ -1184,6 +1186,11 @@ def main():
     roof = stage_roofline(prec, top[4], stage_bytes(R_, I_, J_, names.index(top[2]), prec), top[3], on_tc, peaks,
                           lambda: measured_fp64_tflops(torch, dev))
     roof["traffic"] = traffic_for(f"{top[1]}:{kern_names[top[2]]}")
+    roof["traffic_cold"] = traffic_for(f"{top[1]}:{kern_names[top[2]]}", "cold_bytes_per_launch")
+    if roof["traffic"] is not None:
+        roof["traffic_note"] = ("DRAM bytes of one launch with the caches kept (ncu --cache-control none), as in the "
+                                "step's graph: the tables are L2-resident, so the kernel is latency-bound and the "
+                                "HBM fraction is notional; traffic_cold: the same launch from flushed caches")
     roof["kernel"] = f"{top[2]} ({kern_names[top[2]]}) at {top[1]}"
     roof["kernel_ms"] = top[3]
     roof["share_of_step"] = top[0] / step_ms_mean
