@@ -473,19 +473,28 @@ def run_ensemble(args):
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
-    def timed(prec_, K):
-        ens, groups, keep, states = build_ensemble(M, torch, dev, prec_)
-        for _ in range(3):
+    def step(ens, states, persistent):
+        if persistent:
+            M.mlsdc_ensemble_step_persistent(ens, states, w["dt"], w["n_iter"], w["n_coarse"])
+        else:
             M.mlsdc_ensemble_step(ens, states, w["dt"], w["n_iter"], w["n_coarse"], use_graph=True)
+
+    def time_steps(ens, states, K, persistent):
+        for _ in range(3):
+            step(ens, states, persistent)
         torch.cuda.synchronize()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
         for k in range(K):
             flush.zero_()
             ev[k][0].record(stream)
-            M.mlsdc_ensemble_step(ens, states, w["dt"], w["n_iter"], w["n_coarse"], use_graph=True)
+            step(ens, states, persistent)
             ev[k][1].record(stream)
         torch.cuda.synchronize()
-        return sum(a.elapsed_time(b) for a, b in ev), ens, groups, keep, states
+        return sum(a.elapsed_time(b) for a, b in ev)
+
+    def timed(prec_, K):
+        ens, groups, keep, states = build_ensemble(M, torch, dev, prec_)
+        return time_steps(ens, states, K, False), ens, groups, keep, states
 
     K = args.steps
     clocks = ClockSampler(0)
@@ -550,6 +559,14 @@ def run_ensemble(args):
             "e2e": {"value": members * Ke / (e2e_ms * 1e-3), "unit": "member-steps/s", "h2d_bytes_per_step": nbytes,
                     "d2h_bytes_per_step": nbytes},
             }
+    # the same step as one persistent kernel launch per ensemble step (lockstep
+    # phases, device-side grid barrier), on the same ensemble
+    ms_p = time_steps(ens, states, K, True)
+    info = ens.persistent_info()
+    line["persistent_kernel"] = {"member_steps_per_s": members * K / (ms_p * 1e-3), "ms_per_step": ms_p / K,
+                                 "gpu_launches_per_step": ens.launch_count(), "phases": info["phases"],
+                                 "recorded_launches": info["records"], "ctas": info["ctas"],
+                                 "in_graph": bool(info["in_graph"]), "device_error": ens.device_error()}
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_ensemble()
     if prec != "fp64":

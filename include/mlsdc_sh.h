@@ -389,6 +389,34 @@ mlsdc_status mlsdc_ensemble_step(mlsdc_ensemble_t ens, double* const* states, do
                                  int n_coarse_sweeps, int use_graph, void* stream);
 mlsdc_status mlsdc_ensemble_launch_count(mlsdc_ensemble_t ens, int64_t* launches);
 
+/* The same ensemble step as ONE persistent kernel launch (with two 4-byte
+ * memsets) captured in a CUDA graph: the groups' launches of the step are
+ * recorded once per (states, dt, n_iter, n_coarse_sweeps) and laid out as
+ * lockstep phases (phase i = the i-th launch of every group's step; Algorithm
+ * 1, Sec. 4.3.2, for all members), which one cooperative launch of one CTA
+ * per SM runs with a device-side grid barrier between phases.  Every barrier
+ * wait is bounded (4 s of the global timer): a wait that gives up ends the
+ * launch and leaves code 3 in mlsdc_ensemble_device_error.  Results equal
+ * mlsdc_ensemble_step's bit for bit (the same device code over the same
+ * blocks).  MLSDC_ERR_INVALID, with the reason in mlsdc_last_error(), for
+ * implicit-Coriolis levels or a launch the kernel cannot host; a stream that
+ * cannot capture the cooperative launch gets it launched directly. */
+mlsdc_status mlsdc_ensemble_step_persistent(mlsdc_ensemble_t ens, double* const* states, double dt, int n_iter,
+                                            int n_coarse_sweeps, void* stream);
+/* Shape of the last persistent step: phases, recorded launches, CTAs of the
+ * launch, and whether it runs from a graph.  MLSDC_ERR_INVALID before the
+ * first persistent step.  Null outputs are skipped. */
+mlsdc_status mlsdc_ensemble_persistent_info(mlsdc_ensemble_t ens, int* phases, int* records, int* ctas,
+                                            int* in_graph);
+/* The persistent kernel's error word (sticky): 0, or 3 when a grid-barrier
+ * wait gave up (synchronous read). */
+mlsdc_status mlsdc_ensemble_device_error(mlsdc_ensemble_t ens, int* code);
+/* Check of the grid barrier's bound: two CTAs wait at a barrier that
+ * expects one arrival more than the grid makes, with a limit of timeout_ms
+ * (1..2000); *code = 3 when the waits gave up and returned (synchronous).
+ * Not a paper operation. */
+mlsdc_status mlsdc_selftest_grid_barrier_timeout(int timeout_ms, int* code);
+
 /* Stage timing of swe_explicit_rhs for roofline reporting: captures `reps`
  * back-to-back launches of each of the plan's F_E stage kernels into a CUDA
  * graph (as the step runs them), replays it once to warm up and once timed

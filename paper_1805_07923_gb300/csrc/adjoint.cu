@@ -159,14 +159,15 @@ __global__ void __launch_bounds__(256) k_grid_ad(const double2* __restrict__ fou
     const int j = blockIdx.x;
     const int Hn = I >> 1, logH = logI - 1;
     double2* stab = sx + 9 * Hn;
-    fft4_stage_twiddles(stab, tw, Hn, logH, I);
+    const Blk bk = hw_blk(smem_raw);
+    fft4_stage_twiddles(bk, stab, tw, Hn, logH, I);
     const size_t fs = (size_t)J * (R + 1);
     for (int t = threadIdx.x; t < 9 * Hn; t += blockDim.x) {
         const int f = t >> logH, k = t & (Hn - 1);
         sx[f * Hn + swz(k)] = irfft_pack(four_in + f * fs + (size_t)j * (R + 1), k, R, Hn, tw);
     }
     __syncthreads();
-    fft4_dif(sx, 9, Hn, logH, stab, true);
+    fft4_dif(bk, sx, 9, Hn, logH, stab, true);
     // lat[j] = (mu, 1/(1-mu^2), w/((1-mu^2) I), w/I)
     const double f = two_omega * lat[4 * j];
     const double rc = lat[4 * j + 1];
@@ -192,7 +193,7 @@ __global__ void __launch_bounds__(256) k_grid_ad(const double2* __restrict__ fou
         for (int k = 0; k < 4; ++k) sx[k * Hn + q] = make_double2(o[k][0], o[k][1]);
     }
     __syncthreads();
-    fft4_dit(sx, 4, Hn, logH, stab, false);
+    fft4_dit(bk, sx, 4, Hn, logH, stab, false);
     for (int t = threadIdx.x; t < 4 * (R + 1); t += blockDim.x) {
         const int fld = t / (R + 1);
         const int m = t - fld * (R + 1);

@@ -4,6 +4,8 @@
 
 #include <cuda_runtime.h>
 
+#include "vblock.cuh"
+
 namespace mlsdc {
 
 template <class T> struct cplx;
@@ -121,19 +123,20 @@ template <class C> __device__ __forceinline__ C times_s(C z, bool inverse) {  //
 template <class C> __device__ __forceinline__ C maybe_conj(C w, bool inverse) { return inverse ? cconj(w) : w; }
 
 // Fill the stage table (N - 1 entries) from tw[k] = exp(-2 pi i k / I),
-// k < I/2 (any memory space); the caller synchronises before use.
+// k < I/2 (any memory space); the caller synchronises before use.  These
+// three work over the threads of the (virtual) block bk.
 template <class C>
-__device__ void fft4_stage_twiddles(C* tab, const C* __restrict__ tw, int N, int logN, int I) {
+__device__ __forceinline__ void fft4_stage_twiddles(const Blk& bk, C* tab, const C* __restrict__ tw, int N, int logN, int I) {
     const int half = I >> 1;
     int off = 0;
     if (logN & 1) {
         const int H = N >> 1;
-        for (int j = threadIdx.x; j < H; j += blockDim.x) tab[j] = tw[2 * j];
+        for (int j = bk.t; j < H; j += bk.nt) tab[j] = tw[2 * j];
         off = H;
     }
     for (int logL = (logN & 1) ? logN - 1 : logN; logL >= 2; logL -= 2) {
         const int Q = 1 << (logL - 2), st = I >> logL;
-        for (int e = threadIdx.x; e < 3 * Q; e += blockDim.x) {
+        for (int e = bk.t; e < 3 * Q; e += bk.nt) {
             const int q = e / Q + 1, j = e - (q - 1) * Q;
             tab[off + e] = tw_at(tw, q * j * st, half);
         }
@@ -142,11 +145,11 @@ __device__ void fft4_stage_twiddles(C* tab, const C* __restrict__ tw, int N, int
 }
 
 template <class C>
-__device__ void fft4_dif(C* x, int narr, int N, int logN, const C* tab, bool inverse) {
+__device__ __forceinline__ void fft4_dif(const Blk& bk, C* x, int narr, int N, int logN, const C* tab, bool inverse) {
     int L = N, logL = logN, off = 0;
     if (logN & 1) {
         const int H = N >> 1;
-        for (int t = threadIdx.x; t < narr * H; t += blockDim.x) {
+        for (int t = bk.t; t < narr * H; t += bk.nt) {
             const int ar = t >> (logN - 1), j = t & (H - 1);
             C* xa = x + ar * N;
             const C w = maybe_conj(tab[j], inverse);
@@ -154,7 +157,7 @@ __device__ void fft4_dif(C* x, int narr, int N, int logN, const C* tab, bool inv
             xa[swz(j)] = cadd(u, v);
             xa[swz(j + H)] = cmul(csub(u, v), w);
         }
-        __syncthreads();
+        bk.sync();
         off = H;
         L >>= 1;
         --logL;
@@ -162,7 +165,7 @@ __device__ void fft4_dif(C* x, int narr, int N, int logN, const C* tab, bool inv
     for (; L >= 4; L >>= 2, logL -= 2) {
         const int Q = L >> 2, logQ = logL - 2;
         const C* tq = tab + off;
-        for (int t = threadIdx.x; t < narr * (N >> 2); t += blockDim.x) {
+        for (int t = bk.t; t < narr * (N >> 2); t += bk.nt) {
             const int ar = t >> (logN - 2), r = t & ((N >> 2) - 1);
             const int g = r >> logQ, j = r & (Q - 1);
             C* xa = x + ar * N;
@@ -174,13 +177,13 @@ __device__ void fft4_dif(C* x, int narr, int N, int logN, const C* tab, bool inv
             xa[swz(i0 + 2 * Q)] = cmul(csub(apc, bpd), maybe_conj(tq[Q + j], inverse));
             xa[swz(i0 + 3 * Q)] = cmul(csub(amc, sbmd), maybe_conj(tq[2 * Q + j], inverse));
         }
-        __syncthreads();
+        bk.sync();
         off += 3 * Q;
     }
 }
 
 template <class C>
-__device__ void fft4_dit(C* x, int narr, int N, int logN, const C* tab, bool inverse) {
+__device__ __forceinline__ void fft4_dit(const Blk& bk, C* x, int narr, int N, int logN, const C* tab, bool inverse) {
     const int top = (logN & 1) ? logN - 1 : logN;
     const int r2 = (logN & 1) ? (N >> 1) : 0;  // entries of the radix-2 stage
     for (int logL = 2; logL <= top; logL += 2) {
@@ -189,7 +192,7 @@ __device__ void fft4_dit(C* x, int narr, int N, int logN, const C* tab, bool inv
         int off = r2;
         for (int l2 = top; l2 > logL; l2 -= 2) off += 3 * (1 << (l2 - 2));
         const C* tq = tab + off;
-        for (int t = threadIdx.x; t < narr * (N >> 2); t += blockDim.x) {
+        for (int t = bk.t; t < narr * (N >> 2); t += bk.nt) {
             const int ar = t >> (logN - 2), r = t & ((N >> 2) - 1);
             const int g = r >> logQ, j = r & (Q - 1);
             C* xa = x + ar * N;
@@ -204,11 +207,11 @@ __device__ void fft4_dit(C* x, int narr, int N, int logN, const C* tab, bool inv
             xa[swz(i0 + 2 * Q)] = csub(apc, bpd);
             xa[swz(i0 + 3 * Q)] = csub(amc, sbmd);
         }
-        __syncthreads();
+        bk.sync();
     }
     if (logN & 1) {
         const int H = N >> 1;
-        for (int t = threadIdx.x; t < narr * H; t += blockDim.x) {
+        for (int t = bk.t; t < narr * H; t += bk.nt) {
             const int ar = t >> (logN - 1), j = t & (H - 1);
             C* xa = x + ar * N;
             const C w = maybe_conj(tab[j], inverse);
@@ -216,7 +219,7 @@ __device__ void fft4_dit(C* x, int narr, int N, int logN, const C* tab, bool inv
             xa[swz(j)] = cadd(u, v);
             xa[swz(j + H)] = csub(u, v);
         }
-        __syncthreads();
+        bk.sync();
     }
 }
 

@@ -11,6 +11,7 @@
 
 #include "mlsdc_sh.h"
 #include "node_update.cuh"
+#include "vblock.cuh"
 
 namespace mlsdc {
 
@@ -83,6 +84,10 @@ void set_carveout_once(const void* kernel);
 template <typename... KArgs, typename... Args>
 inline cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
                             Args&&... args) {
+    if (Recorder* r = active_recorder()) {  // a kernel the persistent kernel has no body for
+        r->refused = true;
+        return cudaErrorNotSupported;
+    }
     set_carveout_once((const void*)kernel);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = grid;
@@ -95,6 +100,21 @@ inline cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, siz
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
+// launch_k for a kernel whose body the persistent ensemble kernel can run:
+// with a recorder installed on this thread the launch is recorded (body,
+// grid, the shared memory the body needs: `smem` plus `static_smem` that the
+// kernel itself declares, tensor-memory columns per block, packed
+// arguments) instead of issued.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_b(Body body, int tmem_cols, size_t static_smem, void (*kernel)(KArgs...), dim3 grid,
+                            dim3 block, size_t smem, cudaStream_t st, Args&&... args) {
+    if (Recorder* r = active_recorder()) {
+        record_launch(r, body, tmem_cols, smem + static_smem, kernel, grid, block, std::forward<Args>(args)...);
+        return cudaSuccess;
+    }
+    return launch_k(kernel, grid, block, smem, st, std::forward<Args>(args)...);
 }
 
 #define MLSDC_LAUNCH(name, call)                          \

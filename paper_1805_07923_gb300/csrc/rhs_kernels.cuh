@@ -54,24 +54,20 @@ struct MemberStrides {
 // U^m = (1/a) sum_n [ i m chi P - psi H ],  V^m = (1/a) sum_n [ i m psi P + chi H ]
 // with psi, chi = -a^2/(n(n+1)) (zeta, delta) (Helmholtz, Sec. 2).
 template <class T>
-__global__ void __launch_bounds__(32 * kSynthWarps) k_synth_rhs(const double2* __restrict__ state,
-                                                                const T* __restrict__ P, const T* __restrict__ H,
-                                                                const T* __restrict__ invnn,
-                                                                const Chunk* __restrict__ chunks, int R, int J2,
-                                                                int nc, double na2, double ia, C_t<T>* __restrict__ four,
-                                                                MemberStrides ms) {
+__device__ __forceinline__ void b_synth_rhs(const Blk& bk, const double2* state, const T* P, const T* H,
+                                            const T* invnn, const Chunk* chunks, int R, int J2, int nc, double na2,
+                                            double ia, C_t<T>* four, MemberStrides ms) {
     using C = C_t<T>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* sc = reinterpret_cast<C*>(smem_raw);  // [nm][4]: zeta, Phi', chi, psi; reused for the reduction
+    C* sc = reinterpret_cast<C*>(bk.smem);  // [nm][4]: zeta, Phi', chi, psi; reused for the reduction
     pdl_wait();
     pdl_launch();
-    state += blockIdx.y * ms.state;
-    four += blockIdx.y * ms.four_in;
-    const Chunk ch = chunks[blockIdx.x];
+    state += bk.idx.y * ms.state;
+    four += bk.idx.y * ms.four_in;
+    const Chunk ch = chunks[bk.idx.x];
     const int m = ch.m;
     const int nm = R + 1 - m;
     const int off = m * (R + 1) - m * (m - 1) / 2;
-    for (int k = threadIdx.x; k < nm; k += blockDim.x) {
+    for (int k = bk.t; k < nm; k += bk.nt) {
         // psi, chi = -a^2/(n(n+1)) (zeta, delta), the factor from the plan's table
         const T s = T(na2) * invnn[m + k];
         const double2 ph = state[off + k];
@@ -82,9 +78,9 @@ __global__ void __launch_bounds__(32 * kSynthWarps) k_synth_rhs(const double2* _
         sc[4 * k + 2] = mkc(T(de.x) * s, T(de.y) * s);
         sc[4 * k + 3] = mkc(T(ze.x) * s, T(ze.y) * s);
     }
-    __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const int wid = threadIdx.x >> 5;
+    bk.sync();
+    const int lane = bk.t & 31;
+    const int wid = bk.t >> 5;
     const int j = ch.start + lane;
     const bool live = j < J2;
     const C zero = mkc(T(0), T(0));
@@ -105,7 +101,7 @@ __global__ void __launch_bounds__(32 * kSynthWarps) k_synth_rhs(const double2* _
             cfma(axH, h, x);
         }
     }
-    __syncthreads();  // coefficient table no longer needed: reuse it for the partial sums
+    bk.sync();  // coefficient table no longer needed: reuse it for the partial sums
     C* red = sc;      // [kSynthWarps][6][32]
     red[(wid * 6 + 0) * 32 + lane] = az;
     red[(wid * 6 + 1) * 32 + lane] = ap;
@@ -113,7 +109,7 @@ __global__ void __launch_bounds__(32 * kSynthWarps) k_synth_rhs(const double2* _
     red[(wid * 6 + 3) * 32 + lane] = asP;
     red[(wid * 6 + 4) * 32 + lane] = asH;
     red[(wid * 6 + 5) * 32 + lane] = axH;
-    __syncthreads();
+    bk.sync();
     if (wid != 0 || !live) return;
     C e[6], o[6];
     for (int q = 0; q < 6; ++q) {
@@ -142,36 +138,44 @@ __global__ void __launch_bounds__(32 * kSynthWarps) k_synth_rhs(const double2* _
     four[3 * fs + iN] = cscale(cadd(cim(dm, sPN), xHN), iaT);
     four[3 * fs + iS] = cscale(cadd(cim(dm, sPS), xHS), iaT);
 }
+template <class T>
+__global__ void __launch_bounds__(32 * kSynthWarps) k_synth_rhs(const double2* __restrict__ state,
+                                                                const T* __restrict__ P, const T* __restrict__ H,
+                                                                const T* __restrict__ invnn,
+                                                                const Chunk* __restrict__ chunks, int R, int J2,
+                                                                int nc, double na2, double ia, C_t<T>* __restrict__ four,
+                                                                MemberStrides ms) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    b_synth_rhs<T>(hw_blk(smem_raw), state, P, H, invnn, chunks, R, J2, nc, na2, ia, four, ms);
+}
 
 // LPB latitudes per CTA (1, or 2 adjacent ones for latitude-contiguous
 // output: the two values of a (field, m) pair then leave in one store).
 template <class T, int LPB>
-__global__ void __launch_bounds__(256) k_grid_rhs(const C_t<T>* __restrict__ four_in, C_t<T>* __restrict__ four_out,
-                                                  const T* __restrict__ lat, const C_t<T>* __restrict__ tw,
-                                                  int R, int I, int logI, int J,
-                                                  double two_omega, MemberStrides ms, FourStride fx) {
+__device__ __forceinline__ void b_grid_rhs(const Blk& bk, const C_t<T>* four_in, C_t<T>* four_out, const T* lat,
+                                           const C_t<T>* __restrict__ tw, int R, int I, int logI, int J,
+                                           double two_omega, MemberStrides ms, FourStride fx) {
     using C = C_t<T>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     // [LPB][4][I/2]: zeta, Phi', U, V packed rows; then [LPB][5][I/2]: A..E; then the twiddles
-    C* sx = reinterpret_cast<C*>(smem_raw);
+    C* sx = reinterpret_cast<C*>(bk.smem);
     const int Hn = I >> 1, logH = logI - 1;
     C* stab = sx + 9 * LPB * Hn;                 // stage twiddles (I/2 - 1 entries)
-    fft4_stage_twiddles(stab, tw, Hn, logH, I);  // constant table
+    fft4_stage_twiddles(bk, stab, tw, Hn, logH, I);  // constant table
     pdl_wait();
     pdl_launch();
-    four_in += blockIdx.y * ms.four_in;
-    four_out += blockIdx.y * ms.four_out;
-    const int j0 = blockIdx.x * LPB;
+    four_in += bk.idx.y * ms.four_in;
+    four_out += bk.idx.y * ms.four_out;
+    const int j0 = bk.idx.x * LPB;
     const size_t fs = (size_t)J * (R + 1);
-    for (int t = threadIdx.x; t < 4 * LPB * Hn; t += blockDim.x) {
+    for (int t = bk.t; t < 4 * LPB * Hn; t += bk.nt) {
         const int r = t >> logH, k = t & (Hn - 1);  // row r = 4 l + f
         const int l = r >> 2, f = r & 3;
         sx[r * Hn + swz(k)] = irfft_pack(four_in + f * fs + (size_t)(j0 + l) * (R + 1), k, R, Hn, tw);
     }
-    __syncthreads();
+    bk.sync();
     // inverse by decimation in frequency: slot q now holds the longitude pair
     // at the digit-reversed position of q
-    fft4_dif(sx, 4 * LPB, Hn, logH, stab, true);
+    fft4_dif(bk, sx, 4 * LPB, Hn, logH, stab, true);
     C* y = sx + 4 * LPB * Hn;
     // lat[j] = (mu, 1/(1-mu^2), w/((1-mu^2) I), w/I): no float64 division here
     T fl[LPB], rcl[LPB];
@@ -180,7 +184,7 @@ __global__ void __launch_bounds__(256) k_grid_rhs(const C_t<T>* __restrict__ fou
         fl[l] = T(two_omega) * lat[4 * (j0 + l)];
         rcl[l] = lat[4 * (j0 + l) + 1];
     }
-    for (int t = threadIdx.x; t < LPB * Hn; t += blockDim.x) {
+    for (int t = bk.t; t < LPB * Hn; t += bk.nt) {
         const int l = LPB == 1 ? 0 : t >> logH;
         const C* xl = sx + 4 * l * Hn;
         C* yl = y + 5 * l * Hn;
@@ -198,16 +202,16 @@ __global__ void __launch_bounds__(256) k_grid_rhs(const C_t<T>* __restrict__ fou
         yl[4 * Hn + q] = mkc(T(0.5) * (u.x * u.x + v.x * v.x) * rc,               // E
                              T(0.5) * (u.y * u.y + v.y * v.y) * rc);
     }
-    __syncthreads();
+    bk.sync();
     // forward by decimation in time from the digit-reversed slots: natural order out
-    fft4_dit(y, 5 * LPB, Hn, logH, stab, false);
+    fft4_dit(bk, y, 5 * LPB, Hn, logH, stab, false);
     T sAD[LPB], sE[LPB];  // w/((1-mu^2) I) for A..D, w/I for E
 #pragma unroll
     for (int l = 0; l < LPB; ++l) {
         sAD[l] = lat[4 * (j0 + l) + 2];
         sE[l] = lat[4 * (j0 + l) + 3];
     }
-    for (int t = threadIdx.x; t < 5 * (R + 1); t += blockDim.x) {
+    for (int t = bk.t; t < 5 * (R + 1); t += bk.nt) {
         const int fld = t / (R + 1);
         const int m = t - fld * (R + 1);
         if (LPB == 1) {
@@ -229,36 +233,49 @@ __global__ void __launch_bounds__(256) k_grid_rhs(const C_t<T>* __restrict__ fou
         }
     }
 }
+template <class T, int LPB>
+__global__ void __launch_bounds__(256) k_grid_rhs(const C_t<T>* __restrict__ four_in, C_t<T>* __restrict__ four_out,
+                                                  const T* __restrict__ lat, const C_t<T>* __restrict__ tw,
+                                                  int R, int I, int logI, int J,
+                                                  double two_omega, MemberStrides ms, FourStride fx) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    b_grid_rhs<T, LPB>(hw_blk(smem_raw), four_in, four_out, lat, tw, R, I, logI, J, two_omega, ms, fx);
+}
 
 // div(X,Y)^m_n = (1/a) sum_j [ i m X' P - Y' H ], curl(X,Y)^m_n = (1/a) sum_j [ i m Y' P + X' H ]
 // with X', Y' the weighted Fourier coefficients (integration by parts of the
 // mu-derivatives); E^m_n = sum_j E' P.  With two_omega_lin != 0 the grid
 // products were formed without f and the Coriolis part is added here exactly.
+constexpr int kAnalTW = 32;  // latitudes per tile of the CUDA-core analysis
+// shared memory of the CUDA-core analysis: per warp [lat][field A..E][even,
+// odd] sums, then the partial sums of warps 1.. for the reduction
 template <class T>
-__global__ void __launch_bounds__(32 * kAnalWarpsMax) k_anal_rhs(const C_t<T>* __restrict__ four_out,
-                                                                 const T* __restrict__ P, const T* __restrict__ H,
-                                                                 const Chunk* __restrict__ chunks, int R, int J2,
-                                                                 int nc, double ia, double2* __restrict__ FE,
-                                                                 const double2* __restrict__ state,
-                                                                 double two_omega_lin, const double* __restrict__ cor,
-                                                                 MemberStrides ms, FourStride fx) {
+constexpr size_t anal_smem_bytes() {
+    return sizeof(C_t<T>) * ((size_t)kAnalWarpsMax * kAnalTW * 5 * 2 + (size_t)(kAnalWarpsMax - 1) * 7 * 32);
+}
+
+template <class T>
+__device__ __forceinline__ void b_anal_rhs(const Blk& bk, const C_t<T>* four_out, const T* P, const T* H,
+                                           const Chunk* chunks, int R, int J2, int nc, double ia, double2* FE,
+                                           const double2* state, double two_omega_lin, const double* cor,
+                                           MemberStrides ms, FourStride fx) {
     using C = C_t<T>;
-    constexpr int TW = 32;                    // latitudes per tile
+    constexpr int TW = kAnalTW;
     pdl_wait();
     pdl_launch();
-    four_out += blockIdx.y * ms.four_out;
-    FE += blockIdx.y * ms.fe;
-    state += blockIdx.y * ms.state;
-    __shared__ C sG[kAnalWarpsMax][TW][5][2];  // per warp: [lat][field A..E][even, odd]
-    __shared__ C red[kAnalWarpsMax - 1][7][32];
-    const Chunk ch = chunks[blockIdx.x];
+    four_out += bk.idx.y * ms.four_out;
+    FE += bk.idx.y * ms.fe;
+    state += bk.idx.y * ms.state;
+    C(*sG)[TW][5][2] = reinterpret_cast<C(*)[TW][5][2]>(bk.smem);  // [warp][lat][field][even, odd]
+    C(*red)[7][32] = reinterpret_cast<C(*)[7][32]>(bk.smem + sizeof(C) * kAnalWarpsMax * TW * 5 * 2);
+    const Chunk ch = chunks[bk.idx.x];
     const int m = ch.m;
     const int nm = R + 1 - m;
     const int off = m * (R + 1) - m * (m - 1) / 2;
     const int k0 = ch.start;
-    const int lane = threadIdx.x & 31;
-    const int wid = threadIdx.x >> 5;
-    const int nw = blockDim.x >> 5;
+    const int lane = bk.t & 31;
+    const int wid = bk.t >> 5;
+    const int nw = bk.nt >> 5;
     const int k = k0 + lane;
     const int par = k & 1;
     const int J = 2 * J2;
@@ -304,7 +321,7 @@ __global__ void __launch_bounds__(32 * kAnalWarpsMax) k_anal_rhs(const C_t<T>* _
         red[wid - 1][5][lane] = hB;
         red[wid - 1][6][lane] = hA;
     }
-    __syncthreads();
+    bk.sync();
     if (wid != 0 || !live) return;
     // The sums of the other warps, then div, curl and the kinetic-energy
     // term in the working precision T: float64 on the float64 path; float32
@@ -327,6 +344,17 @@ __global__ void __launch_bounds__(32 * kAnalWarpsMax) k_anal_rhs(const C_t<T>* _
     FE[off + k] = f0;
     FE[nc + off + k] = f1;
     FE[2 * nc + off + k] = f2;
+}
+template <class T>
+__global__ void __launch_bounds__(32 * kAnalWarpsMax) k_anal_rhs(const C_t<T>* __restrict__ four_out,
+                                                                 const T* __restrict__ P, const T* __restrict__ H,
+                                                                 const Chunk* __restrict__ chunks, int R, int J2,
+                                                                 int nc, double ia, double2* __restrict__ FE,
+                                                                 const double2* __restrict__ state,
+                                                                 double two_omega_lin, const double* __restrict__ cor,
+                                                                 MemberStrides ms, FourStride fx) {
+    __shared__ __align__(16) unsigned char sm[anal_smem_bytes<T>()];
+    b_anal_rhs<T>(hw_blk(sm), four_out, P, H, chunks, R, J2, nc, ia, FE, state, two_omega_lin, cor, ms, fx);
 }
 
 // Launch helpers shared by both precisions.

@@ -15,25 +15,13 @@
 
 #include "internal.h"
 #include "sdc_internal.h"
+#include "sdc_kernels.cuh"
 
 namespace mlsdc {
 
 
-__global__ void k_implicit_rhs(const double2* __restrict__ x, double2* __restrict__ F,
-                               const int* __restrict__ ndeg, int nc, Phys ph, size_t ms_x, size_t ms_f) {
-    pdl_wait();
-    pdl_launch();
-    x += blockIdx.y * ms_x;
-    F += blockIdx.y * ms_f;
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) {
-        const double n = ndeg[c];
-        const double L = -n * (n + 1.0) * ph.inv_a2;
-        double2 fp, fz, fd;
-        implicit_rhs_coef(L, ph, x[c], x[nc + c], x[2 * nc + c], fp, fz, fd);
-        F[c] = fp;
-        F[nc + c] = fz;
-        F[2 * nc + c] = fd;
-    }
+__global__ void k_implicit_rhs(const double2* __restrict__ x, double2* __restrict__ F, const int* __restrict__ ndeg, int nc, Phys ph, size_t ms_x, size_t ms_f) {
+    b_implicit_rhs(hw_blk(nullptr), x, F, ndeg, nc, ph, ms_x, ms_f);
 }
 
 __global__ void k_implicit_solve(const double2* __restrict__ b, double2* __restrict__ x,
@@ -70,43 +58,9 @@ __global__ void k_solve_coefs(double2* __restrict__ tab, int R, int M, QiDiag qd
 // into the new ones.  Each CTA takes kNodeCoefs coefficients with one thread
 // per (field, coefficient) for the weighted sums; the three fields of a
 // coefficient meet in shared memory for the coupled solve.
-__global__ void __launch_bounds__(3 * kNodeCoefs) k_sweep_node(double2* Th, const double2* __restrict__ FIo,
-                                                             const double2* __restrict__ FEo, double2* FIn,
-                                                             double2* FEn, const double2* __restrict__ tau,
-                                                             const int* __restrict__ ndeg,
-                                                             const double2* __restrict__ recips, int nc,
-                                                             NodeRow row, Phys ph, size_t ms) {
-    __shared__ double2 sb[3][kNodeCoefs];
-    pdl_wait();
-    pdl_launch();
-    const size_t mo = blockIdx.y * ms;
-    Th += mo;
-    FIo += mo;
-    FEo += mo;
-    FIn += mo;
-    FEn += mo;
-    if (tau) tau += mo;
-    const size_t node = (size_t)3 * nc;
-    const int m = row.m;
-    const int f = threadIdx.x / kNodeCoefs, cl = threadIdx.x - f * kNodeCoefs;
-    const int c = blockIdx.x * kNodeCoefs + cl;
-    const bool live = c < nc;
-    const size_t o = (size_t)f * nc + c;
-    if (live) sb[f][cl] = node_rhs(Th, FIo, FEo, FIn, FEn, tau, node, o, row);
-    __syncthreads();
-    if (!live) return;
-    const int nd = ndeg[c];
-    const double n = nd;
-    const double L = -n * (n + 1.0) * ph.inv_a2;
-    double2 th, fi;  // each thread only its own field (warp-uniform f)
-    node_solve_field(f, L, row.qimm, ph, recips[nd], sb[0][cl], sb[1][cl], sb[2][cl], th, fi);
-    const size_t om = (m + 1) * node + o;
-    Th[om] = th;
-    FIn[om] = fi;
-    if (m == 0) {
-        FIn[o] = FIo[o];
-        FEn[o] = FEo[o];
-    }
+__global__ void __launch_bounds__(3 * kNodeCoefs) k_sweep_node(double2* Th, const double2* __restrict__ FIo, const double2* __restrict__ FEo, double2* FIn, double2* FEn, const double2* __restrict__ tau, const int* __restrict__ ndeg, const double2* __restrict__ recips, int nc, const __grid_constant__ NodeRow row, Phys ph, size_t ms) {
+    __shared__ __align__(16) unsigned char smem_nd[kNodeSmem];
+    b_sweep_node(hw_blk(smem_nd), Th, FIo, FEo, FIn, FEn, tau, ndeg, recips, nc, row, ph, ms);
 }
 
 // The node updates of one sweep with the sweep-constant part gathered once.
@@ -122,148 +76,33 @@ __global__ void __launch_bounds__(3 * kNodeCoefs) k_sweep_node(double2* Th, cons
 // old F array once instead of once per node update), uses S_1 itself and
 // keeps S_2..S_M in the level's array S ([members][M-1][3][nc]); the m >= 1
 // launches read S_{m+1} and the new values of nodes 1..m only.
-struct SweepMats {  // dt-scaled rows 1..M of Q, Q_E, Q_I
-    double q[kMaxNodes][kMaxNodes], qe[kMaxNodes][kMaxNodes], qi[kMaxNodes][kMaxNodes];
-};
 
 template <int MM>
-__global__ void __launch_bounds__(3 * kNodeCoefs) k_sweep_node0(double2* Th, const double2* __restrict__ FIo,
-                                                              const double2* __restrict__ FEo, double2* FIn,
-                                                              double2* FEn, const double2* __restrict__ tau,
-                                                              double2* __restrict__ S, const int* __restrict__ ndeg,
-                                                              const double2* __restrict__ recips, int nc,
-                                                              SweepMats sm, Phys ph, size_t ms, size_t ms_s) {
-    __shared__ double2 sb[3][kNodeCoefs];
-    pdl_wait();
-    pdl_launch();
-    const size_t mo = blockIdx.y * ms;
-    Th += mo;
-    FIo += mo;
-    FEo += mo;
-    FIn += mo;
-    FEn += mo;
-    if (tau) tau += mo;
-    S += blockIdx.y * ms_s;
-    const size_t node = (size_t)3 * nc;
-    const int f = threadIdx.x / kNodeCoefs, cl = threadIdx.x - f * kNodeCoefs;
-    const int c = blockIdx.x * kNodeCoefs + cl;
-    const bool live = c < nc;
-    const size_t o = (size_t)f * nc + c;
-    if (live) {
-        double2 acc[MM + 1];
-        const double2 t0 = Th[o];
-#pragma unroll
-        for (int r = 1; r <= MM; ++r) acc[r] = tau ? make_double2(t0.x + tau[r * node + o].x, t0.y + tau[r * node + o].y)
-                                                   : t0;
-#pragma unroll
-        for (int j = 0; j <= MM; ++j) {
-            const double2 fi = FIo[j * node + o], fe = FEo[j * node + o];
-            const double2 s = make_double2(fi.x + fe.x, fi.y + fe.y);
-#pragma unroll
-            for (int r = 1; r <= MM; ++r) {
-                acc[r] = cax(acc[r], sm.q[r][j], s);
-                if (j >= 1 && j < r) {
-                    acc[r] = cax(acc[r], -sm.qe[r][j], fe);
-                    acc[r] = cax(acc[r], -sm.qi[r][j], fi);
-                } else if (j == r) {
-                    acc[r] = cax(acc[r], -sm.qi[r][r], fi);
-                }
-            }
-        }
-#pragma unroll
-        for (int r = 2; r <= MM; ++r) S[(r - 2) * node + o] = acc[r];
-        sb[f][cl] = acc[1];
-    }
-    __syncthreads();
-    if (!live) return;
-    const int nd = ndeg[c];
-    const double n = nd;
-    const double L = -n * (n + 1.0) * ph.inv_a2;
-    double2 th, fi;
-    node_solve_field(f, L, sm.qi[1][1], ph, recips[nd], sb[0][cl], sb[1][cl], sb[2][cl], th, fi);
-    Th[node + o] = th;
-    FIn[node + o] = fi;
-    FIn[o] = FIo[o];
-    FEn[o] = FEo[o];
+__global__ void __launch_bounds__(3 * kNodeCoefs) k_sweep_node0(double2* Th, const double2* __restrict__ FIo, const double2* __restrict__ FEo, double2* FIn, double2* FEn, const double2* __restrict__ tau, double2* __restrict__ S, const int* __restrict__ ndeg, const double2* __restrict__ recips, int nc, const __grid_constant__ SweepMats sm, Phys ph, size_t ms, size_t ms_s) {
+    __shared__ __align__(16) unsigned char smem_nd[kNodeSmem];
+    b_sweep_node0<MM>(hw_blk(smem_nd), Th, FIo, FEo, FIn, FEn, tau, S, ndeg, recips, nc, sm, ph, ms, ms_s);
 }
 
 // Node update m >= 1 of a sweep whose m = 0 launch (k_sweep_node0) left
 // S_{m+1} in S: b = S_{m+1} + sum_{j=1..m} (qE_j FEn_j + qI_j FIn_j), then
 // the solve and F_I as k_sweep_node.  `row` is dt_scaled.
-__global__ void __launch_bounds__(3 * kNodeCoefs) k_sweep_node_s(double2* Th, double2* FIn,
-                                                               const double2* __restrict__ FEn,
-                                                               const double2* __restrict__ S,
-                                                               const int* __restrict__ ndeg,
-                                                               const double2* __restrict__ recips, int nc,
-                                                               NodeRow row, Phys ph, size_t ms, size_t ms_s) {
-    __shared__ double2 sb[3][kNodeCoefs];
-    pdl_wait();
-    pdl_launch();
-    const size_t mo = blockIdx.y * ms;
-    Th += mo;
-    FIn += mo;
-    FEn += mo;
-    S += blockIdx.y * ms_s;
-    const size_t node = (size_t)3 * nc;
-    const int m = row.m;
-    const int f = threadIdx.x / kNodeCoefs, cl = threadIdx.x - f * kNodeCoefs;
-    const int c = blockIdx.x * kNodeCoefs + cl;
-    const bool live = c < nc;
-    const size_t o = (size_t)f * nc + c;
-    if (live) {
-        double2 acc = S[(m - 1) * node + o];
-        for (int j = 1; j <= m; ++j) {
-            acc = cax(acc, row.qe[j], FEn[j * node + o]);
-            acc = cax(acc, row.qi[j], FIn[j * node + o]);
-        }
-        sb[f][cl] = acc;
-    }
-    __syncthreads();
-    if (!live) return;
-    const int nd = ndeg[c];
-    const double n = nd;
-    const double L = -n * (n + 1.0) * ph.inv_a2;
-    double2 th, fi;
-    node_solve_field(f, L, row.qimm, ph, recips[nd], sb[0][cl], sb[1][cl], sb[2][cl], th, fi);
-    const size_t om = (m + 1) * node + o;
-    Th[om] = th;
-    FIn[om] = fi;
+__global__ void __launch_bounds__(3 * kNodeCoefs) k_sweep_node_s(double2* Th, double2* FIn, const double2* __restrict__ FEn, const double2* __restrict__ S, const int* __restrict__ ndeg, const double2* __restrict__ recips, int nc, const __grid_constant__ NodeRow row, Phys ph, size_t ms, size_t ms_s) {
+    __shared__ __align__(16) unsigned char smem_nd[kNodeSmem];
+    b_sweep_node_s(hw_blk(smem_nd), Th, FIn, FEn, S, ndeg, recips, nc, row, ph, ms, ms_s);
 }
 
 // dst[k] = src for k = 0..count-1 (node broadcast), src and dst [3 nc] complex
 // per member.
-__global__ void k_broadcast(const double2* __restrict__ src, double2* __restrict__ dst, int n3, int count,
-                            size_t ms_src, size_t ms_dst) {
-    pdl_wait();
-    pdl_launch();
-    src += blockIdx.y * ms_src;
-    dst += blockIdx.y * ms_dst;
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n3; c += gridDim.x * blockDim.x) {
-        const double2 v = src[c];
-        for (int k = 0; k < count; ++k) dst[(size_t)k * n3 + c] = v;
-    }
+__global__ void k_broadcast(const double2* __restrict__ src, double2* __restrict__ dst, int n3, int count, size_t ms_src, size_t ms_dst) {
+    b_broadcast(hw_blk(nullptr), src, dst, n3, count, ms_src, ms_dst);
 }
 
 
 // Restriction (Eqs. two_step_restriction, time_restriction, space_restriction):
 // Theta_c[i] = D( sum_j Pi^c_f[i][j] Theta_f[j] ) for i in [i0, i1); one
 // thread per (coarse node, field, coarse coefficient).
-__global__ void k_restrict(const double2* __restrict__ Tf, double2* __restrict__ Tc, const int* __restrict__ c2f,
-                           int ncf, int ncc, int nf_nodes, int i0, int i1, TransferMat Pcf, size_t msf, size_t msc) {
-    pdl_wait();
-    pdl_launch();
-    Tf += blockIdx.y * msf;
-    Tc += blockIdx.y * msc;
-    const int nc3 = 3 * ncc;
-    const int total = (i1 - i0) * nc3;
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
-        const int i = i0 + t / nc3, r = t % nc3;
-        const int f = r / ncc, k = r - f * ncc;
-        const size_t of = (size_t)f * ncf + c2f[k];
-        double2 acc{0.0, 0.0};
-        for (int j = 0; j < nf_nodes; ++j) acc = cax(acc, Pcf.a[i * nf_nodes + j], Tf[(size_t)j * 3 * ncf + of]);
-        Tc[(size_t)i * nc3 + r] = acc;
-    }
+__global__ void k_restrict(const double2* __restrict__ Tf, double2* __restrict__ Tc, const int* __restrict__ c2f, int ncf, int ncc, int nf_nodes, int i0, int i1, const __grid_constant__ TransferMat Pcf, size_t msf, size_t msc) {
+    b_restrict(hw_blk(nullptr), Tf, Tc, c2f, ncf, ncc, nf_nodes, i0, i1, Pcf, msf, msc);
 }
 
 
@@ -272,114 +111,61 @@ __global__ void k_restrict(const double2* __restrict__ Tf, double2* __restrict__
 // folded form of FasFwd; one thread per (coarse node i, field, coarse
 // coefficient).  The same pass saves the restricted coarse values Theta_c,
 // F_I,c, F_E,c (Algorithm 1 step B) into Ts, FIs, FEs for step D.
-__global__ void k_fas_tau(const double2* __restrict__ Tf, const double2* __restrict__ FIf,
-                          const double2* __restrict__ FEf, const double2* __restrict__ Tc,
-                          const double2* __restrict__ FIc, const double2* __restrict__ FEc,
-                          double2* __restrict__ tau, double2* __restrict__ Ts, double2* __restrict__ FIs,
-                          double2* __restrict__ FEs, const double2* __restrict__ tauf,
-                          const int* __restrict__ c2f, int ncf, int ncc, FasFwd A, size_t msf, size_t msc) {
-    pdl_wait();
-    pdl_launch();
-    const size_t of_m = blockIdx.y * msf, oc_m = blockIdx.y * msc;
-    Tf += of_m;
-    FIf += of_m;
-    FEf += of_m;
-    if (tauf) tauf += of_m;
-    Tc += oc_m;
-    FIc += oc_m;
-    FEc += oc_m;
-    tau += oc_m;
-    Ts += oc_m;
-    FIs += oc_m;
-    FEs += oc_m;
-    const int nc3 = 3 * ncc;
-    const size_t nf3 = (size_t)3 * ncf;
-    const int total = A.ncn * nc3;
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
-        const int i = t / nc3, r = t - i * nc3;
-        const int f = r / ncc, k = r - f * ncc;
-        const size_t of = (size_t)f * ncf + c2f[k];
-        const size_t oc = (size_t)i * nc3 + r;
-        const double2 tc = Tc[oc];
-        Ts[oc] = tc;
-        FIs[oc] = FIc[oc];
-        FEs[oc] = FEc[oc];
-        double2 acc = tc;
-        for (int j = 0; j < A.nfn; ++j) {
-            const size_t oj = (size_t)j * nf3 + of;
-            const double2 sf = make_double2(FIf[oj].x + FEf[oj].x, FIf[oj].y + FEf[oj].y);
-            acc = cax(acc, -A.Pcf[i * A.nfn + j], Tf[oj]);
-            acc = cax(acc, A.dPQf[i * A.nfn + j], sf);
-        }
-        for (int l = 0; l < A.ncn; ++l) {
-            const size_t ol = (size_t)l * nc3 + r;
-            const double2 sc = make_double2(FIc[ol].x + FEc[ol].x, FIc[ol].y + FEc[ol].y);
-            acc = cax(acc, -A.dQc[i * A.ncn + l], sc);
-        }
-        if (tauf)  // + R tau_f on a level below the finest (Eq. tau_term_level_l+1)
-            for (int j = 0; j < A.nfn; ++j) acc = cax(acc, A.Pcf[i * A.nfn + j], tauf[(size_t)j * nf3 + of]);
-        tau[oc] = acc;
-    }
+__global__ void k_fas_tau(const double2* __restrict__ Tf, const double2* __restrict__ FIf, const double2* __restrict__ FEf, const double2* __restrict__ Tc, const double2* __restrict__ FIc, const double2* __restrict__ FEc, double2* __restrict__ tau, double2* __restrict__ Ts, double2* __restrict__ FIs, double2* __restrict__ FEs, const double2* __restrict__ tauf, const int* __restrict__ c2f, int ncf, int ncc, const __grid_constant__ FasFwd A, size_t msf, size_t msc) {
+    b_fas_tau(hw_blk(nullptr), Tf, FIf, FEf, Tc, FIc, FEc, tau, Ts, FIs, FEs, tauf, c2f, ncf, ncc, A, msf, msc);
 }
 
 // Step D: X_f[m] += P( sum_i Pi^f_c[m][i] (X_c[i] - X_s[i]) ), m = 1..M_f,
 // for X = Theta, F_I, F_E (zero-padding leaves the fine-only modes
 // unchanged); one thread per (fine node m, field, coarse coefficient), the
 // zero weights (fine nodes that are coarse nodes) skipped.
-__global__ void k_interp(double2* __restrict__ Tf, double2* __restrict__ FIf, double2* __restrict__ FEf,
-                         const double2* __restrict__ Tc, const double2* __restrict__ FIc,
-                         const double2* __restrict__ FEc, const double2* __restrict__ Ts,
-                         const double2* __restrict__ FIs, const double2* __restrict__ FEs,
-                         const int* __restrict__ c2f, int ncf, int ncc, int nfn, int ncn, TransferMat Pfc,
-                         size_t msf, size_t msc) {
-    pdl_wait();
-    pdl_launch();
-    const size_t of_m = blockIdx.y * msf, oc_m = blockIdx.y * msc;
-    Tf += of_m;
-    FIf += of_m;
-    FEf += of_m;
-    Tc += oc_m;
-    FIc += oc_m;
-    FEc += oc_m;
-    Ts += oc_m;
-    FIs += oc_m;
-    FEs += oc_m;
-    const int nc3 = 3 * ncc;
-    const size_t nf3 = (size_t)3 * ncf;
-    const int total = (nfn - 1) * nc3;
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
-        const int m = 1 + t / nc3, r = t % nc3;
-        const int f = r / ncc, k = r - f * ncc;
-        const size_t of = (size_t)f * ncf + c2f[k];
-        double2 aT{0, 0}, aI{0, 0}, aE{0, 0};
-        for (int i = 0; i < ncn; ++i) {
-            const double w = Pfc.a[m * ncn + i];
-            if (w == 0.0) continue;
-            const size_t oc = (size_t)i * nc3 + r;
-            aT = cax(aT, w, make_double2(Tc[oc].x - Ts[oc].x, Tc[oc].y - Ts[oc].y));
-            aI = cax(aI, w, make_double2(FIc[oc].x - FIs[oc].x, FIc[oc].y - FIs[oc].y));
-            aE = cax(aE, w, make_double2(FEc[oc].x - FEs[oc].x, FEc[oc].y - FEs[oc].y));
-        }
-        const size_t o = (size_t)m * nf3 + of;
-        Tf[o] = make_double2(Tf[o].x + aT.x, Tf[o].y + aT.y);
-        FIf[o] = make_double2(FIf[o].x + aI.x, FIf[o].y + aI.y);
-        FEf[o] = make_double2(FEf[o].x + aE.x, FEf[o].y + aE.y);
-    }
+__global__ void k_interp(double2* __restrict__ Tf, double2* __restrict__ FIf, double2* __restrict__ FEf, const double2* __restrict__ Tc, const double2* __restrict__ FIc, const double2* __restrict__ FEc, const double2* __restrict__ Ts, const double2* __restrict__ FIs, const double2* __restrict__ FEs, const int* __restrict__ c2f, int ncf, int ncc, int nfn, int ncn, const __grid_constant__ TransferMat Pfc, size_t msf, size_t msc) {
+    b_interp(hw_blk(nullptr), Tf, FIf, FEf, Tc, FIc, FEc, Ts, FIs, FEs, c2f, ncf, ncc, nfn, ncn, Pfc, msf, msc);
 }
 
 // X_f += zero-pad(X_c - X_0) at one node per member (X_0 shared by every
 // member): the coarse change of a node carried to the fine level without
 // interpolation in time; one thread per (field, coarse coefficient).
-__global__ void k_pad_add(double2* __restrict__ Xf, const double2* __restrict__ Xc,
-                          const double2* __restrict__ X0, const int* __restrict__ c2f, int ncf, int ncc,
-                          size_t msf, size_t msc) {
-    Xf += blockIdx.y * msf;
-    Xc += blockIdx.y * msc;
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < 3 * ncc; t += gridDim.x * blockDim.x) {
-        const int f = t / ncc, k = t - f * ncc;
-        const size_t o = (size_t)f * ncf + c2f[k];
-        Xf[o] = make_double2(Xf[o].x + (Xc[t].x - X0[t].x), Xf[o].y + (Xc[t].y - X0[t].y));
+__global__ void k_pad_add(double2* __restrict__ Xf, const double2* __restrict__ Xc, const double2* __restrict__ X0, const int* __restrict__ c2f, int ncf, int ncc, size_t msf, size_t msc) {
+    b_pad_add(hw_blk(nullptr), Xf, Xc, X0, c2f, ncf, ncc, msf, msc);
+}
+
+__global__ void k_copy2d(unsigned char* __restrict__ dst, size_t dpitch, const unsigned char* __restrict__ src,
+                         size_t spitch, size_t width, int height) {
+    b_copy2d(hw_blk(nullptr), dst, dpitch, src, spitch, width, height);
+}
+
+// each kernel's recorded arguments are its body's (the persistent kernel
+// reads them through the body's parameter list)
+MLSDC_SAME_PACK(k_implicit_rhs, b_implicit_rhs);
+MLSDC_SAME_PACK(k_sweep_node, b_sweep_node);
+MLSDC_SAME_PACK(k_sweep_node0<2>, b_sweep_node0<2>);
+MLSDC_SAME_PACK(k_sweep_node_s, b_sweep_node_s);
+MLSDC_SAME_PACK(k_broadcast, b_broadcast);
+MLSDC_SAME_PACK(k_restrict, b_restrict);
+MLSDC_SAME_PACK(k_fas_tau, b_fas_tau);
+MLSDC_SAME_PACK(k_interp, b_interp);
+MLSDC_SAME_PACK(k_pad_add, b_pad_add);
+MLSDC_SAME_PACK(k_copy2d, b_copy2d);
+
+// A device-to-device copy of `height` rows of `width` bytes (cudaMemcpy2DAsync;
+// height 1: cudaMemcpyAsync), or under a recorder the copy body of the
+// persistent ensemble kernel (16-byte words: every array of a step is complex).
+static cudaError_t copy_rows(void* dst, size_t dpitch, const void* src, size_t spitch, size_t width, size_t height,
+                             cudaStream_t st) {
+    if (Recorder* r = active_recorder()) {
+        if (width % 16 || dpitch % 16 || spitch % 16 || (((uintptr_t)dst | (uintptr_t)src) & 15)) {
+            r->refused = true;
+            return cudaErrorNotSupported;
+        }
+        const size_t words = width / 16 * height;
+        const unsigned blocks = (unsigned)std::max<size_t>(1, std::min<size_t>((words + 255) / 256, 152 * 4));
+        record_launch(r, Body::Copy2D, 0, 0, k_copy2d, dim3(blocks), dim3(256), (unsigned char*)dst, dpitch,
+                      (const unsigned char*)src, spitch, width, (int)height);
+        return cudaSuccess;
     }
+    if (height == 1) return cudaMemcpyAsync(dst, src, width, cudaMemcpyDeviceToDevice, st);
+    return cudaMemcpy2DAsync(dst, dpitch, src, spitch, width, height, cudaMemcpyDeviceToDevice, st);
 }
 
 __global__ void k_finite(const double* __restrict__ x, int64_t n, int* __restrict__ bad) {
@@ -490,7 +276,7 @@ static mlsdc_status eval_FI(sdc_level_t L, const double2* x, double2* FI, cudaSt
     const int nc = L->plan->nc;
     const size_t ms = nodes > 0 ? L->node() : L->ms();
     if (L->options & MLSDC_CORIOLIS_IMPLICIT) return cor_fi_launch(L, x, FI, nodes > 0 ? nodes : L->members, ms, st);
-    MLSDC_LAUNCH("k_implicit_rhs", launch_k(k_implicit_rhs, dim3(grid_for(nc), nodes > 0 ? nodes : L->members),
+    MLSDC_LAUNCH("k_implicit_rhs", launch_b(Body::ImplicitRhs, 0, 0, k_implicit_rhs, dim3(grid_for(nc), nodes > 0 ? nodes : L->members),
                                             dim3(256), 0, st, x, FI, (const int*)L->plan->d_ndeg, nc,
                                             phys_of(L->prm), ms, ms));
     L->launches++;
@@ -540,7 +326,7 @@ static mlsdc_status launch_node(sdc_level_t L, double dt, const NodeRow& row, do
             switch (M) {
 #define MLSDC_NODE0(MM)                                                                                          \
     case MM:                                                                                                     \
-        e = launch_k(k_sweep_node0<MM>, grid, block, 0, st, Th, FIo, FEo, FIn, FEn, tau, L->S,                   \
+        e = launch_b((Body)((int)Body::SweepNode0_2 + MM - 2), 0, kNodeSmem, k_sweep_node0<MM>, grid, block, 0, st, Th, FIo, FEo, FIn, FEn, tau, L->S,                   \
                      (const int*)L->plan->d_ndeg, rec, nc, sm, phys_of(L->prm), L->ms(), ms_s);                  \
         break;
                 MLSDC_NODE0(2) MLSDC_NODE0(3) MLSDC_NODE0(4) MLSDC_NODE0(5) MLSDC_NODE0(6) MLSDC_NODE0(7)
@@ -549,7 +335,7 @@ static mlsdc_status launch_node(sdc_level_t L, double dt, const NodeRow& row, do
             }
             MLSDC_LAUNCH("k_sweep_node0", e);
         } else {
-            MLSDC_LAUNCH("k_sweep_node_s", launch_k(k_sweep_node_s, grid, block, 0, st, Th, FIn, (const double2*)FEn,
+            MLSDC_LAUNCH("k_sweep_node_s", launch_b(Body::SweepNodeS, 0, kNodeSmem, k_sweep_node_s, grid, block, 0, st, Th, FIn, (const double2*)FEn,
                                                     (const double2*)L->S, (const int*)L->plan->d_ndeg, rec, nc,
                                                     dt_scaled(row, dt), phys_of(L->prm), L->ms(),
                                                     (size_t)(M - 1) * L->node()));
@@ -558,7 +344,7 @@ static mlsdc_status launch_node(sdc_level_t L, double dt, const NodeRow& row, do
         return MLSDC_OK;
     }
     MLSDC_LAUNCH("k_sweep_node",
-                 launch_k(k_sweep_node, grid, block, 0, st, Th, FIo, FEo, FIn, FEn, tau, (const int*)L->plan->d_ndeg,
+                 launch_b(Body::SweepNode, 0, kNodeSmem, k_sweep_node, grid, block, 0, st, Th, FIo, FEo, FIn, FEn, tau, (const int*)L->plan->d_ndeg,
                           rec, nc, dt_scaled(row, dt), phys_of(L->prm), L->ms()));
     L->launches++;
     return MLSDC_OK;
@@ -566,7 +352,7 @@ static mlsdc_status launch_node(sdc_level_t L, double dt, const NodeRow& row, do
 
 static mlsdc_status launch_bcast(sdc_level_t L, const double2* src, double2* dst, int n3, int count, size_t ms_src,
                                  size_t ms_dst, cudaStream_t st) {
-    MLSDC_LAUNCH("k_broadcast", launch_k(k_broadcast, dim3(grid_for(n3), L->members), dim3(256), 0, st, src, dst, n3,
+    MLSDC_LAUNCH("k_broadcast", launch_b(Body::Broadcast, 0, 0, k_broadcast, dim3(grid_for(n3), L->members), dim3(256), 0, st, src, dst, n3,
                                          count, ms_src, ms_dst));
     L->launches++;
     return MLSDC_OK;
@@ -657,15 +443,6 @@ mlsdc_status implicit_rhs_launch(sh_plan_t p, const swe_params* prm, const doubl
 }  // namespace mlsdc
 
 
-struct mlsdc_ensemble_s {
-    std::vector<mlsdc_t> groups;
-    std::vector<cudaStream_t> streams;  // one per group (fork-join branches)
-    std::vector<cudaEvent_t> done;      // one per group
-    cudaEvent_t fork = nullptr;
-    cudaStream_t cap = nullptr;
-    std::map<std::tuple<std::vector<double*>, double, int, int>, cudaGraphExec_t> graphs;
-    int64_t launches = 0;
-};
 
 extern "C" mlsdc_status swe_implicit_rhs(sh_plan_t p, const swe_params* prm, const double* state, double* FI,
                                          void* stream) {
@@ -1058,8 +835,10 @@ mlsdc_status run_ops(mlsdc_t ml, const std::vector<Op>& ops, cudaStream_t st, in
     for (sdc_level_t L : lv) L->launches = 0;
     int64_t own = 0;
     mlsdc_status s = MLSDC_OK;
+    Recorder* rec = active_recorder();
     for (size_t oi = 0; oi < ops.size(); ++oi) {
         const Op& o = ops[oi];
+        if (rec) rec->begin_op((int)oi);
         // the level pair of a transfer operation (the two-level object by default)
         const mlsdc_s* P = o.pair ? o.pair : ml;
         sdc_level_t F = P->f, C = P->c;
@@ -1090,12 +869,12 @@ mlsdc_status run_ops(mlsdc_t ml, const std::vector<Op>& ops, cudaStream_t st, in
                 break;
             case OpK::Restrict:
                 MLSDC_LAUNCH("k_restrict",
-                             launch_k(k_restrict, gt((o.i1 - o.i0) * 3 * ncc), dim3(256), 0, st, o.p[0], o.p[1],
+                             launch_b(Body::Restrict, 0, 0, k_restrict, gt((o.i1 - o.i0) * 3 * ncc), dim3(256), 0, st, o.p[0], o.p[1],
                                       (const int*)P->d_c2f, ncf, ncc, nfn, o.i0, o.i1, P->Pcf, msf, msc));
                 own++;
                 break;
             case OpK::Copy:
-                MLSDC_CUDA(cudaMemcpyAsync(o.p[1], o.p[0], o.bytes, cudaMemcpyDeviceToDevice, st));
+                MLSDC_CUDA(copy_rows(o.p[1], o.bytes, o.p[0], o.bytes, o.bytes, 1, st));
                 break;
             case OpK::Fas: {
                 FasFwd fw;
@@ -1111,7 +890,7 @@ mlsdc_status run_ops(mlsdc_t ml, const std::vector<Op>& ops, cudaStream_t st, in
                     }
                     for (int l = 0; l < ncn; ++l) fw.dQc[i * ncn + l] = o.dt * C->Q[i * ncn + l];
                 }
-                MLSDC_LAUNCH("k_fas_tau", launch_k(k_fas_tau, gt(ncn * 3 * ncc), dim3(256), 0, st, o.p[0], o.p[1],
+                MLSDC_LAUNCH("k_fas_tau", launch_b(Body::FasTau, 0, 0, k_fas_tau, gt(ncn * 3 * ncc), dim3(256), 0, st, o.p[0], o.p[1],
                                                    o.p[2], o.p[3], o.p[4], o.p[5], o.p[6], o.p[7], o.p[8], o.p[9],
                                                    (const double2*)o.tauf, (const int*)P->d_c2f, ncf, ncc, fw, msf,
                                                    msc));
@@ -1120,7 +899,7 @@ mlsdc_status run_ops(mlsdc_t ml, const std::vector<Op>& ops, cudaStream_t st, in
             }
             case OpK::Interp:
                 MLSDC_LAUNCH("k_interp",
-                             launch_k(k_interp, gt((nfn - 1) * 3 * ncc), dim3(256), 0, st, o.p[0], o.p[1], o.p[2],
+                             launch_b(Body::Interp, 0, 0, k_interp, gt((nfn - 1) * 3 * ncc), dim3(256), 0, st, o.p[0], o.p[1], o.p[2],
                                       o.p[3], o.p[4], o.p[5], o.p[6], o.p[7], o.p[8], (const int*)P->d_c2f, ncf, ncc,
                                       nfn, ncn, P->Pfc, msf, msc));
                 own++;
@@ -1130,16 +909,15 @@ mlsdc_status run_ops(mlsdc_t ml, const std::vector<Op>& ops, cudaStream_t st, in
                 break;
             case OpK::CopyLast: {
                 const size_t w = o.L->node() * sizeof(double2);
-                MLSDC_CUDA(cudaMemcpy2DAsync(o.p[1], w, o.p[0], o.L->ms() * sizeof(double2), w,
-                                             (size_t)o.L->members, cudaMemcpyDeviceToDevice, st));
+                MLSDC_CUDA(copy_rows(o.p[1], w, o.p[0], o.L->ms() * sizeof(double2), w, (size_t)o.L->members, st));
                 break;
             }
             case OpK::Copy2D:
-                MLSDC_CUDA(cudaMemcpy2DAsync(o.p[1], o.ms_dst * sizeof(double2), o.p[0], o.ms_src * sizeof(double2),
-                                             o.bytes, (size_t)o.count, cudaMemcpyDeviceToDevice, st));
+                MLSDC_CUDA(copy_rows(o.p[1], o.ms_dst * sizeof(double2), o.p[0], o.ms_src * sizeof(double2), o.bytes,
+                                     (size_t)o.count, st));
                 break;
             case OpK::PadAdd:
-                MLSDC_LAUNCH("k_pad_add", launch_k(k_pad_add, dim3(grid_for(3 * ncc), o.count), dim3(256), 0, st,
+                MLSDC_LAUNCH("k_pad_add", launch_b(Body::PadAdd, 0, 0, k_pad_add, dim3(grid_for(3 * ncc), o.count), dim3(256), 0, st,
                                                    o.p[0], (const double2*)o.p[1], (const double2*)o.p[2],
                                                    (const int*)P->d_c2f, ncf, ncc, msf, msc));
                 own++;
@@ -1156,7 +934,7 @@ mlsdc_status run_ops(mlsdc_t ml, const std::vector<Op>& ops, cudaStream_t st, in
 
 // Work a step at dt needs done once, outside any graph capture: the
 // factored Coriolis chains of implicit-Coriolis levels.
-static mlsdc_status prepare_levels(mlsdc_t ml, double dt, cudaStream_t st) {
+mlsdc_status prepare_levels(mlsdc_t ml, double dt, cudaStream_t st) {
     for (sdc_level_t L : {ml->f, ml->c}) {
         mlsdc_status s = prepare_level_tables(L, dt, st);
         if (s != MLSDC_OK) return s;
@@ -1351,6 +1129,7 @@ extern "C" mlsdc_status mlsdc_ensemble_destroy(mlsdc_ensemble_t e) {
     for (auto ev : e->done) cudaEventDestroy(ev);
     if (e->fork) cudaEventDestroy(e->fork);
     if (e->cap) cudaStreamDestroy(e->cap);
+    persistent_free(e);
     delete e;
     return MLSDC_OK;
 }

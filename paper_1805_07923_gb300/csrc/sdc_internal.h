@@ -160,7 +160,25 @@ struct mlsdc_s {
     int64_t launches = 0;
 };
 
+struct mlsdc_ensemble_s {
+    std::vector<mlsdc_t> groups;
+    std::vector<cudaStream_t> streams;  // one per group (fork-join branches)
+    std::vector<cudaEvent_t> done;      // one per group
+    cudaEvent_t fork = nullptr;
+    cudaStream_t cap = nullptr;
+    std::map<std::tuple<std::vector<double*>, double, int, int>, cudaGraphExec_t> graphs;
+    int64_t launches = 0;
+    void* persist = nullptr;  // the persistent-kernel form of the step (persistent.cu)
+};
+
 namespace mlsdc {
+
+// Release the persistent-kernel state of an ensemble (persistent.cu).
+void persistent_free(mlsdc_ensemble_t e);
+
+// Work a step at dt needs done once, outside any graph capture (the
+// per-dt tables of both levels).
+mlsdc_status prepare_levels(mlsdc_t ml, double dt, cudaStream_t st);
 
 // The operations of one MLSDC step on `state` (Algorithm 1, n_iter
 // iterations of one fine and n_c coarse sweeps), starting from the levels'

@@ -128,20 +128,20 @@ mlsdc_status rhs_explicit_f64(sh_plan_t p, const swe_params* prm, const double* 
     const FourStride fo = four_out_layout(p->J, R, false);  // float64 path: m-contiguous
     if (stage == 0 || stage < 0) {
         MLSDC_LAUNCH("k_synth_rhs<double>",
-                     launch_k(k_synth_rhs<double>, dim3(p->n_synth, b.members), dim3(32 * kSynthWarps),
+                     launch_b(Body::SynthF64, 0, 0, k_synth_rhs<double>, dim3(p->n_synth, b.members), dim3(32 * kSynthWarps),
                               synth_smem<double>(R), st, (const double2*)state, (const double*)p->d_P,
                               (const double*)p->d_H, (const double*)p->d_invnn, (const Chunk*)p->d_synth, R, p->J2,
                               p->nc, -prm->a * prm->a, 1.0 / prm->a, p->d_four_in, ms));
     }
     if (stage == 1 || stage < 0) {
         MLSDC_LAUNCH("k_grid_rhs<double>",
-                     launch_k(k_grid_rhs<double, 1>, dim3(p->J, b.members), dim3(256), grid_smem<double>(p->I),
+                     launch_b(Body::GridF64x1, 0, 0, k_grid_rhs<double, 1>, dim3(p->J, b.members), dim3(256), grid_smem<double>(p->I),
                               st, (const double2*)p->d_four_in, p->d_four_out, (const double*)p->d_lat,
                               (const double2*)p->d_tw, R, p->I, p->logI, p->J, 2.0 * prm->omega, ms, fo));
     }
     if (stage == 2 || stage < 0) {
         MLSDC_LAUNCH("k_anal_rhs<double>",
-                     launch_k(k_anal_rhs<double>, dim3(p->n_anal, b.members), dim3(32 * anal_warps(p->J2)), 0, st,
+                     launch_b(Body::AnalF64, 0, anal_smem_bytes<double>(), k_anal_rhs<double>, dim3(p->n_anal, b.members), dim3(32 * anal_warps(p->J2)), 0, st,
                               (const double2*)p->d_four_out, (const double*)p->d_P, (const double*)p->d_H,
                               (const Chunk*)p->d_anal, R, p->J2, p->nc, 1.0 / prm->a, (double2*)FE,
                               (const double2*)state, 0.0, (const double*)p->d_cor, ms, fo));

@@ -34,7 +34,14 @@ mlsdc_status tc_synth(sh_plan_t p, const double* state, double a, RhsBatch b, cu
 mlsdc_status tc_anal(sh_plan_t p, double a, double* FE, const double* state, double two_omega, RhsBatch b,
                      FourStride fo, cudaStream_t st);
 
-constexpr int kStageAuto = 0, kStageTc = 1, kStageSimt = 2;
+constexpr int kStageAuto = 0, kStageTc = 1;
+
+// each kernel's recorded arguments are its body's (persistent.cu)
+MLSDC_SAME_PACK(k_synth_rhs<float>, b_synth_rhs<float>);
+MLSDC_SAME_PACK(k_synth_rhs<double>, b_synth_rhs<double>);
+MLSDC_SAME_PACK((k_grid_rhs<float, 1>), (b_grid_rhs<float, 1>));
+MLSDC_SAME_PACK(k_anal_rhs<float>, b_anal_rhs<float>);
+MLSDC_SAME_PACK(k_anal_rhs<double>, b_anal_rhs<double>);
 
 // Which kernel a Legendre stage of a tensor-core plan runs for a launch of
 // `members` states.  The rule is the outcome of timing both kernels on GB300
@@ -111,7 +118,7 @@ mlsdc_status rhs_explicit_mp(sh_plan_t p, const swe_params* prm, const double* s
             if ((s = tc_synth(p, state, prm->a, b, st)) != MLSDC_OK) return s;
         } else {
             MLSDC_LAUNCH("k_synth_rhs<float>",
-                         launch_k(k_synth_rhs<float>, dim3(p->n_synth, b.members), dim3(32 * kSynthWarps),
+                         launch_b(Body::SynthF32, 0, 0, k_synth_rhs<float>, dim3(p->n_synth, b.members), dim3(32 * kSynthWarps),
                                   synth_smem<float>(R), st, (const double2*)state, (const float*)t.P32,
                                   (const float*)t.H32, (const float*)t.invnn32, (const Chunk*)p->d_synth, R, p->J2,
                                   p->nc, -prm->a * prm->a, 1.0 / prm->a, t.four_in, ms));
@@ -120,12 +127,12 @@ mlsdc_status rhs_explicit_mp(sh_plan_t p, const swe_params* prm, const double* s
     if (stage == 1 || stage < 0) {
         if (fo.sj == 1) {  // latitude-contiguous output: two adjacent latitudes per CTA
             MLSDC_LAUNCH("k_grid_rhs<float, 2>",
-                         launch_k(k_grid_rhs<float, 2>, dim3(p->J / 2, b.members), dim3(256),
+                         launch_b(Body::GridF32x2, 0, 0, k_grid_rhs<float, 2>, dim3(p->J / 2, b.members), dim3(256),
                                   grid_smem<float>(p->I, 2), st, (const float2*)t.four_in, t.four_out,
                                   (const float*)t.lat32, (const float2*)t.tw32, R, p->I, p->logI, p->J, 0.0, ms, fo));
         } else {
             MLSDC_LAUNCH("k_grid_rhs<float, 1>",
-                         launch_k(k_grid_rhs<float, 1>, dim3(p->J, b.members), dim3(256), grid_smem<float>(p->I), st,
+                         launch_b(Body::GridF32x1, 0, 0, k_grid_rhs<float, 1>, dim3(p->J, b.members), dim3(256), grid_smem<float>(p->I), st,
                                   (const float2*)t.four_in, t.four_out, (const float*)t.lat32,
                                   (const float2*)t.tw32, R, p->I, p->logI, p->J, 0.0, ms, fo));
         }
@@ -135,7 +142,7 @@ mlsdc_status rhs_explicit_mp(sh_plan_t p, const swe_params* prm, const double* s
             if ((s = tc_anal(p, prm->a, FE, state, 2.0 * prm->omega, b, fo, st)) != MLSDC_OK) return s;
         } else {
             MLSDC_LAUNCH("k_anal_rhs<float>",
-                         launch_k(k_anal_rhs<float>, dim3(p->n_anal, b.members), dim3(32 * anal_warps(p->J2)), 0, st,
+                         launch_b(Body::AnalF32, 0, anal_smem_bytes<float>(), k_anal_rhs<float>, dim3(p->n_anal, b.members), dim3(32 * anal_warps(p->J2)), 0, st,
                                   (const float2*)t.four_out, (const float*)t.P32, (const float*)t.H32,
                                   (const Chunk*)p->d_anal, R, p->J2, p->nc, 1.0 / prm->a,
                                   (double2*)FE, (const double2*)state, 2.0 * prm->omega, (const double*)p->d_cor, ms,

@@ -55,6 +55,11 @@ _SIGS = {
     "mlsdc_ensemble_destroy": ([_VP], _I),
     "mlsdc_ensemble_step": ([_VP, ctypes.POINTER(_VP), _D, _I, _I, _I, _VP], _I),
     "mlsdc_ensemble_launch_count": ([_VP, ctypes.POINTER(_I64)], _I),
+    "mlsdc_ensemble_step_persistent": ([_VP, ctypes.POINTER(_VP), _D, _I, _I, _VP], _I),
+    "mlsdc_ensemble_persistent_info": ([_VP, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I),
+                                        ctypes.POINTER(_I)], _I),
+    "mlsdc_ensemble_device_error": ([_VP, ctypes.POINTER(_I)], _I),
+    "mlsdc_selftest_grid_barrier_timeout": ([_I, ctypes.POINTER(_I)], _I),
     "sh_plan_destroy": ([_VP], _I),
     "sh_plan_grid": ([_VP, _DP, _DP], _I),
     "sh_plan_device_bytes": ([_VP, ctypes.POINTER(_I64)], _I),
@@ -487,6 +492,37 @@ class Ensemble:
         v = ctypes.c_int64()
         _check(lib().mlsdc_ensemble_launch_count(self.h, ctypes.byref(v)), "mlsdc_ensemble_launch_count")
         return v.value
+
+    def persistent_info(self) -> dict:
+        """phases, records, ctas, in_graph of the last persistent step."""
+        v = [ctypes.c_int() for _ in range(4)]
+        _check(lib().mlsdc_ensemble_persistent_info(self.h, *[ctypes.byref(x) for x in v]),
+               "mlsdc_ensemble_persistent_info")
+        return dict(zip(("phases", "records", "ctas", "in_graph"), (x.value for x in v)))
+
+    def device_error(self) -> int:
+        c = ctypes.c_int()
+        _check(lib().mlsdc_ensemble_device_error(self.h, ctypes.byref(c)), "mlsdc_ensemble_device_error")
+        return c.value
+
+
+def mlsdc_ensemble_step_persistent(ens: Ensemble, states: list[torch.Tensor], dt: float, n_iter: int,
+                                   n_coarse_sweeps: int, stream=None):
+    """The ensemble step as one persistent kernel launch (captured in a graph)."""
+    if len(states) != len(ens.groups):
+        raise MlsdcError("one state tensor per group")
+    ptrs = [_ptr(s, 6 * g.fine.plan.nc * g.fine.members) for s, g in zip(states, ens.groups)]
+    arr = (ctypes.c_void_p * len(ptrs))(*[p.value for p in ptrs])
+    _check(lib().mlsdc_ensemble_step_persistent(ens.h, arr, float(dt), int(n_iter), int(n_coarse_sweeps),
+                                                _stream(stream)), "mlsdc_ensemble_step_persistent")
+
+
+def selftest_grid_barrier_timeout(timeout_ms: int = 20) -> int:
+    """Two CTAs at a grid barrier that never completes: returns the code they leave (3 = gave up)."""
+    c = ctypes.c_int(-1)
+    _check(lib().mlsdc_selftest_grid_barrier_timeout(int(timeout_ms), ctypes.byref(c)),
+           "mlsdc_selftest_grid_barrier_timeout")
+    return c.value
 
 
 def mlsdc_ensemble_step(ens: Ensemble, states: list[torch.Tensor], dt: float, n_iter: int, n_coarse_sweeps: int,
