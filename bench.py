@@ -559,14 +559,18 @@ def run_ensemble(args):
             "e2e": {"value": members * Ke / (e2e_ms * 1e-3), "unit": "member-steps/s", "h2d_bytes_per_step": nbytes,
                     "d2h_bytes_per_step": nbytes},
             }
-    # the same step as one persistent kernel launch per ensemble step (lockstep
-    # phases, device-side grid barrier), on the same ensemble
-    ms_p = time_steps(ens, states, K, True)
-    info = ens.persistent_info()
-    line["persistent_kernel"] = {"member_steps_per_s": members * K / (ms_p * 1e-3), "ms_per_step": ms_p / K,
-                                 "gpu_launches_per_step": ens.launch_count(), "phases": info["phases"],
-                                 "recorded_launches": info["records"], "ctas": info["ctas"],
-                                 "in_graph": bool(info["in_graph"]), "device_error": ens.device_error()}
+    # the same step as one persistent kernel launch per ensemble step, on the
+    # same ensemble, under both of its schedules
+    line["persistent_kernel"] = {}
+    for sched in ("lockstep", "dataflow"):
+        ens.set_persistent_schedule(sched)
+        ms_p = time_steps(ens, states, K, True)
+        info = ens.persistent_info()
+        line["persistent_kernel"][sched] = {
+            "member_steps_per_s": members * K / (ms_p * 1e-3), "ms_per_step": ms_p / K,
+            "gpu_launches_per_step": ens.launch_count(), "phases": info["phases"],
+            "recorded_launches": info["records"], "ctas": info["ctas"], "in_graph": bool(info["in_graph"]),
+            "device_error": ens.device_error()}
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_ensemble()
     if prec != "fp64":

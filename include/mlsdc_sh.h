@@ -392,22 +392,40 @@ mlsdc_status mlsdc_ensemble_launch_count(mlsdc_ensemble_t ens, int64_t* launches
 /* The same ensemble step as ONE persistent kernel launch (with two 4-byte
  * memsets) captured in a CUDA graph: the groups' launches of the step are
  * recorded once per (states, dt, n_iter, n_coarse_sweeps) and laid out as
- * lockstep phases (phase i = the i-th launch of every group's step; Algorithm
- * 1, Sec. 4.3.2, for all members), which one cooperative launch of one CTA
- * per SM runs with a device-side grid barrier between phases.  Every barrier
- * wait is bounded (4 s of the global timer): a wait that gives up ends the
- * launch and leaves code 3 in mlsdc_ensemble_device_error.  Results equal
+ * phases (phase i = the i-th launch of every group's step; Algorithm 1,
+ * Sec. 4.3.2, for all members), which one cooperative launch of one CTA per
+ * SM runs with device-side synchronisation between phases (the schedule:
+ * mlsdc_ensemble_persistent_schedule).  Every device wait is bounded (4 s of
+ * the global timer): a wait that gives up ends the launch and leaves code 3
+ * in mlsdc_ensemble_device_error.  Results equal
  * mlsdc_ensemble_step's bit for bit (the same device code over the same
  * blocks).  MLSDC_ERR_INVALID, with the reason in mlsdc_last_error(), for
  * implicit-Coriolis levels or a launch the kernel cannot host; a stream that
  * cannot capture the cooperative launch gets it launched directly. */
 mlsdc_status mlsdc_ensemble_step_persistent(mlsdc_ensemble_t ens, double* const* states, double dt, int n_iter,
                                             int n_coarse_sweeps, void* stream);
+/* Which schedule later persistent steps use (one graph per schedule):
+ * 0 (the default) lockstep: every CTA meets every other at a grid barrier
+ * after each phase; 1 dataflow: one ticket counter hands out the work items
+ * of all recorded launches in phase order, and an item first waits (bounded,
+ * code 3 on giving up) until the previous launch of its own group has
+ * completed, so the groups advance through their phases independently, as
+ * per-group streams do.  MLSDC_ERR_INVALID for other values. */
+mlsdc_status mlsdc_ensemble_persistent_schedule(mlsdc_ensemble_t ens, int schedule);
 /* Shape of the last persistent step: phases, recorded launches, CTAs of the
  * launch, and whether it runs from a graph.  MLSDC_ERR_INVALID before the
  * first persistent step.  Null outputs are skipped. */
 mlsdc_status mlsdc_ensemble_persistent_info(mlsdc_ensemble_t ens, int* phases, int* records, int* ctas,
                                             int* in_graph);
+/* Measurement utility: one more run of the last persistent step on `stream`
+ * (synchronous), with CTA 0 reading the global timer at every phase
+ * boundary: phase_us[p] = duration of phase p (microseconds), phase_body[p]
+ * = the body (enum Body of the library's sources) of the phase's largest
+ * recorded launch.  cap: room in both arrays (at least the phase count).
+ * The step's states advance by one step.  Lockstep schedule only
+ * (MLSDC_ERR_INVALID otherwise). */
+mlsdc_status mlsdc_ensemble_persistent_phase_times(mlsdc_ensemble_t ens, float* phase_us, int* phase_body, int cap,
+                                                   void* stream);
 /* The persistent kernel's error word (sticky): 0, or 3 when a grid-barrier
  * wait gave up (synchronous read). */
 mlsdc_status mlsdc_ensemble_device_error(mlsdc_ensemble_t ens, int* code);

@@ -57,16 +57,19 @@ constexpr int kErrBarrierTimeout = 3;              // (1 and 2 are the tensor-co
 constexpr unsigned kSlotBar0 = 2;                  // slot s: named barriers 2 + 2s and 3 + 2s
 constexpr unsigned kMaxSlots = 7;                  // (16 named barriers per CTA)
 
-// One recorded launch inside a phase.
+// One recorded launch (a task).  Tasks are stored phase by phase, and within
+// a phase the larger groups' first.
 struct PRec {
     int body;                 // Body
     unsigned nt;              // threads per virtual block
     unsigned vpc;             // virtual blocks side by side per CTA
     unsigned gx, gy, gz;      // grid
     unsigned nblk;            // gx gy gz
-    unsigned item0;           // the phase's first item of this record
+    unsigned items;           // work items: ceil(nblk / vpc)
+    unsigned item0;           // lockstep: the phase's first item of this task
+    unsigned gitem0;          // dataflow: the step's first item of this task
+    int dep;                  // dataflow: the same group's previous task (-1: none)
     unsigned smem;            // shared-memory slice per virtual block (bytes)
-    unsigned pad;
     unsigned long long args;  // byte offset of the packed arguments
 };
 struct PPhase {
@@ -74,15 +77,31 @@ struct PPhase {
     unsigned items;  // work items of the phase
     int pad;
 };
+// The two schedules of the step's tasks:
+//   lockstep: phase after phase, every CTA meeting the others at a grid
+//     barrier between phases (the groups' launches of a phase side by side);
+//   dataflow: one ticket counter hands out the work items of all tasks in
+//     their stored order; a CTA that draws an item first waits until the
+//     group's previous task has completed all its items (a per-task
+//     completion counter), runs it, and counts it complete.  The groups move
+//     through their phases independently, as the graph's per-group streams
+//     do.  An item only waits on items with smaller tickets, which CTAs that
+//     are running hold, so the schedule always progresses.
+constexpr int kLockstep = 0, kDataflow = 1;
+
 struct PArgs {
     const PPhase* phases;
     const PRec* recs;
     const unsigned char* argbuf;
-    int nphases;
-    unsigned* bar;  // arrivals so far (zeroed before each launch)
-    int* err;       // kErrBarrierTimeout when a barrier wait gave up (sticky)
-    int* abort;     // raised by a CTA that gave up (zeroed before each launch)
+    int nphases, nrecs, schedule;
+    unsigned total_items;
+    unsigned* bar;     // lockstep: arrivals so far            } zeroed before
+    int* abort;        // raised by a CTA whose wait gave up    } each launch
+    unsigned* ticket;  // dataflow: next item                   }
+    unsigned* done;    // dataflow: completed items per task    }
+    int* err;          // kErrBarrierTimeout when a wait gave up (sticky)
     uint64_t limit_ns;
+    uint64_t* stamps;  // lockstep only: null, or [nphases + 1] timer readings of CTA 0 at the phase boundaries
 };
 
 __device__ __forceinline__ uint64_t now_ns() {
@@ -104,32 +123,33 @@ __device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
     asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+// Thread 0: wait until *count reaches target (acquire), or give up (this
+// thread's limit, recorded, or another CTA's abort).
+__device__ bool wait_count(const unsigned* count, unsigned target, int* err, int* abort, uint64_t limit_ns) {
+    const uint64_t t0 = now_ns();
+    for (uint32_t i = 0;; ++i) {
+        if (ld_acquire(count) >= target) break;
+        if (ld_relaxed(abort)) return false;
+        if (((i & 15) == 15 && now_ns() - t0 > limit_ns) || i >= kBarrierSpins) {
+            atomicExch(err, kErrBarrierTimeout);
+            atomicExch(abort, 1);
+            return false;
+        }
+        __nanosleep(32);
+    }
+    __threadfence();
+    return true;
+}
+
 // Every CTA arrives; returns once `target` arrivals are counted, or false if
 // the wait gave up (this CTA's limit, or another CTA's abort).
 __device__ bool grid_barrier(unsigned* count, unsigned target, int* err, int* abort, uint64_t limit_ns) {
     __shared__ int s_ok;
     __syncthreads();  // the CTA's work of the phase is done
     if (threadIdx.x == 0) {
-        int ok = 1;
         __threadfence();
         red_release_add(count, 1);
-        const uint64_t t0 = now_ns();
-        for (uint32_t i = 0;; ++i) {
-            if (ld_acquire(count) >= target) break;
-            if (ld_relaxed(abort)) {
-                ok = 0;
-                break;
-            }
-            if (((i & 15) == 15 && now_ns() - t0 > limit_ns) || i >= kBarrierSpins) {
-                atomicExch(err, kErrBarrierTimeout);
-                atomicExch(abort, 1);
-                ok = 0;
-                break;
-            }
-            __nanosleep(32);
-        }
-        __threadfence();
-        s_ok = ok;
+        s_ok = wait_count(count, target, err, abort, limit_ns) ? 1 : 0;
     }
     __syncthreads();
     return s_ok != 0;
@@ -181,36 +201,73 @@ __device__ __forceinline__ void run_body(int body, const Blk& b, const unsigned 
     }
 }
 
+// Item `item` of task R: vpc virtual blocks side by side, then the CTA's
+// barrier (every thread of the CTA calls this).
+__device__ __forceinline__ void run_item(const PArgs& a, const PRec& R, unsigned item, unsigned char* smem_p) {
+    const unsigned slot = threadIdx.x / R.nt;
+    const unsigned vb = item * R.vpc + slot;
+    if (slot < R.vpc && vb < R.nblk) {
+        Blk b;
+        b.idx = make_uint3(vb % R.gx, (vb / R.gx) % R.gy, vb / (R.gx * R.gy));
+        b.dim = make_uint3(R.gx, R.gy, R.gz);
+        b.t = threadIdx.x - slot * R.nt;
+        b.nt = R.nt;
+        b.bar = R.nt == kPThreads ? 0u : kSlotBar0 + 2 * slot;
+        b.bar2 = kSlotBar0 + 2 * slot + 1;
+        b.smem = smem_p + (size_t)slot * R.smem;
+        b.persist = true;
+        run_body(R.body, b, a.argbuf + R.args);
+    }
+    // the next item's bodies may hand this shared memory to TMA or the
+    // tensor cores (async proxy): order this thread's accesses first
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+}
+
 __global__ void __launch_bounds__(kPThreads, 1) k_persistent(const __grid_constant__ PArgs a) {
     extern __shared__ __align__(1024) unsigned char smem_p[];
+    if (a.schedule == kDataflow) {
+        __shared__ int s_r;
+        __shared__ unsigned s_item;
+        int r_cur = 0;  // thread 0: this CTA's tickets only grow, so the task search moves forward
+        for (;;) {
+            if (threadIdx.x == 0) {
+                int r = -1;
+                unsigned item = 0;
+                const unsigned t = atomicAdd(a.ticket, 1u);
+                if (t < a.total_items && !ld_relaxed(a.abort)) {
+                    while (r_cur + 1 < a.nrecs && t >= a.recs[r_cur + 1].gitem0) ++r_cur;
+                    r = r_cur;
+                    item = t - a.recs[r].gitem0;
+                    const int dep = a.recs[r].dep;
+                    if (dep >= 0 && !wait_count(a.done + dep, a.recs[dep].items, a.err, a.abort, a.limit_ns)) r = -1;
+                }
+                s_r = r;
+                s_item = item;
+            }
+            __syncthreads();
+            const int r = s_r;
+            if (r < 0) break;
+            run_item(a, a.recs[r], s_item, smem_p);
+            if (threadIdx.x == 0) {
+                __threadfence();
+                red_release_add(a.done + r, 1);
+            }
+        }
+        return;
+    }
+    if (a.stamps && blockIdx.x == 0 && threadIdx.x == 0) a.stamps[0] = now_ns();
     for (int ph = 0; ph < a.nphases; ++ph) {
         const PPhase P = a.phases[ph];
         for (unsigned it = blockIdx.x; it < P.items; it += gridDim.x) {
             int r = P.r0;
             while (r + 1 < P.r1 && it >= a.recs[r + 1].item0) ++r;
-            const PRec R = a.recs[r];
-            const unsigned slot = threadIdx.x / R.nt;
-            const unsigned vb = (it - R.item0) * R.vpc + slot;
-            if (slot < R.vpc && vb < R.nblk) {
-                Blk b;
-                b.idx = make_uint3(vb % R.gx, (vb / R.gx) % R.gy, vb / (R.gx * R.gy));
-                b.dim = make_uint3(R.gx, R.gy, R.gz);
-                b.t = threadIdx.x - slot * R.nt;
-                b.nt = R.nt;
-                b.bar = R.nt == kPThreads ? 0u : kSlotBar0 + 2 * slot;
-                b.bar2 = kSlotBar0 + 2 * slot + 1;
-                b.smem = smem_p + (size_t)slot * R.smem;
-                b.persist = true;
-                run_body(R.body, b, a.argbuf + R.args);
-            }
-            // the next item's bodies may hand this shared memory to TMA or
-            // the tensor cores (async proxy): order this thread's accesses first
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            __syncthreads();
+            run_item(a, a.recs[r], it - a.recs[r].item0, smem_p);
         }
         if (ph + 1 < a.nphases &&
             !grid_barrier(a.bar, (unsigned)(ph + 1) * gridDim.x, a.err, a.abort, a.limit_ns))
             return;
+        if (a.stamps && blockIdx.x == 0 && threadIdx.x == 0) a.stamps[ph + 1] = now_ns();
     }
 }
 
@@ -222,20 +279,22 @@ __global__ void k_barrier_selftest(unsigned* count, int* err, int* abort, uint64
 
 // The recorded form of one ensemble step (one per states, dt, n_iter, n_c).
 struct PStep {
+    int schedule = kLockstep;
     std::vector<PPhase> phases;
     std::vector<PRec> recs;
     std::vector<unsigned char> args;
+    unsigned total_items = 0;
     PPhase* d_phases = nullptr;
     PRec* d_recs = nullptr;
     unsigned char* d_args = nullptr;
-    cudaGraphExec_t graph = nullptr;  // memsets + the kernel (null: launched directly)
+    unsigned* d_sync = nullptr;       // [0] barrier, [1] abort, [2] ticket, [3] unused, [4..) completed items per task
+    cudaGraphExec_t graph = nullptr;  // the reset and the kernel (null: launched directly)
 };
 struct PState {
-    std::map<std::tuple<std::vector<double*>, double, int, int>, PStep*> steps;
-    unsigned* d_bar = nullptr;
+    std::map<std::tuple<std::vector<double*>, double, int, int, int>, PStep*> steps;
     int* d_err = nullptr;
-    int* d_abort = nullptr;
     int ctas = 0;
+    int schedule = kLockstep;  // measured faster than the dataflow schedule on the 96-member ensemble
     PStep* last = nullptr;
 };
 
@@ -245,6 +304,7 @@ void free_step(PStep* s) {
     cudaFree(s->d_phases);
     cudaFree(s->d_recs);
     cudaFree(s->d_args);
+    cudaFree(s->d_sync);
     delete s;
 }
 
@@ -252,9 +312,7 @@ mlsdc_status pstate_of(mlsdc_ensemble_t e, PState** out) {
     if (!e->persist) {
         PState* ps = new PState();
         e->persist = ps;
-        MLSDC_CUDA(cudaMalloc((void**)&ps->d_bar, sizeof(unsigned)));
         MLSDC_CUDA(cudaMalloc((void**)&ps->d_err, sizeof(int)));
-        MLSDC_CUDA(cudaMalloc((void**)&ps->d_abort, sizeof(int)));
         MLSDC_CUDA(cudaMemset(ps->d_err, 0, sizeof(int)));
         MLSDC_CUDA(cudaFuncSetAttribute(k_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPSmem));
         int dev = 0, sms = 0, per_sm = 0;
@@ -293,10 +351,18 @@ mlsdc_status build_step(mlsdc_ensemble_t e, const std::vector<double*>& states, 
     std::map<std::pair<int, int>, std::vector<const RecLaunch*>> by_key;
     for (const auto& recs : per_group)
         for (const RecLaunch& r : recs) by_key[{r.op, r.sub}].push_back(&r);
-    for (const auto& kv : by_key) {
+    std::map<const RecLaunch*, int> group_of;
+    for (size_t g = 0; g < per_group.size(); ++g)
+        for (const RecLaunch& r : per_group[g]) group_of[&r] = (int)g;
+    std::vector<int> last_task(per_group.size(), -1);
+    for (auto& kv : by_key) {
         PPhase P{};
         P.r0 = (int)ps->recs.size();
         unsigned items = 0;
+        // the larger launches of the phase first (the dataflow schedule hands them out first)
+        std::stable_sort(kv.second.begin(), kv.second.end(), [](const RecLaunch* x, const RecLaunch* y) {
+            return (size_t)x->grid.x * x->grid.y * x->grid.z > (size_t)y->grid.x * y->grid.y * y->grid.z;
+        });
         for (const RecLaunch* r : kv.second) {
             if (r->block.y != 1 || r->block.z != 1 || r->block.x % 32 || r->block.x > (unsigned)kPThreads)
                 return invalid_arg("persistent ensemble step: a launch's block shape does not fit the kernel");
@@ -313,8 +379,14 @@ mlsdc_status build_step(mlsdc_ensemble_t e, const std::vector<double*>& states, 
             R.gy = r->grid.y;
             R.gz = r->grid.z;
             R.nblk = R.gx * R.gy * R.gz;
+            R.items = (R.nblk + vpc - 1) / vpc;
             R.item0 = items;
-            items += (R.nblk + vpc - 1) / vpc;
+            items += R.items;
+            R.gitem0 = ps->total_items;
+            ps->total_items += R.items;
+            const int g = group_of[r];
+            R.dep = last_task[g];
+            last_task[g] = (int)ps->recs.size();
             size_t off = (ps->args.size() + 127) / 128 * 128;
             ps->args.resize(off + r->args.size());
             std::memcpy(ps->args.data() + off, r->args.data(), r->args.size());
@@ -332,22 +404,28 @@ mlsdc_status build_step(mlsdc_ensemble_t e, const std::vector<double*>& states, 
                           cudaMemcpyHostToDevice));
     MLSDC_CUDA(cudaMemcpy(ps->d_recs, ps->recs.data(), ps->recs.size() * sizeof(PRec), cudaMemcpyHostToDevice));
     MLSDC_CUDA(cudaMemcpy(ps->d_args, ps->args.data(), ps->args.size(), cudaMemcpyHostToDevice));
+    MLSDC_CUDA(cudaMalloc((void**)&ps->d_sync, (4 + ps->recs.size()) * sizeof(unsigned)));
     return MLSDC_OK;
 }
 
 // The two resets and the cooperative launch of one step.
-mlsdc_status enqueue_step(const PState* st, const PStep* ps, cudaStream_t s) {
-    MLSDC_CUDA(cudaMemsetAsync(st->d_bar, 0, sizeof(unsigned), s));
-    MLSDC_CUDA(cudaMemsetAsync(st->d_abort, 0, sizeof(int), s));
+mlsdc_status enqueue_step(const PState* st, const PStep* ps, cudaStream_t s, uint64_t* stamps = nullptr) {
+    MLSDC_CUDA(cudaMemsetAsync(ps->d_sync, 0, (4 + ps->recs.size()) * sizeof(unsigned), s));
     PArgs a;
     a.phases = ps->d_phases;
     a.recs = ps->d_recs;
     a.argbuf = ps->d_args;
     a.nphases = (int)ps->phases.size();
-    a.bar = st->d_bar;
+    a.nrecs = (int)ps->recs.size();
+    a.schedule = ps->schedule;
+    a.total_items = ps->total_items;
+    a.bar = ps->d_sync;
+    a.abort = reinterpret_cast<int*>(ps->d_sync + 1);
+    a.ticket = ps->d_sync + 2;
+    a.done = ps->d_sync + 4;
     a.err = st->d_err;
-    a.abort = st->d_abort;
     a.limit_ns = kBarrierNs;
+    a.stamps = stamps;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(st->ctas);
     cfg.blockDim = dim3(kPThreads);
@@ -368,9 +446,7 @@ void persistent_free(mlsdc_ensemble_t e) {
     PState* st = reinterpret_cast<PState*>(e->persist);
     if (!st) return;
     for (auto& kv : st->steps) free_step(kv.second);
-    cudaFree(st->d_bar);
     cudaFree(st->d_err);
-    cudaFree(st->d_abort);
     delete st;
     e->persist = nullptr;
 }
@@ -395,10 +471,11 @@ extern "C" mlsdc_status mlsdc_ensemble_step_persistent(mlsdc_ensemble_t e, doubl
     PState* ps = nullptr;
     mlsdc_status s = pstate_of(e, &ps);
     if (s != MLSDC_OK) return s;
-    auto key = std::make_tuple(sv, dt, n_iter, n_coarse_sweeps);
+    auto key = std::make_tuple(sv, dt, n_iter, n_coarse_sweeps, ps->schedule);
     auto it = ps->steps.find(key);
     if (it == ps->steps.end()) {
         PStep* step = new PStep();
+        step->schedule = ps->schedule;
         s = build_step(e, sv, dt, n_iter, n_coarse_sweeps, step);
         if (s != MLSDC_OK) {
             free_step(step);
@@ -430,6 +507,15 @@ extern "C" mlsdc_status mlsdc_ensemble_step_persistent(mlsdc_ensemble_t e, doubl
         return MLSDC_OK;
     }
     return enqueue_step(ps, it->second, st);
+}
+
+extern "C" mlsdc_status mlsdc_ensemble_persistent_schedule(mlsdc_ensemble_t e, int schedule) {
+    if (!e || (schedule != kLockstep && schedule != kDataflow)) return MLSDC_ERR_INVALID;
+    PState* ps = nullptr;
+    mlsdc_status s = pstate_of(e, &ps);
+    if (s != MLSDC_OK) return s;
+    ps->schedule = schedule;
+    return MLSDC_OK;
 }
 
 extern "C" mlsdc_status mlsdc_ensemble_persistent_info(mlsdc_ensemble_t e, int* phases, int* records, int* ctas,
@@ -468,6 +554,41 @@ extern "C" mlsdc_status mlsdc_selftest_grid_barrier_timeout(int timeout_ms, int*
     if (err != cudaSuccess) {
         set_error("k_barrier_selftest", err);
         return MLSDC_ERR_CUDA;
+    }
+    return MLSDC_OK;
+}
+
+extern "C" mlsdc_status mlsdc_ensemble_persistent_phase_times(mlsdc_ensemble_t e, float* phase_us, int* phase_body,
+                                                              int cap, void* stream) {
+    if (!e || !e->persist || !phase_us || !phase_body || cap < 1) return MLSDC_ERR_INVALID;
+    const PState* ps = reinterpret_cast<const PState*>(e->persist);
+    const PStep* step = ps->last;
+    if (!step) return MLSDC_ERR_INVALID;
+    if (step->schedule != kLockstep)
+        return invalid_arg("mlsdc_ensemble_persistent_phase_times: phases are timed under the lockstep schedule");
+    const int np = (int)step->phases.size();
+    if (cap < np) return invalid_arg("mlsdc_ensemble_persistent_phase_times: room for fewer phases than the step has");
+    cudaStream_t st = (cudaStream_t)stream;
+    uint64_t* d = nullptr;
+    MLSDC_CUDA(cudaMalloc((void**)&d, (size_t)(np + 1) * sizeof(uint64_t)));
+    std::vector<uint64_t> h(np + 1, 0);
+    mlsdc_status s = enqueue_step(ps, step, st, d);
+    cudaError_t err = s == MLSDC_OK ? cudaStreamSynchronize(st) : cudaSuccess;
+    if (s == MLSDC_OK && err == cudaSuccess)
+        err = cudaMemcpy(h.data(), d, h.size() * sizeof(uint64_t), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (s != MLSDC_OK) return s;
+    if (err != cudaSuccess) {
+        set_error("mlsdc_ensemble_persistent_phase_times", err);
+        return MLSDC_ERR_CUDA;
+    }
+    for (int p = 0; p < np; ++p) {
+        phase_us[p] = (float)((double)(h[p + 1] - h[p]) * 1e-3);
+        // the body of the phase's record with the most blocks
+        int best = step->phases[p].r0;
+        for (int r = step->phases[p].r0; r < step->phases[p].r1; ++r)
+            if (step->recs[r].nblk > step->recs[best].nblk) best = r;
+        phase_body[p] = step->recs[best].body;
     }
     return MLSDC_OK;
 }

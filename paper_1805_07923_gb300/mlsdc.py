@@ -59,6 +59,9 @@ _SIGS = {
     "mlsdc_ensemble_persistent_info": ([_VP, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I),
                                         ctypes.POINTER(_I)], _I),
     "mlsdc_ensemble_device_error": ([_VP, ctypes.POINTER(_I)], _I),
+    "mlsdc_ensemble_persistent_schedule": ([_VP, _I], _I),
+    "mlsdc_ensemble_persistent_phase_times": ([_VP, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(_I), _I, _VP],
+                                              _I),
     "mlsdc_selftest_grid_barrier_timeout": ([_I, ctypes.POINTER(_I)], _I),
     "sh_plan_destroy": ([_VP], _I),
     "sh_plan_grid": ([_VP, _DP, _DP], _I),
@@ -500,10 +503,30 @@ class Ensemble:
                "mlsdc_ensemble_persistent_info")
         return dict(zip(("phases", "records", "ctas", "in_graph"), (x.value for x in v)))
 
+    def set_persistent_schedule(self, schedule: str):
+        """'lockstep' (default) or 'dataflow' for later persistent steps."""
+        code = {"lockstep": 0, "dataflow": 1}[schedule]
+        _check(lib().mlsdc_ensemble_persistent_schedule(self.h, code), "mlsdc_ensemble_persistent_schedule")
+
     def device_error(self) -> int:
         c = ctypes.c_int()
         _check(lib().mlsdc_ensemble_device_error(self.h, ctypes.byref(c)), "mlsdc_ensemble_device_error")
         return c.value
+
+    # the persistent kernel's bodies, in the library's Body order (vblock.cuh)
+    BODIES = ["SynthF32", "SynthF64", "GridF32x1", "GridF32x2", "GridF64x1", "AnalF32", "AnalF64", "TcSynthTf32",
+              "TcSynthBf16", "TcAnalTf32", "TcAnalBf16", "TcAnalWsTf32", "TcAnalWsBf16", "ImplicitRhs", "SweepNode",
+              "SweepNode0_2", "SweepNode0_3", "SweepNode0_4", "SweepNode0_5", "SweepNode0_6", "SweepNode0_7",
+              "SweepNode0_8", "SweepNodeS", "Broadcast", "Restrict", "FasTau", "Interp", "PadAdd", "Copy2D"]
+
+    def persistent_phase_times(self, stream=None) -> list[tuple[str, float]]:
+        """One more persistent step with per-phase timer readings: (body, microseconds) per phase."""
+        n = self.persistent_info()["phases"]
+        us = (ctypes.c_float * n)()
+        body = (ctypes.c_int * n)()
+        _check(lib().mlsdc_ensemble_persistent_phase_times(self.h, us, body, n, _stream(stream)),
+               "mlsdc_ensemble_persistent_phase_times")
+        return [(self.BODIES[body[i]], float(us[i])) for i in range(n)]
 
 
 def mlsdc_ensemble_step_persistent(ens: Ensemble, states: list[torch.Tensor], dt: float, n_iter: int,

@@ -97,3 +97,26 @@ def test_planned_entry_points_refuse_misaligned_pointers(lib_path):
     lib.sh_forward.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
     assert lib.sh_forward(fake_plan, good, odd, 1, None) == -1
     assert b"sh_forward: spec is not 16-byte aligned" in lib.mlsdc_last_error()
+
+
+def test_persistent_body_names_follow_the_body_enum():
+    """The binding's names of the persistent kernel's bodies (phase timing)
+    are the Body enumerators of the library, in order."""
+    import re
+    from paper_1805_07923_gb300 import mlsdc as M
+    src = open(os.path.join(ROOT, "paper_1805_07923_gb300", "csrc", "vblock.cuh")).read()
+    body = re.search(r"enum class Body : int \{(.*?)\};", src, re.S).group(1)
+    names = [n.strip() for n in body.split(",") if n.strip() and n.strip() != "Count"]
+    assert names == M.Ensemble.BODIES
+
+
+def test_persistent_entry_points_refuse_bad_arguments(lib_path):
+    lib = ctypes.CDLL(lib_path)
+    lib.mlsdc_ensemble_persistent_schedule.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    assert lib.mlsdc_ensemble_persistent_schedule(None, 0) == -1
+    lib.mlsdc_ensemble_persistent_info.argtypes = [ctypes.c_void_p] + [ctypes.c_void_p] * 4
+    assert lib.mlsdc_ensemble_persistent_info(None, None, None, None, None) == -1
+    lib.mlsdc_selftest_grid_barrier_timeout.argtypes = [ctypes.c_int, ctypes.c_void_p]
+    code = ctypes.c_int()
+    assert lib.mlsdc_selftest_grid_barrier_timeout(0, ctypes.byref(code)) == -1
+    assert lib.mlsdc_selftest_grid_barrier_timeout(5000, ctypes.byref(code)) == -1

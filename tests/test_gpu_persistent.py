@@ -40,13 +40,15 @@ def ensemble_states(specs, base_R=170):
     return out
 
 
-def run(specs, prec, steps, persistent, dt=150.0):
+def run(specs, prec, steps, persistent, dt=150.0, schedule="lockstep"):
     groups, keep = [], []
     for spec in specs:
         ml, k = group(spec, prec)
         groups.append(ml)
         keep.append(k)
     ens = M.Ensemble(groups)
+    if persistent:
+        ens.set_persistent_schedule(schedule)
     states = [torch.from_numpy(x).cuda() for x in ensemble_states(specs)]
     for _ in range(steps):
         if persistent:
@@ -89,9 +91,10 @@ def field_diffs(specs, a, b):
     return np.array(out)
 
 
-def test_persistent_fp64_equals_graph():
+@pytest.mark.parametrize("schedule", ["dataflow", "lockstep"])
+def test_persistent_fp64_equals_graph(schedule):
     a, _, _, _ = run(SMALL, "fp64", 3, False)
-    b, info, err, launches = run(SMALL, "fp64", 3, True)
+    b, info, err, launches = run(SMALL, "fp64", 3, True, schedule=schedule)
     assert err == 0
     assert launches == 1
     assert info["phases"] > 100 and info["ctas"] >= 1
@@ -119,9 +122,10 @@ def test_persistent_one_member_matches_oracle():
 MIXED = [(42, 128, 64, 21, 64, 32, 4), (85, 256, 128, 42, 128, 64, 4), (170, 512, 256, 85, 256, 128, 16)]
 
 
-def test_persistent_bf16x3_equals_graph():
+@pytest.mark.parametrize("schedule", ["dataflow", "lockstep"])
+def test_persistent_bf16x3_equals_graph(schedule):
     a, _, _, _ = run(MIXED, "bf16x3", 2, False)
-    b, info, err, _ = run(MIXED, "bf16x3", 2, True)
+    b, info, err, _ = run(MIXED, "bf16x3", 2, True, schedule=schedule)
     assert err == 0
     for y in b:
         assert np.all(np.isfinite(y))
@@ -136,3 +140,15 @@ def test_implicit_coriolis_group_is_refused():
     states = [torch.from_numpy(ensemble_states([(21, 64, 32, 10, 32, 16, 2)])[0]).cuda()]
     with pytest.raises(M.MlsdcError):
         M.mlsdc_ensemble_step_persistent(ens, states, 150.0, 4, 2)
+
+
+def test_lockstep_phase_times_cover_every_phase():
+    spec = (42, 128, 64, 21, 64, 32, 2)
+    ml, keep = group(spec, "fp64")
+    ens = M.Ensemble([ml])
+    states = [torch.from_numpy(ensemble_states([spec])[0]).cuda()]
+    M.mlsdc_ensemble_step_persistent(ens, states, 150.0, 4, 2)
+    times = ens.persistent_phase_times()
+    assert len(times) == ens.persistent_info()["phases"]
+    assert all(us > 0 for _, us in times)
+    assert {b for b, _ in times} >= {"SynthF64", "GridF64x1", "AnalF64", "SweepNode0_4", "SweepNodeS"}
