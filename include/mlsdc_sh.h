@@ -118,6 +118,14 @@ mlsdc_status sh_plan_device_error(sh_plan_t plan, int* code);
  * recorded value (0 would mean the barrier completed).  Synchronises the
  * device.  MLSDC_ERR_INVALID for a null pointer or a limit out of range. */
 mlsdc_status mlsdc_selftest_wait_timeout(int timeout_ms, int* code);
+/* How the float32 CUDA-core synthesis (MLSDC_FP32, and the synthesis of
+ * tensor-core plans where it runs on CUDA cores) reads its Legendre tables:
+ * 0 = by size (TMA into shared memory for up to two 32-row boxes per work
+ * item, R <= 63, or three boxes with at most 4 members; plain loads
+ * otherwise), 1 = TMA whenever the plan allows it (nlat/2 a multiple of 4),
+ * 2 = plain loads.  Results are identical either way (the same sums in the
+ * same order).  MLSDC_ERR_INVALID for float64 plans or other modes. */
+mlsdc_status sh_plan_set_synth_tma(sh_plan_t plan, int mode);
 /* Which kernel each Legendre stage of a tensor-core plan (MLSDC_TF32 /
  * MLSDC_BF16X3) runs: the tcgen05 kernel or the float32 CUDA-core kernel of
  * MLSDC_FP32.  By default the choice follows a fixed rule per launch (measured

@@ -1,6 +1,7 @@
 // Internal declarations of the MLSDC-SH library (not part of the ABI).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -180,6 +181,19 @@ struct Chunk {
     int start;
 };
 
+// 2-D tensor maps over the float32 synthesis tables P32 and H32 ([nc][J2]
+// floats, boxes of min(32, J2) latitudes x 32 rows, no swizzle): the float32
+// synthesis can stream each work item's table rows into shared memory by TMA.
+struct SynMaps {
+    CUtensorMap P, H;
+};
+constexpr int kSynBoxRows = 32;
+
+// Encode a 2-D float32 tensor map over a row-major [rows][cols] array with a
+// box of box_cols x box_rows and no swizzle (false if the driver refuses).
+bool make_rows_map_f32(CUtensorMap* map, const void* base, uint64_t cols, uint64_t rows, uint32_t box_cols,
+                       uint32_t box_rows);
+
 // Mixed-precision tables and scratch of a plan (float32 path).
 struct MPTables {
     float* P32 = nullptr;        // [nc][J2] float32 copy of P
@@ -189,6 +203,10 @@ struct MPTables {
     float2* four_out = nullptr;  // [5][R+1][J] (latitude-contiguous)
     float* lat32 = nullptr;      // [J][4] float32 copy of the plan's d_lat
     float* invnn32 = nullptr;    // [R+1] float32 copy of d_invnn
+    SynMaps syn_maps;            // TMA maps of P32 / H32 for the float32 synthesis
+    bool syn_tma = false;        // false: the synthesis reads the tables with plain loads (J2 % 4 != 0)
+    int syn_tma_mode = 0;        // 0: by size (synth_uses_tma), 1: TMA whenever syn_tma, 2: plain loads
+    int* d_err = nullptr;        // error word of the float32 synthesis's bounded TMA waits
     // tensor-core state (legendre_tc.cu): operand tables, tensor maps, error flag
     void* tc = nullptr;
     int64_t tc_bytes = 0;

@@ -9,6 +9,7 @@
 #include <cuda.h>
 #include <cuda_bf16.h>
 
+#include "async_copy.cuh"
 #include "complex.cuh"
 #include "internal.h"
 #include "rhs_kernels.cuh"  // coriolis_linear, FourStride
@@ -20,12 +21,7 @@ constexpr int kTcThreads = 128;
 constexpr int kTileRows = 128;   // MMA M
 constexpr int kMaxKS = 192;      // synthesis K limit (R + 1 <= 192)
 constexpr int kTileBytes = 16384;  // 128 rows x 128 B
-// Every mbarrier wait is bounded in time (the waits of these kernels complete
-// in microseconds): after kWaitNs of the global timer the wait gives up, with
-// an iteration cap as a second bound.
-constexpr uint64_t kWaitNs = 2000000000ull;
-constexpr uint32_t kSpinLimit = 1u << 30;
-constexpr int kErrTmaTimeout = 1, kErrMmaTimeout = 2;
+
 
 enum { MODE_TF32 = 0, MODE_BF16X3 = 1 };
 
@@ -34,47 +30,6 @@ struct Maps {
 };
 
 // ---------------------------------------------------------------- PTX helpers
-__device__ __forceinline__ uint32_t sa(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-__device__ __forceinline__ uint64_t global_ns() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint64_t limit_ns = kWaitNs) {
-    if (mbar_try_wait(bar, parity)) return true;
-    const uint64_t t0 = global_ns();
-    for (uint32_t i = 1; i < kSpinLimit; ++i) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if ((i & 255) == 0 && global_ns() - t0 > limit_ns) return false;
-    }
-    return false;
-}
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-            dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
-        : "memory");
-}
-__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -360,9 +315,6 @@ __device__ __forceinline__ uint32_t idesc_for(int N) {
     return base | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(kTileRows >> 4) << 24);
 }
 
-__device__ __forceinline__ void mbar_inval(uint32_t bar) {
-    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
-}
 // Free the block's tensor memory.  In the persistent kernel the block's
 // shared memory then serves other bodies: its mbarriers (the four pipeline
 // barriers, and with ws_bars the warp-specialised kernel's four accumulator

@@ -167,8 +167,9 @@ __device__ bool grid_barrier(unsigned* count, unsigned target, int* err, int* ab
 
 __device__ __forceinline__ void run_body(int body, const Blk& b, const unsigned char* a) {
     switch ((Body)body) {
-        MLSDC_BODY_CASE(SynthF32, (b_synth_rhs<float>))
-        MLSDC_BODY_CASE(SynthF64, (b_synth_rhs<double>))
+        MLSDC_BODY_CASE(SynthF32, (b_synth_rhs<float, false>))
+        MLSDC_BODY_CASE(SynthF32Tma, (b_synth_rhs<float, true>))
+        MLSDC_BODY_CASE(SynthF64, (b_synth_rhs<double, false>))
         MLSDC_BODY_CASE(GridF32x1, (b_grid_rhs<float, 1>))
         MLSDC_BODY_CASE(GridF32x2, (b_grid_rhs<float, 2>))
         MLSDC_BODY_CASE(GridF64x1, (b_grid_rhs<double, 1>))

@@ -351,12 +351,17 @@ extern "C" mlsdc_status sh_plan_device_bytes(sh_plan_t p, int64_t* bytes) {
 
 namespace mlsdc {
 mlsdc_status tc_error(sh_plan_t p, int* code);
+mlsdc_status mp_error(sh_plan_t p, int* code);
 }
 
 extern "C" mlsdc_status sh_plan_device_error(sh_plan_t p, int* code) {
     if (!p || !code) return MLSDC_ERR_INVALID;
     *code = 0;
-    if (p->precision != MLSDC_TF32 && p->precision != MLSDC_BF16X3) return MLSDC_OK;
+    if (p->precision == MLSDC_FP64) return MLSDC_OK;
     MLSDC_CUDA(cudaDeviceSynchronize());
-    return mlsdc::tc_error(p, code);
+    int c_mp = 0, c_tc = 0;
+    mlsdc_status s = mlsdc::mp_error(p, &c_mp);
+    if (s == MLSDC_OK && (p->precision == MLSDC_TF32 || p->precision == MLSDC_BF16X3)) s = mlsdc::tc_error(p, &c_tc);
+    *code = c_tc ? c_tc : c_mp;
+    return s;
 }

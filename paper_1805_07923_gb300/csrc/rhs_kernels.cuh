@@ -25,6 +25,9 @@
 // only when a launch carries several members (measured on GB300: from three).
 #pragma once
 
+#include <type_traits>
+
+#include "async_copy.cuh"
 #include "complex.cuh"
 #include "internal.h"
 
@@ -51,22 +54,66 @@ struct MemberStrides {
     size_t state, four_in, four_out, fe;
 };
 
+template <class T>
+inline size_t synth_smem(int R) {
+    const size_t coef = sizeof(C_t<T>) * 4 * (R + 1);
+    const size_t red = sizeof(C_t<T>) * kSynthWarps * 6 * 32;
+    return coef > red ? coef : red;
+}
+// The float32 synthesis with its tables streamed by TMA: the coefficient /
+// reduction area, 128 bytes of alignment slack, the P and H rows of one work
+// item (up to R + 1 rows of 32 latitudes each, in boxes of kSynBoxRows rows),
+// and one mbarrier per box.
+__host__ __device__ inline int synth_boxes(int R) { return (R + 1 + kSynBoxRows - 1) / kSynBoxRows; }
+__host__ __device__ inline size_t synth_coef_bytes(int R) {
+    const size_t coef = sizeof(float2) * 4 * (size_t)(R + 1), red = sizeof(float2) * kSynthWarps * 6 * 32;
+    return ((coef > red ? coef : red) + 127) / 128 * 128;
+}
+inline size_t synth_tma_smem(int R) {
+    return synth_coef_bytes(R) + 128 + (size_t)2 * synth_boxes(R) * kSynBoxRows * 32 * sizeof(float) +
+           8 * (size_t)synth_boxes(R);
+}
+
 // U^m = (1/a) sum_n [ i m chi P - psi H ],  V^m = (1/a) sum_n [ i m psi P + chi H ]
 // with psi, chi = -a^2/(n(n+1)) (zeta, delta) (Helmholtz, Sec. 2).
-template <class T>
-__device__ __forceinline__ void b_synth_rhs(const Blk& bk, const double2* state, const T* P, const T* H,
-                                            const T* invnn, const Chunk* chunks, int R, int J2, int nc, double na2,
-                                            double ia, C_t<T>* four, MemberStrides ms) {
+// With TMA (float32 only) the work item's table rows come into
+// shared memory by TMA (maps: boxes of min(32, J2) latitudes x kSynBoxRows
+// rows, one mbarrier per box of P and H rows), all issued before the
+// coefficients are read; the warps wait for each box as their degrees reach
+// it (bounded; a wait that gives up records kErrTmaTimeout in *err).
+// Otherwise every thread reads its latitude's table entries from global
+// memory.  Both forms form the same sums in the same order.
+template <class T, bool TMA>
+__device__ __forceinline__ void b_synth_rhs(const Blk& bk, const SynMaps& maps, int* err, const double2* state,
+                                            const T* P, const T* H, const T* invnn, const Chunk* chunks, int R,
+                                            int J2, int nc, double na2, double ia, C_t<T>* four, MemberStrides ms) {
     using C = C_t<T>;
     C* sc = reinterpret_cast<C*>(bk.smem);  // [nm][4]: zeta, Phi', chi, psi; reused for the reduction
-    pdl_wait();
-    pdl_launch();
-    state += bk.idx.y * ms.state;
-    four += bk.idx.y * ms.four_in;
     const Chunk ch = chunks[bk.idx.x];
     const int m = ch.m;
     const int nm = R + 1 - m;
     const int off = m * (R + 1) - m * (m - 1) / 2;
+    constexpr bool tma = TMA && std::is_same<T, float>::value;
+    const int bw = J2 < 32 ? J2 : 32;  // latitudes per table row in shared memory
+    const int nbox = (nm + kSynBoxRows - 1) / kSynBoxRows;
+    float* tP = reinterpret_cast<float*>(((uintptr_t)(bk.smem + synth_coef_bytes(R)) + 127) & ~(uintptr_t)127);
+    float* tH = tP + (size_t)synth_boxes(R) * kSynBoxRows * 32;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(tH + (size_t)synth_boxes(R) * kSynBoxRows * 32);
+    if (tma && bk.t == 0) {  // the tables are constant: their loads may start before the previous kernel ends
+        for (int i = 0; i < nbox; ++i) mbar_init(sa(&bars[i]), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        for (int i = 0; i < nbox; ++i) {
+            mbar_expect_tx(sa(&bars[i]), (uint32_t)(2 * kSynBoxRows * bw * sizeof(float)));
+            tma_load_2d(sa(tP + (size_t)i * kSynBoxRows * bw), &maps.P, ch.start, off + i * kSynBoxRows,
+                        sa(&bars[i]));
+            tma_load_2d(sa(tH + (size_t)i * kSynBoxRows * bw), &maps.H, ch.start, off + i * kSynBoxRows,
+                        sa(&bars[i]));
+        }
+    }
+    pdl_wait();
+    pdl_launch();
+    state += bk.idx.y * ms.state;
+    four += bk.idx.y * ms.four_in;
     for (int k = bk.t; k < nm; k += bk.nt) {
         // psi, chi = -a^2/(n(n+1)) (zeta, delta), the factor from the plan's table
         const T s = T(na2) * invnn[m + k];
@@ -86,7 +133,30 @@ __device__ __forceinline__ void b_synth_rhs(const Blk& bk, const double2* state,
     const C zero = mkc(T(0), T(0));
     // this warp sums k = wid, wid + 4, ...: one parity (wid & 1) only
     C az = zero, ap = zero, axP = zero, asP = zero, asH = zero, axH = zero;
-    if (live) {
+    if (tma) {
+        const float* Pm = tP + lane;
+        const float* Hm = tH + lane;
+        for (int i = 0; i < nbox; ++i) {
+            if (!mbar_wait(sa(&bars[i]), 0)) {
+                atomicExch(err, kErrTmaTimeout);
+                break;
+            }
+            if (!live) continue;
+            const int k1 = min(nm, (i + 1) * kSynBoxRows);
+            // this warp's degrees in the box: k = wid mod kSynthWarps
+#pragma unroll 8
+            for (int k = i * kSynBoxRows + wid; k < k1; k += kSynthWarps) {
+                const T p = Pm[k * bw], h = Hm[k * bw];
+                const C z = sc[4 * k], f = sc[4 * k + 1], x = sc[4 * k + 2], s = sc[4 * k + 3];
+                cfma(az, p, z);
+                cfma(ap, p, f);
+                cfma(axP, p, x);
+                cfma(asP, p, s);
+                cfma(asH, h, s);
+                cfma(axH, h, x);
+            }
+        }
+    } else if (live) {
         const T* Pm = P + (size_t)off * J2 + j;
         const T* Hm = H + (size_t)off * J2 + j;
 #pragma unroll 8
@@ -102,6 +172,9 @@ __device__ __forceinline__ void b_synth_rhs(const Blk& bk, const double2* state,
         }
     }
     bk.sync();  // coefficient table no longer needed: reuse it for the partial sums
+    // (every thread's waits are over: a block of the persistent kernel retires the barriers)
+    if (tma && bk.persist && bk.t == 0)
+        for (int i = 0; i < nbox; ++i) mbar_inval(sa(&bars[i]));
     C* red = sc;      // [kSynthWarps][6][32]
     red[(wid * 6 + 0) * 32 + lane] = az;
     red[(wid * 6 + 1) * 32 + lane] = ap;
@@ -138,15 +211,17 @@ __device__ __forceinline__ void b_synth_rhs(const Blk& bk, const double2* state,
     four[3 * fs + iN] = cscale(cadd(cim(dm, sPN), xHN), iaT);
     four[3 * fs + iS] = cscale(cadd(cim(dm, sPS), xHS), iaT);
 }
-template <class T>
-__global__ void __launch_bounds__(32 * kSynthWarps) k_synth_rhs(const double2* __restrict__ state,
+template <class T, bool TMA>
+__global__ void __launch_bounds__(32 * kSynthWarps) k_synth_rhs(const __grid_constant__ SynMaps maps,
+                                                                int* __restrict__ err,
+                                                                const double2* __restrict__ state,
                                                                 const T* __restrict__ P, const T* __restrict__ H,
                                                                 const T* __restrict__ invnn,
                                                                 const Chunk* __restrict__ chunks, int R, int J2,
                                                                 int nc, double na2, double ia, C_t<T>* __restrict__ four,
                                                                 MemberStrides ms) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    b_synth_rhs<T>(hw_blk(smem_raw), state, P, H, invnn, chunks, R, J2, nc, na2, ia, four, ms);
+    b_synth_rhs<T, TMA>(hw_blk(smem_raw), maps, err, state, P, H, invnn, chunks, R, J2, nc, na2, ia, four, ms);
 }
 
 // LPB latitudes per CTA (1, or 2 adjacent ones for latitude-contiguous
@@ -361,12 +436,6 @@ __global__ void __launch_bounds__(32 * kAnalWarpsMax) k_anal_rhs(const C_t<T>* _
 template <class T>
 inline size_t grid_smem(int I, int lpb = 1) {
     return sizeof(C_t<T>) * (9 * lpb + 1) * (size_t)(I / 2);  // nine rows per latitude and the twiddles
-}
-template <class T>
-inline size_t synth_smem(int R) {
-    const size_t coef = sizeof(C_t<T>) * 4 * (R + 1);
-    const size_t red = sizeof(C_t<T>) * kSynthWarps * 6 * 32;
-    return coef > red ? coef : red;
 }
 inline int anal_warps(int J2) {
     const int tiles = (J2 + 31) / 32;

@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(32) k_anal_scalar_f64(const double2* __restric
 mlsdc_status f64_prepare(sh_plan_t p) {
     mlsdc_status s;
     if ((s = raise_smem_limit((const void*)k_grid_rhs<double, 1>, grid_smem<double>(p->I))) != MLSDC_OK) return s;
-    if ((s = raise_smem_limit((const void*)k_synth_rhs<double>, synth_smem<double>(p->R))) != MLSDC_OK) return s;
+    if ((s = raise_smem_limit((const void*)k_synth_rhs<double, false>, synth_smem<double>(p->R))) != MLSDC_OK) return s;
     return MLSDC_OK;
 }
 
@@ -128,8 +128,9 @@ mlsdc_status rhs_explicit_f64(sh_plan_t p, const swe_params* prm, const double* 
     const FourStride fo = four_out_layout(p->J, R, false);  // float64 path: m-contiguous
     if (stage == 0 || stage < 0) {
         MLSDC_LAUNCH("k_synth_rhs<double>",
-                     launch_b(Body::SynthF64, 0, 0, k_synth_rhs<double>, dim3(p->n_synth, b.members), dim3(32 * kSynthWarps),
-                              synth_smem<double>(R), st, (const double2*)state, (const double*)p->d_P,
+                     launch_b(Body::SynthF64, 0, 0, k_synth_rhs<double, false>, dim3(p->n_synth, b.members), dim3(32 * kSynthWarps),
+                              synth_smem<double>(R), st, SynMaps{}, (int*)nullptr, (const double2*)state,
+                              (const double*)p->d_P,
                               (const double*)p->d_H, (const double*)p->d_invnn, (const Chunk*)p->d_synth, R, p->J2,
                               p->nc, -prm->a * prm->a, 1.0 / prm->a, p->d_four_in, ms));
     }

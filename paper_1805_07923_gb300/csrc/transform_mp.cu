@@ -9,6 +9,8 @@
 // times the vorticity) instead of the full (zeta + f) V flux.
 // The float32 tables are rounded on the device from the float64 master tables
 // that sh_plan computes on the host.
+#include <algorithm>
+
 #include "complex.cuh"
 #include "internal.h"
 #include "rhs_kernels.cuh"
@@ -37,8 +39,9 @@ mlsdc_status tc_anal(sh_plan_t p, double a, double* FE, const double* state, dou
 constexpr int kStageAuto = 0, kStageTc = 1;
 
 // each kernel's recorded arguments are its body's (persistent.cu)
-MLSDC_SAME_PACK(k_synth_rhs<float>, b_synth_rhs<float>);
-MLSDC_SAME_PACK(k_synth_rhs<double>, b_synth_rhs<double>);
+MLSDC_SAME_PACK((k_synth_rhs<float, false>), (b_synth_rhs<float, false>));
+MLSDC_SAME_PACK((k_synth_rhs<float, true>), (b_synth_rhs<float, true>));
+MLSDC_SAME_PACK((k_synth_rhs<double, false>), (b_synth_rhs<double, false>));
 MLSDC_SAME_PACK((k_grid_rhs<float, 1>), (b_grid_rhs<float, 1>));
 MLSDC_SAME_PACK(k_anal_rhs<float>, b_anal_rhs<float>);
 MLSDC_SAME_PACK(k_anal_rhs<double>, b_anal_rhs<double>);
@@ -55,6 +58,21 @@ bool stage_uses_tc(const sh_plan_s* p, int stage, int members) {
     const int mode = stage == 0 ? p->mp.synth_mode : p->mp.anal_mode;
     if (mode != kStageAuto) return mode == kStageTc;
     return stage == 0 ? (p->R >= 128 && members >= 8) : p->R >= 64;
+}
+
+// Whether a float32 synthesis launch of `members` states streams its tables
+// by TMA (synth_boxes(R) boxes of 32 rows per work item, all resident in
+// shared memory) or reads them with plain loads.  The TMA form takes one
+// table latency per work item instead of one per unrolled group of degrees,
+// but its shared memory (8 KB per box) limits the CTAs per SM, so it pays for
+// few boxes, and for three boxes only with few members (many members give the
+// plain loads enough CTAs to hide their latency).
+bool synth_uses_tma(const sh_plan_s* p, int members) {
+    const MPTables& t = p->mp;
+    if (!t.syn_tma || t.syn_tma_mode == 2) return false;
+    if (t.syn_tma_mode == 1) return true;
+    const int boxes = synth_boxes(p->R);
+    return boxes <= 2 || (boxes <= 3 && members <= 4);
 }
 
 mlsdc_status mp_init(sh_plan_t p) {
@@ -83,7 +101,17 @@ mlsdc_status mp_init(sh_plan_t p) {
     k_round_f32<<<8, 256>>>(p->d_invnn, t.invnn32, (size_t)(p->R + 1));
     MLSDC_LAUNCHED("k_round_f32");
     MLSDC_CUDA(cudaDeviceSynchronize());
-    mlsdc_status rs = raise_smem_limit((const void*)k_grid_rhs<float, 1>, grid_smem<float>(p->I));
+    // the synthesis can stream its tables by TMA where the row pitch allows (J2 a multiple of 4 floats)
+    MLSDC_CUDA(cudaMalloc((void**)&t.d_err, sizeof(int)));
+    MLSDC_CUDA(cudaMemset(t.d_err, 0, sizeof(int)));
+    const uint32_t bw = (uint32_t)std::min(32, p->J2);
+    t.syn_tma = p->J2 % 4 == 0 &&
+                make_rows_map_f32(&t.syn_maps.P, t.P32, (uint64_t)p->J2, (uint64_t)p->nc, bw, kSynBoxRows) &&
+                make_rows_map_f32(&t.syn_maps.H, t.H32, (uint64_t)p->J2, (uint64_t)p->nc, bw, kSynBoxRows);
+    mlsdc_status rs = raise_smem_limit((const void*)k_synth_rhs<float, false>, synth_smem<float>(p->R));
+    if (rs == MLSDC_OK && t.syn_tma)
+        rs = raise_smem_limit((const void*)k_synth_rhs<float, true>, synth_tma_smem(p->R));
+    if (rs == MLSDC_OK) rs = raise_smem_limit((const void*)k_grid_rhs<float, 1>, grid_smem<float>(p->I));
     if (rs == MLSDC_OK) rs = raise_smem_limit((const void*)k_grid_rhs<float, 2>, grid_smem<float>(p->I, 2));
     if (rs != MLSDC_OK) return rs;
     if (p->precision == MLSDC_TF32 || p->precision == MLSDC_BF16X3) return tc_init(p);
@@ -100,6 +128,7 @@ void mp_free(sh_plan_t p) {
     cudaFree(t.four_out);
     cudaFree(t.lat32);
     cudaFree(t.invnn32);
+    cudaFree(t.d_err);
     t = MPTables();
 }
 
@@ -117,11 +146,22 @@ mlsdc_status rhs_explicit_mp(sh_plan_t p, const swe_params* prm, const double* s
         if (tc && stage_uses_tc(p, 0, b.members)) {
             if ((s = tc_synth(p, state, prm->a, b, st)) != MLSDC_OK) return s;
         } else {
-            MLSDC_LAUNCH("k_synth_rhs<float>",
-                         launch_b(Body::SynthF32, 0, 0, k_synth_rhs<float>, dim3(p->n_synth, b.members), dim3(32 * kSynthWarps),
-                                  synth_smem<float>(R), st, (const double2*)state, (const float*)t.P32,
-                                  (const float*)t.H32, (const float*)t.invnn32, (const Chunk*)p->d_synth, R, p->J2,
-                                  p->nc, -prm->a * prm->a, 1.0 / prm->a, t.four_in, ms));
+            const bool tma = synth_uses_tma(p, b.members);
+            const dim3 grid(p->n_synth, b.members), block(32 * kSynthWarps);
+            const double na2 = -prm->a * prm->a, ia = 1.0 / prm->a;
+            if (tma) {
+                MLSDC_LAUNCH("k_synth_rhs<float, tma>",
+                             launch_b(Body::SynthF32Tma, 0, 0, k_synth_rhs<float, true>, grid, block,
+                                      synth_tma_smem(R), st, t.syn_maps, t.d_err, (const double2*)state,
+                                      (const float*)t.P32, (const float*)t.H32, (const float*)t.invnn32,
+                                      (const Chunk*)p->d_synth, R, p->J2, p->nc, na2, ia, t.four_in, ms));
+            } else {
+                MLSDC_LAUNCH("k_synth_rhs<float>",
+                             launch_b(Body::SynthF32, 0, 0, k_synth_rhs<float, false>, grid, block,
+                                      synth_smem<float>(R), st, t.syn_maps, (int*)nullptr, (const double2*)state,
+                                      (const float*)t.P32, (const float*)t.H32, (const float*)t.invnn32,
+                                      (const Chunk*)p->d_synth, R, p->J2, p->nc, na2, ia, t.four_in, ms));
+            }
         }
     }
     if (stage == 1 || stage < 0) {
@@ -153,6 +193,14 @@ mlsdc_status rhs_explicit_mp(sh_plan_t p, const swe_params* prm, const double* s
     return MLSDC_OK;
 }
 
+// The float32 synthesis's error word (0, or kErrTmaTimeout).
+mlsdc_status mp_error(sh_plan_t p, int* code) {
+    *code = 0;
+    if (!p->mp.d_err) return MLSDC_OK;
+    MLSDC_CUDA(cudaMemcpy(code, p->mp.d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    return MLSDC_OK;
+}
+
 }  // namespace mlsdc
 
 extern "C" mlsdc_status sh_plan_stage_kernels(sh_plan_t p, int members, int* synth_tc, int* anal_tc) {
@@ -178,6 +226,12 @@ extern "C" mlsdc_status sh_plan_set_tc_config(sh_plan_t p, int stage, int member
                                               int warp_specialised) {
     if (!p || !(p->precision == MLSDC_TF32 || p->precision == MLSDC_BF16X3)) return MLSDC_ERR_INVALID;
     return mlsdc::tc_set_config(p, stage, members_per_cta, stages, warp_specialised);
+}
+
+extern "C" mlsdc_status sh_plan_set_synth_tma(sh_plan_t p, int mode) {
+    if (!p || p->precision == MLSDC_FP64 || mode < 0 || mode > 2) return MLSDC_ERR_INVALID;
+    p->mp.syn_tma_mode = mode;
+    return MLSDC_OK;
 }
 
 extern "C" mlsdc_status sh_plan_set_stage_kernels(sh_plan_t p, int synth_mode, int anal_mode) {

@@ -82,6 +82,7 @@ enum class Body : int {
     Interp,
     PadAdd,
     Copy2D,
+    SynthF32Tma,
     Count
 };
 

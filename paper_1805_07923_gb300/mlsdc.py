@@ -55,6 +55,7 @@ _SIGS = {
     "mlsdc_ensemble_destroy": ([_VP], _I),
     "mlsdc_ensemble_step": ([_VP, ctypes.POINTER(_VP), _D, _I, _I, _I, _VP], _I),
     "mlsdc_ensemble_launch_count": ([_VP, ctypes.POINTER(_I64)], _I),
+    "sh_plan_set_synth_tma": ([_VP, _I], _I),
     "mlsdc_ensemble_step_persistent": ([_VP, ctypes.POINTER(_VP), _D, _I, _I, _VP], _I),
     "mlsdc_ensemble_persistent_info": ([_VP, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I),
                                         ctypes.POINTER(_I)], _I),
@@ -239,6 +240,10 @@ class Plan:
         """Per-stage kernel mode of a tensor-core plan: "auto" (the size rule), "tc" or "simt"."""
         _check(lib().sh_plan_set_stage_kernels(self.h, self.STAGE_MODES[synth], self.STAGE_MODES[anal]),
                "sh_plan_set_stage_kernels")
+
+    def set_synth_tma(self, mode: str = "auto"):
+        """How the float32 synthesis reads its tables: "auto" (the size rule), "tma" or "loads"."""
+        _check(lib().sh_plan_set_synth_tma(self.h, {"auto": 0, "tma": 1, "loads": 2}[mode]), "sh_plan_set_synth_tma")
 
 
 def selftest_wait_timeout(timeout_ms: int = 20) -> int:
@@ -517,7 +522,8 @@ class Ensemble:
     BODIES = ["SynthF32", "SynthF64", "GridF32x1", "GridF32x2", "GridF64x1", "AnalF32", "AnalF64", "TcSynthTf32",
               "TcSynthBf16", "TcAnalTf32", "TcAnalBf16", "TcAnalWsTf32", "TcAnalWsBf16", "ImplicitRhs", "SweepNode",
               "SweepNode0_2", "SweepNode0_3", "SweepNode0_4", "SweepNode0_5", "SweepNode0_6", "SweepNode0_7",
-              "SweepNode0_8", "SweepNodeS", "Broadcast", "Restrict", "FasTau", "Interp", "PadAdd", "Copy2D"]
+              "SweepNode0_8", "SweepNodeS", "Broadcast", "Restrict", "FasTau", "Interp", "PadAdd", "Copy2D",
+              "SynthF32Tma"]
 
     def persistent_phase_times(self, stream=None) -> list[tuple[str, float]]:
         """One more persistent step with per-phase timer readings: (body, microseconds) per phase."""
