@@ -126,6 +126,12 @@ mlsdc_status mlsdc_selftest_wait_timeout(int timeout_ms, int* code);
  * 2 = plain loads.  Results are identical either way (the same sums in the
  * same order).  MLSDC_ERR_INVALID for float64 plans or other modes. */
 mlsdc_status sh_plan_set_synth_tma(sh_plan_t plan, int mode);
+/* Check of the float32 -> float64 conversion the analysis kernels use for
+ * F_E (bit rearrangement on the integer pipes instead of the conversion
+ * instruction, which uses the slow float64 pipe): for n device values f_in
+ * writes the library's conversion to d_ours and the hardware's to d_hw
+ * (asynchronous on `stream`).  Not a paper operation. */
+mlsdc_status mlsdc_selftest_convert(const float* f_in, int n, double* d_ours, double* d_hw, void* stream);
 /* Which kernel each Legendre stage of a tensor-core plan (MLSDC_TF32 /
  * MLSDC_BF16X3) runs: the tcgen05 kernel or the float32 CUDA-core kernel of
  * MLSDC_FP32.  By default the choice follows a fixed rule per launch (measured

@@ -11,6 +11,7 @@
 
 #include "async_copy.cuh"
 #include "complex.cuh"
+#include "convert.cuh"
 #include "internal.h"
 #include "rhs_kernels.cuh"  // coriolis_linear, FourStride
 
@@ -613,14 +614,8 @@ __device__ __forceinline__ void b_tc_anal(const Blk& bk, const Maps& maps, const
         const int n = m + k;
         // the nonlinear part from the float32 sums, combined in float32 (its
         // rounding is far below the operands' split-BF16 / TF32 rounding)
-        const float ia = g.ia_f, dm = (float)m;
-        const float2 divCD = cscale(csub(cim(dm, sC), hD), ia);
-        const float2 divAB = cscale(csub(cim(dm, sA), hB), ia);
-        const float2 curlAB = cscale(cadd(cim(dm, sB), hA), ia);
-        const float lap = (float)n * (float)(n + 1) * ia * ia;
-        double2 f0 = make_double2(-(double)divCD.x, -(double)divCD.y);
-        double2 f1 = make_double2(-(double)divAB.x, -(double)divAB.y);
-        double2 f2 = make_double2((double)(curlAB.x + lap * sE.x), (double)(curlAB.y + lap * sE.y));
+        double2 f0, f1, f2;
+        fe_rows(sC, sA, sB, sE, hD, hB, hA, (float)m, g.ia_f, n, f0, f1, f2);
         // the Coriolis part, exactly in float64 (grid products carry no f)
         coriolis_add(g.state + (size_t)(b0 + b) * g.state_ms, g.cor, g.nc, R, m, n, off, g.two_omega, f1, f2);
         if (m == 0) f0.y = f1.y = f2.y = 0.0;
@@ -844,14 +839,8 @@ __device__ __forceinline__ void b_tc_anal_ws(const Blk& bk, const Maps& maps, co
                 const float2 sC{P8[0], P8[1]}, sA{P8[2], P8[3]}, sB{P8[4], P8[5]}, sE{P8[6], P8[7]};
                 const float2 hD{H8[0], H8[1]}, hB{H8[2], H8[3]}, hA{H8[4], H8[5]};
                 const int n = m + k;
-                const float ia = g.ia_f, dm = (float)m;
-                const float2 divCD = cscale(csub(cim(dm, sC), hD), ia);
-                const float2 divAB = cscale(csub(cim(dm, sA), hB), ia);
-                const float2 curlAB = cscale(cadd(cim(dm, sB), hA), ia);
-                const float lap = (float)n * (float)(n + 1) * ia * ia;
-                double2 f0 = make_double2(-(double)divCD.x, -(double)divCD.y);
-                double2 f1 = make_double2(-(double)divAB.x, -(double)divAB.y);
-                double2 f2 = make_double2((double)(curlAB.x + lap * sE.x), (double)(curlAB.y + lap * sE.y));
+                double2 f0, f1, f2;
+                fe_rows(sC, sA, sB, sE, hD, hB, hA, (float)m, g.ia_f, n, f0, f1, f2);
                 coriolis_add(g.state + (size_t)(b0 + b) * g.state_ms, g.cor, g.nc, R, m, n, off, g.two_omega, f1, f2);
                 if (m == 0) f0.y = f1.y = f2.y = 0.0;
                 double2* FE = g.FE + (size_t)(b0 + b) * g.fe_ms;

@@ -29,6 +29,7 @@
 
 #include "async_copy.cuh"
 #include "complex.cuh"
+#include "convert.cuh"
 #include "internal.h"
 
 namespace mlsdc {
@@ -321,6 +322,31 @@ __global__ void __launch_bounds__(256) k_grid_rhs(const C_t<T>* __restrict__ fou
 // with X', Y' the weighted Fourier coefficients (integration by parts of the
 // mu-derivatives); E^m_n = sum_j E' P.  With two_omega_lin != 0 the grid
 // products were formed without f and the Coriolis part is added here exactly.
+// Products and sums rounded as written (never contracted by the compiler),
+// in float32 or float64.
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// F_E's rows from the analysis sums of one coefficient (m, n) (Sec. 2):
+// f0 = -div(C, D), f1 = -div(A, B), f2 = curl(A, B) + n(n+1)/a^2 E, with
+// div(X, Y) = (1/a)(i m X_P - Y_H) and curl(X, Y) = (1/a)(i m Y_P + X_H),
+// in the sums' type T with every operation rounded explicitly, so that each
+// kernel and the persistent kernel's copy of it round alike; then widened to
+// float64 (exactly).  s*: the P-table sums, h*: the H-table sums.
+template <class C, class T>
+__device__ __forceinline__ void fe_rows(C sC, C sA, C sB, C sE, C hD, C hB, C hA, T dm, T ia, int n, double2& f0,
+                                        double2& f1, double2& f2) {
+    const T dCDx = mul_rn(fma_rn(-dm, sC.y, -hD.x), ia), dCDy = mul_rn(fma_rn(dm, sC.x, -hD.y), ia);
+    const T dABx = mul_rn(fma_rn(-dm, sA.y, -hB.x), ia), dABy = mul_rn(fma_rn(dm, sA.x, -hB.y), ia);
+    const T cABx = mul_rn(fma_rn(-dm, sB.y, hA.x), ia), cABy = mul_rn(fma_rn(dm, sB.x, hA.y), ia);
+    const T lap = mul_rn(mul_rn(mul_rn(T(n), T(n + 1)), ia), ia);
+    f0 = make_double2(f64_of(-dCDx), f64_of(-dCDy));
+    f1 = make_double2(f64_of(-dABx), f64_of(-dABy));
+    f2 = make_double2(f64_of(fma_rn(lap, sE.x, cABx)), f64_of(fma_rn(lap, sE.y, cABy)));
+}
+
 constexpr int kAnalTW = 32;  // latitudes per tile of the CUDA-core analysis
 // shared memory of the CUDA-core analysis: per warp [lat][field A..E][even,
 // odd] sums, then the partial sums of warps 1.. for the reduction
@@ -406,14 +432,8 @@ __device__ __forceinline__ void b_anal_rhs(const Blk& bk, const C_t<T>* four_out
     for (int w2 = 1; w2 < nw; ++w2)
         for (int q = 0; q < 7; ++q) s[q] = cadd(s[q], red[w2 - 1][q][lane]);
     const int n = m + k;
-    const T dm = T(m), iaT = T(ia);
-    const C divCD = cscale(csub(cim(dm, s[0]), s[4]), iaT);
-    const C divAB = cscale(csub(cim(dm, s[1]), s[5]), iaT);
-    const C curlAB = cscale(cadd(cim(dm, s[2]), s[6]), iaT);
-    const T lap = T(n) * T(n + 1) * iaT * iaT;
-    double2 f0 = make_double2(-(double)divCD.x, -(double)divCD.y);
-    double2 f1 = make_double2(-(double)divAB.x, -(double)divAB.y);
-    double2 f2 = make_double2((double)(curlAB.x + lap * s[3].x), (double)(curlAB.y + lap * s[3].y));
+    double2 f0, f1, f2;
+    fe_rows(s[0], s[1], s[2], s[3], s[4], s[5], s[6], T(m), T(ia), n, f0, f1, f2);
     if (two_omega_lin != 0.0) coriolis_add(state, cor, nc, R, m, n, off, two_omega_lin, f1, f2);
     if (m == 0) f0.y = f1.y = f2.y = 0.0;
     FE[off + k] = f0;

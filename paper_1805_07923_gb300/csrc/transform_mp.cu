@@ -12,6 +12,7 @@
 #include <algorithm>
 
 #include "complex.cuh"
+#include "convert.cuh"
 #include "internal.h"
 #include "rhs_kernels.cuh"
 
@@ -193,6 +194,16 @@ mlsdc_status rhs_explicit_mp(sh_plan_t p, const swe_params* prm, const double* s
     return MLSDC_OK;
 }
 
+// The integer-pipe conversion of convert.cuh next to the hardware one,
+// element by element (mlsdc_selftest_convert).
+__global__ void k_convert_selftest(const float* __restrict__ f_in, int n, double* __restrict__ d_ours,
+                                   double* __restrict__ d_hw) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        d_ours[i] = f64_of(f_in[i]);
+        d_hw[i] = (double)f_in[i];
+    }
+}
+
 // The float32 synthesis's error word (0, or kErrTmaTimeout).
 mlsdc_status mp_error(sh_plan_t p, int* code) {
     *code = 0;
@@ -226,6 +237,15 @@ extern "C" mlsdc_status sh_plan_set_tc_config(sh_plan_t p, int stage, int member
                                               int warp_specialised) {
     if (!p || !(p->precision == MLSDC_TF32 || p->precision == MLSDC_BF16X3)) return MLSDC_ERR_INVALID;
     return mlsdc::tc_set_config(p, stage, members_per_cta, stages, warp_specialised);
+}
+
+extern "C" mlsdc_status mlsdc_selftest_convert(const float* f_in, int n, double* d_ours, double* d_hw,
+                                              void* stream) {
+    if (!f_in || !d_ours || !d_hw || n < 1) return MLSDC_ERR_INVALID;
+    mlsdc::k_convert_selftest<<<std::min(1024, (n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(f_in, n, d_ours,
+                                                                                                d_hw);
+    MLSDC_LAUNCHED("k_convert_selftest");
+    return MLSDC_OK;
 }
 
 extern "C" mlsdc_status sh_plan_set_synth_tma(sh_plan_t p, int mode) {

@@ -56,6 +56,7 @@ _SIGS = {
     "mlsdc_ensemble_step": ([_VP, ctypes.POINTER(_VP), _D, _I, _I, _I, _VP], _I),
     "mlsdc_ensemble_launch_count": ([_VP, ctypes.POINTER(_I64)], _I),
     "sh_plan_set_synth_tma": ([_VP, _I], _I),
+    "mlsdc_selftest_convert": ([_DP, _I, _DP, _DP, _VP], _I),
     "mlsdc_ensemble_step_persistent": ([_VP, ctypes.POINTER(_VP), _D, _I, _I, _VP], _I),
     "mlsdc_ensemble_persistent_info": ([_VP, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I),
                                         ctypes.POINTER(_I)], _I),
@@ -544,6 +545,18 @@ def mlsdc_ensemble_step_persistent(ens: Ensemble, states: list[torch.Tensor], dt
     arr = (ctypes.c_void_p * len(ptrs))(*[p.value for p in ptrs])
     _check(lib().mlsdc_ensemble_step_persistent(ens.h, arr, float(dt), int(n_iter), int(n_coarse_sweeps),
                                                 _stream(stream)), "mlsdc_ensemble_step_persistent")
+
+
+def selftest_convert(f_in: torch.Tensor, stream=None):
+    """The library's float32 -> float64 conversion next to the hardware's: (d_ours, d_hw)."""
+    if f_in.dtype != torch.float32:
+        raise MlsdcError("selftest_convert: f_in must be float32")
+    n = f_in.numel()
+    d_ours = torch.empty(n, dtype=torch.float64, device=f_in.device)
+    d_hw = torch.empty_like(d_ours)
+    p = lambda t: ctypes.c_void_p(t.data_ptr())
+    _check(lib().mlsdc_selftest_convert(p(f_in), n, p(d_ours), p(d_hw), _stream(stream)), "mlsdc_selftest_convert")
+    return d_ours, d_hw
 
 
 def selftest_grid_barrier_timeout(timeout_ms: int = 20) -> int:
