@@ -199,6 +199,7 @@ struct MPTables {
     float* P32 = nullptr;        // [nc][J2] float32 copy of P
     float* H32 = nullptr;        // [nc][J2]
     float2* tw32 = nullptr;      // [I/2] float32 twiddles
+    float2* stab32 = nullptr;    // [I/2] float32 stage-twiddle table of the radix-4 FFTs (I/2 - 1 used)
     float2* four_in = nullptr;   // [4][J][R+1]
     float2* four_out = nullptr;  // [5][R+1][J] (latitude-contiguous)
     float* lat32 = nullptr;      // [J][4] float32 copy of the plan's d_lat
@@ -227,6 +228,7 @@ struct sh_plan_s {
     double* d_P = nullptr;            // [nc][J2], northern latitudes
     double* d_H = nullptr;            // [nc][J2]
     double2* d_tw = nullptr;          // [I/2] exp(-2 pi i k / I)
+    double2* d_stab = nullptr;        // [I/2] stage-twiddle table of the radix-4 FFTs (I/2 - 1 used)
     int* d_ndeg = nullptr;            // [nc] total degree n of each coefficient
     double* d_cor = nullptr;          // [nc][4] Coriolis factors alpha, beta, gamma, 0 (coriolis_add)
     // Per-latitude and per-degree constants, computed on the host in float64

@@ -168,6 +168,7 @@ static void free_plan(sh_plan_t p) {
     cudaFree(p->d_P);
     cudaFree(p->d_H);
     cudaFree(p->d_tw);
+    cudaFree(p->d_stab);
     cudaFree(p->d_ndeg);
     cudaFree(p->d_cor);
     cudaFree(p->d_lat);

@@ -227,16 +227,28 @@ __global__ void __launch_bounds__(32 * kSynthWarps) k_synth_rhs(const __grid_con
 
 // LPB latitudes per CTA (1, or 2 adjacent ones for latitude-contiguous
 // output: the two values of a (field, m) pair then leave in one store).
+// stabg: the plan's stage-twiddle table (fft4_stage_twiddles of tw, I/2 - 1
+// entries, formed once per plan by k_stage_twiddles), copied into shared
+// memory with its load issued before the packing loads so that the two
+// latencies overlap.
 template <class T, int LPB>
 __device__ __forceinline__ void b_grid_rhs(const Blk& bk, const C_t<T>* four_in, C_t<T>* four_out, const T* lat,
-                                           const C_t<T>* __restrict__ tw, int R, int I, int logI, int J,
-                                           double two_omega, MemberStrides ms, FourStride fx) {
+                                           const C_t<T>* __restrict__ tw, const C_t<T>* __restrict__ stabg, int R,
+                                           int I, int logI, int J, double two_omega, MemberStrides ms,
+                                           FourStride fx) {
     using C = C_t<T>;
     // [LPB][4][I/2]: zeta, Phi', U, V packed rows; then [LPB][5][I/2]: A..E; then the twiddles
     C* sx = reinterpret_cast<C*>(bk.smem);
     const int Hn = I >> 1, logH = logI - 1;
-    C* stab = sx + 9 * LPB * Hn;                 // stage twiddles (I/2 - 1 entries)
-    fft4_stage_twiddles(bk, stab, tw, Hn, logH, I);  // constant table
+    C* stab = sx + 9 * LPB * Hn;  // stage twiddles (I/2 - 1 entries)
+    const int nst = Hn - 1;
+    const bool one_each = nst <= (int)bk.nt;  // one entry per thread: held in a register over the packing loop
+    C twr = mkc(T(0), T(0));
+    if (one_each) {
+        if ((int)bk.t < nst) twr = stabg[bk.t];
+    } else {
+        for (int e = bk.t; e < nst; e += bk.nt) stab[e] = stabg[e];
+    }
     pdl_wait();
     pdl_launch();
     four_in += bk.idx.y * ms.four_in;
@@ -248,6 +260,7 @@ __device__ __forceinline__ void b_grid_rhs(const Blk& bk, const C_t<T>* four_in,
         const int l = r >> 2, f = r & 3;
         sx[r * Hn + swz(k)] = irfft_pack(four_in + f * fs + (size_t)(j0 + l) * (R + 1), k, R, Hn, tw);
     }
+    if (one_each && (int)bk.t < nst) stab[bk.t] = twr;
     bk.sync();
     // inverse by decimation in frequency: slot q now holds the longitude pair
     // at the digit-reversed position of q
@@ -312,10 +325,17 @@ __device__ __forceinline__ void b_grid_rhs(const Blk& bk, const C_t<T>* four_in,
 template <class T, int LPB>
 __global__ void __launch_bounds__(256) k_grid_rhs(const C_t<T>* __restrict__ four_in, C_t<T>* __restrict__ four_out,
                                                   const T* __restrict__ lat, const C_t<T>* __restrict__ tw,
-                                                  int R, int I, int logI, int J,
+                                                  const C_t<T>* __restrict__ stabg, int R, int I, int logI, int J,
                                                   double two_omega, MemberStrides ms, FourStride fx) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    b_grid_rhs<T, LPB>(hw_blk(smem_raw), four_in, four_out, lat, tw, R, I, logI, J, two_omega, ms, fx);
+    b_grid_rhs<T, LPB>(hw_blk(smem_raw), four_in, four_out, lat, tw, stabg, R, I, logI, J, two_omega, ms, fx);
+}
+
+// The stage-twiddle table of a plan (fft4_stage_twiddles into global memory),
+// formed once by one CTA.
+template <class C>
+__global__ void k_stage_twiddles(C* __restrict__ tab, const C* __restrict__ tw, int N, int logN, int I) {
+    fft4_stage_twiddles(hw_blk(nullptr), tab, tw, N, logN, I);
 }
 
 // div(X,Y)^m_n = (1/a) sum_j [ i m X' P - Y' H ], curl(X,Y)^m_n = (1/a) sum_j [ i m Y' P + X' H ]

@@ -114,6 +114,10 @@ __global__ void __launch_bounds__(32) k_anal_scalar_f64(const double2* __restric
 
 mlsdc_status f64_prepare(sh_plan_t p) {
     mlsdc_status s;
+    MLSDC_CUDA(cudaMalloc((void**)&p->d_stab, (size_t)(p->I / 2) * sizeof(double2)));
+    p->bytes += (int64_t)(p->I / 2) * sizeof(double2);
+    k_stage_twiddles<double2><<<1, 256>>>(p->d_stab, p->d_tw, p->I / 2, p->logI - 1, p->I);
+    MLSDC_LAUNCHED("k_stage_twiddles");
     if ((s = raise_smem_limit((const void*)k_grid_rhs<double, 1>, grid_smem<double>(p->I))) != MLSDC_OK) return s;
     if ((s = raise_smem_limit((const void*)k_synth_rhs<double, false>, synth_smem<double>(p->R))) != MLSDC_OK) return s;
     return MLSDC_OK;
@@ -138,7 +142,8 @@ mlsdc_status rhs_explicit_f64(sh_plan_t p, const swe_params* prm, const double* 
         MLSDC_LAUNCH("k_grid_rhs<double>",
                      launch_b(Body::GridF64x1, 0, 0, k_grid_rhs<double, 1>, dim3(p->J, b.members), dim3(256), grid_smem<double>(p->I),
                               st, (const double2*)p->d_four_in, p->d_four_out, (const double*)p->d_lat,
-                              (const double2*)p->d_tw, R, p->I, p->logI, p->J, 2.0 * prm->omega, ms, fo));
+                              (const double2*)p->d_tw, (const double2*)p->d_stab, R, p->I, p->logI, p->J, 2.0 * prm->omega, ms,
+                              fo));
     }
     if (stage == 2 || stage < 0) {
         MLSDC_LAUNCH("k_anal_rhs<double>",

@@ -87,6 +87,7 @@ mlsdc_status mp_init(sh_plan_t p) {
     };
     bool ok = alloc((void**)&t.P32, ntab * sizeof(float)) && alloc((void**)&t.H32, ntab * sizeof(float)) &&
               alloc((void**)&t.tw32, (p->I / 2) * sizeof(float2)) &&
+              alloc((void**)&t.stab32, (p->I / 2) * sizeof(float2)) &&
               alloc((void**)&t.four_in, 4 * nfour * p->max_members * sizeof(float2)) &&
               alloc((void**)&t.four_out, 5 * nfour * p->max_members * sizeof(float2)) &&
               alloc((void**)&t.lat32, (size_t)4 * p->J * sizeof(float)) &&
@@ -98,6 +99,7 @@ mlsdc_status mp_init(sh_plan_t p) {
     k_round_f32<<<1024, 256>>>(p->d_P, t.P32, ntab);
     k_round_f32<<<1024, 256>>>(p->d_H, t.H32, ntab);
     k_round_c32<<<8, 256>>>(p->d_tw, t.tw32, p->I / 2);
+    k_stage_twiddles<float2><<<1, 256>>>(t.stab32, t.tw32, p->I / 2, p->logI - 1, p->I);
     k_round_f32<<<8, 256>>>(p->d_lat, t.lat32, (size_t)4 * p->J);
     k_round_f32<<<8, 256>>>(p->d_invnn, t.invnn32, (size_t)(p->R + 1));
     MLSDC_LAUNCHED("k_round_f32");
@@ -125,6 +127,7 @@ void mp_free(sh_plan_t p) {
     cudaFree(t.P32);
     cudaFree(t.H32);
     cudaFree(t.tw32);
+    cudaFree(t.stab32);
     cudaFree(t.four_in);
     cudaFree(t.four_out);
     cudaFree(t.lat32);
@@ -170,12 +173,12 @@ mlsdc_status rhs_explicit_mp(sh_plan_t p, const swe_params* prm, const double* s
             MLSDC_LAUNCH("k_grid_rhs<float, 2>",
                          launch_b(Body::GridF32x2, 0, 0, k_grid_rhs<float, 2>, dim3(p->J / 2, b.members), dim3(256),
                                   grid_smem<float>(p->I, 2), st, (const float2*)t.four_in, t.four_out,
-                                  (const float*)t.lat32, (const float2*)t.tw32, R, p->I, p->logI, p->J, 0.0, ms, fo));
+                                  (const float*)t.lat32, (const float2*)t.tw32, (const float2*)t.stab32, R, p->I, p->logI, p->J, 0.0, ms, fo));
         } else {
             MLSDC_LAUNCH("k_grid_rhs<float, 1>",
                          launch_b(Body::GridF32x1, 0, 0, k_grid_rhs<float, 1>, dim3(p->J, b.members), dim3(256), grid_smem<float>(p->I), st,
                                   (const float2*)t.four_in, t.four_out, (const float*)t.lat32,
-                                  (const float2*)t.tw32, R, p->I, p->logI, p->J, 0.0, ms, fo));
+                                  (const float2*)t.tw32, (const float2*)t.stab32, R, p->I, p->logI, p->J, 0.0, ms, fo));
         }
     }
     if (stage == 2 || stage < 0) {
