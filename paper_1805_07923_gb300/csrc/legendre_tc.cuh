@@ -811,6 +811,14 @@ __device__ __forceinline__ void b_tc_anal_ws(const Blk& bk, const Maps& maps, co
         int tcount = 0;
         for (int tile = bk.idx.x; tile < g.n_tiles; tile += bk.dim.x, ++tcount) {
             const int buf = tcount & 1;
+            const int2 tl = g.tiles[tile];
+            const int m = tl.x, t = tl.y;
+            const int nm = R + 1 - m;
+            const int off = m * (R + 1) - m * (m - 1) / 2;
+            const int k = t * kTileRows + 32 * (warp & 3) + lane;
+            // the first member's Coriolis operands, loaded while the tile's MMAs run
+            CorIn cn{};
+            if (k < nm) cn = coriolis_load(g.state + (size_t)b0 * g.state_ms, g.cor, g.nc, R, m, m + k, off);
             if (!mbar_wait(sa(&acc_full[buf]), (uint32_t)(tcount / 2) & 1)) {
                 if (lane == 0) atomicExch(g.err, kErrMmaTimeout);
                 *c.abort = 1;
@@ -818,13 +826,11 @@ __device__ __forceinline__ void b_tc_anal_ws(const Blk& bk, const Maps& maps, co
                 break;
             }
             tc_fence_after();
-            const int2 tl = g.tiles[tile];
-            const int m = tl.x, t = tl.y;
-            const int nm = R + 1 - m;
-            const int off = m * (R + 1) - m * (m - 1) / 2;
-            const int k = t * kTileRows + 32 * (warp & 3) + lane;
             const uint32_t base = tmem + lane_rows + (uint32_t)(buf * 2 * N);
             for (int b = 0; b < bc; ++b) {
+                const CorIn cc = cn;
+                if (k < nm && b + 1 < bc)
+                    cn = coriolis_load(g.state + (size_t)(b0 + b + 1) * g.state_ms, g.cor, g.nc, R, m, m + k, off);
                 float vP[16], vH[16];
                 tmem_ld16(base + 16 * b, vP);
                 tmem_ld16(base + N + 16 * b, vH);
@@ -841,7 +847,7 @@ __device__ __forceinline__ void b_tc_anal_ws(const Blk& bk, const Maps& maps, co
                 const int n = m + k;
                 double2 f0, f1, f2;
                 fe_rows(sC, sA, sB, sE, hD, hB, hA, (float)m, g.ia_f, n, f0, f1, f2);
-                coriolis_add(g.state + (size_t)(b0 + b) * g.state_ms, g.cor, g.nc, R, m, n, off, g.two_omega, f1, f2);
+                coriolis_apply(cc, g.two_omega, f1, f2);
                 if (m == 0) f0.y = f1.y = f2.y = 0.0;
                 double2* FE = g.FE + (size_t)(b0 + b) * g.fe_ms;
                 FE[off + k] = f0;

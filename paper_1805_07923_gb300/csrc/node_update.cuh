@@ -151,6 +151,42 @@ __device__ __forceinline__ void coriolis_terms(const double* __restrict__ cf, do
     coriolis_delta_row(cf, zl, dk, zu, two_omega, f2);
 }
 
+// The operands of coriolis_add for one coefficient, read ahead of their use
+// (the analysis epilogues issue these loads before they wait for their sums).
+struct CorIn {
+    double2 zl, zk, zu, dl, dk, du;
+    double al, be, ga;
+};
+__device__ __forceinline__ CorIn coriolis_load(const double2* __restrict__ state, const double* __restrict__ cor,
+                                               int nc, int R, int m, int n, int off) {
+    const int k = n - m;
+    const double2* z = state + nc + off;
+    const double2* d = state + 2 * nc + off;
+    CorIn c;
+    c.zl = c.zu = c.dl = c.du = make_double2(0.0, 0.0);
+    if (n - 1 >= m) { c.zl = z[k - 1]; c.dl = d[k - 1]; }
+    if (n + 1 <= R) { c.zu = z[k + 1]; c.du = d[k + 1]; }
+    c.zk = z[k];
+    c.dk = d[k];
+    const double* cf = cor + 4 * (size_t)(off + k);
+    const double2 ab = *reinterpret_cast<const double2*>(cf);
+    c.al = ab.x;
+    c.be = ab.y;
+    c.ga = cf[2];
+    return c;
+}
+// coriolis_terms on loaded operands (the same operations in the same order).
+__device__ __forceinline__ void coriolis_apply(const CorIn& c, double two_omega, double2& f1, double2& f2) {
+    const double ux = fma(c.al, c.dl.x, fma(c.be, c.du.x, -c.ga * c.zk.y));
+    const double uy = fma(c.al, c.dl.y, fma(c.be, c.du.y, c.ga * c.zk.x));
+    f1.x = fma(-two_omega, ux, f1.x);
+    f1.y = fma(-two_omega, uy, f1.y);
+    const double vx = fma(c.al, c.zl.x, fma(c.be, c.zu.x, c.ga * c.dk.y));
+    const double vy = fma(c.al, c.zl.y, fma(c.be, c.zu.y, -c.ga * c.dk.x));
+    f2.x = fma(two_omega, vx, f2.x);
+    f2.y = fma(two_omega, vy, f2.y);
+}
+
 __device__ inline void coriolis_add(const double2* __restrict__ state, const double* __restrict__ cor, int nc, int R,
                                     int m, int n, int off, double two_omega, double2& f1, double2& f2) {
     const int k = n - m;
