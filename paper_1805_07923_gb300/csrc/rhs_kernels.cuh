@@ -249,11 +249,22 @@ __device__ __forceinline__ void b_grid_rhs(const Blk& bk, const C_t<T>* four_in,
     } else {
         for (int e = bk.t; e < nst; e += bk.nt) stab[e] = stabg[e];
     }
+    const int j0 = bk.idx.x * LPB;
+    // lat[j] = (mu, 1/(1-mu^2), w/((1-mu^2) I), w/I): no float64 division
+    // here.  A constant table: with one latitude per CTA (launches of one or
+    // two members, few CTAs) it is loaded ahead of its uses between the FFT
+    // passes, taking its latency off the chain of barriers; with two (batched
+    // launches, many CTAs per SM) the extra registers measured slower, and it
+    // is read where it is used.
+    T latv[LPB][4];
+    if (LPB == 1) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) latv[0][q] = lat[4 * j0 + q];
+    }
     pdl_wait();
     pdl_launch();
     four_in += bk.idx.y * ms.four_in;
     four_out += bk.idx.y * ms.four_out;
-    const int j0 = bk.idx.x * LPB;
     const size_t fs = (size_t)J * (R + 1);
     for (int t = bk.t; t < 4 * LPB * Hn; t += bk.nt) {
         const int r = t >> logH, k = t & (Hn - 1);  // row r = 4 l + f
@@ -266,12 +277,15 @@ __device__ __forceinline__ void b_grid_rhs(const Blk& bk, const C_t<T>* four_in,
     // at the digit-reversed position of q
     fft4_dif(bk, sx, 4 * LPB, Hn, logH, stab, true);
     C* y = sx + 4 * LPB * Hn;
-    // lat[j] = (mu, 1/(1-mu^2), w/((1-mu^2) I), w/I): no float64 division here
     T fl[LPB], rcl[LPB];
 #pragma unroll
     for (int l = 0; l < LPB; ++l) {
-        fl[l] = T(two_omega) * lat[4 * (j0 + l)];
-        rcl[l] = lat[4 * (j0 + l) + 1];
+        if (LPB > 1) {
+            latv[l][0] = lat[4 * (j0 + l)];
+            latv[l][1] = lat[4 * (j0 + l) + 1];
+        }
+        fl[l] = T(two_omega) * latv[l][0];
+        rcl[l] = latv[l][1];
     }
     for (int t = bk.t; t < LPB * Hn; t += bk.nt) {
         const int l = LPB == 1 ? 0 : t >> logH;
@@ -297,8 +311,12 @@ __device__ __forceinline__ void b_grid_rhs(const Blk& bk, const C_t<T>* four_in,
     T sAD[LPB], sE[LPB];  // w/((1-mu^2) I) for A..D, w/I for E
 #pragma unroll
     for (int l = 0; l < LPB; ++l) {
-        sAD[l] = lat[4 * (j0 + l) + 2];
-        sE[l] = lat[4 * (j0 + l) + 3];
+        if (LPB > 1) {
+            latv[l][2] = lat[4 * (j0 + l) + 2];
+            latv[l][3] = lat[4 * (j0 + l) + 3];
+        }
+        sAD[l] = latv[l][2];
+        sE[l] = latv[l][3];
     }
     for (int t = bk.t; t < 5 * (R + 1); t += bk.nt) {
         const int fld = t / (R + 1);

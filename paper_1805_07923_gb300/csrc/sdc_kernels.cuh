@@ -55,14 +55,20 @@ __device__ __forceinline__ void b_sweep_node(const Blk& bk, double2* Th, const d
     const int c = bk.idx.x * kNodeCoefs + cl;
     const bool live = c < nc;
     const size_t o = (size_t)f * nc + c;
+    // the degree and the solve reciprocals (constant tables): loaded ahead, their latency under the sums
+    int nd = 0;
+    double2 rc = make_double2(0.0, 0.0);
+    if (live) {
+        nd = ndeg[c];
+        rc = recips[nd];
+    }
     if (live) sb[f][cl] = node_rhs(Th, FIo, FEo, FIn, FEn, tau, node, o, row);
     bk.sync();
     if (!live) return;
-    const int nd = ndeg[c];
     const double n = nd;
     const double L = -n * (n + 1.0) * ph.inv_a2;
     double2 th, fi;  // each thread only its own field (warp-uniform f)
-    node_solve_field(f, L, row.qimm, ph, recips[nd], sb[0][cl], sb[1][cl], sb[2][cl], th, fi);
+    node_solve_field(f, L, row.qimm, ph, rc, sb[0][cl], sb[1][cl], sb[2][cl], th, fi);
     const size_t om = (m + 1) * node + o;
     Th[om] = th;
     FIn[om] = fi;
@@ -90,6 +96,13 @@ __device__ __forceinline__ void b_sweep_node0(const Blk& bk, double2* Th, const 
     const int c = bk.idx.x * kNodeCoefs + cl;
     const bool live = c < nc;
     const size_t o = (size_t)f * nc + c;
+    // the degree and the solve reciprocals (constant tables): loaded ahead, their latency under the sums
+    int nd = 0;
+    double2 rc = make_double2(0.0, 0.0);
+    if (live) {
+        nd = ndeg[c];
+        rc = recips[nd];
+    }
     if (live) {
         double2 acc[MM + 1];
         const double2 t0 = Th[o];
@@ -117,11 +130,10 @@ __device__ __forceinline__ void b_sweep_node0(const Blk& bk, double2* Th, const 
     }
     bk.sync();
     if (!live) return;
-    const int nd = ndeg[c];
     const double n = nd;
     const double L = -n * (n + 1.0) * ph.inv_a2;
     double2 th, fi;
-    node_solve_field(f, L, sm.qi[1][1], ph, recips[nd], sb[0][cl], sb[1][cl], sb[2][cl], th, fi);
+    node_solve_field(f, L, sm.qi[1][1], ph, rc, sb[0][cl], sb[1][cl], sb[2][cl], th, fi);
     Th[node + o] = th;
     FIn[node + o] = fi;
     FIn[o] = FIo[o];
@@ -143,6 +155,13 @@ __device__ __forceinline__ void b_sweep_node_s(const Blk& bk, double2* Th, doubl
     const int c = bk.idx.x * kNodeCoefs + cl;
     const bool live = c < nc;
     const size_t o = (size_t)f * nc + c;
+    // the degree and the solve reciprocals (constant tables): loaded ahead, their latency under the sums
+    int nd = 0;
+    double2 rc = make_double2(0.0, 0.0);
+    if (live) {
+        nd = ndeg[c];
+        rc = recips[nd];
+    }
     if (live) {
         double2 acc = S[(m - 1) * node + o];
         for (int j = 1; j <= m; ++j) {
@@ -153,11 +172,10 @@ __device__ __forceinline__ void b_sweep_node_s(const Blk& bk, double2* Th, doubl
     }
     bk.sync();
     if (!live) return;
-    const int nd = ndeg[c];
     const double n = nd;
     const double L = -n * (n + 1.0) * ph.inv_a2;
     double2 th, fi;
-    node_solve_field(f, L, row.qimm, ph, recips[nd], sb[0][cl], sb[1][cl], sb[2][cl], th, fi);
+    node_solve_field(f, L, row.qimm, ph, rc, sb[0][cl], sb[1][cl], sb[2][cl], th, fi);
     const size_t om = (m + 1) * node + o;
     Th[om] = th;
     FIn[om] = fi;
