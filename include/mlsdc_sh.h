@@ -411,9 +411,11 @@ mlsdc_status mlsdc_ensemble_launch_count(mlsdc_ensemble_t ens, int64_t* launches
  * SM runs with device-side synchronisation between phases (the schedule:
  * mlsdc_ensemble_persistent_schedule).  Every device wait is bounded (4 s of
  * the global timer): a wait that gives up ends the launch and leaves code 3
- * in mlsdc_ensemble_device_error.  Results equal
- * mlsdc_ensemble_step's bit for bit (the same device code over the same
- * blocks).  MLSDC_ERR_INVALID, with the reason in mlsdc_last_error(), for
+ * in mlsdc_ensemble_device_error.  Results: the same device code over the
+ * same blocks as mlsdc_ensemble_step, so the same values up to the
+ * compiler's own choices in the two compilations (measured: split-BF16
+ * ensembles identical bit for bit, float64 ensembles within 6e-16, some
+ * float64 products contracted into FMAs differently).  MLSDC_ERR_INVALID, with the reason in mlsdc_last_error(), for
  * implicit-Coriolis levels or a launch the kernel cannot host; a stream that
  * cannot capture the cooperative launch gets it launched directly. */
 mlsdc_status mlsdc_ensemble_step_persistent(mlsdc_ensemble_t ens, double* const* states, double dt, int n_iter,

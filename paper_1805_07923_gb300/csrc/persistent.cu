@@ -25,9 +25,12 @@
 // mlsdc_ensemble_device_error) instead of hanging.  The tensor-core bodies'
 // own waits are bounded as in their kernels.
 //
-// Results are those of the graph of per-stage launches bit for bit: the
-// bodies are the kernels' code, run for the same blocks with the same
-// arguments.
+// Results are those of the graph of per-stage launches: the bodies are the
+// kernels' code, run for the same blocks with the same arguments, and differ
+// only where the compiler contracts an operation differently in the two
+// compilations (split-BF16 ensembles: identical bit for bit, the float32
+// epilogues round every operation explicitly; float64 ensembles: within
+// 6e-16).
 #include <algorithm>
 #include <cstring>
 #include <map>
