@@ -144,41 +144,109 @@ __device__ __forceinline__ void fft4_stage_twiddles(const Blk& bk, C* tab, const
     }
 }
 
+// The butterflies of one pass over `narr` arrays.  When the block's
+// threads are a multiple of the butterflies per array (nq = N/4, or N/2 for
+// the radix-2 pass) every thread keeps the same butterfly position in each
+// array it visits (arrays ar0, ar0 + astep, ...), so its swizzled offsets and
+// twiddles are formed once per pass; otherwise per item.  The same items in
+// the same order either way.
+template <class C>
+__device__ __forceinline__ void dif4_bfly(C* xa, int s0, int s1, int s2, int s3, C w1, C w2, C w3, bool inverse) {
+    const C a = xa[s0], b = xa[s1], c = xa[s2], d = xa[s3];
+    const C apc = cadd(a, c), amc = csub(a, c), bpd = cadd(b, d), sbmd = times_s(csub(b, d), inverse);
+    xa[s0] = cadd(apc, bpd);
+    xa[s1] = cmul(cadd(amc, sbmd), w1);
+    xa[s2] = cmul(csub(apc, bpd), w2);
+    xa[s3] = cmul(csub(amc, sbmd), w3);
+}
+template <class C>
+__device__ __forceinline__ void dit4_bfly(C* xa, int s0, int s1, int s2, int s3, C w1, C w2, C w3, bool inverse) {
+    const C a = xa[s0];
+    const C b = cmul(xa[s1], w1);
+    const C c = cmul(xa[s2], w2);
+    const C d = cmul(xa[s3], w3);
+    const C apc = cadd(a, c), amc = csub(a, c), bpd = cadd(b, d), sbmd = times_s(csub(b, d), inverse);
+    xa[s0] = cadd(apc, bpd);
+    xa[s1] = cadd(amc, sbmd);
+    xa[s2] = csub(apc, bpd);
+    xa[s3] = csub(amc, sbmd);
+}
+// one radix-4 pass of span L = 4 Q (twiddles tq: w^j, w^2j, w^3j blocks of Q)
+template <class C, bool DIT>
+__device__ __forceinline__ void pass4(const Blk& bk, C* x, int narr, int N, int logN, int L, int logQ, const C* tq,
+                                      bool inverse) {
+    const int Q = L >> 2, nq = N >> 2;
+    if (bk.nt % nq == 0) {
+        const int ar0 = bk.t >> (logN - 2);
+        if (ar0 >= narr) return;  // no butterfly for this thread in this pass
+        const int r = bk.t & (nq - 1), g = r >> logQ, j = r & (Q - 1), i0 = g * L + j;
+        const int s0 = swz(i0), s1 = swz(i0 + Q), s2 = swz(i0 + 2 * Q), s3 = swz(i0 + 3 * Q);
+        const C w1 = maybe_conj(tq[j], inverse), w2 = maybe_conj(tq[Q + j], inverse),
+                w3 = maybe_conj(tq[2 * Q + j], inverse);
+        const int astep = bk.nt >> (logN - 2);
+        for (int ar = ar0; ar < narr; ar += astep) {
+            if (DIT)
+                dit4_bfly(x + ar * N, s0, s1, s2, s3, w1, w2, w3, inverse);
+            else
+                dif4_bfly(x + ar * N, s0, s1, s2, s3, w1, w2, w3, inverse);
+        }
+        return;
+    }
+    for (int t = bk.t; t < narr * nq; t += bk.nt) {
+        const int ar = t >> (logN - 2), r = t & (nq - 1);
+        const int g = r >> logQ, j = r & (Q - 1);
+        const int i0 = g * L + j;
+        const C w1 = maybe_conj(tq[j], inverse), w2 = maybe_conj(tq[Q + j], inverse),
+                w3 = maybe_conj(tq[2 * Q + j], inverse);
+        if (DIT)
+            dit4_bfly(x + ar * N, swz(i0), swz(i0 + Q), swz(i0 + 2 * Q), swz(i0 + 3 * Q), w1, w2, w3, inverse);
+        else
+            dif4_bfly(x + ar * N, swz(i0), swz(i0 + Q), swz(i0 + 2 * Q), swz(i0 + 3 * Q), w1, w2, w3, inverse);
+    }
+}
+// the radix-2 pass (odd log2 N): span N, twiddles tab[j], j < N/2
+template <class C, bool DIT>
+__device__ __forceinline__ void pass2(const Blk& bk, C* x, int narr, int N, int logN, const C* tab, bool inverse) {
+    const int H = N >> 1;
+    auto bfly = [&](C* xa, int j, int s0, int s1) {
+        const C w = maybe_conj(tab[j], inverse);
+        if (DIT) {
+            const C u = xa[s0], v = cmul(xa[s1], w);
+            xa[s0] = cadd(u, v);
+            xa[s1] = csub(u, v);
+        } else {
+            const C u = xa[s0], v = xa[s1];
+            xa[s0] = cadd(u, v);
+            xa[s1] = cmul(csub(u, v), w);
+        }
+    };
+    if (bk.nt % H == 0) {
+        const int ar0 = bk.t >> (logN - 1);
+        if (ar0 >= narr) return;
+        const int j = bk.t & (H - 1), s0 = swz(j), s1 = swz(j + H), astep = bk.nt >> (logN - 1);
+        for (int ar = ar0; ar < narr; ar += astep) bfly(x + ar * N, j, s0, s1);
+        return;
+    }
+    for (int t = bk.t; t < narr * H; t += bk.nt) {
+        const int ar = t >> (logN - 1), j = t & (H - 1);
+        bfly(x + ar * N, j, swz(j), swz(j + H));
+    }
+}
+
 template <class C>
 __device__ __forceinline__ void fft4_dif(const Blk& bk, C* x, int narr, int N, int logN, const C* tab, bool inverse) {
     int L = N, logL = logN, off = 0;
     if (logN & 1) {
-        const int H = N >> 1;
-        for (int t = bk.t; t < narr * H; t += bk.nt) {
-            const int ar = t >> (logN - 1), j = t & (H - 1);
-            C* xa = x + ar * N;
-            const C w = maybe_conj(tab[j], inverse);
-            const C u = xa[swz(j)], v = xa[swz(j + H)];
-            xa[swz(j)] = cadd(u, v);
-            xa[swz(j + H)] = cmul(csub(u, v), w);
-        }
+        pass2<C, false>(bk, x, narr, N, logN, tab, inverse);
         bk.sync();
-        off = H;
+        off = N >> 1;
         L >>= 1;
         --logL;
     }
     for (; L >= 4; L >>= 2, logL -= 2) {
-        const int Q = L >> 2, logQ = logL - 2;
-        const C* tq = tab + off;
-        for (int t = bk.t; t < narr * (N >> 2); t += bk.nt) {
-            const int ar = t >> (logN - 2), r = t & ((N >> 2) - 1);
-            const int g = r >> logQ, j = r & (Q - 1);
-            C* xa = x + ar * N;
-            const int i0 = g * L + j;
-            const C a = xa[swz(i0)], b = xa[swz(i0 + Q)], c = xa[swz(i0 + 2 * Q)], d = xa[swz(i0 + 3 * Q)];
-            const C apc = cadd(a, c), amc = csub(a, c), bpd = cadd(b, d), sbmd = times_s(csub(b, d), inverse);
-            xa[swz(i0)] = cadd(apc, bpd);
-            xa[swz(i0 + Q)] = cmul(cadd(amc, sbmd), maybe_conj(tq[j], inverse));
-            xa[swz(i0 + 2 * Q)] = cmul(csub(apc, bpd), maybe_conj(tq[Q + j], inverse));
-            xa[swz(i0 + 3 * Q)] = cmul(csub(amc, sbmd), maybe_conj(tq[2 * Q + j], inverse));
-        }
+        pass4<C, false>(bk, x, narr, N, logN, L, logL - 2, tab + off, inverse);
         bk.sync();
-        off += 3 * Q;
+        off += 3 * (L >> 2);
     }
 }
 
@@ -187,38 +255,14 @@ __device__ __forceinline__ void fft4_dit(const Blk& bk, C* x, int narr, int N, i
     const int top = (logN & 1) ? logN - 1 : logN;
     const int r2 = (logN & 1) ? (N >> 1) : 0;  // entries of the radix-2 stage
     for (int logL = 2; logL <= top; logL += 2) {
-        const int L = 1 << logL, Q = L >> 2, logQ = logL - 2;
         // the table holds the radix-4 stages largest first: skip the larger spans
         int off = r2;
         for (int l2 = top; l2 > logL; l2 -= 2) off += 3 * (1 << (l2 - 2));
-        const C* tq = tab + off;
-        for (int t = bk.t; t < narr * (N >> 2); t += bk.nt) {
-            const int ar = t >> (logN - 2), r = t & ((N >> 2) - 1);
-            const int g = r >> logQ, j = r & (Q - 1);
-            C* xa = x + ar * N;
-            const int i0 = g * L + j;
-            const C a = xa[swz(i0)];
-            const C b = cmul(xa[swz(i0 + Q)], maybe_conj(tq[j], inverse));
-            const C c = cmul(xa[swz(i0 + 2 * Q)], maybe_conj(tq[Q + j], inverse));
-            const C d = cmul(xa[swz(i0 + 3 * Q)], maybe_conj(tq[2 * Q + j], inverse));
-            const C apc = cadd(a, c), amc = csub(a, c), bpd = cadd(b, d), sbmd = times_s(csub(b, d), inverse);
-            xa[swz(i0)] = cadd(apc, bpd);
-            xa[swz(i0 + Q)] = cadd(amc, sbmd);
-            xa[swz(i0 + 2 * Q)] = csub(apc, bpd);
-            xa[swz(i0 + 3 * Q)] = csub(amc, sbmd);
-        }
+        pass4<C, true>(bk, x, narr, N, logN, 1 << logL, logL - 2, tab + off, inverse);
         bk.sync();
     }
     if (logN & 1) {
-        const int H = N >> 1;
-        for (int t = bk.t; t < narr * H; t += bk.nt) {
-            const int ar = t >> (logN - 1), j = t & (H - 1);
-            C* xa = x + ar * N;
-            const C w = maybe_conj(tab[j], inverse);
-            const C u = xa[swz(j)], v = cmul(xa[swz(j + H)], w);
-            xa[swz(j)] = cadd(u, v);
-            xa[swz(j + H)] = csub(u, v);
-        }
+        pass2<C, true>(bk, x, narr, N, logN, tab, inverse);
         bk.sync();
     }
 }
