@@ -71,6 +71,22 @@ __device__ __forceinline__ void pdl_launch() { asm volatile("griddepcontrol.laun
 // environment sets MLSDC_PDL=1).
 bool pdl_enabled();
 
+// Programmatic serialisation for the launches made on this thread while a
+// PdlScope(true) is alive, whatever pdl_enabled() says: for a kernel whose
+// set-up before pdl_wait() (tensor memory, barriers, the first table tiles)
+// is worth running beside its predecessor's tail.  Used for the
+// tensor-core analysis after the FFT kernel; measured on the split-BF16
+// step (150-step runs, two boxes): 1070 -> 1076 and 1081 steps/s.  The same
+// for the synthesis, the FFT, the node updates or the transfers made the
+// step slower (FFT 994, node updates 1045, transfers 1068): their
+// successors' CTAs then sit on SMs the predecessor still needs.
+bool& pdl_scope_flag();
+struct PdlScope {
+    bool prev;
+    explicit PdlScope(bool on) : prev(pdl_scope_flag()) { pdl_scope_flag() = prev || on; }
+    ~PdlScope() { pdl_scope_flag() = prev; }
+};
+
 // One shared-memory carveout for every kernel launched through launch_k:
 // two thirds of the SM's configurable L1/shared memory as shared memory.
 // An SM switches its L1/shared split only when idle, so a sequence of
@@ -97,7 +113,7 @@ inline cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, siz
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = pdl_enabled() ? 1 : 0;
+    attr[0].val.programmaticStreamSerializationAllowed = (pdl_enabled() || pdl_scope_flag()) ? 1 : 0;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);

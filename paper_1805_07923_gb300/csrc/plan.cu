@@ -31,13 +31,20 @@ mlsdc_status check_aligned16(const char* where, std::initializer_list<std::pair<
 }
 
 bool pdl_enabled() {
-    // Off by default: measured inside the step's CUDA graph on GB300, the
-    // programmatic edges made the step slower (565 -> 465 steps/s split-BF16,
-    // 199 -> 115 float64), although isolated back-to-back launches gained.
+    // Off by default for every launch: measured inside the step's CUDA graph
+    // on GB300, programmatic edges on all launches made the step slower
+    // (565 -> 465 steps/s split-BF16, 199 -> 115 float64), although isolated
+    // back-to-back launches gained.  The tensor-core analysis alone takes
+    // them (PdlScope).
     static const bool on = [] {
         const char* v = std::getenv("MLSDC_PDL");
         return v && v[0] == '1';
     }();
+    return on;
+}
+
+bool& pdl_scope_flag() {
+    thread_local bool on = false;
     return on;
 }
 

@@ -183,6 +183,7 @@ mlsdc_status rhs_explicit_mp(sh_plan_t p, const swe_params* prm, const double* s
     }
     if (stage == 2 || stage < 0) {
         if (tc && stage_uses_tc(p, 2, b.members)) {
+            PdlScope pdl(true);  // its set-up and first table tiles overlap the FFT kernel's tail
             if ((s = tc_anal(p, prm->a, FE, state, 2.0 * prm->omega, b, fo, st)) != MLSDC_OK) return s;
         } else {
             MLSDC_LAUNCH("k_anal_rhs<float>",
