@@ -146,7 +146,18 @@ mlsdc_status rhs_explicit_mp(sh_plan_t p, const swe_params* prm, const double* s
     const MemberStrides ms{b.state_ms, 4 * fs, 5 * fs, b.fe_ms};
     const FourStride fo = four_out_layout(p->J, R, b.members >= kLatContigMembers);
     mlsdc_status s;
+    // A level whose FFT grid (one CTA per latitude and member) is at most
+    // 128 CTAs -- the coarse level of a single-member step -- runs every
+    // stage as a fraction of one wave: its synthesis and FFT kernels are
+    // then launched with programmatic serialisation too, their CTAs waiting
+    // on the SMs the predecessor leaves free.  Measured on the split-BF16
+    // step (150-step runs, one box): 1070 -> 1087 (synthesis), 1088 (FFT),
+    // 1101 steps/s (both); the synthesis at T170 as well (684 CTAs) 972,
+    // the FFT at both levels 994: there the successor's early CTAs take SMs
+    // the predecessor's later CTAs still need.
+    const bool small_level = (size_t)p->J * b.members <= 128;
     if (stage == 0 || stage < 0) {
+        PdlScope pdl(small_level);
         if (tc && stage_uses_tc(p, 0, b.members)) {
             if ((s = tc_synth(p, state, prm->a, b, st)) != MLSDC_OK) return s;
         } else {
@@ -169,6 +180,7 @@ mlsdc_status rhs_explicit_mp(sh_plan_t p, const swe_params* prm, const double* s
         }
     }
     if (stage == 1 || stage < 0) {
+        PdlScope pdl(small_level);
         if (fo.sj == 1) {  // latitude-contiguous output: two adjacent latitudes per CTA
             MLSDC_LAUNCH("k_grid_rhs<float, 2>",
                          launch_b(Body::GridF32x2, 0, 0, k_grid_rhs<float, 2>, dim3(p->J / 2, b.members), dim3(256),
